@@ -1,0 +1,544 @@
+"""Pins of the CPU oracle against facts fixed outside it: closed forms,
+brute force on tiny maps, textbook/library routines and published vectors.
+
+Each test names the passage of the paper (or the definition) it checks.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_15846_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RES = 0.05
+
+
+def ulp32(x):
+    x = np.float32(abs(x))
+    return float(np.spacing(x)) if x > 0 else float(np.spacing(np.float32(0)))
+
+
+# --------------------------------------------------------------------------
+# sin / cos used for headings and beams (Eq. 4)
+# --------------------------------------------------------------------------
+def test_sincos_within_two_ulp_of_fp64(oracle):
+    xs = np.concatenate([np.linspace(-math.pi - 0.2, math.pi + 0.2, 20001, dtype=np.float32),
+                         np.float32([0.0, -0.0, np.float32(math.pi), -np.float32(math.pi),
+                                     np.float32(math.pi / 2), np.float32(math.pi / 4)])])
+    worst = 0.0
+    for x in xs:
+        s, c = oracle.sincosf(float(x))
+        ts, tc = math.sin(float(x)), math.cos(float(x))
+        es = abs(float(s) - ts) / ulp32(ts)
+        ec = abs(float(c) - tc) / ulp32(tc)
+        worst = max(worst, es, ec)
+    assert worst <= 2.0, worst
+
+
+def test_sincos_special_values(oracle):
+    s, c = oracle.sincosf(0.0)
+    assert s == 0.0 and c == 1.0
+
+
+# --------------------------------------------------------------------------
+# counter-based reset RNG: SplitMix64 finaliser, published outputs
+# --------------------------------------------------------------------------
+def test_hash_matches_published_splitmix64(oracle):
+    gamma = 0x9E3779B97F4A7C15
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "splitmix64.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for s, k, want in rows:
+        s, k, want = int(s), int(k), int(want)
+        state = (s + (k - 1) * gamma) % (1 << 64)
+        assert oracle.hash64(state, 0, 0, 0) == want
+
+
+def test_hash_bits_uniform(oracle):
+    n = 20000
+    top = np.array([oracle.hash64(7, e, 3, 5) >> 60 for e in range(n)])
+    cnt = np.bincount(top, minlength=16)
+    chi2 = float(((cnt - n / 16) ** 2 / (n / 16)).sum())
+    assert chi2 < 45.0  # 15 dof, p ~ 1e-4
+
+
+# --------------------------------------------------------------------------
+# Ray casting (Eq. 4-5): exact grid traversal
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("direction", ["+x", "-x", "+y", "-y"])
+def test_axis_wall_range_is_analytic(oracle, direction):
+    n = 64
+    occ = np.zeros((n, n), np.uint8)
+    c = 50
+    x0, y0 = np.float32(10.37 * RES), np.float32(20.61 * RES)
+    xc = float(np.float32(x0 * np.float32(1 / RES)))
+    yc = float(np.float32(y0 * np.float32(1 / RES)))
+    if direction == "+x":
+        occ[:, c] = 1
+        d, want = (1.0, 0.0), (c - xc)
+    elif direction == "-x":
+        occ[:, 3] = 1
+        d, want = (-1.0, 0.0), (xc - 4)
+    elif direction == "+y":
+        occ[c, :] = 1
+        d, want = (0.0, 1.0), (c - yc)
+    else:
+        occ[5, :] = 1
+        d, want = (0.0, -1.0), (yc - 6)
+    r, hit, vis = oracle.cast_ray(occ, RES, float(x0), float(y0), d[0], d[1], 10.0)
+    assert abs(float(r) - want * RES) <= 2 * ulp32(want * RES)
+    assert hit >= 0 and occ.flat[hit] == 1
+    assert vis == int(abs(want)) + 2
+
+
+def test_empty_map_returns_max_range(oracle):
+    n = 256
+    occ = np.zeros((n, n), np.uint8)
+    x = y = n * RES / 2
+    for k in range(360):
+        a = -math.pi + (k + 0.5) * 2 * math.pi / 360
+        r, hit, _ = oracle.cast_ray(occ, RES, x, y, math.cos(a), math.sin(a), 4.0)
+        assert r == np.float32(4.0) and hit == -2
+
+
+def test_leaving_the_map_is_an_obstacle(oracle):
+    occ = np.zeros((16, 16), np.uint8)
+    r, hit, _ = oracle.cast_ray(occ, RES, 8.5 * RES, 8.5 * RES, 1.0, 0.0, 10.0)
+    assert hit == -1
+    assert abs(float(r) - 7.5 * RES) < 1e-6
+
+
+def _march(occ, xc, yc, dx, dy, rmax_c, step=1e-4):
+    """Brute force: sample the ray every `step` cells (float64); return the
+    first blocked cell (or -1 off-map, -2 none), its first sample's t and the
+    ordered list of distinct cells met before it."""
+    h, w = occ.shape
+    t = np.arange(0.0, rmax_c + step, step)
+    px = xc + t * dx
+    py = yc + t * dy
+    ci = np.floor(px).astype(np.int64)
+    cj = np.floor(py).astype(np.int64)
+    out = (ci < 0) | (cj < 0) | (ci >= w) | (cj >= h)
+    blocked = out.copy()
+    inside = ~out
+    blocked[inside] = occ[cj[inside], ci[inside]] != 0
+    idx = np.flatnonzero(blocked)
+    if idx.size == 0:
+        return -2, None, None
+    f = idx[0]
+    cid = -1 if out[f] else int(cj[f] * w + ci[f])
+    return cid, t[f], (ci[:f], cj[:f])
+
+
+def _near_corner(xc, yc, dx, dy, rmax_c, eps=2e-4):
+    """True when the ray passes within eps of a grid corner (tie cases)."""
+    t = np.linspace(0, rmax_c, int(rmax_c * 400) + 1)
+    px, py = xc + t * dx, yc + t * dy
+    fx = np.abs(px - np.round(px))
+    fy = np.abs(py - np.round(py))
+    return bool(np.any((fx < eps) & (fy < eps)))
+
+
+@pytest.mark.parametrize("size", [4, 8, 12, 16])
+def test_dda_agrees_with_supersampled_march(oracle, size):
+    rng = np.random.default_rng(size)
+    n_checked = 0
+    for trial in range(60):
+        occ = (rng.random((size, size)) < 0.25).astype(np.uint8)
+        free = np.argwhere(occ == 0)
+        if len(free) == 0:
+            continue
+        j, i = free[rng.integers(len(free))]
+        x = float(np.float32((i + rng.uniform(0.05, 0.95)) * RES))
+        y = float(np.float32((j + rng.uniform(0.05, 0.95)) * RES))
+        a = rng.uniform(-math.pi, math.pi)
+        dx, dy = float(np.float32(math.cos(a))), float(np.float32(math.sin(a)))
+        rmax = 0.4
+        r, hit, _ = oracle.cast_ray(occ, RES, x, y, dx, dy, rmax)
+        xc = float(np.float32(np.float32(x) * np.float32(1 / RES)))
+        yc = float(np.float32(np.float32(y) * np.float32(1 / RES)))
+        rmax_c = rmax / RES
+        if _near_corner(xc, yc, dx, dy, rmax_c):
+            continue
+        cid, tb, _ = _march(occ, xc, yc, dx, dy, rmax_c)
+        n_checked += 1
+        assert hit == cid, (trial, hit, cid)
+        if cid != -2:
+            assert abs(float(r) - tb * RES) <= 1e-4 * RES + 1e-6
+        else:
+            assert r == np.float32(rmax)
+    assert n_checked > 30
+
+
+def test_dda_invariants(oracle):
+    wl = W.config_small()
+    occ = wl.maps[0]
+    rng = np.random.default_rng(3)
+    free = np.argwhere(occ == 0)
+    for _ in range(300):
+        j, i = free[rng.integers(len(free))]
+        x, y = (i + 0.5) * RES, (j + 0.5) * RES
+        a = rng.uniform(-math.pi, math.pi)
+        r, hit, vis = oracle.cast_ray(occ, RES, x, y, math.cos(a), math.sin(a), 4.0)
+        assert 0.0 <= r <= np.float32(4.0)
+        if hit >= 0:
+            assert occ.flat[hit] == 1
+        assert vis >= 1
+
+
+def test_quarter_turn_permutes_beams(oracle):
+    """Rotating the map (and the position) by +90 deg while the heading stays
+    put maps beam k to beam k + K/4 (360 deg field of view, K divisible by 4):
+    beam k + K/4 of the unrotated robot points 90 deg left of beam k."""
+    rng = np.random.default_rng(11)
+    occ = W.make_map(5, 80, 64, 0.15)
+    H = occ.shape[0]
+    rot = np.zeros((occ.shape[1], H), np.uint8)  # W' = H, H' = W
+    jj, ii = np.nonzero(occ)
+    rot[ii, H - 1 - jj] = 1
+    K = 360
+    par = W.Params(goal_dmin=0.0, goal_dmax=1e9)
+    mk = lambda m: oracle.OracleSim([m], np.zeros(1, np.int32), np.full(1, K, np.int32),
+                                    np.zeros(1, np.int32), [W.DISC], 3.0, par, RES)
+    s0, s1 = mk(occ), mk(rot)
+    s0.reset(0)
+    s1.reset(0)
+    free = np.argwhere(occ == 0)
+    agree = total = 0
+    stay = np.array([[-1.0, 0.0]], np.float32)  # v = 0, w = 0
+    tried = 0
+    while total < 6 * K and tried < 200:
+        tried += 1
+        j, i = free[rng.integers(len(free))]
+        x, y = (i + 0.37) * RES, (j + 0.71) * RES
+        th = float(np.float32(rng.uniform(-math.pi, math.pi)))
+        xr, yr = H * RES - y, x
+        if oracle.footprint(occ, RES, W.DISC, x, y, th) or \
+                oracle.footprint(rot, RES, W.DISC, xr, yr, th):
+            continue
+        s0.set_state(0, np.array([[x, y, th, 0, 0, -50, -50, 100]], np.float32),
+                     np.zeros((1, 2), np.int32))
+        s1.set_state(0, np.array([[xr, yr, th, 0, 0, -50, -50, 100]], np.float32),
+                     np.zeros((1, 2), np.int32))
+        _, _, d0 = s0.step(stay)
+        _, _, d1 = s1.step(stay)
+        assert d0[0] == 0 and d1[0] == 0
+        r0, _, _ = s0.debug()
+        r1, _, _ = s1.debug()
+        for k in range(K):
+            total += 1
+            agree += abs(float(r0[k]) - float(r1[(k + K // 4) % K])) < 1e-4
+    assert total >= 6 * K
+    assert agree / total > 0.99, (agree, total)
+
+
+# --------------------------------------------------------------------------
+# Unicycle integration (Sec. 2.2.3): exact arc
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("w", [1.0, -1.5, 0.3, 1e-7])
+def test_constant_omega_follows_the_circle(oracle, w):
+    x0, y0, th0, v, dt = 2.0, 3.0, 0.4, 0.5, 0.1
+    x, y, th = np.float32(x0), np.float32(y0), np.float32(th0)
+    n = 20
+    for _ in range(n):
+        x, y, th = oracle.integrate(float(x), float(y), float(th), v, w, dt)
+    w32 = float(np.float32(w))
+    T = n * dt
+    if abs(w32) > 1e-6:
+        thn = th0 + w32 * T
+        xe = x0 + (v / w32) * (math.sin(thn) - math.sin(th0))
+        ye = y0 - (v / w32) * (math.cos(thn) - math.cos(th0))
+    else:
+        thn = th0 + w32 * T
+        xe, ye = x0 + v * T * math.cos(th0), y0 + v * T * math.sin(th0)
+    wrap = (thn + math.pi) % (2 * math.pi) - math.pi
+    assert abs(float(x) - xe) < 1e-5 and abs(float(y) - ye) < 1e-5
+    assert abs(float(th) - wrap) < 1e-5
+
+
+def test_zero_omega_is_a_straight_line(oracle):
+    x, y, th = oracle.integrate(1.0, 1.0, 0.0, 0.5, 0.0, 0.1)
+    assert abs(float(x) - 1.05) < 1e-7 and float(y) == 1.0 and float(th) == 0.0
+
+
+def test_heading_wraps_into_half_open_interval(oracle):
+    _, _, th = oracle.integrate(1.0, 1.0, 3.1, 0.0, 1.5, 0.1)
+    assert -math.pi <= float(th) < math.pi
+    assert abs(float(th) - (3.25 - 2 * math.pi)) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Footprint collision (Sec. 2.2.3, Tables 8-9): exact, vs float64 geometry
+# --------------------------------------------------------------------------
+def _disc_exact(occ, xc, yc, rc):
+    """float64: does the open disc meet a blocked closed cell?  Returns
+    (hit, margin) where margin is the smallest |dist - r| over cells near."""
+    h, w = occ.shape
+    hit, margin = False, np.inf
+    for j in range(int(math.floor(yc - rc)) - 1, int(math.ceil(yc + rc)) + 1):
+        for i in range(int(math.floor(xc - rc)) - 1, int(math.ceil(xc + rc)) + 1):
+            blocked = i < 0 or j < 0 or i >= w or j >= h or occ[j, i]
+            if not blocked:
+                continue
+            dx = max(i - xc, xc - (i + 1), 0.0)
+            dy = max(j - yc, yc - (j + 1), 0.0)
+            d = math.hypot(dx, dy)
+            margin = min(margin, abs(d - rc))
+            hit |= d < rc
+    return hit, margin
+
+
+def _rect_exact(occ, xc, yc, th, hl, hw):
+    """float64 separating-axis test of the open rectangle vs blocked cells."""
+    h, w = occ.shape
+    u = np.array([math.cos(th), math.sin(th)])
+    nrm = np.array([-math.sin(th), math.cos(th)])
+    c = np.array([xc, yc])
+    P = np.array([c + hl * u + hw * nrm, c - hl * u + hw * nrm,
+                  c - hl * u - hw * nrm, c + hl * u - hw * nrm])
+    axes = [np.array([1.0, 0.0]), np.array([0.0, 1.0]), u, nrm]
+    R = hl + hw + 2
+    hit, margin = False, np.inf
+    for j in range(int(math.floor(yc - R)), int(math.ceil(yc + R)) + 1):
+        for i in range(int(math.floor(xc - R)), int(math.ceil(xc + R)) + 1):
+            blocked = i < 0 or j < 0 or i >= w or j >= h or occ[j, i]
+            if not blocked:
+                continue
+            S = np.array([[i, j], [i + 1, j], [i + 1, j + 1], [i, j + 1]], float)
+            ov = min(min(max(P @ a), max(S @ a)) - max(min(P @ a), min(S @ a)) for a in axes)
+            margin = min(margin, abs(ov))
+            hit |= ov > 0
+    return hit, margin
+
+
+def test_disc_footprint_matches_exact_geometry(oracle):
+    rng = np.random.default_rng(5)
+    n = 0
+    for trial in range(400):
+        occ = (rng.random((12, 12)) < 0.2).astype(np.uint8)
+        x = float(np.float32(rng.uniform(0.0, 12 * RES)))
+        y = float(np.float32(rng.uniform(0.0, 12 * RES)))
+        got = oracle.footprint(occ, RES, W.DISC, x, y, 0.0)
+        xc = float(np.float32(np.float32(x) * np.float32(1 / RES)))
+        yc = float(np.float32(np.float32(y) * np.float32(1 / RES)))
+        rc = float(np.float32(np.float32(0.18) * np.float32(1 / RES)))
+        want, margin = _disc_exact(occ, xc, yc, rc)
+        if margin < 1e-5:
+            continue
+        n += 1
+        assert got == want, trial
+    assert n > 300
+
+
+def test_rect_footprint_matches_exact_geometry(oracle):
+    rng = np.random.default_rng(6)
+    n = 0
+    for trial in range(300):
+        occ = (rng.random((24, 24)) < 0.08).astype(np.uint8)
+        x = float(np.float32(rng.uniform(0.2, 24 * RES - 0.2)))
+        y = float(np.float32(rng.uniform(0.2, 24 * RES - 0.2)))
+        th = float(np.float32(rng.uniform(-math.pi, math.pi)))
+        got = oracle.footprint(occ, RES, W.RECT, x, y, th)
+        xc, yc = x / RES, y / RES
+        want, margin = _rect_exact(occ, xc, yc, th, 0.35 / RES, 0.155 / RES)
+        if margin < 1e-4:
+            continue
+        n += 1
+        assert got == want, trial
+    assert n > 200
+
+
+def test_disc_touching_a_wall_is_not_a_collision(oracle):
+    occ = np.zeros((16, 16), np.uint8)
+    occ[:, 10] = 1
+    # centre 3.6 cells left of the wall face at x = 10: the open disc touches
+    # the face only when rc == 3.6 exactly; 1e-3 cells inside must collide
+    rc = float(np.float32(np.float32(0.18) * np.float32(20.0)))
+    xc_touch = 10.0 - rc
+    assert not oracle.footprint(occ, RES, W.DISC, (xc_touch - 1e-3) * RES, 8.0 * RES, 0.0)
+    assert oracle.footprint(occ, RES, W.DISC, (xc_touch + 1e-3) * RES, 8.0 * RES, 0.0)
+
+
+# --------------------------------------------------------------------------
+# Reward, goal, collision, timeout (Eq. 3, Sec. 2.2.3, Table 7)
+# --------------------------------------------------------------------------
+def _one_env(oracle, occ, robot=W.DISC, params=None):
+    params = params or W.Params(goal_dmin=0.0, goal_dmax=1e9)
+    sim = oracle.OracleSim([occ], np.zeros(1, np.int32), np.full(1, 8, np.int32),
+                           np.zeros(1, np.int32), [robot], 2.0, params, RES)
+    sim.reset(1)
+    return sim
+
+
+def _set(sim, x, y, th, gx, gy, dprev, step=0):
+    f = np.array([[x, y, th, 0, 0, gx, gy, dprev]], np.float32)
+    i = np.array([[step, 0]], np.int32)
+    sim.set_state(1, f, i)
+
+
+def test_progress_reward_and_no_flags(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 1.5, 1.6, 0.5)
+    # action (1, 0): v = 0.5 m/s, w = 0 -> moves 0.05 m towards the goal
+    _, rew, done = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert done[0] == 0
+    assert abs(float(rew[0]) - (2.0 * 0.05 - 0.01)) < 1e-5
+
+
+def test_goal_reached_inclusive_threshold(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 1.21, 1.6, 0.21)
+    _, rew, done = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert done[0] & 1 and done[0] & 4 and not done[0] & 8 and not done[0] & 2
+    assert abs(float(rew[0]) - (2.0 * 0.05 - 0.01 + 10.0)) < 1e-5
+
+
+def test_goal_not_reached_just_outside(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 1.30, 1.6, 0.30)
+    _, rew, done = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert done[0] == 0  # d = 0.25 > 0.2
+
+
+def test_collision_flags_and_penalty(oracle):
+    occ = np.zeros((64, 64), np.uint8)
+    occ[:, 25] = 1  # wall face at x = 1.25 m
+    sim = _one_env(oracle, occ)
+    _set(sim, 1.06, 1.6, 0.0, 0.5, 1.6, 0.56)  # disc edge at 1.24, moves 0.05
+    _, rew, done = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert done[0] & 1 and done[0] & 8 and not done[0] & 4
+    assert abs(float(rew[0]) - (2.0 * (0.56 - 0.61) - 0.01 - 10.0)) < 1e-5
+
+
+def test_timeout_is_truncation_only(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 2.5, 1.6, 1.5, step=199)
+    _, _, done = sim.step(np.array([[-1.0, 0.0]], np.float32))  # v = 0
+    assert done[0] == 2
+
+
+def test_timeout_with_terminal_event_is_termination(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 1.21, 1.6, 0.21, step=199)
+    _, _, done = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert done[0] == 1 | 4
+
+
+def test_exclusive_reward_mode(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8),
+                   params=W.Params(goal_dmin=0.0, goal_dmax=1e9, reward_mode=1))
+    _set(sim, 1.0, 1.6, 0.0, 1.21, 1.6, 0.21)
+    _, rew, _ = sim.step(np.array([[1.0, 0.0]], np.float32))
+    assert float(rew[0]) == 10.0
+
+
+def test_final_observation_is_pre_reset(oracle):
+    sim = _one_env(oracle, np.zeros((64, 64), np.uint8))
+    _set(sim, 1.0, 1.6, 0.0, 1.21, 1.6, 0.21)
+    obs, _, done, fin = sim.step(np.array([[1.0, 0.0]], np.float32), want_final=True)
+    assert done[0] & 1
+    assert abs(float(fin[8]) - 0.16) < 1e-5  # goal distance at the terminal pose
+    f, i, _ = sim.get_state()
+    assert i[0, 0] == 0 and i[0, 1] == 1  # counters cleared, episode advanced
+    assert abs(float(obs[8]) - float(f[0, 7])) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Reset (Sec. 2.2.3 sparse reset)
+# --------------------------------------------------------------------------
+def test_spawnable_cells_and_components_match_library_labelling(oracle):
+    scipy_ndimage = pytest.importorskip("scipy.ndimage")
+    wl = W.config_small()
+    sim = oracle.OracleSim.from_workload(wl)
+    occ = wl.maps[0]
+    rc = float(np.float32(np.float32(0.18) * np.float32(1 / RES)))
+    ok = np.zeros(occ.shape, bool)
+    for j in range(occ.shape[0]):
+        for i in range(occ.shape[1]):
+            hit, margin = _disc_exact(occ, i + 0.5, j + 0.5, rc)
+            ok[j, i] = not hit
+    labels = sim.comp_labels(0)
+    assert ((labels >= 0) == ok).all()
+    ref, n = scipy_ndimage.label(ok)  # 4-connectivity by default
+    assert n == len(np.unique(labels[labels >= 0]))
+    for lab in range(1, n + 1):
+        assert len(np.unique(labels[ref == lab])) == 1
+
+
+def test_reset_is_deterministic_and_valid(oracle):
+    wl = W.config_small()
+    s1 = oracle.OracleSim.from_workload(wl)
+    s2 = oracle.OracleSim.from_workload(wl)
+    o1, o2 = s1.reset(42), s2.reset(42)
+    assert np.array_equal(o1, o2)
+    f, i, _ = s1.get_state()
+    occ = wl.maps[0]
+    labels = s1.comp_labels(0)
+    for e in range(wl.n_envs):
+        x, y, th, v, w, gx, gy, dprev = f[e]
+        assert not oracle.footprint(occ, RES, W.DISC, float(x), float(y), float(th))
+        ci, cj = int(x / RES), int(y / RES)
+        gi, gj = int(gx / RES), int(gy / RES)
+        assert labels[cj, ci] >= 0 and labels[cj, ci] == labels[gj, gi]
+        assert v == 0 and w == 0 and i[e, 0] == 0 and i[e, 1] == 0
+        assert -math.pi <= th < math.pi
+    o3 = oracle.OracleSim.from_workload(wl).reset(43)
+    assert not np.array_equal(o1, o3)
+
+
+def test_goal_distance_in_band_when_possible(oracle):
+    wl = W.config_throughput(n_envs=64, n_maps=2)
+    sim = oracle.OracleSim.from_workload(wl)
+    sim.reset(9)
+    f, _, _ = sim.get_state()
+    d = np.hypot(f[:, 5] - f[:, 0], f[:, 6] - f[:, 1])
+    assert ((d >= 2.0 - 1e-5) & (d <= 8.0 + 1e-5)).mean() > 0.95
+
+
+def test_spawn_cells_uniform_over_spawnable_list(oracle):
+    occ = W.make_map(3, 24, 24, 0.10)
+    n_env = 256
+    sim = oracle.OracleSim([occ], np.zeros(n_env, np.int32), np.full(n_env, 4, np.int32),
+                           np.zeros(n_env, np.int32), [W.DISC], 1.0,
+                           W.Params(goal_dmin=0.0, goal_dmax=1e9), RES)
+    counts = {}
+    for seed in range(40):
+        sim.reset(seed)
+        f, _, _ = sim.get_state()
+        for x, y in f[:, :2]:
+            c = (int(x / RES), int(y / RES))
+            counts[c] = counts.get(c, 0) + 1
+    n_sp = sim.spawn_count(0, 0)
+    assert len(counts) <= n_sp
+    total = n_env * 40
+    obs_c = np.array(list(counts.values()) + [0] * (n_sp - len(counts)), float)
+    exp = total / n_sp
+    chi2 = float(((obs_c - exp) ** 2 / exp).sum())
+    dof = n_sp - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+# --------------------------------------------------------------------------
+# Free-running invariants on the small workload
+# --------------------------------------------------------------------------
+def test_free_running_invariants(oracle):
+    wl = W.config_small()
+    sim = oracle.OracleSim.from_workload(wl)
+    obs = sim.reset(1)
+    acts = W.uniform_actions(1, 200, wl.n_envs)
+    K = 180
+    prev_ep = np.zeros(wl.n_envs, np.int64)
+    for t in range(200):
+        obs, rew, done = sim.step(acts[t])
+        o = obs.reshape(wl.n_envs, K + 4)
+        assert (o[:, :K] >= 0).all() and (o[:, :K] <= np.float32(4.0)).all()
+        f, i, _ = sim.get_state()
+        ended = (done & 3) != 0
+        assert (i[ended, 0] == 0).all()
+        assert (i[ended, 1] == prev_ep[ended] + 1).all()
+        assert (i[~ended, 1] == prev_ep[~ended]).all()
+        assert ((done & 1) != 0).sum() == (((done & 4) != 0) | ((done & 8) != 0)).sum()
+        assert not ((done & 1) & ((done & 2) >> 1)).any()
+        prev_ep = i[:, 1].astype(np.int64)
