@@ -1,0 +1,342 @@
+"""Throughput benchmark of the batched bitmap simulator step.
+
+Workload: 4096 envs over 16 seeded 256x256 maps (10-25 % boxes, discs and
+corridor walls, 0.05 m cells), 360 beams over 360 deg, r_max 6 m, disc robot,
+goals 2-8 m, uniform random actions, auto-reset.  One step = one fused launch
+that advances every env (action decode, arc integration, footprint, reward,
+flags, sparse reset, 360-beam scan, observation).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank simulates its own
+4096 envs on its own GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s (360-beam scan)"
+UNIT = "env-steps/s"
+SEED = 12345
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT = 148
+SM_MAX_MHZ = 2032.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank: int):
+    from paper_2606_15846_b300 import workloads as W
+    # each rank simulates its own 4096 envs on its own 16 maps (weak scaling)
+    return W.config_throughput(seed0=100 + 1000 * rank)
+
+
+def cpu_baseline(wl, seconds: float = 12.0):
+    """The oracle, as it stands, on all host cores over a bounded sample of the
+    same workload: full 4096-env steps until ~`seconds` have elapsed."""
+    from oracle import oracle
+    from paper_2606_15846_b300 import workloads as W
+    cores = os.cpu_count() or 1
+    ref = oracle.OracleSim.from_workload(wl, threads=cores)
+    ref.reset(SEED)
+    acts = W.uniform_actions(SEED, 64, wl.n_envs)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        ref.step(acts[n % 64])
+        n += 1
+        el = time.perf_counter() - t0
+        if (el > seconds and n >= 3) or n >= 64:
+            break
+    return {"value": wl.n_envs * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} full steps of the {wl.n_envs}-env workload (C oracle, OpenMP over "
+                      f"envs, {cores} threads), {el:.1f} s"}
+
+
+def _sub_workload(wl, n):
+    """The first n envs of a workload (same maps, beams and robots)."""
+    import dataclasses
+    return dataclasses.replace(wl, env_map=wl.env_map[:n].copy(),
+                               env_beams=wl.env_beams[:n].copy(),
+                               env_robot=wl.env_robot[:n].copy())
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only).
+    Each step is one oracle step over a bounded sample of the workload's envs,
+    sized from a probe so that warm-up plus timed steps take about 2 minutes."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2606_15846_b300 import workloads as W
+    wl = make_workload(0)
+    cores = os.cpu_count() or 1
+    probe = oracle.OracleSim.from_workload(wl, threads=cores)
+    probe.reset(SEED)
+    acts = W.uniform_actions(SEED, 64, wl.n_envs)
+    t0 = time.perf_counter()
+    probe.step(acts[0])
+    probe.step(acts[1])
+    per_env_s = (time.perf_counter() - t0) / 2 / wl.n_envs
+    del probe
+    budget_s = 120.0
+    n = int(budget_s / max(args.steps + args.warmup, 1) / max(per_env_s, 1e-12))
+    n = max(min(n, wl.n_envs), min(64, wl.n_envs))
+    sub = _sub_workload(wl, n)
+    ref = oracle.OracleSim.from_workload(sub, threads=cores)
+    ref.reset(SEED)
+    for t in range(args.warmup):
+        ref.step(acts[t % 64, :n])
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        ref.step(acts[(args.warmup + t) % 64, :n])
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n_envs": wl.n_envs, "n_maps": len(wl.maps),
+                   "map": "256x256", "beams": 360, "max_range_m": wl.max_range},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: the first {n} of the {wl.n_envs} envs "
+                                   f"(C oracle, OpenMP over envs, {cores} threads); "
+                                   f"{args.steps} timed steps after {args.warmup} warm-up"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2606_15846_b300 import flashnav
+    from paper_2606_15846_b300 import workloads as W
+
+    wl = make_workload(rank)
+    E = wl.n_envs
+    sim = flashnav.NavSim.from_workload(wl, device=local)
+    stream = torch.cuda.current_stream(dev)
+    total_steps = args.warmup + args.steps
+    # inputs resident in HBM before the timed region
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(SEED + rank)
+    actions = (torch.rand(total_steps, E, 2, device=dev, generator=gen) * 2 - 1).contiguous()
+    obs = sim.new_obs()
+    rew = torch.empty(E, device=dev)
+    done = torch.empty(E, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sim.reset(SEED + rank, obs)
+    for t in range(args.warmup):
+        sim.step(actions[t], obs, rew, done)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for t in range(args.steps):
+            flush.fill_(float(t))  # L2 flush between timed steps (untimed)
+            starts[t].record(stream)
+            sim.step(actions[args.warmup + t], obs, rew, done)
+            ends[t].record(stream)
+        barrier()
+        wall = time.perf_counter() - w0
+    sim.sync(60000)
+    dur_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = float(np.sum(dur_ms))
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = world * E * args.steps / (step_ms / 1e3)
+
+    # work counted on an identical replay (same seed and actions): cell visits
+    sim.reset(SEED + rank, obs)
+    for t in range(args.warmup):
+        sim.step(actions[t], obs, rew, done)
+    sim.set_stats(True)
+    for t in range(args.steps):
+        sim.step(actions[args.warmup + t], obs, rew, done)
+    visits, rays = sim.stats()
+    sim.set_stats(False)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e_steps = min(args.steps, 2000)
+    h_act = torch.empty(e2e_steps, E, 2, dtype=torch.float32, pin_memory=True)
+    h_act.copy_(actions[args.warmup:args.warmup + e2e_steps].cpu())
+    h_obs = torch.empty(sim.obs_size, dtype=torch.float32, pin_memory=True)
+    h_rew = torch.empty(E, dtype=torch.float32, pin_memory=True)
+    h_done = torch.empty(E, dtype=torch.uint8, pin_memory=True)
+    sim.reset(SEED + rank, obs)
+    for t in range(args.warmup):
+        sim.step(actions[t], obs, rew, done)
+    barrier()
+    e2e_s = 0.0
+    for t in range(e2e_steps):
+        flush.fill_(float(t))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step_host_ptrs(h_act[t].data_ptr(), h_obs.data_ptr(), h_rew.data_ptr(),
+                           h_done.data_ptr())
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * E * e2e_steps / e2e_s
+
+    if rank == 0:
+        peaks, src = _peaks()
+        sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+        mean_launch_s = step_ms / 1e3 / args.steps
+        visits_per_launch = visits / args.steps
+        achieved = visits_per_launch / mean_launch_s / 1e9
+        # one visit = one 32-bit shared-memory word gathered per lane; the SM
+        # serves 32 such lanes per clock
+        peak = SM_COUNT * 32 * sm_mhz * 1e6 / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n_envs": E, "n_maps": len(wl.maps),
+                       "map": "256x256", "beams": 360, "max_range_m": wl.max_range,
+                       "robot": "disc r=0.18 m", "actions": "uniform [-1,1]^2",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"env shards x{world}"},
+            "beam_casts_per_s": world * rays / (step_ms / 1e3),
+            "cell_visits_per_s": world * visits / (step_ms / 1e3),
+            "visits_per_step": visits_per_launch,
+            "timed_region_wall_s": wall,
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "Gvisit/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
+                                        f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
+                         "kernel": "step_kernel<false>"},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": E * 2 * 4,
+                    "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,
+                    "steps": e2e_steps},
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * flashnav.h -- C ABI of the B300 batched bitmap navigation simulator
+ * (FlashNav, Sec. 2.2: vectorised bitmap simulator; Eq. 1-7; Tables 7-9).
+ *
+ * One handle simulates n_envs independent goal-navigation environments on
+ * one CUDA device.  Every call is asynchronous on the handle's stream unless
+ * it says otherwise.  Device pointers ("*_dev") are caller-owned CUDA global
+ * memory (for example torch tensors); host pointers ("*_host") are caller-
+ * owned host memory.  The library owns the packed bitmaps, the per-map spawn
+ * tables and the per-env state (structure of arrays) in device memory.
+ *
+ * Errors: every int-returning call returns NAV_OK (0) or a negative NAV_E_*
+ * code and records a message readable with nav_last_error().  No C++
+ * exception crosses this boundary.  Kernels never trap: an anomaly found on
+ * the device sets a status word that nav_sync() reports as NAV_E_INTERNAL.
+ *
+ * Geometry (Sec. 2.2.1): a map is a W x H occupancy bitmap with square cells
+ * of `resolution` metres; cell (i, j) covers [i, i+1] x [j, j+1] in cell
+ * units, i = column (x), j = row (y); the world origin is the corner of cell
+ * (0, 0).  Positions outside the map are obstacles.
+ */
+#ifndef FLASHNAV_H
+#define FLASHNAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    NAV_OK = 0,
+    NAV_E_INVAL = -1,    /* bad argument (null pointer, size, range)        */
+    NAV_E_CUDA = -2,     /* a CUDA runtime call failed                       */
+    NAV_E_NOMEM = -3,    /* device or host allocation failed                 */
+    NAV_E_NOSPAWN = -4,  /* a map has no cell where the robot fits           */
+    NAV_E_INTERNAL = -5, /* the device status word reported an anomaly       */
+    NAV_E_TIMEOUT = -6   /* nav_sync's deadline passed before the GPU was done */
+};
+
+typedef struct nav_handle nav_handle;
+
+/* Occupancy map (Sec. 2.2.1 binary bitmap).  occ: host, row-major H x W,
+ * nonzero = occupied.  Copied and packed 1 bit per cell by nav_create. */
+typedef struct {
+    int width, height;
+    float resolution;
+    const uint8_t *occ;
+} nav_map;
+
+/* Robot preset (Sec. 2.2.1 presets; Tables 8-9).  shape 0 = disc of
+ * `radius`; shape 1 = rectangle `length` (along the heading) x `width`.
+ * Normalised actions a in [-1, 1]^2 map affinely onto [v_min, v_max] (m/s)
+ * and [w_min, w_max] (rad/s). */
+typedef struct {
+    int shape;
+    float radius, length, width;
+    float v_min, v_max, w_min, w_max;
+} nav_robot;
+
+/* Episode constants (Table 7).  reward_mode 0: r = c_progress (d_prev - d)
+ * - step_penalty + r_goal [goal] - r_coll [collision]; reward_mode 1: the
+ * exclusive cases of Eq. 3 (goal, else collision, else progress).
+ * fov_deg: beam fan, beam k at alpha_k = -fov/2 + (k + 1/2) fov / K (Eq. 4).
+ * Goals are drawn with distance in [goal_dmin, goal_dmax] m when possible.
+ * n_dyn moving discs per env (radius dyn_radius, speed <= dyn_speed_max,
+ * spawned >= dyn_min_sep from the robot) are stamped into a per-env layer. */
+typedef struct {
+    float dt, goal_tol, c_progress, step_penalty, r_goal, r_coll;
+    int horizon;
+    float goal_dmin, goal_dmax, fov_deg;
+    int n_dyn;
+    float dyn_radius, dyn_speed_max, dyn_min_sep;
+    int reward_mode;
+} nav_params;
+
+/* Fills the Table 7 defaults: dt 0.1 s, goal 0.2 m, c1 = 2, penalty 0.01,
+ * +10 / -10, horizon 200, goals 2-8 m, 360 deg, no moving discs. */
+void nav_default_params(nav_params *p);
+
+/* Creates a simulator (Sec. 2.2.1 batched state).  All envs use n_beams beams
+ * and robots[0]; env e uses map e mod n_maps.  max_range in metres (Eq. 5's
+ * r_max).  params may be NULL (defaults).  Host arrays are copied.  Returns
+ * NAV_E_NOSPAWN if a used map has no free cell for the robot.  Synchronous. */
+int nav_create(const nav_map *maps, int n_maps, int n_envs, int n_beams, float max_range,
+               const nav_robot *robot, const nav_params *params, nav_handle **out);
+
+/* Like nav_create with per-env arrays (each host, length n_envs, or NULL for
+ * the default): env_map (default e mod n_maps), env_beams (required),
+ * env_robot index into robots[0..n_robots) (default 0).  Envs of one handle
+ * may mix map sizes, beam counts and robot shapes (one launch steps them). */
+int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int *env_beams,
+                  const int *env_robot, int n_envs, float max_range, const nav_robot *robots,
+                  int n_robots, const nav_params *params, nav_handle **out);
+
+/* Binds a cudaStream_t (NULL = the legacy default stream). */
+int nav_set_stream(nav_handle *h, void *cuda_stream);
+
+/* Observation layout: env e's row starts at offsets[e] and holds
+ * [K_e clipped ranges, goal distance, goal bearing, v, w] (Eq. 1 with the raw
+ * K_e-beam scan).  offsets has n_envs + 1 entries (host); offsets[n_envs] is
+ * the total float count.  With one beam count K, offsets[e] = e (K + 4). */
+int nav_obs_offsets(const nav_handle *h, int64_t *offsets_host);
+int nav_num_envs(const nav_handle *h);
+int64_t nav_obs_size(const nav_handle *h);
+
+/* Resets every env (episode 0) from the counter RNG keyed by seed and writes
+ * the first observation to obs_dev (nav_obs_size floats). */
+int nav_reset(nav_handle *h, uint64_t seed, float *obs_dev);
+
+/* One simulator step (Eq. 7): A_t -> X_{t+1} -> R_{t+1} -> (c, r, delta)
+ * -> O_{t+1} -> O~_{t+1}.
+ *   actions_dev   [n_envs][2] float, normalised, clamped to [-1, 1]
+ *   obs_dev       [nav_obs_size] float, post-reset observation O~_{t+1}
+ *   reward_dev    [n_envs] float
+ *   done_dev      [n_envs] uint8: bit0 terminated (goal or collision),
+ *                 bit1 truncated (horizon reached without a terminal event),
+ *                 bit2 goal, bit3 collision
+ *   final_obs_dev NULL, or [nav_obs_size] float: for envs that finished this
+ *                 step the pre-reset observation O_{t+1}; other rows untouched.
+ * Finished envs are reset in place (Sec. 2.2.3 sparse reset). */
+int nav_step(nav_handle *h, const float *actions_dev, float *obs_dev, float *reward_dev,
+             uint8_t *done_dev, float *final_obs_dev);
+
+/* nav_step with host buffers: copies the actions in, steps, copies obs,
+ * reward, done (and final obs when non-NULL) back, and waits for the stream.
+ * Device staging buffers are allocated on the first call and kept. */
+int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host,
+                  float *reward_host, uint8_t *done_host, float *final_obs_host);
+
+/* Waits for the handle's stream for at most timeout_ms (<= 0: no limit), then
+ * checks the device status word.  NAV_E_TIMEOUT if the deadline passed. */
+int nav_sync(nav_handle *h, int timeout_ms);
+
+/* State exchange for parity checks and checkpoints (synchronous, host):
+ *   f8  [n_envs][8] float: x, y, theta, v, w, goal_x, goal_y, d_prev
+ *   i2  [n_envs][2] int32: step counter, episode counter
+ *   dyn [n_envs][n_dyn][4] float (x, y, vx, vy) or NULL
+ * nav_set_state also sets the RNG seed used by later resets. */
+int nav_get_state(nav_handle *h, float *f8_host, int32_t *i2_host, float *dyn_host);
+int nav_set_state(nav_handle *h, uint64_t seed, const float *f8_host, const int32_t *i2_host,
+                  const float *dyn_host);
+
+/* Debug capture of the last scan of each env (the post-reset scan for envs
+ * reset this step): enable once, then after a step read (synchronous) the
+ * unclipped ranges (m), hit ids (j*W+i occupied cell, -1 left the map, -2
+ * reached r_max) and cell visits per beam, each [sum_e K_e] (host). */
+int nav_set_debug(nav_handle *h, int enable);
+int nav_get_debug(nav_handle *h, float *ranges_host, int32_t *hits_host,
+                  uint32_t *visits_host);
+
+/* Work counters: with stats enabled every step adds the number of bitmap
+ * cells the ray casts looked up (one visit = one cell of Amanatides-Woo
+ * traversal) and the number of rays cast.  nav_get_stats is synchronous. */
+int nav_set_stats(nav_handle *h, int enable);
+int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
+
+/* Launch shape: envs per CTA tile (1..32) and threads per CTA (64..1024,
+ * multiple of 32); smem_map_bytes caps the bitmap size staged into shared
+ * memory (larger maps are read through L1/L2).  0 keeps the current value. */
+int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes);
+int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads,
+                   int *smem_map_bytes);
+
+const char *nav_last_error(const nav_handle *h);
+void nav_free(nav_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,774 @@
+// Host runtime of the C ABI declared in include/flashnav.h: argument checks,
+// bit-packing of the maps, per-(map, robot) spawn tables, beam tables, the
+// env -> tile schedule, device memory and the launches.
+//
+// Compiled with -ffp-contract=off: the spawnability test below decides which
+// cells a reset may draw, so its binary32 arithmetic must round exactly like
+// the device footprint test it stands for.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nav_internal.h"
+
+using namespace flashnav;
+
+namespace {
+
+struct DevArena {
+    std::vector<void *> ptrs;
+    ~DevArena() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T> cudaError_t alloc(T **out, size_t count) {
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(p);
+        *out = static_cast<T *>(p);
+        return cudaSuccess;
+    }
+    template <class T> cudaError_t upload(T **out, const std::vector<T> &v) {
+        cudaError_t e = alloc(out, v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+};
+
+struct CsHost {
+    std::vector<int> spawn, spawn_comp, comp_start, comp_count, comp_cells;
+};
+
+// Cells of row j met by the open disc (xc, yc, rc) in cell units.
+bool disc_row_host(float xc, float yc, float rc, int j, int &i0, int &i1) {
+    const float fj = (float)j;
+    float dy = 0.0f;
+    if (yc < fj) dy = fj - yc;
+    else if (yc > fj + 1.0f) dy = yc - (fj + 1.0f);
+    if (!(dy < rc)) return false;
+    const float hh = std::sqrt(rc * rc - dy * dy);
+    i0 = (int)std::floor(xc - hh);
+    i1 = (int)std::ceil(xc + hh) - 1;
+    return true;
+}
+
+// Spawnable cells: the circumscribed disc of the footprint at the cell centre
+// meets no blocked cell.  Components are 4-connected sets of spawnable cells;
+// goals are drawn from the spawn cell's component.  Row prefix counts make
+// each row-span test O(1).
+void build_cspace(const uint8_t *occ, int W, int H, float res, float inv_res, float rcirc_m,
+                  CsHost &cs) {
+    std::vector<int> pref((size_t)H * (W + 1), 0);
+    for (int j = 0; j < H; ++j) {
+        int *p = &pref[(size_t)j * (W + 1)];
+        for (int i = 0; i < W; ++i) p[i + 1] = p[i] + (occ[(size_t)j * W + i] != 0);
+    }
+    const float rc = rcirc_m * inv_res;
+    std::vector<uint8_t> ok((size_t)W * H, 0);
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            const float xc = (((float)i + 0.5f) * res) * inv_res;
+            const float yc = (((float)j + 0.5f) * res) * inv_res;
+            const int r0 = (int)std::floor(yc - rc);
+            const int r1 = (int)std::ceil(yc + rc) - 1;
+            bool blocked = false;
+            for (int r = r0; r <= r1 && !blocked; ++r) {
+                int a, b;
+                if (!disc_row_host(xc, yc, rc, r, a, b) || a > b) continue;
+                if (r < 0 || r >= H || a < 0 || b >= W) blocked = true;
+                else blocked = pref[(size_t)r * (W + 1) + b + 1] - pref[(size_t)r * (W + 1) + a] > 0;
+            }
+            ok[(size_t)j * W + i] = !blocked;
+        }
+    std::vector<int> comp((size_t)W * H, -1);
+    std::vector<int> stack;
+    int ncomp = 0;
+    for (size_t c0 = 0; c0 < ok.size(); ++c0) {
+        if (!ok[c0]) continue;
+        cs.spawn.push_back((int)c0);
+        if (comp[c0] >= 0) continue;
+        comp[c0] = ncomp;
+        stack.assign(1, (int)c0);
+        while (!stack.empty()) {
+            const int c = stack.back();
+            stack.pop_back();
+            const int ci = c % W, cj = c / W;
+            const int nb[4] = {ci > 0 ? c - 1 : -1, ci + 1 < W ? c + 1 : -1, cj > 0 ? c - W : -1,
+                               cj + 1 < H ? c + W : -1};
+            for (int t = 0; t < 4; ++t)
+                if (nb[t] >= 0 && ok[nb[t]] && comp[nb[t]] < 0) {
+                    comp[nb[t]] = ncomp;
+                    stack.push_back(nb[t]);
+                }
+        }
+        ++ncomp;
+    }
+    cs.comp_count.assign(ncomp, 0);
+    for (int c : cs.spawn) cs.comp_count[comp[c]]++;
+    cs.comp_start.assign(ncomp, 0);
+    for (int k = 1; k < ncomp; ++k) cs.comp_start[k] = cs.comp_start[k - 1] + cs.comp_count[k - 1];
+    cs.comp_cells.assign(cs.spawn.size(), 0);
+    std::vector<int> fill(ncomp, 0);
+    cs.spawn_comp.resize(cs.spawn.size());
+    for (size_t s = 0; s < cs.spawn.size(); ++s) {
+        const int id = comp[cs.spawn[s]];
+        cs.spawn_comp[s] = id;
+        cs.comp_cells[cs.comp_start[id] + fill[id]++] = cs.spawn[s];
+    }
+}
+
+float circ_radius(const nav_robot &r) {
+    if (r.shape == 0) return r.radius;
+    return 0.5f * std::sqrt(r.length * r.length + r.width * r.width);
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+} // namespace
+
+struct nav_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_envs = 0, n_maps = 0, n_robots = 0, max_k = 0;
+    float max_range = 0.0f;
+    nav_params par{};
+    std::vector<int64_t> obs_off, ray_off;
+    std::vector<int> env_map, env_tab, env_k;
+    std::vector<MapDev> maps;
+    int tile_envs = 8, block_threads = 256, smem_map_bytes = 96 * 1024;
+    int max_map_words = 0;
+    int debug = 0, stats = 0;
+    uint64_t seed = 0;
+    std::string err;
+    DevArena arena;
+    StepArgs a{};
+    TileDev *d_tiles = nullptr;
+    int *d_perm = nullptr;
+    int tiles_cap = 0;
+    unsigned long long *d_stats = nullptr;
+    float *d_dbg_range = nullptr;
+    int *d_dbg_hit = nullptr;
+    unsigned *d_dbg_vis = nullptr;
+    // nav_step_host staging
+    float *h_act = nullptr, *h_obs = nullptr, *h_rew = nullptr, *h_fin = nullptr;
+    unsigned char *h_done = nullptr;
+};
+
+namespace {
+
+int fail(nav_handle *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(nav_handle *h, cudaError_t e, const char *what) {
+    return fail(h, NAV_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Groups envs by (map, beam table) and cuts each group into tiles of at most
+// tile_envs envs; the tile list runs over the largest maps first so that the
+// longest CTAs start early.
+int build_tiles(nav_handle *h) {
+    const int E = h->n_envs;
+    std::vector<int> perm(E);
+    for (int e = 0; e < E; ++e) perm[e] = e;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+        const long long ka = (long long)h->env_map[a] * 4096 + h->env_tab[a];
+        const long long kb = (long long)h->env_map[b] * 4096 + h->env_tab[b];
+        return ka < kb;
+    });
+    std::vector<TileDev> tiles;
+    int s = 0;
+    while (s < E) {
+        int t = s;
+        while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
+               h->env_tab[perm[t]] == h->env_tab[perm[s]])
+            ++t;
+        for (int b = s; b < t; b += h->tile_envs) {
+            TileDev td;
+            td.map = h->env_map[perm[s]];
+            td.tab = h->env_tab[perm[s]];
+            td.env_begin = b;
+            td.env_count = std::min(h->tile_envs, t - b);
+            tiles.push_back(td);
+        }
+        s = t;
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &x, const TileDev &y) {
+        const long long wx = (long long)h->maps[x.map].n_words * h->env_k[perm[x.env_begin]];
+        const long long wy = (long long)h->maps[y.map].n_words * h->env_k[perm[y.env_begin]];
+        return wx > wy;
+    });
+    cudaError_t e;
+    if ((int)tiles.size() > h->tiles_cap) {
+        e = h->arena.alloc(&h->d_tiles, tiles.size());
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(tiles)");
+        h->tiles_cap = (int)tiles.size();
+    }
+    if (!h->d_perm) {
+        e = h->arena.alloc(&h->d_perm, (size_t)E);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(perm)");
+    }
+    e = cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_perm, perm.data(), (size_t)E * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(tiles)");
+    h->a.tiles = h->d_tiles;
+    h->a.perm = h->d_perm;
+    h->a.n_tiles = (int)tiles.size();
+    return NAV_OK;
+}
+
+void set_smem_cap(nav_handle *h) {
+    int cap_words = h->smem_map_bytes / 4;
+    // stage every map that fits: the region is sized for the largest of them
+    int used = 0;
+    for (const MapDev &m : h->maps)
+        if (m.n_words <= cap_words) used = std::max(used, m.n_words);
+    h->a.smem_map_words = used;
+}
+
+int launch(nav_handle *h) {
+    int rc = launch_step(h->a, h->block_threads, h->tile_envs, h->stream);
+    if (rc != 0) return cuda_fail(h, (cudaError_t)rc, "step kernel launch");
+    return NAV_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void nav_default_params(nav_params *p) {
+    if (!p) return;
+    p->dt = 0.1f;
+    p->goal_tol = 0.2f;
+    p->c_progress = 2.0f;
+    p->step_penalty = 0.01f;
+    p->r_goal = 10.0f;
+    p->r_coll = 10.0f;
+    p->horizon = 200;
+    p->goal_dmin = 2.0f;
+    p->goal_dmax = 8.0f;
+    p->fov_deg = 360.0f;
+    p->n_dyn = 0;
+    p->dyn_radius = 0.18f;
+    p->dyn_speed_max = 0.5f;
+    p->dyn_min_sep = 1.0f;
+    p->reward_mode = 0;
+}
+
+int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int *env_beams,
+                  const int *env_robot, int n_envs, float max_range, const nav_robot *robots,
+                  int n_robots, const nav_params *params, nav_handle **out) {
+    if (!out) return NAV_E_INVAL;
+    *out = nullptr;
+    if (!maps || n_maps <= 0 || !env_beams || n_envs <= 0 || !robots || n_robots <= 0 ||
+        !finite_pos(max_range))
+        return NAV_E_INVAL;
+    nav_handle *h = new (std::nothrow) nav_handle();
+    if (!h) return NAV_E_NOMEM;
+    auto bail = [&](int code) {
+        if (code != NAV_OK) {
+            // keep the message for the caller only through stderr: the handle dies
+            std::fprintf(stderr, "nav_create: %s\n", h->err.c_str());
+            delete h;
+        }
+        return code;
+    };
+    h->n_envs = n_envs;
+    h->n_maps = n_maps;
+    h->n_robots = n_robots;
+    h->max_range = max_range;
+    if (params) h->par = *params;
+    else nav_default_params(&h->par);
+    const nav_params &P = h->par;
+    if (!finite_pos(P.dt) || !(P.goal_tol >= 0.0f) || P.horizon <= 0 || P.n_dyn < 0 ||
+        P.n_dyn > kMaxDyn || !finite_pos(P.fov_deg) || P.fov_deg > 360.0f ||
+        !(P.goal_dmin <= P.goal_dmax) || (P.reward_mode != 0 && P.reward_mode != 1))
+        return bail(fail(h, NAV_E_INVAL, "bad nav_params"));
+    if (P.n_dyn > 0 && (!finite_pos(P.dyn_radius) || !(P.dyn_speed_max >= 0.0f)))
+        return bail(fail(h, NAV_E_INVAL, "bad moving-disc parameters"));
+    for (int r = 0; r < n_robots; ++r) {
+        const nav_robot &rb = robots[r];
+        const bool shape_ok = (rb.shape == 0 && finite_pos(rb.radius)) ||
+                              (rb.shape == 1 && finite_pos(rb.length) && finite_pos(rb.width));
+        if (!shape_ok || !(rb.v_min <= rb.v_max) || !(rb.w_min <= rb.w_max) ||
+            !std::isfinite(rb.v_min) || !std::isfinite(rb.v_max) || !std::isfinite(rb.w_min) ||
+            !std::isfinite(rb.w_max))
+            return bail(fail(h, NAV_E_INVAL, "bad nav_robot " + std::to_string(r)));
+    }
+    // maps: validate and pack (free bits, one blocked padding cell per side)
+    std::vector<uint32_t> words;
+    for (int m = 0; m < n_maps; ++m) {
+        const nav_map &mp = maps[m];
+        if (!mp.occ || mp.width <= 0 || mp.height <= 0 || mp.width > 16384 || mp.height > 16384 ||
+            !finite_pos(mp.resolution))
+            return bail(fail(h, NAV_E_INVAL, "bad nav_map " + std::to_string(m)));
+        if (max_range / mp.resolution > 65536.0f)
+            return bail(fail(h, NAV_E_INVAL, "max_range spans more than 65536 cells"));
+        if (P.n_dyn > 0 &&
+            std::ceil(2.0f * P.dyn_radius / mp.resolution) + 1.0f > (float)kMaxDynRows)
+            return bail(fail(h, NAV_E_INVAL, "dyn_radius too large for the map resolution"));
+        MapDev md;
+        md.w = mp.width;
+        md.h = mp.height;
+        int pitch = (mp.width + 2 + 31) / 32;
+        if ((pitch & 1) == 0) pitch += 1;
+        md.pitch = pitch;
+        const long long nw = (long long)(mp.height + 2) * pitch;
+        md.n_words = (int)((nw + 3) / 4 * 4);
+        md.word_off = (long long)words.size();
+        md.res = mp.resolution;
+        md.inv_res = (float)(1.0 / (double)mp.resolution);
+        words.resize(words.size() + md.n_words, 0u);
+        uint32_t *base = words.data() + md.word_off;
+        for (int j = 0; j < mp.height; ++j)
+            for (int i = 0; i < mp.width; ++i)
+                if (!mp.occ[(size_t)j * mp.width + i]) {
+                    const long long b = (long long)(j + 1) * pitch * 32 + (i + 1);
+                    base[b >> 5] |= 1u << (b & 31);
+                }
+        h->max_map_words = std::max(h->max_map_words, md.n_words);
+        h->maps.push_back(md);
+    }
+    // envs
+    h->env_map.resize(n_envs);
+    h->env_k.resize(n_envs);
+    h->env_tab.resize(n_envs);
+    std::vector<int> env_robot_v(n_envs), env_cs(n_envs);
+    h->obs_off.assign(n_envs + 1, 0);
+    h->ray_off.assign(n_envs + 1, 0);
+    std::vector<int> tab_k;
+    for (int e = 0; e < n_envs; ++e) {
+        const int m = env_map ? env_map[e] : e % n_maps;
+        const int k = env_beams[e];
+        const int r = env_robot ? env_robot[e] : 0;
+        if (m < 0 || m >= n_maps || k <= 0 || k > kMaxBeams || r < 0 || r >= n_robots)
+            return bail(fail(h, NAV_E_INVAL, "bad per-env entry at env " + std::to_string(e)));
+        h->env_map[e] = m;
+        h->env_k[e] = k;
+        env_robot_v[e] = r;
+        int t = (int)(std::find(tab_k.begin(), tab_k.end(), k) - tab_k.begin());
+        if (t == (int)tab_k.size()) tab_k.push_back(k);
+        h->env_tab[e] = t;
+        h->max_k = std::max(h->max_k, k);
+        h->obs_off[e + 1] = h->obs_off[e] + k + 4;
+        h->ray_off[e + 1] = h->ray_off[e] + k;
+    }
+    // beam tables: alpha_k = -FOV/2 + (k + 1/2) FOV / K, cos and sin in binary64
+    // rounded to binary32 (Eq. 4)
+    std::vector<float> beam_c, beam_s;
+    std::vector<int> tab_off;
+    const double fov = (double)P.fov_deg * (3.14159265358979323846 / 180.0);
+    for (int K : tab_k) {
+        tab_off.push_back((int)beam_c.size());
+        for (int k = 0; k < K; ++k) {
+            const double a = -0.5 * fov + ((double)k + 0.5) * fov / (double)K;
+            beam_c.push_back((float)std::cos(a));
+            beam_s.push_back((float)std::sin(a));
+        }
+    }
+    // spawn tables per used (map, robot)
+    std::vector<CsDev> cs_dev;
+    std::vector<int> spawn, spawn_comp, comp_start, comp_count, comp_cells;
+    std::vector<int> cs_index((size_t)n_maps * n_robots, -1);
+    for (int e = 0; e < n_envs; ++e) {
+        const size_t key = (size_t)h->env_map[e] * n_robots + env_robot_v[e];
+        if (cs_index[key] < 0) {
+            const int m = h->env_map[e];
+            const MapDev &md = h->maps[m];
+            CsHost c;
+            build_cspace(maps[m].occ, md.w, md.h, md.res, md.inv_res,
+                         circ_radius(robots[env_robot_v[e]]), c);
+            if (c.spawn.empty()) {
+                fail(h, NAV_E_NOSPAWN,
+                     "map " + std::to_string(m) + " has no cell where robot " +
+                         std::to_string(env_robot_v[e]) + " fits");
+                return bail(NAV_E_NOSPAWN);
+            }
+            CsDev d;
+            d.n_spawn = (int)c.spawn.size();
+            d.spawn_off = (int)spawn.size();
+            d.comp_off = (int)comp_start.size();
+            d.cells_off = (int)comp_cells.size();
+            spawn.insert(spawn.end(), c.spawn.begin(), c.spawn.end());
+            spawn_comp.insert(spawn_comp.end(), c.spawn_comp.begin(), c.spawn_comp.end());
+            comp_start.insert(comp_start.end(), c.comp_start.begin(), c.comp_start.end());
+            comp_count.insert(comp_count.end(), c.comp_count.begin(), c.comp_count.end());
+            comp_cells.insert(comp_cells.end(), c.comp_cells.begin(), c.comp_cells.end());
+            cs_index[key] = (int)cs_dev.size();
+            cs_dev.push_back(d);
+        }
+        env_cs[e] = cs_index[key];
+    }
+    std::vector<RobotDev> rdev(n_robots);
+    for (int r = 0; r < n_robots; ++r) {
+        rdev[r] = RobotDev{robots[r].shape, robots[r].radius, robots[r].length, robots[r].width,
+                           robots[r].v_min, robots[r].v_max, robots[r].w_min, robots[r].w_max};
+    }
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaGetDevice"));
+    StepArgs &A = h->a;
+    std::vector<long long> obs_off_ll(h->obs_off.begin(), h->obs_off.end());
+    std::vector<long long> ray_off_ll(h->ray_off.begin(), h->ray_off.end());
+    uint32_t *bits;
+    MapDev *d_maps;
+    CsDev *d_cs;
+    RobotDev *d_rob;
+    int *d_spawn, *d_spawn_comp, *d_comp_start, *d_comp_count, *d_comp_cells, *d_tab_off, *d_tab_k;
+    int *d_env_map, *d_env_tab, *d_env_robot, *d_env_cs;
+    float *d_bc, *d_bs;
+    long long *d_obs_off, *d_ray_off;
+#define NAV_UP(ptr, vec)                                                          \
+    do {                                                                          \
+        ce = h->arena.upload(&ptr, vec);                                          \
+        if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "upload " #vec));     \
+    } while (0)
+    NAV_UP(bits, words);
+    NAV_UP(d_maps, h->maps);
+    NAV_UP(d_cs, cs_dev);
+    NAV_UP(d_rob, rdev);
+    NAV_UP(d_spawn, spawn);
+    NAV_UP(d_spawn_comp, spawn_comp);
+    NAV_UP(d_comp_start, comp_start);
+    NAV_UP(d_comp_count, comp_count);
+    NAV_UP(d_comp_cells, comp_cells);
+    NAV_UP(d_tab_off, tab_off);
+    NAV_UP(d_tab_k, tab_k);
+    NAV_UP(d_env_map, h->env_map);
+    NAV_UP(d_env_tab, h->env_tab);
+    NAV_UP(d_env_robot, env_robot_v);
+    NAV_UP(d_env_cs, env_cs);
+    NAV_UP(d_bc, beam_c);
+    NAV_UP(d_bs, beam_s);
+    NAV_UP(d_obs_off, obs_off_ll);
+    NAV_UP(d_ray_off, ray_off_ll);
+#undef NAV_UP
+    A.bits = bits;
+    A.maps = d_maps;
+    A.cs = d_cs;
+    A.robots = d_rob;
+    A.spawn = d_spawn;
+    A.spawn_comp = d_spawn_comp;
+    A.comp_start = d_comp_start;
+    A.comp_count = d_comp_count;
+    A.comp_cells = d_comp_cells;
+    A.tab_off = d_tab_off;
+    A.tab_k = d_tab_k;
+    A.beam_c = d_bc;
+    A.beam_s = d_bs;
+    A.env_map = d_env_map;
+    A.env_tab = d_env_tab;
+    A.env_robot = d_env_robot;
+    A.env_cs = d_env_cs;
+    A.obs_off = d_obs_off;
+    A.ray_off = d_ray_off;
+    const size_t E = (size_t)n_envs;
+    float *f[8];
+    for (int i = 0; i < 8; ++i) {
+        ce = h->arena.alloc(&f[i], E);
+        if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMalloc(state)"));
+        cudaMemset(f[i], 0, E * sizeof(float));
+    }
+    A.x = f[0]; A.y = f[1]; A.th = f[2]; A.v = f[3]; A.w = f[4];
+    A.gx = f[5]; A.gy = f[6]; A.dprev = f[7];
+    ce = h->arena.alloc(&A.step, E);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.episode, E);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.dyn, E * std::max(P.n_dyn, 1));
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.status, 1);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&h->d_stats, 2);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMalloc(state)"));
+    cudaMemset(A.step, 0, E * sizeof(int));
+    cudaMemset(A.episode, 0, E * sizeof(unsigned));
+    cudaMemset(A.status, 0, sizeof(int));
+    cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long));
+    A.stats = nullptr;
+    A.p = ParamsDev{P.dt, P.goal_tol, P.c_progress, P.step_penalty, P.r_goal, P.r_coll,
+                    P.horizon, P.goal_dmin, P.goal_dmax, P.n_dyn, P.dyn_radius,
+                    P.dyn_speed_max, P.dyn_min_sep, P.reward_mode};
+    A.max_range = max_range;
+    A.max_k = h->max_k;
+    set_smem_cap(h);
+    int rc = build_tiles(h);
+    if (rc != NAV_OK) return bail(rc);
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "create"));
+    *out = h;
+    return NAV_OK;
+}
+
+int nav_create(const nav_map *maps, int n_maps, int n_envs, int n_beams, float max_range,
+               const nav_robot *robot, const nav_params *params, nav_handle **out) {
+    if (n_envs <= 0 || n_beams <= 0) return NAV_E_INVAL;
+    std::vector<int> beams((size_t)n_envs, n_beams);
+    return nav_create_ex(maps, n_maps, nullptr, beams.data(), nullptr, n_envs, max_range, robot,
+                         1, params, out);
+}
+
+int nav_set_stream(nav_handle *h, void *cuda_stream) {
+    if (!h) return NAV_E_INVAL;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return NAV_OK;
+}
+
+int nav_obs_offsets(const nav_handle *h, int64_t *offsets_host) {
+    if (!h || !offsets_host) return NAV_E_INVAL;
+    std::memcpy(offsets_host, h->obs_off.data(), sizeof(int64_t) * h->obs_off.size());
+    return NAV_OK;
+}
+
+int nav_num_envs(const nav_handle *h) { return h ? h->n_envs : NAV_E_INVAL; }
+
+int64_t nav_obs_size(const nav_handle *h) { return h ? h->obs_off.back() : NAV_E_INVAL; }
+
+int nav_reset(nav_handle *h, uint64_t seed, float *obs_dev) {
+    if (!h || !obs_dev) return fail(h, NAV_E_INVAL, "nav_reset: null argument");
+    h->seed = seed;
+    StepArgs &A = h->a;
+    A.seed = seed;
+    A.mode = 1;
+    A.actions = nullptr;
+    A.obs = obs_dev;
+    A.reward = nullptr;
+    A.done = nullptr;
+    A.final_obs = nullptr;
+    return launch(h);
+}
+
+int nav_step(nav_handle *h, const float *actions_dev, float *obs_dev, float *reward_dev,
+             uint8_t *done_dev, float *final_obs_dev) {
+    if (!h || !actions_dev || !obs_dev || !reward_dev || !done_dev)
+        return fail(h, NAV_E_INVAL, "nav_step: null argument");
+    if ((reinterpret_cast<uintptr_t>(actions_dev) & 7u) != 0)
+        return fail(h, NAV_E_INVAL, "nav_step: actions must be 8-byte aligned");
+    StepArgs &A = h->a;
+    A.seed = h->seed;
+    A.mode = 0;
+    A.actions = actions_dev;
+    A.obs = obs_dev;
+    A.reward = reward_dev;
+    A.done = done_dev;
+    A.final_obs = final_obs_dev;
+    return launch(h);
+}
+
+int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, float *reward_host,
+                  uint8_t *done_host, float *final_obs_host) {
+    if (!h || !actions_host || !obs_host || !reward_host || !done_host)
+        return fail(h, NAV_E_INVAL, "nav_step_host: null argument");
+    const size_t E = (size_t)h->n_envs, O = (size_t)h->obs_off.back();
+    cudaError_t e = cudaSuccess;
+    if (!h->h_act) {
+        e = h->arena.alloc(&h->h_act, 2 * E);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->h_obs, O);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->h_rew, E);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->h_done, E);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->h_fin, O);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(staging)");
+    }
+    e = cudaMemcpyAsync(h->h_act, actions_host, 2 * E * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(actions)");
+    int rc = nav_step(h, h->h_act, h->h_obs, h->h_rew, h->h_done, final_obs_host ? h->h_fin : nullptr);
+    if (rc != NAV_OK) return rc;
+    e = cudaMemcpyAsync(obs_host, h->h_obs, O * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(reward_host, h->h_rew, E * sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(done_host, h->h_done, E, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && final_obs_host)
+        e = cudaMemcpyAsync(final_obs_host, h->h_fin, O * sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(results)");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return NAV_OK;
+}
+
+int nav_sync(nav_handle *h, int timeout_ms) {
+    if (!h) return NAV_E_INVAL;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+    e = cudaEventRecord(ev, h->stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return cuda_fail(h, e, "cudaEventRecord");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e != cudaErrorNotReady) break;
+        if (timeout_ms > 0 &&
+            std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
+            cudaEventDestroy(ev);
+            return fail(h, NAV_E_TIMEOUT, "nav_sync: deadline passed");
+        }
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream");
+    int status = 0;
+    e = cudaMemcpy(&status, h->a.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(status)");
+    if (status != 0) {
+        cudaMemset(h->a.status, 0, sizeof(int));
+        return fail(h, NAV_E_INTERNAL, "device status word " + std::to_string(status));
+    }
+    return NAV_OK;
+}
+
+int nav_get_state(nav_handle *h, float *f8_host, int32_t *i2_host, float *dyn_host) {
+    if (!h || !f8_host || !i2_host) return fail(h, NAV_E_INVAL, "nav_get_state: null argument");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    const size_t E = (size_t)h->n_envs;
+    std::vector<float> col(E);
+    float *src[8] = {h->a.x, h->a.y, h->a.th, h->a.v, h->a.w, h->a.gx, h->a.gy, h->a.dprev};
+    for (int c = 0; c < 8; ++c) {
+        e = cudaMemcpy(col.data(), src[c], E * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(state)");
+        for (size_t i = 0; i < E; ++i) f8_host[8 * i + c] = col[i];
+    }
+    std::vector<int32_t> st(E), ep(E);
+    e = cudaMemcpy(st.data(), h->a.step, E * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(ep.data(), h->a.episode, E * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(counters)");
+    for (size_t i = 0; i < E; ++i) {
+        i2_host[2 * i] = st[i];
+        i2_host[2 * i + 1] = ep[i];
+    }
+    if (dyn_host && h->par.n_dyn > 0) {
+        e = cudaMemcpy(dyn_host, h->a.dyn, E * h->par.n_dyn * sizeof(float4), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(dyn)");
+    }
+    return NAV_OK;
+}
+
+int nav_set_state(nav_handle *h, uint64_t seed, const float *f8_host, const int32_t *i2_host,
+                  const float *dyn_host) {
+    if (!h || !f8_host || !i2_host) return fail(h, NAV_E_INVAL, "nav_set_state: null argument");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    const size_t E = (size_t)h->n_envs;
+    std::vector<float> col(E);
+    float *dst[8] = {h->a.x, h->a.y, h->a.th, h->a.v, h->a.w, h->a.gx, h->a.gy, h->a.dprev};
+    for (int c = 0; c < 8; ++c) {
+        for (size_t i = 0; i < E; ++i) col[i] = f8_host[8 * i + c];
+        e = cudaMemcpy(dst[c], col.data(), E * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(state)");
+    }
+    std::vector<int32_t> st(E), ep(E);
+    for (size_t i = 0; i < E; ++i) {
+        st[i] = i2_host[2 * i];
+        ep[i] = i2_host[2 * i + 1];
+    }
+    e = cudaMemcpy(h->a.step, st.data(), E * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->a.episode, ep.data(), E * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && dyn_host && h->par.n_dyn > 0)
+        e = cudaMemcpy(h->a.dyn, dyn_host, E * h->par.n_dyn * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(state)");
+    h->seed = seed;
+    return NAV_OK;
+}
+
+int nav_set_debug(nav_handle *h, int enable) {
+    if (!h) return NAV_E_INVAL;
+    if (enable && !h->d_dbg_range) {
+        const size_t n = (size_t)h->ray_off.back();
+        cudaError_t e = h->arena.alloc(&h->d_dbg_range, n);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->d_dbg_hit, n);
+        if (e == cudaSuccess) e = h->arena.alloc(&h->d_dbg_vis, n);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(debug)");
+    }
+    h->debug = enable ? 1 : 0;
+    h->a.dbg_range = h->debug ? h->d_dbg_range : nullptr;
+    h->a.dbg_hit = h->debug ? h->d_dbg_hit : nullptr;
+    h->a.dbg_vis = h->debug ? h->d_dbg_vis : nullptr;
+    return NAV_OK;
+}
+
+int nav_get_debug(nav_handle *h, float *ranges_host, int32_t *hits_host, uint32_t *visits_host) {
+    if (!h) return NAV_E_INVAL;
+    if (!h->debug) return fail(h, NAV_E_INVAL, "nav_get_debug: debug capture is off");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    const size_t n = (size_t)h->ray_off.back();
+    if (ranges_host) e = cudaMemcpy(ranges_host, h->d_dbg_range, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hits_host)
+        e = cudaMemcpy(hits_host, h->d_dbg_hit, n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && visits_host)
+        e = cudaMemcpy(visits_host, h->d_dbg_vis, n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(debug)");
+    return NAV_OK;
+}
+
+int nav_set_stats(nav_handle *h, int enable) {
+    if (!h) return NAV_E_INVAL;
+    h->stats = enable ? 1 : 0;
+    h->a.stats = h->stats ? h->d_stats : nullptr;
+    if (enable) {
+        cudaError_t e = cudaMemsetAsync(h->d_stats, 0, 2 * sizeof(unsigned long long), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync(stats)");
+    }
+    return NAV_OK;
+}
+
+int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays) {
+    if (!h) return NAV_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    unsigned long long v[2];
+    e = cudaMemcpy(v, h->d_stats, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(stats)");
+    if (visits) *visits = v[0];
+    if (rays) *rays = v[1];
+    return NAV_OK;
+}
+
+int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes) {
+    if (!h) return NAV_E_INVAL;
+    if (tile_envs < 0 || tile_envs > kMaxTileEnvs || block_threads < 0 || block_threads > 512 ||
+        (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
+        smem_map_bytes < 0 || smem_map_bytes > 200 * 1024)
+        return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");
+    if (block_threads) h->block_threads = block_threads;
+    if (smem_map_bytes) {
+        h->smem_map_bytes = smem_map_bytes;
+        set_smem_cap(h);
+    }
+    if (tile_envs && tile_envs != h->tile_envs) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        h->tile_envs = tile_envs;
+        return build_tiles(h);
+    }
+    return NAV_OK;
+}
+
+int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int *smem_map_bytes) {
+    if (!h) return NAV_E_INVAL;
+    if (tile_envs) *tile_envs = h->tile_envs;
+    if (block_threads) *block_threads = h->block_threads;
+    if (smem_map_bytes) *smem_map_bytes = h->smem_map_bytes;
+    return NAV_OK;
+}
+
+const char *nav_last_error(const nav_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+void nav_free(nav_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+} // extern "C"

@@ -1,0 +1,779 @@
+// Fused simulator step for sm_103a (FlashNav Sec. 2.2, Eq. 7).
+//
+// One CTA owns a tile of envs that share a map and a beam count.  It stages
+// the tile's packed bitmap into shared memory with one bulk TMA copy
+// (cp.async.bulk + mbarrier) when it fits, otherwise reads it through L1/L2.
+// Phase 1 (one thread per env): action decode, exact-arc integration, moving
+// discs, footprint collision, reward and flags, sparse reset.  Phase 2 (all
+// warps): every beam of every env in the tile is cast by Amanatides-Woo grid
+// traversal over the bitmap; warps fetch 32-ray chunks from a shared counter
+// and a warp retires a chunk when its last ray stops.
+//
+// Geometry is compiled with FMA contraction off (-fmad=false) and IEEE
+// division and square root, so every binary32 operation rounds once and the
+// results (hit cells, flags, resets) are a fixed function of the inputs.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "nav_internal.h"
+
+namespace flashnav {
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Scalar building blocks
+// ---------------------------------------------------------------------------
+
+// sin and cos of a binary32 angle.  x = k (pi/2) + r with pi/2 split into
+// three binary32 parts (Cody-Waite; the first two have 12 significant bits so
+// k times them is exact for small k), then the Taylor series of sin through
+// r^11 and of cos through r^12 on |r| <= pi/4, Horner form, coefficients
+// (-1)^n / n! rounded from binary64; the quadrant k mod 4 selects signs.
+__device__ __forceinline__ void sincos_taylor(float x, float &s, float &c) {
+    const float k = rintf(x * 0.636619772367581343076f);
+    float r = x - k * 0x1.92p+0f;
+    r = r - k * 0x1.fb4p-12f;
+    r = r - k * 0x1.4442d2p-24f;
+    const float r2 = r * r;
+    float p = (float)(-1.0 / 39916800.0);
+    p = p * r2 + (float)(1.0 / 362880.0);
+    p = p * r2 + (float)(-1.0 / 5040.0);
+    p = p * r2 + (float)(1.0 / 120.0);
+    p = p * r2 + (float)(-1.0 / 6.0);
+    const float sr = r + (r * r2) * p;
+    float q = (float)(1.0 / 479001600.0);
+    q = q * r2 + (float)(-1.0 / 3628800.0);
+    q = q * r2 + (float)(1.0 / 40320.0);
+    q = q * r2 + (float)(-1.0 / 720.0);
+    q = q * r2 + (float)(1.0 / 24.0);
+    q = q * r2 + (float)(-1.0 / 2.0);
+    const float cr = 1.0f + r2 * q;
+    switch (((int)k) & 3) {
+    case 0: s = sr; c = cr; break;
+    case 1: s = cr; c = -sr; break;
+    case 2: s = -sr; c = -cr; break;
+    default: s = -cr; c = sr; break;
+    }
+}
+
+__device__ __forceinline__ float wrap_angle(float a) {
+    if (a >= kPi) return a - kTwoPi;
+    if (a < -kPi) return a + kTwoPi;
+    return a;
+}
+
+// Counter-based RNG: SplitMix64's finaliser applied to the key
+// seed ^ env*G ^ episode*P2 ^ draw*P3 (G the golden gamma, P2/P3 odd 64-bit
+// multipliers), so a reset draw depends only on (seed, env, episode, draw).
+__device__ __forceinline__ unsigned long long draw64(unsigned long long seed, unsigned env,
+                                                     unsigned episode, unsigned k) {
+    unsigned long long z = seed ^ ((unsigned long long)env * 0x9E3779B97F4A7C15ull) ^
+                           ((unsigned long long)episode * 0xC2B2AE3D27D4EB4Full) ^
+                           ((unsigned long long)k * 0x165667B19E3779F9ull);
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// index in [0, n) from the high word (multiply-shift)
+__device__ __forceinline__ int draw_index(unsigned long long h, int n) {
+    return (int)__umulhi((unsigned)(h >> 32), (unsigned)n);
+}
+
+// [0, 1) from 24 bits
+__device__ __forceinline__ float draw_unit(unsigned bits24) {
+    return (float)bits24 * (1.0f / 16777216.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Bitmap access
+// ---------------------------------------------------------------------------
+template <bool SMEM> struct Bits;
+template <> struct Bits<true> {
+    const uint32_t *w; // shared memory
+    __device__ __forceinline__ uint32_t word(int i) const { return w[i]; }
+};
+template <> struct Bits<false> {
+    const uint32_t *__restrict__ w; // global, read-only for the kernel's lifetime
+    __device__ __forceinline__ uint32_t word(int i) const { return __ldg(w + i); }
+};
+
+template <class B>
+__device__ __forceinline__ bool cell_free(const B &bits, int b) {
+    return (bits.word(b >> 5) >> (b & 31)) & 1u;
+}
+
+// Is any cell of row j, columns [i0, i1], blocked (occupied or off-map)?
+template <class B>
+__device__ bool row_blocked(const B &bits, const MapDev &M, int j, int i0, int i1) {
+    if (i0 > i1) return false;
+    if (j < 0 || j >= M.h || i0 < 0 || i1 >= M.w) return true;
+    const int base = (j + 1) * M.pitch * 32 + 1;
+    const int c0 = base + i0, c1 = base + i1;
+    const int w0 = c0 >> 5, w1 = c1 >> 5;
+    for (int wd = w0; wd <= w1; ++wd) {
+        uint32_t m = kFull;
+        if (wd == w0) m &= kFull << (c0 & 31);
+        if (wd == w1) m &= kFull >> (31 - (c1 & 31));
+        if (~bits.word(wd) & m) return true;
+    }
+    return false;
+}
+
+// Cells of row j whose closed square meets the open disc (centre xc, yc,
+// radius rc, cell units): [i0, i1]; false if the row's slab is out of reach.
+__device__ __forceinline__ bool disc_row(float xc, float yc, float rc, int j, int &i0, int &i1) {
+    const float fj = (float)j;
+    float dy = 0.0f;
+    if (yc < fj) dy = fj - yc;
+    else if (yc > fj + 1.0f) dy = yc - (fj + 1.0f);
+    if (!(dy < rc)) return false;
+    const float hh = sqrtf(rc * rc - dy * dy);
+    i0 = (int)floorf(xc - hh);
+    i1 = (int)ceilf(xc + hh) - 1;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Moving-disc layer (per env, per step): stamped row spans in shared memory
+// ---------------------------------------------------------------------------
+struct DynEnv {
+    short j0[kMaxDyn], nr[kMaxDyn], bi0[kMaxDyn], bi1[kMaxDyn];
+    short lo[kMaxDyn][kMaxDynRows], hi[kMaxDyn][kMaxDynRows];
+};
+
+__device__ void stamp_discs(const float4 *ob, int nd, float inv_res, float rdc, DynEnv &de) {
+    for (int q = 0; q < nd; ++q) {
+        const float oxc = ob[q].x * inv_res, oyc = ob[q].y * inv_res;
+        const int j0 = (int)floorf(oyc - rdc);
+        const int j1 = (int)ceilf(oyc + rdc) - 1;
+        int nr = j1 - j0 + 1;
+        if (nr > kMaxDynRows) nr = kMaxDynRows; // bounded by the create-time check
+        int bmin = 1 << 30, bmax = -(1 << 30);
+        for (int r = 0; r < nr; ++r) {
+            int a, b;
+            if (!disc_row(oxc, oyc, rdc, j0 + r, a, b)) { a = 1; b = 0; }
+            de.lo[q][r] = (short)a;
+            de.hi[q][r] = (short)b;
+            if (a <= b) { bmin = min(bmin, a); bmax = max(bmax, b); }
+        }
+        de.j0[q] = (short)j0;
+        de.nr[q] = (short)(bmin <= bmax ? nr : 0);
+        de.bi0[q] = (short)bmin;
+        de.bi1[q] = (short)bmax;
+    }
+}
+
+__device__ __forceinline__ bool dyn_cell(const DynEnv &de, int nd, int i, int j) {
+    for (int q = 0; q < nd; ++q) {
+        const int r = j - de.j0[q];
+        if ((unsigned)r < (unsigned)de.nr[q] && i >= de.lo[q][r] && i <= de.hi[q][r]) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool dyn_row(const DynEnv &de, int nd, int j, int i0, int i1) {
+    if (i0 > i1) return false;
+    for (int q = 0; q < nd; ++q) {
+        const int r = j - de.j0[q];
+        if ((unsigned)r < (unsigned)de.nr[q] && max(i0, (int)de.lo[q][r]) <= min(i1, (int)de.hi[q][r]))
+            return true;
+    }
+    return false;
+}
+
+// Parameter interval along the ray in which it can enter a stamped cell: the
+// union of its crossings of every stamp's bounding box grown by one cell.
+// Outside it the per-cell disc test is skipped (it could not succeed).
+__device__ void dyn_gate(const DynEnv &de, int nd, float xc, float yc, float dx, float dy,
+                         float &glo, float &ghi) {
+    glo = INFINITY;
+    ghi = -INFINITY;
+    for (int q = 0; q < nd; ++q) {
+        if (de.nr[q] == 0) continue;
+        const float x0 = (float)(de.bi0[q] - 1), x1 = (float)(de.bi1[q] + 2);
+        const float y0 = (float)(de.j0[q] - 1), y1 = (float)(de.j0[q] + de.nr[q] + 1);
+        float ta = 0.0f, tb = INFINITY;
+        if (dx != 0.0f) {
+            const float u = (x0 - xc) / dx, v = (x1 - xc) / dx;
+            ta = fmaxf(ta, fminf(u, v));
+            tb = fminf(tb, fmaxf(u, v));
+        } else if (xc < x0 || xc > x1) {
+            continue;
+        }
+        if (dy != 0.0f) {
+            const float u = (y0 - yc) / dy, v = (y1 - yc) / dy;
+            ta = fmaxf(ta, fminf(u, v));
+            tb = fminf(tb, fmaxf(u, v));
+        } else if (yc < y0 || yc > y1) {
+            continue;
+        }
+        if (ta <= tb) {
+            glo = fminf(glo, ta);
+            ghi = fmaxf(ghi, tb);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ray cast: Amanatides-Woo traversal over the padded free-bit map (Eq. 4-5).
+// Starting cell (floor xc, floor yc); per iteration the axis whose next
+// boundary is nearer is stepped (a tie steps x first), the entry parameter
+// t of the new cell is checked against r_max, then the cell is looked up.
+// The padding cells read as blocked, so leaving the map stops the walk
+// without a bounds test.  The loop ends within 2 r_max/res + 3 iterations:
+// each iteration adds tDelta >= 1 to one of tMaxX, tMaxY.
+// Returns the range in metres; hit = j*W+i, -1 off-map, -2 r_max.
+// ---------------------------------------------------------------------------
+template <bool DYN, class B>
+__device__ __forceinline__ float cast_ray(const B &bits, const MapDev &M, float xc, float yc,
+                                          float dx, float dy, float rmax_c, float max_range,
+                                          const DynEnv *de, int nd, int &hit, unsigned &vis) {
+    const int pb = M.pitch * 32;
+    if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
+    const float fx = floorf(xc), fy = floorf(yc);
+    const int i0 = (int)fx, j0 = (int)fy;
+    if (i0 >= M.w || j0 >= M.h) { hit = -1; vis = 1; return 0.0f; }
+    int b = (j0 + 1) * pb + (i0 + 1);
+    if (!cell_free(bits, b) || (DYN && dyn_cell(*de, nd, i0, j0))) {
+        hit = j0 * M.w + i0;
+        vis = 1;
+        return 0.0f;
+    }
+    int sbx = 0, sby = 0;
+    float tdx = INFINITY, tdy = INFINITY, tmx = INFINITY, tmy = INFINITY;
+    if (dx > 0.0f) { sbx = 1; tdx = 1.0f / dx; tmx = ((fx + 1.0f) - xc) * tdx; }
+    else if (dx < 0.0f) { sbx = -1; tdx = 1.0f / -dx; tmx = (xc - fx) * tdx; }
+    if (dy > 0.0f) { sby = pb; tdy = 1.0f / dy; tmy = ((fy + 1.0f) - yc) * tdy; }
+    else if (dy < 0.0f) { sby = -pb; tdy = 1.0f / -dy; tmy = (yc - fy) * tdy; }
+    float glo = INFINITY, ghi = -INFINITY;
+    if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
+    float t = 0.0f;
+    bool stopped = false;
+    for (;;) {
+        const bool sx = tmx <= tmy;
+        t = sx ? tmx : tmy;
+        if (t > rmax_c) break;
+        b += sx ? sbx : sby;
+        if (sx) tmx = tmx + tdx;
+        else tmy = tmy + tdy;
+        if (!cell_free(bits, b)) { stopped = true; break; }
+        if (DYN && t >= glo && t <= ghi) {
+            const int r = b / pb;
+            if (dyn_cell(*de, nd, b - r * pb - 1, r - 1)) { stopped = true; break; }
+        }
+    }
+    const int r = b / pb;
+    const int i = b - r * pb - 1, j = r - 1;
+    vis = 1u + (unsigned)(abs(i - i0) + abs(j - j0));
+    if (!stopped) { hit = -2; return max_range; }
+    hit = (i < 0 || j < 0 || i >= M.w || j >= M.h) ? -1 : j * M.w + i;
+    return t * M.res;
+}
+
+// ---------------------------------------------------------------------------
+// Footprints (Sec. 2.2.3 collision check; Tables 8-9 presets)
+// ---------------------------------------------------------------------------
+template <bool DYN, class B>
+__device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc, float rc,
+                             const DynEnv *de, int nd) {
+    const int j0 = (int)floorf(yc - rc);
+    const int j1 = (int)ceilf(yc + rc) - 1;
+    for (int j = j0; j <= j1; ++j) {
+        int a, b;
+        if (!disc_row(xc, yc, rc, j, a, b)) continue;
+        if (row_blocked(bits, M, j, a, b)) return true;
+        if (DYN && dyn_row(*de, nd, j, a, b)) return true;
+    }
+    return false;
+}
+
+// Open rectangle (half-length hl along the heading (ct, st), half-width hw,
+// cell units) against closed cells: per row slab [j, j+1], the x-extent of
+// the polygon within the slab is the hull of its vertices inside the slab
+// and its edges' crossings of y = j and y = j + 1.
+template <bool DYN, class B>
+__device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc, float st,
+                             float ct, float hl, float hw, const DynEnv *de, int nd) {
+    const float ax = hl * ct, ay = hl * st;
+    const float bx = -(hw * st), by = hw * ct;
+    float px[4], py[4];
+    px[0] = (xc + ax) + bx; py[0] = (yc + ay) + by;
+    px[1] = (xc - ax) + bx; py[1] = (yc - ay) + by;
+    px[2] = (xc - ax) - bx; py[2] = (yc - ay) - by;
+    px[3] = (xc + ax) - bx; py[3] = (yc + ay) - by;
+    float ymin = py[0], ymax = py[0];
+#pragma unroll
+    for (int v = 1; v < 4; ++v) {
+        ymin = py[v] < ymin ? py[v] : ymin;
+        ymax = py[v] > ymax ? py[v] : ymax;
+    }
+    const int j0 = (int)floorf(ymin);
+    const int j1 = (int)ceilf(ymax) - 1;
+    for (int j = j0; j <= j1; ++j) {
+        const float lo = (float)j, hi = (float)j + 1.0f;
+        float xlo = INFINITY, xhi = -INFINITY;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (py[v] >= lo && py[v] <= hi) {
+                xlo = px[v] < xlo ? px[v] : xlo;
+                xhi = px[v] > xhi ? px[v] : xhi;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int u = (v + 1) & 3;
+            const float ya = py[v], yb = py[u];
+            if (ya == yb) continue;
+            const float ylo = ya < yb ? ya : yb, yhi = ya < yb ? yb : ya;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float yl = s ? hi : lo;
+                if (yl > ylo && yl < yhi) {
+                    const float xx = px[v] + (yl - ya) * (px[u] - px[v]) / (yb - ya);
+                    xlo = xx < xlo ? xx : xlo;
+                    xhi = xx > xhi ? xx : xhi;
+                }
+            }
+        }
+        if (!(xlo <= xhi)) continue;
+        const int a = (int)floorf(xlo), b = (int)ceilf(xhi) - 1;
+        if (row_blocked(bits, M, j, a, b)) return true;
+        if (DYN && dyn_row(*de, nd, j, a, b)) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Env phase
+// ---------------------------------------------------------------------------
+struct EnvSlot {
+    float xc, yc, st, ct;     // pose of the scan written to obs
+    float fxc, fyc, fst, fct; // pre-reset pose (final observation)
+    long long obs_off, ray_off;
+    int env;
+    int fin;
+};
+
+template <class B>
+__device__ __forceinline__ bool static_blocked(const B &bits, const MapDev &M, int i, int j) {
+    if (i < 0 || j < 0 || i >= M.w || j >= M.h) return true;
+    return !cell_free(bits, (j + 1) * M.pitch * 32 + (i + 1));
+}
+
+// Sparse reset of env e for `episode` (Sec. 2.2.3): spawn cell uniform over
+// the map's spawnable cells (draw 0), heading uniform (draw 1), goal from the
+// spawn cell's component with distance in [dmin, dmax] (draws 2..65; after
+// 64 misses the draw nearest the band, first on ties), moving discs from
+// spawnable cells at least dyn_min_sep away (draws 1024 + 64 q + a, a < 16)
+// with speed and heading from draw 1024 + 64 q + 48.
+template <class B>
+__device__ void reset_env(const StepArgs &A, const B &bits, const MapDev &M, int e,
+                          unsigned episode, float &x, float &y, float &th, float &gx, float &gy,
+                          float &dprev, float4 *ob) {
+    const CsDev cs = A.cs[A.env_cs[e]];
+    if (cs.n_spawn <= 0) {
+        atomicOr(A.status, kStatusNoSpawn);
+        x = y = th = gx = gy = dprev = 0.0f;
+        return;
+    }
+    const unsigned long long h0 = draw64(A.seed, (unsigned)e, episode, 0);
+    const int si = cs.spawn_off + draw_index(h0, cs.n_spawn);
+    const int cell = A.spawn[si];
+    const int comp = A.spawn_comp[si];
+    x = ((float)(cell % M.w) + 0.5f) * M.res;
+    y = ((float)(cell / M.w) + 0.5f) * M.res;
+    th = draw_unit((unsigned)(draw64(A.seed, (unsigned)e, episode, 1) >> 40)) * kTwoPi - kPi;
+    const int cstart = cs.cells_off + A.comp_start[cs.comp_off + comp];
+    const int ccount = A.comp_count[cs.comp_off + comp];
+    const float dmin = A.p.goal_dmin, dmax = A.p.goal_dmax;
+    float bx = x, by = y, berr = INFINITY;
+    for (int a = 0; a < 64; ++a) {
+        const unsigned long long hg = draw64(A.seed, (unsigned)e, episode, 2u + (unsigned)a);
+        const int gc = A.comp_cells[cstart + draw_index(hg, ccount)];
+        const float cx = ((float)(gc % M.w) + 0.5f) * M.res;
+        const float cy = ((float)(gc / M.w) + 0.5f) * M.res;
+        const float ddx = cx - x, ddy = cy - y;
+        const float d = sqrtf(ddx * ddx + ddy * ddy);
+        const float err = d < dmin ? dmin - d : (d > dmax ? d - dmax : 0.0f);
+        if (err < berr) { berr = err; bx = cx; by = cy; }
+        if (err == 0.0f) break;
+    }
+    gx = bx;
+    gy = by;
+    {
+        const float ddx = bx - x, ddy = by - y;
+        dprev = sqrtf(ddx * ddx + ddy * ddy);
+    }
+    const int nd = A.p.n_dyn;
+    for (int q = 0; q < nd; ++q) {
+        float ox = x, oy = y;
+        for (int a = 0; a < 16; ++a) {
+            const unsigned long long hp =
+                draw64(A.seed, (unsigned)e, episode, 1024u + 64u * (unsigned)q + (unsigned)a);
+            const int oc = A.spawn[cs.spawn_off + draw_index(hp, cs.n_spawn)];
+            ox = ((float)(oc % M.w) + 0.5f) * M.res;
+            oy = ((float)(oc / M.w) + 0.5f) * M.res;
+            const float ddx = ox - x, ddy = oy - y;
+            if (sqrtf(ddx * ddx + ddy * ddy) >= A.p.dyn_min_sep) break;
+        }
+        const unsigned long long hv = draw64(A.seed, (unsigned)e, episode, 1024u + 64u * (unsigned)q + 48u);
+        const float sp = draw_unit((unsigned)(hv >> 40)) * A.p.dyn_speed_max;
+        const float hd = draw_unit((unsigned)((hv >> 8) & 0xFFFFFFull)) * kTwoPi - kPi;
+        float sh, ch;
+        sincos_taylor(hd, sh, ch);
+        ob[q] = make_float4(ox, oy, sp * ch, sp * sh);
+    }
+}
+
+// Observation tail (Eq. 1): goal distance, bearing in the body frame, v, w.
+__device__ __forceinline__ void write_tail(float *row, float x, float y, float th, float gx,
+                                           float gy, float v, float w) {
+    const float ddx = gx - x, ddy = gy - y;
+    row[0] = sqrtf(ddx * ddx + ddy * ddy);
+    float phi = atan2f(ddy, ddx) - th;
+    if (phi >= kPi) phi -= kTwoPi;
+    else if (phi < -kPi) phi += kTwoPi;
+    row[1] = phi;
+    row[2] = v;
+    row[3] = w;
+}
+
+template <bool DYN, class B>
+__device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int K, int slot_id,
+                          EnvSlot &slot, DynEnv *dmain, DynEnv *dfin) {
+    const int e = slot.env;
+    const int nd = DYN ? A.p.n_dyn : 0;
+    float4 ob[kMaxDyn];
+    const float rdc = A.p.dyn_radius * M.inv_res;
+    float x, y, th, v, w, gx, gy, dprev;
+    int step;
+    unsigned episode;
+    bool restamp = true; // spans in dmain must describe the discs after this step
+    slot.fin = 0;
+    if (A.mode == 1) {
+        episode = 0;
+        reset_env(A, bits, M, e, episode, x, y, th, gx, gy, dprev, ob);
+        v = w = 0.0f;
+        step = 0;
+    } else {
+        x = A.x[e]; y = A.y[e]; th = A.th[e];
+        gx = A.gx[e]; gy = A.gy[e]; dprev = A.dprev[e];
+        step = A.step[e];
+        episode = A.episode[e];
+        if (DYN)
+            for (int q = 0; q < nd; ++q) ob[q] = A.dyn[(size_t)e * nd + q];
+        const RobotDev rb = A.robots[A.env_robot[e]];
+        // a1: clamp and map the normalised action onto the preset's bounds
+        const float2 act = reinterpret_cast<const float2 *>(A.actions)[e];
+        const float a0 = fminf(fmaxf(act.x, -1.0f), 1.0f);
+        const float a1 = fminf(fmaxf(act.y, -1.0f), 1.0f);
+        v = rb.v_min + ((a0 + 1.0f) * 0.5f) * (rb.v_max - rb.v_min);
+        w = rb.w_min + ((a1 + 1.0f) * 0.5f) * (rb.w_max - rb.w_min);
+        // a2: exact arc over dt (chord length v dt sinc(w dt / 2) along the
+        // mid-step heading), heading wrapped to [-pi, pi)
+        const float dt = A.p.dt;
+        const float hd = (w * dt) * 0.5f;
+        float sc;
+        if (fabsf(hd) < 0.1f) {
+            const float h2 = hd * hd;
+            float p = (float)(-1.0 / 5040.0);
+            p = p * h2 + (float)(1.0 / 120.0);
+            p = p * h2 + (float)(-1.0 / 6.0);
+            sc = 1.0f + h2 * p;
+        } else {
+            float sh, ch;
+            sincos_taylor(hd, sh, ch);
+            sc = sh / hd;
+        }
+        float sm, cm;
+        sincos_taylor(th + hd, sm, cm);
+        const float chord = (v * dt) * sc;
+        x = x + chord * cm;
+        y = y + chord * sm;
+        th = wrap_angle(th + w * dt);
+        // a5: moving discs, constant velocity, reflect off blocked cells
+        if (DYN) {
+            for (int q = 0; q < nd; ++q) {
+                float4 o = ob[q];
+                const float nx = o.x + o.z * dt;
+                if (static_blocked(bits, M, (int)floorf(nx * M.inv_res), (int)floorf(o.y * M.inv_res)))
+                    o.z = -o.z;
+                else
+                    o.x = nx;
+                const float ny = o.y + o.w * dt;
+                if (static_blocked(bits, M, (int)floorf(o.x * M.inv_res), (int)floorf(ny * M.inv_res)))
+                    o.w = -o.w;
+                else
+                    o.y = ny;
+                ob[q] = o;
+            }
+            stamp_discs(ob, nd, M.inv_res, rdc, *dmain);
+            restamp = false;
+        }
+        // a6: footprint against the bitmap (and the moving-disc layer)
+        const float xc = x * M.inv_res, yc = y * M.inv_res;
+        float st, ct;
+        sincos_taylor(th, st, ct);
+        bool coll;
+        if (rb.shape == 0)
+            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, nd);
+        else
+            coll = rect_blocked<DYN>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
+                                     (0.5f * rb.width) * M.inv_res, dmain, nd);
+        // a7: goal test, reward, flags
+        const float ddx = gx - x, ddy = gy - y;
+        const float d = sqrtf(ddx * ddx + ddy * ddy);
+        const bool goal = d <= A.p.goal_tol;
+        float r;
+        if (A.p.reward_mode == 0) {
+            r = A.p.c_progress * (dprev - d);
+            r = r - A.p.step_penalty;
+            if (goal) r = r + A.p.r_goal;
+            if (coll) r = r - A.p.r_coll;
+        } else {
+            r = goal ? A.p.r_goal : (coll ? -A.p.r_coll : A.p.c_progress * (dprev - d));
+        }
+        dprev = d;
+        step += 1;
+        const bool term = goal || coll;
+        const bool trunc = !term && step >= A.p.horizon;
+        A.reward[e] = r;
+        A.done[e] = (unsigned char)((term ? 1 : 0) | (trunc ? 2 : 0) | (goal ? 4 : 0) | (coll ? 8 : 0));
+        if (term || trunc) {
+            // a9 (final): O_{t+1} before the reset, scanned in phase 2
+            if (A.final_obs) {
+                write_tail(A.final_obs + slot.obs_off + K, x, y, th, gx, gy, v, w);
+                slot.fin = 1;
+                slot.fxc = xc; slot.fyc = yc; slot.fst = st; slot.fct = ct;
+                if (DYN) *dfin = *dmain;
+            }
+            // a8: sparse reset in place
+            episode += 1;
+            reset_env(A, bits, M, e, episode, x, y, th, gx, gy, dprev, ob);
+            v = w = 0.0f;
+            step = 0;
+            restamp = true;
+        }
+    }
+    A.x[e] = x; A.y[e] = y; A.th[e] = th; A.v[e] = v; A.w[e] = w;
+    A.gx[e] = gx; A.gy[e] = gy; A.dprev[e] = dprev;
+    A.step[e] = step;
+    A.episode[e] = episode;
+    if (DYN) {
+        for (int q = 0; q < nd; ++q) A.dyn[(size_t)e * nd + q] = ob[q];
+        if (restamp) stamp_discs(ob, nd, M.inv_res, rdc, *dmain);
+    }
+    // a9: observation tail of the scan written to obs
+    write_tail(A.obs + slot.obs_off + K, x, y, th, gx, gy, v, w);
+    float st, ct;
+    sincos_taylor(th, st, ct);
+    slot.xc = x * M.inv_res;
+    slot.yc = y * M.inv_res;
+    slot.st = st;
+    slot.ct = ct;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) copy of the bitmap into shared memory
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void stage_bitmap(uint32_t *dst, const uint32_t *src, int n_words,
+                                             unsigned long long *bar) {
+    const unsigned b = smem_u32(bar);
+    const unsigned bytes = (unsigned)n_words * 4u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                 : "memory");
+    const unsigned chunk = 32768u;
+    for (unsigned off = 0; off < bytes; off += chunk) {
+        const unsigned n = bytes - off < chunk ? bytes - off : chunk;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(dst) + off),
+            "l"((const char *)src + off), "r"(n), "r"(b)
+            : "memory");
+    }
+}
+
+// Bounded wait for the staging copy: polls the mbarrier's phase 0.
+__device__ __forceinline__ bool wait_bitmap(unsigned long long *bar) {
+    const unsigned b = smem_u32(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(b)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Ray phase
+// ---------------------------------------------------------------------------
+template <bool DYN, class B>
+__device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, const TileDev &T,
+                          int K, const float2 *beams, const EnvSlot *slots, const int *fin_slot,
+                          int n_fin, const DynEnv *dyn, int *next_chunk) {
+    const int lane = threadIdx.x & 31;
+    const int n_main = T.env_count * K;
+    const int total = n_main + n_fin * K;
+    const float rmax_c = A.max_range * M.inv_res;
+    const int nd = DYN ? A.p.n_dyn : 0;
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(next_chunk, 1);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        const int base = chunk * 32;
+        if (base >= total) break;
+        const int rid = base + lane;
+        unsigned vis = 0;
+        if (rid < total) {
+            const bool fin = rid >= n_main;
+            const int rr = fin ? rid - n_main : rid;
+            const int q = rr / K;
+            const int k = rr - q * K;
+            const int s = fin ? fin_slot[q] : q;
+            const EnvSlot &es = slots[s];
+            const float sx = fin ? es.fst : es.st, cx = fin ? es.fct : es.ct;
+            const float ox = fin ? es.fxc : es.xc, oy = fin ? es.fyc : es.yc;
+            const float2 ab = beams[k];
+            // Eq. 4: direction of theta + alpha_k by angle addition
+            const float dx = cx * ab.x - sx * ab.y;
+            const float dy = sx * ab.x + cx * ab.y;
+            int hit;
+            const float range = cast_ray<DYN>(bits, M, ox, oy, dx, dy, rmax_c, A.max_range,
+                                              DYN ? &dyn[2 * s + (fin ? 1 : 0)] : nullptr, nd,
+                                              hit, vis);
+            float *dst = fin ? A.final_obs : A.obs;
+            dst[es.obs_off + k] = fminf(range, A.max_range);
+            if (!fin && A.dbg_range) {
+                const long long ro = es.ray_off + k;
+                A.dbg_range[ro] = range;
+                A.dbg_hit[ro] = hit;
+                A.dbg_vis[ro] = vis;
+            }
+        }
+        if (A.stats) {
+            unsigned v = vis;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            const int nr = min(32, total - base);
+            if (lane == 0) {
+                atomicAdd(&A.stats[0], (unsigned long long)v);
+                atomicAdd(&A.stats[1], (unsigned long long)nr);
+            }
+        }
+    }
+}
+
+template <bool DYN>
+__global__ void __launch_bounds__(512) step_kernel(const StepArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ EnvSlot slots[kMaxTileEnvs];
+    __shared__ int fin_slot[kMaxTileEnvs];
+    __shared__ int n_fin;
+    __shared__ int next_chunk;
+    __shared__ __align__(8) unsigned long long bar;
+
+    const TileDev T = A.tiles[blockIdx.x];
+    const MapDev M = A.maps[T.map];
+    const int K = A.tab_k[T.tab];
+    const bool staged = M.n_words <= A.smem_map_words;
+    uint32_t *sbits = reinterpret_cast<uint32_t *>(smem);
+    float2 *sbeam = reinterpret_cast<float2 *>(smem + (size_t)A.smem_map_words * 4);
+    DynEnv *sdyn = reinterpret_cast<DynEnv *>(smem + (size_t)A.smem_map_words * 4 +
+                                              (size_t)A.max_k * sizeof(float2));
+    const uint32_t *gbits = A.bits + M.word_off;
+    const int tid = threadIdx.x;
+
+    if (staged && tid == 0) stage_bitmap(sbits, gbits, M.n_words, &bar);
+    const int toff = A.tab_off[T.tab];
+    for (int k = tid; k < K; k += blockDim.x)
+        sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
+    if (tid < T.env_count) {
+        const int e = A.perm[T.env_begin + tid];
+        slots[tid].env = e;
+        slots[tid].obs_off = A.obs_off[e];
+        slots[tid].ray_off = A.ray_off[e];
+    }
+    if (tid == 0) next_chunk = 0;
+    __syncthreads();
+    // every thread polls the copy's mbarrier (bounded); the block then agrees
+    // on one outcome so that all threads take the same path below
+    const bool ok = staged ? wait_bitmap(&bar) : true;
+    const bool failed = __syncthreads_or(!ok) != 0;
+    if (failed) {
+        // the copy did not land in time: report it, wait (bounded) for the
+        // copy in flight, and read the bitmap from global memory instead
+        if (tid == 0) atomicOr(A.status, kStatusCopyTimeout);
+        if (!ok) wait_bitmap(&bar);
+        __syncthreads();
+    }
+    const bool use_smem = staged && !failed;
+    if (tid < T.env_count) {
+        if (use_smem)
+            env_phase<DYN>(A, Bits<true>{sbits}, M, K, tid, slots[tid], &sdyn[2 * tid],
+                           &sdyn[2 * tid + 1]);
+        else
+            env_phase<DYN>(A, Bits<false>{gbits}, M, K, tid, slots[tid], &sdyn[2 * tid],
+                           &sdyn[2 * tid + 1]);
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const bool f = tid < T.env_count && slots[tid].fin;
+        const unsigned m = __ballot_sync(kFull, f);
+        if (f) fin_slot[__popc(m & ((1u << tid) - 1u))] = tid;
+        if (tid == 0) n_fin = __popc(m);
+    }
+    __syncthreads();
+    if (use_smem)
+        ray_phase<DYN>(A, Bits<true>{sbits}, M, T, K, sbeam, slots, fin_slot, n_fin, sdyn,
+                       &next_chunk);
+    else
+        ray_phase<DYN>(A, Bits<false>{gbits}, M, T, K, sbeam, slots, fin_slot, n_fin, sdyn,
+                       &next_chunk);
+}
+
+} // namespace
+
+size_t dyn_env_bytes() { return sizeof(DynEnv); }
+
+int launch_step(const StepArgs &a, int block_threads, int tile_envs, void *stream) {
+    if (a.n_tiles <= 0) return 0;
+    const bool dyn = a.p.n_dyn > 0;
+    const size_t smem = (size_t)a.smem_map_words * 4 + (size_t)a.max_k * sizeof(float2) +
+                        (dyn ? (size_t)2 * tile_envs * sizeof(DynEnv) : 0);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t err;
+    if (dyn) {
+        err = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err != cudaSuccess) return (int)err;
+        step_kernel<true><<<a.n_tiles, block_threads, smem, s>>>(a);
+    } else {
+        err = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err != cudaSuccess) return (int)err;
+        step_kernel<false><<<a.n_tiles, block_threads, smem, s>>>(a);
+    }
+    return (int)cudaGetLastError();
+}
+
+} // namespace flashnav

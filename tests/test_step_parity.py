@@ -1,0 +1,270 @@
+"""Parity of the CUDA step (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs.
+
+Bit-exact: done flags, hit cells, per-beam visit counts, step and episode
+counters, goals (they come from the reset RNG).  Toleranced (FP32, north
+star): ranges 1e-4 m, poses 1e-5; the observation bearing, which the oracle
+computes with a binary64 atan2, 1e-4 rad.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_15846_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RANGE_TOL = 1e-4
+POSE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def mods(oracle):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_15846_b300 import flashnav
+    return flashnav, oracle, torch
+
+
+def _ang(a, b):
+    d = np.abs(a - b)
+    return np.minimum(d, 2 * np.pi - d)
+
+
+def _compare_obs(obs, ref, beams, rows=None, what="obs"):
+    off = np.concatenate([[0], np.cumsum(beams.astype(np.int64) + 4)])
+    env_ids = range(len(beams)) if rows is None else rows
+    for e in env_ids:
+        k = int(beams[e])
+        a, b = obs[off[e]:off[e + 1]], ref[off[e]:off[e + 1]]
+        dr = np.abs(a[:k] - b[:k]).max() if k else 0.0
+        assert dr <= RANGE_TOL, f"{what} env {e}: range error {dr}"
+        assert abs(a[k] - b[k]) <= POSE_TOL * 10, f"{what} env {e}: goal distance"
+        assert _ang(a[k + 1], b[k + 1]) <= 1e-4, f"{what} env {e}: bearing"
+        assert a[k + 2] == b[k + 2] and a[k + 3] == b[k + 3], f"{what} env {e}: velocity"
+
+
+def _compare_state(sim, ref, tag):
+    f, i, d = sim.get_state()
+    rf, ri, rd = ref.get_state()
+    assert np.array_equal(i, ri), f"{tag}: step/episode counters differ"
+    assert np.array_equal(f[:, 5:7], rf[:, 5:7]), f"{tag}: goals differ"
+    assert np.abs(f[:, :2] - rf[:, :2]).max() <= POSE_TOL, f"{tag}: positions"
+    assert _ang(f[:, 2], rf[:, 2]).max() <= POSE_TOL, f"{tag}: headings"
+    assert np.abs(f[:, 7] - rf[:, 7]).max() <= POSE_TOL, f"{tag}: d_prev"
+    if d.size:
+        assert np.abs(d - rd).max() <= POSE_TOL, f"{tag}: moving discs"
+    return int((f == rf).all())
+
+
+def _compare_debug(sim, ref, tag):
+    r, h, v = sim.debug()
+    rr, rh, rv = ref.debug()
+    assert np.array_equal(h, rh), f"{tag}: hit cells differ at {np.flatnonzero(h != rh)[:8]}"
+    assert np.array_equal(v, rv), f"{tag}: visit counts differ"
+    assert np.abs(r - rr).max() <= RANGE_TOL, f"{tag}: ranges"
+
+
+def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=8,
+               check_state_every=1):
+    flashnav, oracle, torch = mods
+    sim = flashnav.NavSim.from_workload(wl)
+    sim.set_debug(True)
+    if launch:
+        sim.set_launch(*launch)
+    ref = oracle.OracleSim.from_workload(wl, threads=threads)
+    obs = sim.reset(seed)
+    robs = ref.reset(seed)
+    _compare_obs(obs.cpu().numpy(), robs, wl.env_beams, what="reset obs")
+    _compare_state(sim, ref, "reset")
+    _compare_debug(sim, ref, "reset")
+    acts = W.uniform_actions(seed + 1000, n_steps, wl.n_envs)
+    n_done = 0
+    for t in range(n_steps):
+        a = torch.from_numpy(acts[t]).cuda()
+        if want_final:
+            o, r, d, fo = sim.step(a, want_final=True)
+            ro, rr, rd, rfo = ref.step(acts[t], want_final=True)
+        else:
+            o, r, d = sim.step(a)
+            ro, rr, rd = ref.step(acts[t])
+        d = d.cpu().numpy()
+        assert np.array_equal(d, rd), f"step {t}: done flags differ at {np.flatnonzero(d != rd)[:8]}"
+        assert np.abs(r.cpu().numpy() - rr).max() <= 1e-5, f"step {t}: reward"
+        _compare_obs(o.cpu().numpy(), ro, wl.env_beams, what=f"step {t} obs")
+        if want_final:
+            ended = np.flatnonzero(d & 3)
+            n_done += len(ended)
+            if len(ended):
+                _compare_obs(fo.cpu().numpy(), rfo, wl.env_beams, rows=ended,
+                             what=f"step {t} final obs")
+        _compare_debug(sim, ref, f"step {t}")
+        if t % check_state_every == 0 or t == n_steps - 1:
+            _compare_state(sim, ref, f"step {t}")
+    sim.sync(60000)
+    return sim, ref, n_done
+
+
+def test_reset_and_1000_free_running_steps_small(mods):
+    """64 envs, one 64x64 map, 180 beams, 4 m, 1000 steps with auto-reset."""
+    wl = W.config_small()
+    _, _, n_done = run_parity(mods, wl, 1000, seed=1)
+    assert n_done > 100  # resets are exercised
+
+
+def test_throughput_workload_steps(mods):
+    """4096 envs over 16 maps of 256x256, 360 beams, r_max 6 m, in the launch
+    shape the benchmark times."""
+    wl = W.config_throughput()
+    run_parity(mods, wl, 4, seed=5, want_final=False)
+
+
+def test_visit_counter_matches_oracle(mods):
+    flashnav, oracle, torch = mods
+    wl = W.config_throughput(n_envs=512, n_maps=4)
+    sim = flashnav.NavSim.from_workload(wl)
+    ref = oracle.OracleSim.from_workload(wl, threads=8)
+    sim.reset(2)
+    ref.reset(2)
+    sim.set_stats(True)
+    v0 = ref.visits()
+    acts = W.uniform_actions(2, 6, wl.n_envs)
+    for t in range(6):
+        sim.step(torch.from_numpy(acts[t]).cuda(), want_final=True)
+        ref.step(acts[t], want_final=True)
+    visits, rays = sim.stats()
+    assert visits == ref.visits() - v0
+    assert rays >= 6 * wl.n_envs * 360
+
+
+@pytest.mark.parametrize("launch", [(1, 64, 0), (3, 96, 0), (32, 512, 0), (8, 256, 16),
+                                    (5, 128, 16)])
+def test_launch_shapes_and_ragged_tiles(mods, launch):
+    """Ragged env count, a beam count that is not a multiple of 32, tiles of
+    1..32 envs, 64..512 threads, and the L2 path (bitmap not staged)."""
+    wl = W.config_small(n_envs=37)
+    wl.env_beams[:] = 37
+    run_parity(mods, wl, 60, seed=7, launch=launch)
+
+
+def test_single_env_single_beam(mods):
+    wl = W.config_small(n_envs=1)
+    wl.env_beams[:] = 1
+    run_parity(mods, wl, 50, seed=3)
+
+
+def _mixed(n_envs=96, n_dyn=0, sizes=(48, 96, 160, 200), seed0=40):
+    maps = [W.make_map(seed0 + i, s, s + 8 * i, 0.12 + 0.03 * i, corridors=True)
+            for i, s in enumerate(sizes)]
+    e = np.arange(n_envs)
+    return W.Workload(
+        name="mixed", maps=maps, env_map=(e % len(maps)).astype(np.int32),
+        env_beams=np.array([180, 360, 720, 45], np.int32)[(e // 4) % 4],
+        env_robot=(e % 2).astype(np.int32), robots=[W.DISC, W.RECT], max_range=6.0,
+        params=W.Params(n_dyn=n_dyn, goal_dmin=1.0, goal_dmax=6.0))
+
+
+def test_mixed_maps_beams_and_rectangles(mods):
+    run_parity(mods, _mixed(), 80, seed=11)
+
+
+def test_moving_discs(mods):
+    run_parity(mods, _mixed(n_dyn=8), 80, seed=12)
+
+
+def test_moving_discs_l2_path(mods):
+    run_parity(mods, _mixed(n_dyn=3), 40, seed=13, launch=(4, 128, 16))
+
+
+def test_exclusive_reward_and_270_degree_fan(mods):
+    wl = W.config_small(n_envs=40)
+    wl.params = W.Params(goal_dmin=1.0, goal_dmax=1e9, reward_mode=1, fov_deg=270.0)
+    wl.env_beams[:] = 34
+    run_parity(mods, wl, 200, seed=4)
+
+
+def test_cramped_map(mods):
+    wl = W.config_small(n_envs=48)
+    wl.maps = [W.make_map(77, 96, 96, 0.40)]
+    run_parity(mods, wl, 100, seed=8)
+
+
+def test_lockstep_random_states(mods):
+    """Injected states (positions anywhere in free space, any heading, step
+    counters at the horizon) give the same single step on both sides."""
+    flashnav, oracle, torch = mods
+    wl = W.config_throughput(n_envs=1024, n_maps=4)
+    sim = flashnav.NavSim.from_workload(wl)
+    sim.set_debug(True)
+    ref = oracle.OracleSim.from_workload(wl, threads=8)
+    sim.reset(0)
+    ref.reset(0)
+    rng = np.random.default_rng(0)
+    f = np.zeros((wl.n_envs, 8), np.float32)
+    i2 = np.zeros((wl.n_envs, 2), np.int32)
+    for e in range(wl.n_envs):
+        occ = wl.maps[wl.env_map[e]]
+        free = np.argwhere(occ == 0)
+        j, i = free[rng.integers(len(free))]
+        f[e, 0] = (i + rng.random()) * W.RES
+        f[e, 1] = (j + rng.random()) * W.RES
+        f[e, 2] = rng.uniform(-math.pi, math.pi)
+        j2, i2_ = free[rng.integers(len(free))]
+        f[e, 5] = (i2_ + 0.5) * W.RES
+        f[e, 6] = (j2 + 0.5) * W.RES
+        f[e, 7] = rng.uniform(0, 10)
+        i2[e, 0] = rng.integers(0, 201)
+        i2[e, 1] = rng.integers(0, 1000)
+    sim.set_state(99, f, i2)
+    ref.set_state(99, f, i2)
+    acts = W.uniform_actions(99, 1, wl.n_envs)[0]
+    o, r, d, fo = sim.step(torch.from_numpy(acts).cuda(), want_final=True)
+    ro, rr, rd, rfo = ref.step(acts, want_final=True)
+    d = d.cpu().numpy()
+    assert np.array_equal(d, rd)
+    assert np.abs(r.cpu().numpy() - rr).max() <= 1e-5
+    _compare_obs(o.cpu().numpy(), ro, wl.env_beams)
+    ended = np.flatnonzero(d & 3)
+    assert len(ended) > 10
+    _compare_obs(fo.cpu().numpy(), rfo, wl.env_beams, rows=ended, what="final obs")
+    _compare_debug(sim, ref, "lockstep")
+    _compare_state(sim, ref, "lockstep")
+
+
+def test_step_host_matches_device_step(mods):
+    flashnav, oracle, torch = mods
+    wl = W.config_small(n_envs=64)
+    a_sim = flashnav.NavSim.from_workload(wl)
+    b_sim = flashnav.NavSim.from_workload(wl)
+    a_sim.reset(5)
+    b_sim.reset(5)
+    acts = W.uniform_actions(5, 30, wl.n_envs)
+    n = a_sim.obs_size
+    for t in range(30):
+        o, r, d, fo = a_sim.step(torch.from_numpy(acts[t]).cuda(), want_final=True)
+        ho = np.zeros(n, np.float32)
+        hr = np.zeros(wl.n_envs, np.float32)
+        hd = np.zeros(wl.n_envs, np.uint8)
+        hf = np.zeros(n, np.float32)
+        b_sim.step_host(np.ascontiguousarray(acts[t]), ho, hr, hd, hf)
+        dd = d.cpu().numpy()
+        assert np.array_equal(o.cpu().numpy(), ho)
+        assert np.array_equal(r.cpu().numpy(), hr)
+        assert np.array_equal(dd, hd)
+        ended = np.flatnonzero(dd & 3)
+        off = a_sim.obs_offsets
+        fa = fo.cpu().numpy()
+        for e in ended:
+            assert np.array_equal(fa[off[e]:off[e + 1]], hf[off[e]:off[e + 1]])
+
+
+def test_sync_reports_clean_status(mods):
+    flashnav, oracle, torch = mods
+    wl = W.config_small(n_envs=8)
+    sim = flashnav.NavSim.from_workload(wl)
+    sim.reset(1)
+    sim.sync(10000)
