@@ -112,7 +112,7 @@ def make_workload(rank: int):
     return W.config_throughput(seed0=100 + 1000 * rank)
 
 
-def cpu_baseline(wl, seconds: float = 12.0):
+def cpu_baseline(wl, seconds: float = 15.0):
     """The oracle, as it stands, on all host cores over a bounded sample of the
     same workload: full 4096-env steps until ~`seconds` have elapsed."""
     from oracle import oracle
@@ -127,7 +127,7 @@ def cpu_baseline(wl, seconds: float = 12.0):
         ref.step(acts[n % 64])
         n += 1
         el = time.perf_counter() - t0
-        if (el > seconds and n >= 3) or n >= 64:
+        if (el > seconds and n >= 3) or n >= 512:
             break
     return {"value": wl.n_envs * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} full steps of the {wl.n_envs}-env workload (C oracle, OpenMP over "
@@ -221,6 +221,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     sim.reset(SEED + rank, obs)
+    if args.launch:
+        sim.set_launch(*[int(v) for v in args.launch.split(",")])
+    else:
+        sim.autotune(steps=12)
+    launch = sim.get_launch()
+    sim.reset(SEED + rank, obs)
     for t in range(args.warmup):
         sim.step(actions[t], obs, rew, done)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -297,7 +303,11 @@ def run_gpu(args):
                        "map": "256x256", "beams": 360, "max_range_m": wl.max_range,
                        "robot": "disc r=0.18 m", "actions": "uniform [-1,1]^2",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"env shards x{world}"},
+                       "parallelism": f"env shards x{world}",
+                       "launch": {"tile_envs": launch[0], "block_threads": launch[1],
+                                  "smem_map_bytes": launch[2], "max_regs": launch[3],
+                                  "byte_cells": launch[4],
+                                  "chosen_by": "fixed" if args.launch else "autotuner"}},
             "beam_casts_per_s": world * rays / (step_ms / 1e3),
             "cell_visits_per_s": world * visits / (step_ms / 1e3),
             "visits_per_step": visits_per_launch,
@@ -329,6 +339,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="",
+                    help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells "
+                         "(default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

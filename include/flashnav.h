@@ -156,12 +156,45 @@ int nav_get_debug(nav_handle *h, float *ranges_host, int32_t *hits_host,
 int nav_set_stats(nav_handle *h, int enable);
 int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
 
-/* Launch shape: envs per CTA tile (1..32) and threads per CTA (64..1024,
- * multiple of 32); smem_map_bytes caps the bitmap size staged into shared
- * memory (larger maps are read through L1/L2).  0 keeps the current value. */
-int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes);
+/* Launch shape.  One persistent grid per step (SMs x resident CTAs, each CTA
+ * taking tiles of envs that share a map and a beam count from a queue):
+ *   tile_envs      envs per CTA tile (1..32)
+ *   block_threads  threads per CTA (64..512, multiple of 32)
+ *   smem_map_bytes shared-memory budget for the staged map (<= 200 KiB); a
+ *                  map that does not fit is read as packed bits through L1/L2
+ *   max_regs       register cap per thread: 32, 40 or 64 (more resident CTAs
+ *                  against fewer registers)
+ *   byte_cells     1: stage maps that fit as one byte per cell (expanded from
+ *                  the packed bits; cheaper lookups), 2: stage packed bits
+ *                  (bulk TMA copy)
+ * 0 keeps the current value.  Synchronises the handle's stream. */
+int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes,
+                   int max_regs, int byte_cells);
 int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads,
-                   int *smem_map_bytes);
+                   int *smem_map_bytes, int *max_regs, int *byte_cells);
+
+/* Autotuner (no paper counterpart; it picks the launch shape for this
+ * handle's mix of map sizes, beam counts and robots).  From a device copy of
+ * the current state it times `steps` steps of each candidate with uniform
+ * random actions: first tile_envs x block_threads x max_regs, then the
+ * staging mode and shared-memory budget for the best shape.  It restores the
+ * state and keeps the fastest candidate.  Synchronous.  best_ms (host, may be
+ * NULL) receives the winner's mean step time. */
+int nav_autotune(nav_handle *h, int steps, float *best_ms);
+
+/* Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step) to
+ * actions_dev ([n_envs][2] float) on the handle's stream: a seeded input
+ * generator for throughput runs. */
+int nav_uniform_actions(nav_handle *h, uint64_t seed, uint32_t step, float *actions_dev);
+
+/* CUDA graph of n_steps consecutive nav_step calls: step t reads
+ * actions_dev + t * 2 * n_envs ([n_steps][n_envs][2] float) and overwrites
+ * obs_dev, reward_dev, done_dev (and final_obs_dev if not NULL).  The graph is
+ * owned by the handle (a new capture replaces it) and needs a non-default
+ * stream bound with nav_set_stream.  nav_graph_launch replays it. */
+int nav_graph_capture(nav_handle *h, int n_steps, const float *actions_dev, float *obs_dev,
+                      float *reward_dev, uint8_t *done_dev, float *final_obs_dev);
+int nav_graph_launch(nav_handle *h);
 
 const char *nav_last_error(const nav_handle *h);
 void nav_free(nav_handle *h);

@@ -144,8 +144,10 @@ struct nav_handle {
     std::vector<int64_t> obs_off, ray_off;
     std::vector<int> env_map, env_tab, env_k;
     std::vector<MapDev> maps;
-    int tile_envs = 8, block_threads = 256, smem_map_bytes = 96 * 1024;
-    int max_map_words = 0;
+    LaunchCfg cfg;
+    int smem_map_bytes = 80 * 1024;
+    int byte_cells = 1;
+    MapDev *d_maps = nullptr;
     int debug = 0, stats = 0;
     uint64_t seed = 0;
     std::string err;
@@ -158,6 +160,11 @@ struct nav_handle {
     float *d_dbg_range = nullptr;
     int *d_dbg_hit = nullptr;
     unsigned *d_dbg_vis = nullptr;
+    // state snapshot (autotuner), graph, tuning buffers
+    float *snap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    float *tune_act = nullptr, *tune_obs = nullptr, *tune_rew = nullptr;
+    unsigned char *tune_done = nullptr;
     // nav_step_host staging
     float *h_act = nullptr, *h_obs = nullptr, *h_rew = nullptr, *h_fin = nullptr;
     unsigned char *h_done = nullptr;
@@ -193,12 +200,12 @@ int build_tiles(nav_handle *h) {
         while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
                h->env_tab[perm[t]] == h->env_tab[perm[s]])
             ++t;
-        for (int b = s; b < t; b += h->tile_envs) {
+        for (int b = s; b < t; b += h->cfg.tile_envs) {
             TileDev td;
             td.map = h->env_map[perm[s]];
             td.tab = h->env_tab[perm[s]];
             td.env_begin = b;
-            td.env_count = std::min(h->tile_envs, t - b);
+            td.env_count = std::min(h->cfg.tile_envs, t - b);
             tiles.push_back(td);
         }
         s = t;
@@ -228,17 +235,31 @@ int build_tiles(nav_handle *h) {
     return NAV_OK;
 }
 
-void set_smem_cap(nav_handle *h) {
-    int cap_words = h->smem_map_bytes / 4;
-    // stage every map that fits: the region is sized for the largest of them
-    int used = 0;
-    for (const MapDev &m : h->maps)
-        if (m.n_words <= cap_words) used = std::max(used, m.n_words);
-    h->a.smem_map_words = used;
+// Chooses each map's staging: one byte per cell in shared memory when byte
+// maps are enabled and it fits under the cap, else packed bits in shared
+// memory when they fit, else packed bits read through L1/L2.  The shared
+// region is sized for the largest staged map.
+int set_map_modes(nav_handle *h) {
+    int region = 0;
+    for (MapDev &m : h->maps) {
+        if (h->byte_cells == 1 && m.n_bytes <= h->smem_map_bytes) m.mode = kMapSharedBytes;
+        else if (m.n_words * 4 <= h->smem_map_bytes) m.mode = kMapSharedBits;
+        else m.mode = kMapGlobal;
+        const int need = m.mode == kMapSharedBytes ? m.n_bytes
+                         : m.mode == kMapSharedBits ? m.n_words * 4 : 0;
+        region = std::max(region, need);
+    }
+    h->a.smem_region_bytes = region;
+    if (h->d_maps) {
+        cudaError_t e = cudaMemcpy(h->d_maps, h->maps.data(), h->maps.size() * sizeof(MapDev),
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(maps)");
+    }
+    return NAV_OK;
 }
 
 int launch(nav_handle *h) {
-    int rc = launch_step(h->a, h->block_threads, h->tile_envs, h->stream);
+    int rc = launch_step(h->a, h->cfg, h->stream);
     if (rc != 0) return cuda_fail(h, (cudaError_t)rc, "step kernel launch");
     return NAV_OK;
 }
@@ -321,10 +342,16 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         MapDev md;
         md.w = mp.width;
         md.h = mp.height;
-        int pitch = (mp.width + 2 + 31) / 32;
+        int pitch = (mp.width + 2 * kPad + 31) / 32;
         if ((pitch & 1) == 0) pitch += 1;
         md.pitch = pitch;
-        const long long nw = (long long)(mp.height + 2) * pitch;
+        const long long nw = (long long)(mp.height + 2 * kPad) * pitch;
+        int bstride = (mp.width + 2 * kPad + 3) / 4 * 4;
+        if (((bstride / 4) & 1) == 0) bstride += 4;
+        md.byte_stride = bstride;
+        const long long nb = (long long)(mp.height + 2 * kPad) * bstride;
+        md.n_bytes = nb > (1 << 30) ? (1 << 30) : (int)((nb + 15) / 16 * 16);
+        md.mode = kMapGlobal;
         md.n_words = (int)((nw + 3) / 4 * 4);
         md.word_off = (long long)words.size();
         md.res = mp.resolution;
@@ -334,10 +361,9 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         for (int j = 0; j < mp.height; ++j)
             for (int i = 0; i < mp.width; ++i)
                 if (!mp.occ[(size_t)j * mp.width + i]) {
-                    const long long b = (long long)(j + 1) * pitch * 32 + (i + 1);
+                    const long long b = (long long)(j + kPad) * pitch * 32 + (i + kPad);
                     base[b >> 5] |= 1u << (b & 31);
                 }
-        h->max_map_words = std::max(h->max_map_words, md.n_words);
         h->maps.push_back(md);
     }
     // envs
@@ -435,6 +461,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     } while (0)
     NAV_UP(bits, words);
     NAV_UP(d_maps, h->maps);
+    h->d_maps = d_maps;
     NAV_UP(d_cs, cs_dev);
     NAV_UP(d_rob, rdev);
     NAV_UP(d_spawn, spawn);
@@ -485,11 +512,13 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.episode, E);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.dyn, E * std::max(P.n_dyn, 1));
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.status, 1);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.tile_queue, 2);
     if (ce == cudaSuccess) ce = h->arena.alloc(&h->d_stats, 2);
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMalloc(state)"));
     cudaMemset(A.step, 0, E * sizeof(int));
     cudaMemset(A.episode, 0, E * sizeof(unsigned));
     cudaMemset(A.status, 0, sizeof(int));
+    cudaMemset(A.tile_queue, 0, 2 * sizeof(int));
     cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long));
     A.stats = nullptr;
     A.p = ParamsDev{P.dt, P.goal_tol, P.c_progress, P.step_penalty, P.r_goal, P.r_coll,
@@ -497,8 +526,8 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
                     P.dyn_speed_max, P.dyn_min_sep, P.reward_mode};
     A.max_range = max_range;
     A.max_k = h->max_k;
-    set_smem_cap(h);
-    int rc = build_tiles(h);
+    int rc = set_map_modes(h);
+    if (rc == NAV_OK) rc = build_tiles(h);
     if (rc != NAV_OK) return bail(rc);
     ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "create"));
@@ -735,31 +764,215 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays) {
     return NAV_OK;
 }
 
-int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes) {
+int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes,
+                   int max_regs, int byte_cells) {
     if (!h) return NAV_E_INVAL;
     if (tile_envs < 0 || tile_envs > kMaxTileEnvs || block_threads < 0 || block_threads > 512 ||
         (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
-        smem_map_bytes < 0 || smem_map_bytes > 200 * 1024)
+        smem_map_bytes < 0 || smem_map_bytes > 200 * 1024 ||
+        !(max_regs == 0 || max_regs == 32 || max_regs == 40 || max_regs == 64) ||
+        byte_cells < 0 || byte_cells > 2)
         return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");
-    if (block_threads) h->block_threads = block_threads;
-    if (smem_map_bytes) {
-        h->smem_map_bytes = smem_map_bytes;
-        set_smem_cap(h);
-    }
-    if (tile_envs && tile_envs != h->tile_envs) {
-        cudaError_t e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-        h->tile_envs = tile_envs;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if (block_threads) h->cfg.block_threads = block_threads;
+    if (max_regs) h->cfg.max_regs = max_regs;
+    if (smem_map_bytes) h->smem_map_bytes = smem_map_bytes;
+    if (byte_cells) h->byte_cells = byte_cells;
+    int rc = set_map_modes(h);
+    if (rc != NAV_OK) return rc;
+    if (tile_envs && tile_envs != h->cfg.tile_envs) {
+        h->cfg.tile_envs = tile_envs;
         return build_tiles(h);
     }
     return NAV_OK;
 }
 
-int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int *smem_map_bytes) {
+int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int *smem_map_bytes,
+                   int *max_regs, int *byte_cells) {
     if (!h) return NAV_E_INVAL;
-    if (tile_envs) *tile_envs = h->tile_envs;
-    if (block_threads) *block_threads = h->block_threads;
+    if (tile_envs) *tile_envs = h->cfg.tile_envs;
+    if (block_threads) *block_threads = h->cfg.block_threads;
     if (smem_map_bytes) *smem_map_bytes = h->smem_map_bytes;
+    if (max_regs) *max_regs = h->cfg.max_regs;
+    if (byte_cells) *byte_cells = h->byte_cells;
+    return NAV_OK;
+}
+
+namespace {
+
+// Device-to-device copy of the per-env state (save = true keeps a copy in the
+// handle's snapshot buffer, false restores it).
+int copy_state(nav_handle *h, bool save) {
+    const size_t E = (size_t)h->n_envs;
+    const size_t nd = (size_t)std::max(h->par.n_dyn, 1);
+    cudaError_t e = cudaSuccess;
+    if (!h->snap) {
+        e = h->arena.alloc(&h->snap, 10 * E + 4 * nd * E);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(snapshot)");
+    }
+    StepArgs &A = h->a;
+    void *cols[10] = {A.x, A.y, A.th, A.v, A.w, A.gx, A.gy, A.dprev, A.step, A.episode};
+    for (int c = 0; c < 10 && e == cudaSuccess; ++c) {
+        float *sn = h->snap + c * E;
+        e = save ? cudaMemcpyAsync(sn, cols[c], E * 4, cudaMemcpyDeviceToDevice, h->stream)
+                 : cudaMemcpyAsync(cols[c], sn, E * 4, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e == cudaSuccess) {
+        float *sn = h->snap + 10 * E;
+        e = save ? cudaMemcpyAsync(sn, A.dyn, nd * E * 16, cudaMemcpyDeviceToDevice, h->stream)
+                 : cudaMemcpyAsync(A.dyn, sn, nd * E * 16, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "state snapshot copy");
+    return NAV_OK;
+}
+
+int ensure_tune_buffers(nav_handle *h) {
+    if (h->tune_act) return NAV_OK;
+    const size_t E = (size_t)h->n_envs, O = (size_t)h->obs_off.back();
+    cudaError_t e = h->arena.alloc(&h->tune_act, 2 * E);
+    if (e == cudaSuccess) e = h->arena.alloc(&h->tune_obs, O);
+    if (e == cudaSuccess) e = h->arena.alloc(&h->tune_rew, E);
+    if (e == cudaSuccess) e = h->arena.alloc(&h->tune_done, E);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(tuning buffers)");
+    return NAV_OK;
+}
+
+// Mean device time of `steps` steps (after 2 untimed) from the snapshot state
+// with hash-uniform actions; +inf if a launch fails.
+float time_config(nav_handle *h, int steps, cudaEvent_t e0, cudaEvent_t e1) {
+    StepArgs A = h->a;
+    A.mode = 0;
+    A.obs = h->tune_obs;
+    A.reward = h->tune_rew;
+    A.done = h->tune_done;
+    A.final_obs = nullptr;
+    A.actions = h->tune_act;
+    A.stats = nullptr;
+    A.dbg_range = nullptr;
+    A.dbg_hit = nullptr;
+    A.dbg_vis = nullptr;
+    if (copy_state(h, false) != NAV_OK) return INFINITY;
+    float total = 0.0f;
+    for (int t = 0; t < steps + 2; ++t) {
+        launch_uniform_actions(h->tune_act, h->n_envs, 0x7A11ull, (unsigned)t, h->stream);
+        cudaEventRecord(e0, h->stream);
+        if (launch_step(A, h->cfg, h->stream) != 0) {
+            cudaGetLastError();
+            cudaStreamSynchronize(h->stream);
+            return INFINITY;
+        }
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return INFINITY;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (t >= 2) total += ms;
+    }
+    return total / steps;
+}
+
+} // namespace
+
+int nav_autotune(nav_handle *h, int steps, float *best_ms) {
+    if (!h || steps <= 0) return fail(h, NAV_E_INVAL, "nav_autotune: bad argument");
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamSynchronize");
+    int rc = ensure_tune_buffers(h);
+    if (rc == NAV_OK) rc = copy_state(h, true);
+    if (rc != NAV_OK) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = INFINITY;
+    LaunchCfg best_cfg = h->cfg;
+    int best_cap = h->smem_map_bytes, best_bytes = h->byte_cells;
+    // pass 1: launch shape with the current staging choice
+    const int tiles[] = {1, 2, 4, 8, 16};
+    const int blocks[] = {128, 256, 512};
+    const int regs[] = {32, 40, 64};
+    for (int te : tiles) {
+        if (te > 1 && te > h->n_envs) continue;
+        h->cfg.tile_envs = te;
+        if ((rc = build_tiles(h)) != NAV_OK) break;
+        for (int bt : blocks)
+            for (int mr : regs) {
+                h->cfg.block_threads = bt;
+                h->cfg.max_regs = mr;
+                const float ms = time_config(h, steps, e0, e1);
+                if (ms < best) { best = ms; best_cfg = h->cfg; }
+            }
+    }
+    // pass 2: staging (byte cells or packed bits) and the shared-memory cap
+    if (rc == NAV_OK) {
+        h->cfg = best_cfg;
+        rc = build_tiles(h);
+        const int caps[] = {24 * 1024, 80 * 1024, 160 * 1024};
+        for (int bc = 1; bc <= 2 && rc == NAV_OK; ++bc)
+            for (int cap : caps) {
+                h->byte_cells = bc;
+                h->smem_map_bytes = cap;
+                if ((rc = set_map_modes(h)) != NAV_OK) break;
+                const float ms = time_config(h, steps, e0, e1);
+                if (ms < best) { best = ms; best_cap = cap; best_bytes = bc; }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg = best_cfg;
+    h->smem_map_bytes = best_cap;
+    h->byte_cells = best_bytes;
+    int rc2 = set_map_modes(h);
+    if (rc2 == NAV_OK) rc2 = build_tiles(h);
+    int rc3 = copy_state(h, false);
+    ce = cudaStreamSynchronize(h->stream);
+    if (rc != NAV_OK) return rc;
+    if (rc2 != NAV_OK) return rc2;
+    if (rc3 != NAV_OK) return rc3;
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "nav_autotune");
+    if (!(best < INFINITY)) return fail(h, NAV_E_CUDA, "nav_autotune: no launch shape ran");
+    if (best_ms) *best_ms = best;
+    return NAV_OK;
+}
+
+int nav_uniform_actions(nav_handle *h, uint64_t seed, uint32_t step, float *actions_dev) {
+    if (!h || !actions_dev) return fail(h, NAV_E_INVAL, "nav_uniform_actions: null argument");
+    int rc = launch_uniform_actions(actions_dev, h->n_envs, seed, step, h->stream);
+    if (rc != 0) return cuda_fail(h, (cudaError_t)rc, "uniform actions kernel");
+    return NAV_OK;
+}
+
+int nav_graph_capture(nav_handle *h, int n_steps, const float *actions_dev, float *obs_dev,
+                      float *reward_dev, uint8_t *done_dev, float *final_obs_dev) {
+    if (!h || n_steps <= 0 || !actions_dev || !obs_dev || !reward_dev || !done_dev)
+        return fail(h, NAV_E_INVAL, "nav_graph_capture: bad argument");
+    if (!h->stream) return fail(h, NAV_E_INVAL, "nav_graph_capture: bind a non-default stream");
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    int rc = NAV_OK;
+    for (int t = 0; t < n_steps && rc == NAV_OK; ++t)
+        rc = nav_step(h, actions_dev + (size_t)t * 2 * h->n_envs, obs_dev, reward_dev, done_dev,
+                      final_obs_dev);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != NAV_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    return NAV_OK;
+}
+
+int nav_graph_launch(nav_handle *h) {
+    if (!h || !h->graph) return fail(h, NAV_E_INVAL, "nav_graph_launch: no graph captured");
+    cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
     return NAV_OK;
 }
 
@@ -768,6 +981,7 @@ const char *nav_last_error(const nav_handle *h) { return h ? h->err.c_str() : "n
 void nav_free(nav_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     delete h;
 }
 

@@ -12,14 +12,20 @@ constexpr int kMaxDynRows = 16; // rows spanned by one stamped disc
 constexpr int kMaxTileEnvs = 32;
 constexpr int kMaxBeams = 2048;
 
-// Packed map: free bits (1 = free), one padding cell on every side that reads
-// as blocked, rows of `pitch` 32-bit words (odd, to spread smem banks); the
-// padded bit index of cell (i, j) is (j + 1) * pitch * 32 + (i + 1).
+// Packed map: free bits (1 = free), kPad padding cells on every side that
+// read as blocked, rows of `pitch` 32-bit words (odd, to spread smem banks);
+// the padded bit index of cell (i, j) is (j + kPad) * pitch * 32 + (i + kPad).
+// The same padded map as one byte per cell (1 = free) has a row stride of
+// byte_stride bytes (a multiple of 4 whose word count is odd).
+constexpr int kPad = 1;
 struct MapDev {
     int w, h, pitch, n_words; // n_words is a multiple of 4 (16-byte copies)
     long long word_off;       // into the concatenated bitmap, multiple of 4
     float res, inv_res;
+    int byte_stride, n_bytes; // byte view; n_bytes is a multiple of 16
+    int mode;                 // staging, one of MapMode
 };
+enum MapMode { kMapGlobal = 0, kMapSharedBits = 1, kMapSharedBytes = 2 };
 
 // C-space of one (map, robot) pair: spawnable cells ascending, the component
 // of each, and every component's cells grouped and ascending.
@@ -61,6 +67,7 @@ struct StepArgs {
     const TileDev *tiles;
     const int *perm;
     int n_tiles;
+    int *tile_queue; // [0] next tile to hand out, [1] CTAs finished; zero between launches
     // state (structure of arrays)
     float *x, *y, *th, *v, *w, *gx, *gy, *dprev;
     int *step;
@@ -80,13 +87,24 @@ struct StepArgs {
     unsigned long long seed;
     float max_range;
     int mode; // 0 step, 1 reset all
-    int smem_map_words; // capacity of the staged-bitmap region (0 = none)
+    int smem_region_bytes; // shared-memory region holding a staged map (0 = none)
     int max_k;
 };
 
 enum StatusBits { kStatusNoSpawn = 1, kStatusCopyTimeout = 2, kStatusBadPose = 4 };
 
-// Launches one step (or reset) of every tile on `stream`.
-int launch_step(const StepArgs &a, int block_threads, int tile_envs, void *stream);
+struct LaunchCfg {
+    int tile_envs = 2;     // envs per CTA tile
+    int block_threads = 256;
+    int max_regs = 32;     // register cap per thread: 32, 40 or 64
+};
+
+// Launches one step (or reset) of every tile on `stream`: persistent CTAs,
+// grid = SMs x resident CTAs per SM, capped by the tile count.
+int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
+
+// Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step).
+int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,
+                           void *stream);
 
 } // namespace flashnav

@@ -14,6 +14,7 @@
 // results (hit cells, flags, resets) are a fixed function of the inputs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "nav_internal.h"
@@ -92,38 +93,69 @@ __device__ __forceinline__ float draw_unit(unsigned bits24) {
 }
 
 // ---------------------------------------------------------------------------
-// Bitmap access
+// Map views.  Each view indexes the padded map (kPad blocked cells around the
+// W x H map) linearly: idx(i, j) = (j + kPad) * stride + (i + kPad), so a
+// step in x is +-1 and a step in y is +-stride.
+//   BitsShared  packed free bits staged in shared memory (bulk TMA copy)
+//   BitsGlobal  packed free bits read through L1/L2
+//   BytesShared one byte per cell in shared memory, expanded from the packed
+//               bits: a lookup is one byte load and one compare, which moves
+//               the shift and mask work of the bit lookup off the ALU pipe
 // ---------------------------------------------------------------------------
-template <bool SMEM> struct Bits;
-template <> struct Bits<true> {
-    const uint32_t *w; // shared memory
+struct BitsShared {
+    const uint32_t *w;
+    int stride; // pitch * 32
+    __device__ __forceinline__ bool free_at(int b) const {
+        return (__funnelshift_r(w[b >> 5], 0u, (unsigned)b) & 1u) != 0u;
+    }
     __device__ __forceinline__ uint32_t word(int i) const { return w[i]; }
 };
-template <> struct Bits<false> {
-    const uint32_t *__restrict__ w; // global, read-only for the kernel's lifetime
+struct BitsGlobal {
+    const uint32_t *__restrict__ w;
+    int stride;
+    __device__ __forceinline__ bool free_at(int b) const {
+        return (__funnelshift_r(__ldg(w + (b >> 5)), 0u, (unsigned)b) & 1u) != 0u;
+    }
     __device__ __forceinline__ uint32_t word(int i) const { return __ldg(w + i); }
 };
+struct BytesShared {
+    const uint8_t *c;
+    int stride; // byte pitch
+    __device__ __forceinline__ bool free_at(int b) const { return c[b] != 0; }
+};
 
-template <class B>
-__device__ __forceinline__ bool cell_free(const B &bits, int b) {
-    return (bits.word(b >> 5) >> (b & 31)) & 1u;
+template <class V> __device__ __forceinline__ int cell_index(const V &v, int i, int j) {
+    return (j + kPad) * v.stride + (i + kPad);
 }
 
-// Is any cell of row j, columns [i0, i1], blocked (occupied or off-map)?
-template <class B>
-__device__ bool row_blocked(const B &bits, const MapDev &M, int j, int i0, int i1) {
-    if (i0 > i1) return false;
-    if (j < 0 || j >= M.h || i0 < 0 || i1 >= M.w) return true;
-    const int base = (j + 1) * M.pitch * 32 + 1;
-    const int c0 = base + i0, c1 = base + i1;
+// Is any cell of row j, columns [i0, i1] (all inside the map), blocked?
+template <class V>
+__device__ __forceinline__ bool span_blocked(const V &v, int j, int i0, int i1) {
+    const int c0 = cell_index(v, i0, j), c1 = c0 + (i1 - i0);
     const int w0 = c0 >> 5, w1 = c1 >> 5;
     for (int wd = w0; wd <= w1; ++wd) {
         uint32_t m = kFull;
         if (wd == w0) m &= kFull << (c0 & 31);
         if (wd == w1) m &= kFull >> (31 - (c1 & 31));
-        if (~bits.word(wd) & m) return true;
+        if (~v.word(wd) & m) return true;
     }
     return false;
+}
+template <>
+__device__ __forceinline__ bool span_blocked<BytesShared>(const BytesShared &v, int j, int i0,
+                                                          int i1) {
+    const int c0 = cell_index(v, i0, j);
+    for (int k = 0; k <= i1 - i0; ++k)
+        if (!v.c[c0 + k]) return true;
+    return false;
+}
+
+// Is any cell of row j, columns [i0, i1], blocked (occupied or off-map)?
+template <class V>
+__device__ bool row_blocked(const V &v, const MapDev &M, int j, int i0, int i1) {
+    if (i0 > i1) return false;
+    if (j < 0 || j >= M.h || i0 < 0 || i1 >= M.w) return true;
+    return span_blocked(v, j, i0, i1);
 }
 
 // Cells of row j whose closed square meets the open disc (centre xc, yc,
@@ -222,26 +254,25 @@ __device__ void dyn_gate(const DynEnv &de, int nd, float xc, float yc, float dx,
 }
 
 // ---------------------------------------------------------------------------
-// Ray cast: Amanatides-Woo traversal over the padded free-bit map (Eq. 4-5).
-// Starting cell (floor xc, floor yc); per iteration the axis whose next
-// boundary is nearer is stepped (a tie steps x first), the entry parameter
-// t of the new cell is checked against r_max, then the cell is looked up.
-// The padding cells read as blocked, so leaving the map stops the walk
-// without a bounds test.  The loop ends within 2 r_max/res + 3 iterations:
-// each iteration adds tDelta >= 1 to one of tMaxX, tMaxY.
+// Ray cast: Amanatides-Woo traversal over a padded map view (Eq. 4-5).
+// Starting cell (floor xc, floor yc); per step the axis whose next boundary
+// is nearer is stepped (a tie steps x first), the entry parameter t of the
+// new cell is checked against r_max, then the cell is looked up.  Leaving the
+// map stops the walk at a padding cell without a bounds test.  The walk ends
+// within 2 r_max/res + 3 steps: each step adds tDelta >= 1 to tMaxX or tMaxY.
 // Returns the range in metres; hit = j*W+i, -1 off-map, -2 r_max.
 // ---------------------------------------------------------------------------
-template <bool DYN, class B>
-__device__ __forceinline__ float cast_ray(const B &bits, const MapDev &M, float xc, float yc,
+template <bool DYN, class V>
+__device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float xc, float yc,
                                           float dx, float dy, float rmax_c, float max_range,
                                           const DynEnv *de, int nd, int &hit, unsigned &vis) {
-    const int pb = M.pitch * 32;
+    const int pb = view.stride;
     if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
     const float fx = floorf(xc), fy = floorf(yc);
     const int i0 = (int)fx, j0 = (int)fy;
     if (i0 >= M.w || j0 >= M.h) { hit = -1; vis = 1; return 0.0f; }
-    int b = (j0 + 1) * pb + (i0 + 1);
-    if (!cell_free(bits, b) || (DYN && dyn_cell(*de, nd, i0, j0))) {
+    int b = cell_index(view, i0, j0);
+    if (!view.free_at(b) || (DYN && dyn_cell(*de, nd, i0, j0))) {
         hit = j0 * M.w + i0;
         vis = 1;
         return 0.0f;
@@ -263,14 +294,14 @@ __device__ __forceinline__ float cast_ray(const B &bits, const MapDev &M, float 
         b += sx ? sbx : sby;
         if (sx) tmx = tmx + tdx;
         else tmy = tmy + tdy;
-        if (!cell_free(bits, b)) { stopped = true; break; }
+        if (!view.free_at(b)) { stopped = true; break; }
         if (DYN && t >= glo && t <= ghi) {
             const int r = b / pb;
-            if (dyn_cell(*de, nd, b - r * pb - 1, r - 1)) { stopped = true; break; }
+            if (dyn_cell(*de, nd, b - r * pb - kPad, r - kPad)) { stopped = true; break; }
         }
     }
     const int r = b / pb;
-    const int i = b - r * pb - 1, j = r - 1;
+    const int i = b - r * pb - kPad, j = r - kPad;
     vis = 1u + (unsigned)(abs(i - i0) + abs(j - j0));
     if (!stopped) { hit = -2; return max_range; }
     hit = (i < 0 || j < 0 || i >= M.w || j >= M.h) ? -1 : j * M.w + i;
@@ -361,10 +392,10 @@ struct EnvSlot {
     int fin;
 };
 
-template <class B>
-__device__ __forceinline__ bool static_blocked(const B &bits, const MapDev &M, int i, int j) {
+template <class V>
+__device__ __forceinline__ bool static_blocked(const V &v, const MapDev &M, int i, int j) {
     if (i < 0 || j < 0 || i >= M.w || j >= M.h) return true;
-    return !cell_free(bits, (j + 1) * M.pitch * 32 + (i + 1));
+    return !v.free_at(cell_index(v, i, j));
 }
 
 // Sparse reset of env e for `episode` (Sec. 2.2.3): spawn cell uniform over
@@ -581,18 +612,24 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
 }
 
 // ---------------------------------------------------------------------------
-// Bulk (TMA) copy of the bitmap into shared memory
+// Staging of a map into shared memory
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ void init_copy_barrier(unsigned long long *bar) {
+    const unsigned b = smem_u32(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Issued by one thread: one arrive that expects n_words*4 bytes, then the
+// bulk copies (global -> shared, completion counted on the mbarrier).
 __device__ __forceinline__ void stage_bitmap(uint32_t *dst, const uint32_t *src, int n_words,
                                              unsigned long long *bar) {
     const unsigned b = smem_u32(bar);
     const unsigned bytes = (unsigned)n_words * 4u;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
                  : "memory");
@@ -607,21 +644,41 @@ __device__ __forceinline__ void stage_bitmap(uint32_t *dst, const uint32_t *src,
     }
 }
 
-// Bounded wait for the staging copy: polls the mbarrier's phase 0.
-__device__ __forceinline__ bool wait_bitmap(unsigned long long *bar) {
+// Bounded wait for the copy whose completion completes mbarrier phase `parity`.
+__device__ __forceinline__ bool wait_bitmap(unsigned long long *bar, unsigned parity) {
     const unsigned b = smem_u32(bar);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < (1 << 22); ++it) {
         unsigned ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(b)
+            : "r"(b), "r"(parity)
             : "memory");
         if (ok) return true;
     }
     return false;
+}
+
+// Expands a map's packed free bits (global) into one byte per cell in shared
+// memory; every thread of the CTA takes part.
+__device__ void expand_bytes(uint8_t *dst, const uint32_t *__restrict__ src, const MapDev &M) {
+    const int q4 = M.byte_stride >> 2; // 4-cell groups per row
+    const int rows = M.h + 2 * kPad;
+    const int pb = M.pitch * 32;
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (int q = threadIdx.x; q < rows * q4; q += blockDim.x) {
+        const int r = q / q4;
+        const int c = (q - r * q4) * 4;
+        uint32_t out = 0;
+        if (c < pb) { // four bits of one word: bit offsets are multiples of 4
+            const int bi = r * pb + c;
+            const uint32_t nib = (__ldg(src + (bi >> 5)) >> (bi & 31)) & 0xFu;
+            out = (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
+        }
+        d32[q] = out;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -683,96 +740,169 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     }
 }
 
-template <bool DYN>
-__global__ void __launch_bounds__(512) step_kernel(const StepArgs A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ EnvSlot slots[kMaxTileEnvs];
-    __shared__ int fin_slot[kMaxTileEnvs];
-    __shared__ int n_fin;
-    __shared__ int next_chunk;
-    __shared__ __align__(8) unsigned long long bar;
-
-    const TileDev T = A.tiles[blockIdx.x];
-    const MapDev M = A.maps[T.map];
-    const int K = A.tab_k[T.tab];
-    const bool staged = M.n_words <= A.smem_map_words;
-    uint32_t *sbits = reinterpret_cast<uint32_t *>(smem);
-    float2 *sbeam = reinterpret_cast<float2 *>(smem + (size_t)A.smem_map_words * 4);
-    DynEnv *sdyn = reinterpret_cast<DynEnv *>(smem + (size_t)A.smem_map_words * 4 +
-                                              (size_t)A.max_k * sizeof(float2));
-    const uint32_t *gbits = A.bits + M.word_off;
+template <bool DYN, class V>
+__device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const MapDev &M,
+                                         const TileDev &T, int K, const float2 *sbeam,
+                                         EnvSlot *slots, int *fin_slot, int *n_fin, DynEnv *sdyn,
+                                         int *next_chunk) {
     const int tid = threadIdx.x;
-
-    if (staged && tid == 0) stage_bitmap(sbits, gbits, M.n_words, &bar);
-    const int toff = A.tab_off[T.tab];
-    for (int k = tid; k < K; k += blockDim.x)
-        sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
-    if (tid < T.env_count) {
-        const int e = A.perm[T.env_begin + tid];
-        slots[tid].env = e;
-        slots[tid].obs_off = A.obs_off[e];
-        slots[tid].ray_off = A.ray_off[e];
-    }
-    if (tid == 0) next_chunk = 0;
-    __syncthreads();
-    // every thread polls the copy's mbarrier (bounded); the block then agrees
-    // on one outcome so that all threads take the same path below
-    const bool ok = staged ? wait_bitmap(&bar) : true;
-    const bool failed = __syncthreads_or(!ok) != 0;
-    if (failed) {
-        // the copy did not land in time: report it, wait (bounded) for the
-        // copy in flight, and read the bitmap from global memory instead
-        if (tid == 0) atomicOr(A.status, kStatusCopyTimeout);
-        if (!ok) wait_bitmap(&bar);
-        __syncthreads();
-    }
-    const bool use_smem = staged && !failed;
-    if (tid < T.env_count) {
-        if (use_smem)
-            env_phase<DYN>(A, Bits<true>{sbits}, M, K, tid, slots[tid], &sdyn[2 * tid],
-                           &sdyn[2 * tid + 1]);
-        else
-            env_phase<DYN>(A, Bits<false>{gbits}, M, K, tid, slots[tid], &sdyn[2 * tid],
-                           &sdyn[2 * tid + 1]);
-    }
+    if (tid < T.env_count)
+        env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1]);
     __syncthreads();
     if (tid < 32) {
         const bool f = tid < T.env_count && slots[tid].fin;
         const unsigned m = __ballot_sync(kFull, f);
         if (f) fin_slot[__popc(m & ((1u << tid) - 1u))] = tid;
-        if (tid == 0) n_fin = __popc(m);
+        if (tid == 0) *n_fin = __popc(m);
     }
     __syncthreads();
-    if (use_smem)
-        ray_phase<DYN>(A, Bits<true>{sbits}, M, T, K, sbeam, slots, fin_slot, n_fin, sdyn,
-                       &next_chunk);
-    else
-        ray_phase<DYN>(A, Bits<false>{gbits}, M, T, K, sbeam, slots, fin_slot, n_fin, sdyn,
-                       &next_chunk);
+    ray_phase<DYN>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
+}
+
+// Persistent CTAs: each CTA takes tiles from a global queue until none are
+// left.  A tile's map is staged into shared memory (bytes expanded from the
+// packed bits, or the packed bits by bulk TMA copy) only when the CTA's
+// previous tile used another map.  The last CTA to finish zeroes the queue
+// for the next launch on the stream.
+// MINB: resident 512-thread CTAs per SM the register allocation must allow
+// (4, 3, 2 -> at most 32, 40, 64 registers per thread).
+template <bool DYN, int MINB>
+__global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ EnvSlot slots[kMaxTileEnvs];
+    __shared__ int fin_slot[kMaxTileEnvs];
+    __shared__ int n_fin;
+    __shared__ int next_chunk;
+    __shared__ int tile_id;
+    __shared__ int staged_map;
+    __shared__ __align__(8) unsigned long long bar;
+
+    uint32_t *sbits = reinterpret_cast<uint32_t *>(smem);
+    uint8_t *sbytes = smem;
+    float2 *sbeam = reinterpret_cast<float2 *>(smem + (size_t)A.smem_region_bytes);
+    DynEnv *sdyn = reinterpret_cast<DynEnv *>(smem + (size_t)A.smem_region_bytes +
+                                              (size_t)A.max_k * sizeof(float2));
+    const int tid = threadIdx.x;
+    unsigned parity = 0;
+    int beam_tab = -1;
+    if (tid == 0) {
+        init_copy_barrier(&bar);
+        staged_map = -1;
+    }
+    for (;;) {
+        if (tid == 0) {
+            tile_id = atomicAdd(&A.tile_queue[0], 1);
+            next_chunk = 0;
+        }
+        __syncthreads();
+        const int tile = tile_id;
+        if (tile >= A.n_tiles) break;
+        const TileDev T = A.tiles[tile];
+        const MapDev M = A.maps[T.map];
+        const int K = A.tab_k[T.tab];
+        const uint32_t *gbits = A.bits + M.word_off;
+        const bool fresh = staged_map != T.map;
+        const bool copy = M.mode == kMapSharedBits && fresh;
+        if (copy && tid == 0) stage_bitmap(sbits, gbits, M.n_words, &bar);
+        if (M.mode == kMapSharedBytes && fresh) expand_bytes(sbytes, gbits, M);
+        if (T.tab != beam_tab) {
+            const int toff = A.tab_off[T.tab];
+            for (int k = tid; k < K; k += blockDim.x)
+                sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
+            beam_tab = T.tab;
+        }
+        if (tid < T.env_count) {
+            const int e = A.perm[T.env_begin + tid];
+            slots[tid].env = e;
+            slots[tid].obs_off = A.obs_off[e];
+            slots[tid].ray_off = A.ray_off[e];
+        }
+        bool ok = true;
+        if (copy) {
+            ok = wait_bitmap(&bar, parity);
+            parity ^= 1u;
+        }
+        // the block agrees on one outcome so that all threads take one path
+        const bool failed = __syncthreads_or(!ok) != 0;
+        if (failed) {
+            // the copy did not land in time: report it, wait (bounded) for the
+            // copy in flight, and read this tile's bitmap from global memory
+            if (tid == 0) atomicOr(A.status, kStatusCopyTimeout);
+            if (!ok) wait_bitmap(&bar, parity ^ 1u);
+        }
+        const int mode = failed ? (int)kMapGlobal : M.mode;
+        if (tid == 0) staged_map = mode == kMapGlobal ? -1 : T.map;
+        if (mode == kMapSharedBytes)
+            run_tile<DYN>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
+                          &n_fin, sdyn, &next_chunk);
+        else if (mode == kMapSharedBits)
+            run_tile<DYN>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+                          &n_fin, sdyn, &next_chunk);
+        else
+            run_tile<DYN>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+                          &n_fin, sdyn, &next_chunk);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        __threadfence();
+        const int done = atomicAdd(&A.tile_queue[1], 1);
+        if (done == (int)gridDim.x - 1) {
+            // every CTA has taken its last (empty) tile: reset for the next launch
+            A.tile_queue[0] = 0;
+            A.tile_queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// Uniform actions in [-1, 1]^2 from the counter hash keyed by (seed, env, step):
+// an input generator for autotuning and throughput runs (not part of a step).
+__global__ void uniform_actions_kernel(float2 *out, int n_envs, unsigned long long seed,
+                                       unsigned step) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_envs) return;
+    const unsigned long long h = draw64(seed, (unsigned)e, step, 0x5EEDu);
+    const float a = draw_unit((unsigned)(h >> 40)) * 2.0f - 1.0f;
+    const float b = draw_unit((unsigned)((h >> 8) & 0xFFFFFFull)) * 2.0f - 1.0f;
+    out[e] = make_float2(a, b);
+}
+
+template <bool DYN> const void *pick_kernel(int max_regs) {
+    if (max_regs <= 32) return (const void *)step_kernel<DYN, 4>;
+    if (max_regs <= 40) return (const void *)step_kernel<DYN, 3>;
+    return (const void *)step_kernel<DYN, 2>;
 }
 
 } // namespace
 
-size_t dyn_env_bytes() { return sizeof(DynEnv); }
-
-int launch_step(const StepArgs &a, int block_threads, int tile_envs, void *stream) {
+int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     if (a.n_tiles <= 0) return 0;
     const bool dyn = a.p.n_dyn > 0;
-    const size_t smem = (size_t)a.smem_map_words * 4 + (size_t)a.max_k * sizeof(float2) +
-                        (dyn ? (size_t)2 * tile_envs * sizeof(DynEnv) : 0);
+    const size_t smem = (size_t)a.smem_region_bytes + (size_t)a.max_k * sizeof(float2) +
+                        (dyn ? (size_t)2 * cfg.tile_envs * sizeof(DynEnv) : 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t err;
-    if (dyn) {
-        err = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
-        if (err != cudaSuccess) return (int)err;
-        step_kernel<true><<<a.n_tiles, block_threads, smem, s>>>(a);
-    } else {
-        err = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
-        if (err != cudaSuccess) return (int)err;
-        step_kernel<false><<<a.n_tiles, block_threads, smem, s>>>(a);
-    }
+    const void *fn = dyn ? pick_kernel<true>(cfg.max_regs) : pick_kernel<false>(cfg.max_regs);
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cfg.block_threads, smem);
+    if (err != cudaSuccess) return (int)err;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    const int grid = std::min(a.n_tiles, n_sm * per_sm);
+    void *args[] = {const_cast<StepArgs *>(&a)};
+    err = cudaLaunchKernel(fn, dim3(grid), dim3(cfg.block_threads), args, smem, s);
+    if (err != cudaSuccess) return (int)err;
+    return (int)cudaGetLastError();
+}
+
+int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,
+                           void *stream) {
+    const int bs = 256;
+    uniform_actions_kernel<<<(n_envs + bs - 1) / bs, bs, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<float2 *>(out), n_envs, seed, step);
     return (int)cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ EXPORTS = [
     "nav_default_params", "nav_create", "nav_create_ex", "nav_set_stream", "nav_obs_offsets",
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
-    "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_last_error", "nav_free",
+    "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
+    "nav_graph_capture", "nav_graph_launch", "nav_last_error", "nav_free",
 ]
 
 
@@ -83,8 +84,12 @@ def load():
         "nav_get_debug": (I, [P, P, P, P]),
         "nav_set_stats": (I, [P, I]),
         "nav_get_stats": (I, [P, P, P]),
-        "nav_set_launch": (I, [P, I, I, I]),
-        "nav_get_launch": (I, [P, P, P, P]),
+        "nav_set_launch": (I, [P, I, I, I, I, I]),
+        "nav_get_launch": (I, [P, P, P, P, P, P]),
+        "nav_autotune": (I, [P, I, P]),
+        "nav_uniform_actions": (I, [P, U64, C.c_uint32, P]),
+        "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
+        "nav_graph_launch": (I, [P]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }
@@ -261,10 +266,39 @@ class NavSim:
         self._check(load().nav_get_stats(self._h, C.byref(v), C.byref(r)))
         return int(v.value), int(r.value)
 
-    def set_launch(self, tile_envs=0, block_threads=0, smem_map_bytes=0):
-        self._check(load().nav_set_launch(self._h, tile_envs, block_threads, smem_map_bytes))
+    def set_launch(self, tile_envs=0, block_threads=0, smem_map_bytes=0, max_regs=0,
+                   byte_cells=0):
+        self._bind_stream()
+        self._check(load().nav_set_launch(self._h, tile_envs, block_threads, smem_map_bytes,
+                                          max_regs, byte_cells))
 
     def get_launch(self):
-        a, b, c = C.c_int(), C.c_int(), C.c_int()
-        self._check(load().nav_get_launch(self._h, C.byref(a), C.byref(b), C.byref(c)))
-        return a.value, b.value, c.value
+        v = [C.c_int() for _ in range(5)]
+        self._check(load().nav_get_launch(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def autotune(self, steps: int = 5) -> float:
+        """Picks the fastest launch shape for this handle; returns its ms/step."""
+        self._bind_stream()
+        ms = C.c_float()
+        self._check(load().nav_autotune(self._h, steps, C.byref(ms)))
+        return float(ms.value)
+
+    def uniform_actions(self, seed: int, step: int, out=None):
+        out = self._torch.empty(self.n_envs, 2, dtype=self._torch.float32, device=self.device) \
+            if out is None else out
+        self._bind_stream()
+        self._check(load().nav_uniform_actions(self._h, C.c_uint64(seed), C.c_uint32(step),
+                                               _t_ptr(out)))
+        return out
+
+    def graph_capture(self, actions, obs, reward, done, final_obs=None):
+        """Captures actions.shape[0] consecutive steps into a CUDA graph."""
+        self._bind_stream()
+        self._check(load().nav_graph_capture(self._h, int(actions.shape[0]), _t_ptr(actions),
+                                             _t_ptr(obs), _t_ptr(reward), _t_ptr(done),
+                                             _t_ptr(final_obs)))
+
+    def graph_launch(self):
+        self._bind_stream()
+        self._check(load().nav_graph_launch(self._h))

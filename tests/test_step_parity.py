@@ -70,13 +70,16 @@ def _compare_debug(sim, ref, tag):
 
 
 def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=8,
-               check_state_every=1):
+               check_state_every=1, autotune=False):
     flashnav, oracle, torch = mods
     sim = flashnav.NavSim.from_workload(wl)
-    sim.set_debug(True)
     if launch:
         sim.set_launch(*launch)
     ref = oracle.OracleSim.from_workload(wl, threads=threads)
+    if autotune:
+        sim.reset(seed)
+        sim.autotune(steps=3)
+    sim.set_debug(True)
     obs = sim.reset(seed)
     robs = ref.reset(seed)
     _compare_obs(obs.cpu().numpy(), robs, wl.env_beams, what="reset obs")
@@ -117,10 +120,16 @@ def test_reset_and_1000_free_running_steps_small(mods):
 
 
 def test_throughput_workload_steps(mods):
-    """4096 envs over 16 maps of 256x256, 360 beams, r_max 6 m, in the launch
-    shape the benchmark times."""
+    """4096 envs over 16 maps of 256x256, 360 beams, r_max 6 m, with the
+    autotuned launch shape, as the benchmark times it."""
     wl = W.config_throughput()
-    run_parity(mods, wl, 4, seed=5, want_final=False)
+    run_parity(mods, wl, 4, seed=5, want_final=False, autotune=True)
+
+
+@pytest.mark.parametrize("byte_cells", [1, 2])
+def test_throughput_workload_both_staging_modes(mods, byte_cells):
+    wl = W.config_throughput(n_envs=1024, n_maps=4)
+    run_parity(mods, wl, 3, seed=6, launch=(2, 256, 0, 32, byte_cells))
 
 
 def test_visit_counter_matches_oracle(mods):
@@ -141,11 +150,14 @@ def test_visit_counter_matches_oracle(mods):
     assert rays >= 6 * wl.n_envs * 360
 
 
-@pytest.mark.parametrize("launch", [(1, 64, 0), (3, 96, 0), (32, 512, 0), (8, 256, 16),
-                                    (5, 128, 16)])
+# (tile_envs, block_threads, smem_map_bytes, max_regs, byte_cells): smem cap
+# 16 bytes forces the L1/L2 path, byte_cells 2 the packed-bit shared path
+@pytest.mark.parametrize("launch", [(1, 64, 0, 32, 1), (3, 96, 0, 64, 2), (32, 512, 0, 40, 1),
+                                    (8, 256, 16, 40, 1), (5, 128, 16, 32, 2),
+                                    (2, 224, 0, 64, 2)])
 def test_launch_shapes_and_ragged_tiles(mods, launch):
     """Ragged env count, a beam count that is not a multiple of 32, tiles of
-    1..32 envs, 64..512 threads, and the L2 path (bitmap not staged)."""
+    1..32 envs, 64..512 threads, register caps, and all three map stagings."""
     wl = W.config_small(n_envs=37)
     wl.env_beams[:] = 37
     run_parity(mods, wl, 60, seed=7, launch=launch)
@@ -176,8 +188,12 @@ def test_moving_discs(mods):
     run_parity(mods, _mixed(n_dyn=8), 80, seed=12)
 
 
+def test_moving_discs_packed_bits(mods):
+    run_parity(mods, _mixed(n_dyn=8), 40, seed=14, launch=(4, 256, 0, 40, 2))
+
+
 def test_moving_discs_l2_path(mods):
-    run_parity(mods, _mixed(n_dyn=3), 40, seed=13, launch=(4, 128, 16))
+    run_parity(mods, _mixed(n_dyn=3), 40, seed=13, launch=(4, 128, 16, 64, 1))
 
 
 def test_exclusive_reward_and_270_degree_fan(mods):
@@ -268,3 +284,60 @@ def test_sync_reports_clean_status(mods):
     sim = flashnav.NavSim.from_workload(wl)
     sim.reset(1)
     sim.sync(10000)
+
+
+def test_autotune_keeps_state_and_results(mods):
+    """The autotuner times candidate shapes on a copy of the state: the
+    trajectory afterwards still matches the oracle."""
+    flashnav, oracle, torch = mods
+    wl = W.config_throughput(n_envs=256, n_maps=2)
+    sim = flashnav.NavSim.from_workload(wl)
+    ref = oracle.OracleSim.from_workload(wl, threads=8)
+    sim.reset(21)
+    ref.reset(21)
+    assert sim.autotune(steps=2) > 0
+    acts = W.uniform_actions(21, 5, wl.n_envs)
+    for t in range(5):
+        o, r, d = sim.step(torch.from_numpy(acts[t]).cuda())
+        ro, rr, rd = ref.step(acts[t])
+        assert np.array_equal(d.cpu().numpy(), rd)
+        _compare_obs(o.cpu().numpy(), ro, wl.env_beams)
+    _compare_state(sim, ref, "after autotune")
+
+
+def test_graph_replay_matches_eager_steps(mods):
+    flashnav, oracle, torch = mods
+    wl = W.config_small(n_envs=64)
+    a = flashnav.NavSim.from_workload(wl)
+    b = flashnav.NavSim.from_workload(wl)
+    n = 16
+    acts = torch.from_numpy(W.uniform_actions(3, n, wl.n_envs)).cuda().contiguous()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a.reset(3)
+        b.reset(3)
+        obs = b.new_obs()
+        rew = torch.empty(wl.n_envs, device="cuda")
+        done = torch.empty(wl.n_envs, dtype=torch.uint8, device="cuda")
+        b.graph_capture(acts, obs, rew, done)
+        b.graph_launch()
+        for t in range(n):
+            eo, er, ed = a.step(acts[t])
+    torch.cuda.synchronize()
+    assert torch.equal(eo, obs) and torch.equal(er, rew) and torch.equal(ed, done)
+    fa, ia, _ = a.get_state()
+    fb, ib, _ = b.get_state()
+    assert np.array_equal(fa, fb) and np.array_equal(ia, ib)
+
+
+def test_uniform_action_generator_range(mods):
+    flashnav, oracle, torch = mods
+    wl = W.config_small(n_envs=4096)
+    sim = flashnav.NavSim.from_workload(wl)
+    a = sim.uniform_actions(1, 0)
+    torch.cuda.synchronize()
+    a = a.cpu().numpy()
+    assert a.min() >= -1.0 and a.max() < 1.0
+    assert abs(a.mean()) < 0.05
+    b = sim.uniform_actions(1, 1).cpu().numpy()
+    assert not np.array_equal(a, b)
