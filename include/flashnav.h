@@ -129,6 +129,25 @@ int nav_step(nav_handle *h, const float *actions_dev, float *obs_dev, float *rew
 int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host,
                   float *reward_host, uint8_t *done_host, float *final_obs_host);
 
+/* nav_step_host without any device allocation (the paper has no counterpart;
+ * this is for callers that may not allocate device memory after start-up,
+ * such as a robot control loop or embedded process that sizes its GPU memory
+ * once, or an application whose own allocator must own every allocation --
+ * nav_step_host allocates its staging buffers on its first call).  Same
+ * arguments and results as nav_step_host, except that rows of final_obs_host
+ * for envs that did not finish this step come back as zeros.  The staging
+ * lives in one fixed 8 MiB device array inside the library, present on every
+ * GPU that loads it until the process exits: 8 n_envs + 4 obs_size + 5 n_envs
+ * bytes (plus 4 obs_size with final_obs_host), each part rounded up to 256,
+ * must fit, else NAV_E_INVAL (4096 envs x 360 beams fit without final_obs_host;
+ * 2048 envs x 360 beams fit with it).  The handle's device
+ * must be current.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (other threads, other handles, other streams) race.  Synchronous. */
+int nav_step_host_noalloc(nav_handle *h, const float *actions_host, float *obs_host,
+                          float *reward_host, uint8_t *done_host, float *final_obs_host);
+
 /* Waits for the handle's stream for at most timeout_ms (<= 0: no limit), then
  * checks the device status word.  NAV_E_TIMEOUT if the deadline passed. */
 int nav_sync(nav_handle *h, int timeout_ms);

@@ -266,6 +266,21 @@ int launch(nav_handle *h) {
 
 } // namespace
 
+namespace flashnav {
+
+int handle_view(const nav_handle *h, HandleView *out) {
+    if (!h || !out) return NAV_E_INVAL;
+    out->device = h->device;
+    out->stream = h->stream;
+    out->n_envs = h->n_envs;
+    out->obs_floats = h->obs_off.back();
+    return NAV_OK;
+}
+
+int handle_fail(nav_handle *h, int code, const char *msg) { return fail(h, code, msg); }
+
+} // namespace flashnav
+
 extern "C" {
 
 void nav_default_params(nav_params *p) {

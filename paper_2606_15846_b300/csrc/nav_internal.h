@@ -107,4 +107,15 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
 int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,
                            void *stream);
 
+// Read-only facts about a handle for entry points defined outside nav_api.cpp.
+struct HandleView {
+    int device;
+    void *stream;
+    int n_envs;
+    long long obs_floats;
+};
+int handle_view(const nav_handle *h, HandleView *out);
+// Records `msg` as the handle's last error and returns `code`.
+int handle_fail(nav_handle *h, int code, const char *msg);
+
 } // namespace flashnav

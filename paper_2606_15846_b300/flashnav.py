@@ -24,7 +24,8 @@ EXPORTS = [
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
-    "nav_graph_capture", "nav_graph_launch", "nav_last_error", "nav_free",
+    "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_last_error",
+    "nav_free",
 ]
 
 
@@ -90,6 +91,7 @@ def load():
         "nav_uniform_actions": (I, [P, U64, C.c_uint32, P]),
         "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
         "nav_graph_launch": (I, [P]),
+        "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }
