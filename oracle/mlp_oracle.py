@@ -1,0 +1,192 @@
+"""FP64 reference of the learned parts: the policy / critic MLPs (Sec. 2.1:
+MLPs with LeakyReLU), the tanh-squashed Gaussian actor, Adam, and the
+FastDSAC update (Sec. 2.3, FastDSAC paragraph; Table 4).
+
+TEST INFRASTRUCTURE ONLY: used by tests/ and the CPU-baseline leg of the
+benchmark; it never imports the CUDA package.  Plain numpy in binary64; the
+matrix product is the only library primitive.
+
+Readings (the paper states FastDSAC only in prose):
+* hidden activation LeakyReLU with slope 0.01;
+* actor head: mean u (2) and raw log-std r (2); log sigma = LS_MIN +
+  (LS_MAX - LS_MIN) (tanh(r) + 1) / 2 with [LS_MIN, LS_MAX] = [-5, 0]
+  (Table 4 log sigma range); action a = tanh(u + sigma eps);
+* critic head: mean m and raw scale q; sigma_Q = softplus(q) + SIG_FLOOR;
+* target: z ~ N(m', sigma_Q') of the target critic with the smaller mean
+  (clipped double Q), clipped to m' +- 3 sigma_Q'; y = rs r + gamma (1 - term)
+  (z - alpha logpi'), y_mean the same with m' in place of z;
+* critic loss per critic: w Huber_delta(m - y_mean) + NLL(y | sg(m), sigma_Q)
+  with w = clip(sg(sbar^2 / (sigma_Q^2 + 1e-6)), 0.5, 2.0) (Table 4 scale
+  range) and sbar a running mean of the batch-mean sigma_Q (rate tau_b);
+* actor loss: mean(alpha logpi - min_i m_i(s, a~)); temperature: log alpha
+  descends mean(-log alpha (logpi + target_entropy)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SLOPE = 0.01
+LS_MIN, LS_MAX = -5.0, 0.0
+SIG_FLOOR = 0.1
+LOG_2PI = math.log(2.0 * math.pi)
+
+
+# ---------------------------------------------------------------------------
+# MLP: x -> [W1 x + b1 -> leaky] -> [W2 . + b2 -> leaky] -> W3 . + b3
+# weights W_l have shape [out, in] (y = x W^T + b)
+# ---------------------------------------------------------------------------
+def init_mlp(rng, sizes):
+    """Kaiming-uniform style init: U(-1/sqrt(in), 1/sqrt(in)) for W and b."""
+    params = []
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        lim = 1.0 / math.sqrt(fan_in)
+        params.append([rng.uniform(-lim, lim, (fan_out, fan_in)), rng.uniform(-lim, lim, fan_out)])
+    return params
+
+
+def leaky(z):
+    return np.where(z > 0, z, SLOPE * z)
+
+
+def mlp_forward(params, x):
+    """Returns the output and the cache of layer inputs and pre-activations."""
+    cache = []
+    h = x
+    for li, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        cache.append((h, z))
+        h = leaky(z) if li < len(params) - 1 else z
+    return h, cache
+
+
+def mlp_backward(params, cache, dout):
+    """Gradients [dW, db] per layer and the gradient w.r.t. the input."""
+    grads = [None] * len(params)
+    g = dout
+    for li in range(len(params) - 1, -1, -1):
+        W, _ = params[li]
+        h, z = cache[li]
+        if li < len(params) - 1:
+            g = g * np.where(z > 0, 1.0, SLOPE)
+        grads[li] = [g.T @ h, g.sum(axis=0)]
+        g = g @ W
+    return grads, g
+
+
+# ---------------------------------------------------------------------------
+# Adam (Kingma & Ba 2015, Algorithm 1), bias-corrected, no weight decay
+# ---------------------------------------------------------------------------
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.95, eps=1e-8):
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# tanh-squashed Gaussian policy
+# ---------------------------------------------------------------------------
+def actor_head(out, eps):
+    """out [B, 4] = (u0, u1, r0, r1); eps [B, 2] standard normal.
+    Returns action a, log pi(a|s) and the intermediates."""
+    u, r = out[:, :2], out[:, 2:4]
+    ls = LS_MIN + (LS_MAX - LS_MIN) * 0.5 * (np.tanh(r) + 1.0)
+    sig = np.exp(ls)
+    pre = u + sig * eps
+    a = np.tanh(pre)
+    logp = (-0.5 * eps ** 2 - ls - 0.5 * LOG_2PI - np.log(1.0 - a ** 2 + 1e-6)).sum(axis=1)
+    return a, logp, (u, r, ls, sig, pre)
+
+
+def actor_head_grad(out, eps, da, dlogp):
+    """Backward of actor_head: d(out) from dL/da [B,2] and dL/dlogp [B]."""
+    u, r, ls, sig, pre = actor_head(out, eps)[2]
+    a = np.tanh(pre)
+    dpre_a = 1.0 - a ** 2
+    # logp = sum(-eps^2/2 - ls - c - log(1 - tanh(pre)^2 + 1e-6)), eps fixed
+    dlog_dpre = 2.0 * a * (1.0 - a ** 2) / (1.0 - a ** 2 + 1e-6)
+    dpre = da * dpre_a + dlogp[:, None] * dlog_dpre
+    du = dpre
+    dls = dpre * sig * eps - dlogp[:, None]
+    dr = dls * (LS_MAX - LS_MIN) * 0.5 * (1.0 - np.tanh(r) ** 2)
+    return np.concatenate([du, dr], axis=1)
+
+
+def softplus(x):
+    return np.log1p(np.exp(-np.abs(x))) + np.maximum(x, 0.0)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def huber(x, delta):
+    ax = np.abs(x)
+    return np.where(ax <= delta, 0.5 * x * x, delta * (ax - 0.5 * delta))
+
+
+def huber_grad(x, delta):
+    return np.clip(x, -delta, delta)
+
+
+# ---------------------------------------------------------------------------
+# FastDSAC update pieces
+# ---------------------------------------------------------------------------
+def critic_targets(rew, term, tq1, tq2, logp_next, alpha, znoise, gamma, rscale):
+    """tq_i [B, 2] target-critic heads (mean, raw scale); znoise [B] ~ N(0,1).
+    Returns the sampled target y and the mean target y_mean."""
+    m1, s1 = tq1[:, 0], softplus(tq1[:, 1]) + SIG_FLOOR
+    m2, s2 = tq2[:, 0], softplus(tq2[:, 1]) + SIG_FLOOR
+    pick1 = m1 <= m2
+    m = np.where(pick1, m1, m2)
+    s = np.where(pick1, s1, s2)
+    z = m + s * np.clip(znoise, -3.0, 3.0)
+    cont = gamma * (1.0 - term)
+    y = rscale * rew + cont * (z - alpha * logp_next)
+    y_mean = rscale * rew + cont * (m - alpha * logp_next)
+    return y, y_mean
+
+
+def critic_loss(q, y, y_mean, sbar, delta=50.0, m_sg=None):
+    """q [B, 2] (mean, raw scale).  Returns the batch-mean loss and dL/dq.
+    m_sg: the stop-gradient copy of the mean used by the NLL term (defaults
+    to the value of q[:, 0]; pass a fixed copy to differentiate numerically)."""
+    B = q.shape[0]
+    m, qr = q[:, 0], q[:, 1]
+    m_sg = m.copy() if m_sg is None else m_sg
+    s = softplus(qr) + SIG_FLOOR
+    w = np.clip(sbar ** 2 / (s ** 2 + 1e-6), 0.5, 2.0)  # treated as a constant
+    e = m - y_mean
+    loss_mean = w * huber(e, delta)
+    # Gaussian NLL of y under (sg(m), s): log s + (y - m)^2 / (2 s^2)
+    d2 = (y - m_sg) ** 2
+    loss_std = np.log(s) + d2 / (2.0 * s * s)
+    loss = (loss_mean + loss_std).mean()
+    dm = w * huber_grad(e, delta) / B
+    ds = (1.0 / s - d2 / s ** 3) / B
+    dq = np.stack([dm, ds * sigmoid(qr)], axis=1)
+    return loss, dq
+
+
+def actor_loss_grads(logp, q1_mean, q2_mean, alpha):
+    """L = mean(alpha logp - min(q1, q2)); returns L, dL/dlogp, dL/dq1, dL/dq2."""
+    B = logp.shape[0]
+    pick1 = q1_mean <= q2_mean
+    qmin = np.where(pick1, q1_mean, q2_mean)
+    loss = (alpha * logp - qmin).mean()
+    dlogp = np.full(B, alpha / B)
+    dq1 = np.where(pick1, -1.0 / B, 0.0)
+    dq2 = np.where(pick1, 0.0, -1.0 / B)
+    return loss, dlogp, dq1, dq2
+
+
+def alpha_grad(log_alpha, logp, target_entropy):
+    """d/dlog_alpha of mean(-log_alpha (logp + target_entropy))."""
+    return -(logp + target_entropy).mean()
+
+
+def soft_update(target, online, tau):
+    return (1.0 - tau) * target + tau * online

@@ -1,0 +1,138 @@
+"""Pins of the FP64 MLP / FastDSAC oracle (oracle/mlp_oracle.py) against
+facts fixed outside it: central finite differences, Adam's first step in
+closed form (Kingma & Ba, Algorithm 1), normalisation of the squashed
+Gaussian density, Huber's closed form, and the clipped-double-Q choice."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+
+def _fd(f, x, h=1e-6):
+    g = np.zeros_like(x)
+    it = np.nditer(x, flags=["multi_index"])
+    for _ in it:
+        i = it.multi_index
+        old = x[i]
+        x[i] = old + h
+        fp = f()
+        x[i] = old - h
+        fm = f()
+        x[i] = old
+        g[i] = (fp - fm) / (2 * h)
+    return g
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-12)
+
+
+def test_mlp_backward_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    params = M.init_mlp(rng, [7, 6, 5, 3])
+    x = rng.normal(size=(4, 7))
+    R = rng.normal(size=(4, 3))
+    loss = lambda: float((M.mlp_forward(params, x)[0] * R).sum())
+    out, cache = M.mlp_forward(params, x)
+    grads, dx = M.mlp_backward(params, cache, R)
+    for (W, b), (dW, db) in zip(params, grads):
+        assert _rel(dW, _fd(loss, W)) < 1e-6
+        assert _rel(db, _fd(loss, b)) < 1e-6
+    assert _rel(dx, _fd(loss, x)) < 1e-6
+
+
+def test_leaky_relu_slope():
+    z = np.array([-2.0, 0.0, 3.0])
+    assert np.allclose(M.leaky(z), [-0.02, 0.0, 3.0])
+
+
+def test_actor_head_gradient_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    out = rng.normal(size=(5, 4))
+    eps = rng.normal(size=(5, 2))
+    ca = rng.normal(size=(5, 2))
+    cl = rng.normal(size=5)
+    loss = lambda: float((M.actor_head(out, eps)[0] * ca).sum() + (M.actor_head(out, eps)[1] * cl).sum())
+    g = M.actor_head_grad(out, eps, ca, cl)
+    assert _rel(g, _fd(loss, out)) < 1e-6
+
+
+def test_squashed_gaussian_density_integrates_to_one():
+    quad = pytest.importorskip("scipy.integrate").quad
+    for u, r in [(0.3, -0.5), (-1.2, 0.4), (0.0, 2.0)]:
+        ls = M.LS_MIN + (M.LS_MAX - M.LS_MIN) * 0.5 * (math.tanh(r) + 1)
+        sig = math.exp(ls)
+
+        def dens(a):
+            pre = math.atanh(a)
+            eps = (pre - u) / sig
+            out = np.array([[u, u, r, r]])
+            _, logp, _ = M.actor_head(out, np.array([[eps, eps]]))
+            return math.exp(float(logp[0]) / 2.0)  # one of two identical dims
+        val = quad(dens, -1 + 1e-12, 1 - 1e-12, limit=400, points=[math.tanh(u)])[0]
+        assert abs(val - 1.0) < 2e-3, (u, r, val)
+
+
+def test_log_sigma_range():
+    out = np.array([[0, 0, -50.0, 50.0]])
+    _, _, (u, r, ls, sig, pre) = M.actor_head(out, np.zeros((1, 2)))
+    assert ls[0, 0] == pytest.approx(M.LS_MIN) and ls[0, 1] == pytest.approx(M.LS_MAX)
+
+
+def test_adam_first_step_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    lr = 3e-4
+    p1, m, v = M.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr, 0.9, 0.95, 1e-8)
+    # bias-corrected moments equal g and g^2 after one step
+    assert np.allclose(p1, p - lr * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.05 * g * g)
+
+
+def test_huber_closed_form():
+    d = 50.0
+    assert M.huber(np.array([3.0]), d)[0] == 4.5
+    assert M.huber(np.array([-60.0]), d)[0] == d * (60.0 - 25.0)
+    assert M.huber(np.array([d]), d)[0] == 0.5 * d * d  # continuous at delta
+    assert np.array_equal(M.huber_grad(np.array([-70.0, 2.0, 80.0]), d), [-50.0, 2.0, 50.0])
+
+
+def test_critic_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    q = rng.normal(size=(6, 2))
+    y = rng.normal(size=6)
+    ym = rng.normal(size=6)
+    for sbar in (1e-3, 1e3):  # the weight sits on a clip bound: constant in q
+        m_sg = q[:, 0].copy()  # stop-gradient copy held fixed
+        loss = lambda: M.critic_loss(q, y, ym, sbar, m_sg=m_sg)[0]
+        _, dq = M.critic_loss(q, y, ym, sbar)
+        assert _rel(dq, _fd(loss, q)) < 1e-6
+
+
+def test_targets_use_the_smaller_mean_and_clip_the_sample():
+    rew = np.array([1.0, 1.0])
+    term = np.array([0.0, 1.0])
+    tq1 = np.array([[2.0, 0.0], [2.0, 0.0]])
+    tq2 = np.array([[3.0, 5.0], [1.0, 5.0]])
+    y, ym = M.critic_targets(rew, term, tq1, tq2, np.zeros(2), 0.0, np.array([10.0, 0.0]),
+                             0.99, 0.4)
+    s1 = M.softplus(0.0) + M.SIG_FLOOR
+    assert ym[0] == pytest.approx(0.4 + 0.99 * 2.0)
+    assert y[0] == pytest.approx(0.4 + 0.99 * (2.0 + 3.0 * s1))  # clipped at 3 sigma
+    assert ym[1] == pytest.approx(0.4) and y[1] == pytest.approx(0.4)  # terminal
+
+
+def test_actor_loss_gradients():
+    logp = np.array([0.5, -1.0])
+    q1 = np.array([1.0, 3.0])
+    q2 = np.array([2.0, 0.0])
+    loss, dl, d1, d2 = M.actor_loss_grads(logp, q1, q2, 0.2)
+    assert loss == pytest.approx(((0.2 * 0.5 - 1.0) + (0.2 * -1.0 - 0.0)) / 2)
+    assert np.allclose(dl, [0.1, 0.1]) and np.allclose(d1, [-0.5, 0]) and np.allclose(d2, [0, -0.5])
+
+
+def test_softplus_is_stable():
+    assert M.softplus(np.array([800.0]))[0] == 800.0
+    assert M.softplus(np.array([0.0]))[0] == pytest.approx(math.log(2.0))
