@@ -215,6 +215,21 @@ int nav_graph_capture(nav_handle *h, int n_steps, const float *actions_dev, floa
                       float *reward_dev, uint8_t *done_dev, float *final_obs_dev);
 int nav_graph_launch(nav_handle *h);
 
+/* Tensor-core GEMM of the policy and critic MLPs (Sec. 2.1 LeakyReLU MLPs;
+ * the learner of Sec. 2.3): C = act(A B^T + bias) on the stream `stream`
+ * (cudaStream_t, NULL = default).
+ *   a_dev [m][lda] BF16, b_dev [n][ldb] BF16 (both K-major: k contiguous),
+ *         16-byte aligned, lda and ldb multiples of 8 and >= k
+ *   bias_dev [n] float or NULL; act 0 = none, 1 = LeakyReLU (slope 0.01)
+ *   outputs (each optional): c32_dev [m][ldc32] float, c16_dev [m][ldc16]
+ *         BF16, c16t_dev [n][ldct] BF16 (the transpose, for the next GEMM's
+ *         K-major operand)
+ *   status_dev int or NULL: bit 0 set if a tensor-core completion wait timed out
+ * FP32 accumulation; tcgen05 MMA with TMEM accumulators, 128 x <=256 tiles. */
+int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m, int n, int k,
+                  const float *bias_dev, int act, float *c32_dev, int ldc32, void *c16_dev,
+                  int ldc16, void *c16t_dev, int ldct, int *status_dev, void *stream);
+
 const char *nav_last_error(const nav_handle *h);
 void nav_free(nav_handle *h);
 

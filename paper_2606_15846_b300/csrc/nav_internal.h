@@ -107,6 +107,12 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
 int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,
                            void *stream);
 
+// Tensor-core GEMM C = A B^T (BF16 in, FP32 accumulate) with bias, optional
+// LeakyReLU, and FP32 / BF16 / transposed-BF16 outputs (each may be null).
+int launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                     const float *bias, int act, float *C32, int ldc32, void *C16, int ldc16,
+                     void *C16T, int ldct, int *status, void *stream);
+
 // Read-only facts about a handle for entry points defined outside nav_api.cpp.
 struct HandleView {
     int device;

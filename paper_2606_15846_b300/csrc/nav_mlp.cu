@@ -1,0 +1,219 @@
+// Tensor-core GEMM for the policy and critic MLPs (Sec. 2.1 MLPs; the
+// FastDSAC learner of Sec. 2.3): C = A B^T with A [M][K] and B [N][K] BF16,
+// both K-major, FP32 accumulation in tensor memory (tcgen05, sm_100-family).
+//
+// One CTA (4 warps) owns a 128 x BN output tile (BN <= 256, a multiple of 16).
+// For each 64-wide K chunk the CTA copies A and B rows into shared memory in
+// the 128-byte-swizzled K-major layout (8-row atoms of 1024 bytes, 16-byte
+// piece c of row r stored at piece c ^ (r mod 8)), zero-filling rows past M/N
+// and columns past K; one thread issues four tcgen05.mma (K = 16 each) into
+// the TMEM accumulator and commits them to an mbarrier.  The epilogue reads
+// the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e.
+// rows), adds the bias, applies LeakyReLU if asked, and stores FP32 and/or
+// BF16 and/or the BF16 transpose.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "nav_internal.h"
+
+namespace flashnav {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kChunkK = 64; // BF16 elements per 128-byte swizzle row
+constexpr int kThreads = 128;
+constexpr float kLeakySlope = 0.01f;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), start address in 16-byte units.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)1 << 16;                 // leading byte offset (unused here)
+    d |= (unsigned long long)(1024u >> 4) << 32;      // stride byte offset
+    d |= (unsigned long long)1 << 46;                 // descriptor version
+    d |= (unsigned long long)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
+__device__ __forceinline__ unsigned instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
+           ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Copies rows [r0, r0 + rows) x K-chunk [k0, k0 + 64) of a K-major matrix
+// into a swizzled tile; out-of-range rows and columns are zero.
+__device__ __forceinline__ void load_tile(unsigned dst, const __nv_bfloat16 *src, int ld,
+                                          int r0, int rows, int nrows_total, int k0, int K) {
+    for (int p = threadIdx.x; p < rows * 8; p += kThreads) {
+        const int r = p >> 3, c = p & 7;
+        const int gr = r0 + r, k = k0 + c * 8;
+        int bytes = 0;
+        const __nv_bfloat16 *g = src;
+        if (gr < nrows_total && k < K) {
+            bytes = K - k >= 8 ? 16 : 2 * (K - k);
+            g = src + (size_t)gr * ld + k;
+        }
+        const unsigned d = dst + (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(bytes)
+                     : "memory");
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
+                 int ldb, int M, int N, int K, int BN, const float *__restrict__ bias, int act,
+                 float *C32, int ldc32, __nv_bfloat16 *C16, int ldc16, __nv_bfloat16 *C16T,
+                 int ldct, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ unsigned tmem_base;
+    // 1024-byte alignment of the swizzled tiles
+    const unsigned raw = smem_addr(smem_raw);
+    const unsigned sA = (raw + 1023u) & ~1023u;
+    const unsigned sB = sA + kTileM * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * BN;
+    int ncols = 32;
+    while (ncols < BN) ncols <<= 1;
+    const unsigned b = smem_addr(&bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    const unsigned idesc = instr_desc(kTileM, BN);
+    unsigned parity = 0;
+    bool ok = true;
+    const int n_chunks = (K + kChunkK - 1) / kChunkK;
+    for (int kc = 0; kc < n_chunks; ++kc) {
+        load_tile(sA, A, lda, m0, kTileM, M, kc * kChunkK, K);
+        load_tile(sB, B, ldb, n0, BN, N, kc * kChunkK, K);
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k16 = 0; k16 < kChunkK / 16; ++k16) {
+                const unsigned long long da = smem_desc(sA + 32u * k16);
+                const unsigned long long db = smem_desc(sB + 32u * k16);
+                const unsigned accum = (kc > 0 || k16 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b)
+                : "memory");
+        }
+        // the MMAs must finish reading the tiles before they are overwritten
+        ok = mbar_wait(b, parity) && ok;
+        parity ^= 1u;
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok && status && threadIdx.x == 0) atomicOr(status, 1);
+    // epilogue: warp w holds rows m0 + 32 w + lane
+    const int row = m0 + warp * 32 + lane;
+    for (int cb = 0; cb < BN; cb += 8) {
+        unsigned r[8];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = n0 + cb + j;
+            if (col >= N) break;
+            float v = __uint_as_float(r[j]);
+            if (bias) v += bias[col];
+            if (act == 1) v = v > 0.0f ? v : kLeakySlope * v;
+            if (C32) C32[(size_t)row * ldc32 + col] = v;
+            if (C16) C16[(size_t)row * ldc16 + col] = __float2bfloat16_rn(v);
+            if (C16T) C16T[(size_t)col * ldct + row] = __float2bfloat16_rn(v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                     : "memory");
+}
+
+} // namespace
+
+int launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                     const float *bias, int act, float *C32, int ldc32, void *C16, int ldc16,
+                     void *C16T, int ldct, int *status, void *stream) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    const int BN = N >= 256 ? 256 : (N + 15) / 16 * 16;
+    const size_t smem = 1024 + (size_t)kTileM * 128 + (size_t)BN * 128;
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    dim3 grid((M + kTileM - 1) / kTileM, (N + BN - 1) / BN);
+    gemm_bf16_tc<<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(A), lda, static_cast<const __nv_bfloat16 *>(B), ldb, M,
+        N, K, BN, bias, act, C32, ldc32, static_cast<__nv_bfloat16 *>(C16), ldc16,
+        static_cast<__nv_bfloat16 *>(C16T), ldct, status);
+    return (int)cudaGetLastError();
+}
+
+} // namespace flashnav
+
+// C ABI: see include/flashnav.h (nav_gemm_bf16).
+extern "C" int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m, int n,
+                             int k, const float *bias_dev, int act, float *c32_dev, int ldc32,
+                             void *c16_dev, int ldc16, void *c16t_dev, int ldct, int *status_dev,
+                             void *stream) {
+    if (!a_dev || !b_dev || m < 0 || n < 0 || k < 0 || (act != 0 && act != 1)) return NAV_E_INVAL;
+    if ((lda % 8) || (ldb % 8) || lda < k || ldb < k) return NAV_E_INVAL;
+    if ((reinterpret_cast<uintptr_t>(a_dev) & 15u) || (reinterpret_cast<uintptr_t>(b_dev) & 15u))
+        return NAV_E_INVAL;
+    if ((c32_dev && ldc32 < n) || (c16_dev && ldc16 < n) || (c16t_dev && ldct < m))
+        return NAV_E_INVAL;
+    const int rc = flashnav::launch_gemm_bf16(a_dev, lda, b_dev, ldb, m, n, k, bias_dev, act,
+                                              c32_dev, ldc32, c16_dev, ldc16, c16t_dev, ldct,
+                                              status_dev, stream);
+    return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}

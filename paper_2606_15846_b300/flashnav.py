@@ -24,8 +24,8 @@ EXPORTS = [
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
-    "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_last_error",
-    "nav_free",
+    "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
+    "nav_last_error", "nav_free",
 ]
 
 
@@ -92,6 +92,7 @@ def load():
         "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
         "nav_graph_launch": (I, [P]),
         "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
+        "nav_gemm_bf16": (I, [P, I, P, I, I, I, I, P, I, P, I, P, I, P, I, P, P]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }
