@@ -230,6 +230,43 @@ int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m,
                   const float *bias_dev, int act, float *c32_dev, int ldc32, void *c16_dev,
                   int ldc16, void *c16t_dev, int ldct, int *status_dev, void *stream);
 
+/* Policy network (Sec. 2.1 policy MLP; the FastDSAC actor of Sec. 2.3): a
+ * tanh-squashed Gaussian actor obs_dim -> hidden -> hidden -> 4 (mean 2, raw
+ * log-std 2) with LeakyReLU (slope 0.01); log sigma = -5 + 5 (tanh(r) + 1)/2,
+ * action a = tanh(mean + sigma eps).  FP32 master weights initialised
+ * U(-1/sqrt(in), 1/sqrt(in)) from a counter hash of `seed`, BF16 copies for
+ * the tensor cores.  max_batch bounds the rows of one nav_policy_act call.
+ * Weights in host order [W1 (hidden x obs_dim, row-major), b1, W2, b2, W3, b3]. */
+typedef struct nav_policy nav_policy;
+int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out);
+void nav_policy_free(nav_policy *p);
+int64_t nav_policy_num_params(const nav_policy *p);
+int nav_policy_get_weights(nav_policy *p, float *host);       /* synchronous */
+int nav_policy_set_weights(nav_policy *p, const float *host); /* synchronous */
+
+/* Actions for n observation rows (obs_dev row r at r * obs_stride floats):
+ * mode 0 deterministic a = tanh(mean), mode 1 sampled with eps from the
+ * counter hash of (seed, row, step).  actions_dev [n][2] float; logp_dev [n]
+ * and out_dev [n][4] (the network's raw outputs) may be NULL.  BF16 tensor
+ * cores (tcgen05) with FP32 accumulation; asynchronous on `stream`.
+ * nav_policy_act_fp32 is the same in plain FP32 on CUDA cores. */
+int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n, int mode,
+                   uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
+                   float *out_dev, void *stream);
+int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n, int mode,
+                        uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
+                        float *out_dev, void *stream);
+
+/* Rollout with the policy in the loop (Sec. 2.3 collector side): n_steps of
+ * [policy actions from obs_dev -> nav_step], all on the handle's stream (so a
+ * CUDA graph can capture it).  obs_dev must hold the current observation
+ * (from nav_reset or the previous step); every env must use the same beam
+ * count.  actions_dev [n_envs][2], reward_dev, done_dev as for nav_step hold
+ * the last step's values.  fp32_path 1 uses nav_policy_act_fp32. */
+int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t seed,
+                uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
+                uint8_t *done_dev, int fp32_path);
+
 const char *nav_last_error(const nav_handle *h);
 void nav_free(nav_handle *h);
 

@@ -274,6 +274,9 @@ int handle_view(const nav_handle *h, HandleView *out) {
     out->stream = h->stream;
     out->n_envs = h->n_envs;
     out->obs_floats = h->obs_off.back();
+    out->uniform_k = h->env_k.empty() ? -1 : h->env_k[0];
+    for (int k : h->env_k)
+        if (k != out->uniform_k) out->uniform_k = -1;
     return NAV_OK;
 }
 

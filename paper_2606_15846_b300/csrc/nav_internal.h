@@ -119,6 +119,7 @@ struct HandleView {
     void *stream;
     int n_envs;
     long long obs_floats;
+    int uniform_k; // the beam count if every env has the same one, else -1
 };
 int handle_view(const nav_handle *h, HandleView *out);
 // Records `msg` as the handle's last error and returns `code`.

@@ -1,0 +1,374 @@
+// Policy network and its in-loop inference (Sec. 2.1 policy MLP; the FastDSAC
+// actor of Sec. 2.3, a tanh-squashed Gaussian).  The actor is
+// obs -> 256 -> 256 -> (mean 2, raw log-std 2) with LeakyReLU (slope 0.01);
+// weights are kept in FP32 (master) with BF16 copies for the tensor cores:
+// W [out][ld_in] (forward, K-major) and W^T [in][ld_out] (backward data).
+//
+// Inference: observations (FP32 rows) are converted to BF16 rows padded to a
+// multiple of 8, run through three tcgen05 GEMMs (bias and LeakyReLU fused in
+// the epilogues) and the squashed-Gaussian head:
+//   log sigma = -5 + 5 (tanh(r) + 1) / 2,  a = tanh(u + sigma eps)
+// with eps standard normal from the counter hash keyed by (seed, row, step)
+// (Box-Muller), or a = tanh(u) when deterministic.  A plain FP32 SIMT path
+// (one thread per output element, no tensor cores) is kept as the unfused
+// baseline.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nav_internal.h"
+#include "nav_policy.h"
+
+namespace flashnav {
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void obs_to_bf16(const float *__restrict__ obs, int n, int dim, long long stride,
+                            __nv_bfloat16 *out, int ld) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * ld) return;
+    const int r = (int)(i / ld), c = (int)(i - (long long)r * ld);
+    out[i] = __float2bfloat16_rn(c < dim ? obs[(long long)r * stride + c] : 0.0f);
+}
+
+// a = tanh(u + sigma eps) (or tanh(u)), logp per row.
+__global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
+                               unsigned long long seed, unsigned step, float *act, float *logp,
+                               float *eps_out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float *o = out4 + (size_t)r * 4;
+    float lp = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        const float u = o[d];
+        const float ls = kLogStdMin + (kLogStdMax - kLogStdMin) * 0.5f * (tanhf(o[2 + d]) + 1.0f);
+        float e = 0.0f;
+        if (mode == 1) {
+            const unsigned long long h = mix64(seed ^ ((unsigned long long)r * 0xD1B54A32D192ED03ull) ^
+                                               ((unsigned long long)step << 32) ^ (unsigned)d);
+            const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+            const float u2 = (float)((h >> 8) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+            e = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        }
+        const float a = tanhf(u + expf(ls) * e);
+        lp += -0.5f * e * e - ls - 0.91893853320467274f - logf(1.0f - a * a + 1e-6f);
+        act[(size_t)r * 2 + d] = a;
+        if (eps_out) eps_out[(size_t)r * 2 + d] = e;
+    }
+    if (logp) logp[r] = lp;
+}
+
+// Plain FP32 layer: y[r][o] = act(sum_k x[r][k] W[o][k] + b[o]); one thread
+// per output element (the unfused baseline; no tensor cores).
+__global__ void dense_fp32(const float *__restrict__ x, long long ldx, int n, int in,
+                           const float *__restrict__ W, const float *__restrict__ b, int out,
+                           int leaky, float *y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * out) return;
+    const int r = (int)(i / out), o = (int)(i - (long long)r * out);
+    const float *xr = x + r * ldx;
+    const float *w = W + (size_t)o * in;
+    float s = b[o];
+    for (int k = 0; k < in; ++k) s = fmaf(xr[k], w[k], s);
+    if (leaky) s = s > 0.0f ? s : 0.01f * s;
+    y[i] = s;
+}
+
+// FP32 master -> BF16 W [out][ld_in] and W^T [in][ld_out] (pads zero)
+__global__ void refresh_bf16(const float *__restrict__ W, int out, int in, __nv_bfloat16 *W16,
+                             int ld_in, __nv_bfloat16 *WT16, int ld_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out * in) return;
+    const int o = i / in, k = i - o * in;
+    const __nv_bfloat16 v = __float2bfloat16_rn(W[i]);
+    W16[(size_t)o * ld_in + k] = v;
+    WT16[(size_t)k * ld_out + o] = v;
+}
+
+} // namespace
+
+int Mlp::init(const std::vector<int> &sizes, unsigned long long seed, std::string &err) {
+    n_layers = (int)sizes.size() - 1;
+    if (n_layers < 1 || n_layers > kMaxLayers) {
+        err = "bad layer count";
+        return NAV_E_INVAL;
+    }
+    // U(-1/sqrt(in), 1/sqrt(in)) for weights and biases, from the counter hash
+    std::vector<float> host;
+    for (int l = 0; l < n_layers; ++l) {
+        Layer &L = layer[l];
+        L.in = sizes[l];
+        L.out = sizes[l + 1];
+        L.ld_in = (L.in + 7) / 8 * 8;
+        L.ld_out = (L.out + 7) / 8 * 8;
+        const size_t nw = (size_t)L.in * L.out;
+        const float lim = 1.0f / std::sqrt((float)L.in);
+        host.resize(nw + L.out);
+        for (size_t i = 0; i < host.size(); ++i) {
+            unsigned long long z = seed ^ ((unsigned long long)(l + 1) << 56) ^ (i * 0x9E3779B97F4A7C15ull);
+            z += 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            host[i] = lim * (2.0f * ((float)(z >> 40) * (1.0f / 16777216.0f)) - 1.0f);
+        }
+        cudaError_t e = cudaSuccess;
+        auto A = [&](void **p, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+            if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+        };
+        A((void **)&L.W, nw * 4);
+        A((void **)&L.b, L.out * 4);
+        A((void **)&L.W16, (size_t)L.out * L.ld_in * 2);
+        A((void **)&L.WT16, (size_t)L.in * L.ld_out * 2);
+        A((void **)&L.mW, nw * 4);
+        A((void **)&L.vW, nw * 4);
+        A((void **)&L.mb, L.out * 4);
+        A((void **)&L.vb, L.out * 4);
+        A((void **)&L.gW, nw * 4);
+        A((void **)&L.gb, L.out * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(L.W, host.data(), nw * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(L.b, host.data() + nw, L.out * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            err = cudaGetErrorString(e);
+            return NAV_E_CUDA;
+        }
+    }
+    return refresh(nullptr) == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+void Mlp::release() {
+    for (int l = 0; l < n_layers; ++l) {
+        Layer &L = layer[l];
+        void *ps[] = {L.W, L.b, L.W16, L.WT16, L.mW, L.vW, L.mb, L.vb, L.gW, L.gb};
+        for (void *p : ps)
+            if (p) cudaFree(p);
+        L = Layer{};
+    }
+    n_layers = 0;
+}
+
+int Mlp::refresh(void *stream) {
+    for (int l = 0; l < n_layers; ++l) {
+        Layer &L = layer[l];
+        const int n = L.in * L.out;
+        refresh_bf16<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            L.W, L.out, L.in, static_cast<__nv_bfloat16 *>(L.W16), L.ld_in,
+            static_cast<__nv_bfloat16 *>(L.WT16), L.ld_out);
+    }
+    return (int)cudaGetLastError();
+}
+
+long long Mlp::num_params() const {
+    long long n = 0;
+    for (int l = 0; l < n_layers; ++l) n += (long long)layer[l].in * layer[l].out + layer[l].out;
+    return n;
+}
+
+int Mlp::copy_params(float *host, bool to_host) {
+    long long off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        Layer &L = layer[l];
+        const size_t nw = (size_t)L.in * L.out;
+        cudaError_t e;
+        if (to_host) {
+            e = cudaMemcpy(host + off, L.W, nw * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(host + off + nw, L.b, L.out * 4, cudaMemcpyDeviceToHost);
+        } else {
+            e = cudaMemcpy(L.W, host + off, nw * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(L.b, host + off + nw, L.out * 4, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return (int)e;
+        off += (long long)nw + L.out;
+    }
+    return to_host ? 0 : refresh(nullptr);
+}
+
+// Forward through the tensor cores: x16 [n][layer0.ld_in] BF16 -> out32 [n][out]
+// FP32; hidden activations h16[l] [n][256] and (if ht16) their transposes.
+int Mlp::forward_tc(const void *x16, int n, void *const *h16, void *const *ht16, float *out32,
+                    int *status, void *stream) const {
+    const void *in = x16;
+    int ld = layer[0].ld_in;
+    for (int l = 0; l < n_layers; ++l) {
+        const Layer &L = layer[l];
+        const bool last = l == n_layers - 1;
+        const int rc = launch_gemm_bf16(in, ld, L.W16, L.ld_in, n, L.out, L.in, L.b, last ? 0 : 1,
+                                        last ? out32 : nullptr, L.out, last ? nullptr : h16[l],
+                                        L.out, (!last && ht16) ? ht16[l] : nullptr, n, status,
+                                        stream);
+        if (rc != 0) return rc;
+        in = h16[l];
+        ld = L.out;
+    }
+    return 0;
+}
+
+int Mlp::forward_fp32(const float *x, long long ldx, int n, float *const *h32, float *out32,
+                      void *stream) const {
+    const float *in = x;
+    long long ld = ldx;
+    for (int l = 0; l < n_layers; ++l) {
+        const Layer &L = layer[l];
+        const bool last = l == n_layers - 1;
+        float *y = last ? out32 : h32[l];
+        const long long tot = (long long)n * L.out;
+        dense_fp32<<<(unsigned)((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            in, ld, n, L.in, L.W, L.b, L.out, last ? 0 : 1, y);
+        in = y;
+        ld = L.out;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, void *out, int ld,
+                       void *stream) {
+    const long long tot = (long long)n * ld;
+    obs_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        obs, n, dim, stride, static_cast<__nv_bfloat16 *>(out), ld);
+    return (int)cudaGetLastError();
+}
+
+int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
+                      float *act, float *logp, float *eps, void *stream) {
+    actor_head_fwd<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        out4, n, mode, seed, step, act, logp, eps);
+    return (int)cudaGetLastError();
+}
+
+} // namespace flashnav
+
+using namespace flashnav;
+
+struct nav_policy {
+    Mlp actor;
+    int obs_dim = 0, max_batch = 0;
+    std::string err;
+    // inference scratch, sized for max_batch rows at create
+    void *x16 = nullptr, *h16[2] = {nullptr, nullptr};
+    float *out32 = nullptr, *h32[2] = {nullptr, nullptr};
+    int *status = nullptr;
+};
+
+extern "C" {
+
+int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out) {
+    if (!out || obs_dim <= 0 || hidden <= 0 || hidden % 16 || max_batch <= 0) return NAV_E_INVAL;
+    *out = nullptr;
+    nav_policy *p = new (std::nothrow) nav_policy();
+    if (!p) return NAV_E_NOMEM;
+    p->obs_dim = obs_dim;
+    p->max_batch = max_batch;
+    int rc = p->actor.init({obs_dim, hidden, hidden, 4}, seed, p->err);
+    cudaError_t e = cudaSuccess;
+    const int ld0 = (obs_dim + 7) / 8 * 8;
+    if (rc == NAV_OK) {
+        e = cudaMalloc(&p->x16, (size_t)max_batch * ld0 * 2);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&p->h16[i], (size_t)max_batch * hidden * 2);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&p->h32[i], (size_t)max_batch * hidden * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&p->out32, (size_t)max_batch * 4 * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&p->status, 4);
+        if (e == cudaSuccess) e = cudaMemset(p->status, 0, 4);
+        if (e != cudaSuccess) rc = NAV_E_CUDA;
+    }
+    if (rc != NAV_OK) {
+        nav_policy_free(p);
+        return rc;
+    }
+    *out = p;
+    return NAV_OK;
+}
+
+void nav_policy_free(nav_policy *p) {
+    if (!p) return;
+    p->actor.release();
+    void *ps[] = {p->x16, p->h16[0], p->h16[1], p->h32[0], p->h32[1], p->out32, p->status};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+int64_t nav_policy_num_params(const nav_policy *p) { return p ? p->actor.num_params() : NAV_E_INVAL; }
+
+int nav_policy_get_weights(nav_policy *p, float *host) {
+    if (!p || !host) return NAV_E_INVAL;
+    return p->actor.copy_params(host, true) == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_policy_set_weights(nav_policy *p, const float *host) {
+    if (!p || !host) return NAV_E_INVAL;
+    int rc = p->actor.copy_params(const_cast<float *>(host), false);
+    if (rc == 0) rc = (int)cudaDeviceSynchronize();
+    return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n, int mode,
+                   uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
+                   float *out_dev, void *stream) {
+    if (!p || !obs_dev || !actions_dev || n <= 0 || n > p->max_batch || obs_stride < p->obs_dim ||
+        (mode != 0 && mode != 1))
+        return NAV_E_INVAL;
+    const int ld0 = p->actor.layer[0].ld_in;
+    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->x16, ld0, stream);
+    if (rc == 0) rc = p->actor.forward_tc(p->x16, n, p->h16, nullptr, p->out32, p->status, stream);
+    if (rc == 0) rc = launch_actor_head(p->out32, n, mode, seed, step, actions_dev, logp_dev, nullptr, stream);
+    if (rc == 0 && out_dev)
+        rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+    return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n, int mode,
+                        uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
+                        float *out_dev, void *stream) {
+    if (!p || !obs_dev || !actions_dev || n <= 0 || n > p->max_batch || obs_stride < p->obs_dim ||
+        (mode != 0 && mode != 1))
+        return NAV_E_INVAL;
+    int rc = p->actor.forward_fp32(obs_dev, obs_stride, n, p->h32, p->out32, stream);
+    if (rc == 0) rc = launch_actor_head(p->out32, n, mode, seed, step, actions_dev, logp_dev, nullptr, stream);
+    if (rc == 0 && out_dev)
+        rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+    return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t seed,
+                uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
+                uint8_t *done_dev, int fp32_path) {
+    HandleView hv;
+    if (!h || !p || handle_view(h, &hv) != NAV_OK) return NAV_E_INVAL;
+    if (!obs_dev || !actions_dev || !reward_dev || !done_dev || n_steps <= 0)
+        return handle_fail(h, NAV_E_INVAL, "nav_rollout: bad argument");
+    if (hv.uniform_k < 0 || hv.uniform_k + 4 != p->obs_dim || hv.n_envs > p->max_batch)
+        return handle_fail(h, NAV_E_INVAL,
+                           "nav_rollout: policy obs_dim / max_batch do not match the handle");
+    for (int t = 0; t < n_steps; ++t) {
+        int rc = fp32_path
+                     ? nav_policy_act_fp32(p, obs_dev, p->obs_dim, hv.n_envs, mode, seed,
+                                           step0 + (uint32_t)t, actions_dev, nullptr, nullptr,
+                                           hv.stream)
+                     : nav_policy_act(p, obs_dev, p->obs_dim, hv.n_envs, mode, seed,
+                                      step0 + (uint32_t)t, actions_dev, nullptr, nullptr,
+                                      hv.stream);
+        if (rc != NAV_OK) return handle_fail(h, rc, "nav_rollout: policy launch failed");
+        rc = nav_step(h, actions_dev, obs_dev, reward_dev, done_dev, nullptr);
+        if (rc != NAV_OK) return rc;
+    }
+    return NAV_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,43 @@
+// Private declarations of the MLP pieces shared by nav_policy.cu and
+// nav_learn.cu.  Not part of the public ABI.
+#pragma once
+#include <string>
+#include <vector>
+
+namespace flashnav {
+
+constexpr float kLogStdMin = -5.0f; // actor log-std range (Table 4)
+constexpr float kLogStdMax = 0.0f;
+constexpr int kMaxLayers = 3;
+
+// One dense layer: FP32 master weights W [out][in] and bias, BF16 copies for
+// the tensor cores (W16 [out][ld_in], WT16 [in][ld_out]), Adam moments and
+// gradient buffers.
+struct Layer {
+    int in = 0, out = 0, ld_in = 0, ld_out = 0;
+    float *W = nullptr, *b = nullptr;
+    void *W16 = nullptr, *WT16 = nullptr;
+    float *mW = nullptr, *vW = nullptr, *mb = nullptr, *vb = nullptr;
+    float *gW = nullptr, *gb = nullptr;
+};
+
+struct Mlp {
+    Layer layer[kMaxLayers];
+    int n_layers = 0;
+    int init(const std::vector<int> &sizes, unsigned long long seed, std::string &err);
+    void release();
+    int refresh(void *stream); // FP32 master -> BF16 copies
+    long long num_params() const;
+    int copy_params(float *host, bool to_host); // [W0, b0, W1, b1, ...]
+    int forward_tc(const void *x16, int n, void *const *h16, void *const *ht16, float *out32,
+                   int *status, void *stream) const;
+    int forward_fp32(const float *x, long long ldx, int n, float *const *h32, float *out32,
+                     void *stream) const;
+};
+
+int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, void *out, int ld,
+                       void *stream);
+int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
+                      float *act, float *logp, float *eps, void *stream);
+
+} // namespace flashnav

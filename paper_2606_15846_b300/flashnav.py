@@ -25,6 +25,8 @@ EXPORTS = [
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
+    "nav_policy_create", "nav_policy_free", "nav_policy_num_params", "nav_policy_get_weights",
+    "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_rollout",
     "nav_last_error", "nav_free",
 ]
 
@@ -93,6 +95,14 @@ def load():
         "nav_graph_launch": (I, [P]),
         "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
         "nav_gemm_bf16": (I, [P, I, P, I, I, I, I, P, I, P, I, P, I, P, I, P, P]),
+        "nav_policy_create": (I, [I, I, I, U64, P]),
+        "nav_policy_free": (None, [P]),
+        "nav_policy_num_params": (C.c_int64, [P]),
+        "nav_policy_get_weights": (I, [P, P]),
+        "nav_policy_set_weights": (I, [P, P]),
+        "nav_policy_act": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
+        "nav_policy_act_fp32": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
+        "nav_rollout": (I, [P, P, I, I, U64, C.c_uint32, P, P, P, P, I]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }
