@@ -267,6 +267,71 @@ int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t se
                 uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
                 uint8_t *done_dev, int fp32_path);
 
+/* FastDSAC learner (Sec. 2.3, FastDSAC paragraph; hyperparameters of Table 4,
+ * workload overrides for batch, gamma and the optimiser).  Actor as in
+ * nav_policy; twin critics (obs_dim + 2) -> hidden -> hidden -> (mean, raw
+ * scale) with sigma = softplus(raw) + 0.1; target critics by Polyak
+ * averaging (tau).  Critic loss w Huber(m - y_mean) + Gaussian NLL of the
+ * sampled target y (clipped double Q, draw clipped to +-3 sigma) with the
+ * uncertainty weight w = clip(sbar^2 / sigma^2, 0.5, 2); actor loss
+ * alpha logpi - min_i m_i every policy_freq critic updates; log alpha by Adam
+ * towards target_entropy.  BF16 tensor-core GEMMs (tcgen05) with FP32 master
+ * weights and FP32 Adam. */
+typedef struct {
+    int obs_dim, hidden, batch;
+    long long replay_capacity;
+    float lr_actor, lr_critic, lr_alpha, beta1, beta2, gamma, tau, tau_b, reward_scale,
+        huber_delta, alpha_init, target_entropy;
+    int policy_freq;
+    uint64_t seed;
+} nav_train_cfg;
+typedef struct nav_trainer nav_trainer;
+void nav_train_default_cfg(nav_train_cfg *c); /* obs 364, hidden 256, batch 4096, replay 4 Mi,
+                                                 lr 3e-4, betas (0.9, 0.95), gamma 0.99, tau 0.1,
+                                                 tau_b 0.005, reward scale 0.4, Huber 50,
+                                                 alpha 0.001, target entropy -1, policy freq 2 */
+int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out); /* synchronous */
+void nav_trainer_free(nav_trainer *t);
+const char *nav_trainer_last_error(const nav_trainer *t);
+
+/* Appends n_envs transitions to the device replay ring (obs and next obs
+ * stored as BF16): next obs = final_obs_dev's row for envs whose done flag
+ * has bit0 or bit1 set (final_obs_dev may be NULL), else next_obs_dev's;
+ * terminal = bit0 (a truncated episode still bootstraps).  All arrays are
+ * device rows of obs_dim floats / [n_envs][2] actions / [n_envs] rewards. */
+int nav_train_insert(nav_trainer *t, const float *obs_dev, const float *act_dev,
+                     const float *rew_dev, const uint8_t *done_dev, const float *next_obs_dev,
+                     const float *final_obs_dev, int n_envs, void *stream);
+
+/* n_updates gradient steps on batches drawn uniformly from the replay (needs
+ * at least one batch of transitions), asynchronous on `stream`. */
+int nav_train_update(nav_trainer *t, int n_updates, void *stream);
+
+/* Copies the trainer's actor into a policy handle (actor-weight sync). */
+int nav_trainer_sync_policy(nav_trainer *t, nav_policy *p, void *stream);
+
+/* Parity hooks (synchronous, host buffers): what 0..4 = parameters of actor,
+ * critic 1, critic 2, target 1, target 2 (order as nav_policy weights; set=1
+ * writes); 10..12 = last gradients of actor, critic 1, critic 2; 20 batch
+ * indices, 21 actor-update noise, 22 next-action noise, 23 target noise,
+ * 24 scalars (log alpha, sbar, ...), 25 y, 26 y_mean, 27 critic-1 outputs,
+ * 28 logpi of the actor update, 29 its actions, 30 actor outputs, 31 logpi of
+ * the next actions. */
+int nav_trainer_io(nav_trainer *t, int what, int set, void *host);
+int nav_trainer_counts(const nav_trainer *t, int64_t *replay_size, int64_t *critic_updates,
+                       int64_t *actor_updates);
+
+/* Evaluation (success-rate protocol of Sec. 3.2): begin clears per-env
+ * accumulators, accumulate adds one step's rewards (FP64) to envs whose first
+ * episode is still running and records success (goal without collision) when
+ * it ends, result reduces success count and return sum in FP64 and copies the
+ * two doubles to the host (synchronous). */
+int nav_eval_begin(nav_trainer *t, int n_envs, void *stream);
+int nav_eval_accumulate(nav_trainer *t, const float *reward_dev, const uint8_t *done_dev,
+                        int n_envs, void *stream);
+int nav_eval_result(nav_trainer *t, int n_envs, double *successes, double *return_sum,
+                    void *stream);
+
 const char *nav_last_error(const nav_handle *h);
 void nav_free(nav_handle *h);
 

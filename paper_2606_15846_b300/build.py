@@ -20,7 +20,7 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_GEOMETRY = ["nav_step.cu"]
-CU_DEFAULT = ["nav_noalloc.cu", "nav_mlp.cu", "nav_policy.cu"]
+CU_DEFAULT = ["nav_noalloc.cu", "nav_mlp.cu", "nav_policy.cu", "nav_learn.cu"]
 CPP = ["nav_api.cpp"]
 
 

@@ -113,6 +113,11 @@ int launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int 
                      const float *bias, int act, float *C32, int ldc32, void *C16, int ldc16,
                      void *C16T, int ldct, int *status, void *stream);
 
+// Split-K variant for weight gradients (large K = batch): C32 = A B^T, C32
+// zeroed on the stream first, partial products added atomically.
+int launch_gemm_bf16_splitk(const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                            float *C32, int ldc32, int *status, void *stream);
+
 // Read-only facts about a handle for entry points defined outside nav_api.cpp.
 struct HandleView {
     int device;

@@ -1,0 +1,827 @@
+// FastDSAC learner on the GPU (Sec. 2.3, FastDSAC paragraph; Table 4) and the
+// evaluation reductions.  Readings of the update (the paper states it in prose):
+//  critic i outputs (mean m_i, raw scale q_i), sigma_i = softplus(q_i) + 0.1;
+//  target: z ~ N(m', sigma') of the target critic with the smaller mean
+//  (clipped double Q), the normal draw clipped to +-3;
+//  y = rs r + gamma (1 - term) (z - alpha logpi(a'|s')), y_mean with m';
+//  critic loss w Huber_delta(m - y_mean) + log sigma + (y - sg(m))^2/(2 sigma^2),
+//  w = clip(sbar^2 / (sigma^2 + 1e-6), 0.5, 2) constant, sbar a running mean
+//  (rate tau_b) of the batch-mean sigma;
+//  actor loss mean(alpha logpi(a~|s) - min_i m_i(s, a~)), every policy_freq
+//  critic updates; log alpha by Adam on mean(-log alpha (logpi + H_target));
+//  target critics by Polyak averaging with rate tau.
+// All GEMMs run on the tcgen05 kernel (BF16 operands, FP32 accumulation);
+// master weights, Adam moments and every reduction are FP32, the evaluation
+// success count and return sums FP64.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nav_internal.h"
+#include "nav_policy.h"
+
+namespace flashnav {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ unsigned long long hmix(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float softplusf(float x) {
+    return log1pf(expf(-fabsf(x))) + fmaxf(x, 0.0f);
+}
+
+// ---------------------------------------------------------------- replay ---
+__global__ void k_replay_insert(const float *__restrict__ obs, const float *__restrict__ act,
+                                const float *__restrict__ rew, const unsigned char *__restrict__ done,
+                                const float *__restrict__ obs_next,
+                                const float *__restrict__ final_obs, int E, int od, int ld,
+                                long long head, long long cap, bf16 *r_obs, bf16 *r_next,
+                                float *r_act, float *r_rew, float *r_term) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)E * ld) return;
+    const int e = (int)(i / ld), c = (int)(i - (long long)e * ld);
+    const long long slot = (head + e) % cap;
+    const bool ended = (done[e] & 3) != 0;
+    const float *nxt = (ended && final_obs) ? final_obs : obs_next;
+    r_obs[slot * ld + c] = __float2bfloat16_rn(c < od ? obs[(long long)e * od + c] : 0.0f);
+    r_next[slot * ld + c] = __float2bfloat16_rn(c < od ? nxt[(long long)e * od + c] : 0.0f);
+    if (c == 0) {
+        r_act[slot * 2] = act[2 * e];
+        r_act[slot * 2 + 1] = act[2 * e + 1];
+        r_rew[slot] = rew[e];
+        r_term[slot] = (done[e] & 1) ? 1.0f : 0.0f; // truncation still bootstraps
+    }
+}
+
+__global__ void k_sample(int *idx, int B, long long size, unsigned long long seed,
+                         unsigned long long update) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const unsigned long long h = hmix(seed ^ (update * 0xD6E8FEB86659FD93ull) ^ ((unsigned long long)b << 1));
+    idx[b] = (int)(((h >> 32) * (unsigned long long)size) >> 32);
+}
+
+// batch rows: Xo = obs, Xn = next obs (BF16 [B][ld]); Xc = [obs, act] ([B][ldc])
+__global__ void k_gather(const int *__restrict__ idx, const bf16 *__restrict__ r_obs,
+                         const bf16 *__restrict__ r_next, const float *__restrict__ r_act,
+                         const float *__restrict__ r_rew, const float *__restrict__ r_term, int B,
+                         int od, int ld, int ldc, bf16 *Xo, bf16 *Xn, bf16 *Xc, float *rew,
+                         float *term) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * ldc) return;
+    const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
+    const long long s = idx[b];
+    if (c < ld) {
+        Xo[(long long)b * ld + c] = r_obs[s * ld + c];
+        Xn[(long long)b * ld + c] = r_next[s * ld + c];
+    }
+    bf16 v = __float2bfloat16_rn(0.0f);
+    if (c < od) v = r_obs[s * ld + c];
+    else if (c < od + 2) v = __float2bfloat16_rn(r_act[s * 2 + (c - od)]);
+    Xc[(long long)b * ldc + c] = v;
+    if (c == 0) {
+        rew[b] = r_rew[s];
+        term[b] = r_term[s];
+    }
+}
+
+// Xc = [Xo[:, :od], a] for the actor's own action
+__global__ void k_concat(const bf16 *__restrict__ Xo, int ld, const float *__restrict__ a, int B,
+                         int od, int ldc, bf16 *Xc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * ldc) return;
+    const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
+    bf16 v = __float2bfloat16_rn(0.0f);
+    if (c < od) v = Xo[(long long)b * ld + c];
+    else if (c < od + 2) v = __float2bfloat16_rn(a[2 * b + (c - od)]);
+    Xc[(long long)b * ldc + c] = v;
+}
+
+// out[c][r] = in[r][c] for r < rows, c < cols (32 x 32 tiles through smem)
+__global__ void k_transpose(const bf16 *__restrict__ in, int ld_in, int rows, int cols, bf16 *out,
+                            int ld_out) {
+    __shared__ bf16 t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[j][threadIdx.x] = in[(long long)r * ld_in + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(long long)c * ld_out + r] = t[threadIdx.x][j];
+    }
+}
+
+// ----------------------------------------------------------------- heads ---
+__global__ void k_targets(const float *__restrict__ rew, const float *__restrict__ term,
+                          const float *__restrict__ tq1, const float *__restrict__ tq2,
+                          const float *__restrict__ logp_next, const float *__restrict__ log_alpha,
+                          int B, float gamma, float rs, unsigned long long seed,
+                          unsigned long long update, float *y, float *ym, float *znoise) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float m1 = tq1[2 * b], s1 = softplusf(tq1[2 * b + 1]) + 0.1f;
+    const float m2 = tq2[2 * b], s2 = softplusf(tq2[2 * b + 1]) + 0.1f;
+    const bool p1 = m1 <= m2;
+    const float m = p1 ? m1 : m2, s = p1 ? s1 : s2;
+    const unsigned long long h = hmix(seed ^ (update * 0x8CB92BA72F3D8DD7ull) ^ ((unsigned long long)b << 20) ^ 0xA11CEull);
+    const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = (float)((h >> 8) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+    const float zn = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float z = m + s * fminf(fmaxf(zn, -3.0f), 3.0f);
+    const float alpha = expf(*log_alpha);
+    const float cont = gamma * (1.0f - term[b]);
+    y[b] = rs * rew[b] + cont * (z - alpha * logp_next[b]);
+    ym[b] = rs * rew[b] + cont * (m - alpha * logp_next[b]);
+    if (znoise) znoise[b] = zn;
+}
+
+// dL/dq for one critic; accumulates the batch sum of sigma and the loss
+__global__ void k_critic_grad(const float *__restrict__ q, const float *__restrict__ y,
+                              const float *__restrict__ ym, const float *__restrict__ sbar, int B,
+                              float delta, float *dq, float *acc /*[0] sum sigma, [1] loss*/) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float ss = 0.0f, ll = 0.0f;
+    if (b < B) {
+        const float m = q[2 * b], qr = q[2 * b + 1];
+        const float s = softplusf(qr) + 0.1f;
+        const float sb = *sbar;
+        const float w = fminf(fmaxf(sb * sb / (s * s + 1e-6f), 0.5f), 2.0f);
+        const float e = m - ym[b];
+        const float ae = fabsf(e);
+        const float hub = ae <= delta ? 0.5f * e * e : delta * (ae - 0.5f * delta);
+        const float d2 = (y[b] - m) * (y[b] - m);
+        ll = w * hub + logf(s) + d2 / (2.0f * s * s);
+        const float inv = 1.0f / (float)B;
+        dq[2 * b] = w * fminf(fmaxf(e, -delta), delta) * inv;
+        const float sig = 1.0f / (1.0f + expf(-qr));
+        dq[2 * b + 1] = (1.0f / s - d2 / (s * s * s)) * inv * sig;
+        ss = s;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        ll += __shfl_xor_sync(0xffffffffu, ll, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], ss);
+        atomicAdd(&acc[1], ll);
+    }
+}
+
+__global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
+    *sbar = (1.0f - tau_b) * (*sbar) + tau_b * (acc[0] / (float)n);
+    acc[2] = acc[1];
+    acc[0] = 0.0f;
+    acc[1] = 0.0f;
+}
+
+// actor loss mean(alpha logp - min(q1, q2)) -> dL/dlogp and dL/dq_i (mean column)
+__global__ void k_actor_loss(const float *__restrict__ logp, const float *__restrict__ q1,
+                             const float *__restrict__ q2, const float *__restrict__ log_alpha,
+                             int B, float *dlogp, float *dq1, float *dq2, float *acc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float ll = 0.0f, lp = 0.0f;
+    if (b < B) {
+        const float alpha = expf(*log_alpha);
+        const bool p1 = q1[2 * b] <= q2[2 * b];
+        const float inv = 1.0f / (float)B;
+        dlogp[b] = alpha * inv;
+        dq1[2 * b] = p1 ? -inv : 0.0f;
+        dq2[2 * b] = p1 ? 0.0f : -inv;
+        dq1[2 * b + 1] = 0.0f;
+        dq2[2 * b + 1] = 0.0f;
+        ll = alpha * logp[b] - (p1 ? q1[2 * b] : q2[2 * b]);
+        lp = logp[b];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        lp += __shfl_xor_sync(0xffffffffu, lp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], ll);
+        atomicAdd(&acc[1], lp);
+    }
+}
+
+// backward of the squashed-Gaussian head: d out4 from dL/da and dL/dlogp
+__global__ void k_actor_head_bwd(const float *__restrict__ out4, const float *__restrict__ eps,
+                                 const float *__restrict__ dX1, const float *__restrict__ dX2,
+                                 int ldx, int od, const float *__restrict__ dlogp, int B,
+                                 float *dout) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        const float u = out4[4 * b + d], r = out4[4 * b + 2 + d];
+        const float tr = tanhf(r);
+        const float ls = kLogStdMin + (kLogStdMax - kLogStdMin) * 0.5f * (tr + 1.0f);
+        const float sg = expf(ls);
+        const float e = eps[2 * b + d];
+        const float a = tanhf(u + sg * e);
+        const float da = dX1[(long long)b * ldx + od + d] + dX2[(long long)b * ldx + od + d];
+        const float om = 1.0f - a * a;
+        const float dpre = da * om + dlogp[b] * (2.0f * a * om / (om + 1e-6f));
+        const float dls = dpre * sg * e - dlogp[b];
+        dout[4 * b + d] = dpre;
+        dout[4 * b + 2 + d] = dls * (kLogStdMax - kLogStdMin) * 0.5f * (1.0f - tr * tr);
+    }
+}
+
+// ------------------------------------------------------------- backward ---
+// FP32 [B][n] -> BF16 [B][ldp] (zero pad) and its transpose [n][B]
+__global__ void k_grad_to_bf16(const float *__restrict__ g, int B, int n, int ldp, bf16 *g16,
+                               bf16 *gT16) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * ldp) return;
+    const int b = (int)(i / ldp), c = (int)(i - (long long)b * ldp);
+    const bf16 v = __float2bfloat16_rn(c < n ? g[(long long)b * n + c] : 0.0f);
+    g16[i] = v;
+    if (c < n) gT16[(long long)c * B + b] = v;
+}
+
+// dZ = dH * leaky'(z) with the sign of z read from the activation h = leaky(z);
+// writes dZ in place (FP32), as BF16 [B][H] and as BF16 [H][B] (32 x 32 tiles)
+__global__ void k_leaky_bwd(float *dH, const bf16 *__restrict__ h, int B, int H, bf16 *dZ16,
+                            bf16 *dZT16) {
+    __shared__ bf16 t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        if (r < B && c < H) {
+            const long long o = (long long)r * H + c;
+            const float d = dH[o] * (__bfloat162float(h[o]) > 0.0f ? 1.0f : 0.01f);
+            dH[o] = d;
+            const bf16 v = __float2bfloat16_rn(d);
+            dZ16[o] = v;
+            t[j][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (r < B && c < H) dZT16[(long long)c * B + r] = t[threadIdx.x][j];
+    }
+}
+
+// column sums of FP32 [B][n] (bias gradients)
+__global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) {
+    __shared__ float part[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    float s = 0.0f;
+    if (c < n)
+        for (int r = threadIdx.y; r < B; r += 8) s += g[(long long)r * n + c];
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < n) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
+        out[c] = t;
+    }
+}
+
+// ----------------------------------------------------------- optimiser ---
+// Adam (bias-corrected, no weight decay); weights also refresh their BF16
+// copies W16 [out][ld_in] and WT16 [in][ld_out] (pass null for biases).
+__global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v, int n, float lr,
+                       float b1, float b2, float c1, float c2, int in, bf16 *W16, int ld_in,
+                       bf16 *WT16, int ld_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    p[i] = pi;
+    if (W16) {
+        const int o = i / in, k = i - o * in;
+        const bf16 b16 = __float2bfloat16_rn(pi);
+        W16[(long long)o * ld_in + k] = b16;
+        WT16[(long long)k * ld_out + o] = b16;
+    }
+}
+
+__global__ void k_polyak(float *t, const float *__restrict__ s, int n, float tau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t[i] = (1.0f - tau) * t[i] + tau * s[i];
+}
+
+// log alpha <- Adam step on mean(-log alpha (logp + H_target)); acc[1] = sum logp
+__global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc, int B,
+                        float target_entropy, float lr, float b1, float b2, float c1, float c2) {
+    const float g = -(acc[1] / (float)B + target_entropy);
+    const float mi = b1 * (*am) + (1.0f - b1) * g;
+    const float vi = b2 * (*av) + (1.0f - b2) * g * g;
+    *am = mi;
+    *av = vi;
+    *log_alpha -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+__global__ void k_zero(float *p, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0.0f;
+}
+
+// ----------------------------------------------------------- evaluation ---
+// first episode of each env: FP64 return, success = goal before collision or
+// timeout
+__global__ void k_eval_acc(const float *__restrict__ rew, const unsigned char *__restrict__ done,
+                           int E, unsigned char *finished, unsigned char *success, double *ret) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E || finished[e]) return;
+    ret[e] += (double)rew[e];
+    if (done[e] & 3) {
+        finished[e] = 1;
+        success[e] = (done[e] & 4) && !(done[e] & 8) ? 1 : 0;
+    }
+}
+
+// FP64 block reduction of success count and return sum into out[0..1]
+__global__ void k_eval_reduce(const unsigned char *__restrict__ success,
+                              const double *__restrict__ ret, int E, double *out) {
+    __shared__ double s0[256], s1[256];
+    double a = 0.0, b = 0.0;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        a += (double)success[e];
+        b += ret[e];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s0[threadIdx.x] += s0[threadIdx.x + w];
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s0[0];
+        out[1] = s1[0];
+    }
+}
+
+unsigned blocks(long long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+} // namespace
+} // namespace flashnav
+
+using namespace flashnav;
+
+struct nav_trainer {
+    nav_train_cfg cfg{};
+    int od = 0, ld = 0, ldc = 0, H = 0, B = 0;
+    long long cap = 0, size = 0, head = 0;
+    unsigned long long n_critic = 0, n_actor = 0, n_alpha = 0;
+    Mlp actor, q[2], qt[2];
+    std::string err;
+    std::vector<void *> mem;
+    // replay
+    bf16 *r_obs = nullptr, *r_next = nullptr;
+    float *r_act = nullptr, *r_rew = nullptr, *r_term = nullptr;
+    // batch
+    int *idx = nullptr;
+    bf16 *Xo = nullptr, *Xn = nullptr, *Xc = nullptr, *Xnc = nullptr, *Xa = nullptr;
+    bf16 *XoT = nullptr, *XcT = nullptr;
+    float *rew = nullptr, *term = nullptr;
+    // activations: [0] actor, [1] q0, [2] q1, [3] scratch
+    bf16 *h16[4][2] = {}, *ht16[4][2] = {};
+    float *out_a = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
+    float *a_next = nullptr, *logp_next = nullptr, *a_new = nullptr, *logp_new = nullptr,
+          *eps_new = nullptr, *eps_next = nullptr;
+    float *y = nullptr, *ym = nullptr, *znoise = nullptr, *dq[2] = {}, *dlogp = nullptr,
+          *dout = nullptr;
+    float *dH = nullptr, *dX[2] = {};
+    bf16 *g16 = nullptr, *gT16 = nullptr, *dZ16 = nullptr, *dZT16 = nullptr;
+    float *scal = nullptr; // [0] log_alpha [1] sbar [2..3] alpha Adam [4..7] critic acc [8..9] actor acc
+    int *status = nullptr;
+    // evaluation
+    unsigned char *ev_fin = nullptr, *ev_succ = nullptr;
+    double *ev_ret = nullptr, *ev_out = nullptr;
+    int ev_cap = 0;
+};
+
+namespace {
+
+template <class T> cudaError_t talloc(nav_trainer *t, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
+    if (e == cudaSuccess) {
+        cudaMemset(q, 0, std::max<size_t>(count * sizeof(T), 16));
+        t->mem.push_back(q);
+        *p = static_cast<T *>(q);
+    }
+    return e;
+}
+
+int tfail(nav_trainer *t, int code, const std::string &m) {
+    if (t) t->err = m;
+    return code;
+}
+
+// Backward through a 3-layer MLP from dL/dout (FP32 [B][n_out]).  `s` holds
+// the saved activations (BF16 and transposed), XT the transposed input.
+// wgrad: fill layer gradients; dX: input gradient FP32 [B][ldx] (may be null).
+int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 *XT, bool wgrad,
+                 float *dX, int ldx, cudaStream_t st) {
+    const int B = T->B, H = T->H;
+    Layer &L3 = net.layer[2], &L2 = net.layer[1], &L1 = net.layer[0];
+    const int n_out = L3.out;
+    int rc = 0;
+    k_grad_to_bf16<<<blocks((long long)B * 8), 256, 0, st>>>(dout, B, n_out, 8, T->g16, T->gT16);
+    if (wgrad) {
+        rc |= launch_gemm_bf16_splitk(T->gT16, B, T->ht16[s][1], B, n_out, H, B, L3.gW, H,
+                                      T->status, st);
+        k_colsum<<<blocks(n_out, 32), dim3(32, 8), 0, st>>>(dout, B, n_out, L3.gb);
+    }
+    rc |= launch_gemm_bf16(T->g16, 8, L3.WT16, L3.ld_out, B, H, n_out, nullptr, 0, T->dH, H,
+                           nullptr, 0, nullptr, 0, T->status, st);
+    const dim3 tb(32, 8), tg((H + 31) / 32, (B + 31) / 32);
+    k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][1], B, H, T->dZ16, T->dZT16);
+    if (wgrad) {
+        rc |= launch_gemm_bf16_splitk(T->dZT16, B, T->ht16[s][0], B, H, H, B, L2.gW, H,
+                                      T->status, st);
+        k_colsum<<<blocks(H, 32), dim3(32, 8), 0, st>>>(T->dH, B, H, L2.gb);
+    }
+    rc |= launch_gemm_bf16(T->dZ16, H, L2.WT16, L2.ld_out, B, H, H, nullptr, 0, T->dH, H, nullptr,
+                           0, nullptr, 0, T->status, st);
+    k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][0], B, H, T->dZ16, T->dZT16);
+    if (wgrad) {
+        rc |= launch_gemm_bf16_splitk(T->dZT16, B, XT, B, H, L1.in, B, L1.gW, L1.in, T->status, st);
+        k_colsum<<<blocks(H, 32), dim3(32, 8), 0, st>>>(T->dH, B, H, L1.gb);
+    }
+    if (dX)
+        rc |= launch_gemm_bf16(T->dZ16, H, L1.WT16, L1.ld_out, B, L1.in, H, nullptr, 0, dX, ldx,
+                               nullptr, 0, nullptr, 0, T->status, st);
+    rc |= (int)cudaGetLastError();
+    return rc;
+}
+
+int adam_net(nav_trainer *T, Mlp &net, float lr, unsigned long long step, cudaStream_t st) {
+    const float b1 = T->cfg.beta1, b2 = T->cfg.beta2;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    for (int l = 0; l < net.n_layers; ++l) {
+        Layer &L = net.layer[l];
+        const int nw = L.in * L.out;
+        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, c1, c2, L.in,
+                                           static_cast<bf16 *>(L.W16), L.ld_in,
+                                           static_cast<bf16 *>(L.WT16), L.ld_out);
+        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, c1, c2, 0,
+                                              nullptr, 0, nullptr, 0);
+    }
+    return (int)cudaGetLastError();
+}
+
+int polyak_net(Mlp &tgt, const Mlp &src, float tau, cudaStream_t st) {
+    for (int l = 0; l < tgt.n_layers; ++l) {
+        const int nw = tgt.layer[l].in * tgt.layer[l].out;
+        k_polyak<<<blocks(nw), 256, 0, st>>>(tgt.layer[l].W, src.layer[l].W, nw, tau);
+        k_polyak<<<blocks(tgt.layer[l].out), 256, 0, st>>>(tgt.layer[l].b, src.layer[l].b,
+                                                           tgt.layer[l].out, tau);
+    }
+    return tgt.refresh(st);
+}
+
+int copy_net(Mlp &dst, const Mlp &src) {
+    for (int l = 0; l < dst.n_layers; ++l) {
+        const size_t nw = (size_t)dst.layer[l].in * dst.layer[l].out;
+        cudaMemcpy(dst.layer[l].W, src.layer[l].W, nw * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(dst.layer[l].b, src.layer[l].b, dst.layer[l].out * 4, cudaMemcpyDeviceToDevice);
+    }
+    return dst.refresh(nullptr);
+}
+
+// forward with saved activations (slot s) of a network on BF16 input x
+int fwd(nav_trainer *T, const Mlp &net, const bf16 *x, int s, bool save_t, float *out,
+        cudaStream_t st) {
+    void *h[2] = {T->h16[s][0], T->h16[s][1]};
+    void *ht[2] = {T->ht16[s][0], T->ht16[s][1]};
+    return net.forward_tc(x, T->B, h, save_t ? ht : nullptr, out, T->status, st);
+}
+
+} // namespace
+
+extern "C" {
+
+void nav_train_default_cfg(nav_train_cfg *c) {
+    if (!c) return;
+    c->obs_dim = 364;
+    c->hidden = 256;
+    c->batch = 4096;
+    c->replay_capacity = 4 << 20;
+    c->lr_actor = 3e-4f;
+    c->lr_critic = 3e-4f;
+    c->lr_alpha = 3e-4f;
+    c->beta1 = 0.9f;
+    c->beta2 = 0.95f;
+    c->gamma = 0.99f;
+    c->tau = 0.1f;
+    c->tau_b = 0.005f;
+    c->reward_scale = 0.4f;
+    c->huber_delta = 50.0f;
+    c->alpha_init = 0.001f;
+    c->target_entropy = -1.0f;
+    c->policy_freq = 2;
+    c->seed = 1;
+}
+
+void nav_trainer_free(nav_trainer *t) {
+    if (!t) return;
+    cudaDeviceSynchronize();
+    t->actor.release();
+    for (int i = 0; i < 2; ++i) {
+        t->q[i].release();
+        t->qt[i].release();
+    }
+    for (void *p : t->mem) cudaFree(p);
+    delete t;
+}
+
+int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
+    if (!out) return NAV_E_INVAL;
+    *out = nullptr;
+    nav_train_cfg c;
+    if (cfg) c = *cfg;
+    else nav_train_default_cfg(&c);
+    if (c.obs_dim <= 0 || c.hidden <= 0 || c.hidden % 32 || c.batch < 128 || c.batch % 128 ||
+        c.replay_capacity < c.batch || c.replay_capacity > ((long long)1 << 31) ||
+        c.policy_freq < 1)
+        return NAV_E_INVAL;
+    nav_trainer *T = new (std::nothrow) nav_trainer();
+    if (!T) return NAV_E_NOMEM;
+    T->cfg = c;
+    T->od = c.obs_dim;
+    T->ld = (c.obs_dim + 7) / 8 * 8;
+    T->ldc = (c.obs_dim + 2 + 7) / 8 * 8;
+    T->H = c.hidden;
+    T->B = c.batch;
+    T->cap = c.replay_capacity;
+    int rc = T->actor.init({T->od, T->H, T->H, 4}, c.seed * 4 + 1, T->err);
+    for (int i = 0; i < 2 && rc == NAV_OK; ++i) {
+        rc = T->q[i].init({T->od + 2, T->H, T->H, 2}, c.seed * 4 + 2 + i, T->err);
+        if (rc == NAV_OK) rc = T->qt[i].init({T->od + 2, T->H, T->H, 2}, c.seed * 4 + 2 + i, T->err);
+    }
+    cudaError_t e = rc == NAV_OK ? cudaSuccess : cudaErrorUnknown;
+    const long long B = T->B, H = T->H;
+#define TA(p, n) if (e == cudaSuccess) e = talloc(T, &(p), (size_t)(n))
+    TA(T->r_obs, T->cap * T->ld);
+    TA(T->r_next, T->cap * T->ld);
+    TA(T->r_act, T->cap * 2);
+    TA(T->r_rew, T->cap);
+    TA(T->r_term, T->cap);
+    TA(T->idx, B);
+    TA(T->Xo, B * T->ld);
+    TA(T->Xn, B * T->ld);
+    TA(T->Xc, B * T->ldc);
+    TA(T->Xnc, B * T->ldc);
+    TA(T->Xa, B * T->ldc);
+    TA(T->XoT, (long long)T->od * B);
+    TA(T->XcT, (long long)(T->od + 2) * B);
+    TA(T->rew, B);
+    TA(T->term, B);
+    for (int s = 0; s < 4; ++s)
+        for (int l = 0; l < 2; ++l) {
+            TA(T->h16[s][l], B * H);
+            TA(T->ht16[s][l], B * H);
+        }
+    TA(T->out_a, B * 4);
+    for (int i = 0; i < 2; ++i) {
+        TA(T->qo[i], B * 2);
+        TA(T->tq[i], B * 2);
+        TA(T->qa[i], B * 2);
+        TA(T->dq[i], B * 2);
+        TA(T->dX[i], B * T->ldc);
+    }
+    TA(T->a_next, B * 2);
+    TA(T->logp_next, B);
+    TA(T->a_new, B * 2);
+    TA(T->logp_new, B);
+    TA(T->eps_new, B * 2);
+    TA(T->eps_next, B * 2);
+    TA(T->y, B);
+    TA(T->ym, B);
+    TA(T->znoise, B);
+    TA(T->dlogp, B);
+    TA(T->dout, B * 4);
+    TA(T->dH, B * H);
+    TA(T->g16, B * 8);
+    TA(T->gT16, 8 * B);
+    TA(T->dZ16, B * H);
+    TA(T->dZT16, B * H);
+    TA(T->scal, 16);
+    TA(T->status, 1);
+#undef TA
+    if (e != cudaSuccess) {
+        nav_trainer_free(T);
+        return rc != NAV_OK ? rc : NAV_E_NOMEM;
+    }
+    copy_net(T->qt[0], T->q[0]);
+    copy_net(T->qt[1], T->q[1]);
+    float init[2] = {std::log(c.alpha_init), 1.0f};
+    cudaMemcpy(T->scal, init, sizeof(init), cudaMemcpyHostToDevice);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        nav_trainer_free(T);
+        return NAV_E_CUDA;
+    }
+    *out = T;
+    return NAV_OK;
+}
+
+const char *nav_trainer_last_error(const nav_trainer *t) { return t ? t->err.c_str() : "null"; }
+
+int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
+                     const float *rew_dev, const uint8_t *done_dev, const float *next_obs_dev,
+                     const float *final_obs_dev, int n_envs, void *stream) {
+    if (!T || !obs_dev || !act_dev || !rew_dev || !done_dev || !next_obs_dev || n_envs <= 0 ||
+        n_envs > T->cap)
+        return tfail(T, NAV_E_INVAL, "nav_train_insert: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_replay_insert<<<blocks((long long)n_envs * T->ld), 256, 0, st>>>(
+        obs_dev, act_dev, rew_dev, done_dev, next_obs_dev, final_obs_dev, n_envs, T->od, T->ld,
+        T->head, T->cap, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
+    T->head = (T->head + n_envs) % T->cap;
+    T->size = std::min(T->cap, T->size + n_envs);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
+    if (!T || n_updates <= 0) return tfail(T, NAV_E_INVAL, "nav_train_update: bad argument");
+    if (T->size < T->B) return tfail(T, NAV_E_INVAL, "nav_train_update: replay smaller than a batch");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const nav_train_cfg &c = T->cfg;
+    const int B = T->B;
+    int rc = 0;
+    for (int u = 0; u < n_updates; ++u) {
+        const unsigned long long un = T->n_critic;
+        // ---- critic update
+        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->size, c.seed, un);
+        k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
+            T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
+            T->Xo, T->Xn, T->Xc, T->rew, T->term);
+        const dim3 tb(32, 8);
+        k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
+            T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
+        // next action from the current actor
+        rc |= fwd(T, T->actor, T->Xn, 3, false, T->out_a, st);
+        rc |= launch_actor_head(T->out_a, B, 1, c.seed ^ 0x5A5Aull, (unsigned)(2 * un + 1),
+                                T->a_next, T->logp_next, T->eps_next, st);
+        k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
+                                                                T->ldc, T->Xnc);
+        for (int i = 0; i < 2; ++i) rc |= fwd(T, T->qt[i], T->Xnc, 3, false, T->tq[i], st);
+        k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
+                                             T->scal + 0, B, c.gamma, c.reward_scale, c.seed, un,
+                                             T->y, T->ym, T->znoise);
+        for (int i = 0; i < 2; ++i) {
+            rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], st);
+            k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
+                                                     c.huber_delta, T->dq[i], T->scal + 4);
+        }
+        k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+        for (int i = 0; i < 2; ++i) {
+            rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, st);
+            rc |= adam_net(T, T->q[i], c.lr_critic, un + 1, st);
+        }
+        T->n_critic++;
+        // ---- actor and temperature update every policy_freq critic updates
+        if (T->n_critic % (unsigned long long)c.policy_freq == 0) {
+            const unsigned long long an = T->n_actor;
+            k_transpose<<<dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st>>>(T->Xo, T->ld, B,
+                                                                              T->od, T->XoT, B);
+            rc |= fwd(T, T->actor, T->Xo, 0, true, T->out_a, st);
+            rc |= launch_actor_head(T->out_a, B, 1, c.seed ^ 0xA5A5ull, (unsigned)(2 * an),
+                                    T->a_new, T->logp_new, T->eps_new, st);
+            k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xo, T->ld, T->a_new, B,
+                                                                    T->od, T->ldc, T->Xa);
+            for (int i = 0; i < 2; ++i) rc |= fwd(T, T->q[i], T->Xa, 1 + i, false, T->qa[i], st);
+            k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
+            k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
+                                                    B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+            for (int i = 0; i < 2; ++i)
+                rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, nullptr, false, T->dX[i], T->ldc,
+                                   st);
+            k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
+                                                        T->ldc, T->od, T->dlogp, B, T->dout);
+            rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true, nullptr, 0, st);
+            rc |= adam_net(T, T->actor, c.lr_actor, an + 1, st);
+            const float c1 = 1.0f - powf(c.beta1, (float)(an + 1));
+            const float c2 = 1.0f - powf(c.beta2, (float)(an + 1));
+            k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
+                                     c.target_entropy, c.lr_alpha, c.beta1, c.beta2, c1, c2);
+            T->n_actor++;
+        }
+        for (int i = 0; i < 2; ++i) rc |= polyak_net(T->qt[i], T->q[i], c.tau, st);
+        rc |= (int)cudaGetLastError();
+        if (rc) return tfail(T, NAV_E_CUDA, "nav_train_update: launch failed");
+    }
+    return NAV_OK;
+}
+
+int nav_trainer_io(nav_trainer *T, int what, int set, void *host) {
+    if (!T || !host) return NAV_E_INVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return NAV_E_CUDA;
+    Mlp *nets[5] = {&T->actor, &T->q[0], &T->q[1], &T->qt[0], &T->qt[1]};
+    float *fh = static_cast<float *>(host);
+    if (what >= 0 && what < 5) return nets[what]->copy_params(fh, !set) == 0 ? NAV_OK : NAV_E_CUDA;
+    if (what >= 10 && what < 13 && !set) {
+        Mlp &n = *nets[what - 10];
+        long long off = 0;
+        for (int l = 0; l < n.n_layers; ++l) {
+            const size_t nw = (size_t)n.layer[l].in * n.layer[l].out;
+            cudaMemcpy(fh + off, n.layer[l].gW, nw * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(fh + off + nw, n.layer[l].gb, n.layer[l].out * 4, cudaMemcpyDeviceToHost);
+            off += (long long)nw + n.layer[l].out;
+        }
+        return NAV_OK;
+    }
+    const size_t B = (size_t)T->B;
+    struct { int id; void *p; size_t bytes; } bufs[] = {
+        {20, T->idx, B * 4},        {21, T->eps_new, B * 8},  {22, T->eps_next, B * 8},
+        {23, T->znoise, B * 4},     {24, T->scal, 16 * 4},    {25, T->y, B * 4},
+        {26, T->ym, B * 4},         {27, T->qo[0], B * 8},    {28, T->logp_new, B * 4},
+        {29, T->a_new, B * 8},      {30, T->out_a, B * 16},   {31, T->logp_next, B * 4}};
+    for (auto &b : bufs)
+        if (b.id == what) {
+            const cudaError_t e = set ? cudaMemcpy(b.p, host, b.bytes, cudaMemcpyHostToDevice)
+                                      : cudaMemcpy(host, b.p, b.bytes, cudaMemcpyDeviceToHost);
+            return e == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+        }
+    return NAV_E_INVAL;
+}
+
+int nav_trainer_sync_policy(nav_trainer *T, nav_policy *p, void *stream) {
+    Mlp *dst = p ? policy_actor(p) : nullptr;
+    if (!T || !dst || dst->n_layers != T->actor.n_layers) return NAV_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int l = 0; l < dst->n_layers; ++l) {
+        const Layer &S = T->actor.layer[l];
+        Layer &D = dst->layer[l];
+        if (D.in != S.in || D.out != S.out) return NAV_E_INVAL;
+        cudaMemcpyAsync(D.W, S.W, (size_t)S.in * S.out * 4, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(D.b, S.b, (size_t)S.out * 4, cudaMemcpyDeviceToDevice, st);
+    }
+    return dst->refresh(stream) == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_trainer_counts(const nav_trainer *T, int64_t *replay_size, int64_t *critic_updates,
+                       int64_t *actor_updates) {
+    if (!T) return NAV_E_INVAL;
+    if (replay_size) *replay_size = T->size;
+    if (critic_updates) *critic_updates = (int64_t)T->n_critic;
+    if (actor_updates) *actor_updates = (int64_t)T->n_actor;
+    return NAV_OK;
+}
+
+int nav_eval_begin(nav_trainer *T, int n_envs, void *stream) {
+    if (!T || n_envs <= 0) return NAV_E_INVAL;
+    if (n_envs > T->ev_cap) {
+        cudaError_t e = talloc(T, &T->ev_fin, n_envs);
+        if (e == cudaSuccess) e = talloc(T, &T->ev_succ, n_envs);
+        if (e == cudaSuccess) e = talloc(T, &T->ev_ret, n_envs);
+        if (e == cudaSuccess && !T->ev_out) e = talloc(T, &T->ev_out, 2);
+        if (e != cudaSuccess) return NAV_E_NOMEM;
+        T->ev_cap = n_envs;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(T->ev_fin, 0, n_envs, st);
+    cudaMemsetAsync(T->ev_succ, 0, n_envs, st);
+    cudaMemsetAsync(T->ev_ret, 0, n_envs * sizeof(double), st);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_eval_accumulate(nav_trainer *T, const float *reward_dev, const uint8_t *done_dev,
+                        int n_envs, void *stream) {
+    if (!T || !reward_dev || !done_dev || n_envs <= 0 || n_envs > T->ev_cap) return NAV_E_INVAL;
+    k_eval_acc<<<blocks(n_envs), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reward_dev, done_dev, n_envs, T->ev_fin, T->ev_succ, T->ev_ret);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_eval_result(nav_trainer *T, int n_envs, double *successes, double *return_sum,
+                    void *stream) {
+    if (!T || n_envs <= 0 || n_envs > T->ev_cap) return NAV_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_eval_reduce<<<1, 256, 0, st>>>(T->ev_succ, T->ev_ret, n_envs, T->ev_out);
+    double out[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(out, T->ev_out, sizeof(out), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return NAV_E_CUDA;
+    if (successes) *successes = out[0];
+    if (return_sum) *return_sum = out[1];
+    return NAV_OK;
+}
+
+} // extern "C"

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "nav_internal.h"
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kThreads)
     gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
                  int ldb, int M, int N, int K, int BN, const float *__restrict__ bias, int act,
                  float *C32, int ldc32, __nv_bfloat16 *C16, int ldc16, __nv_bfloat16 *C16T,
-                 int ldct, int *status) {
+                 int ldct, int *status, int k_split) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ unsigned tmem_base;
@@ -117,8 +118,12 @@ __global__ void __launch_bounds__(kThreads)
     const unsigned idesc = instr_desc(kTileM, BN);
     unsigned parity = 0;
     bool ok = true;
-    const int n_chunks = (K + kChunkK - 1) / kChunkK;
-    for (int kc = 0; kc < n_chunks; ++kc) {
+    // split-K: CTA z covers chunks [z * k_split, (z + 1) * k_split) and adds
+    // its partial product into C32 (zeroed by the caller)
+    const int n_chunks_all = (K + kChunkK - 1) / kChunkK;
+    const int kc0 = k_split > 0 ? blockIdx.z * k_split : 0;
+    const int kc1 = k_split > 0 ? min(n_chunks_all, kc0 + k_split) : n_chunks_all;
+    for (int kc = kc0; kc < kc1; ++kc) {
         load_tile(sA, A, lda, m0, kTileM, M, kc * kChunkK, K);
         load_tile(sB, B, ldb, n0, BN, N, kc * kChunkK, K);
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(kThreads)
             for (int k16 = 0; k16 < kChunkK / 16; ++k16) {
                 const unsigned long long da = smem_desc(sA + 32u * k16);
                 const unsigned long long db = smem_desc(sB + 32u * k16);
-                const unsigned accum = (kc > 0 || k16 > 0) ? 1u : 0u;
+                const unsigned accum = (kc > kc0 || k16 > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -166,6 +171,10 @@ __global__ void __launch_bounds__(kThreads)
             const int col = n0 + cb + j;
             if (col >= N) break;
             float v = __uint_as_float(r[j]);
+            if (k_split > 0) {
+                atomicAdd(&C32[(size_t)row * ldc32 + col], v);
+                continue;
+            }
             if (bias) v += bias[col];
             if (act == 1) v = v > 0.0f ? v : kLeakySlope * v;
             if (C32) C32[(size_t)row * ldc32 + col] = v;
@@ -195,7 +204,32 @@ int launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int 
     gemm_bf16_tc<<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(
         static_cast<const __nv_bfloat16 *>(A), lda, static_cast<const __nv_bfloat16 *>(B), ldb, M,
         N, K, BN, bias, act, C32, ldc32, static_cast<__nv_bfloat16 *>(C16), ldc16,
-        static_cast<__nv_bfloat16 *>(C16T), ldct, status);
+        static_cast<__nv_bfloat16 *>(C16T), ldct, status, 0);
+    return (int)cudaGetLastError();
+}
+
+int launch_gemm_bf16_splitk(const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                            float *C32, int ldc32, int *status, void *stream) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    const int BN = N >= 256 ? 256 : (N + 15) / 16 * 16;
+    const size_t smem = 1024 + (size_t)kTileM * 128 + (size_t)BN * 128;
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemset2DAsync(C32, (size_t)ldc32 * 4, 0, (size_t)N * 4, (size_t)M, s);
+    if (e != cudaSuccess) return (int)e;
+    const int n_chunks = (K + kChunkK - 1) / kChunkK;
+    const int tiles = ((M + kTileM - 1) / kTileM) * ((N + BN - 1) / BN);
+    // aim for >= 148 CTAs, at least 2 chunks each
+    int splits = (148 + tiles - 1) / tiles;
+    splits = std::max(1, std::min(splits, n_chunks / 2));
+    const int per = (n_chunks + splits - 1) / splits;
+    splits = (n_chunks + per - 1) / per;
+    dim3 grid((M + kTileM - 1) / kTileM, (N + BN - 1) / BN, splits);
+    gemm_bf16_tc<<<grid, kThreads, smem, s>>>(
+        static_cast<const __nv_bfloat16 *>(A), lda, static_cast<const __nv_bfloat16 *>(B), ldb, M,
+        N, K, BN, nullptr, 0, C32, ldc32, nullptr, 0, nullptr, 0, status, per);
     return (int)cudaGetLastError();
 }
 

@@ -264,6 +264,10 @@ struct nav_policy {
     int *status = nullptr;
 };
 
+namespace flashnav {
+Mlp *policy_actor(nav_policy *p) { return p ? &p->actor : nullptr; }
+} // namespace flashnav
+
 extern "C" {
 
 int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out) {

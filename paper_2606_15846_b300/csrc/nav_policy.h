@@ -41,3 +41,10 @@ int launch_actor_head(const float *out4, int n, int mode, unsigned long long see
                       float *act, float *logp, float *eps, void *stream);
 
 } // namespace flashnav
+
+struct nav_policy;
+namespace flashnav {
+// The actor network inside a policy handle (weights shared with a trainer
+// through nav_trainer_sync_policy).
+Mlp *policy_actor(nav_policy *p);
+} // namespace flashnav

@@ -27,8 +27,21 @@ EXPORTS = [
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
     "nav_policy_create", "nav_policy_free", "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_rollout",
+    "nav_train_default_cfg", "nav_trainer_create", "nav_trainer_free", "nav_trainer_last_error",
+    "nav_train_insert", "nav_train_update", "nav_trainer_sync_policy", "nav_trainer_io",
+    "nav_trainer_counts", "nav_eval_begin", "nav_eval_accumulate", "nav_eval_result",
     "nav_last_error", "nav_free",
 ]
+
+
+class nav_train_cfg(C.Structure):
+    _fields_ = [("obs_dim", C.c_int), ("hidden", C.c_int), ("batch", C.c_int),
+                ("replay_capacity", C.c_longlong), ("lr_actor", C.c_float),
+                ("lr_critic", C.c_float), ("lr_alpha", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("gamma", C.c_float), ("tau", C.c_float),
+                ("tau_b", C.c_float), ("reward_scale", C.c_float), ("huber_delta", C.c_float),
+                ("alpha_init", C.c_float), ("target_entropy", C.c_float),
+                ("policy_freq", C.c_int), ("seed", C.c_uint64)]
 
 
 class NavError(RuntimeError):
@@ -103,6 +116,18 @@ def load():
         "nav_policy_act": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
         "nav_policy_act_fp32": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
         "nav_rollout": (I, [P, P, I, I, U64, C.c_uint32, P, P, P, P, I]),
+        "nav_train_default_cfg": (None, [P]),
+        "nav_trainer_create": (I, [P, P]),
+        "nav_trainer_free": (None, [P]),
+        "nav_trainer_last_error": (C.c_char_p, [P]),
+        "nav_train_insert": (I, [P, P, P, P, P, P, P, I, P]),
+        "nav_train_update": (I, [P, I, P]),
+        "nav_trainer_sync_policy": (I, [P, P, P]),
+        "nav_trainer_io": (I, [P, I, I, P]),
+        "nav_trainer_counts": (I, [P, P, P, P]),
+        "nav_eval_begin": (I, [P, I, P]),
+        "nav_eval_accumulate": (I, [P, P, P, I, P]),
+        "nav_eval_result": (I, [P, I, P, P, P]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }

@@ -1,0 +1,174 @@
+"""GPU parity of the FastDSAC learner (Sec. 2.3; Table 4) with the FP64
+oracle (oracle/mlp_oracle.py): one critic + actor update on a known replay,
+with the batch indices and noise the GPU drew read back and replayed in FP64.
+BF16 tensor-core operands make the gradients approximate; every layer's
+relative L2 error against FP64 is printed and bounded."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+OD = 364
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_15846_b300 import flashnav
+    return flashnav, torch
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _bf16(x):
+    import torch
+    return torch.tensor(np.asarray(x, np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _unpack(w, sizes):
+    params, off = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = w[off:off + a * b].reshape(b, a).astype(np.float64)
+        off += a * b
+        params.append([W, w[off:off + b].astype(np.float64)])
+        off += b
+    return params
+
+
+def _io(lib, T, what, n, dtype=np.float32):
+    buf = np.zeros(n, dtype)
+    assert lib.nav_trainer_io(T, what, 0, buf.ctypes.data_as(C.c_void_p)) == 0
+    return buf
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_one_update_matches_fp64(env):
+    from oracle import mlp_oracle as M
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.batch, cfg.replay_capacity, cfg.policy_freq, cfg.seed = 256, 2048, 1, 7
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+    na = lib.nav_policy_num_params  # noqa: F841 (sizes below)
+    sa, sc = [OD, 256, 256, 4], [OD + 2, 256, 256, 2]
+    n_a = sum(a * b + b for a, b in zip(sa[:-1], sa[1:]))
+    n_c = sum(a * b + b for a, b in zip(sc[:-1], sc[1:]))
+    actor0 = _unpack(_io(lib, T, 0, n_a), sa)
+    q0 = [_unpack(_io(lib, T, 1 + i, n_c), sc) for i in range(2)]
+    qt0 = [_unpack(_io(lib, T, 3 + i, n_c), sc) for i in range(2)]
+    scal0 = _io(lib, T, 24, 16)
+    rng = np.random.default_rng(3)
+    N = 700
+    obs = rng.uniform(0, 6, (N, OD)).astype(np.float32)
+    nxt = np.clip(obs + rng.normal(0, 0.05, (N, OD)), 0, 6).astype(np.float32)
+    act = rng.uniform(-0.99, 0.99, (N, 2)).astype(np.float32)
+    rew = rng.normal(0, 1, N).astype(np.float32)
+    done = rng.choice([0, 0, 0, 1, 2, 5, 9], N).astype(np.uint8)
+    dev = [torch.from_numpy(a).cuda() for a in (obs, act, rew, done, nxt)]
+    assert lib.nav_train_insert(T, *[_p(d) for d in dev], None, N, None) == 0
+    assert lib.nav_train_update(T, 1, None) == 0
+    torch.cuda.synchronize()
+    B = 256
+    idx = _io(lib, T, 20, B, np.int32)
+    eps_new = _io(lib, T, 21, 2 * B).reshape(B, 2).astype(np.float64)
+    eps_next = _io(lib, T, 22, 2 * B).reshape(B, 2).astype(np.float64)
+    zn = _io(lib, T, 23, B).astype(np.float64)
+    y_gpu, ym_gpu = _io(lib, T, 25, B), _io(lib, T, 26, B)
+    assert (idx >= 0).all() and (idx < N).all()
+    ob, nb = _bf16(obs[idx]), _bf16(nxt[idx])
+    ab = _bf16(act[idx])
+    rb, tb = rew[idx].astype(np.float64), (done[idx] & 1).astype(np.float64)
+    alpha = float(np.exp(scal0[0]))
+    sbar = float(scal0[1])
+    # critic targets
+    out_n, _ = M.mlp_forward(actor0, nb)
+    a_next, logp_next, _ = M.actor_head(out_n, eps_next)
+    xnc = np.concatenate([nb, _bf16(a_next)], axis=1)
+    tq = [M.mlp_forward(qt0[i], xnc)[0] for i in range(2)]
+    y, ym = M.critic_targets(rb, tb, tq[0], tq[1], logp_next, alpha, zn, cfg.gamma,
+                             cfg.reward_scale)
+    print(f"targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
+    assert _rel(y_gpu, y) < 2e-2 and _rel(ym_gpu, ym) < 2e-2
+    # critic gradients
+    xc = np.concatenate([ob, ab], axis=1)
+    for i in range(2):
+        q, cache = M.mlp_forward(q0[i], xc)
+        _, dq = M.critic_loss(q, y, ym, sbar, cfg.huber_delta)
+        grads, _ = M.mlp_backward(q0[i], cache, dq)
+        g_gpu = _unpack(_io(lib, T, 11 + i, n_c), sc)
+        for li, ((dW, db), (gW, gb)) in enumerate(zip(grads, g_gpu)):
+            eW, eb = _rel(gW, dW), _rel(gb, db)
+            print(f"critic {i + 1} layer {li + 1} grad rel err W {eW:.2e} b {eb:.2e}")
+            assert eW < 6e-2 and eb < 6e-2
+    # Adam's first step on the GPU's own gradients
+    q1_post = _unpack(_io(lib, T, 1, n_c), sc)
+    g1 = _unpack(_io(lib, T, 11, n_c), sc)
+    for (W0, b0), (g, gb), (W1, b1) in zip(q0[0], g1, q1_post):
+        Wr, _, _ = M.adam_step(W0, g, 0 * g, 0 * g, 1, cfg.lr_critic, cfg.beta1, cfg.beta2)
+        assert np.abs(W1 - Wr).max() < 1e-6
+    # actor gradients (critics after their Adam step, as the GPU uses them)
+    q_post = [_unpack(_io(lib, T, 1 + i, n_c), sc) for i in range(2)]
+    out_a, cache_a = M.mlp_forward(actor0, ob)
+    a_new, logp, _ = M.actor_head(out_a, eps_new)
+    xa = np.concatenate([ob, _bf16(a_new)], axis=1)
+    qa, caches = [], []
+    for i in range(2):
+        o, c = M.mlp_forward(q_post[i], xa)
+        qa.append(o)
+        caches.append(c)
+    _, dlogp, dq1, dq2 = M.actor_loss_grads(logp, qa[0][:, 0], qa[1][:, 0], alpha)
+    da = np.zeros((B, 2))
+    for i, dqi in enumerate((dq1, dq2)):
+        _, dX = M.mlp_backward(q_post[i], caches[i], np.stack([dqi, 0 * dqi], axis=1))
+        da += dX[:, OD:OD + 2]
+    dout = M.actor_head_grad(out_a, eps_new, da, dlogp)
+    grads_a, _ = M.mlp_backward(actor0, cache_a, dout)
+    g_gpu = _unpack(_io(lib, T, 10, n_a), sa)
+    for li, ((dW, db), (gW, gb)) in enumerate(zip(grads_a, g_gpu)):
+        eW, eb = _rel(gW, dW), _rel(gb, db)
+        print(f"actor layer {li + 1} grad rel err W {eW:.2e} b {eb:.2e}")
+        assert eW < 1e-1 and eb < 1e-1
+    lib.nav_trainer_free(T)
+
+
+def test_eval_reduction_fp64(env):
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.batch, cfg.replay_capacity = 128, 256
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+    E, S = 1000, 40
+    rng = np.random.default_rng(5)
+    rew = rng.normal(0, 3, (S, E)).astype(np.float32)
+    done = rng.choice([0] * 30 + [1 | 4, 1 | 8, 2, 1 | 4 | 8], (S, E)).astype(np.uint8)
+    assert lib.nav_eval_begin(T, E, None) == 0
+    for t in range(S):
+        r, d = torch.from_numpy(rew[t]).cuda(), torch.from_numpy(done[t]).cuda()
+        assert lib.nav_eval_accumulate(T, _p(r), _p(d), E, None) == 0
+    succ, ret = C.c_double(), C.c_double()
+    assert lib.nav_eval_result(T, E, C.byref(succ), C.byref(ret), None) == 0
+    want_s, want_r = 0.0, 0.0
+    for e in range(E):
+        for t in range(S):
+            want_r += float(rew[t, e])
+            if done[t, e] & 3:
+                want_s += 1.0 if (done[t, e] & 4 and not done[t, e] & 8) else 0.0
+                break
+    assert succ.value == want_s
+    assert abs(ret.value - want_r) <= 1e-9 * max(1.0, abs(want_r))
+    lib.nav_trainer_free(T)
