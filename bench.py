@@ -134,6 +134,64 @@ def cpu_baseline(wl, seconds: float = 15.0):
                       f"envs, {cores} threads), {el:.1f} s"}
 
 
+def policy_rollout(steps: int = 20):
+    """Rollout with the policy in the loop on 65536 envs over 16 256x256 maps,
+    360 beams: the BF16 tensor-core policy against the plain FP32 SIMT policy
+    (same simulator kernel, same random-init weights)."""
+    import ctypes as C
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    from paper_2606_15846_b300 import workloads as W
+    wl = W.config_throughput(n_envs=65536)
+    sim = flashnav.NavSim.from_workload(wl)
+    lib = flashnav.load()
+    pol = C.c_void_p()
+    assert lib.nav_policy_create(364, 256, wl.n_envs, 7, C.byref(pol)) == 0
+    E = wl.n_envs
+    obs = sim.new_obs()
+    act = torch.empty(E, 2, device="cuda")
+    rew = torch.empty(E, device="cuda")
+    done = torch.empty(E, dtype=torch.uint8, device="cuda")
+    P = lambda t: C.c_void_p(t.data_ptr())
+    out = {}
+    for name, fp32 in (("bf16_tensor_core_policy", 0), ("fp32_simt_policy", 1)):
+        sim.reset(SEED, obs)
+        sim._bind_stream()
+        assert lib.nav_rollout(sim._h, pol, 3, 1, 5, 0, P(obs), P(act), P(rew), P(done), fp32) == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        assert lib.nav_rollout(sim._h, pol, steps, 1, 5, 3, P(obs), P(act), P(rew), P(done),
+                               fp32) == 0
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"env_steps_per_s": E / (ms / 1e3), "ms_per_step": ms}
+    out["speedup_bf16_vs_fp32"] = (out["bf16_tensor_core_policy"]["env_steps_per_s"] /
+                                   out["fp32_simt_policy"]["env_steps_per_s"])
+    out["config"] = "65536 envs, 16 maps 256x256, 360 beams, actor 364-256-256-4, sampled actions"
+    lib.nav_policy_free(pol)
+    return out
+
+
+def training_run(seconds: float):
+    """FastDSAC from scratch for a bounded wall-clock budget: time at which the
+    deterministic policy first reaches each success threshold on 1000 held-out
+    maps (evaluation time included)."""
+    from paper_2606_15846_b300 import train as TR
+    cfg = TR.TrainConfig(time_budget_s=seconds, threshold=1.0)
+    res = TR.train(cfg, log=lambda *a: None)
+    hist = res["history"]
+    reach = {}
+    for thr in (0.25, 0.40, 0.50, 1.00):
+        hit = [h["t"] for h in hist if h["success"] >= thr]
+        reach[f"{int(thr * 100)}%"] = hit[0] if hit else None
+    return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
+            "budget_s": seconds, "env_steps": res["env_steps"],
+            "config": "16384 envs on 64 training maps 256x256, 1000 held-out maps, disc robot, "
+                      "batch 4096, 4 updates per env step, eval every 1 s"}
+
+
 def _sub_workload(wl, n):
     """The first n envs of a workload (same maps, beams and robots)."""
     import dataclasses
@@ -326,6 +384,10 @@ def run_gpu(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
+        if world == 1 and args.extras:
+            line["policy_rollout"] = policy_rollout()
+            if args.train_seconds > 0:
+                line["training"] = training_run(args.train_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -339,6 +401,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="1: also time the policy-in-the-loop rollout and a training run")
+    ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells "
                          "(default: autotune)")

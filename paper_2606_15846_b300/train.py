@@ -1,0 +1,153 @@
+"""End-to-end FastDSAC training on the batched simulator (Sec. 2.3 and the
+time-to-threshold protocol of Sec. 3.2): a thin loop over the C ABI.  Every
+computation runs in the library's kernels; this module only orders the calls.
+
+Per environment step: policy actions (sampled, BF16 tensor cores) -> nav_step
+(with final observations) -> replay insert -> `utd` learner updates -> actor
+weights copied to the acting policy.  Every `eval_every_s` seconds of wall
+clock the deterministic policy runs one episode on each held-out map and the
+FP64 success count is read back; evaluation time is part of the clock.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import time
+
+import numpy as np
+
+from . import flashnav as F
+from . import workloads as W
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+@dataclasses.dataclass
+class TrainConfig:
+    robot: str = "disc"
+    n_envs: int = 16384
+    n_train_maps: int = 64
+    n_eval: int = 1000
+    map_size: int = 256
+    beams: int = 360
+    max_range: float = 6.0
+    batch: int = 4096
+    replay: int = 4 << 20
+    utd: int = 4
+    learning_starts: int = 8192
+    eval_every_s: float = 1.0
+    time_budget_s: float = 60.0
+    threshold: float = 1.0
+    seed: int = 0
+
+
+def make_workloads(cfg: TrainConfig):
+    robot = W.DISC if cfg.robot == "disc" else W.RECT
+    train_maps = [W.make_map(10_000 + cfg.seed * 1000 + m, cfg.map_size, cfg.map_size,
+                             float(np.random.default_rng(10_000 + m).uniform(0.10, 0.25)),
+                             corridors=True) for m in range(cfg.n_train_maps)]
+    eval_maps = [W.make_map(1_000_000 + m, cfg.map_size, cfg.map_size,
+                            float(np.random.default_rng(1_000_000 + m).uniform(0.10, 0.25)),
+                            corridors=True) for m in range(cfg.n_eval)]
+    e = np.arange(cfg.n_envs, dtype=np.int32)
+    train = W.Workload(name="train", maps=train_maps,
+                       env_map=(e % cfg.n_train_maps).astype(np.int32),
+                       env_beams=np.full(cfg.n_envs, cfg.beams, np.int32),
+                       env_robot=np.zeros(cfg.n_envs, np.int32), robots=[robot],
+                       max_range=cfg.max_range, params=W.Params())
+    ev = W.Workload(name="eval", maps=eval_maps,
+                    env_map=np.arange(cfg.n_eval, dtype=np.int32),
+                    env_beams=np.full(cfg.n_eval, cfg.beams, np.int32),
+                    env_robot=np.zeros(cfg.n_eval, np.int32), robots=[robot],
+                    max_range=cfg.max_range, params=W.Params())
+    return train, ev
+
+
+def train(cfg: TrainConfig, log=print):
+    import torch
+    lib = F.load()
+    train_wl, eval_wl = make_workloads(cfg)
+    sim = F.NavSim.from_workload(train_wl)
+    ev = F.NavSim.from_workload(eval_wl)
+    od = cfg.beams + 4
+    pol = C.c_void_p()
+    assert lib.nav_policy_create(od, 256, max(cfg.n_envs, cfg.n_eval), cfg.seed + 11,
+                                 C.byref(pol)) == 0
+    tc = F.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(tc))
+    tc.obs_dim, tc.batch, tc.replay_capacity, tc.seed = od, cfg.batch, cfg.replay, cfg.seed + 1
+    T = C.c_void_p()
+    rc = lib.nav_trainer_create(C.byref(tc), C.byref(T))
+    if rc:
+        raise F.NavError(rc, "nav_trainer_create failed")
+    dev = torch.device("cuda")
+    E = cfg.n_envs
+    obs = [sim.new_obs(), sim.new_obs()]
+    fin = sim.new_obs()
+    act = torch.empty(E, 2, device=dev)
+    rew = torch.empty(E, device=dev)
+    done = torch.empty(E, dtype=torch.uint8, device=dev)
+    ev_obs = ev.new_obs()
+    ev_act = torch.empty(cfg.n_eval, 2, device=dev)
+    ev_rew = torch.empty(cfg.n_eval, device=dev)
+    ev_done = torch.empty(cfg.n_eval, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    S = C.c_void_p(stream)
+    sim.reset(cfg.seed + 100, obs[0])
+    assert lib.nav_trainer_sync_policy(T, pol, S) == 0
+    history = []
+    cur = 0
+    step = 0
+    n_transitions = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    next_eval = 0.0
+    reached = None
+
+    def evaluate():
+        ev.reset(777, ev_obs)
+        assert lib.nav_eval_begin(T, cfg.n_eval, S) == 0
+        ev._bind_stream()
+        for t in range(200):
+            assert lib.nav_policy_act(pol, _p(ev_obs), od, cfg.n_eval, 0, 0, t, _p(ev_act), None,
+                                      None, S) == 0
+            ev.step(ev_act, ev_obs, ev_rew, ev_done)
+            assert lib.nav_eval_accumulate(T, _p(ev_rew), _p(ev_done), cfg.n_eval, S) == 0
+        succ, ret = C.c_double(), C.c_double()
+        assert lib.nav_eval_result(T, cfg.n_eval, C.byref(succ), C.byref(ret), S) == 0
+        return succ.value / cfg.n_eval, ret.value / cfg.n_eval
+
+    while True:
+        el = time.perf_counter() - t0
+        if el >= next_eval:
+            rate, mret = evaluate()
+            el = time.perf_counter() - t0
+            history.append({"t": el, "success": rate, "return": mret, "env_steps": step * E,
+                            "transitions": n_transitions})
+            log(f"t={el:6.2f}s env_steps={step * E:>10d} success={rate:.3f} return={mret:8.3f}")
+            if rate >= cfg.threshold and reached is None:
+                reached = el
+                break
+            next_eval = el + cfg.eval_every_s
+        if el >= cfg.time_budget_s:
+            break
+        nxt = 1 - cur
+        assert lib.nav_policy_act(pol, _p(obs[cur]), od, E, 1, cfg.seed, step, _p(act), None,
+                                  None, S) == 0
+        sim.step(act, obs[nxt], rew, done, final_obs=fin)
+        assert lib.nav_train_insert(T, _p(obs[cur]), _p(act), _p(rew), _p(done), _p(obs[nxt]),
+                                    _p(fin), E, S) == 0
+        n_transitions += E
+        if n_transitions >= max(cfg.learning_starts, cfg.batch):
+            rc = lib.nav_train_update(T, cfg.utd, S)
+            if rc:
+                raise F.NavError(rc, lib.nav_trainer_last_error(T).decode())
+            assert lib.nav_trainer_sync_policy(T, pol, S) == 0
+        cur = nxt
+        step += 1
+    torch.cuda.synchronize()
+    lib.nav_trainer_free(T)
+    lib.nav_policy_free(pol)
+    return {"time_to_threshold_s": reached, "history": history, "env_steps": step * E}
