@@ -35,12 +35,24 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// one thread per 4 columns of a row: FP32 -> BF16, zero beyond dim
 __global__ void obs_to_bf16(const float *__restrict__ obs, int n, int dim, long long stride,
                             __nv_bfloat16 *out, int ld) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n * ld) return;
-    const int r = (int)(i / ld), c = (int)(i - (long long)r * ld);
-    out[i] = __float2bfloat16_rn(c < dim ? obs[(long long)r * stride + c] : 0.0f);
+    const int groups = ld >> 2;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n || g >= groups) return;
+    const float *src = obs + (long long)r * stride;
+    const int c = 4 * g;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = c + k < dim ? src[c + k] : 0.0f;
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 pk;
+    pk.x = *reinterpret_cast<const unsigned *>(&a);
+    pk.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(out + (long long)r * ld + c) = pk;
 }
 
 // a = tanh(u + sigma eps) (or tanh(u)), logp per row.
@@ -237,8 +249,8 @@ int Mlp::forward_fp32(const float *x, long long ldx, int n, float *const *h32, f
 
 int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, void *out, int ld,
                        void *stream) {
-    const long long tot = (long long)n * ld;
-    obs_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+    const dim3 tb(32, 8), grid((ld / 4 + 31) / 32, (n + 7) / 8);
+    obs_to_bf16<<<grid, tb, 0, static_cast<cudaStream_t>(stream)>>>(
         obs, n, dim, stride, static_cast<__nv_bfloat16 *>(out), ld);
     return (int)cudaGetLastError();
 }
