@@ -174,6 +174,56 @@ def policy_rollout(steps: int = 20):
     return out
 
 
+def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
+    """Uneven batch in one persistent launch per step: 16384 envs over 64 maps
+    of 128..1024 cells, beams 180/360/720, disc and rectangle robots, 8 moving
+    discs per env; autotuned; steps captured in one CUDA graph; L2 flushed
+    between graph replays."""
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    from paper_2606_15846_b300 import workloads as W
+    wl = W.config_uneven()
+    sim = flashnav.NavSim.from_workload(wl)
+    E = wl.n_envs
+    s = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        obs = sim.reset(SEED)
+        tune_ms = sim.autotune(steps=3)
+        obs = sim.reset(SEED, obs)
+        acts = torch.empty(steps_per_graph, E, 2, device="cuda")
+        for t in range(steps_per_graph):
+            sim.uniform_actions(SEED, t, acts[t])
+        rew = torch.empty(E, device="cuda")
+        done = torch.empty(E, dtype=torch.uint8, device="cuda")
+        # work count on a graph captured with the visit counter on
+        sim.set_stats(True)
+        sim.graph_capture(acts, obs, rew, done)
+        sim.graph_launch()
+        visits, rays = sim.stats()
+        sim.set_stats(False)
+        sim.graph_capture(acts, obs, rew, done)
+        sim.graph_launch()
+        tot = 0.0
+        for r in range(replays):
+            flush.fill_(float(r))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            sim.graph_launch()
+            e1.record(s)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+    ms = tot / (replays * steps_per_graph)
+    return {"env_steps_per_s": E / (ms / 1e3), "ms_per_step": ms,
+            "beam_casts_per_step": rays / steps_per_graph,
+            "cell_visits_per_s": visits / steps_per_graph / (ms / 1e3),
+            "launch": dict(zip(("tile_envs", "block_threads", "smem_map_bytes", "max_regs",
+                                "byte_cells"), sim.get_launch())),
+            "autotune_ms_per_step": tune_ms,
+            "config": "16384 envs, 64 maps 128..1024 cells, beams 180/360/720, disc+rect, "
+                      "8 moving discs, graph of 20 steps, L2 flushed between replays"}
+
+
 def training_run(seconds: float):
     """FastDSAC from scratch for a bounded wall-clock budget: time at which the
     deterministic policy first reaches each success threshold on 1000 held-out
@@ -386,6 +436,7 @@ def run_gpu(args):
             line["cpu_baseline"] = cpu_baseline(wl)
         if world == 1 and args.extras:
             line["policy_rollout"] = policy_rollout()
+            line["uneven_batch"] = uneven_batch()
             if args.train_seconds > 0:
                 line["training"] = training_run(args.train_seconds)
         print(json.dumps(line), flush=True)

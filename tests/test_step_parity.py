@@ -341,3 +341,11 @@ def test_uniform_action_generator_range(mods):
     assert abs(a.mean()) < 0.05
     b = sim.uniform_actions(1, 1).cpu().numpy()
     assert not np.array_equal(a, b)
+
+
+def test_uneven_workload_full_size(mods):
+    """16384 envs over 64 maps of 128..1024 cells, beams 180/360/720, disc and
+    rectangle robots, 8 moving discs per env, autotuned launch: reset and two
+    steps compared in full (flags, hit cells, visits, observations, state)."""
+    wl = W.config_uneven()
+    run_parity(mods, wl, 2, seed=3, autotune=True, threads=16)
