@@ -238,8 +238,9 @@ def training_run(seconds: float):
         reach[f"{int(thr * 100)}%"] = hit[0] if hit else None
     return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
             "budget_s": seconds, "env_steps": res["env_steps"],
-            "config": "16384 envs on 64 training maps 256x256, 1000 held-out maps, disc robot, "
-                      "batch 4096, 4 updates per env step, eval every 1 s"}
+            "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
+            "config": "4096 envs on 64 training maps 256x256, 1000 held-out maps, disc robot, "
+                      "batch 4096, 8 updates per env step, eval every 1 s"}
 
 
 def _sub_workload(wl, n):

@@ -257,6 +257,20 @@ int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride,
                         uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
                         float *out_dev, void *stream);
 
+/* Per-feature input scale (host, obs_dim floats) multiplied into the
+ * observation before the network (NULL removes it).  Synchronous. */
+int nav_policy_set_input_scale(nav_policy *p, const float *scale_host);
+
+/* Reactive goal-seeking controller, the fallback policy without learning
+ * (no paper counterpart): among beams whose range and both neighbours' exceed
+ * 0.6 m, head for the one closest to the goal bearing; turn rate 2 x heading
+ * error, speed scaled by the heading error's cosine and the range straight
+ * ahead; rotate in place when no beam is clear.  obs rows as nav_step writes
+ * them (n_beams beams over fov_deg), actions_dev [n][2] normalised for a
+ * robot with speeds [0, v_max] and turn rates [-w_max, w_max]. */
+int nav_reactive_act(const float *obs_dev, int64_t obs_stride, int n, int n_beams, float fov_deg,
+                     float v_max, float w_max, float *actions_dev, void *stream);
+
 /* Rollout with the policy in the loop (Sec. 2.3 collector side): n_steps of
  * [policy actions from obs_dev -> nav_step], all on the handle's stream (so a
  * CUDA graph can capture it).  obs_dev must hold the current observation
@@ -306,6 +320,10 @@ int nav_train_insert(nav_trainer *t, const float *obs_dev, const float *act_dev,
 /* n_updates gradient steps on batches drawn uniformly from the replay (needs
  * at least one batch of transitions), asynchronous on `stream`. */
 int nav_train_update(nav_trainer *t, int n_updates, void *stream);
+
+/* Per-feature input scale applied to observations as they enter the replay
+ * (the same scale must be set on the acting policy).  Synchronous. */
+int nav_trainer_set_input_scale(nav_trainer *t, const float *scale_host);
 
 /* Copies the trainer's actor into a policy handle (actor-weight sync). */
 int nav_trainer_sync_policy(nav_trainer *t, nav_policy *p, void *stream);

@@ -47,16 +47,18 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
                                 const float *__restrict__ rew, const unsigned char *__restrict__ done,
                                 const float *__restrict__ obs_next,
                                 const float *__restrict__ final_obs, int E, int od, int ld,
-                                long long head, long long cap, bf16 *r_obs, bf16 *r_next,
-                                float *r_act, float *r_rew, float *r_term) {
+                                long long head, long long cap, const float *__restrict__ scale,
+                                bf16 *r_obs, bf16 *r_next, float *r_act, float *r_rew,
+                                float *r_term) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)E * ld) return;
     const int e = (int)(i / ld), c = (int)(i - (long long)e * ld);
     const long long slot = (head + e) % cap;
     const bool ended = (done[e] & 3) != 0;
     const float *nxt = (ended && final_obs) ? final_obs : obs_next;
-    r_obs[slot * ld + c] = __float2bfloat16_rn(c < od ? obs[(long long)e * od + c] : 0.0f);
-    r_next[slot * ld + c] = __float2bfloat16_rn(c < od ? nxt[(long long)e * od + c] : 0.0f);
+    const float sc = (scale && c < od) ? scale[c] : 1.0f;
+    r_obs[slot * ld + c] = __float2bfloat16_rn(c < od ? obs[(long long)e * od + c] * sc : 0.0f);
+    r_next[slot * ld + c] = __float2bfloat16_rn(c < od ? nxt[(long long)e * od + c] * sc : 0.0f);
     if (c == 0) {
         r_act[slot * 2] = act[2 * e];
         r_act[slot * 2 + 1] = act[2 * e + 1];
@@ -413,6 +415,7 @@ struct nav_trainer {
     unsigned char *ev_fin = nullptr, *ev_succ = nullptr;
     double *ev_ret = nullptr, *ev_out = nullptr;
     int ev_cap = 0;
+    float *scale = nullptr; // per-feature input scale applied when storing obs
 };
 
 namespace {
@@ -652,7 +655,7 @@ int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_replay_insert<<<blocks((long long)n_envs * T->ld), 256, 0, st>>>(
         obs_dev, act_dev, rew_dev, done_dev, next_obs_dev, final_obs_dev, n_envs, T->od, T->ld,
-        T->head, T->cap, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
+        T->head, T->cap, T->scale, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
     T->head = (T->head + n_envs) % T->cap;
     T->size = std::min(T->cap, T->size + n_envs);
     return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
@@ -760,6 +763,14 @@ int nav_trainer_io(nav_trainer *T, int what, int set, void *host) {
             return e == cudaSuccess ? NAV_OK : NAV_E_CUDA;
         }
     return NAV_E_INVAL;
+}
+
+int nav_trainer_set_input_scale(nav_trainer *T, const float *scale_host) {
+    if (!T || !scale_host) return NAV_E_INVAL;
+    cudaError_t e = cudaSuccess;
+    if (!T->scale) e = talloc(T, &T->scale, T->od);
+    if (e == cudaSuccess) e = cudaMemcpy(T->scale, scale_host, (size_t)T->od * 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? NAV_OK : NAV_E_CUDA;
 }
 
 int nav_trainer_sync_policy(nav_trainer *T, nav_policy *p, void *stream) {

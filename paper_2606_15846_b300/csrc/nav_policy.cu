@@ -37,7 +37,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 
 // one thread per 4 columns of a row: FP32 -> BF16, zero beyond dim
 __global__ void obs_to_bf16(const float *__restrict__ obs, int n, int dim, long long stride,
-                            __nv_bfloat16 *out, int ld) {
+                            const float *__restrict__ scale, __nv_bfloat16 *out, int ld) {
     const int groups = ld >> 2;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,7 +46,8 @@ __global__ void obs_to_bf16(const float *__restrict__ obs, int n, int dim, long 
     const int c = 4 * g;
     float v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = c + k < dim ? src[c + k] : 0.0f;
+    for (int k = 0; k < 4; ++k)
+        v[k] = c + k < dim ? (scale ? src[c + k] * scale[c + k] : src[c + k]) : 0.0f;
     const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
     const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
     uint2 pk;
@@ -108,6 +109,40 @@ __global__ void refresh_bf16(const float *__restrict__ W, int out, int in, __nv_
     const __nv_bfloat16 v = __float2bfloat16_rn(W[i]);
     W16[(size_t)o * ld_in + k] = v;
     WT16[(size_t)k * ld_out + o] = v;
+}
+
+// Reactive goal-seeking controller (the fallback policy without learning):
+// among beams whose range and both neighbours' ranges exceed `clear` metres,
+// head for the one closest in angle to the goal bearing; turn rate
+// proportional to that heading error, speed reduced while turning or when
+// the beam straight ahead is short.  Outputs normalised actions.
+__global__ void reactive_kernel(const float *__restrict__ obs, long long stride, int n, int K,
+                                float fov, float v_max, float w_max, float clear, float *act) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float *o = obs + (long long)r * stride;
+    const float dgoal = o[K], phi = o[K + 1];
+    const float step = fov / (float)K;
+    float best = -2.0f, target = 0.0f;
+    for (int k = 0; k < K; ++k) {
+        const int km = k == 0 ? K - 1 : k - 1, kp = k == K - 1 ? 0 : k + 1;
+        const float need = fminf(clear, dgoal + 0.1f);
+        if (o[k] < need || o[km] < need || o[kp] < need) continue;
+        const float a = -0.5f * fov + ((float)k + 0.5f) * step;
+        const float sc = cosf(a - phi);
+        if (sc > best) { best = sc; target = a; }
+    }
+    float w = 2.0f * target, v;
+    if (best < -1.5f) { // boxed in: rotate in place
+        w = w_max;
+        v = 0.0f;
+    } else {
+        const int kf = (int)(0.5f * (float)K - 0.5f); // beam nearest straight ahead (360 deg fan)
+        const float front = o[kf < 0 ? 0 : kf];
+        v = v_max * fmaxf(0.0f, cosf(target)) * fminf(1.0f, front / 1.0f);
+    }
+    act[2 * r] = fminf(fmaxf(2.0f * v / v_max - 1.0f, -1.0f), 1.0f);
+    act[2 * r + 1] = fminf(fmaxf(w / w_max, -1.0f), 1.0f);
 }
 
 } // namespace
@@ -247,11 +282,11 @@ int Mlp::forward_fp32(const float *x, long long ldx, int n, float *const *h32, f
     return (int)cudaGetLastError();
 }
 
-int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, void *out, int ld,
-                       void *stream) {
+int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, const float *scale,
+                       void *out, int ld, void *stream) {
     const dim3 tb(32, 8), grid((ld / 4 + 31) / 32, (n + 7) / 8);
     obs_to_bf16<<<grid, tb, 0, static_cast<cudaStream_t>(stream)>>>(
-        obs, n, dim, stride, static_cast<__nv_bfloat16 *>(out), ld);
+        obs, n, dim, stride, scale, static_cast<__nv_bfloat16 *>(out), ld);
     return (int)cudaGetLastError();
 }
 
@@ -274,6 +309,7 @@ struct nav_policy {
     void *x16 = nullptr, *h16[2] = {nullptr, nullptr};
     float *out32 = nullptr, *h32[2] = {nullptr, nullptr};
     int *status = nullptr;
+    float *scale = nullptr; // per-feature input scale (null: none)
 };
 
 namespace flashnav {
@@ -312,7 +348,8 @@ int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav
 void nav_policy_free(nav_policy *p) {
     if (!p) return;
     p->actor.release();
-    void *ps[] = {p->x16, p->h16[0], p->h16[1], p->h32[0], p->h32[1], p->out32, p->status};
+    void *ps[] = {p->x16, p->h16[0], p->h16[1], p->h32[0], p->h32[1], p->out32, p->status,
+                  p->scale};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete p;
@@ -339,7 +376,7 @@ int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int 
         (mode != 0 && mode != 1))
         return NAV_E_INVAL;
     const int ld0 = p->actor.layer[0].ld_in;
-    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->x16, ld0, stream);
+    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->scale, p->x16, ld0, stream);
     if (rc == 0) rc = p->actor.forward_tc(p->x16, n, p->h16, nullptr, p->out32, p->status, stream);
     if (rc == 0) rc = launch_actor_head(p->out32, n, mode, seed, step, actions_dev, logp_dev, nullptr, stream);
     if (rc == 0 && out_dev)
@@ -360,6 +397,31 @@ int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride,
         rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice,
                                   static_cast<cudaStream_t>(stream));
     return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_policy_set_input_scale(nav_policy *p, const float *scale_host) {
+    if (!p) return NAV_E_INVAL;
+    if (!scale_host) {
+        if (p->scale) cudaFree(p->scale);
+        p->scale = nullptr;
+        return NAV_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!p->scale) e = cudaMalloc(&p->scale, (size_t)p->obs_dim * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->scale, scale_host, (size_t)p->obs_dim * 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_reactive_act(const float *obs_dev, int64_t obs_stride, int n, int n_beams, float fov_deg,
+                     float v_max, float w_max, float *actions_dev, void *stream) {
+    if (!obs_dev || !actions_dev || n <= 0 || n_beams <= 0 || obs_stride < n_beams + 4 ||
+        !(v_max > 0.0f) || !(w_max > 0.0f))
+        return NAV_E_INVAL;
+    reactive_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        obs_dev, obs_stride, n, n_beams, fov_deg * 0.017453292519943295f, v_max, w_max, 0.6f,
+        actions_dev);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
 }
 
 int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t seed,

@@ -35,8 +35,8 @@ struct Mlp {
                      void *stream) const;
 };
 
-int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, void *out, int ld,
-                       void *stream);
+int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, const float *scale,
+                       void *out, int ld, void *stream);
 int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
                       float *act, float *logp, float *eps, void *stream);
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "nav_train_default_cfg", "nav_trainer_create", "nav_trainer_free", "nav_trainer_last_error",
     "nav_train_insert", "nav_train_update", "nav_trainer_sync_policy", "nav_trainer_io",
     "nav_trainer_counts", "nav_eval_begin", "nav_eval_accumulate", "nav_eval_result",
+    "nav_policy_set_input_scale", "nav_reactive_act", "nav_trainer_set_input_scale",
     "nav_last_error", "nav_free",
 ]
 
@@ -128,6 +129,9 @@ def load():
         "nav_eval_begin": (I, [P, I, P]),
         "nav_eval_accumulate": (I, [P, P, P, I, P]),
         "nav_eval_result": (I, [P, I, P, P, P]),
+        "nav_policy_set_input_scale": (I, [P, P]),
+        "nav_reactive_act": (I, [P, C.c_int64, I, I, F, F, F, P, P]),
+        "nav_trainer_set_input_scale": (I, [P, P]),
         "nav_last_error": (C.c_char_p, [P]),
         "nav_free": (None, [P]),
     }

@@ -27,7 +27,7 @@ def _p(t):
 @dataclasses.dataclass
 class TrainConfig:
     robot: str = "disc"
-    n_envs: int = 16384
+    n_envs: int = 4096
     n_train_maps: int = 64
     n_eval: int = 1000
     map_size: int = 256
@@ -35,12 +35,13 @@ class TrainConfig:
     max_range: float = 6.0
     batch: int = 4096
     replay: int = 4 << 20
-    utd: int = 4
+    utd: int = 8
     learning_starts: int = 8192
     eval_every_s: float = 1.0
     time_budget_s: float = 60.0
     threshold: float = 1.0
     seed: int = 0
+    scale_inputs: bool = True
 
 
 def make_workloads(cfg: TrainConfig):
@@ -65,6 +66,47 @@ def make_workloads(cfg: TrainConfig):
     return train, ev
 
 
+def input_scale(cfg: TrainConfig, robot) -> np.ndarray:
+    """Per-feature scale of the observation: ranges by r_max, goal distance by
+    8 m, bearing by pi, v and w by their bounds."""
+    sc = np.full(cfg.beams + 4, 1.0 / cfg.max_range, np.float32)
+    sc[cfg.beams:] = [1.0 / 8.0, 1.0 / np.pi, 1.0 / robot.v_max,
+                      1.0 / max(abs(robot.w_min), abs(robot.w_max))]
+    return sc
+
+
+def evaluate_reactive(cfg: TrainConfig, log=print):
+    """Success rate of the reactive controller (no learning) on the held-out
+    maps, same episodes and FP64 reduction as the policy evaluation."""
+    import torch
+    lib = F.load()
+    _, eval_wl = make_workloads(cfg)
+    robot = eval_wl.robots[0]
+    ev = F.NavSim.from_workload(eval_wl)
+    tc = F.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(tc))
+    tc.obs_dim, tc.batch, tc.replay_capacity = cfg.beams + 4, 128, 256
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(tc), C.byref(T)) == 0
+    S = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    obs = ev.new_obs()
+    act = torch.empty(cfg.n_eval, 2, device="cuda")
+    rew = torch.empty(cfg.n_eval, device="cuda")
+    done = torch.empty(cfg.n_eval, dtype=torch.uint8, device="cuda")
+    ev.reset(777, obs)
+    assert lib.nav_eval_begin(T, cfg.n_eval, S) == 0
+    for t in range(200):
+        assert lib.nav_reactive_act(_p(obs), cfg.beams + 4, cfg.n_eval, cfg.beams, 360.0,
+                                    robot.v_max, max(abs(robot.w_min), abs(robot.w_max)),
+                                    _p(act), S) == 0
+        ev.step(act, obs, rew, done)
+        assert lib.nav_eval_accumulate(T, _p(rew), _p(done), cfg.n_eval, S) == 0
+    succ, ret = C.c_double(), C.c_double()
+    assert lib.nav_eval_result(T, cfg.n_eval, C.byref(succ), C.byref(ret), S) == 0
+    lib.nav_trainer_free(T)
+    return succ.value / cfg.n_eval, ret.value / cfg.n_eval
+
+
 def train(cfg: TrainConfig, log=print):
     import torch
     lib = F.load()
@@ -82,6 +124,11 @@ def train(cfg: TrainConfig, log=print):
     rc = lib.nav_trainer_create(C.byref(tc), C.byref(T))
     if rc:
         raise F.NavError(rc, "nav_trainer_create failed")
+    if cfg.scale_inputs:
+        sc = input_scale(cfg, train_wl.robots[0])
+        ptr = sc.ctypes.data_as(C.c_void_p)
+        assert lib.nav_policy_set_input_scale(pol, ptr) == 0
+        assert lib.nav_trainer_set_input_scale(T, ptr) == 0
     dev = torch.device("cuda")
     E = cfg.n_envs
     obs = [sim.new_obs(), sim.new_obs()]
@@ -147,6 +194,12 @@ def train(cfg: TrainConfig, log=print):
             assert lib.nav_trainer_sync_policy(T, pol, S) == 0
         cur = nxt
         step += 1
+    if reached is None and (not history or history[-1]["t"] < time.perf_counter() - t0 - 1e-3):
+        rate, mret = evaluate()
+        el = time.perf_counter() - t0
+        history.append({"t": el, "success": rate, "return": mret, "env_steps": step * E,
+                        "transitions": n_transitions})
+        log(f"t={el:6.2f}s env_steps={step * E:>10d} success={rate:.3f} return={mret:8.3f}")
     torch.cuda.synchronize()
     lib.nav_trainer_free(T)
     lib.nav_policy_free(pol)
