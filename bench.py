@@ -456,6 +456,8 @@ def main():
     ap.add_argument("--extras", type=int, default=1,
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
+    ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "training"],
+                    help="run one of the extra measurements alone")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells "
                          "(default: autotune)")
@@ -464,6 +466,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
+              "training": lambda: training_run(args.train_seconds)}[args.only]
+        print(json.dumps({args.only: fn()}), flush=True)
     else:
         run_gpu(args)
 
