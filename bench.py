@@ -218,7 +218,7 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
             "beam_casts_per_step": rays / steps_per_graph,
             "cell_visits_per_s": visits / steps_per_graph / (ms / 1e3),
             "launch": dict(zip(("tile_envs", "block_threads", "smem_map_bytes", "max_regs",
-                                "byte_cells"), sim.get_launch())),
+                                "byte_cells", "split"), sim.get_launch())),
             "autotune_ms_per_step": tune_ms,
             "config": "16384 envs, 64 maps 128..1024 cells, beams 180/360/720, disc+rect, "
                       "8 moving discs, graph of 20 steps, L2 flushed between replays"}
@@ -415,18 +415,18 @@ def run_gpu(args):
                        "parallelism": f"env shards x{world}",
                        "launch": {"tile_envs": launch[0], "block_threads": launch[1],
                                   "smem_map_bytes": launch[2], "max_regs": launch[3],
-                                  "byte_cells": launch[4],
+                                  "byte_cells": launch[4], "split": launch[5],
                                   "chosen_by": "fixed" if args.launch else "autotuner"}},
             "beam_casts_per_s": world * rays / (step_ms / 1e3),
             "cell_visits_per_s": world * visits / (step_ms / 1e3),
             "visits_per_step": visits_per_launch,
             "timed_region_wall_s": wall,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if launch[5] == 1 else 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Gvisit/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
                                         f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
-                         "kernel": "step_kernel<false>"},
+                         "kernel": "step kernel (fused) or ray_kernel (split), per launch.split"},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": E * 2 * 4,
                     "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,
@@ -459,7 +459,7 @@ def main():
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "training"],
                     help="run one of the extra measurements alone")
     ap.add_argument("--launch", default="",
-                    help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells "
+                    help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
                          "(default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -186,17 +186,24 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
  *   byte_cells     1: stage maps that fit as one byte per cell (expanded from
  *                  the packed bits; cheaper lookups), 2: stage packed bits
  *                  (bulk TMA copy)
+ *   split          1: when every map and beam table fits in one CTA's shared
+ *                  memory (<= 200 KiB) and there are no moving discs, run the
+ *                  step as an env-phase kernel then a ray kernel whose CTAs
+ *                  keep every map resident and whose warps take 32-ray chunks
+ *                  from a queue (no per-tile barriers); 2: the fused tiled
+ *                  kernel.  nav_get_launch reports the path in use (1 or 2).
  * 0 keeps the current value.  Synchronises the handle's stream. */
 int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes,
-                   int max_regs, int byte_cells);
+                   int max_regs, int byte_cells, int split);
 int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads,
-                   int *smem_map_bytes, int *max_regs, int *byte_cells);
+                   int *smem_map_bytes, int *max_regs, int *byte_cells, int *split);
 
 /* Autotuner (no paper counterpart; it picks the launch shape for this
  * handle's mix of map sizes, beam counts and robots).  From a device copy of
  * the current state it times `steps` steps of each candidate with uniform
  * random actions: first tile_envs x block_threads x max_regs, then the
- * staging mode and shared-memory budget for the best shape.  It restores the
+ * staging mode and shared-memory budget for the best shape, then the split
+ * step when eligible.  It restores the
  * state and keeps the fastest candidate.  Synchronous.  best_ms (host, may be
  * NULL) receives the winner's mean step time. */
 int nav_autotune(nav_handle *h, int steps, float *best_ms);

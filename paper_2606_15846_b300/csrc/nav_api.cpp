@@ -157,6 +157,9 @@ struct nav_handle {
     int *d_perm = nullptr;
     int tiles_cap = 0;
     unsigned long long *d_stats = nullptr;
+    int2 *d_chunks = nullptr;
+    int chunks_cap = 0;
+    bool split_ok = false; // every map (and beam table) fits in one CTA's shared memory
     float *d_dbg_range = nullptr;
     int *d_dbg_hit = nullptr;
     unsigned *d_dbg_vis = nullptr;
@@ -232,6 +235,21 @@ int build_tiles(nav_handle *h) {
     h->a.tiles = h->d_tiles;
     h->a.perm = h->d_perm;
     h->a.n_tiles = (int)tiles.size();
+    // 32-ray chunks of every tile for the split step
+    std::vector<int2> chunks;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        const int n = tiles[t].env_count * h->env_k[perm[tiles[t].env_begin]];
+        for (int r = 0; r < n; r += 32) chunks.push_back(make_int2((int)t, r));
+    }
+    if ((int)chunks.size() > h->chunks_cap) {
+        e = h->arena.alloc(&h->d_chunks, chunks.size());
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(chunks)");
+        h->chunks_cap = (int)chunks.size();
+    }
+    e = cudaMemcpy(h->d_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(chunks)");
+    h->a.chunks = h->d_chunks;
+    h->a.n_chunks = (int)chunks.size();
     return NAV_OK;
 }
 
@@ -259,7 +277,8 @@ int set_map_modes(nav_handle *h) {
 }
 
 int launch(nav_handle *h) {
-    int rc = launch_step(h->a, h->cfg, h->stream);
+    int rc = (h->cfg.split && h->split_ok) ? launch_step_split(h->a, h->n_envs, h->stream)
+                                           : launch_step(h->a, h->cfg, h->stream);
     if (rc != 0) return cuda_fail(h, (cudaError_t)rc, "step kernel launch");
     return NAV_OK;
 }
@@ -382,6 +401,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
                     const long long b = (long long)(j + kPad) * pitch * 32 + (i + kPad);
                     base[b >> 5] |= 1u << (b & 31);
                 }
+        md.all_off = 0;
         h->maps.push_back(md);
     }
     // envs
@@ -408,10 +428,21 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         h->obs_off[e + 1] = h->obs_off[e] + k + 4;
         h->ray_off[e + 1] = h->ray_off[e] + k;
     }
+    // every map side by side in one shared-memory region (split step)
+    {
+        long long off = 0;
+        for (MapDev &m : h->maps) {
+            m.all_off = (int)std::min<long long>(off, 1 << 30);
+            off += m.n_words;
+        }
+        h->a.all_words = (int)std::min<long long>(off, 1 << 30);
+        h->a.n_maps_split = n_maps;
+    }
     // beam tables: alpha_k = -FOV/2 + (k + 1/2) FOV / K, cos and sin in binary64
     // rounded to binary32 (Eq. 4)
     std::vector<float> beam_c, beam_s;
     std::vector<int> tab_off;
+    h->a.n_beams_total = 0;
     const double fov = (double)P.fov_deg * (3.14159265358979323846 / 180.0);
     for (int K : tab_k) {
         tab_off.push_back((int)beam_c.size());
@@ -493,6 +524,9 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     NAV_UP(d_env_tab, h->env_tab);
     NAV_UP(d_env_robot, env_robot_v);
     NAV_UP(d_env_cs, env_cs);
+    h->a.n_beams_total = (int)beam_c.size();
+    h->split_ok = P.n_dyn == 0 &&
+                  (long long)h->a.all_words * 4 + (long long)beam_c.size() * 8 <= 200 * 1024;
     NAV_UP(d_bc, beam_c);
     NAV_UP(d_bs, beam_s);
     NAV_UP(d_obs_off, obs_off_ll);
@@ -531,12 +565,17 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.dyn, E * std::max(P.n_dyn, 1));
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.status, 1);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.tile_queue, 2);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.split_q, 4);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.ray_main, E);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.ray_fin, E);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.fin_list, E);
     if (ce == cudaSuccess) ce = h->arena.alloc(&h->d_stats, 2);
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMalloc(state)"));
     cudaMemset(A.step, 0, E * sizeof(int));
     cudaMemset(A.episode, 0, E * sizeof(unsigned));
     cudaMemset(A.status, 0, sizeof(int));
     cudaMemset(A.tile_queue, 0, 2 * sizeof(int));
+    cudaMemset(A.split_q, 0, 4 * sizeof(int));
     cudaMemset(h->d_stats, 0, 2 * sizeof(unsigned long long));
     A.stats = nullptr;
     A.p = ParamsDev{P.dt, P.goal_tol, P.c_progress, P.step_penalty, P.r_goal, P.r_coll,
@@ -783,13 +822,13 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays) {
 }
 
 int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes,
-                   int max_regs, int byte_cells) {
+                   int max_regs, int byte_cells, int split) {
     if (!h) return NAV_E_INVAL;
     if (tile_envs < 0 || tile_envs > kMaxTileEnvs || block_threads < 0 || block_threads > 512 ||
         (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
         smem_map_bytes < 0 || smem_map_bytes > 200 * 1024 ||
         !(max_regs == 0 || max_regs == 32 || max_regs == 40 || max_regs == 64) ||
-        byte_cells < 0 || byte_cells > 2)
+        byte_cells < 0 || byte_cells > 2 || split < 0 || split > 2)
         return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
@@ -797,6 +836,7 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
     if (max_regs) h->cfg.max_regs = max_regs;
     if (smem_map_bytes) h->smem_map_bytes = smem_map_bytes;
     if (byte_cells) h->byte_cells = byte_cells;
+    if (split) h->cfg.split = split == 1 ? 1 : 0;
     int rc = set_map_modes(h);
     if (rc != NAV_OK) return rc;
     if (tile_envs && tile_envs != h->cfg.tile_envs) {
@@ -807,13 +847,14 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
 }
 
 int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int *smem_map_bytes,
-                   int *max_regs, int *byte_cells) {
+                   int *max_regs, int *byte_cells, int *split) {
     if (!h) return NAV_E_INVAL;
     if (tile_envs) *tile_envs = h->cfg.tile_envs;
     if (block_threads) *block_threads = h->cfg.block_threads;
     if (smem_map_bytes) *smem_map_bytes = h->smem_map_bytes;
     if (max_regs) *max_regs = h->cfg.max_regs;
     if (byte_cells) *byte_cells = h->byte_cells;
+    if (split) *split = (h->cfg.split && h->split_ok) ? 1 : 2;
     return NAV_OK;
 }
 
@@ -875,7 +916,9 @@ float time_config(nav_handle *h, int steps, cudaEvent_t e0, cudaEvent_t e1) {
     for (int t = 0; t < steps + 2; ++t) {
         launch_uniform_actions(h->tune_act, h->n_envs, 0x7A11ull, (unsigned)t, h->stream);
         cudaEventRecord(e0, h->stream);
-        if (launch_step(A, h->cfg, h->stream) != 0) {
+        const int lrc = (h->cfg.split && h->split_ok) ? launch_step_split(A, h->n_envs, h->stream)
+                                                      : launch_step(A, h->cfg, h->stream);
+        if (lrc != 0) {
             cudaGetLastError();
             cudaStreamSynchronize(h->stream);
             return INFINITY;
@@ -933,6 +976,22 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
                 const float ms = time_config(h, steps, e0, e1);
                 if (ms < best) { best = ms; best_cap = cap; best_bytes = bc; }
             }
+    }
+    // pass 3: the split step (env kernel + all-maps-resident ray kernel)
+    if (rc == NAV_OK && h->split_ok) {
+        h->cfg = best_cfg;
+        h->smem_map_bytes = best_cap;
+        h->byte_cells = best_bytes;
+        if ((rc = set_map_modes(h)) == NAV_OK) rc = build_tiles(h);
+        if (rc == NAV_OK) {
+            h->cfg.split = 1;
+            const float ms = time_config(h, steps, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_cfg = h->cfg;
+            }
+            h->cfg.split = 0;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -24,6 +24,7 @@ struct MapDev {
     float res, inv_res;
     int byte_stride, n_bytes; // byte view; n_bytes is a multiple of 16
     int mode;                 // staging, one of MapMode
+    int all_off;              // word offset when every map is staged together (split step)
 };
 enum MapMode { kMapGlobal = 0, kMapSharedBits = 1, kMapSharedBytes = 2 };
 
@@ -89,6 +90,16 @@ struct StepArgs {
     int mode; // 0 step, 1 reset all
     int smem_region_bytes; // shared-memory region holding a staged map (0 = none)
     int max_k;
+    // split step (all maps resident in shared memory, no moving discs):
+    // env kernel -> per-env ray origins -> ray kernel over 32-ray chunks
+    float4 *ray_main, *ray_fin; // [n_envs] (xc, yc, sin, cos) of the obs scan / final scan
+    int *fin_list;              // [n_envs] envs whose final scan is pending
+    int *split_q;               // [0] next chunk [1] next final env [2] CTAs done [3] final count
+    const int2 *chunks;         // [n_chunks] (tile, first ray of the chunk in the tile)
+    int n_chunks;
+    int all_words;              // words of every map together
+    int n_maps_split;           // maps staged by the ray kernel
+    int n_beams_total;          // entries of the concatenated beam tables
 };
 
 enum StatusBits { kStatusNoSpawn = 1, kStatusCopyTimeout = 2, kStatusBadPose = 4 };
@@ -97,11 +108,16 @@ struct LaunchCfg {
     int tile_envs = 2;     // envs per CTA tile
     int block_threads = 256;
     int max_regs = 32;     // register cap per thread: 32, 40 or 64
+    int split = 0;         // 1: env kernel + all-maps-resident ray kernel when eligible
 };
 
 // Launches one step (or reset) of every tile on `stream`: persistent CTAs,
 // grid = SMs x resident CTAs per SM, capped by the tile count.
 int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
+
+// Split step: env phase for every env, then the ray kernel (all maps staged
+// in shared memory once per CTA, warps take 32-ray chunks from a queue).
+int launch_step_split(const StepArgs &a, int n_envs, void *stream);
 
 // Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step).
 int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,

@@ -867,6 +867,167 @@ __global__ void uniform_actions_kernel(float2 *out, int n_envs, unsigned long lo
     out[e] = make_float2(a, b);
 }
 
+// ---------------------------------------------------------------------------
+// Split step.  env_kernel: one thread per env runs the env phase (decode,
+// arc, footprint, reward, flags, reset) against the packed bits in L1/L2 and
+// records the ray origin of the obs scan (and of the final scan, appending
+// the env to the final list).  ray_kernel: persistent CTAs stage every map
+// and every beam table into shared memory once; each warp then takes 32-ray
+// chunks from a global queue and casts them with no CTA-wide barrier, then
+// takes the pending final scans env by env.  The last CTA resets the queues.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) env_kernel(const StepArgs A, int n_envs) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_envs) return;
+    const MapDev M = A.maps[A.env_map[e]];
+    const int K = A.tab_k[A.env_tab[e]];
+    EnvSlot slot;
+    slot.env = e;
+    slot.obs_off = A.obs_off[e];
+    slot.ray_off = A.ray_off[e];
+    env_phase<false>(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, K, 0, slot, nullptr,
+                     nullptr);
+    A.ray_main[e] = make_float4(slot.xc, slot.yc, slot.st, slot.ct);
+    if (slot.fin) {
+        A.ray_fin[e] = make_float4(slot.fxc, slot.fyc, slot.fst, slot.fct);
+        A.fin_list[atomicAdd(&A.split_q[3], 1)] = e;
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void cast_store(const StepArgs &A, const V &view, const MapDev &M,
+                                           float4 o, float2 ab, int e, int k, bool fin,
+                                           float rmax_c, unsigned &vis) {
+    const float dx = o.w * ab.x - o.z * ab.y;
+    const float dy = o.z * ab.x + o.w * ab.y;
+    int hit;
+    const float range = cast_ray<false>(view, M, o.x, o.y, dx, dy, rmax_c, A.max_range, nullptr,
+                                        0, hit, vis);
+    (fin ? A.final_obs : A.obs)[A.obs_off[e] + k] = fminf(range, A.max_range);
+    if (!fin && A.dbg_range) {
+        const long long ro = A.ray_off[e] + k;
+        A.dbg_range[ro] = range;
+        A.dbg_hit[ro] = hit;
+        A.dbg_vis[ro] = vis;
+    }
+}
+
+__device__ __forceinline__ void add_stats(const StepArgs &A, unsigned vis, int nr) {
+    if (!A.stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vis += __shfl_xor_sync(kFull, vis, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&A.stats[0], (unsigned long long)vis);
+        atomicAdd(&A.stats[1], (unsigned long long)nr);
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar;
+    uint32_t *sbits = reinterpret_cast<uint32_t *>(smem);
+    float2 *sbeam = reinterpret_cast<float2 *>(smem + (size_t)A.all_words * 4);
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        init_copy_barrier(&bar);
+        // every map in one transaction count: the copies of all maps complete
+        // phase 0 of the barrier
+        const unsigned b = smem_u32(&bar);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                     "r"((unsigned)A.all_words * 4u)
+                     : "memory");
+        for (int m = 0; m < A.n_maps_split; ++m) {
+            const MapDev M = A.maps[m];
+            const unsigned bytes = (unsigned)M.n_words * 4u;
+            for (unsigned off = 0; off < bytes; off += 32768u) {
+                const unsigned n = bytes - off < 32768u ? bytes - off : 32768u;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                    "%2, [%3];" ::"r"(smem_u32(sbits + M.all_off) + off),
+                    "l"((const char *)(A.bits + M.word_off) + off), "r"(n), "r"(b)
+                    : "memory");
+            }
+        }
+    }
+    for (int i = tid; i < A.n_beams_total; i += blockDim.x)
+        sbeam[i] = make_float2(A.beam_c[i], A.beam_s[i]);
+    __syncthreads();
+    const bool ok = wait_bitmap(&bar, 0);
+    const bool failed = __syncthreads_or(!ok) != 0;
+    if (failed) {
+        if (tid == 0) atomicOr(A.status, kStatusCopyTimeout);
+        if (!ok) wait_bitmap(&bar, 0);
+        __syncthreads();
+    }
+    // obs scans: each warp takes 32-ray chunks from the queue
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&A.split_q[0], 1);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= A.n_chunks) break;
+        const int2 ch = A.chunks[c];
+        const TileDev T = A.tiles[ch.x];
+        const MapDev M = A.maps[T.map];
+        const int K = A.tab_k[T.tab];
+        const int r = ch.y + lane;
+        unsigned vis = 0;
+        if (r < T.env_count * K) {
+            const int el = r / K, k = r - el * K;
+            const int e = A.perm[T.env_begin + el];
+            const float4 o = A.ray_main[e];
+            const float2 ab = sbeam[A.tab_off[T.tab] + k];
+            if (!failed)
+                cast_store(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M, o, ab, e, k, false,
+                           A.max_range * M.inv_res, vis);
+            else
+                cast_store(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, o, ab, e, k, false,
+                           A.max_range * M.inv_res, vis);
+        }
+        add_stats(A, vis, min(32, T.env_count * K - ch.y));
+    }
+    // final scans of the envs that finished this step
+    if (A.final_obs) {
+        const int n_fin = *(volatile int *)&A.split_q[3];
+        for (;;) {
+            int f = 0;
+            if (lane == 0) f = atomicAdd(&A.split_q[1], 1);
+            f = __shfl_sync(kFull, f, 0);
+            if (f >= n_fin) break;
+            const int e = A.fin_list[f];
+            const MapDev M = A.maps[A.env_map[e]];
+            const int K = A.tab_k[A.env_tab[e]];
+            const int toff = A.tab_off[A.env_tab[e]];
+            const float4 o = A.ray_fin[e];
+            for (int k0 = 0; k0 < K; k0 += 32) {
+                const int k = k0 + lane;
+                unsigned vis = 0;
+                if (k < K) {
+                    if (!failed)
+                        cast_store(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M, o,
+                                   sbeam[toff + k], e, k, true, A.max_range * M.inv_res, vis);
+                    else
+                        cast_store(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, o,
+                                   sbeam[toff + k], e, k, true, A.max_range * M.inv_res, vis);
+                }
+                add_stats(A, vis, min(32, K - k0));
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const int done = atomicAdd(&A.split_q[2], 1);
+        if (done == (int)gridDim.x - 1) {
+            A.split_q[0] = 0;
+            A.split_q[1] = 0;
+            A.split_q[2] = 0;
+            A.split_q[3] = 0;
+            __threadfence();
+        }
+    }
+}
+
 template <bool DYN> const void *pick_kernel(int max_regs) {
     if (max_regs <= 32) return (const void *)step_kernel<DYN, 4>;
     if (max_regs <= 40) return (const void *)step_kernel<DYN, 3>;
@@ -894,6 +1055,24 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     const int grid = std::min(a.n_tiles, n_sm * per_sm);
     void *args[] = {const_cast<StepArgs *>(&a)};
     err = cudaLaunchKernel(fn, dim3(grid), dim3(cfg.block_threads), args, smem, s);
+    if (err != cudaSuccess) return (int)err;
+    return (int)cudaGetLastError();
+}
+
+int launch_step_split(const StepArgs &a, int n_envs, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    env_kernel<<<(n_envs + 127) / 128, 128, 0, s>>>(a, n_envs);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return (int)err;
+    const size_t smem = (size_t)a.all_words * 4 + (size_t)a.n_beams_total * sizeof(float2);
+    err = cudaFuncSetAttribute(ray_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    int dev = 0, n_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return (int)err;
+    void *args[] = {const_cast<StepArgs *>(&a)};
+    err = cudaLaunchKernel((const void *)ray_kernel, dim3(n_sm), dim3(1024), args, smem, s);
     if (err != cudaSuccess) return (int)err;
     return (int)cudaGetLastError();
 }

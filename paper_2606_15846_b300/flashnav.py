@@ -101,8 +101,8 @@ def load():
         "nav_get_debug": (I, [P, P, P, P]),
         "nav_set_stats": (I, [P, I]),
         "nav_get_stats": (I, [P, P, P]),
-        "nav_set_launch": (I, [P, I, I, I, I, I]),
-        "nav_get_launch": (I, [P, P, P, P, P, P]),
+        "nav_set_launch": (I, [P, I, I, I, I, I, I]),
+        "nav_get_launch": (I, [P, P, P, P, P, P, P]),
         "nav_autotune": (I, [P, I, P]),
         "nav_uniform_actions": (I, [P, U64, C.c_uint32, P]),
         "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
@@ -309,13 +309,13 @@ class NavSim:
         return int(v.value), int(r.value)
 
     def set_launch(self, tile_envs=0, block_threads=0, smem_map_bytes=0, max_regs=0,
-                   byte_cells=0):
+                   byte_cells=0, split=0):
         self._bind_stream()
         self._check(load().nav_set_launch(self._h, tile_envs, block_threads, smem_map_bytes,
-                                          max_regs, byte_cells))
+                                          max_regs, byte_cells, split))
 
     def get_launch(self):
-        v = [C.c_int() for _ in range(5)]
+        v = [C.c_int() for _ in range(6)]
         self._check(load().nav_get_launch(self._h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
 

@@ -349,3 +349,22 @@ def test_uneven_workload_full_size(mods):
     steps compared in full (flags, hit cells, visits, observations, state)."""
     wl = W.config_uneven()
     run_parity(mods, wl, 2, seed=3, autotune=True, threads=16)
+
+
+@pytest.mark.parametrize("n_envs,steps", [(64, 300), (37, 80)])
+def test_split_step_small(mods, n_envs, steps):
+    """Env-phase kernel + all-maps-resident ray kernel (split step)."""
+    wl = W.config_small(n_envs=n_envs)
+    run_parity(mods, wl, steps, seed=9, launch=(0, 0, 0, 0, 0, 1))
+
+
+def test_split_step_throughput_maps(mods):
+    wl = W.config_throughput(n_envs=2048, n_maps=16)
+    sim, _, _ = run_parity(mods, wl, 4, seed=10, launch=(0, 0, 0, 0, 0, 1))
+    assert sim.get_launch()[5] == 1
+
+
+def test_split_step_mixed_beams_and_robots(mods):
+    wl = _mixed()
+    wl.maps = [m[:96, :96].copy() for m in wl.maps]
+    run_parity(mods, wl, 60, seed=15, launch=(0, 0, 0, 0, 0, 1))
