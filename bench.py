@@ -224,6 +224,81 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
                       "8 moving discs, graph of 20 steps, L2 flushed between replays"}
 
 
+def paper_sensing(steps: int = 200):
+    """The paper's sensing (Sec. 2.2.2, Eq. 6, Table 7) on its TurtleBot2
+    setting: one shared 10 x 10 m map, 1080 beams over 270 deg to 20 m,
+    30 sector minima.  The 0.03 m fixed-step march against the exact
+    traversal on the same trajectories (uniform actions do not depend on the
+    observation): env-steps/s at 1024 envs (the paper's count) and 16384
+    envs, and the march's range error against the exact range per beam."""
+    import dataclasses
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    from paper_2606_15846_b300 import workloads as W
+    out = {}
+    s = torch.cuda.Stream()
+    for n_envs in (1024, 16384):
+        wl = W.config_paper("turtlebot2", n_envs=n_envs)
+        for name, sensor in (("march_0.03m", 1), ("exact_traversal", 0)):
+            w2 = dataclasses.replace(wl, params=dataclasses.replace(wl.params, sensor=sensor))
+            sim = flashnav.NavSim.from_workload(w2)
+            E = w2.n_envs
+            with torch.cuda.stream(s):
+                obs = sim.reset(SEED)
+                sim.autotune(steps=5)
+                obs = sim.reset(SEED, obs)
+                acts = torch.empty(steps, E, 2, device="cuda")
+                for t in range(steps):
+                    sim.uniform_actions(SEED, t, acts[t])
+                rew = torch.empty(E, device="cuda")
+                done = torch.empty(E, dtype=torch.uint8, device="cuda")
+                for t in range(5):
+                    sim.step(acts[t], obs, rew, done)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for t in range(steps):
+                    sim.step(acts[t], obs, rew, done)
+                e1.record(s)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                sim.set_stats(True)
+                for t in range(20):
+                    sim.step(acts[t], obs, rew, done)
+                visits, rays = sim.stats()
+                sim.set_stats(False)
+            out[f"{name}_{n_envs}env"] = {
+                "env_steps_per_s": E / (ms / 1e3), "ms_per_step": ms,
+                "samples_or_visits_per_ray": visits / max(rays, 1),
+                "launch": sim.get_launch()}
+            sim.close()
+    # range error of the march against the exact traversal, same poses
+    wl = W.config_paper("turtlebot2", n_envs=1024)
+    sims = []
+    for sensor in (1, 0):
+        w2 = dataclasses.replace(wl, params=dataclasses.replace(wl.params, sensor=sensor))
+        sims.append(flashnav.NavSim.from_workload(w2))
+    diffs = []
+    acts = W.uniform_actions(SEED + 1, 40, wl.n_envs)
+    for sm in sims:
+        sm.set_debug(True)
+        sm.reset(SEED)
+    for t in range(40):
+        a = torch.from_numpy(acts[t]).cuda()
+        rs = []
+        for sm in sims:
+            sm.step(a)
+            rs.append(sm.debug()[0])
+        diffs.append(rs[0] - rs[1])
+    d = np.concatenate(diffs).astype(np.float64)
+    out["march_minus_exact_range_m"] = {
+        "rays": int(d.size), "mean": float(d.mean()), "p50": float(np.percentile(d, 50)),
+        "p99": float(np.percentile(d, 99)), "max": float(d.max()), "min": float(d.min()),
+        "frac_over_one_step": float(np.mean(d > 0.03 + 1e-6))}
+    out["config"] = ("TurtleBot2 preset: one 200x200 map (0.05 m cells), 1080 beams, 270 deg, "
+                     "20 m, 30 sectors, uniform actions; autotuned launch per handle")
+    return out
+
+
 def training_run(seconds: float):
     """FastDSAC from scratch for a bounded wall-clock budget: time at which the
     deterministic policy first reaches each success threshold on 1000 held-out
@@ -438,6 +513,7 @@ def run_gpu(args):
         if world == 1 and args.extras:
             line["policy_rollout"] = policy_rollout()
             line["uneven_batch"] = uneven_batch()
+            line["paper_sensing"] = paper_sensing()
             if args.train_seconds > 0:
                 line["training"] = training_run(args.train_seconds)
         print(json.dumps(line), flush=True)
@@ -456,7 +532,7 @@ def main():
     ap.add_argument("--extras", type=int, default=1,
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
-    ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "training"],
+    ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "paper_sensing", "training"],
                     help="run one of the extra measurements alone")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
@@ -468,6 +544,7 @@ def main():
         run_reference(args)
     elif args.only:
         fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
+              "paper_sensing": paper_sensing,
               "training": lambda: training_run(args.train_seconds)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
     else:

@@ -65,7 +65,15 @@ typedef struct {
  * fov_deg: beam fan, beam k at alpha_k = -fov/2 + (k + 1/2) fov / K (Eq. 4).
  * Goals are drawn with distance in [goal_dmin, goal_dmax] m when possible.
  * n_dyn moving discs per env (radius dyn_radius, speed <= dyn_speed_max,
- * spawned >= dyn_min_sep from the robot) are stamped into a per-env layer. */
+ * spawned >= dyn_min_sep from the robot) are stamped into a per-env layer.
+ * sensor 0: exact grid traversal (range = entry distance of the first
+ * blocked cell).  sensor 1: the fixed-step march of Sec. 2.2.2 (samples at
+ * s * march_step metres, s = 0, 1, ...; range = distance of the first sample
+ * in a blocked or off-map cell, r_max if none within r_max); needs
+ * march_step > 0 and max_range / march_step <= 2^22.
+ * n_sectors 0: the observation holds every beam's clipped range.
+ * n_sectors m > 0: Eq. 6, the observation holds m sector minima, sector q
+ * covering beams [q K/m, (q+1) K/m); every env's K must be a multiple of m. */
 typedef struct {
     float dt, goal_tol, c_progress, step_penalty, r_goal, r_coll;
     int horizon;
@@ -73,10 +81,14 @@ typedef struct {
     int n_dyn;
     float dyn_radius, dyn_speed_max, dyn_min_sep;
     int reward_mode;
+    int sensor;
+    float march_step;
+    int n_sectors;
 } nav_params;
 
 /* Fills the Table 7 defaults: dt 0.1 s, goal 0.2 m, c1 = 2, penalty 0.01,
- * +10 / -10, horizon 200, goals 2-8 m, 360 deg, no moving discs. */
+ * +10 / -10, horizon 200, goals 2-8 m, 360 deg, no moving discs, exact
+ * traversal (march_step 0.03 m for sensor 1), raw beams (no sectors). */
 void nav_default_params(nav_params *p);
 
 /* Creates a simulator (Sec. 2.2.1 batched state).  All envs use n_beams beams
@@ -98,9 +110,11 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
 int nav_set_stream(nav_handle *h, void *cuda_stream);
 
 /* Observation layout: env e's row starts at offsets[e] and holds
- * [K_e clipped ranges, goal distance, goal bearing, v, w] (Eq. 1 with the raw
- * K_e-beam scan).  offsets has n_envs + 1 entries (host); offsets[n_envs] is
- * the total float count.  With one beam count K, offsets[e] = e (K + 4). */
+ * [D_e range features, goal distance, goal bearing, v, w] (Eq. 1), where
+ * the range features are the K_e clipped ranges (D_e = K_e) or, with
+ * n_sectors = m, the m sector minima of Eq. 6 (D_e = m).  offsets has
+ * n_envs + 1 entries (host); offsets[n_envs] is the total float count.
+ * With one beam count K and no sectors, offsets[e] = e (K + 4). */
 int nav_obs_offsets(const nav_handle *h, int64_t *offsets_host);
 int nav_num_envs(const nav_handle *h);
 int64_t nav_obs_size(const nav_handle *h);

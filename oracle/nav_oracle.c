@@ -236,6 +236,54 @@ static float or_cast(const or_mapc *m, const or_dyn *dyn, int nd, float rdc,
     return max_range;
 }
 
+/* Fixed-step ray march (Sec. 2.2.2 as printed in the paper): sample the ray
+ * of Eq. 4 at tau = s * step (s = 0, 1, 2, ...) and stop at the first sample
+ * whose cell is occupied or off the map (range tau), or once tau exceeds
+ * r_max (range r_max).  In cell units with step_c = step * inv_res.  Every
+ * sample counts as a visit. */
+static float or_march(const or_mapc *m, const or_dyn *dyn, int nd, float rdc, float xc, float yc,
+                      float dx, float dy, float step_c, float max_range, int32_t *hit,
+                      uint32_t *visits)
+{
+    float rmax_c = max_range * m->inv_res;
+    uint32_t nv = 1;
+    int i = (int)floorf(xc);
+    int j = (int)floorf(yc);
+    if (!(xc >= 0.0f && yc >= 0.0f) || i >= m->w || j >= m->h) {
+        *hit = -1; *visits = nv; return 0.0f;
+    }
+    if (or_blocked_dyn(m, dyn, nd, rdc, i, j)) {
+        *hit = j * m->w + i; *visits = nv; return 0.0f;
+    }
+    for (int s = 1;; ++s) {
+        float tc = (float)s * step_c;
+        if (tc > rmax_c) break;
+        float px = xc + tc * dx;
+        float py = yc + tc * dy;
+        nv += 1;
+        if (!(px >= 0.0f && py >= 0.0f)) { *hit = -1; *visits = nv; return tc * m->res; }
+        i = (int)floorf(px);
+        j = (int)floorf(py);
+        if (i >= m->w || j >= m->h) { *hit = -1; *visits = nv; return tc * m->res; }
+        if (or_blocked_dyn(m, dyn, nd, rdc, i, j)) {
+            *hit = j * m->w + i; *visits = nv; return tc * m->res;
+        }
+    }
+    *hit = -2;
+    *visits = nv;
+    return max_range;
+}
+
+float or_march_ray(const uint8_t *occ, int w, int h, float res, float x, float y, float dx,
+                   float dy, float step, float max_range, int32_t *hit, uint32_t *visits)
+{
+    or_mapc m;
+    m.w = w; m.h = h; m.res = res; m.inv_res = (float)(1.0 / (double)res);
+    m.occ = (uint8_t *)occ;
+    return or_march(&m, NULL, 0, 0.0f, x * m.inv_res, y * m.inv_res, dx, dy, step * m.inv_res,
+                    max_range, hit, visits);
+}
+
 float or_cast_ray(const uint8_t *occ, int w, int h, float res, float x, float y,
                   float dx, float dy, float max_range, int32_t *hit, uint32_t *visits)
 {
@@ -418,6 +466,9 @@ void or_default_params(or_params *p)
     p->dyn_speed_max = 0.5f;
     p->dyn_min_sep = 1.0f;
     p->reward_mode = 0;
+    p->sensor = 0;
+    p->march_step = 0.03f;
+    p->n_sectors = 0;
 }
 
 static float or_circ_radius(const or_robot *r)
@@ -531,7 +582,7 @@ or_sim *or_create(const or_map *maps, int n_maps, const int *env_map, const int 
         s->env_k[e] = env_k[e];
         s->env_robot[e] = env_robot ? env_robot[e] : 0;
         if (env_k[e] > s->max_k) s->max_k = env_k[e];
-        s->obs_off[e + 1] = s->obs_off[e] + env_k[e] + 4;
+        s->obs_off[e + 1] = s->obs_off[e] + (s->par.n_sectors > 0 ? s->par.n_sectors : env_k[e]) + 4;
         s->ray_off[e + 1] = s->ray_off[e] + env_k[e];
     }
     /* beam tables: alpha_k = -FOV/2 + (k + 1/2) FOV / K (Eq. 4's alpha_k) */
@@ -723,12 +774,27 @@ static uint64_t or_scan(or_sim *s, int e, float *obs)
         float dy = st * ca[k] + ct * sa[k];
         int32_t hit;
         uint32_t nv;
-        float r = or_cast(m, dyn, nd, rdc, xc, yc, dx, dy, s->max_range, &hit, &nv);
+        float r = s->par.sensor == 1
+                      ? or_march(m, dyn, nd, rdc, xc, yc, dx, dy, s->par.march_step * m->inv_res,
+                                 s->max_range, &hit, &nv)
+                      : or_cast(m, dyn, nd, rdc, xc, yc, dx, dy, s->max_range, &hit, &nv);
         s->ranges[ro + k] = r;
         s->hits[ro + k] = hit;
         s->ray_visits[ro + k] = nv;
         vis += nv;
-        if (obs) obs[k] = r < s->max_range ? r : s->max_range;
+        if (obs && s->par.n_sectors == 0) obs[k] = r < s->max_range ? r : s->max_range;
+    }
+    /* Eq. 6: sector j = min over its K / m consecutive beams */
+    if (obs && s->par.n_sectors > 0) {
+        int per = K / s->par.n_sectors;
+        for (int q = 0; q < s->par.n_sectors; ++q) {
+            float mn = s->max_range;
+            for (int k = q * per; k < (q + 1) * per; ++k) {
+                float r = s->ranges[ro + k];
+                if (r < mn) mn = r;
+            }
+            obs[q] = mn;
+        }
     }
     return vis;
 }
@@ -760,7 +826,7 @@ int or_reset(or_sim *s, uint64_t seed, float *obs)
     for (int e = 0; e < s->n_envs; ++e) {
         float *o = obs ? obs + s->obs_off[e] : NULL;
         s->visits_total += or_scan(s, e, o);
-        if (o) or_obs_tail(s, e, o + s->env_k[e]);
+        if (o) or_obs_tail(s, e, o + (s->par.n_sectors > 0 ? s->par.n_sectors : s->env_k[e]));
     }
     return 0;
 }
@@ -827,14 +893,15 @@ static uint64_t or_step_env(or_sim *s, int e, const float *act, float *obs, floa
     reward[e] = r;
     done[e] = (uint8_t)((term ? 1 : 0) | (trunc ? 2 : 0) | (goal ? 4 : 0) | (coll ? 8 : 0));
     /* a9: O_{t+1}, kept as the final observation of a finished episode */
-    or_obs_tail(s, e, ob + K);
+    int D = s->par.n_sectors > 0 ? s->par.n_sectors : K;
+    or_obs_tail(s, e, ob + D);
     if (term || trunc) {
-        if (fo) memcpy(fo, ob, sizeof(float) * (size_t)(K + 4));
+        if (fo) memcpy(fo, ob, sizeof(float) * (size_t)(D + 4));
         /* a8: sparse reset, then a fresh scan (O~_{t+1}) */
         s->episode[e] = s->episode[e] + 1;
         if (or_reset_env(s, e)) *err = -4;
         vis += or_scan(s, e, ob);
-        or_obs_tail(s, e, ob + K);
+        or_obs_tail(s, e, ob + D);
     }
     return vis;
 }

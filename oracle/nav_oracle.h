@@ -30,6 +30,9 @@ typedef struct {
     int n_dyn;
     float dyn_radius, dyn_speed_max, dyn_min_sep;
     int reward_mode; /* 0 additive (progress - penalty + goal - collision), 1 exclusive cases of Eq. 3 */
+    int sensor;       /* 0 exact grid traversal, 1 fixed-step march (Sec. 2.2.2) */
+    float march_step; /* metres between march samples */
+    int n_sectors;    /* 0: raw beams in the observation, else min-pooled sectors (Eq. 6) */
 } or_params;
 
 typedef struct or_sim or_sim;
@@ -54,6 +57,8 @@ void or_comp_labels(const or_sim *s, int map, int robot, int *out);
 /* primitives, exposed for the pin tests */
 void or_sincosf(float x, float *s, float *c);
 uint64_t or_hash(uint64_t seed, uint64_t env, uint64_t episode, uint64_t k);
+float or_march_ray(const uint8_t *occ, int w, int h, float res, float x, float y, float dx,
+                   float dy, float step, float max_range, int32_t *hit, uint32_t *visits);
 float or_cast_ray(const uint8_t *occ, int w, int h, float res, float x, float y, float dx,
                   float dy, float max_range, int32_t *hit, uint32_t *visits);
 int or_footprint(const uint8_t *occ, int w, int h, float res, int shape, float radius,

@@ -45,7 +45,8 @@ class _Params(C.Structure):
                 ("horizon", C.c_int), ("goal_dmin", C.c_float), ("goal_dmax", C.c_float),
                 ("fov_deg", C.c_float), ("n_dyn", C.c_int), ("dyn_radius", C.c_float),
                 ("dyn_speed_max", C.c_float), ("dyn_min_sep", C.c_float),
-                ("reward_mode", C.c_int)]
+                ("reward_mode", C.c_int), ("sensor", C.c_int), ("march_step", C.c_float),
+                ("n_sectors", C.c_int)]
 
 
 _lib = None
@@ -77,6 +78,9 @@ def lib():
         L.or_cast_ray.restype = C.c_float
         L.or_cast_ray.argtypes = [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
                                   C.c_float, C.c_float, C.c_float, P, P]
+        L.or_march_ray.restype = C.c_float
+        L.or_march_ray.argtypes = [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+                                   C.c_float, C.c_float, C.c_float, C.c_float, P, P]
         L.or_footprint.argtypes = [P, C.c_int, C.c_int, C.c_float, C.c_int, C.c_float,
                                    C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]
         L.or_integrate.argtypes = [C.c_float] * 6 + [P, P, P]
@@ -104,6 +108,16 @@ def cast_ray(occ: np.ndarray, res: float, x: float, y: float, dx: float, dy: flo
     hit, vis = C.c_int32(), C.c_uint32()
     r = lib().or_cast_ray(_ptr(occ), occ.shape[1], occ.shape[0], res, x, y, dx, dy, max_range,
                           C.byref(hit), C.byref(vis))
+    return np.float32(r), int(hit.value), int(vis.value)
+
+
+def march_ray(occ: np.ndarray, res: float, x: float, y: float, dx: float, dy: float,
+              step: float, max_range: float):
+    """(range, hit, samples) of one fixed-step march (Sec. 2.2.2); step in metres."""
+    occ = np.ascontiguousarray(occ, np.uint8)
+    hit, vis = C.c_int32(), C.c_uint32()
+    r = lib().or_march_ray(_ptr(occ), occ.shape[1], occ.shape[0], res, x, y, dx, dy, step,
+                           max_range, C.byref(hit), C.byref(vis))
     return np.float32(r), int(hit.value), int(vis.value)
 
 
@@ -136,7 +150,9 @@ class OracleSim:
         p = params
         par = _Params(p.dt, p.goal_tol, p.c_progress, p.step_penalty, p.r_goal, p.r_coll,
                       p.horizon, p.goal_dmin, p.goal_dmax, p.fov_deg, p.n_dyn, p.dyn_radius,
-                      p.dyn_speed_max, p.dyn_min_sep, p.reward_mode)
+                      p.dyn_speed_max, p.dyn_min_sep, p.reward_mode,
+                      getattr(p, "sensor", 0), getattr(p, "march_step", 0.03),
+                      getattr(p, "n_sectors", 0))
         self.env_map = np.ascontiguousarray(env_map, np.int32)
         self.env_beams = np.ascontiguousarray(env_beams, np.int32)
         self.env_robot = np.ascontiguousarray(env_robot, np.int32)
@@ -148,7 +164,9 @@ class OracleSim:
         if not self._h:
             raise RuntimeError("or_create failed")
         L.or_set_threads(self._h, threads)
-        self.obs_off = np.concatenate([[0], np.cumsum(self.env_beams.astype(np.int64) + 4)])
+        m = int(getattr(p, "n_sectors", 0))
+        feat = np.full(self.n_envs, m, np.int64) if m > 0 else self.env_beams.astype(np.int64)
+        self.obs_off = np.concatenate([[0], np.cumsum(feat + 4)])
         self.ray_off = np.concatenate([[0], np.cumsum(self.env_beams.astype(np.int64))])
 
     @classmethod

@@ -293,9 +293,10 @@ int handle_view(const nav_handle *h, HandleView *out) {
     out->stream = h->stream;
     out->n_envs = h->n_envs;
     out->obs_floats = h->obs_off.back();
-    out->uniform_k = h->env_k.empty() ? -1 : h->env_k[0];
+    out->uniform_d = h->env_k.empty() ? -1 : h->env_k[0];
     for (int k : h->env_k)
-        if (k != out->uniform_k) out->uniform_k = -1;
+        if (k != out->uniform_d) out->uniform_d = -1;
+    if (h->par.n_sectors > 0) out->uniform_d = h->par.n_sectors;
     return NAV_OK;
 }
 
@@ -322,6 +323,9 @@ void nav_default_params(nav_params *p) {
     p->dyn_speed_max = 0.5f;
     p->dyn_min_sep = 1.0f;
     p->reward_mode = 0;
+    p->sensor = 0;
+    p->march_step = 0.03f;
+    p->n_sectors = 0;
 }
 
 int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int *env_beams,
@@ -355,6 +359,11 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         return bail(fail(h, NAV_E_INVAL, "bad nav_params"));
     if (P.n_dyn > 0 && (!finite_pos(P.dyn_radius) || !(P.dyn_speed_max >= 0.0f)))
         return bail(fail(h, NAV_E_INVAL, "bad moving-disc parameters"));
+    if ((P.sensor != 0 && P.sensor != 1) || P.n_sectors < 0 || P.n_sectors > kMaxBeams)
+        return bail(fail(h, NAV_E_INVAL, "bad sensor or n_sectors"));
+    if (P.sensor == 1 && (!finite_pos(P.march_step) ||
+                          (double)max_range / (double)P.march_step > (double)(1 << 22)))
+        return bail(fail(h, NAV_E_INVAL, "march_step must be > 0 with max_range / step <= 2^22"));
     for (int r = 0; r < n_robots; ++r) {
         const nav_robot &rb = robots[r];
         const bool shape_ok = (rb.shape == 0 && finite_pos(rb.radius)) ||
@@ -418,6 +427,9 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         const int r = env_robot ? env_robot[e] : 0;
         if (m < 0 || m >= n_maps || k <= 0 || k > kMaxBeams || r < 0 || r >= n_robots)
             return bail(fail(h, NAV_E_INVAL, "bad per-env entry at env " + std::to_string(e)));
+        if (P.n_sectors > 0 && k % P.n_sectors != 0)
+            return bail(fail(h, NAV_E_INVAL, "beam count not a multiple of n_sectors at env " +
+                                                 std::to_string(e)));
         h->env_map[e] = m;
         h->env_k[e] = k;
         env_robot_v[e] = r;
@@ -425,7 +437,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         if (t == (int)tab_k.size()) tab_k.push_back(k);
         h->env_tab[e] = t;
         h->max_k = std::max(h->max_k, k);
-        h->obs_off[e + 1] = h->obs_off[e] + k + 4;
+        h->obs_off[e + 1] = h->obs_off[e] + (P.n_sectors > 0 ? P.n_sectors : k) + 4;
         h->ray_off[e + 1] = h->ray_off[e] + k;
     }
     // every map side by side in one shared-memory region (split step)
@@ -580,7 +592,8 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     A.stats = nullptr;
     A.p = ParamsDev{P.dt, P.goal_tol, P.c_progress, P.step_penalty, P.r_goal, P.r_coll,
                     P.horizon, P.goal_dmin, P.goal_dmax, P.n_dyn, P.dyn_radius,
-                    P.dyn_speed_max, P.dyn_min_sep, P.reward_mode};
+                    P.dyn_speed_max, P.dyn_min_sep, P.reward_mode, P.sensor, P.march_step,
+                    P.n_sectors};
     A.max_range = max_range;
     A.max_k = h->max_k;
     int rc = set_map_modes(h);
@@ -947,10 +960,12 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
     float best = INFINITY;
     LaunchCfg best_cfg = h->cfg;
     int best_cap = h->smem_map_bytes, best_bytes = h->byte_cells;
-    // pass 1: launch shape with the current staging choice
+    // pass 1: launch shape with the current staging choice; the three
+    // fastest shapes are timed again with three times the steps
     const int tiles[] = {1, 2, 4, 8, 16};
     const int blocks[] = {128, 256, 512};
     const int regs[] = {32, 40, 64};
+    std::vector<std::pair<float, LaunchCfg>> cand;
     for (int te : tiles) {
         if (te > 1 && te > h->n_envs) continue;
         h->cfg.tile_envs = te;
@@ -959,9 +974,23 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
             for (int mr : regs) {
                 h->cfg.block_threads = bt;
                 h->cfg.max_regs = mr;
-                const float ms = time_config(h, steps, e0, e1);
-                if (ms < best) { best = ms; best_cfg = h->cfg; }
+                cand.push_back({time_config(h, steps, e0, e1), h->cfg});
             }
+    }
+    if (rc == NAV_OK && !cand.empty()) {
+        std::sort(cand.begin(), cand.end(),
+                  [](const std::pair<float, LaunchCfg> &a, const std::pair<float, LaunchCfg> &b) {
+                      return a.first < b.first;
+                  });
+        for (size_t c = 0; c < cand.size() && c < 3; ++c) {
+            h->cfg = cand[c].second;
+            if ((rc = build_tiles(h)) != NAV_OK) break;
+            const float ms = time_config(h, 3 * steps, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_cfg = h->cfg;
+            }
+        }
     }
     // pass 2: staging (byte cells or packed bits) and the shared-memory cap
     if (rc == NAV_OK) {

@@ -48,6 +48,9 @@ struct ParamsDev {
     int n_dyn;
     float dyn_radius, dyn_speed_max, dyn_min_sep;
     int reward_mode;
+    int sensor;       // 0 exact traversal, 1 fixed-step march
+    float march_step; // metres
+    int n_sectors;    // 0 raw beams, else Eq. 6 sector minima
 };
 
 // One CTA work unit: up to kMaxTileEnvs envs sharing a map and a beam count.
@@ -140,7 +143,7 @@ struct HandleView {
     void *stream;
     int n_envs;
     long long obs_floats;
-    int uniform_k; // the beam count if every env has the same one, else -1
+    int uniform_d; // range features per observation row if every env has the same count, else -1
 };
 int handle_view(const nav_handle *h, HandleView *out);
 // Records `msg` as the handle's last error and returns `code`.

@@ -431,7 +431,7 @@ int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t se
     if (!h || !p || handle_view(h, &hv) != NAV_OK) return NAV_E_INVAL;
     if (!obs_dev || !actions_dev || !reward_dev || !done_dev || n_steps <= 0)
         return handle_fail(h, NAV_E_INVAL, "nav_rollout: bad argument");
-    if (hv.uniform_k < 0 || hv.uniform_k + 4 != p->obs_dim || hv.n_envs > p->max_batch)
+    if (hv.uniform_d < 0 || hv.uniform_d + 4 != p->obs_dim || hv.n_envs > p->max_batch)
         return handle_fail(h, NAV_E_INVAL,
                            "nav_rollout: policy obs_dim / max_batch do not match the handle");
     for (int t = 0; t < n_steps; ++t) {

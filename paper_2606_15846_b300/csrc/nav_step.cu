@@ -309,6 +309,77 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-step march (Sec. 2.2.2): the ray of Eq. 4 is sampled at
+// tau_s = s * step_c cells (s = 0, 1, ...); the first sample whose cell is
+// blocked or off the map ends the ray at range tau_s, and a ray whose next
+// sample lies beyond r_max returns r_max.  Every sample is one visit.  The
+// off-map test is explicit, so any step length is valid.  Same outputs as
+// cast_ray: range in metres, hit = j*W+i, -1 off-map, -2 r_max.
+// ---------------------------------------------------------------------------
+template <bool DYN, class V>
+__device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float xc, float yc,
+                                           float dx, float dy, float step_c, float rmax_c,
+                                           float max_range, const DynEnv *de, int nd, int &hit,
+                                           unsigned &vis) {
+    if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
+    int i = (int)floorf(xc), j = (int)floorf(yc);
+    if (i >= M.w || j >= M.h) { hit = -1; vis = 1; return 0.0f; }
+    if (!view.free_at(cell_index(view, i, j)) || (DYN && dyn_cell(*de, nd, i, j))) {
+        hit = j * M.w + i;
+        vis = 1;
+        return 0.0f;
+    }
+    float glo = INFINITY, ghi = -INFINITY;
+    if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
+    for (unsigned s = 1;; ++s) {
+        const float tc = (float)s * step_c;
+        if (tc > rmax_c) { hit = -2; vis = s; return max_range; }
+        const float px = xc + tc * dx, py = yc + tc * dy;
+        i = (int)floorf(px);
+        j = (int)floorf(py);
+        if ((unsigned)i >= (unsigned)M.w || (unsigned)j >= (unsigned)M.h) {
+            hit = -1;
+            vis = s + 1u;
+            return tc * M.res;
+        }
+        if (!view.free_at(cell_index(view, i, j)) ||
+            (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
+            hit = j * M.w + i;
+            vis = s + 1u;
+            return tc * M.res;
+        }
+    }
+}
+
+// Writes beam k's clipped range into its observation row, or, with sectors
+// (Eq. 6), folds it into the minimum of sector k / (K / m) by an atomic min
+// on the float's bits (ranges are >= 0, so integer order is float order).
+// Warp-collective: every lane of the warp calls it, `active` or not.  The
+// lanes of one sector are contiguous in a warp, so a segmented min over the
+// shuffle tree leaves each sector's minimum in its first lane, which alone
+// issues the atomic.  The sector slots hold r_max before the scan.
+__device__ __forceinline__ void put_range(const StepArgs &A, float *row, int k, int K,
+                                          float range, bool active) {
+    const float c = fminf(range, A.max_range);
+    const int m = A.p.n_sectors;
+    if (m == 0) {
+        if (active) row[k] = c;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    unsigned long long key = active ? (unsigned long long)(row + k / (K / m)) : 0ull;
+    int v = active ? __float_as_int(c) : 0x7fffffff;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ov = __shfl_down_sync(kFull, v, o);
+        const unsigned long long ok = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && ok == key) v = min(v, ov);
+    }
+    const unsigned long long pk = __shfl_up_sync(kFull, key, 1);
+    if (active && (lane == 0 || pk != key)) atomicMin(reinterpret_cast<int *>(key), v);
+}
+
+// ---------------------------------------------------------------------------
 // Footprints (Sec. 2.2.3 collision check; Tables 8-9 presets)
 // ---------------------------------------------------------------------------
 template <bool DYN, class B>
@@ -481,6 +552,7 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
                           EnvSlot &slot, DynEnv *dmain, DynEnv *dfin) {
     const int e = slot.env;
     const int nd = DYN ? A.p.n_dyn : 0;
+    const int D = A.p.n_sectors > 0 ? A.p.n_sectors : K; // range features per row
     float4 ob[kMaxDyn];
     const float rdc = A.p.dyn_radius * M.inv_res;
     float x, y, th, v, w, gx, gy, dprev;
@@ -580,7 +652,8 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         if (term || trunc) {
             // a9 (final): O_{t+1} before the reset, scanned in phase 2
             if (A.final_obs) {
-                write_tail(A.final_obs + slot.obs_off + K, x, y, th, gx, gy, v, w);
+                write_tail(A.final_obs + slot.obs_off + D, x, y, th, gx, gy, v, w);
+                for (int q = 0; q < A.p.n_sectors; ++q) A.final_obs[slot.obs_off + q] = A.max_range;
                 slot.fin = 1;
                 slot.fxc = xc; slot.fyc = yc; slot.fst = st; slot.fct = ct;
                 if (DYN) *dfin = *dmain;
@@ -601,8 +674,9 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         for (int q = 0; q < nd; ++q) A.dyn[(size_t)e * nd + q] = ob[q];
         if (restamp) stamp_discs(ob, nd, M.inv_res, rdc, *dmain);
     }
-    // a9: observation tail of the scan written to obs
-    write_tail(A.obs + slot.obs_off + K, x, y, th, gx, gy, v, w);
+    // a9: observation tail of the scan written to obs (sector minima start at r_max)
+    write_tail(A.obs + slot.obs_off + D, x, y, th, gx, gy, v, w);
+    for (int q = 0; q < A.p.n_sectors; ++q) A.obs[slot.obs_off + q] = A.max_range;
     float st, ct;
     sincos_taylor(th, st, ct);
     slot.xc = x * M.inv_res;
@@ -684,7 +758,7 @@ __device__ void expand_bytes(uint8_t *dst, const uint32_t *__restrict__ src, con
 // ---------------------------------------------------------------------------
 // Ray phase
 // ---------------------------------------------------------------------------
-template <bool DYN, class B>
+template <bool DYN, bool MARCH, class B>
 __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, const TileDev &T,
                           int K, const float2 *beams, const EnvSlot *slots, const int *fin_slot,
                           int n_fin, const DynEnv *dyn, int *next_chunk) {
@@ -692,6 +766,7 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     const int n_main = T.env_count * K;
     const int total = n_main + n_fin * K;
     const float rmax_c = A.max_range * M.inv_res;
+    const float step_c = A.p.march_step * M.inv_res;
     const int nd = DYN ? A.p.n_dyn : 0;
     for (;;) {
         int chunk = 0;
@@ -701,11 +776,14 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
         if (base >= total) break;
         const int rid = base + lane;
         unsigned vis = 0;
+        float *row = nullptr;
+        float range = 0.0f;
+        int k = 0;
         if (rid < total) {
             const bool fin = rid >= n_main;
             const int rr = fin ? rid - n_main : rid;
             const int q = rr / K;
-            const int k = rr - q * K;
+            k = rr - q * K;
             const int s = fin ? fin_slot[q] : q;
             const EnvSlot &es = slots[s];
             const float sx = fin ? es.fst : es.st, cx = fin ? es.fct : es.ct;
@@ -714,12 +792,13 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
             // Eq. 4: direction of theta + alpha_k by angle addition
             const float dx = cx * ab.x - sx * ab.y;
             const float dy = sx * ab.x + cx * ab.y;
+            const DynEnv *de = DYN ? &dyn[2 * s + (fin ? 1 : 0)] : nullptr;
             int hit;
-            const float range = cast_ray<DYN>(bits, M, ox, oy, dx, dy, rmax_c, A.max_range,
-                                              DYN ? &dyn[2 * s + (fin ? 1 : 0)] : nullptr, nd,
-                                              hit, vis);
-            float *dst = fin ? A.final_obs : A.obs;
-            dst[es.obs_off + k] = fminf(range, A.max_range);
+            range = MARCH ? march_ray<DYN>(bits, M, ox, oy, dx, dy, step_c, rmax_c, A.max_range,
+                                           de, nd, hit, vis)
+                          : cast_ray<DYN>(bits, M, ox, oy, dx, dy, rmax_c, A.max_range, de, nd,
+                                          hit, vis);
+            row = (fin ? A.final_obs : A.obs) + es.obs_off;
             if (!fin && A.dbg_range) {
                 const long long ro = es.ray_off + k;
                 A.dbg_range[ro] = range;
@@ -727,6 +806,7 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
                 A.dbg_vis[ro] = vis;
             }
         }
+        put_range(A, row, k, K, range, rid < total);
         if (A.stats) {
             unsigned v = vis;
 #pragma unroll
@@ -740,7 +820,7 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     }
 }
 
-template <bool DYN, class V>
+template <bool DYN, bool MARCH, class V>
 __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const MapDev &M,
                                          const TileDev &T, int K, const float2 *sbeam,
                                          EnvSlot *slots, int *fin_slot, int *n_fin, DynEnv *sdyn,
@@ -756,7 +836,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
         if (tid == 0) *n_fin = __popc(m);
     }
     __syncthreads();
-    ray_phase<DYN>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
+    ray_phase<DYN, MARCH>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
 }
 
 // Persistent CTAs: each CTA takes tiles from a global queue until none are
@@ -766,7 +846,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
 // for the next launch on the stream.
 // MINB: resident 512-thread CTAs per SM the register allocation must allow
 // (4, 3, 2 -> at most 32, 40, 64 registers per thread).
-template <bool DYN, int MINB>
+template <bool DYN, int MINB, bool MARCH>
 __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ EnvSlot slots[kMaxTileEnvs];
@@ -833,13 +913,13 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         const int mode = failed ? (int)kMapGlobal : M.mode;
         if (tid == 0) staged_map = mode == kMapGlobal ? -1 : T.map;
         if (mode == kMapSharedBytes)
-            run_tile<DYN>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         else if (mode == kMapSharedBits)
-            run_tile<DYN>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         else
-            run_tile<DYN>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         __syncthreads();
     }
@@ -894,22 +974,28 @@ __global__ void __launch_bounds__(128) env_kernel(const StepArgs A, int n_envs) 
     }
 }
 
-template <class V>
-__device__ __forceinline__ void cast_store(const StepArgs &A, const V &view, const MapDev &M,
-                                           float4 o, float2 ab, int e, int k, bool fin,
-                                           float rmax_c, unsigned &vis) {
+// Casts one ray of the split step (no moving discs) and returns its range;
+// the caller stores it with put_range.
+template <bool MARCH, class V>
+__device__ __forceinline__ float cast_one(const StepArgs &A, const V &view, const MapDev &M,
+                                          float4 o, float2 ab, int e, int k, bool fin,
+                                          unsigned &vis) {
     const float dx = o.w * ab.x - o.z * ab.y;
     const float dy = o.z * ab.x + o.w * ab.y;
+    const float rmax_c = A.max_range * M.inv_res;
     int hit;
-    const float range = cast_ray<false>(view, M, o.x, o.y, dx, dy, rmax_c, A.max_range, nullptr,
-                                        0, hit, vis);
-    (fin ? A.final_obs : A.obs)[A.obs_off[e] + k] = fminf(range, A.max_range);
+    const float range =
+        MARCH ? march_ray<false>(view, M, o.x, o.y, dx, dy, A.p.march_step * M.inv_res, rmax_c,
+                                 A.max_range, nullptr, 0, hit, vis)
+              : cast_ray<false>(view, M, o.x, o.y, dx, dy, rmax_c, A.max_range, nullptr, 0, hit,
+                                vis);
     if (!fin && A.dbg_range) {
         const long long ro = A.ray_off[e] + k;
         A.dbg_range[ro] = range;
         A.dbg_hit[ro] = hit;
         A.dbg_vis[ro] = vis;
     }
+    return range;
 }
 
 __device__ __forceinline__ void add_stats(const StepArgs &A, unsigned vis, int nr) {
@@ -922,6 +1008,7 @@ __device__ __forceinline__ void add_stats(const StepArgs &A, unsigned vis, int n
     }
 }
 
+template <bool MARCH>
 __global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bar;
@@ -971,19 +1058,25 @@ __global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
         const MapDev M = A.maps[T.map];
         const int K = A.tab_k[T.tab];
         const int r = ch.y + lane;
+        const bool active = r < T.env_count * K;
         unsigned vis = 0;
-        if (r < T.env_count * K) {
-            const int el = r / K, k = r - el * K;
+        float range = 0.0f, *row = nullptr;
+        int k = 0;
+        if (active) {
+            const int el = r / K;
+            k = r - el * K;
             const int e = A.perm[T.env_begin + el];
             const float4 o = A.ray_main[e];
             const float2 ab = sbeam[A.tab_off[T.tab] + k];
             if (!failed)
-                cast_store(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M, o, ab, e, k, false,
-                           A.max_range * M.inv_res, vis);
+                range = cast_one<MARCH>(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M, o, ab,
+                                        e, k, false, vis);
             else
-                cast_store(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, o, ab, e, k, false,
-                           A.max_range * M.inv_res, vis);
+                range = cast_one<MARCH>(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, o,
+                                        ab, e, k, false, vis);
+            row = A.obs + A.obs_off[e];
         }
+        put_range(A, row, k, K, range, active);
         add_stats(A, vis, min(32, T.env_count * K - ch.y));
     }
     // final scans of the envs that finished this step
@@ -999,17 +1092,20 @@ __global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
             const int K = A.tab_k[A.env_tab[e]];
             const int toff = A.tab_off[A.env_tab[e]];
             const float4 o = A.ray_fin[e];
+            float *row = A.final_obs + A.obs_off[e];
             for (int k0 = 0; k0 < K; k0 += 32) {
                 const int k = k0 + lane;
                 unsigned vis = 0;
+                float range = 0.0f;
                 if (k < K) {
                     if (!failed)
-                        cast_store(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M, o,
-                                   sbeam[toff + k], e, k, true, A.max_range * M.inv_res, vis);
+                        range = cast_one<MARCH>(A, BitsShared{sbits + M.all_off, M.pitch * 32}, M,
+                                                o, sbeam[toff + k], e, k, true, vis);
                     else
-                        cast_store(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, o,
-                                   sbeam[toff + k], e, k, true, A.max_range * M.inv_res, vis);
+                        range = cast_one<MARCH>(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32},
+                                                M, o, sbeam[toff + k], e, k, true, vis);
                 }
+                put_range(A, row, k, K, range, k < K);
                 add_stats(A, vis, min(32, K - k0));
             }
         }
@@ -1028,10 +1124,10 @@ __global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
     }
 }
 
-template <bool DYN> const void *pick_kernel(int max_regs) {
-    if (max_regs <= 32) return (const void *)step_kernel<DYN, 4>;
-    if (max_regs <= 40) return (const void *)step_kernel<DYN, 3>;
-    return (const void *)step_kernel<DYN, 2>;
+template <bool DYN, bool MARCH> const void *pick_kernel(int max_regs) {
+    if (max_regs <= 32) return (const void *)step_kernel<DYN, 4, MARCH>;
+    if (max_regs <= 40) return (const void *)step_kernel<DYN, 3, MARCH>;
+    return (const void *)step_kernel<DYN, 2, MARCH>;
 }
 
 } // namespace
@@ -1042,7 +1138,11 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     const size_t smem = (size_t)a.smem_region_bytes + (size_t)a.max_k * sizeof(float2) +
                         (dyn ? (size_t)2 * cfg.tile_envs * sizeof(DynEnv) : 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const void *fn = dyn ? pick_kernel<true>(cfg.max_regs) : pick_kernel<false>(cfg.max_regs);
+    const bool march = a.p.sensor == 1;
+    const void *fn = dyn ? (march ? pick_kernel<true, true>(cfg.max_regs)
+                                  : pick_kernel<true, false>(cfg.max_regs))
+                         : (march ? pick_kernel<false, true>(cfg.max_regs)
+                                  : pick_kernel<false, false>(cfg.max_regs));
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     int dev = 0, n_sm = 0, per_sm = 0;
@@ -1065,14 +1165,15 @@ int launch_step_split(const StepArgs &a, int n_envs, void *stream) {
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return (int)err;
     const size_t smem = (size_t)a.all_words * 4 + (size_t)a.n_beams_total * sizeof(float2);
-    err = cudaFuncSetAttribute(ray_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fn = a.p.sensor == 1 ? (const void *)ray_kernel<true> : (const void *)ray_kernel<false>;
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     int dev = 0, n_sm = 0;
     err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return (int)err;
     void *args[] = {const_cast<StepArgs *>(&a)};
-    err = cudaLaunchKernel((const void *)ray_kernel, dim3(n_sm), dim3(1024), args, smem, s);
+    err = cudaLaunchKernel(fn, dim3(n_sm), dim3(1024), args, smem, s);
     if (err != cudaSuccess) return (int)err;
     return (int)cudaGetLastError();
 }

@@ -68,7 +68,8 @@ class nav_params(C.Structure):
                 ("horizon", C.c_int), ("goal_dmin", C.c_float), ("goal_dmax", C.c_float),
                 ("fov_deg", C.c_float), ("n_dyn", C.c_int), ("dyn_radius", C.c_float),
                 ("dyn_speed_max", C.c_float), ("dyn_min_sep", C.c_float),
-                ("reward_mode", C.c_int)]
+                ("reward_mode", C.c_int), ("sensor", C.c_int), ("march_step", C.c_float),
+                ("n_sectors", C.c_int)]
 
 
 _lib = None

@@ -38,6 +38,11 @@ class Robot:
 
 DISC = Robot(shape=0, radius=0.18, v_min=0.0, v_max=0.5, w_min=-1.0, w_max=1.0)
 RECT = Robot(shape=1, length=0.70, width=0.31, v_min=0.0, v_max=1.0, w_min=-1.5, w_max=1.5)
+# The paper's platforms (Tables 8-9): action bounds (0, -pi/4) .. (0.5, pi/4)
+TURTLEBOT2 = Robot(shape=0, radius=0.20, v_min=0.0, v_max=0.5, w_min=-math.pi / 4,
+                   w_max=math.pi / 4)
+GO2 = Robot(shape=1, length=0.80, width=0.41, v_min=0.0, v_max=0.5, w_min=-math.pi / 4,
+            w_max=math.pi / 4)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -58,6 +63,9 @@ class Params:
     dyn_speed_max: float = 0.5
     dyn_min_sep: float = 1.0
     reward_mode: int = 0
+    sensor: int = 0           # 0 exact grid traversal, 1 fixed-step march (Sec. 2.2.2)
+    march_step: float = 0.03  # metres between march samples
+    n_sectors: int = 0        # 0 raw beams, else Eq. 6 sector minima in the observation
 
 
 def _rasterise_box(occ, x0, y0, x1, y1, res):
@@ -210,4 +218,40 @@ def config_uneven(n_envs: int = 16384, n_maps: int = 64, seed0: int = 200,
         robots=[DISC, RECT],
         max_range=6.0,
         params=Params(n_dyn=n_dyn),
+    )
+
+
+def paper_params(fov_deg: float) -> Params:
+    """Table 7's sensing, episode and reward constants: 0.03 m fixed-step
+    march, 30 sector minima (of 1080 beams), horizon 200, dt 0.1 s, goal
+    0.2 m, the exclusive reward cases of Eq. 3 (+10 / -10 / 2 x progress).
+    Goals are any free cell at >= 1 m (the paper gives no distance band)."""
+    return Params(reward_mode=1, step_penalty=0.0, goal_dmin=1.0, goal_dmax=1.0e9,
+                  fov_deg=fov_deg, sensor=1, march_step=0.03, n_sectors=30)
+
+
+def config_paper(robot: str = "turtlebot2", n_envs: int = 1024, seed: int = 31,
+                 occupancy: float = 0.12, beams: int = 1080) -> Workload:
+    """The paper's training setting (Sec. 2.2.1, Tables 7-9): every env on
+    one shared map, 10 x 10 m for the TurtleBot2 (disc r = 0.20 m, 270 deg
+    fan) or 13.5 x 13.5 m for the Go2 (0.80 x 0.41 m rectangle, 360 deg),
+    1080 beams marched at 0.03 m to 20 m and pooled into 30 sectors.  The
+    map content is not published: a seeded map of boxes, discs and corridor
+    walls at `occupancy` stands in (0.05 m cells)."""
+    if robot == "turtlebot2":
+        side, rb, fov = 200, TURTLEBOT2, 270.0
+    elif robot == "go2":
+        side, rb, fov = 270, GO2, 360.0
+    else:
+        raise ValueError(robot)
+    occ = make_map(seed, side, side, occupancy, corridors=True)
+    return Workload(
+        name=f"paper-{robot}-{n_envs}env-{side}x{side}-{beams}beam-march-30sector",
+        maps=[occ],
+        env_map=np.zeros(n_envs, np.int32),
+        env_beams=np.full(n_envs, beams, np.int32),
+        env_robot=np.zeros(n_envs, np.int32),
+        robots=[rb],
+        max_range=20.0,
+        params=paper_params(fov),
     )

@@ -235,6 +235,178 @@ def test_quarter_turn_permutes_beams(oracle):
 
 
 # --------------------------------------------------------------------------
+# Fixed-step march (Sec. 2.2.2, Table 7's 0.03 m step) and the beam fan
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("direction", ["+x", "-y"])
+@pytest.mark.parametrize("step", [0.03, 0.011])
+def test_march_axis_wall_is_first_sample_past_the_face(oracle, direction, step):
+    """Towards a wall at distance D along an axis, the march stops at the
+    first sample s * step >= D, after s + 1 samples."""
+    n = 64
+    occ = np.zeros((n, n), np.uint8)
+    x0, y0 = 10.37 * RES, 40.61 * RES
+    if direction == "+x":
+        occ[:, 50] = 1
+        d, D = (1.0, 0.0), 50 * RES - x0
+    else:
+        occ[5, :] = 1
+        d, D = (0.0, -1.0), y0 - 6 * RES
+    s_star = math.ceil(D / step)
+    assert s_star * step - D > 1e-4 and D - (s_star - 1) * step > 1e-4  # no rounding tie
+    r, hit, vis = oracle.march_ray(occ, RES, x0, y0, d[0], d[1], step, 10.0)
+    assert abs(float(r) - s_star * step) < 2e-5
+    assert hit >= 0 and occ.flat[hit] == 1
+    assert vis == s_star + 1
+
+
+def test_march_empty_map_and_off_map(oracle):
+    occ = np.zeros((256, 256), np.uint8)
+    r, hit, vis = oracle.march_ray(occ, RES, 6.4, 6.4, 0.6, 0.8, 0.03, 4.0)
+    assert r == np.float32(4.0) and hit == -2 and vis == math.floor(4.0 / 0.03 + 1e-6) + 1
+    small = np.zeros((16, 16), np.uint8)
+    r, hit, _ = oracle.march_ray(small, RES, 8.5 * RES, 8.5 * RES, 1.0, 0.0, 0.03, 10.0)
+    assert hit == -1 and abs(float(r) - 0.39) < 2e-5  # first sample at x >= 0.8 m
+
+
+def _chord(i, j, xc, yc, dx, dy):
+    """Length (cells) of the ray's segment inside cell (i, j), exact slabs."""
+    lo, hi = 0.0, math.inf
+    for p, d, a in ((xc, dx, i), (yc, dy, j)):
+        if abs(d) < 1e-12:
+            if not (a <= p < a + 1):
+                return 0.0
+            continue
+        t0, t1 = (a - p) / d, (a + 1 - p) / d
+        lo, hi = max(lo, min(t0, t1)), min(hi, max(t0, t1))
+    return max(0.0, hi - lo)
+
+
+@pytest.mark.parametrize("step", [0.03, 0.07])
+def test_march_against_exact_traversal(oracle, step):
+    """The march never stops before the exact first hit; it stops within one
+    step after it unless the ray only clips that cell for less than a step;
+    and the cell of its stopping sample is blocked or off the map."""
+    wl = W.config_small()
+    occ = wl.maps[0]
+    h, w = occ.shape
+    rng = np.random.default_rng(5)
+    free = np.argwhere(occ == 0)
+    clipped = 0
+    for _ in range(600):
+        j, i = free[rng.integers(len(free))]
+        x, y = (i + rng.uniform(0.1, 0.9)) * RES, (j + rng.uniform(0.1, 0.9)) * RES
+        a = rng.uniform(-math.pi, math.pi)
+        dx, dy = math.cos(a), math.sin(a)
+        rd, hd, _ = oracle.cast_ray(occ, RES, x, y, dx, dy, 4.0)
+        rm, hm, vm = oracle.march_ray(occ, RES, x, y, dx, dy, step, 4.0)
+        assert float(rm) >= float(rd) - 1e-5
+        if hd >= 0 and float(rm) - float(rd) >= step + 1e-5:
+            xc, yc = np.float32(x) * np.float32(1 / RES), np.float32(y) * np.float32(1 / RES)
+            assert _chord(hd % w, hd // w, float(xc), float(yc), dx, dy) * RES < step + 1e-5
+            clipped += 1
+        if hm == -2:
+            assert rm == np.float32(4.0)
+            continue
+        assert vm == round(float(rm) / step) + 1
+        px, py = (x + float(rm) * dx) / RES, (y + float(rm) * dy) / RES
+        if min(abs(px - round(px)), abs(py - round(py))) < 1e-3:
+            continue  # the stopping sample sits on a grid line
+        ci, cj = math.floor(px), math.floor(py)
+        off = ci < 0 or cj < 0 or ci >= w or cj >= h
+        assert off == (hm == -1)
+        if not off:
+            assert occ[cj, ci] == 1 and hm == cj * w + ci
+    assert clipped < 60
+
+
+def test_march_converges_to_exact_range(oracle):
+    wl = W.config_small()
+    occ = wl.maps[0]
+    rng = np.random.default_rng(9)
+    free = np.argwhere(occ == 0)
+    diffs = []
+    for _ in range(300):
+        j, i = free[rng.integers(len(free))]
+        x, y = (i + 0.5) * RES, (j + 0.5) * RES
+        a = rng.uniform(-math.pi, math.pi)
+        rd, _, _ = oracle.cast_ray(occ, RES, x, y, math.cos(a), math.sin(a), 4.0)
+        rm, _, _ = oracle.march_ray(occ, RES, x, y, math.cos(a), math.sin(a), 1e-3, 4.0)
+        diffs.append(float(rm) - float(rd))
+    diffs = np.array(diffs)
+    assert diffs.min() > -1e-5
+    assert np.mean(diffs < 1e-3 + 1e-5) > 0.97
+
+
+def _one_scan(oracle, occ, K, par, x, y, th, max_range):
+    sim = oracle.OracleSim([occ], np.zeros(1, np.int32), np.full(1, K, np.int32),
+                           np.zeros(1, np.int32), [W.DISC], max_range, par, RES)
+    sim.reset(0)
+    sim.set_state(0, np.array([[x, y, th, 0, 0, -50, -50, 100]], np.float32),
+                  np.zeros((1, 2), np.int32))
+    obs, _, done = sim.step(np.array([[-1.0, 0.0]], np.float32))  # v = 0, w = 0
+    assert done[0] == 0
+    r, _, _ = sim.debug()
+    return obs, r
+
+
+def test_fan_of_270_degrees_matches_the_square_border(oracle):
+    """Eq. 4's fan alpha_k = -fov/2 + (k + 1/2) fov / K: from the centre of an
+    empty L x L map, beam k ends on the border at (L/2) / max|cos|, |sin|."""
+    n, K = 128, 1080
+    occ = np.zeros((n, n), np.uint8)
+    c = n * RES / 2
+    th = 0.3
+    par = W.Params(goal_dmin=0.0, goal_dmax=1e9, fov_deg=270.0)
+    _, r = _one_scan(oracle, occ, K, par, c, c, th, 10.0)
+    fov = math.radians(270.0)
+    for k in range(K):
+        a = th - fov / 2 + (k + 0.5) * fov / K
+        want = c / max(abs(math.cos(a)), abs(math.sin(a)))
+        assert abs(float(r[k]) - want) < 2e-5, (k, float(r[k]), want)
+
+
+@pytest.mark.parametrize("sensor", [0, 1])
+def test_sector_pooling_reduces_to_the_raw_scan(oracle, sensor):
+    """Eq. 6 special cases and the 1080 -> 30 x 36 split of Table 7: with one
+    beam per sector the pooled observation is the raw one; every pooled row
+    is the minimum of its beams of the raw run; dynamics, rewards and flags
+    do not depend on the pooling."""
+    wl = W.config_small()
+    K = 1080
+    rng = np.random.default_rng(2)
+    acts = rng.uniform(-1, 1, (25, 4, 2)).astype(np.float32)
+
+    def run(m):
+        par = W.Params(sensor=sensor, n_sectors=m, fov_deg=270.0)
+        sim = oracle.OracleSim(wl.maps, np.zeros(4, np.int32), np.full(4, K, np.int32),
+                               np.zeros(4, np.int32), [W.DISC], 4.0, par, RES)
+        out = [sim.reset(3)]
+        for t in range(25):
+            out.append(sim.step(acts[t], want_final=True))
+        return sim, out
+
+    _, raw = run(0)
+    for m in (K, 30, 1):
+        sim, pooled = run(m)
+        D = m
+        for t, (a, b) in enumerate(zip(raw, pooled)):
+            o_raw = (a if t == 0 else a[0]).reshape(4, K + 4)
+            o_pool = (b if t == 0 else b[0]).reshape(4, D + 4)
+            want = o_raw[:, :K].reshape(4, m, K // m).min(axis=2)
+            np.testing.assert_array_equal(o_pool[:, :D], want)
+            np.testing.assert_array_equal(o_pool[:, D:], o_raw[:, K:])
+            if t:
+                np.testing.assert_array_equal(a[1], b[1])
+                np.testing.assert_array_equal(a[2], b[2])
+                f_raw = a[3].reshape(4, K + 4)
+                f_pool = b[3].reshape(4, D + 4)
+                fin = (a[2] & 3) != 0
+                np.testing.assert_array_equal(
+                    f_pool[fin, :D], f_raw[fin, :K].reshape(-1, m, K // m).min(axis=2))
+                np.testing.assert_array_equal(f_pool[fin, D:], f_raw[fin, K:])
+
+
+# --------------------------------------------------------------------------
 # Unicycle integration (Sec. 2.2.3): exact arc
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("w", [1.0, -1.5, 0.3, 1e-7])

@@ -35,6 +35,12 @@ def _ang(a, b):
     return np.minimum(d, 2 * np.pi - d)
 
 
+def _features(wl):
+    """Range features per observation row: the beams, or Eq. 6's sectors."""
+    m = int(getattr(wl.params, "n_sectors", 0))
+    return np.full(wl.n_envs, m, np.int32) if m > 0 else wl.env_beams
+
+
 def _compare_obs(obs, ref, beams, rows=None, what="obs"):
     off = np.concatenate([[0], np.cumsum(beams.astype(np.int64) + 4)])
     env_ids = range(len(beams)) if rows is None else rows
@@ -82,7 +88,8 @@ def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=
     sim.set_debug(True)
     obs = sim.reset(seed)
     robs = ref.reset(seed)
-    _compare_obs(obs.cpu().numpy(), robs, wl.env_beams, what="reset obs")
+    feat = _features(wl)
+    _compare_obs(obs.cpu().numpy(), robs, feat, what="reset obs")
     _compare_state(sim, ref, "reset")
     _compare_debug(sim, ref, "reset")
     acts = W.uniform_actions(seed + 1000, n_steps, wl.n_envs)
@@ -98,12 +105,12 @@ def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=
         d = d.cpu().numpy()
         assert np.array_equal(d, rd), f"step {t}: done flags differ at {np.flatnonzero(d != rd)[:8]}"
         assert np.abs(r.cpu().numpy() - rr).max() <= 1e-5, f"step {t}: reward"
-        _compare_obs(o.cpu().numpy(), ro, wl.env_beams, what=f"step {t} obs")
+        _compare_obs(o.cpu().numpy(), ro, feat, what=f"step {t} obs")
         if want_final:
             ended = np.flatnonzero(d & 3)
             n_done += len(ended)
             if len(ended):
-                _compare_obs(fo.cpu().numpy(), rfo, wl.env_beams, rows=ended,
+                _compare_obs(fo.cpu().numpy(), rfo, feat, rows=ended,
                              what=f"step {t} final obs")
         _compare_debug(sim, ref, f"step {t}")
         if t % check_state_every == 0 or t == n_steps - 1:
@@ -368,3 +375,63 @@ def test_split_step_mixed_beams_and_robots(mods):
     wl = _mixed()
     wl.maps = [m[:96, :96].copy() for m in wl.maps]
     run_parity(mods, wl, 60, seed=15, launch=(0, 0, 0, 0, 0, 1))
+
+
+# --------------------------------------------------------------------------
+# Paper sensing (Sec. 2.2.2, Eq. 6, Table 7): fixed-step march, sector minima
+# --------------------------------------------------------------------------
+def test_paper_turtlebot2_march_and_sectors(mods):
+    """TurtleBot2 preset: one 10 x 10 m map, 1080 beams over 270 deg marched
+    at 0.03 m to 20 m, 30 sector minima; hit cells and sample counts
+    bit-exact, 120 steps with resets."""
+    wl = W.config_paper("turtlebot2", n_envs=256)
+    _, _, n_done = run_parity(mods, wl, 120, seed=4)
+    assert n_done > 20
+
+
+def test_paper_go2_march_and_sectors(mods):
+    wl = W.config_paper("go2", n_envs=128)
+    run_parity(mods, wl, 60, seed=5)
+
+
+@pytest.mark.parametrize("launch", [(1, 64, 0, 32, 1), (4, 256, 0, 64, 2), (32, 512, 16, 40, 1)])
+def test_march_launch_shapes_and_staging(mods, launch):
+    wl = W.config_paper("turtlebot2", n_envs=97)
+    run_parity(mods, wl, 30, seed=6, launch=launch)
+
+
+def test_march_split_step(mods):
+    wl = W.config_paper("turtlebot2", n_envs=300)
+    sim, _, _ = run_parity(mods, wl, 40, seed=7, launch=(0, 0, 0, 0, 0, 1))
+    assert sim.get_launch()[5] == 1
+
+
+def test_march_with_moving_discs_raw_beams(mods):
+    """March with the moving-disc layer (t-gated per ray), raw 360-beam
+    observation, two map sizes."""
+    wl = _mixed()
+    wl.params = W.Params(sensor=1, march_step=0.03, n_dyn=6, goal_dmin=1.0, goal_dmax=1e9)
+    run_parity(mods, wl, 40, seed=8)
+
+
+def test_march_long_step(mods):
+    """A step longer than a cell (samples may skip cells): the explicit
+    off-map test keeps the march inside the map."""
+    wl = W.config_small()
+    wl.params = W.Params(goal_dmin=1.0, goal_dmax=1e9, sensor=1, march_step=0.13)
+    run_parity(mods, wl, 100, seed=9)
+
+
+@pytest.mark.parametrize("m", [1, 12, 360])
+def test_exact_traversal_with_sectors(mods, m):
+    wl = W.config_throughput(n_envs=512, n_maps=4)
+    wl.params = W.Params(n_sectors=m)
+    run_parity(mods, wl, 20, seed=10)
+
+
+def test_sector_count_must_divide_the_beams(mods):
+    flashnav, _, _ = mods
+    wl = W.config_small()
+    wl.params = W.Params(goal_dmin=1.0, goal_dmax=1e9, n_sectors=7)  # 180 % 7 != 0
+    with pytest.raises(flashnav.NavError):
+        flashnav.NavSim.from_workload(wl)
