@@ -260,6 +260,17 @@ int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m,
  * Weights in host order [W1 (hidden x obs_dim, row-major), b1, W2, b2, W3, b3]. */
 typedef struct nav_policy nav_policy;
 int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out);
+
+/* Like nav_policy_create with n_hidden (1..4) hidden layers of `hidden`
+ * units (any width; Table 3's actor is (100) x 4) and, if ipap_features > 0,
+ * the IPAPRec input transform of Eq. 2 on the first ipap_features
+ * observation features (the range readings): x = 1 / (l - beta), with
+ * beta = ipap_beta (< 0) until a trainer's nav_trainer_sync_policy copies
+ * its trained beta.  Any per-feature input scale multiplies after it. */
+int nav_policy_create_ex(int obs_dim, int hidden, int n_hidden, int ipap_features,
+                         float ipap_beta, int max_batch, uint64_t seed, nav_policy **out);
+/* The policy's current beta of Eq. 2 (synchronous). */
+int nav_policy_get_beta(const nav_policy *p, float *beta_host);
 void nav_policy_free(nav_policy *p);
 int64_t nav_policy_num_params(const nav_policy *p);
 int nav_policy_get_weights(nav_policy *p, float *host);       /* synchronous */
@@ -312,6 +323,14 @@ int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t se
  * alpha logpi - min_i m_i every policy_freq critic updates; log alpha by Adam
  * towards target_entropy.  BF16 tensor-core GEMMs (tcgen05) with FP32 master
  * weights and FP32 Adam. */
+/* n_hidden hidden layers of `hidden` units in every network (1..4).
+ * weight_decay: decoupled (AdamW, Table 3) decay of weights and biases,
+ * p <- p (1 - lr wd) before each Adam step; 0 = Adam.
+ * ipap_features > 0: Eq. 2 on the first ipap_features observation features
+ * of every network's input, x = 1 / (l - beta) with one trainable beta
+ * (initial ipap_beta_init), stored raw in the replay and transformed when a
+ * batch is drawn; beta descends the actor loss by Adam (lr_actor) and is
+ * kept <= ipap_beta_max < 0 so that l - beta > 0 for every range l >= 0. */
 typedef struct {
     int obs_dim, hidden, batch;
     long long replay_capacity;
@@ -319,12 +338,18 @@ typedef struct {
         huber_delta, alpha_init, target_entropy;
     int policy_freq;
     uint64_t seed;
+    int n_hidden;
+    float weight_decay;
+    int ipap_features;
+    float ipap_beta_init, ipap_beta_max;
 } nav_train_cfg;
 typedef struct nav_trainer nav_trainer;
-void nav_train_default_cfg(nav_train_cfg *c); /* obs 364, hidden 256, batch 4096, replay 4 Mi,
-                                                 lr 3e-4, betas (0.9, 0.95), gamma 0.99, tau 0.1,
-                                                 tau_b 0.005, reward scale 0.4, Huber 50,
-                                                 alpha 0.001, target entropy -1, policy freq 2 */
+void nav_train_default_cfg(nav_train_cfg *c); /* obs 364, hidden 256 x 2, batch 4096, replay
+                                                 4 Mi, lr 3e-4, betas (0.9, 0.95), gamma 0.99,
+                                                 tau 0.1, tau_b 0.005, reward scale 0.4,
+                                                 Huber 50, alpha 0.001, target entropy -1,
+                                                 policy freq 2, no weight decay, no Eq. 2
+                                                 (beta -0.2 initial, <= -0.01) */
 int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out); /* synchronous */
 void nav_trainer_free(nav_trainer *t);
 const char *nav_trainer_last_error(const nav_trainer *t);
@@ -353,7 +378,8 @@ int nav_trainer_sync_policy(nav_trainer *t, nav_policy *p, void *stream);
  * critic 1, critic 2, target 1, target 2 (order as nav_policy weights; set=1
  * writes); 10..12 = last gradients of actor, critic 1, critic 2; 20 batch
  * indices, 21 actor-update noise, 22 next-action noise, 23 target noise,
- * 24 scalars (log alpha, sbar, ...), 25 y, 26 y_mean, 27 critic-1 outputs,
+ * 24 scalars (16 floats: [0] log alpha, [1] sbar, [11] last gradient of Eq. 2's
+ * beta, [12] beta), 25 y, 26 y_mean, 27 critic-1 outputs,
  * 28 logpi of the actor update, 29 its actions, 30 actor outputs, 31 logpi of
  * the next actions. */
 int nav_trainer_io(nav_trainer *t, int what, int set, void *host);

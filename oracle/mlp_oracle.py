@@ -7,6 +7,10 @@ benchmark; it never imports the CUDA package.  Plain numpy in binary64; the
 matrix product is the only library primitive.
 
 Readings (the paper states FastDSAC only in prose):
+* Eq. 2 (IPAPRec): one trainable beta shared by the agent's networks, moved
+  by the actor loss only (the critics see the transformed input with beta
+  held fixed), kept below a negative bound so that l - beta > 0;
+* AdamW (Table 3): decoupled decay on weights and biases alike;
 * hidden activation LeakyReLU with slope 0.01;
 * actor head: mean u (2) and raw log-std r (2); log sigma = LS_MIN +
   (LS_MAX - LS_MIN) (tanh(r) + 1) / 2 with [LS_MIN, LS_MAX] = [-5, 0]
@@ -84,6 +88,32 @@ def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.95, eps=1e-8):
     mh = m / (1.0 - b1 ** t)
     vh = v / (1.0 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def adamw_step(p, g, m, v, t, lr, b1=0.9, b2=0.95, wd=0.0, eps=1e-8):
+    """AdamW (Loshchilov & Hutter 2019, decoupled decay; Table 3's optimiser):
+    p <- p (1 - lr wd), then the Adam step of adam_step."""
+    return adam_step(p * (1.0 - lr * wd), g, m, v, t, lr, b1, b2, eps)
+
+
+# ---------------------------------------------------------------------------
+# IPAPRec input transform (Eq. 2): l_hat = 1 / (l - beta), beta trainable
+# ---------------------------------------------------------------------------
+def ipap_forward(x, n, beta, scale=None):
+    """Network input from observation rows x [B, D]: the first n features
+    become 1 / (l - beta); then every feature is multiplied by scale."""
+    out = np.array(x, np.float64, copy=True)
+    out[:, :n] = 1.0 / (out[:, :n] - beta)
+    if scale is not None:
+        out = out * scale
+    return out
+
+
+def ipap_beta_grad(dx, x, n, beta, scale=None):
+    """dL/dbeta from dL/d(input) dx [B, D]: d/dbeta of s / (l - beta) is
+    s / (l - beta)^2."""
+    s = np.ones(n) if scale is None else np.asarray(scale, np.float64)[:n]
+    return float((dx[:, :n] * s / (x[:, :n] - beta) ** 2).sum())
 
 
 # ---------------------------------------------------------------------------

@@ -48,7 +48,7 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
                                 const float *__restrict__ obs_next,
                                 const float *__restrict__ final_obs, int E, int od, int ld,
                                 long long head, long long cap, const float *__restrict__ scale,
-                                bf16 *r_obs, bf16 *r_next, float *r_act, float *r_rew,
+                                int ipap, bf16 *r_obs, bf16 *r_next, float *r_act, float *r_rew,
                                 float *r_term) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)E * ld) return;
@@ -56,7 +56,9 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
     const long long slot = (head + e) % cap;
     const bool ended = (done[e] & 3) != 0;
     const float *nxt = (ended && final_obs) ? final_obs : obs_next;
-    const float sc = (scale && c < od) ? scale[c] : 1.0f;
+    // features under Eq. 2 are stored raw (beta changes while they sit in the
+    // replay); the transform and their scale are applied when a batch is drawn
+    const float sc = (scale && c < od && c >= ipap) ? scale[c] : 1.0f;
     r_obs[slot * ld + c] = __float2bfloat16_rn(c < od ? obs[(long long)e * od + c] * sc : 0.0f);
     r_next[slot * ld + c] = __float2bfloat16_rn(c < od ? nxt[(long long)e * od + c] * sc : 0.0f);
     if (c == 0) {
@@ -75,22 +77,40 @@ __global__ void k_sample(int *idx, int B, long long size, unsigned long long see
     idx[b] = (int)(((h >> 32) * (unsigned long long)size) >> 32);
 }
 
-// batch rows: Xo = obs, Xn = next obs (BF16 [B][ld]); Xc = [obs, act] ([B][ldc])
+// Eq. 2 on a stored raw range: s / (l - beta), rounded to BF16
+__device__ __forceinline__ bf16 ipap_in(bf16 l, float beta, const float *scale, int c) {
+    const float x = 1.0f / (__bfloat162float(l) - beta);
+    return __float2bfloat16_rn(scale ? x * scale[c] : x);
+}
+
+// batch rows: Xo = obs, Xn = next obs (BF16 [B][ld]); Xc = [obs, act] ([B][ldc]);
+// the first ipap features go through Eq. 2 with the current beta, and their
+// raw ranges of obs are kept in Lraw [B][ipap] for the gradient of beta
 __global__ void k_gather(const int *__restrict__ idx, const bf16 *__restrict__ r_obs,
                          const bf16 *__restrict__ r_next, const float *__restrict__ r_act,
                          const float *__restrict__ r_rew, const float *__restrict__ r_term, int B,
-                         int od, int ld, int ldc, bf16 *Xo, bf16 *Xn, bf16 *Xc, float *rew,
-                         float *term) {
+                         int od, int ld, int ldc, int ipap, const float *__restrict__ beta_dev,
+                         const float *__restrict__ scale, bf16 *Xo, bf16 *Xn, bf16 *Xc,
+                         float *Lraw, float *rew, float *term) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * ldc) return;
     const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
     const long long s = idx[b];
+    const float beta = ipap > 0 ? *beta_dev : 0.0f;
+    bf16 xo = __float2bfloat16_rn(0.0f);
     if (c < ld) {
-        Xo[(long long)b * ld + c] = r_obs[s * ld + c];
-        Xn[(long long)b * ld + c] = r_next[s * ld + c];
+        xo = r_obs[s * ld + c];
+        bf16 xn = r_next[s * ld + c];
+        if (c < ipap) {
+            Lraw[(long long)b * ipap + c] = __bfloat162float(xo);
+            xo = ipap_in(xo, beta, scale, c);
+            xn = ipap_in(xn, beta, scale, c);
+        }
+        Xo[(long long)b * ld + c] = xo;
+        Xn[(long long)b * ld + c] = xn;
     }
     bf16 v = __float2bfloat16_rn(0.0f);
-    if (c < od) v = r_obs[s * ld + c];
+    if (c < od) v = xo;
     else if (c < od + 2) v = __float2bfloat16_rn(r_act[s * 2 + (c - od)]);
     Xc[(long long)b * ldc + c] = v;
     if (c == 0) {
@@ -255,19 +275,20 @@ __global__ void k_grad_to_bf16(const float *__restrict__ g, int B, int n, int ld
 }
 
 // dZ = dH * leaky'(z) with the sign of z read from the activation h = leaky(z);
-// writes dZ in place (FP32), as BF16 [B][H] and as BF16 [H][B] (32 x 32 tiles)
-__global__ void k_leaky_bwd(float *dH, const bf16 *__restrict__ h, int B, int H, bf16 *dZ16,
-                            bf16 *dZT16) {
+// writes dZ in place (FP32 [B][H]), as BF16 [B][ldh] and as BF16 [H][B]
+// (32 x 32 tiles); h is BF16 [B][ldh]
+__global__ void k_leaky_bwd(float *dH, const bf16 *__restrict__ h, int B, int H, int ldh,
+                            bf16 *dZ16, bf16 *dZT16) {
     __shared__ bf16 t[32][33];
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         const int r = r0 + j, c = c0 + threadIdx.x;
         if (r < B && c < H) {
-            const long long o = (long long)r * H + c;
-            const float d = dH[o] * (__bfloat162float(h[o]) > 0.0f ? 1.0f : 0.01f);
+            const long long o = (long long)r * H + c, oh = (long long)r * ldh + c;
+            const float d = dH[o] * (__bfloat162float(h[oh]) > 0.0f ? 1.0f : 0.01f);
             dH[o] = d;
             const bf16 v = __float2bfloat16_rn(d);
-            dZ16[o] = v;
+            dZ16[oh] = v;
             t[j][threadIdx.x] = v;
         }
     }
@@ -295,11 +316,12 @@ __global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) 
 }
 
 // ----------------------------------------------------------- optimiser ---
-// Adam (bias-corrected, no weight decay); weights also refresh their BF16
-// copies W16 [out][ld_in] and WT16 [in][ld_out] (pass null for biases).
+// Adam (bias-corrected) with decoupled weight decay wd (AdamW: p <- p (1 -
+// lr wd), then the Adam step; wd = 0 is plain Adam); weights also refresh
+// their BF16 copies W16 [out][ld_in] and WT16 [in][ld_out] (null for biases).
 __global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v, int n, float lr,
-                       float b1, float b2, float c1, float c2, int in, bf16 *W16, int ld_in,
-                       bf16 *WT16, int ld_out) {
+                       float b1, float b2, float c1, float c2, float wd, int in, bf16 *W16,
+                       int ld_in, bf16 *WT16, int ld_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -307,7 +329,8 @@ __global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    const float pd = wd != 0.0f ? p[i] * (1.0f - lr * wd) : p[i];
+    const float pi = pd - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
     p[i] = pi;
     if (W16) {
         const int o = i / in, k = i - o * in;
@@ -331,6 +354,37 @@ __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc
     *am = mi;
     *av = vi;
     *log_alpha -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// dL/dbeta of Eq. 2 through the actor's input: x = s / (l - beta) gives
+// dx/dbeta = s / (l - beta)^2; summed over the batch into *acc
+__global__ void k_beta_grad(const float *__restrict__ dX, int ldx, const float *__restrict__ Lraw,
+                            int B, int ipap, const float *__restrict__ beta_dev,
+                            const float *__restrict__ scale, float *acc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float g = 0.0f;
+    if (i < (long long)B * ipap) {
+        const int b = (int)(i / ipap), c = (int)(i - (long long)b * ipap);
+        const float d = Lraw[i] - *beta_dev;
+        g = dX[(long long)b * ldx + c] * (scale ? scale[c] : 1.0f) / (d * d);
+    }
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, g);
+}
+
+// Adam step on beta (s[0] beta, s[1..2] moments, s[3] gradient, cleared and
+// kept in s[-1]), then beta <- min(beta, beta_max) so that l - beta > 0 for
+// every range l >= 0
+__global__ void k_beta_adam(float *s, float lr, float b1, float b2, float c1, float c2,
+                            float beta_max) {
+    const float g = s[3];
+    s[-1] = g;
+    const float mi = b1 * s[1] + (1.0f - b1) * g;
+    const float vi = b2 * s[2] + (1.0f - b2) * g * g;
+    s[1] = mi;
+    s[2] = vi;
+    s[0] = fminf(s[0] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f), beta_max);
+    s[3] = 0.0f;
 }
 
 __global__ void k_zero(float *p, int n) {
@@ -386,7 +440,7 @@ using namespace flashnav;
 
 struct nav_trainer {
     nav_train_cfg cfg{};
-    int od = 0, ld = 0, ldc = 0, H = 0, B = 0;
+    int od = 0, ld = 0, ldc = 0, H = 0, Hp = 0, NH = 0, B = 0, ipap = 0;
     long long cap = 0, size = 0, head = 0;
     unsigned long long n_critic = 0, n_actor = 0, n_alpha = 0;
     Mlp actor, q[2], qt[2];
@@ -400,8 +454,9 @@ struct nav_trainer {
     bf16 *Xo = nullptr, *Xn = nullptr, *Xc = nullptr, *Xnc = nullptr, *Xa = nullptr;
     bf16 *XoT = nullptr, *XcT = nullptr;
     float *rew = nullptr, *term = nullptr;
-    // activations: [0] actor, [1] q0, [2] q1, [3] scratch
-    bf16 *h16[4][2] = {}, *ht16[4][2] = {};
+    // activations per hidden layer: [0] actor, [1] q0, [2] q1, [3] scratch
+    bf16 *h16[4][kMaxLayers - 1] = {}, *ht16[4][kMaxLayers - 1] = {};
+    float *Lraw = nullptr, *dXa = nullptr; // raw Eq. 2 ranges of obs; actor input gradient
     float *out_a = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
     float *a_next = nullptr, *logp_next = nullptr, *a_new = nullptr, *logp_new = nullptr,
           *eps_new = nullptr, *eps_next = nullptr;
@@ -409,7 +464,9 @@ struct nav_trainer {
           *dout = nullptr;
     float *dH = nullptr, *dX[2] = {};
     bf16 *g16 = nullptr, *gT16 = nullptr, *dZ16 = nullptr, *dZT16 = nullptr;
-    float *scal = nullptr; // [0] log_alpha [1] sbar [2..3] alpha Adam [4..7] critic acc [8..9] actor acc
+    float *scal = nullptr; // [0] log_alpha [1] sbar [2..3] alpha Adam [4..7] critic acc
+                           // [8..9] actor acc [11] last beta gradient [12] beta
+                           // [13..14] its Adam moments [15] its gradient accumulator
     int *status = nullptr;
     // evaluation
     unsigned char *ev_fin = nullptr, *ev_succ = nullptr;
@@ -436,40 +493,43 @@ int tfail(nav_trainer *t, int code, const std::string &m) {
     return code;
 }
 
-// Backward through a 3-layer MLP from dL/dout (FP32 [B][n_out]).  `s` holds
-// the saved activations (BF16 and transposed), XT the transposed input.
-// wgrad: fill layer gradients; dX: input gradient FP32 [B][ldx] (may be null).
+// Backward through an MLP from dL/dout (FP32 [B][n_out], n_out <= 8).  `s`
+// holds the saved hidden activations (BF16 [B][Hp] and transposed [H][B]),
+// XT the transposed input [in][B].  wgrad: fill the layer gradients; dX:
+// input gradient FP32 [B][ldx] (may be null).  Per layer, top down: weight
+// gradient dZ^T x_in (split-K GEMM over the batch), bias gradient (column
+// sums), then the gradient of the layer's input dZ W, gated by LeakyReLU'
+// into the next dZ.
 int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 *XT, bool wgrad,
                  float *dX, int ldx, cudaStream_t st) {
-    const int B = T->B, H = T->H;
-    Layer &L3 = net.layer[2], &L2 = net.layer[1], &L1 = net.layer[0];
-    const int n_out = L3.out;
+    const int B = T->B, H = T->H, Hp = T->Hp;
+    const int last = net.n_layers - 1;
+    const int n_out = net.layer[last].out;
     int rc = 0;
     k_grad_to_bf16<<<blocks((long long)B * 8), 256, 0, st>>>(dout, B, n_out, 8, T->g16, T->gT16);
-    if (wgrad) {
-        rc |= launch_gemm_bf16_splitk(T->gT16, B, T->ht16[s][1], B, n_out, H, B, L3.gW, H,
-                                      T->status, st);
-        k_colsum<<<blocks(n_out, 32), dim3(32, 8), 0, st>>>(dout, B, n_out, L3.gb);
-    }
-    rc |= launch_gemm_bf16(T->g16, 8, L3.WT16, L3.ld_out, B, H, n_out, nullptr, 0, T->dH, H,
-                           nullptr, 0, nullptr, 0, T->status, st);
     const dim3 tb(32, 8), tg((H + 31) / 32, (B + 31) / 32);
-    k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][1], B, H, T->dZ16, T->dZT16);
-    if (wgrad) {
-        rc |= launch_gemm_bf16_splitk(T->dZT16, B, T->ht16[s][0], B, H, H, B, L2.gW, H,
-                                      T->status, st);
-        k_colsum<<<blocks(H, 32), dim3(32, 8), 0, st>>>(T->dH, B, H, L2.gb);
+    for (int l = last; l >= 0; --l) {
+        Layer &L = net.layer[l];
+        const bool top = l == last;
+        const bf16 *G = top ? T->g16 : T->dZ16;
+        const int ldg = top ? 8 : Hp;
+        const bf16 *GT = top ? T->gT16 : T->dZT16;
+        const float *G32 = top ? dout : T->dH;
+        const bf16 *inT = l == 0 ? XT : T->ht16[s][l - 1];
+        if (wgrad) {
+            rc |= launch_gemm_bf16_splitk(GT, B, inT, B, L.out, L.in, B, L.gW, L.in, T->status,
+                                          st);
+            k_colsum<<<blocks(L.out, 32), dim3(32, 8), 0, st>>>(G32, B, L.out, L.gb);
+        }
+        if (l > 0) {
+            rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, H, L.out, nullptr, 0, T->dH, H,
+                                   nullptr, 0, nullptr, 0, T->status, st);
+            k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][l - 1], B, H, Hp, T->dZ16, T->dZT16);
+        } else if (dX) {
+            rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, L.in, L.out, nullptr, 0, dX, ldx,
+                                   nullptr, 0, nullptr, 0, T->status, st);
+        }
     }
-    rc |= launch_gemm_bf16(T->dZ16, H, L2.WT16, L2.ld_out, B, H, H, nullptr, 0, T->dH, H, nullptr,
-                           0, nullptr, 0, T->status, st);
-    k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][0], B, H, T->dZ16, T->dZT16);
-    if (wgrad) {
-        rc |= launch_gemm_bf16_splitk(T->dZT16, B, XT, B, H, L1.in, B, L1.gW, L1.in, T->status, st);
-        k_colsum<<<blocks(H, 32), dim3(32, 8), 0, st>>>(T->dH, B, H, L1.gb);
-    }
-    if (dX)
-        rc |= launch_gemm_bf16(T->dZ16, H, L1.WT16, L1.ld_out, B, L1.in, H, nullptr, 0, dX, ldx,
-                               nullptr, 0, nullptr, 0, T->status, st);
     rc |= (int)cudaGetLastError();
     return rc;
 }
@@ -480,11 +540,12 @@ int adam_net(nav_trainer *T, Mlp &net, float lr, unsigned long long step, cudaSt
     for (int l = 0; l < net.n_layers; ++l) {
         Layer &L = net.layer[l];
         const int nw = L.in * L.out;
-        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, c1, c2, L.in,
-                                           static_cast<bf16 *>(L.W16), L.ld_in,
+        const float wd = T->cfg.weight_decay;
+        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, c1, c2, wd,
+                                           L.in, static_cast<bf16 *>(L.W16), L.ld_in,
                                            static_cast<bf16 *>(L.WT16), L.ld_out);
-        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, c1, c2, 0,
-                                              nullptr, 0, nullptr, 0);
+        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, c1, c2,
+                                              wd, 0, nullptr, 0, nullptr, 0);
     }
     return (int)cudaGetLastError();
 }
@@ -511,8 +572,11 @@ int copy_net(Mlp &dst, const Mlp &src) {
 // forward with saved activations (slot s) of a network on BF16 input x
 int fwd(nav_trainer *T, const Mlp &net, const bf16 *x, int s, bool save_t, float *out,
         cudaStream_t st) {
-    void *h[2] = {T->h16[s][0], T->h16[s][1]};
-    void *ht[2] = {T->ht16[s][0], T->ht16[s][1]};
+    void *h[kMaxLayers - 1], *ht[kMaxLayers - 1];
+    for (int l = 0; l < kMaxLayers - 1; ++l) {
+        h[l] = T->h16[s][l];
+        ht[l] = T->ht16[s][l];
+    }
     return net.forward_tc(x, T->B, h, save_t ? ht : nullptr, out, T->status, st);
 }
 
@@ -540,6 +604,11 @@ void nav_train_default_cfg(nav_train_cfg *c) {
     c->target_entropy = -1.0f;
     c->policy_freq = 2;
     c->seed = 1;
+    c->n_hidden = 2;
+    c->weight_decay = 0.0f;
+    c->ipap_features = 0;
+    c->ipap_beta_init = -0.2f;
+    c->ipap_beta_max = -0.01f;
 }
 
 void nav_trainer_free(nav_trainer *t) {
@@ -560,9 +629,12 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     nav_train_cfg c;
     if (cfg) c = *cfg;
     else nav_train_default_cfg(&c);
-    if (c.obs_dim <= 0 || c.hidden <= 0 || c.hidden % 32 || c.batch < 128 || c.batch % 128 ||
+    if (c.obs_dim <= 0 || c.hidden <= 0 || c.batch < 128 || c.batch % 128 ||
         c.replay_capacity < c.batch || c.replay_capacity > ((long long)1 << 31) ||
-        c.policy_freq < 1)
+        c.policy_freq < 1 || c.n_hidden < 1 || c.n_hidden > kMaxLayers - 1 ||
+        !(c.weight_decay >= 0.0f) || c.ipap_features < 0 || c.ipap_features > c.obs_dim ||
+        (c.ipap_features > 0 &&
+         !(c.ipap_beta_max < 0.0f && c.ipap_beta_init <= c.ipap_beta_max)))
         return NAV_E_INVAL;
     nav_trainer *T = new (std::nothrow) nav_trainer();
     if (!T) return NAV_E_NOMEM;
@@ -571,12 +643,22 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     T->ld = (c.obs_dim + 7) / 8 * 8;
     T->ldc = (c.obs_dim + 2 + 7) / 8 * 8;
     T->H = c.hidden;
+    T->Hp = act_ld(c.hidden);
+    T->NH = c.n_hidden;
+    T->ipap = c.ipap_features;
     T->B = c.batch;
     T->cap = c.replay_capacity;
-    int rc = T->actor.init({T->od, T->H, T->H, 4}, c.seed * 4 + 1, T->err);
+    std::vector<int> sa(1, T->od), sq(1, T->od + 2);
+    for (int l = 0; l < T->NH; ++l) {
+        sa.push_back(T->H);
+        sq.push_back(T->H);
+    }
+    sa.push_back(4);
+    sq.push_back(2);
+    int rc = T->actor.init(sa, c.seed * 4 + 1, T->err);
     for (int i = 0; i < 2 && rc == NAV_OK; ++i) {
-        rc = T->q[i].init({T->od + 2, T->H, T->H, 2}, c.seed * 4 + 2 + i, T->err);
-        if (rc == NAV_OK) rc = T->qt[i].init({T->od + 2, T->H, T->H, 2}, c.seed * 4 + 2 + i, T->err);
+        rc = T->q[i].init(sq, c.seed * 4 + 2 + i, T->err);
+        if (rc == NAV_OK) rc = T->qt[i].init(sq, c.seed * 4 + 2 + i, T->err);
     }
     cudaError_t e = rc == NAV_OK ? cudaSuccess : cudaErrorUnknown;
     const long long B = T->B, H = T->H;
@@ -597,10 +679,12 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->rew, B);
     TA(T->term, B);
     for (int s = 0; s < 4; ++s)
-        for (int l = 0; l < 2; ++l) {
-            TA(T->h16[s][l], B * H);
+        for (int l = 0; l < T->NH; ++l) {
+            TA(T->h16[s][l], B * T->Hp);
             TA(T->ht16[s][l], B * H);
         }
+    TA(T->Lraw, B * std::max(T->ipap, 1));
+    TA(T->dXa, B * T->ld);
     TA(T->out_a, B * 4);
     for (int i = 0; i < 2; ++i) {
         TA(T->qo[i], B * 2);
@@ -623,7 +707,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->dH, B * H);
     TA(T->g16, B * 8);
     TA(T->gT16, 8 * B);
-    TA(T->dZ16, B * H);
+    TA(T->dZ16, B * T->Hp);
     TA(T->dZT16, B * H);
     TA(T->scal, 16);
     TA(T->status, 1);
@@ -636,6 +720,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     copy_net(T->qt[1], T->q[1]);
     float init[2] = {std::log(c.alpha_init), 1.0f};
     cudaMemcpy(T->scal, init, sizeof(init), cudaMemcpyHostToDevice);
+    cudaMemcpy(T->scal + 12, &c.ipap_beta_init, 4, cudaMemcpyHostToDevice);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         nav_trainer_free(T);
         return NAV_E_CUDA;
@@ -655,7 +740,7 @@ int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_replay_insert<<<blocks((long long)n_envs * T->ld), 256, 0, st>>>(
         obs_dev, act_dev, rew_dev, done_dev, next_obs_dev, final_obs_dev, n_envs, T->od, T->ld,
-        T->head, T->cap, T->scale, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
+        T->head, T->cap, T->scale, T->ipap, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
     T->head = (T->head + n_envs) % T->cap;
     T->size = std::min(T->cap, T->size + n_envs);
     return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
@@ -674,7 +759,7 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
         k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->size, c.seed, un);
         k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
             T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
-            T->Xo, T->Xn, T->Xc, T->rew, T->term);
+            T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
         const dim3 tb(32, 8);
         k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
             T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
@@ -718,10 +803,18 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
                                    st);
             k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
-            rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true, nullptr, 0, st);
+            rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
+                               T->ipap > 0 ? T->dXa : nullptr, T->ld, st);
             rc |= adam_net(T, T->actor, c.lr_actor, an + 1, st);
             const float c1 = 1.0f - powf(c.beta1, (float)(an + 1));
             const float c2 = 1.0f - powf(c.beta2, (float)(an + 1));
+            if (T->ipap > 0) {
+                // Eq. 2's beta trained with the actor (same Adam settings)
+                k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
+                    T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
+                k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2, c1, c2,
+                                             c.ipap_beta_max);
+            }
             k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
                                      c.target_entropy, c.lr_alpha, c.beta1, c.beta2, c1, c2);
             T->n_actor++;
@@ -775,8 +868,11 @@ int nav_trainer_set_input_scale(nav_trainer *T, const float *scale_host) {
 
 int nav_trainer_sync_policy(nav_trainer *T, nav_policy *p, void *stream) {
     Mlp *dst = p ? policy_actor(p) : nullptr;
-    if (!T || !dst || dst->n_layers != T->actor.n_layers) return NAV_E_INVAL;
+    if (!T || !dst || dst->n_layers != T->actor.n_layers || policy_ipap(p) != T->ipap)
+        return NAV_E_INVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T->ipap > 0)
+        cudaMemcpyAsync(policy_beta(p), T->scal + 12, 4, cudaMemcpyDeviceToDevice, st);
     for (int l = 0; l < dst->n_layers; ++l) {
         const Layer &S = T->actor.layer[l];
         Layer &D = dst->layer[l];

@@ -35,25 +35,44 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// Network input feature c of an observation row: Eq. 2's 1 / (l - beta) for
+// the first ipap features, then the per-feature scale.
+__device__ __forceinline__ float in_feature(const float *src, int c, const float *scale, int ipap,
+                                            float beta) {
+    float x = src[c];
+    if (c < ipap) x = 1.0f / (x - beta);
+    return scale ? x * scale[c] : x;
+}
+
 // one thread per 4 columns of a row: FP32 -> BF16, zero beyond dim
 __global__ void obs_to_bf16(const float *__restrict__ obs, int n, int dim, long long stride,
-                            const float *__restrict__ scale, __nv_bfloat16 *out, int ld) {
+                            const float *__restrict__ scale, int ipap,
+                            const float *__restrict__ beta_dev, __nv_bfloat16 *out, int ld) {
     const int groups = ld >> 2;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n || g >= groups) return;
     const float *src = obs + (long long)r * stride;
+    const float beta = ipap > 0 ? *beta_dev : 0.0f;
     const int c = 4 * g;
     float v[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        v[k] = c + k < dim ? (scale ? src[c + k] * scale[c + k] : src[c + k]) : 0.0f;
+    for (int k = 0; k < 4; ++k) v[k] = c + k < dim ? in_feature(src, c + k, scale, ipap, beta) : 0.0f;
     const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
     const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
     uint2 pk;
     pk.x = *reinterpret_cast<const unsigned *>(&a);
     pk.y = *reinterpret_cast<const unsigned *>(&b);
     *reinterpret_cast<uint2 *>(out + (long long)r * ld + c) = pk;
+}
+
+__global__ void obs_to_fp32(const float *__restrict__ obs, int n, int dim, long long stride,
+                            const float *__restrict__ scale, int ipap,
+                            const float *__restrict__ beta_dev, float *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * dim) return;
+    const int r = (int)(i / dim), c = (int)(i - (long long)r * dim);
+    out[i] = in_feature(obs + (long long)r * stride, c, scale, ipap, ipap > 0 ? *beta_dev : 0.0f);
 }
 
 // a = tanh(u + sigma eps) (or tanh(u)), logp per row.
@@ -246,7 +265,8 @@ int Mlp::copy_params(float *host, bool to_host) {
 }
 
 // Forward through the tensor cores: x16 [n][layer0.ld_in] BF16 -> out32 [n][out]
-// FP32; hidden activations h16[l] [n][256] and (if ht16) their transposes.
+// FP32; hidden activations h16[l] [n][act_ld(out_l)] and (if ht16) their
+// transposes [out_l][n].
 int Mlp::forward_tc(const void *x16, int n, void *const *h16, void *const *ht16, float *out32,
                     int *status, void *stream) const {
     const void *in = x16;
@@ -256,11 +276,11 @@ int Mlp::forward_tc(const void *x16, int n, void *const *h16, void *const *ht16,
         const bool last = l == n_layers - 1;
         const int rc = launch_gemm_bf16(in, ld, L.W16, L.ld_in, n, L.out, L.in, L.b, last ? 0 : 1,
                                         last ? out32 : nullptr, L.out, last ? nullptr : h16[l],
-                                        L.out, (!last && ht16) ? ht16[l] : nullptr, n, status,
-                                        stream);
+                                        act_ld(L.out), (!last && ht16) ? ht16[l] : nullptr, n,
+                                        status, stream);
         if (rc != 0) return rc;
         in = h16[l];
-        ld = L.out;
+        ld = act_ld(L.out);
     }
     return 0;
 }
@@ -283,10 +303,18 @@ int Mlp::forward_fp32(const float *x, long long ldx, int n, float *const *h32, f
 }
 
 int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, const float *scale,
-                       void *out, int ld, void *stream) {
+                       int ipap, const float *beta_dev, void *out, int ld, void *stream) {
     const dim3 tb(32, 8), grid((ld / 4 + 31) / 32, (n + 7) / 8);
     obs_to_bf16<<<grid, tb, 0, static_cast<cudaStream_t>(stream)>>>(
-        obs, n, dim, stride, scale, static_cast<__nv_bfloat16 *>(out), ld);
+        obs, n, dim, stride, scale, ipap, beta_dev, static_cast<__nv_bfloat16 *>(out), ld);
+    return (int)cudaGetLastError();
+}
+
+int launch_obs_to_fp32(const float *obs, int n, int dim, long long stride, const float *scale,
+                       int ipap, const float *beta_dev, float *out, void *stream) {
+    const long long tot = (long long)n * dim;
+    obs_to_fp32<<<(unsigned)((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        obs, n, dim, stride, scale, ipap, beta_dev, out);
     return (int)cudaGetLastError();
 }
 
@@ -303,38 +331,57 @@ using namespace flashnav;
 
 struct nav_policy {
     Mlp actor;
-    int obs_dim = 0, max_batch = 0;
+    int obs_dim = 0, max_batch = 0, n_hidden = 0, ipap = 0;
     std::string err;
     // inference scratch, sized for max_batch rows at create
-    void *x16 = nullptr, *h16[2] = {nullptr, nullptr};
-    float *out32 = nullptr, *h32[2] = {nullptr, nullptr};
+    void *x16 = nullptr, *h16[kMaxLayers - 1] = {};
+    float *x32 = nullptr, *out32 = nullptr, *h32[kMaxLayers - 1] = {};
     int *status = nullptr;
     float *scale = nullptr; // per-feature input scale (null: none)
+    float *beta = nullptr;  // Eq. 2's beta (device float), used when ipap > 0
 };
 
 namespace flashnav {
 Mlp *policy_actor(nav_policy *p) { return p ? &p->actor : nullptr; }
+int policy_ipap(const nav_policy *p) { return p ? p->ipap : 0; }
+float *policy_beta(nav_policy *p) { return p ? p->beta : nullptr; }
 } // namespace flashnav
 
 extern "C" {
 
-int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out) {
-    if (!out || obs_dim <= 0 || hidden <= 0 || hidden % 16 || max_batch <= 0) return NAV_E_INVAL;
+int nav_policy_create_ex(int obs_dim, int hidden, int n_hidden, int ipap_features,
+                         float ipap_beta, int max_batch, uint64_t seed, nav_policy **out) {
+    if (!out || obs_dim <= 0 || hidden <= 0 || n_hidden < 1 || n_hidden > kMaxLayers - 1 ||
+        max_batch <= 0 || ipap_features < 0 || ipap_features > obs_dim ||
+        (ipap_features > 0 && !(ipap_beta < 0.0f)))
+        return NAV_E_INVAL;
     *out = nullptr;
     nav_policy *p = new (std::nothrow) nav_policy();
     if (!p) return NAV_E_NOMEM;
     p->obs_dim = obs_dim;
     p->max_batch = max_batch;
-    int rc = p->actor.init({obs_dim, hidden, hidden, 4}, seed, p->err);
+    p->n_hidden = n_hidden;
+    p->ipap = ipap_features;
+    std::vector<int> sizes(1, obs_dim);
+    for (int l = 0; l < n_hidden; ++l) sizes.push_back(hidden);
+    sizes.push_back(4);
+    int rc = p->actor.init(sizes, seed, p->err);
     cudaError_t e = cudaSuccess;
-    const int ld0 = (obs_dim + 7) / 8 * 8;
     if (rc == NAV_OK) {
-        e = cudaMalloc(&p->x16, (size_t)max_batch * ld0 * 2);
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&p->h16[i], (size_t)max_batch * hidden * 2);
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&p->h32[i], (size_t)max_batch * hidden * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&p->out32, (size_t)max_batch * 4 * 4);
+        const size_t mb = (size_t)max_batch;
+        e = cudaMalloc(&p->x16, mb * act_ld(obs_dim) * 2);
+        if (e == cudaSuccess) e = cudaMemset(p->x16, 0, mb * act_ld(obs_dim) * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&p->x32, mb * obs_dim * 4);
+        for (int i = 0; i < n_hidden && e == cudaSuccess; ++i) {
+            e = cudaMalloc(&p->h16[i], mb * act_ld(hidden) * 2);
+            if (e == cudaSuccess) e = cudaMemset(p->h16[i], 0, mb * act_ld(hidden) * 2);
+            if (e == cudaSuccess) e = cudaMalloc(&p->h32[i], mb * hidden * 4);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&p->out32, mb * 4 * 4);
         if (e == cudaSuccess) e = cudaMalloc(&p->status, 4);
         if (e == cudaSuccess) e = cudaMemset(p->status, 0, 4);
+        if (e == cudaSuccess) e = cudaMalloc(&p->beta, 4);
+        if (e == cudaSuccess) e = cudaMemcpy(p->beta, &ipap_beta, 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = NAV_E_CUDA;
     }
     if (rc != NAV_OK) {
@@ -345,14 +392,27 @@ int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav
     return NAV_OK;
 }
 
+int nav_policy_create(int obs_dim, int hidden, int max_batch, uint64_t seed, nav_policy **out) {
+    return nav_policy_create_ex(obs_dim, hidden, 2, 0, -1.0f, max_batch, seed, out);
+}
+
 void nav_policy_free(nav_policy *p) {
     if (!p) return;
     p->actor.release();
-    void *ps[] = {p->x16, p->h16[0], p->h16[1], p->h32[0], p->h32[1], p->out32, p->status,
-                  p->scale};
+    for (int i = 0; i < kMaxLayers - 1; ++i) {
+        if (p->h16[i]) cudaFree(p->h16[i]);
+        if (p->h32[i]) cudaFree(p->h32[i]);
+    }
+    void *ps[] = {p->x16, p->x32, p->out32, p->status, p->scale, p->beta};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete p;
+}
+
+int nav_policy_get_beta(const nav_policy *p, float *beta_host) {
+    if (!p || !beta_host) return NAV_E_INVAL;
+    return cudaMemcpy(beta_host, p->beta, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? NAV_OK
+                                                                                    : NAV_E_CUDA;
 }
 
 int64_t nav_policy_num_params(const nav_policy *p) { return p ? p->actor.num_params() : NAV_E_INVAL; }
@@ -376,7 +436,8 @@ int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int 
         (mode != 0 && mode != 1))
         return NAV_E_INVAL;
     const int ld0 = p->actor.layer[0].ld_in;
-    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->scale, p->x16, ld0, stream);
+    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->scale, p->ipap, p->beta,
+                                p->x16, ld0, stream);
     if (rc == 0) rc = p->actor.forward_tc(p->x16, n, p->h16, nullptr, p->out32, p->status, stream);
     if (rc == 0) rc = launch_actor_head(p->out32, n, mode, seed, step, actions_dev, logp_dev, nullptr, stream);
     if (rc == 0 && out_dev)
@@ -391,7 +452,13 @@ int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride,
     if (!p || !obs_dev || !actions_dev || n <= 0 || n > p->max_batch || obs_stride < p->obs_dim ||
         (mode != 0 && mode != 1))
         return NAV_E_INVAL;
-    int rc = p->actor.forward_fp32(obs_dev, obs_stride, n, p->h32, p->out32, stream);
+    const bool prep = p->scale || p->ipap > 0;
+    int rc = prep ? launch_obs_to_fp32(obs_dev, n, p->obs_dim, obs_stride, p->scale, p->ipap,
+                                       p->beta, p->x32, stream)
+                  : 0;
+    if (rc == 0)
+        rc = p->actor.forward_fp32(prep ? p->x32 : obs_dev, prep ? p->obs_dim : obs_stride, n,
+                                   p->h32, p->out32, stream);
     if (rc == 0) rc = launch_actor_head(p->out32, n, mode, seed, step, actions_dev, logp_dev, nullptr, stream);
     if (rc == 0 && out_dev)
         rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice,

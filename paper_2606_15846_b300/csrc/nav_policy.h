@@ -8,7 +8,11 @@ namespace flashnav {
 
 constexpr float kLogStdMin = -5.0f; // actor log-std range (Table 4)
 constexpr float kLogStdMax = 0.0f;
-constexpr int kMaxLayers = 3;
+constexpr int kMaxLayers = 5; // up to four hidden layers and the output layer
+
+// Leading dimension (elements) of a BF16 activation row of n features: the
+// tensor-core GEMM reads K-major rows that start on 16-byte boundaries.
+inline int act_ld(int n) { return (n + 7) / 8 * 8; }
 
 // One dense layer: FP32 master weights W [out][in] and bias, BF16 copies for
 // the tensor cores (W16 [out][ld_in], WT16 [in][ld_out]), Adam moments and
@@ -35,8 +39,14 @@ struct Mlp {
                      void *stream) const;
 };
 
+// Observation rows -> network input: features c < ipap become
+// 1 / (l - beta) (Eq. 2, beta read from beta_dev), then every feature is
+// multiplied by scale[c] (if scale is set).  BF16 [n][ld] (zero pad) for the
+// tensor cores, or FP32 [n][dim] for the SIMT path.
 int launch_obs_to_bf16(const float *obs, int n, int dim, long long stride, const float *scale,
-                       void *out, int ld, void *stream);
+                       int ipap, const float *beta_dev, void *out, int ld, void *stream);
+int launch_obs_to_fp32(const float *obs, int n, int dim, long long stride, const float *scale,
+                       int ipap, const float *beta_dev, float *out, void *stream);
 int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
                       float *act, float *logp, float *eps, void *stream);
 
@@ -45,6 +55,9 @@ int launch_actor_head(const float *out4, int n, int mode, unsigned long long see
 struct nav_policy;
 namespace flashnav {
 // The actor network inside a policy handle (weights shared with a trainer
-// through nav_trainer_sync_policy).
+// through nav_trainer_sync_policy), its IPAPRec feature count and the device
+// float holding its beta.
 Mlp *policy_actor(nav_policy *p);
+int policy_ipap(const nav_policy *p);
+float *policy_beta(nav_policy *p);
 } // namespace flashnav

@@ -25,7 +25,8 @@ EXPORTS = [
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
-    "nav_policy_create", "nav_policy_free", "nav_policy_num_params", "nav_policy_get_weights",
+    "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
+    "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_rollout",
     "nav_train_default_cfg", "nav_trainer_create", "nav_trainer_free", "nav_trainer_last_error",
     "nav_train_insert", "nav_train_update", "nav_trainer_sync_policy", "nav_trainer_io",
@@ -42,7 +43,9 @@ class nav_train_cfg(C.Structure):
                 ("beta2", C.c_float), ("gamma", C.c_float), ("tau", C.c_float),
                 ("tau_b", C.c_float), ("reward_scale", C.c_float), ("huber_delta", C.c_float),
                 ("alpha_init", C.c_float), ("target_entropy", C.c_float),
-                ("policy_freq", C.c_int), ("seed", C.c_uint64)]
+                ("policy_freq", C.c_int), ("seed", C.c_uint64), ("n_hidden", C.c_int),
+                ("weight_decay", C.c_float), ("ipap_features", C.c_int),
+                ("ipap_beta_init", C.c_float), ("ipap_beta_max", C.c_float)]
 
 
 class NavError(RuntimeError):
@@ -111,6 +114,8 @@ def load():
         "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
         "nav_gemm_bf16": (I, [P, I, P, I, I, I, I, P, I, P, I, P, I, P, I, P, P]),
         "nav_policy_create": (I, [I, I, I, U64, P]),
+        "nav_policy_create_ex": (I, [I, I, I, I, C.c_float, I, U64, P]),
+        "nav_policy_get_beta": (I, [P, P]),
         "nav_policy_free": (None, [P]),
         "nav_policy_num_params": (C.c_int64, [P]),
         "nav_policy_get_weights": (I, [P, P]),

@@ -26,7 +26,12 @@ def _p(t):
 
 @dataclasses.dataclass
 class TrainConfig:
-    robot: str = "disc"
+    """setting "maps": training maps and held-out maps (one episode per map
+    scores success).  setting "paper": every env on the paper's one shared
+    map with its sensing (Sec. 2.2.1-2.2.2, Tables 7-9); success is scored on
+    n_eval fresh episodes of that map."""
+    robot: str = "disc"  # disc, rect, turtlebot2, go2
+    setting: str = "maps"
     n_envs: int = 4096
     n_train_maps: int = 64
     n_eval: int = 1000
@@ -42,10 +47,41 @@ class TrainConfig:
     threshold: float = 1.0
     seed: int = 0
     scale_inputs: bool = True
+    hidden: int = 256
+    n_hidden: int = 2
+    gamma: float = 0.99
+    weight_decay: float = 0.0
+    ipap: bool = False  # Eq. 2 on the range features, beta trained with the actor
+    steps_per_sync: int = 1
+
+
+def paper_config(robot: str = "turtlebot2", **kw) -> TrainConfig:
+    """Tables 3-4 and 7-9: 1024 envs on one shared map, 1080 beams marched at
+    0.03 m and pooled into 30 sectors, (100) x 4 networks, batch 1024,
+    gamma 0.97, AdamW 1e-3, UTD 40, learning start 8192, Eq. 2 inputs, actor
+    sync every 1 (TurtleBot2) or 2 (Go2) env steps."""
+    base = dict(robot=robot, setting="paper", n_envs=1024, batch=1024, utd=40, hidden=100,
+                n_hidden=4, gamma=0.97, weight_decay=1e-3, ipap=True, learning_starts=8192,
+                beams=1080, max_range=20.0, steps_per_sync=1 if robot == "turtlebot2" else 2)
+    base.update(kw)
+    return TrainConfig(**base)
+
+
+def _robot(cfg: TrainConfig):
+    return {"disc": W.DISC, "rect": W.RECT, "turtlebot2": W.TURTLEBOT2, "go2": W.GO2}[cfg.robot]
+
+
+def obs_features(cfg: TrainConfig) -> int:
+    """Range features per observation row (sectors in the paper setting)."""
+    return 30 if cfg.setting == "paper" else cfg.beams
 
 
 def make_workloads(cfg: TrainConfig):
-    robot = W.DISC if cfg.robot == "disc" else W.RECT
+    if cfg.setting == "paper":
+        train = W.config_paper(cfg.robot, n_envs=cfg.n_envs, beams=cfg.beams)
+        ev = W.config_paper(cfg.robot, n_envs=cfg.n_eval, beams=cfg.beams)
+        return train, ev
+    robot = _robot(cfg)
     train_maps = [W.make_map(10_000 + cfg.seed * 1000 + m, cfg.map_size, cfg.map_size,
                              float(np.random.default_rng(10_000 + m).uniform(0.10, 0.25)),
                              corridors=True) for m in range(cfg.n_train_maps)]
@@ -67,11 +103,13 @@ def make_workloads(cfg: TrainConfig):
 
 
 def input_scale(cfg: TrainConfig, robot) -> np.ndarray:
-    """Per-feature scale of the observation: ranges by r_max, goal distance by
-    8 m, bearing by pi, v and w by their bounds."""
-    sc = np.full(cfg.beams + 4, 1.0 / cfg.max_range, np.float32)
-    sc[cfg.beams:] = [1.0 / 8.0, 1.0 / np.pi, 1.0 / robot.v_max,
-                      1.0 / max(abs(robot.w_min), abs(robot.w_max))]
+    """Per-feature scale of the observation: ranges by r_max (1 under Eq. 2,
+    whose output is already O(1)), goal distance by 8 m, bearing by pi, v and
+    w by their bounds."""
+    D = obs_features(cfg)
+    sc = np.full(D + 4, 1.0 if cfg.ipap else 1.0 / cfg.max_range, np.float32)
+    sc[D:] = [1.0 / 8.0, 1.0 / np.pi, 1.0 / robot.v_max,
+              1.0 / max(abs(robot.w_min), abs(robot.w_max))]
     return sc
 
 
@@ -83,9 +121,10 @@ def evaluate_reactive(cfg: TrainConfig, log=print):
     _, eval_wl = make_workloads(cfg)
     robot = eval_wl.robots[0]
     ev = F.NavSim.from_workload(eval_wl)
+    D = obs_features(cfg)
     tc = F.nav_train_cfg()
     lib.nav_train_default_cfg(C.byref(tc))
-    tc.obs_dim, tc.batch, tc.replay_capacity = cfg.beams + 4, 128, 256
+    tc.obs_dim, tc.batch, tc.replay_capacity = D + 4, 128, 256
     T = C.c_void_p()
     assert lib.nav_trainer_create(C.byref(tc), C.byref(T)) == 0
     S = C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -96,7 +135,7 @@ def evaluate_reactive(cfg: TrainConfig, log=print):
     ev.reset(777, obs)
     assert lib.nav_eval_begin(T, cfg.n_eval, S) == 0
     for t in range(200):
-        assert lib.nav_reactive_act(_p(obs), cfg.beams + 4, cfg.n_eval, cfg.beams, 360.0,
+        assert lib.nav_reactive_act(_p(obs), D + 4, cfg.n_eval, D, eval_wl.params.fov_deg,
                                     robot.v_max, max(abs(robot.w_min), abs(robot.w_max)),
                                     _p(act), S) == 0
         ev.step(act, obs, rew, done)
@@ -113,13 +152,19 @@ def train(cfg: TrainConfig, log=print):
     train_wl, eval_wl = make_workloads(cfg)
     sim = F.NavSim.from_workload(train_wl)
     ev = F.NavSim.from_workload(eval_wl)
-    od = cfg.beams + 4
-    pol = C.c_void_p()
-    assert lib.nav_policy_create(od, 256, max(cfg.n_envs, cfg.n_eval), cfg.seed + 11,
-                                 C.byref(pol)) == 0
+    D = obs_features(cfg)
+    od = D + 4
+    ipap = D if cfg.ipap else 0
     tc = F.nav_train_cfg()
     lib.nav_train_default_cfg(C.byref(tc))
     tc.obs_dim, tc.batch, tc.replay_capacity, tc.seed = od, cfg.batch, cfg.replay, cfg.seed + 1
+    tc.hidden, tc.n_hidden, tc.gamma, tc.weight_decay = cfg.hidden, cfg.n_hidden, cfg.gamma, \
+        cfg.weight_decay
+    tc.ipap_features = ipap
+    pol = C.c_void_p()
+    assert lib.nav_policy_create_ex(od, cfg.hidden, cfg.n_hidden, ipap,
+                                    C.c_float(tc.ipap_beta_init), max(cfg.n_envs, cfg.n_eval),
+                                    cfg.seed + 11, C.byref(pol)) == 0
     T = C.c_void_p()
     rc = lib.nav_trainer_create(C.byref(tc), C.byref(T))
     if rc:
@@ -191,7 +236,8 @@ def train(cfg: TrainConfig, log=print):
             rc = lib.nav_train_update(T, cfg.utd, S)
             if rc:
                 raise F.NavError(rc, lib.nav_trainer_last_error(T).decode())
-            assert lib.nav_trainer_sync_policy(T, pol, S) == 0
+            if step % cfg.steps_per_sync == 0:
+                assert lib.nav_trainer_sync_policy(T, pol, S) == 0
         cur = nxt
         step += 1
     if reached is None and (not history or history[-1]["t"] < time.perf_counter() - t0 - 1e-3):

@@ -53,17 +53,71 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def test_one_update_matches_fp64(env):
-    from oracle import mlp_oracle as M
+def _emul_grads(M, params, x16, dout):
+    """The GPU's arithmetic with its BF16 rounding points, in FP64: forward on
+    BF16 weights with BF16 activations; backward with the upstream gradient
+    rounded to BF16 for the GEMMs (weight gradient dZ^T h, input gradient
+    dZ W) and kept unrounded for the bias sums."""
+    hs, h = [x16], x16
+    L = len(params)
+    for li, (W, b) in enumerate(params):
+        z = h @ _bf16(W).T + b
+        if li < L - 1:
+            h = _bf16(M.leaky(z))
+            hs.append(h)
+    grads = [None] * L
+    g32 = dout
+    for li in range(L - 1, -1, -1):
+        g16 = _bf16(g32)
+        grads[li] = [g16.T @ hs[li], g32.sum(axis=0)]
+        if li > 0:
+            dh = g16 @ _bf16(params[li][0])
+            g32 = dh * np.where(hs[li] > 0, 1.0, M.SLOPE)
+    return grads
+
+
+CONFIGS = {
+    # the benchmark's learner: 364-256-256-4 actor, Adam, raw ranges
+    "bench": dict(od=OD, hidden=256, n_hidden=2, wd=0.0, ipap=0, scale=False),
+    # Table 3 / Eq. 2: (100) x 4 nets, AdamW 1e-3, 30 sector minima through
+    # 1 / (l - beta), goal / velocity features scaled
+    "paper": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+def test_one_update_matches_fp64(env, name):
     flashnav, torch = env
+    run_update(flashnav, torch, name, CONFIGS[name])
+
+
+def run_update(flashnav, torch, name, P, strict=True):
+    """One learner update on the GPU replayed in FP64; returns the relative
+    errors (and asserts their bounds when strict)."""
+    from oracle import mlp_oracle as M
+    errs = {}
+
+    def check(key, val, bound):
+        errs[key] = val
+        if strict:
+            assert val < bound, (key, val, bound)
+
+    od, H, NH, ipap = P["od"], P["hidden"], P["n_hidden"], P["ipap"]
     lib = flashnav.load()
     cfg = flashnav.nav_train_cfg()
     lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.obs_dim, cfg.hidden, cfg.n_hidden = od, H, NH
     cfg.batch, cfg.replay_capacity, cfg.policy_freq, cfg.seed = 256, 2048, 1, 7
+    cfg.weight_decay, cfg.ipap_features = P["wd"], ipap
     T = C.c_void_p()
     assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
-    na = lib.nav_policy_num_params  # noqa: F841 (sizes below)
-    sa, sc = [OD, 256, 256, 4], [OD + 2, 256, 256, 2]
+    scale = None
+    if P["scale"]:
+        scale = np.ones(od, np.float32)
+        scale[ipap:] = [0.125, 1 / np.pi, 2.0, 4 / np.pi]
+        assert lib.nav_trainer_set_input_scale(T, scale.ctypes.data_as(C.c_void_p)) == 0
+    sa = [od] + [H] * NH + [4]
+    sc = [od + 2] + [H] * NH + [2]
     n_a = sum(a * b + b for a, b in zip(sa[:-1], sa[1:]))
     n_c = sum(a * b + b for a, b in zip(sc[:-1], sc[1:]))
     actor0 = _unpack(_io(lib, T, 0, n_a), sa)
@@ -72,8 +126,8 @@ def test_one_update_matches_fp64(env):
     scal0 = _io(lib, T, 24, 16)
     rng = np.random.default_rng(3)
     N = 700
-    obs = rng.uniform(0, 6, (N, OD)).astype(np.float32)
-    nxt = np.clip(obs + rng.normal(0, 0.05, (N, OD)), 0, 6).astype(np.float32)
+    obs = rng.uniform(0, 6, (N, od)).astype(np.float32)
+    nxt = np.clip(obs + rng.normal(0, 0.05, (N, od)), 0, 6).astype(np.float32)
     act = rng.uniform(-0.99, 0.99, (N, 2)).astype(np.float32)
     rew = rng.normal(0, 1, N).astype(np.float32)
     done = rng.choice([0, 0, 0, 1, 2, 5, 9], N).astype(np.uint8)
@@ -87,8 +141,30 @@ def test_one_update_matches_fp64(env):
     eps_next = _io(lib, T, 22, 2 * B).reshape(B, 2).astype(np.float64)
     zn = _io(lib, T, 23, B).astype(np.float64)
     y_gpu, ym_gpu = _io(lib, T, 25, B), _io(lib, T, 26, B)
+    scal1 = _io(lib, T, 24, 16)
     assert (idx >= 0).all() and (idx < N).all()
-    ob, nb = _bf16(obs[idx]), _bf16(nxt[idx])
+    beta0 = float(scal0[12])
+
+    def net_in(x):
+        """What the GPU feeds its networks: the replay's BF16 row (raw for the
+        Eq. 2 features, scaled for the rest), Eq. 2 and the scale, BF16."""
+        x = np.asarray(x, np.float64)
+        stored = x * (scale if scale is not None and ipap == 0 else 1.0)
+        if ipap:
+            stored = x.copy()
+            if scale is not None:
+                stored[:, ipap:] = x[:, ipap:] * scale[ipap:]
+        stored = _bf16(stored)
+        if not ipap:
+            return stored, stored
+        y = stored.copy()
+        y[:, :ipap] = 1.0 / (stored[:, :ipap] - beta0)
+        if scale is not None:
+            y[:, :ipap] *= scale[:ipap]
+        return _bf16(y), stored
+
+    ob, ob_raw = net_in(obs[idx])
+    nb, _ = net_in(nxt[idx])
     ab = _bf16(act[idx])
     rb, tb = rew[idx].astype(np.float64), (done[idx] & 1).astype(np.float64)
     alpha = float(np.exp(scal0[0]))
@@ -100,25 +176,38 @@ def test_one_update_matches_fp64(env):
     tq = [M.mlp_forward(qt0[i], xnc)[0] for i in range(2)]
     y, ym = M.critic_targets(rb, tb, tq[0], tq[1], logp_next, alpha, zn, cfg.gamma,
                              cfg.reward_scale)
-    print(f"targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
-    assert _rel(y_gpu, y) < 2e-2 and _rel(ym_gpu, ym) < 2e-2
-    # critic gradients
+    print(f"[{name}] targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
+    check("y", _rel(y_gpu, y), 2e-2)
+    check("y_mean", _rel(ym_gpu, ym), 2e-2)
+    # critic gradients: against the same arithmetic with the GPU's BF16
+    # rounding points (tight: checks the kernels), and against pure FP64
+    # (the precision cost of BF16 operands, which grows with depth)
     xc = np.concatenate([ob, ab], axis=1)
+    fp64_bound = 6e-2 if NH <= 2 else 3e-1
     for i in range(2):
         q, cache = M.mlp_forward(q0[i], xc)
         _, dq = M.critic_loss(q, y, ym, sbar, cfg.huber_delta)
         grads, _ = M.mlp_backward(q0[i], cache, dq)
+        emul = _emul_grads(M, q0[i], xc, dq)
         g_gpu = _unpack(_io(lib, T, 11 + i, n_c), sc)
-        for li, ((dW, db), (gW, gb)) in enumerate(zip(grads, g_gpu)):
+        for li, ((dW, db), (mW, mb), (gW, gb)) in enumerate(zip(grads, emul, g_gpu)):
             eW, eb = _rel(gW, dW), _rel(gb, db)
-            print(f"critic {i + 1} layer {li + 1} grad rel err W {eW:.2e} b {eb:.2e}")
-            assert eW < 6e-2 and eb < 6e-2
-    # Adam's first step on the GPU's own gradients
+            mW_, mb_ = _rel(gW, mW), _rel(gb, mb)
+            print(f"[{name}] critic {i + 1} layer {li + 1} grad rel err vs FP64 W {eW:.2e} "
+                  f"b {eb:.2e}; vs BF16-emulated W {mW_:.2e} b {mb_:.2e}")
+            check(f"q{i + 1}.W{li + 1}", eW, fp64_bound)
+            check(f"q{i + 1}.b{li + 1}", eb, fp64_bound)
+            check(f"q{i + 1}.W{li + 1}.emul", mW_, 3e-2)
+            check(f"q{i + 1}.b{li + 1}.emul", mb_, 3e-2)
+    # Adam / AdamW first step on the GPU's own gradients
     q1_post = _unpack(_io(lib, T, 1, n_c), sc)
     g1 = _unpack(_io(lib, T, 11, n_c), sc)
     for (W0, b0), (g, gb), (W1, b1) in zip(q0[0], g1, q1_post):
-        Wr, _, _ = M.adam_step(W0, g, 0 * g, 0 * g, 1, cfg.lr_critic, cfg.beta1, cfg.beta2)
-        assert np.abs(W1 - Wr).max() < 1e-6
+        Wr, _, _ = M.adamw_step(W0, g, 0 * g, 0 * g, 1, cfg.lr_critic, cfg.beta1, cfg.beta2,
+                                wd=cfg.weight_decay)
+        br, _, _ = M.adamw_step(b0, gb, 0 * gb, 0 * gb, 1, cfg.lr_critic, cfg.beta1, cfg.beta2,
+                                wd=cfg.weight_decay)
+        assert np.abs(W1 - Wr).max() < 1e-6 and np.abs(b1 - br).max() < 1e-6
     # actor gradients (critics after their Adam step, as the GPU uses them)
     q_post = [_unpack(_io(lib, T, 1 + i, n_c), sc) for i in range(2)]
     out_a, cache_a = M.mlp_forward(actor0, ob)
@@ -133,15 +222,26 @@ def test_one_update_matches_fp64(env):
     da = np.zeros((B, 2))
     for i, dqi in enumerate((dq1, dq2)):
         _, dX = M.mlp_backward(q_post[i], caches[i], np.stack([dqi, 0 * dqi], axis=1))
-        da += dX[:, OD:OD + 2]
+        da += dX[:, od:od + 2]
     dout = M.actor_head_grad(out_a, eps_new, da, dlogp)
-    grads_a, _ = M.mlp_backward(actor0, cache_a, dout)
+    grads_a, dxa = M.mlp_backward(actor0, cache_a, dout)
     g_gpu = _unpack(_io(lib, T, 10, n_a), sa)
     for li, ((dW, db), (gW, gb)) in enumerate(zip(grads_a, g_gpu)):
         eW, eb = _rel(gW, dW), _rel(gb, db)
-        print(f"actor layer {li + 1} grad rel err W {eW:.2e} b {eb:.2e}")
-        assert eW < 1e-1 and eb < 1e-1
+        print(f"[{name}] actor layer {li + 1} grad rel err W {eW:.2e} b {eb:.2e}")
+        check(f"a.W{li + 1}", eW, 1e-1)
+        check(f"a.b{li + 1}", eb, 1e-1)
+    if ipap:
+        # Eq. 2's beta: gradient through the actor's input, then one Adam step
+        gb_ref = M.ipap_beta_grad(dxa, ob_raw, ipap, beta0, scale)
+        gb_gpu = float(scal1[11])
+        print(f"[{name}] beta grad gpu {gb_gpu:.6e} fp64 {gb_ref:.6e}")
+        check("beta_grad", abs(gb_gpu - gb_ref) / (abs(gb_ref) + 1e-6), 0.1)
+        b1, _, _ = M.adam_step(np.array(beta0), np.array(gb_gpu), 0.0, 0.0, 1, cfg.lr_actor,
+                               cfg.beta1, cfg.beta2)
+        assert abs(float(scal1[12]) - min(float(b1), cfg.ipap_beta_max)) < 1e-6
     lib.nav_trainer_free(T)
+    return errs
 
 
 def test_eval_reduction_fp64(env):

@@ -190,3 +190,44 @@ def test_rollout_with_policy_matches_oracle_sim(env, oracle):
         assert np.array_equal(done.cpu().numpy(), rd)
         assert np.abs(obs.cpu().numpy() - ro).max() <= 1e-4 * 10
     lib.nav_policy_free(h)
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_paper_actor_with_ipap_against_fp64(env, fp32):
+    """Table 3's actor, (100) x 4 hidden units (a width that is not a multiple
+    of the 16-column MMA step), on 30 sector minima through Eq. 2 with
+    beta = -0.3 and a scale on the goal / velocity features; both the BF16
+    tensor-core path and the FP32 SIMT path against the FP64 oracle."""
+    from oracle import mlp_oracle as M
+    flashnav, torch = env
+    lib = flashnav.load()
+    od, n, ipap, beta = 34, 1000, 30, -0.3
+    h = C.c_void_p()
+    assert lib.nav_policy_create_ex(od, 100, 4, ipap, C.c_float(beta), n, 21, C.byref(h)) == 0
+    npar = lib.nav_policy_num_params(h)
+    sizes = [od, 100, 100, 100, 100, 4]
+    assert npar == sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:]))
+    w = np.zeros(npar, np.float32)
+    assert lib.nav_policy_get_weights(h, w.ctypes.data_as(C.c_void_p)) == 0
+    params = _unpack(w, sizes)
+    scale = np.ones(od, np.float32)
+    scale[ipap:] = [0.125, 1 / np.pi, 2.0, 4 / np.pi]
+    assert lib.nav_policy_set_input_scale(h, scale.ctypes.data_as(C.c_void_p)) == 0
+    rng = np.random.default_rng(5)
+    obs = np.concatenate([rng.uniform(0, 20, (n, ipap)), rng.uniform(0, 8, (n, 1)),
+                          rng.uniform(-3, 3, (n, 1)), rng.uniform(0, 0.5, (n, 1)),
+                          rng.uniform(-0.8, 0.8, (n, 1))], axis=1).astype(np.float32)
+    obs_t = torch.from_numpy(obs).cuda()
+    act = torch.empty(n, 2, device="cuda")
+    out = torch.empty(n, 4, device="cuda")
+    fn = lib.nav_policy_act_fp32 if fp32 else lib.nav_policy_act
+    assert fn(h, _p(obs_t), od, n, 0, 0, 0, _p(act), None, _p(out), None) == 0
+    b_got = C.c_float()
+    assert lib.nav_policy_get_beta(h, C.byref(b_got)) == 0 and b_got.value == np.float32(beta)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    ref, _ = M.mlp_forward(params, M.ipap_forward(obs.astype(np.float64), ipap, beta, scale))
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"paper actor ({'FP32 SIMT' if fp32 else 'BF16 tensor cores'}) rel L2 vs FP64: {rel:.2e}")
+    assert rel < (1e-5 if fp32 else 3e-2)
+    lib.nav_policy_free(h)

@@ -136,3 +136,58 @@ def test_actor_loss_gradients():
 def test_softplus_is_stable():
     assert M.softplus(np.array([800.0]))[0] == 800.0
     assert M.softplus(np.array([0.0]))[0] == pytest.approx(math.log(2.0))
+
+
+def test_adamw_without_gradient_is_pure_decay():
+    """AdamW's decay is decoupled: with a zero gradient (zero moments) the
+    step is exactly p (1 - lr wd); with wd = 0 it is Adam's step."""
+    rng = np.random.default_rng(4)
+    p = rng.normal(size=(5, 3))
+    z = np.zeros_like(p)
+    out, _, _ = M.adamw_step(p, z, z, z, 1, 3e-4, wd=1e-3)
+    np.testing.assert_allclose(out, p * (1 - 3e-7), rtol=0, atol=1e-15)
+    g = rng.normal(size=p.shape)
+    a, _, _ = M.adamw_step(p, g, z, z, 1, 3e-4, wd=0.0)
+    b, _, _ = M.adam_step(p, g, z, z, 1, 3e-4)
+    np.testing.assert_array_equal(a, b)
+    # first step: p (1 - lr wd) - lr sign(g) (Kingma & Ba: |step| = lr at t = 1)
+    c, _, _ = M.adamw_step(p, g, z, z, 1, 1e-2, wd=0.5)
+    np.testing.assert_allclose(c, p * (1 - 5e-3) - 1e-2 * np.sign(g), rtol=0, atol=1e-6)
+
+
+def test_ipap_transform_values():
+    """Eq. 2: l_hat = 1 / (l - beta); l = 0 gives -1/beta, long ranges go to
+    zero, other features pass through (then the scale applies)."""
+    x = np.array([[0.0, 1.0, 19.0, 3.5, -2.0]])
+    out = M.ipap_forward(x, 3, -0.25)
+    np.testing.assert_allclose(out[0, :3], [4.0, 0.8, 1.0 / 19.25])
+    np.testing.assert_array_equal(out[0, 3:], x[0, 3:])
+    sc = np.array([1.0, 2.0, 1.0, 0.5, 1.0])
+    np.testing.assert_allclose(M.ipap_forward(x, 3, -0.25, sc), out * sc)
+
+
+def test_ipap_beta_gradient_matches_finite_differences():
+    """dL/dbeta through Eq. 2 and a whole actor (MLP + squashed Gaussian
+    head, eps fixed), against central differences in beta."""
+    rng = np.random.default_rng(8)
+    n, D = 6, 10
+    x = np.concatenate([rng.uniform(0.1, 8.0, (5, n)), rng.normal(size=(5, D - n))], axis=1)
+    params = M.init_mlp(rng, [D, 12, 12, 4])
+    eps = rng.normal(size=(5, 2))
+    R = rng.normal(size=(5, 2))
+    sc = rng.uniform(0.5, 2.0, D)
+
+    def loss(beta):
+        out, _ = M.mlp_forward(params, M.ipap_forward(x, n, beta, sc))
+        a, logp, _ = M.actor_head(out, eps)
+        return float((a * R).sum() + 0.3 * logp.sum())
+
+    beta = -0.3
+    out, cache = M.mlp_forward(params, M.ipap_forward(x, n, beta, sc))
+    a, logp, _ = M.actor_head(out, eps)
+    dout = M.actor_head_grad(out, eps, R, np.full(5, 0.3))
+    _, dx = M.mlp_backward(params, cache, dout)
+    g = M.ipap_beta_grad(dx, x, n, beta, sc)
+    h = 1e-6
+    fd = (loss(beta + h) - loss(beta - h)) / (2 * h)
+    assert abs(g - fd) <= 1e-6 * max(1.0, abs(fd))
