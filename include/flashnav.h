@@ -288,6 +288,13 @@ int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int 
 int nav_policy_act_fp32(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n, int mode,
                         uint64_t seed, uint32_t step, float *actions_dev, float *logp_dev,
                         float *out_dev, void *stream);
+/* nav_policy_act with the noise step read from the device counter step_dev
+ * (one uint64, caller-owned; the low 32 bits are the step) and incremented
+ * after the read, so that a CUDA graph holding the call draws fresh noise on
+ * every replay. */
+int nav_policy_act_counted(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n,
+                           int mode, uint64_t seed, uint64_t *step_dev, float *actions_dev,
+                           float *logp_dev, float *out_dev, void *stream);
 
 /* Per-feature input scale (host, obs_dim floats) multiplied into the
  * observation before the network (NULL removes it).  Synchronous. */
@@ -364,8 +371,17 @@ int nav_train_insert(nav_trainer *t, const float *obs_dev, const float *act_dev,
                      const float *final_obs_dev, int n_envs, void *stream);
 
 /* n_updates gradient steps on batches drawn uniformly from the replay (needs
- * at least one batch of transitions), asynchronous on `stream`. */
+ * at least one batch of transitions), asynchronous on `stream`.  Update
+ * indices, replay size and Adam's bias corrections live in device counters,
+ * so the launches can be captured in a CUDA graph (by the caller, or by
+ * nav_trainer_set_graphs). */
 int nav_train_update(nav_trainer *t, int n_updates, void *stream);
+
+/* on = 1: nav_train_update captures each distinct (n_updates, policy phase)
+ * sequence once on its (non-null) stream and replays the graph afterwards
+ * (about 180 small launches per update become one graph launch).  Results
+ * are those of the launches themselves. */
+int nav_trainer_set_graphs(nav_trainer *t, int on);
 
 /* Per-feature input scale applied to observations as they enter the replay
  * (the same scale must be set on the acting policy).  Synchronous. */
@@ -383,6 +399,7 @@ int nav_trainer_sync_policy(nav_trainer *t, nav_policy *p, void *stream);
  * 28 logpi of the actor update, 29 its actions, 30 actor outputs, 31 logpi of
  * the next actions. */
 int nav_trainer_io(nav_trainer *t, int what, int set, void *host);
+/* Replay size and update counts from the device counters (synchronous). */
 int nav_trainer_counts(const nav_trainer *t, int64_t *replay_size, int64_t *critic_updates,
                        int64_t *actor_updates);
 

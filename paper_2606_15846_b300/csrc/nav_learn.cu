@@ -43,17 +43,37 @@ __device__ __forceinline__ float softplusf(float x) {
 }
 
 // ---------------------------------------------------------------- replay ---
+// Device counters of a trainer (read by the kernels, so that a captured
+// update graph replays correctly): [0] critic updates, [1] actor updates,
+// [2] replay head, [3] replay size.  corr holds Adam's bias corrections
+// (1 - b1^t, 1 - b2^t) of the current critic [0..1] and actor [2..3] step.
+enum { kCtrCritic = 0, kCtrActor = 1, kCtrHead = 2, kCtrSize = 3 };
+
+// Starts critic (which 0) or actor (which 1) step t = ++ctr[which]; the
+// step's kernels use t - 1 as their update index.
+__global__ void k_count(unsigned long long *ctr, int which, float b1, float b2, float *corr) {
+    const unsigned long long t = ++ctr[which];
+    corr[2 * which] = 1.0f - powf(b1, (float)t);
+    corr[2 * which + 1] = 1.0f - powf(b2, (float)t);
+}
+
+__global__ void k_insert_done(unsigned long long *ctr, int n, long long cap) {
+    ctr[kCtrHead] = (ctr[kCtrHead] + (unsigned long long)n) % (unsigned long long)cap;
+    const unsigned long long s = ctr[kCtrSize] + (unsigned long long)n;
+    ctr[kCtrSize] = s < (unsigned long long)cap ? s : (unsigned long long)cap;
+}
+
 __global__ void k_replay_insert(const float *__restrict__ obs, const float *__restrict__ act,
                                 const float *__restrict__ rew, const unsigned char *__restrict__ done,
                                 const float *__restrict__ obs_next,
                                 const float *__restrict__ final_obs, int E, int od, int ld,
-                                long long head, long long cap, const float *__restrict__ scale,
-                                int ipap, bf16 *r_obs, bf16 *r_next, float *r_act, float *r_rew,
-                                float *r_term) {
+                                const unsigned long long *__restrict__ ctr, long long cap,
+                                const float *__restrict__ scale, int ipap, bf16 *r_obs,
+                                bf16 *r_next, float *r_act, float *r_rew, float *r_term) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)E * ld) return;
     const int e = (int)(i / ld), c = (int)(i - (long long)e * ld);
-    const long long slot = (head + e) % cap;
+    const long long slot = (long long)((ctr[kCtrHead] + (unsigned long long)e) % (unsigned long long)cap);
     const bool ended = (done[e] & 3) != 0;
     const float *nxt = (ended && final_obs) ? final_obs : obs_next;
     // features under Eq. 2 are stored raw (beta changes while they sit in the
@@ -69,10 +89,11 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
     }
 }
 
-__global__ void k_sample(int *idx, int B, long long size, unsigned long long seed,
-                         unsigned long long update) {
+__global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__ ctr,
+                         unsigned long long seed) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    const unsigned long long update = ctr[kCtrCritic] - 1, size = ctr[kCtrSize];
     const unsigned long long h = hmix(seed ^ (update * 0xD6E8FEB86659FD93ull) ^ ((unsigned long long)b << 1));
     idx[b] = (int)(((h >> 32) * (unsigned long long)size) >> 32);
 }
@@ -152,9 +173,11 @@ __global__ void k_targets(const float *__restrict__ rew, const float *__restrict
                           const float *__restrict__ tq1, const float *__restrict__ tq2,
                           const float *__restrict__ logp_next, const float *__restrict__ log_alpha,
                           int B, float gamma, float rs, unsigned long long seed,
-                          unsigned long long update, float *y, float *ym, float *znoise) {
+                          const unsigned long long *__restrict__ ctr, float *y, float *ym,
+                          float *znoise) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    const unsigned long long update = ctr[kCtrCritic] - 1;
     const float m1 = tq1[2 * b], s1 = softplusf(tq1[2 * b + 1]) + 0.1f;
     const float m2 = tq2[2 * b], s2 = softplusf(tq2[2 * b + 1]) + 0.1f;
     const bool p1 = m1 <= m2;
@@ -320,10 +343,11 @@ __global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) 
 // lr wd), then the Adam step; wd = 0 is plain Adam); weights also refresh
 // their BF16 copies W16 [out][ld_in] and WT16 [in][ld_out] (null for biases).
 __global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v, int n, float lr,
-                       float b1, float b2, float c1, float c2, float wd, int in, bf16 *W16,
-                       int ld_in, bf16 *WT16, int ld_out) {
+                       float b1, float b2, const float *__restrict__ corr, float wd, int in,
+                       bf16 *W16, int ld_in, bf16 *WT16, int ld_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const float c1 = corr[0], c2 = corr[1];
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -347,7 +371,9 @@ __global__ void k_polyak(float *t, const float *__restrict__ s, int n, float tau
 
 // log alpha <- Adam step on mean(-log alpha (logp + H_target)); acc[1] = sum logp
 __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc, int B,
-                        float target_entropy, float lr, float b1, float b2, float c1, float c2) {
+                        float target_entropy, float lr, float b1, float b2,
+                        const float *__restrict__ corr) {
+    const float c1 = corr[0], c2 = corr[1];
     const float g = -(acc[1] / (float)B + target_entropy);
     const float mi = b1 * (*am) + (1.0f - b1) * g;
     const float vi = b2 * (*av) + (1.0f - b2) * g * g;
@@ -375,8 +401,9 @@ __global__ void k_beta_grad(const float *__restrict__ dX, int ldx, const float *
 // Adam step on beta (s[0] beta, s[1..2] moments, s[3] gradient, cleared and
 // kept in s[-1]), then beta <- min(beta, beta_max) so that l - beta > 0 for
 // every range l >= 0
-__global__ void k_beta_adam(float *s, float lr, float b1, float b2, float c1, float c2,
+__global__ void k_beta_adam(float *s, float lr, float b1, float b2, const float *__restrict__ corr,
                             float beta_max) {
+    const float c1 = corr[0], c2 = corr[1];
     const float g = s[3];
     s[-1] = g;
     const float mi = b1 * s[1] + (1.0f - b1) * g;
@@ -473,6 +500,15 @@ struct nav_trainer {
     double *ev_ret = nullptr, *ev_out = nullptr;
     int ev_cap = 0;
     float *scale = nullptr; // per-feature input scale applied when storing obs
+    unsigned long long *ctr = nullptr; // device counters (kCtr*)
+    float *corr = nullptr;             // device Adam bias corrections
+    // captured update sequences, keyed by (updates per call, policy phase)
+    bool use_graphs = false;
+    struct Graph {
+        int n, phase;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
 };
 
 namespace {
@@ -534,17 +570,16 @@ int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 
     return rc;
 }
 
-int adam_net(nav_trainer *T, Mlp &net, float lr, unsigned long long step, cudaStream_t st) {
+int adam_net(nav_trainer *T, Mlp &net, float lr, const float *corr, cudaStream_t st) {
     const float b1 = T->cfg.beta1, b2 = T->cfg.beta2;
-    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     for (int l = 0; l < net.n_layers; ++l) {
         Layer &L = net.layer[l];
         const int nw = L.in * L.out;
         const float wd = T->cfg.weight_decay;
-        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, c1, c2, wd,
+        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, corr, wd,
                                            L.in, static_cast<bf16 *>(L.W16), L.ld_in,
                                            static_cast<bf16 *>(L.WT16), L.ld_out);
-        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, c1, c2,
+        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, corr,
                                               wd, 0, nullptr, 0, nullptr, 0);
     }
     return (int)cudaGetLastError();
@@ -614,6 +649,7 @@ void nav_train_default_cfg(nav_train_cfg *c) {
 void nav_trainer_free(nav_trainer *t) {
     if (!t) return;
     cudaDeviceSynchronize();
+    for (auto &g : t->graphs) cudaGraphExecDestroy(g.exec);
     t->actor.release();
     for (int i = 0; i < 2; ++i) {
         t->q[i].release();
@@ -711,6 +747,8 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->dZT16, B * H);
     TA(T->scal, 16);
     TA(T->status, 1);
+    TA(T->ctr, 4);
+    TA(T->corr, 4);
 #undef TA
     if (e != cudaSuccess) {
         nav_trainer_free(T);
@@ -740,39 +778,44 @@ int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_replay_insert<<<blocks((long long)n_envs * T->ld), 256, 0, st>>>(
         obs_dev, act_dev, rew_dev, done_dev, next_obs_dev, final_obs_dev, n_envs, T->od, T->ld,
-        T->head, T->cap, T->scale, T->ipap, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
+        T->ctr, T->cap, T->scale, T->ipap, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term);
+    k_insert_done<<<1, 1, 0, st>>>(T->ctr, n_envs, T->cap);
     T->head = (T->head + n_envs) % T->cap;
     T->size = std::min(T->cap, T->size + n_envs);
     return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
 }
 
-int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
-    if (!T || n_updates <= 0) return tfail(T, NAV_E_INVAL, "nav_train_update: bad argument");
-    if (T->size < T->B) return tfail(T, NAV_E_INVAL, "nav_train_update: replay smaller than a batch");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+} // extern "C"
+
+namespace {
+
+// The launches of n critic updates (and the actor updates that fall among
+// them) on `st`; every value that changes from update to update is read from
+// the device counters, so the sequence can be captured once and replayed.
+int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
     int rc = 0;
     for (int u = 0; u < n_updates; ++u) {
-        const unsigned long long un = T->n_critic;
-        // ---- critic update
-        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->size, c.seed, un);
+        // ---- critic update (index ctr[critic] - 1 after k_count)
+        k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
+        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed);
         k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
             T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
             T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
         const dim3 tb(32, 8);
         k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
             T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
-        // next action from the current actor
+        // next action from the current actor (noise step 2 index + 1)
         rc |= fwd(T, T->actor, T->Xn, 3, false, T->out_a, st);
-        rc |= launch_actor_head(T->out_a, B, 1, c.seed ^ 0x5A5Aull, (unsigned)(2 * un + 1),
-                                T->a_next, T->logp_next, T->eps_next, st);
+        rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u,
+                                    1u, T->a_next, T->logp_next, T->eps_next, st);
         k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
                                                                 T->ldc, T->Xnc);
         for (int i = 0; i < 2; ++i) rc |= fwd(T, T->qt[i], T->Xnc, 3, false, T->tq[i], st);
         k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
-                                             T->scal + 0, B, c.gamma, c.reward_scale, c.seed, un,
-                                             T->y, T->ym, T->znoise);
+                                             T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
+                                             T->ctr, T->y, T->ym, T->znoise);
         for (int i = 0; i < 2; ++i) {
             rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], st);
             k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
@@ -781,17 +824,17 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
         k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
         for (int i = 0; i < 2; ++i) {
             rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, st);
-            rc |= adam_net(T, T->q[i], c.lr_critic, un + 1, st);
+            rc |= adam_net(T, T->q[i], c.lr_critic, T->corr, st);
         }
-        T->n_critic++;
+        ++n_critic;
         // ---- actor and temperature update every policy_freq critic updates
-        if (T->n_critic % (unsigned long long)c.policy_freq == 0) {
-            const unsigned long long an = T->n_actor;
+        if (n_critic % (unsigned long long)c.policy_freq == 0) {
+            k_count<<<1, 1, 0, st>>>(T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
             k_transpose<<<dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st>>>(T->Xo, T->ld, B,
                                                                               T->od, T->XoT, B);
             rc |= fwd(T, T->actor, T->Xo, 0, true, T->out_a, st);
-            rc |= launch_actor_head(T->out_a, B, 1, c.seed ^ 0xA5A5ull, (unsigned)(2 * an),
-                                    T->a_new, T->logp_new, T->eps_new, st);
+            rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u,
+                                        0u, T->a_new, T->logp_new, T->eps_new, st);
             k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xo, T->ld, T->a_new, B,
                                                                     T->od, T->ldc, T->Xa);
             for (int i = 0; i < 2; ++i) rc |= fwd(T, T->q[i], T->Xa, 1 + i, false, T->qa[i], st);
@@ -805,24 +848,71 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
             rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
                                T->ipap > 0 ? T->dXa : nullptr, T->ld, st);
-            rc |= adam_net(T, T->actor, c.lr_actor, an + 1, st);
-            const float c1 = 1.0f - powf(c.beta1, (float)(an + 1));
-            const float c2 = 1.0f - powf(c.beta2, (float)(an + 1));
+            rc |= adam_net(T, T->actor, c.lr_actor, T->corr + 2, st);
             if (T->ipap > 0) {
                 // Eq. 2's beta trained with the actor (same Adam settings)
                 k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
                     T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
-                k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2, c1, c2,
-                                             c.ipap_beta_max);
+                k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2,
+                                             T->corr + 2, c.ipap_beta_max);
             }
             k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
-                                     c.target_entropy, c.lr_alpha, c.beta1, c.beta2, c1, c2);
-            T->n_actor++;
+                                     c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
         }
         for (int i = 0; i < 2; ++i) rc |= polyak_net(T->qt[i], T->q[i], c.tau, st);
         rc |= (int)cudaGetLastError();
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+} // namespace
+
+extern "C" {
+
+int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
+    if (!T || n_updates <= 0) return tfail(T, NAV_E_INVAL, "nav_train_update: bad argument");
+    if (T->size < T->B) return tfail(T, NAV_E_INVAL, "nav_train_update: replay smaller than a batch");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int pf = T->cfg.policy_freq;
+    const int phase = (int)(T->n_critic % (unsigned long long)pf);
+    const unsigned long long n_act =
+        (T->n_critic + (unsigned long long)n_updates) / (unsigned long long)pf -
+        T->n_critic / (unsigned long long)pf;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st) cudaStreamIsCapturing(st, &cap);
+    int rc = 0;
+    if (T->use_graphs && st && cap == cudaStreamCaptureStatusNone) {
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : T->graphs)
+            if (g.n == n_updates && g.phase == phase) exec = g.exec;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = update_body(T, n_updates, T->n_critic, st);
+                e = cudaStreamEndCapture(st, &graph);
+            }
+            if (e == cudaSuccess && rc == 0) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess || rc != 0)
+                return tfail(T, NAV_E_CUDA, "nav_train_update: graph capture failed");
+            T->graphs.push_back({n_updates, phase, exec});
+        }
+        if (cudaGraphLaunch(exec, st) != cudaSuccess)
+            return tfail(T, NAV_E_CUDA, "nav_train_update: graph launch failed");
+    } else {
+        rc = update_body(T, n_updates, T->n_critic, st);
         if (rc) return tfail(T, NAV_E_CUDA, "nav_train_update: launch failed");
     }
+    T->n_critic += (unsigned long long)n_updates;
+    T->n_actor += n_act;
+    return NAV_OK;
+}
+
+int nav_trainer_set_graphs(nav_trainer *T, int on) {
+    if (!T) return NAV_E_INVAL;
+    T->use_graphs = on != 0;
     return NAV_OK;
 }
 
@@ -886,9 +976,13 @@ int nav_trainer_sync_policy(nav_trainer *T, nav_policy *p, void *stream) {
 int nav_trainer_counts(const nav_trainer *T, int64_t *replay_size, int64_t *critic_updates,
                        int64_t *actor_updates) {
     if (!T) return NAV_E_INVAL;
-    if (replay_size) *replay_size = T->size;
-    if (critic_updates) *critic_updates = (int64_t)T->n_critic;
-    if (actor_updates) *actor_updates = (int64_t)T->n_actor;
+    unsigned long long c[4];
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(c, T->ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NAV_E_CUDA;
+    if (replay_size) *replay_size = (int64_t)c[kCtrSize];
+    if (critic_updates) *critic_updates = (int64_t)c[kCtrCritic];
+    if (actor_updates) *actor_updates = (int64_t)c[kCtrActor];
     return NAV_OK;
 }
 

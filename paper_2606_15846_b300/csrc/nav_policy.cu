@@ -76,11 +76,16 @@ __global__ void obs_to_fp32(const float *__restrict__ obs, int n, int dim, long 
 }
 
 // a = tanh(u + sigma eps) (or tanh(u)), logp per row.
+// With ctr set, the noise step is mul * (ctr[which] - sub) + add, read on the
+// device (so that a captured launch draws fresh noise on every replay).
 __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
-                               unsigned long long seed, unsigned step, float *act, float *logp,
-                               float *eps_out) {
+                               unsigned long long seed, unsigned step,
+                               const unsigned long long *__restrict__ ctr, int which,
+                               unsigned long long sub, unsigned mul, unsigned add, float *act,
+                               float *logp, float *eps_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
+    if (ctr) step = mul * (unsigned)(ctr[which] - sub) + add;
     const float *o = out4 + (size_t)r * 4;
     float lp = 0.0f;
 #pragma unroll
@@ -102,6 +107,8 @@ __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
     }
     if (logp) logp[r] = lp;
 }
+
+__global__ void k_bump(unsigned long long *c) { *c += 1; }
 
 // Plain FP32 layer: y[r][o] = act(sum_k x[r][k] W[o][k] + b[o]); one thread
 // per output element (the unfused baseline; no tensor cores).
@@ -321,7 +328,15 @@ int launch_obs_to_fp32(const float *obs, int n, int dim, long long stride, const
 int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
                       float *act, float *logp, float *eps, void *stream) {
     actor_head_fwd<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        out4, n, mode, seed, step, act, logp, eps);
+        out4, n, mode, seed, step, nullptr, 0, 0, 0, 0, act, logp, eps);
+    return (int)cudaGetLastError();
+}
+
+int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long seed,
+                          const unsigned long long *ctr, int which, unsigned mul, unsigned add,
+                          float *act, float *logp, float *eps, void *stream) {
+    actor_head_fwd<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        out4, n, mode, seed, 0u, ctr, which, 1ull, mul, add, act, logp, eps);
     return (int)cudaGetLastError();
 }
 
@@ -443,6 +458,28 @@ int nav_policy_act(nav_policy *p, const float *obs_dev, int64_t obs_stride, int 
     if (rc == 0 && out_dev)
         rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice,
                                   static_cast<cudaStream_t>(stream));
+    return rc == 0 ? NAV_OK : NAV_E_CUDA;
+}
+
+int nav_policy_act_counted(nav_policy *p, const float *obs_dev, int64_t obs_stride, int n,
+                           int mode, uint64_t seed, uint64_t *step_dev, float *actions_dev,
+                           float *logp_dev, float *out_dev, void *stream) {
+    if (!p || !obs_dev || !actions_dev || !step_dev || n <= 0 || n > p->max_batch ||
+        obs_stride < p->obs_dim || (mode != 0 && mode != 1))
+        return NAV_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ld0 = p->actor.layer[0].ld_in;
+    int rc = launch_obs_to_bf16(obs_dev, n, p->obs_dim, obs_stride, p->scale, p->ipap, p->beta,
+                                p->x16, ld0, stream);
+    if (rc == 0) rc = p->actor.forward_tc(p->x16, n, p->h16, nullptr, p->out32, p->status, stream);
+    if (rc == 0) {
+        unsigned long long *c = reinterpret_cast<unsigned long long *>(step_dev);
+        k_bump<<<1, 1, 0, st>>>(c);
+        rc = launch_actor_head_ctr(p->out32, n, mode, seed, c, 0, 1u, 0u, actions_dev, logp_dev,
+                                   nullptr, stream);
+    }
+    if (rc == 0 && out_dev)
+        rc = (int)cudaMemcpyAsync(out_dev, p->out32, (size_t)n * 16, cudaMemcpyDeviceToDevice, st);
     return rc == 0 ? NAV_OK : NAV_E_CUDA;
 }
 

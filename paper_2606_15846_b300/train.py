@@ -53,6 +53,11 @@ class TrainConfig:
     weight_decay: float = 0.0
     ipap: bool = False  # Eq. 2 on the range features, beta trained with the actor
     steps_per_sync: int = 1
+    graph: bool = True        # capture collector + updates in one CUDA graph once learning runs
+    goal_dmax: float = 6.0    # paper setting: straight-line goal distance bound (m)
+    occupancy: float = 0.10   # paper setting: occupied fraction of the stand-in map
+    corridors: bool = False   # paper setting: corridor walls in the stand-in map
+    alpha_init: float = 0.001
 
 
 def paper_config(robot: str = "turtlebot2", **kw) -> TrainConfig:
@@ -78,8 +83,10 @@ def obs_features(cfg: TrainConfig) -> int:
 
 def make_workloads(cfg: TrainConfig):
     if cfg.setting == "paper":
-        train = W.config_paper(cfg.robot, n_envs=cfg.n_envs, beams=cfg.beams)
-        ev = W.config_paper(cfg.robot, n_envs=cfg.n_eval, beams=cfg.beams)
+        kw = dict(beams=cfg.beams, goal_dmax=cfg.goal_dmax, occupancy=cfg.occupancy,
+                  corridors=cfg.corridors)
+        train = W.config_paper(cfg.robot, n_envs=cfg.n_envs, **kw)
+        ev = W.config_paper(cfg.robot, n_envs=cfg.n_eval, **kw)
         return train, ev
     robot = _robot(cfg)
     train_maps = [W.make_map(10_000 + cfg.seed * 1000 + m, cfg.map_size, cfg.map_size,
@@ -146,7 +153,10 @@ def evaluate_reactive(cfg: TrainConfig, log=print):
     return succ.value / cfg.n_eval, ret.value / cfg.n_eval
 
 
-def train(cfg: TrainConfig, log=print):
+def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
+    """Runs FastDSAC until the threshold or the time budget.  With
+    keep_policy the result also holds the trained nav_policy handle
+    ("policy", freed by the caller with nav_policy_free)."""
     import torch
     lib = F.load()
     train_wl, eval_wl = make_workloads(cfg)
@@ -161,6 +171,7 @@ def train(cfg: TrainConfig, log=print):
     tc.hidden, tc.n_hidden, tc.gamma, tc.weight_decay = cfg.hidden, cfg.n_hidden, cfg.gamma, \
         cfg.weight_decay
     tc.ipap_features = ipap
+    tc.alpha_init = cfg.alpha_init
     pol = C.c_void_p()
     assert lib.nav_policy_create_ex(od, cfg.hidden, cfg.n_hidden, ipap,
                                     C.c_float(tc.ipap_beta_init), max(cfg.n_envs, cfg.n_eval),
@@ -185,8 +196,17 @@ def train(cfg: TrainConfig, log=print):
     ev_act = torch.empty(cfg.n_eval, 2, device=dev)
     ev_rew = torch.empty(cfg.n_eval, device=dev)
     ev_done = torch.empty(cfg.n_eval, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream().cuda_stream
+    noise_step = torch.zeros(1, dtype=torch.int64, device=dev)  # collector noise counter
+    side = torch.cuda.Stream()
+    ctx = torch.cuda.stream(side)
+    ctx.__enter__()
+    stream = side.cuda_stream
     S = C.c_void_p(stream)
+    # launch shapes of both simulators tuned before the clock starts
+    sim.reset(cfg.seed + 100, obs[0])
+    sim.autotune(steps=5)
+    ev.reset(777, ev_obs)
+    ev.autotune(steps=5)
     sim.reset(cfg.seed + 100, obs[0])
     assert lib.nav_trainer_sync_policy(T, pol, S) == 0
     history = []
@@ -211,6 +231,28 @@ def train(cfg: TrainConfig, log=print):
         assert lib.nav_eval_result(T, cfg.n_eval, C.byref(succ), C.byref(ret), S) == 0
         return succ.value / cfg.n_eval, ret.value / cfg.n_eval
 
+    learning = lambda: n_transitions >= max(cfg.learning_starts, cfg.batch)
+
+    def iteration(cur, sync):
+        """One collector step and, once learning has started, utd updates."""
+        nxt = 1 - cur
+        rc = lib.nav_policy_act_counted(pol, _p(obs[cur]), od, E, 1, cfg.seed, _p(noise_step),
+                                        _p(act), None, None, S)
+        assert rc == 0
+        sim.step(act, obs[nxt], rew, done, final_obs=fin)
+        assert lib.nav_train_insert(T, _p(obs[cur]), _p(act), _p(rew), _p(done), _p(obs[nxt]),
+                                    _p(fin), E, S) == 0
+        if learning():
+            rc = lib.nav_train_update(T, cfg.utd, S)
+            if rc:
+                raise F.NavError(rc, lib.nav_trainer_last_error(T).decode())
+            if sync:
+                assert lib.nav_trainer_sync_policy(T, pol, S) == 0
+
+    # once learning runs, two iterations (obs buffers 0 -> 1 -> 0) are one
+    # CUDA graph: collector, replay insert, the updates and the actor syncs
+    graph = None
+    use_graph = cfg.graph and cfg.utd % tc.policy_freq == 0 and cfg.steps_per_sync in (1, 2)
     while True:
         el = time.perf_counter() - t0
         if el >= next_eval:
@@ -225,20 +267,19 @@ def train(cfg: TrainConfig, log=print):
             next_eval = el + cfg.eval_every_s
         if el >= cfg.time_budget_s:
             break
-        nxt = 1 - cur
-        assert lib.nav_policy_act(pol, _p(obs[cur]), od, E, 1, cfg.seed, step, _p(act), None,
-                                  None, S) == 0
-        sim.step(act, obs[nxt], rew, done, final_obs=fin)
-        assert lib.nav_train_insert(T, _p(obs[cur]), _p(act), _p(rew), _p(done), _p(obs[nxt]),
-                                    _p(fin), E, S) == 0
+        if use_graph and learning() and cur == 0:
+            if graph is None:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+                    iteration(0, cfg.steps_per_sync == 1)
+                    iteration(1, True)
+            graph.replay()
+            n_transitions += 2 * E
+            step += 2
+            continue
+        iteration(cur, step % cfg.steps_per_sync == 0)
         n_transitions += E
-        if n_transitions >= max(cfg.learning_starts, cfg.batch):
-            rc = lib.nav_train_update(T, cfg.utd, S)
-            if rc:
-                raise F.NavError(rc, lib.nav_trainer_last_error(T).decode())
-            if step % cfg.steps_per_sync == 0:
-                assert lib.nav_trainer_sync_policy(T, pol, S) == 0
-        cur = nxt
+        cur = 1 - cur
         step += 1
     if reached is None and (not history or history[-1]["t"] < time.perf_counter() - t0 - 1e-3):
         rate, mret = evaluate()
@@ -247,6 +288,12 @@ def train(cfg: TrainConfig, log=print):
                         "transitions": n_transitions})
         log(f"t={el:6.2f}s env_steps={step * E:>10d} success={rate:.3f} return={mret:8.3f}")
     torch.cuda.synchronize()
+    ctx.__exit__(None, None, None)
+    del graph
     lib.nav_trainer_free(T)
-    lib.nav_policy_free(pol)
-    return {"time_to_threshold_s": reached, "history": history, "env_steps": step * E}
+    out = {"time_to_threshold_s": reached, "history": history, "env_steps": step * E}
+    if keep_policy:
+        out["policy"] = pol
+    else:
+        lib.nav_policy_free(pol)
+    return out

@@ -221,30 +221,33 @@ def config_uneven(n_envs: int = 16384, n_maps: int = 64, seed0: int = 200,
     )
 
 
-def paper_params(fov_deg: float) -> Params:
+def paper_params(fov_deg: float, goal_dmax: float = 6.0) -> Params:
     """Table 7's sensing, episode and reward constants: 0.03 m fixed-step
     march, 30 sector minima (of 1080 beams), horizon 200, dt 0.1 s, goal
     0.2 m, the exclusive reward cases of Eq. 3 (+10 / -10 / 2 x progress).
-    Goals are any free cell at >= 1 m (the paper gives no distance band)."""
-    return Params(reward_mode=1, step_penalty=0.0, goal_dmin=1.0, goal_dmax=1.0e9,
+    The paper gives no goal distance band; goals are drawn 1-6 m away in a
+    straight line, so that a detour still fits the 10 m an episode can travel
+    (200 steps x 0.1 s x 0.5 m/s)."""
+    return Params(reward_mode=1, step_penalty=0.0, goal_dmin=1.0, goal_dmax=goal_dmax,
                   fov_deg=fov_deg, sensor=1, march_step=0.03, n_sectors=30)
 
 
 def config_paper(robot: str = "turtlebot2", n_envs: int = 1024, seed: int = 31,
-                 occupancy: float = 0.12, beams: int = 1080) -> Workload:
+                 occupancy: float = 0.10, beams: int = 1080,
+                 goal_dmax: float = 6.0, corridors: bool = False) -> Workload:
     """The paper's training setting (Sec. 2.2.1, Tables 7-9): every env on
     one shared map, 10 x 10 m for the TurtleBot2 (disc r = 0.20 m, 270 deg
     fan) or 13.5 x 13.5 m for the Go2 (0.80 x 0.41 m rectangle, 360 deg),
     1080 beams marched at 0.03 m to 20 m and pooled into 30 sectors.  The
-    map content is not published: a seeded map of boxes, discs and corridor
-    walls at `occupancy` stands in (0.05 m cells)."""
+    map content is not published: a seeded cluttered room of boxes and discs
+    at `occupancy` stands in (0.05 m cells; corridor walls optional)."""
     if robot == "turtlebot2":
         side, rb, fov = 200, TURTLEBOT2, 270.0
     elif robot == "go2":
         side, rb, fov = 270, GO2, 360.0
     else:
         raise ValueError(robot)
-    occ = make_map(seed, side, side, occupancy, corridors=True)
+    occ = make_map(seed, side, side, occupancy, corridors=corridors)
     return Workload(
         name=f"paper-{robot}-{n_envs}env-{side}x{side}-{beams}beam-march-30sector",
         maps=[occ],
@@ -253,5 +256,5 @@ def config_paper(robot: str = "turtlebot2", n_envs: int = 1024, seed: int = 31,
         env_robot=np.zeros(n_envs, np.int32),
         robots=[rb],
         max_range=20.0,
-        params=paper_params(fov),
+        params=paper_params(fov, goal_dmax),
     )

@@ -272,3 +272,46 @@ def test_eval_reduction_fp64(env):
     assert succ.value == want_s
     assert abs(ret.value - want_r) <= 1e-9 * max(1.0, abs(want_r))
     lib.nav_trainer_free(T)
+
+
+def test_graph_replayed_updates_match_eager(env):
+    """The update reads its indices, replay size and Adam corrections from
+    device counters, so a captured sequence replayed twice does what eight
+    eager updates do (same draws; split-K atomics may reorder sums)."""
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.obs_dim, cfg.hidden, cfg.n_hidden, cfg.ipap_features = 34, 100, 4, 30
+    cfg.batch, cfg.replay_capacity, cfg.seed, cfg.weight_decay = 256, 4096, 5, 1e-3
+    rng = np.random.default_rng(1)
+    N = 1500
+    data = [rng.uniform(0, 6, (N, 34)).astype(np.float32),
+            rng.uniform(-1, 1, (N, 2)).astype(np.float32),
+            rng.normal(0, 1, N).astype(np.float32),
+            rng.choice([0, 0, 1, 2], N).astype(np.uint8),
+            rng.uniform(0, 6, (N, 34)).astype(np.float32)]
+    dev = [torch.from_numpy(a).cuda() for a in data]
+    s = torch.cuda.Stream()
+    S = C.c_void_p(s.cuda_stream)
+    out = []
+    for graphs in (0, 1):
+        T = C.c_void_p()
+        assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+        assert lib.nav_trainer_set_graphs(T, graphs) == 0
+        with torch.cuda.stream(s):
+            assert lib.nav_train_insert(T, *[_p(d) for d in dev], None, N, S) == 0
+            for _ in range(2):
+                assert lib.nav_train_update(T, 4, S) == 0
+        s.synchronize()
+        sizes = [34, 100, 100, 100, 100, 4]
+        n_a = sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:]))
+        out.append((_io(lib, T, 0, n_a), _io(lib, T, 24, 16), _io(lib, T, 20, 256, np.int32)))
+        rs, cu, au = C.c_int64(), C.c_int64(), C.c_int64()
+        assert lib.nav_trainer_counts(T, C.byref(rs), C.byref(cu), C.byref(au)) == 0
+        assert (rs.value, cu.value, au.value) == (N, 8, 4)
+        lib.nav_trainer_free(T)
+    (wa, sa, ia), (wb, sb, ib) = out
+    assert np.array_equal(ia, ib)  # the last batch drawn is the same
+    assert _rel(wb, wa) < 1e-5
+    assert abs(float(sa[12]) - float(sb[12])) < 1e-6  # beta
