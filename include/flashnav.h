@@ -383,6 +383,15 @@ int nav_train_update(nav_trainer *t, int n_updates, void *stream);
  * are those of the launches themselves. */
 int nav_trainer_set_graphs(nav_trainer *t, int on);
 
+/* Path of the updates.  Networks whose every width is <= 128 (with <= 8
+ * outputs, batch a multiple of 128) run on fused passes by default: one
+ * launch runs every layer of a network's forward or backward for 128 batch
+ * rows (operands in shared memory, accumulators in TMEM), the twin critics
+ * share launches, and one kernel applies AdamW to a whole network; ~25
+ * launches per update instead of ~180.  on = 0 selects the per-layer GEMM
+ * path (same arithmetic); on = 1 fails with NAV_E_INVAL for wider networks. */
+int nav_trainer_set_fused(nav_trainer *t, int on);
+
 /* Per-feature input scale applied to observations as they enter the replay
  * (the same scale must be set on the acting policy).  Synchronous. */
 int nav_trainer_set_input_scale(nav_trainer *t, const float *scale_host);

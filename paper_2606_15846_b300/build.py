@@ -20,7 +20,7 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_GEOMETRY = ["nav_step.cu"]
-CU_DEFAULT = ["nav_noalloc.cu", "nav_mlp.cu", "nav_policy.cu", "nav_learn.cu"]
+CU_DEFAULT = ["nav_noalloc.cu", "nav_mlp.cu", "nav_fused.cu", "nav_policy.cu", "nav_learn.cu"]
 CPP = ["nav_api.cpp"]
 
 
@@ -38,7 +38,7 @@ def _stale(out, srcs):
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "flashnav.h"))
     objs = []
     common_nv = ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

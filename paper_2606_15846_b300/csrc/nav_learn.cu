@@ -484,6 +484,7 @@ struct nav_trainer {
     // activations per hidden layer: [0] actor, [1] q0, [2] q1, [3] scratch
     bf16 *h16[4][kMaxLayers - 1] = {}, *ht16[4][kMaxLayers - 1] = {};
     float *Lraw = nullptr, *dXa = nullptr; // raw Eq. 2 ranges of obs; actor input gradient
+    unsigned *mask[4][kMaxLayers - 1] = {}; // fused passes: LeakyReLU' sign bits per slot
     float *out_a = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
     float *a_next = nullptr, *logp_next = nullptr, *a_new = nullptr, *logp_new = nullptr,
           *eps_new = nullptr, *eps_next = nullptr;
@@ -500,6 +501,11 @@ struct nav_trainer {
     double *ev_ret = nullptr, *ev_out = nullptr;
     int ev_cap = 0;
     float *scale = nullptr; // per-feature input scale applied when storing obs
+    // fused small-network passes (every width <= 128): per-CTA partial
+    // gradients [n_cta][params] of the actor and the two critics
+    bool fused = false;
+    int n_cta = 0;
+    float *part_a = nullptr, *part_q[2] = {};
     unsigned long long *ctr = nullptr; // device counters (kCtr*)
     float *corr = nullptr;             // device Adam bias corrections
     // captured update sequences, keyed by (updates per call, policy phase)
@@ -749,6 +755,14 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->status, 1);
     TA(T->ctr, 4);
     TA(T->corr, 4);
+    T->fused = rc == NAV_OK && fused_ok(T->actor, T->B) && fused_ok(T->q[0], T->B);
+    if (T->fused) {
+        T->n_cta = T->B / 128;
+        for (int sl = 0; sl < 4; ++sl)
+            for (int l = 0; l < T->NH; ++l) TA(T->mask[sl][l], B * 4);
+        TA(T->part_a, (long long)T->n_cta * T->actor.num_params());
+        for (int i = 0; i < 2; ++i) TA(T->part_q[i], (long long)T->n_cta * T->q[i].num_params());
+    }
 #undef TA
     if (e != cudaSuccess) {
         nav_trainer_free(T);
@@ -789,6 +803,132 @@ int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
 
 namespace {
 
+// forward of up to two networks through the fused pass; slot[k] >= 0 saves
+// the hidden activations (and, with save_t, their transposes) there
+int ffwd(nav_trainer *T, Mlp *const *nets, int n, const bf16 *X, int ldx, float *const *out,
+         const int *slot, bool save_t, cudaStream_t st) {
+    FGroup g{};
+    g.n_nets = n;
+    g.B = T->B;
+    g.status = T->status;
+    for (int k = 0; k < n; ++k) {
+        FNet &f = g.net[k];
+        fused_layers(*nets[k], f);
+        f.X = X;
+        f.ldx = ldx;
+        f.out32 = out[k];
+        f.ldh = T->Hp;
+        for (int l = 0; l + 1 < nets[k]->n_layers; ++l) {
+            f.M[l] = slot[k] >= 0 ? T->mask[slot[k]][l] : nullptr;
+            f.HT16[l] = (slot[k] >= 0 && save_t) ? T->ht16[slot[k]][l] : nullptr;
+        }
+    }
+    return launch_mlp_fwd_fused(g, st);
+}
+
+// backward of up to two networks: part[k] receives the per-CTA partial
+// gradients (null: no weight gradients), dX[k] the input gradient (or null)
+int fbwd(nav_trainer *T, Mlp *const *nets, int n, float *const *dout, const int *slot,
+         const bf16 *XT, float *const *part, float *const *dX, int lddx, cudaStream_t st) {
+    FGroup g{};
+    g.n_nets = n;
+    g.B = T->B;
+    g.status = T->status;
+    for (int k = 0; k < n; ++k) {
+        const Mlp &m = *nets[k];
+        FNet &f = g.net[k];
+        fused_layers(m, f);
+        f.dout = dout[k];
+        f.XT = XT;
+        f.ldh = T->Hp;
+        f.cta_stride = m.num_params();
+        f.dX = dX ? dX[k] : nullptr;
+        f.lddx = lddx;
+        long long off = 0;
+        for (int l = 0; l < m.n_layers; ++l) {
+            const Layer &L = m.layer[l];
+            if (l + 1 < m.n_layers) {
+                f.M[l] = T->mask[slot[k]][l];
+                f.HT16[l] = T->ht16[slot[k]][l];
+            }
+            f.gWp[l] = part ? part[k] + off : nullptr;
+            f.gbp[l] = part ? part[k] + off + (long long)L.in * L.out : nullptr;
+            off += (long long)L.in * L.out + L.out;
+        }
+    }
+    return launch_mlp_bwd_fused(g, st);
+}
+
+// One critic update (and the actor update that falls on it) on the fused
+// passes: the same arithmetic as the per-layer path, ~25 launches.
+int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
+    const nav_train_cfg &c = T->cfg;
+    const int B = T->B;
+    int rc = 0;
+    const dim3 tb(32, 8);
+    Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
+    const int none[2] = {-1, -1}, qslot[2] = {1, 2}, aslot[1] = {0};
+    k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
+    k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed);
+    k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
+        T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
+        T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
+    k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
+        T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
+    // targets
+    float *oa[1] = {T->out_a};
+    rc |= ffwd(T, act, 1, T->Xn, T->ld, oa, none, false, st);
+    rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u, 1u,
+                                T->a_next, T->logp_next, T->eps_next, st);
+    k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
+                                                            T->ldc, T->Xnc);
+    rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
+    k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
+                                         T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr,
+                                         T->y, T->ym, T->znoise);
+    // critics
+    rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
+    for (int i = 0; i < 2; ++i)
+        k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
+                                                 c.huber_delta, T->dq[i], T->scal + 4);
+    k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+    rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
+    rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
+                            c.weight_decay, st);
+    if (actor_step) {
+        k_count<<<1, 1, 0, st>>>(T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
+        k_transpose<<<dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st>>>(T->Xo, T->ld, B,
+                                                                          T->od, T->XoT, B);
+        rc |= ffwd(T, act, 1, T->Xo, T->ld, oa, aslot, true, st);
+        rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
+                                    T->a_new, T->logp_new, T->eps_new, st);
+        k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xo, T->ld, T->a_new, B, T->od,
+                                                                T->ldc, T->Xa);
+        rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
+        k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
+        k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0, B,
+                                                T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+        rc |= fbwd(T, qs, 2, T->dq, qslot, nullptr, nullptr, T->dX, T->ldc, st);
+        k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
+                                                    T->ldc, T->od, T->dlogp, B, T->dout);
+        float *douts[1] = {T->dout}, *pa[1] = {T->part_a}, *dxa[1] = {T->dXa};
+        rc |= fbwd(T, act, 1, douts, aslot, T->XoT, pa, T->ipap > 0 ? dxa : nullptr, T->ld, st);
+        rc |= launch_adam_fused(act, pa, 1, T->n_cta, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
+                                c.weight_decay, st);
+        if (T->ipap > 0) {
+            k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
+                T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
+            k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
+                                         c.ipap_beta_max);
+        }
+        k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
+                                 c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
+    }
+    rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);
+    rc |= (int)cudaGetLastError();
+    return rc;
+}
+
 // The launches of n critic updates (and the actor updates that fall among
 // them) on `st`; every value that changes from update to update is read from
 // the device counters, so the sequence can be captured once and replayed.
@@ -796,6 +936,14 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
     int rc = 0;
+    if (T->fused) {
+        for (int u = 0; u < n_updates; ++u) {
+            ++n_critic;
+            rc |= fused_update(T, n_critic % (unsigned long long)c.policy_freq == 0, st);
+            if (rc) return rc;
+        }
+        return 0;
+    }
     for (int u = 0; u < n_updates; ++u) {
         // ---- critic update (index ctr[critic] - 1 after k_count)
         k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
@@ -907,6 +1055,15 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
     }
     T->n_critic += (unsigned long long)n_updates;
     T->n_actor += n_act;
+    return NAV_OK;
+}
+
+int nav_trainer_set_fused(nav_trainer *T, int on) {
+    if (!T) return NAV_E_INVAL;
+    if (on && !T->part_a) return tfail(T, NAV_E_INVAL, "networks too wide for the fused passes");
+    T->fused = on != 0;
+    for (auto &g : T->graphs) cudaGraphExecDestroy(g.exec);
+    T->graphs.clear();
     return NAV_OK;
 }
 

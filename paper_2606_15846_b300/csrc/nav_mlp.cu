@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "nav_internal.h"
+#include "tc_util.cuh"
 
 namespace flashnav {
 namespace {
@@ -28,62 +29,6 @@ constexpr int kChunkK = 64; // BF16 elements per 128-byte swizzle row
 constexpr int kStages = 4;  // K chunks in flight
 constexpr int kThreads = 128;
 constexpr float kLeakySlope = 0.01f;
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride byte offset), start address in 16-byte units.
-__device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
-    d |= (unsigned long long)1 << 16;                 // leading byte offset (unused here)
-    d |= (unsigned long long)(1024u >> 4) << 32;      // stride byte offset
-    d |= (unsigned long long)1 << 46;                 // descriptor version
-    d |= (unsigned long long)2 << 61;                 // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
-__device__ __forceinline__ unsigned instr_desc(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
-           ((unsigned)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// Copies rows [r0, r0 + rows) x K-chunk [k0, k0 + 64) of a K-major matrix
-// into a swizzled tile; out-of-range rows and columns are zero.
-__device__ __forceinline__ void load_tile(unsigned dst, const __nv_bfloat16 *src, int ld,
-                                          int r0, int rows, int nrows_total, int k0, int K) {
-    for (int p = threadIdx.x; p < rows * 8; p += kThreads) {
-        const int r = p >> 3, c = p & 7;
-        const int gr = r0 + r, k = k0 + c * 8;
-        int bytes = 0;
-        const __nv_bfloat16 *g = src;
-        if (gr < nrows_total && k < K) {
-            bytes = K - k >= 8 ? 16 : 2 * (K - k);
-            g = src + (size_t)gr * ld + k;
-        }
-        const unsigned d = dst + (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(bytes)
-                     : "memory");
-    }
-}
 
 __global__ void __launch_bounds__(kThreads)
     gemm_bf16_tc(const __nv_bfloat16 *__restrict__ A, int lda, const __nv_bfloat16 *__restrict__ B,
@@ -127,8 +72,8 @@ __global__ void __launch_bounds__(kThreads)
     const int nk = kc1 - kc0;
     auto load_chunk = [&](int j) {
         const unsigned sa = base + (unsigned)(j % kStages) * stage_bytes;
-        load_tile(sa, A, lda, m0, kTileM, M, (kc0 + j) * kChunkK, K);
-        load_tile(sa + kTileM * 128, B, ldb, n0, BN, N, (kc0 + j) * kChunkK, K);
+        load_tile<kThreads>(sa, A, lda, m0, kTileM, M, (kc0 + j) * kChunkK, K);
+        load_tile<kThreads>(sa + kTileM * 128, B, ldb, n0, BN, N, (kc0 + j) * kChunkK, K);
     };
     // pipeline: chunk j's copies form cp.async group j; chunk j + kStages - 1
     // is fetched into the stage of chunk j - 1 once that chunk's MMAs are done

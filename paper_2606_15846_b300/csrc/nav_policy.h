@@ -11,8 +11,9 @@ constexpr float kLogStdMax = 0.0f;
 constexpr int kMaxLayers = 5; // up to four hidden layers and the output layer
 
 // Leading dimension (elements) of a BF16 activation row of n features: the
-// tensor-core GEMM reads K-major rows that start on 16-byte boundaries.
-inline int act_ld(int n) { return (n + 7) / 8 * 8; }
+// tensor-core GEMM reads K-major rows that start on 16-byte boundaries, and
+// the fused passes read whole 16-column groups.
+inline int act_ld(int n) { return (n + 15) / 16 * 16; }
 
 // One dense layer: FP32 master weights W [out][in] and bias, BF16 copies for
 // the tensor cores (W16 [out][ld_in], WT16 [in][ld_out]), Adam moments and
@@ -53,6 +54,68 @@ int launch_actor_head(const float *out4, int n, int mode, unsigned long long see
 int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long seed,
                           const unsigned long long *ctr, int which, unsigned mul, unsigned add,
                           float *act, float *logp, float *eps, void *stream);
+
+// ---------------------------------------------------------------------------
+// Fused passes for small networks (every layer's in and out <= 128, at most
+// 8 outputs, batch a multiple of 128): one CTA per 128 batch rows runs every
+// layer of a network with its operands in shared memory and accumulators in
+// TMEM; grid.y selects one of up to two networks (the twin critics).
+// ---------------------------------------------------------------------------
+constexpr int kFusedMaxWidth = 128;
+
+struct FLayer {
+    const void *W16, *WT16; // BF16 [out][ld_in] and [in][ld_out]
+    const float *b;
+    int ld_in, ld_out, in, out;
+};
+
+struct FNet {
+    FLayer L[kMaxLayers];
+    int n_layers;
+    // forward: X [B][ldx] (K = L[0].in) -> out32 [B][n_out]; optional saves of
+    // every hidden activation, H16 [B][ldh] and HT16 [H][B]
+    const void *X;
+    int ldx;
+    float *out32;
+    void *H16[kMaxLayers - 1], *HT16[kMaxLayers - 1];
+    int ldh;
+    // LeakyReLU' of every hidden activation as sign bits, [B][4] words per
+    // layer (bit c of word w: activation 32 w + c > 0); written by the
+    // forward when set, read by the backward
+    unsigned *M[kMaxLayers - 1];
+    // backward: dout [B][n_out] -> per-CTA partial gradients, CTA c's at
+    // gWp[l] + c cta_stride ([out][in]) and gbp[l] + c cta_stride ([out])
+    // (gWp[l] null: that layer's gradients are not formed),
+    // input gradient dX [B][lddx] (null: none); XT [in0][B] for layer 0's dW
+    const float *dout;
+    const void *XT;
+    float *gWp[kMaxLayers], *gbp[kMaxLayers];
+    long long cta_stride; // floats between two CTAs' partials
+    float *dX;
+    int lddx;
+};
+
+struct FGroup {
+    FNet net[2];
+    int n_nets, B;
+    int *status;
+};
+
+// True when the net fits the fused passes.
+bool fused_ok(const Mlp &m, int B);
+// Fills the layer table of an FNet from an Mlp (io fields untouched).
+void fused_layers(const Mlp &m, FNet &f);
+int launch_mlp_fwd_fused(const FGroup &g, void *stream);
+int launch_mlp_bwd_fused(const FGroup &g, void *stream);
+
+// One Adam / AdamW step on every parameter of up to two networks, whose
+// gradients are the sums of n_cta partials (written back to gW / gb for
+// inspection); BF16 copies refreshed.  corr: device bias corrections.
+int launch_adam_fused(Mlp *const *nets, float *const *gWp_base, int n_nets, int n_cta, float lr,
+                      float b1, float b2, const float *corr, float wd, void *stream);
+// Polyak averaging tgt <- (1 - tau) tgt + tau src of up to two networks, with
+// the targets' BF16 copies refreshed.
+int launch_polyak_fused(Mlp *const *tgt, Mlp *const *src, int n_nets, float tau, void *stream);
 
 } // namespace flashnav
 

@@ -82,6 +82,9 @@ CONFIGS = {
     # Table 3 / Eq. 2: (100) x 4 nets, AdamW 1e-3, 30 sector minima through
     # 1 / (l - beta), goal / velocity features scaled
     "paper": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True),
+    # the same networks on the per-layer GEMM path instead of the fused passes
+    "paper_per_layer": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True,
+                            fused=0),
 }
 
 
@@ -111,6 +114,8 @@ def run_update(flashnav, torch, name, P, strict=True):
     cfg.weight_decay, cfg.ipap_features = P["wd"], ipap
     T = C.c_void_p()
     assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+    if "fused" in P:
+        assert lib.nav_trainer_set_fused(T, P["fused"]) == 0
     scale = None
     if P["scale"]:
         scale = np.ones(od, np.float32)
@@ -315,3 +320,56 @@ def test_graph_replayed_updates_match_eager(env):
     assert np.array_equal(ia, ib)  # the last batch drawn is the same
     assert _rel(wb, wa) < 1e-5
     assert abs(float(sa[12]) - float(sb[12])) < 1e-6  # beta
+
+
+def test_fused_and_per_layer_paths_agree(env):
+    """Four updates of the (100) x 4 networks on the fused passes and on the
+    per-layer GEMM path from the same state and draws: the weights agree up
+    to summation order (split-K atomics vs partial sums)."""
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.obs_dim, cfg.hidden, cfg.n_hidden, cfg.ipap_features = 34, 100, 4, 30
+    cfg.batch, cfg.replay_capacity, cfg.seed, cfg.weight_decay = 512, 4096, 9, 1e-3
+    rng = np.random.default_rng(2)
+    N = 2000
+    data = [rng.uniform(0, 6, (N, 34)).astype(np.float32),
+            rng.uniform(-1, 1, (N, 2)).astype(np.float32),
+            rng.normal(0, 1, N).astype(np.float32),
+            rng.choice([0, 0, 1, 2], N).astype(np.uint8),
+            rng.uniform(0, 6, (N, 34)).astype(np.float32)]
+    dev = [torch.from_numpy(a).cuda() for a in data]
+    sa = [34, 100, 100, 100, 100, 4]
+    sc = [36, 100, 100, 100, 100, 2]
+    n_a = sum(a * b + b for a, b in zip(sa[:-1], sa[1:]))
+    n_c = sum(a * b + b for a, b in zip(sc[:-1], sc[1:]))
+    out = []
+    for fused in (1, 0):
+        T = C.c_void_p()
+        assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+        assert lib.nav_trainer_set_fused(T, fused) == 0
+        assert lib.nav_train_insert(T, *[_p(d) for d in dev], None, N, None) == 0
+        assert lib.nav_train_update(T, 4, None) == 0
+        torch.cuda.synchronize()
+        out.append((_io(lib, T, 0, n_a), _io(lib, T, 1, n_c), _io(lib, T, 2, n_c),
+                    _io(lib, T, 3, n_c), _io(lib, T, 24, 16), _io(lib, T, 11, n_c)))
+        lib.nav_trainer_free(T)
+    names = ["actor", "critic 1", "critic 2", "target 1", "scalars", "critic 1 grad"]
+    for name, a, b in zip(names, *out):
+        e = _rel(a, b)
+        print(f"fused vs per-layer {name}: rel {e:.2e}")
+        assert e < (2e-2 if name.endswith("grad") else 1e-3), (name, e)
+
+
+def test_fused_path_is_refused_for_wide_networks(env):
+    flashnav, _ = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.batch, cfg.replay_capacity = 256, 1024
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0  # 364 inputs, 256 wide
+    assert lib.nav_trainer_set_fused(T, 1) != 0
+    assert lib.nav_trainer_set_fused(T, 0) == 0
+    lib.nav_trainer_free(T)
