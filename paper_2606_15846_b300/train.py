@@ -252,6 +252,7 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
     # once learning runs, two iterations (obs buffers 0 -> 1 -> 0) are one
     # CUDA graph: collector, replay insert, the updates and the actor syncs
     graph = None
+    inflight = []
     use_graph = cfg.graph and cfg.utd % tc.policy_freq == 0 and cfg.steps_per_sync in (1, 2)
     while True:
         el = time.perf_counter() - t0
@@ -274,6 +275,12 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
                     iteration(0, cfg.steps_per_sync == 1)
                     iteration(1, True)
             graph.replay()
+            # at most two replays in flight, so that the wall clock the loop
+            # reads (evaluation cadence, budget) tracks the device
+            inflight.append(torch.cuda.Event())
+            inflight[-1].record(side)
+            if len(inflight) > 2:
+                inflight.pop(0).synchronize()
             n_transitions += 2 * E
             step += 2
             continue
