@@ -332,12 +332,17 @@ def training_paper(seconds: float, robot: str = "turtlebot2"):
     for thr in (0.90, 0.95, 1.00):
         hit = [h["t"] for h in hist if h["success"] >= thr]
         reach[f"{int(thr * 100)}%"] = hit[0] if hit else None
+    # training-cycle time of the serial graph, for Sec. 3.3's comparison
+    serial = TR.train(TR.paper_config(robot, time_budget_s=3.0, threshold=2.0, overlap=False),
+                      log=lambda *a: None)
     return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
             "budget_s": seconds, "env_steps": res["env_steps"],
+            "cycle_ms_overlapped": res["cycle_ms"], "cycle_ms_serial": serial["cycle_ms"],
             "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
             "config": f"{robot} preset: 1024 envs, one shared map, 1080 beams marched 0.03 m, "
-                      "30 sectors, Eq. 2 inputs, (100)x4 nets, batch 1024, UTD 40, gamma 0.97, "
-                      "AdamW 1e-3, eval every 1 s on 1000 fresh episodes"}
+                      "30 sectors, Eq. 2 inputs, (100)x4 nets on the fused passes, batch 1024, "
+                      "UTD 40, gamma 0.97, AdamW 1e-3, collector/learner overlapped, one CUDA "
+                      "graph per two env steps, eval every 1 s on 1000 fresh episodes"}
 
 
 def _sub_workload(wl, n):
@@ -536,6 +541,8 @@ def run_gpu(args):
             line["policy_rollout"] = policy_rollout()
             line["uneven_batch"] = uneven_batch()
             line["paper_sensing"] = paper_sensing()
+            if args.train_seconds > 0:
+                line["training_paper_turtlebot2"] = training_paper(min(args.train_seconds, 25.0))
             if args.train_seconds > 0:
                 line["training"] = training_run(args.train_seconds)
         print(json.dumps(line), flush=True)

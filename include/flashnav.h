@@ -377,6 +377,15 @@ int nav_train_insert(nav_trainer *t, const float *obs_dev, const float *act_dev,
  * nav_trainer_set_graphs). */
 int nav_train_update(nav_trainer *t, int n_updates, void *stream);
 
+/* Overlapped collector / learner (Sec. 3.3's producer-consumer pipeline):
+ * before updates that run concurrently with a nav_train_insert of n_pending
+ * transitions on another stream, call this on the learner's stream ahead of
+ * the fork point; it snapshots the replay's head and size, and the updates'
+ * draws then skip the n_pending slots the insert overwrites (so no update
+ * reads a slot being written).  n_pending = 0 (after the join) restores the
+ * plain draw.  Asynchronous on `stream`. */
+int nav_train_overlap(nav_trainer *t, int n_pending, void *stream);
+
 /* on = 1: nav_train_update captures each distinct (n_updates, policy phase)
  * sequence once on its (non-null) stream and replays the graph afterwards
  * (about 180 small launches per update become one graph launch).  Results

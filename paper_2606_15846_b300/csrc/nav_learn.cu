@@ -47,7 +47,8 @@ __device__ __forceinline__ float softplusf(float x) {
 // update graph replays correctly): [0] critic updates, [1] actor updates,
 // [2] replay head, [3] replay size.  corr holds Adam's bias corrections
 // (1 - b1^t, 1 - b2^t) of the current critic [0..1] and actor [2..3] step.
-enum { kCtrCritic = 0, kCtrActor = 1, kCtrHead = 2, kCtrSize = 3 };
+enum { kCtrCritic = 0, kCtrActor = 1, kCtrHead = 2, kCtrSize = 3, kCtrSnapHead = 4,
+       kCtrSnapSize = 5, kCtrPending = 6 };
 
 // Starts critic (which 0) or actor (which 1) step t = ++ctr[which]; the
 // step's kernels use t - 1 as their update index.
@@ -89,13 +90,31 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
     }
 }
 
+// Uniform replay indices.  While a collector inserts E = ctr[pending]
+// transitions concurrently (overlapped pipeline), the draw uses the (head,
+// size) snapshot taken before the insert began and skips the E slots it
+// writes: with s + E <= cap those lie beyond the s valid ones; otherwise the
+// n = cap - E safe slots start right after them.
 __global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__ ctr,
-                         unsigned long long seed) {
+                         unsigned long long seed, long long cap) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const unsigned long long update = ctr[kCtrCritic] - 1, size = ctr[kCtrSize];
+    const unsigned long long update = ctr[kCtrCritic] - 1, E = ctr[kCtrPending];
+    const unsigned long long s = E ? ctr[kCtrSnapSize] : ctr[kCtrSize];
+    const unsigned long long hd = E ? ctr[kCtrSnapHead] : ctr[kCtrHead];
+    const unsigned long long C = (unsigned long long)cap;
+    const bool wrap = s + E > C;
+    const unsigned long long n = wrap ? C - E : s;
     const unsigned long long h = hmix(seed ^ (update * 0xD6E8FEB86659FD93ull) ^ ((unsigned long long)b << 1));
-    idx[b] = (int)(((h >> 32) * (unsigned long long)size) >> 32);
+    const unsigned long long r = ((h >> 32) * n) >> 32;
+    idx[b] = (int)(wrap ? (hd + E + r) % C : r);
+}
+
+// overlapped pipeline: snapshot (head, size) and the pending insert count
+__global__ void k_overlap(unsigned long long *ctr, unsigned long long pending) {
+    ctr[kCtrSnapHead] = ctr[kCtrHead];
+    ctr[kCtrSnapSize] = ctr[kCtrSize];
+    ctr[kCtrPending] = pending;
 }
 
 // Eq. 2 on a stored raw range: s / (l - beta), rounded to BF16
@@ -753,7 +772,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->dZT16, B * H);
     TA(T->scal, 16);
     TA(T->status, 1);
-    TA(T->ctr, 4);
+    TA(T->ctr, 8);
     TA(T->corr, 4);
     T->fused = rc == NAV_OK && fused_ok(T->actor, T->B) && fused_ok(T->q[0], T->B);
     if (T->fused) {
@@ -869,7 +888,7 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
     const int none[2] = {-1, -1}, qslot[2] = {1, 2}, aslot[1] = {0};
     k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
-    k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed);
+    k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed, T->cap);
     k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
         T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
         T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
@@ -947,7 +966,7 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
     for (int u = 0; u < n_updates; ++u) {
         // ---- critic update (index ctr[critic] - 1 after k_count)
         k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
-        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed);
+        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed, T->cap);
         k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
             T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
             T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
@@ -1056,6 +1075,14 @@ int nav_train_update(nav_trainer *T, int n_updates, void *stream) {
     T->n_critic += (unsigned long long)n_updates;
     T->n_actor += n_act;
     return NAV_OK;
+}
+
+int nav_train_overlap(nav_trainer *T, int n_pending, void *stream) {
+    if (!T || n_pending < 0 || (long long)n_pending >= T->cap)
+        return tfail(T, NAV_E_INVAL, "nav_train_overlap: bad argument");
+    k_overlap<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(T->ctr,
+                                                             (unsigned long long)n_pending);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
 }
 
 int nav_trainer_set_fused(nav_trainer *T, int on) {

@@ -28,7 +28,7 @@ EXPORTS = [
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
     "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_policy_act_counted",
-    "nav_rollout", "nav_trainer_set_graphs", "nav_trainer_set_fused",
+    "nav_rollout", "nav_trainer_set_graphs", "nav_trainer_set_fused", "nav_train_overlap",
     "nav_train_default_cfg", "nav_trainer_create", "nav_trainer_free", "nav_trainer_last_error",
     "nav_train_insert", "nav_train_update", "nav_trainer_sync_policy", "nav_trainer_io",
     "nav_trainer_counts", "nav_eval_begin", "nav_eval_accumulate", "nav_eval_result",
@@ -132,6 +132,7 @@ def load():
         "nav_train_update": (I, [P, I, P]),
         "nav_trainer_set_graphs": (I, [P, I]),
         "nav_trainer_set_fused": (I, [P, I]),
+        "nav_train_overlap": (I, [P, I, P]),
         "nav_policy_act_counted": (I, [P, P, C.c_int64, I, I, U64, P, P, P, P, P]),
         "nav_trainer_sync_policy": (I, [P, P, P]),
         "nav_trainer_io": (I, [P, I, I, P]),

@@ -54,6 +54,7 @@ class TrainConfig:
     ipap: bool = False  # Eq. 2 on the range features, beta trained with the actor
     steps_per_sync: int = 1
     graph: bool = True        # capture collector + updates in one CUDA graph once learning runs
+    overlap: bool = False     # collector of step t + 1 on a second stream beside step t's updates
     goal_dmax: float = 6.0    # paper setting: straight-line goal distance bound (m)
     occupancy: float = 0.10   # paper setting: occupied fraction of the stand-in map
     corridors: bool = False   # paper setting: corridor walls in the stand-in map
@@ -64,10 +65,12 @@ def paper_config(robot: str = "turtlebot2", **kw) -> TrainConfig:
     """Tables 3-4 and 7-9: 1024 envs on one shared map, 1080 beams marched at
     0.03 m and pooled into 30 sectors, (100) x 4 networks, batch 1024,
     gamma 0.97, AdamW 1e-3, UTD 40, learning start 8192, Eq. 2 inputs, actor
-    sync every 1 (TurtleBot2) or 2 (Go2) env steps."""
+    sync every 1 (TurtleBot2) or 2 (Go2) env steps, collector and learner
+    overlapped (Sec. 3.3)."""
     base = dict(robot=robot, setting="paper", n_envs=1024, batch=1024, utd=40, hidden=100,
                 n_hidden=4, gamma=0.97, weight_decay=1e-3, ipap=True, learning_starts=8192,
-                beams=1080, max_range=20.0, steps_per_sync=1 if robot == "turtlebot2" else 2)
+                beams=1080, max_range=20.0, steps_per_sync=1 if robot == "turtlebot2" else 2,
+                overlap=True)
     base.update(kw)
     return TrainConfig(**base)
 
@@ -249,10 +252,38 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
             if sync:
                 assert lib.nav_trainer_sync_policy(T, pol, S) == 0
 
+    coll = torch.cuda.Stream()
+    S_coll = C.c_void_p(coll.cuda_stream)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+
+    def iteration_overlapped(cur, sync):
+        """Producer-consumer (Sec. 3.3): the collector step on its own stream
+        runs beside the updates on the learner's, which draw only replay slots
+        the concurrent insert does not write; the actor sync waits for both."""
+        nxt = 1 - cur
+        assert lib.nav_train_overlap(T, E, S) == 0
+        fork.record(side)
+        coll.wait_event(fork)
+        with torch.cuda.stream(coll):
+            assert lib.nav_policy_act_counted(pol, _p(obs[cur]), od, E, 1, cfg.seed,
+                                              _p(noise_step), _p(act), None, None, S_coll) == 0
+            sim.step(act, obs[nxt], rew, done, final_obs=fin)
+            assert lib.nav_train_insert(T, _p(obs[cur]), _p(act), _p(rew), _p(done),
+                                        _p(obs[nxt]), _p(fin), E, S_coll) == 0
+        rc = lib.nav_train_update(T, cfg.utd, S)
+        if rc:
+            raise F.NavError(rc, lib.nav_trainer_last_error(T).decode())
+        join.record(coll)
+        side.wait_event(join)
+        assert lib.nav_train_overlap(T, 0, S) == 0
+        if sync:
+            assert lib.nav_trainer_sync_policy(T, pol, S) == 0
+
     # once learning runs, two iterations (obs buffers 0 -> 1 -> 0) are one
     # CUDA graph: collector, replay insert, the updates and the actor syncs
     graph = None
     inflight = []
+    n_replays = 0
     use_graph = cfg.graph and cfg.utd % tc.policy_freq == 0 and cfg.steps_per_sync in (1, 2)
     while True:
         el = time.perf_counter() - t0
@@ -271,10 +302,12 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
         if use_graph and learning() and cur == 0:
             if graph is None:
                 graph = torch.cuda.CUDAGraph()
+                step_fn = iteration_overlapped if cfg.overlap else iteration
                 with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
-                    iteration(0, cfg.steps_per_sync == 1)
-                    iteration(1, True)
+                    step_fn(0, cfg.steps_per_sync == 1)
+                    step_fn(1, True)
             graph.replay()
+            n_replays += 1
             # at most two replays in flight, so that the wall clock the loop
             # reads (evaluation cadence, budget) tracks the device
             inflight.append(torch.cuda.Event())
@@ -294,11 +327,24 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
         history.append({"t": el, "success": rate, "return": mret, "env_steps": step * E,
                         "transitions": n_transitions})
         log(f"t={el:6.2f}s env_steps={step * E:>10d} success={rate:.3f} return={mret:8.3f}")
+    # training-cycle time (Sec. 3.3): device time of one collector step with
+    # its UTD updates, from 10 extra graph replays after the run
+    cycle_ms = None
+    if graph is not None:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for _ in range(10):
+            graph.replay()
+        e1.record(side)
+        e1.synchronize()
+        cycle_ms = e0.elapsed_time(e1) / 20.0
     torch.cuda.synchronize()
     ctx.__exit__(None, None, None)
     del graph
     lib.nav_trainer_free(T)
-    out = {"time_to_threshold_s": reached, "history": history, "env_steps": step * E}
+    out = {"time_to_threshold_s": reached, "history": history, "env_steps": step * E,
+           "cycle_ms": cycle_ms}
     if keep_policy:
         out["policy"] = pol
     else:

@@ -373,3 +373,45 @@ def test_fused_path_is_refused_for_wide_networks(env):
     assert lib.nav_trainer_set_fused(T, 1) != 0
     assert lib.nav_trainer_set_fused(T, 0) == 0
     lib.nav_trainer_free(T)
+
+
+@pytest.mark.parametrize("size,pending,lo,hi", [(2000, 1000, 952, 2000), (2048, 512, 0, 2048)])
+def test_overlapped_draws_skip_the_slots_being_written(env, size, pending, lo, hi):
+    """Producer-consumer pipeline: with an insert of `pending` transitions in
+    flight, the updates draw only slots that insert leaves alone (ring of
+    2048; head at `size` mod 2048)."""
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.obs_dim, cfg.hidden, cfg.n_hidden = 34, 100, 2
+    cfg.batch, cfg.replay_capacity, cfg.seed = 1024, 2048, 3
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+    rng = np.random.default_rng(0)
+    n_ins = size if size < 2048 else 2048 + 700  # full ring with the head at 700
+    data = [rng.uniform(0, 6, (n_ins, 34)).astype(np.float32),
+            rng.uniform(-1, 1, (n_ins, 2)).astype(np.float32),
+            rng.normal(0, 1, n_ins).astype(np.float32),
+            np.zeros(n_ins, np.uint8),
+            rng.uniform(0, 6, (n_ins, 34)).astype(np.float32)]
+    dev = [torch.from_numpy(a).cuda() for a in data]
+    for s0 in range(0, n_ins, 1000):
+        n = min(1000, n_ins - s0)
+        part = [d[s0:s0 + n].contiguous() for d in dev]
+        assert lib.nav_train_insert(T, *[_p(d) for d in part], None, n, None) == 0
+    head = n_ins % 2048
+    assert lib.nav_train_overlap(T, pending, None) == 0
+    seen = []
+    for _ in range(6):
+        assert lib.nav_train_update(T, 1, None) == 0
+        seen.append(_io(lib, T, 20, 1024, np.int32))
+    assert lib.nav_train_overlap(T, 0, None) == 0
+    idx = np.concatenate(seen)
+    written = {(head + e) % 2048 for e in range(pending)}
+    assert not (set(idx.tolist()) & written)
+    if size < 2048:
+        assert idx.min() >= lo and idx.max() < hi
+    # the safe set is covered roughly uniformly
+    assert len(set(idx.tolist())) > 0.9 * min(2048 - pending, len(idx)) * 0.6
+    lib.nav_trainer_free(T)
