@@ -220,3 +220,80 @@ def alpha_grad(log_alpha, logp, target_entropy):
 
 def soft_update(target, online, tau):
     return (1.0 - tau) * target + tau * online
+
+
+# ---------------------------------------------------------------------------
+# FastSAC with categorical (C51) critics (Sec. 2.3 FastSAC paragraph; Table 5:
+# 101 atoms on [-20, 20]).  Readings: each critic outputs one logit per atom;
+# the target takes, per sample, the target critic whose expected value is
+# smaller (clipped double Q); soft target atoms rs r + gamma (1 - term)
+# (z_j - alpha logpi') are clipped to [v_min, v_max] and projected onto the
+# fixed support by linear interpolation (Bellemare et al. 2017, Algorithm 1);
+# both critics minimise the cross-entropy to that target; the actor minimises
+# mean(alpha logpi - min_j E[Q_j]).
+# ---------------------------------------------------------------------------
+def c51_support(n_atoms, v_min, v_max):
+    return np.linspace(v_min, v_max, n_atoms)
+
+
+def softmax(x):
+    e = np.exp(x - x.max(axis=1, keepdims=True))
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def c51_project(p, shift, scale, v_min, v_max):
+    """Projection of the distribution p [B, n] on the support z, moved to
+    shift + scale z (per sample), onto the same support."""
+    B, n = p.shape
+    z = c51_support(n, v_min, v_max)
+    dz = (v_max - v_min) / (n - 1)
+    tz = np.clip(shift[:, None] + scale[:, None] * z[None, :], v_min, v_max)
+    b = (tz - v_min) / dz
+    lo = np.floor(b).astype(np.int64)
+    hi = np.ceil(b).astype(np.int64)
+    m = np.zeros_like(p)
+    for i in range(B):
+        for j in range(n):
+            if lo[i, j] == hi[i, j]:
+                m[i, lo[i, j]] += p[i, j]
+            else:
+                m[i, lo[i, j]] += p[i, j] * (hi[i, j] - b[i, j])
+                m[i, hi[i, j]] += p[i, j] * (b[i, j] - lo[i, j])
+    return m
+
+
+def c51_targets(rew, term, tl1, tl2, logp_next, alpha, gamma, rscale, v_min, v_max):
+    """Target distribution from the two target critics' logits [B, n]."""
+    n = tl1.shape[1]
+    z = c51_support(n, v_min, v_max)
+    p1, p2 = softmax(tl1), softmax(tl2)
+    pick1 = (p1 @ z) <= (p2 @ z)
+    p = np.where(pick1[:, None], p1, p2)
+    cont = gamma * (1.0 - term)
+    shift = rscale * rew - cont * alpha * logp_next
+    return c51_project(p, shift, cont, v_min, v_max)
+
+
+def c51_critic_loss(logits, m):
+    """Mean cross-entropy -sum_i m_i log softmax(logits)_i and its gradient."""
+    B = logits.shape[0]
+    lse = np.log(np.exp(logits - logits.max(axis=1, keepdims=True)).sum(axis=1)) + logits.max(axis=1)
+    logp = logits - lse[:, None]
+    loss = -(m * logp).sum(axis=1).mean()
+    return loss, (softmax(logits) - m) / B
+
+
+def c51_actor_grads(logp, l1, l2, alpha, v_min, v_max):
+    """L = mean(alpha logp - min_j E[Q_j]) with E[Q_j] = softmax(l_j) . z:
+    returns L, dL/dlogp and dL/dl_j (the logits of both critics)."""
+    B, n = l1.shape
+    z = c51_support(n, v_min, v_max)
+    p1, p2 = softmax(l1), softmax(l2)
+    q1, q2 = p1 @ z, p2 @ z
+    pick1 = q1 <= q2
+    loss = (alpha * logp - np.where(pick1, q1, q2)).mean()
+    dq1 = -(p1 * (z[None, :] - q1[:, None])) / B
+    dq2 = -(p2 * (z[None, :] - q2[:, None])) / B
+    dl1 = np.where(pick1[:, None], dq1, 0.0)
+    dl2 = np.where(pick1[:, None], 0.0, dq2)
+    return loss, np.full(B, alpha / B), dl1, dl2

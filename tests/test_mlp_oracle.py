@@ -191,3 +191,73 @@ def test_ipap_beta_gradient_matches_finite_differences():
     h = 1e-6
     fd = (loss(beta + h) - loss(beta - h)) / (2 * h)
     assert abs(g - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+# --------------------------------------------------------------------------
+# FastSAC C51 pieces (Table 5: 101 atoms, [-20, 20])
+# --------------------------------------------------------------------------
+def _dist(rng, B, n):
+    return M.softmax(rng.normal(0, 2, (B, n)))
+
+
+def test_c51_projection_keeps_mass_and_identity():
+    rng = np.random.default_rng(0)
+    p = _dist(rng, 6, 101)
+    m = M.c51_project(p, rng.normal(0, 3, 6), rng.uniform(0, 1, 6), -20, 20)
+    np.testing.assert_allclose(m.sum(axis=1), 1.0, atol=1e-12)
+    assert (m >= -1e-15).all()
+    # shift 0, scale 1: every atom lands on itself
+    np.testing.assert_allclose(M.c51_project(p, np.zeros(6), np.ones(6), -20, 20), p, atol=1e-12)
+
+
+def test_c51_projection_moves_mass_by_whole_atoms():
+    """A shift of exactly k atoms moves the distribution by k, clamped at the
+    ends of the support (Bellemare et al. 2017, Algorithm 1)."""
+    rng = np.random.default_rng(1)
+    p = _dist(rng, 3, 101)
+    m = M.c51_project(p, np.full(3, 2 * 0.4), np.ones(3), -20, 20)
+    np.testing.assert_allclose(m[:, 2:100], p[:, 0:98], atol=1e-12)
+    np.testing.assert_allclose(m[:, 100], p[:, 98:].sum(axis=1), atol=1e-12)
+    assert np.abs(m[:, :2]).max() < 1e-15
+
+
+def test_c51_projection_preserves_the_mean_inside_the_support():
+    """Linear interpolation keeps the expectation: E_m[z] = shift + scale E_p[z]
+    when no atom is clipped."""
+    rng = np.random.default_rng(2)
+    z = M.c51_support(101, -20, 20)
+    p = np.zeros((5, 101))
+    p[:, 30:70] = _dist(rng, 5, 40)
+    shift, scale = rng.uniform(-3, 3, 5), rng.uniform(0.5, 1.0, 5)
+    m = M.c51_project(p, shift, scale, -20, 20)
+    np.testing.assert_allclose(m @ z, shift + scale * (p @ z), atol=1e-10)
+
+
+def test_c51_targets_pick_the_lower_critic():
+    rng = np.random.default_rng(3)
+    n = 101
+    l1, l2 = rng.normal(0, 1, (4, n)), rng.normal(0, 1, (4, n))
+    l2[:2] += np.linspace(-3, 3, n)  # critic 2 higher on samples 0, 1
+    l1[2:] += np.linspace(-3, 3, n)  # critic 1 higher on samples 2, 3
+    m = M.c51_targets(np.zeros(4), np.zeros(4), l1, l2, np.zeros(4), 0.0, 1.0, 1.0, -20, 20)
+    np.testing.assert_allclose(m[:2], M.softmax(l1[:2]), atol=1e-12)
+    np.testing.assert_allclose(m[2:], M.softmax(l2[2:]), atol=1e-12)
+
+
+def test_c51_critic_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    logits = rng.normal(0, 1, (3, 11))
+    m = _dist(rng, 3, 11)
+    _, g = M.c51_critic_loss(logits, m)
+    fd = _fd(lambda: M.c51_critic_loss(logits, m)[0], logits)
+    assert _rel(g, fd) < 1e-6
+
+
+def test_c51_actor_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    l1, l2 = rng.normal(0, 1, (4, 11)), rng.normal(0, 1, (4, 11))
+    logp = rng.normal(0, 1, 4)
+    _, dlogp, d1, d2 = M.c51_actor_grads(logp, l1, l2, 0.3, -20, 20)
+    f = lambda: M.c51_actor_grads(logp, l1, l2, 0.3, -20, 20)[0]
+    assert _rel(d1, _fd(f, l1)) < 1e-6 and _rel(d2, _fd(f, l2)) < 1e-6
+    assert _rel(dlogp, _fd(f, logp)) < 1e-6
