@@ -318,14 +318,14 @@ def training_run(seconds: float):
                       "batch 4096, 8 updates per env step, eval every 1 s"}
 
 
-def training_paper(seconds: float, robot: str = "turtlebot2"):
+def training_paper(seconds: float, robot: str = "turtlebot2", algo: str = "fastdsac"):
     """The paper's own training setting (Tables 3-4, 7-9; Table 2's protocol):
     FastDSAC from scratch on one shared map, 1024 envs, the 0.03 m march with
     30 sector minima through Eq. 2, (100) x 4 networks, UTD 40, batch 1024;
     wall-clock seconds (evaluation included) to 90 / 95 / 100 % success over
     1000 fresh episodes of that map."""
     from paper_2606_15846_b300 import train as TR
-    cfg = TR.paper_config(robot, time_budget_s=seconds, threshold=1.0)
+    cfg = TR.paper_config(robot, algo, time_budget_s=seconds, threshold=1.0)
     res = TR.train(cfg, log=lambda *a: None)
     hist = res["history"]
     reach = {}
@@ -333,13 +333,13 @@ def training_paper(seconds: float, robot: str = "turtlebot2"):
         hit = [h["t"] for h in hist if h["success"] >= thr]
         reach[f"{int(thr * 100)}%"] = hit[0] if hit else None
     # training-cycle time of the serial graph, for Sec. 3.3's comparison
-    serial = TR.train(TR.paper_config(robot, time_budget_s=3.0, threshold=2.0, overlap=False),
-                      log=lambda *a: None)
+    serial = TR.train(TR.paper_config(robot, algo, time_budget_s=3.0, threshold=2.0,
+                                      overlap=False), log=lambda *a: None)
     return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
             "budget_s": seconds, "env_steps": res["env_steps"],
             "cycle_ms_overlapped": res["cycle_ms"], "cycle_ms_serial": serial["cycle_ms"],
             "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
-            "config": f"{robot} preset: 1024 envs, one shared map, 1080 beams marched 0.03 m, "
+            "config": f"{robot} preset, {algo}: 1024 envs, one shared map, 1080 beams marched 0.03 m, "
                       "30 sectors, Eq. 2 inputs, (100)x4 nets on the fused passes, batch 1024, "
                       "UTD 40, gamma 0.97, AdamW 1e-3, collector/learner overlapped, one CUDA "
                       "graph per two env steps, eval every 1 s on 1000 fresh episodes"}
@@ -562,7 +562,7 @@ def main():
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "paper_sensing", "training",
-                             "training_paper", "training_paper_go2"],
+                             "training_paper", "training_paper_go2", "training_paper_fastsac"],
                     help="run one of the extra measurements alone")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
@@ -577,7 +577,9 @@ def main():
               "paper_sensing": paper_sensing,
               "training": lambda: training_run(args.train_seconds),
               "training_paper": lambda: training_paper(args.train_seconds),
-              "training_paper_go2": lambda: training_paper(args.train_seconds, "go2")}[args.only]
+              "training_paper_go2": lambda: training_paper(args.train_seconds, "go2"),
+              "training_paper_fastsac": lambda: training_paper(args.train_seconds, "turtlebot2",
+                                                               "fastsac")}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
     else:
         run_gpu(args)

@@ -330,7 +330,16 @@ int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t se
  * alpha logpi - min_i m_i every policy_freq critic updates; log alpha by Adam
  * towards target_entropy.  BF16 tensor-core GEMMs (tcgen05) with FP32 master
  * weights and FP32 Adam. */
-/* n_hidden hidden layers of `hidden` units in every network (1..4).
+/* algo 1 (Sec. 2.3 FastSAC; Table 5): twin categorical critics with n_atoms
+ * logits on the support z_i = v_min + i (v_max - v_min) / (n_atoms - 1); the
+ * target takes, per sample, the target critic with the smaller expected
+ * value, moves its atoms to rs r + gamma (1 - term) (z - alpha logpi') (clipped
+ * to the support) and projects them back by linear interpolation; both
+ * critics descend the cross-entropy to it; the actor descends
+ * mean(alpha logpi - min_j E[Q_j]); alpha as for FastDSAC.  Needs networks on
+ * the fused passes (every width <= 128).  Gaussian-critic fields (tau_b,
+ * huber_delta) are unused.
+ * n_hidden hidden layers of `hidden` units in every network (1..4).
  * weight_decay: decoupled (AdamW, Table 3) decay of weights and biases,
  * p <- p (1 - lr wd) before each Adam step; 0 = Adam.
  * ipap_features > 0: Eq. 2 on the first ipap_features observation features
@@ -349,6 +358,9 @@ typedef struct {
     float weight_decay;
     int ipap_features;
     float ipap_beta_init, ipap_beta_max;
+    int algo;           /* 0 FastDSAC (Gaussian critics), 1 FastSAC (C51 critics) */
+    int n_atoms;        /* FastSAC: atoms of the categorical critics (2..128) */
+    float v_min, v_max; /* FastSAC: support [v_min, v_max] */
 } nav_train_cfg;
 typedef struct nav_trainer nav_trainer;
 void nav_train_default_cfg(nav_train_cfg *c); /* obs 364, hidden 256 x 2, batch 4096, replay
@@ -392,8 +404,8 @@ int nav_train_overlap(nav_trainer *t, int n_pending, void *stream);
  * are those of the launches themselves. */
 int nav_trainer_set_graphs(nav_trainer *t, int on);
 
-/* Path of the updates.  Networks whose every width is <= 128 (with <= 8
- * outputs, batch a multiple of 128) run on fused passes by default: one
+/* Path of the updates.  Networks whose every width is <= 128 (batch a
+ * multiple of 128) run on fused passes by default: one
  * launch runs every layer of a network's forward or backward for 128 batch
  * rows (operands in shared memory, accumulators in TMEM), the twin critics
  * share launches, and one kernel applies AdamW to a whole network; ~25
@@ -413,7 +425,8 @@ int nav_trainer_sync_policy(nav_trainer *t, nav_policy *p, void *stream);
  * writes); 10..12 = last gradients of actor, critic 1, critic 2; 20 batch
  * indices, 21 actor-update noise, 22 next-action noise, 23 target noise,
  * 24 scalars (16 floats: [0] log alpha, [1] sbar, [11] last gradient of Eq. 2's
- * beta, [12] beta), 25 y, 26 y_mean, 27 critic-1 outputs,
+ * beta, [12] beta), 32 FastSAC target distributions [batch][n_atoms], 25 y,
+ * 26 y_mean, 27 critic-1 outputs ([batch][2], FastSAC [batch][n_atoms]),
  * 28 logpi of the actor update, 29 its actions, 30 actor outputs, 31 logpi of
  * the next actions. */
 int nav_trainer_io(nav_trainer *t, int what, int set, void *host);

@@ -289,23 +289,27 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
     };
     fetch(top, 0);
     const unsigned tmem = tmem_alloc(&tmem_slot, 256); // synchronises: G is zero
-    // top layer: G = dout (FP32 for the bias sums, BF16 in both layouts)
-    if (half == 0) {
-        float d[8];
+    // top layer: G = dout (FP32 for the bias sums, BF16 in both layouts);
+    // the halves split its columns as in the epilogues
+    {
+        const int j0 = 64 * half, j1 = min(round16(nout), j0 + 64);
+        for (int j = j0; j < j1; j += 16) {
+            float v[16];
+            const float *src = N.dout + (long long)grow * nout + j;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) d[i] = i < nout ? N.dout[(long long)grow * nout + i] : 0.0f;
-        for (int i = 0; i < nout; ++i) {
-            const bf16 h = __float2bfloat16_rn(d[i]);
-            *reinterpret_cast<bf16 *>(gnp + swz(row, i, kChunk)) = h;
-            *reinterpret_cast<bf16 *>(gtp + swz(i, row, kChunk)) = h;
-            float s = d[i];
+            for (int i = 0; i < 16; ++i) v[i] = j + i < nout ? src[i] : 0.0f;
+            *reinterpret_cast<uint4 *>(gnp + swz(row, j, kChunk)) = pack8(v);
+            *reinterpret_cast<uint4 *>(gnp + swz(row, j + 8, kChunk)) = pack8(v + 8);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) atomicAdd(&sdb[i], s);
+            for (int i = 0; i < 16; ++i)
+                *reinterpret_cast<bf16 *>(gtp + swz(j + i, row, kChunk)) = __float2bfloat16_rn(v[i]);
+            const float cs = colsum16(v, lane);
+            if ((lane & 1) == 0) atomicAdd(&sdb[j + colsum16_col(lane)], cs);
         }
     }
     __syncthreads();
-    if (N.gbp[top] && tid < nout) N.gbp[top][(long long)cta * N.cta_stride + tid] = sdb[tid];
+    if (N.gbp[top])
+        for (int t = tid; t < nout; t += kT) N.gbp[top][(long long)cta * N.cta_stride + t] = sdb[t];
     unsigned phase = 0;
     for (int l = top; l >= 0; --l) {
         const FLayer &L = N.L[l];
@@ -489,7 +493,6 @@ static_assert(kBwdSmem + 2048 <= 227 * 1024, "shared memory");
 
 bool fused_ok(const Mlp &m, int B) {
     if (B <= 0 || B % 128 || m.n_layers < 2) return false;
-    if (m.layer[m.n_layers - 1].out > 8) return false;
     for (int l = 0; l < m.n_layers; ++l) {
         if (m.layer[l].in > kFusedMaxWidth || m.layer[l].out > kFusedMaxWidth) return false;
         // one saved-activation row stride: every hidden layer has one width

@@ -401,6 +401,117 @@ __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc
     *log_alpha -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
 }
 
+// ------------------------------------------------------- FastSAC (C51) ---
+// One thread per sample; atoms z_i = v_min + i dz.
+__device__ __forceinline__ void c51_softmax_mean(const float *l, int n, float v_min, float dz,
+                                                 float &mx, float &sum, float &mean) {
+    mx = l[0];
+    for (int i = 1; i < n; ++i) mx = fmaxf(mx, l[i]);
+    sum = 0.0f;
+    float zs = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const float e = expf(l[i] - mx);
+        sum += e;
+        zs += e * (v_min + (float)i * dz);
+    }
+    mean = zs / sum;
+}
+
+// Target distribution m [B][n]: the target critic with the smaller expected
+// value, atoms moved to rs r + gamma (1 - term) (z - alpha logpi') and
+// clipped, projected back by linear interpolation.
+__global__ void k_c51_targets(const float *__restrict__ rew, const float *__restrict__ term,
+                              const float *__restrict__ tl1, const float *__restrict__ tl2,
+                              const float *__restrict__ logp_next,
+                              const float *__restrict__ log_alpha, int B, int n, float gamma,
+                              float rs, float v_min, float v_max, float *m) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float dz = (v_max - v_min) / (float)(n - 1);
+    const float *l1 = tl1 + (size_t)b * n, *l2 = tl2 + (size_t)b * n;
+    float mx1, s1, q1, mx2, s2, q2;
+    c51_softmax_mean(l1, n, v_min, dz, mx1, s1, q1);
+    c51_softmax_mean(l2, n, v_min, dz, mx2, s2, q2);
+    const bool p1 = q1 <= q2;
+    const float *l = p1 ? l1 : l2;
+    const float mx = p1 ? mx1 : mx2, inv = 1.0f / (p1 ? s1 : s2);
+    const float cont = gamma * (1.0f - term[b]);
+    const float shift = rs * rew[b] - cont * expf(*log_alpha) * logp_next[b];
+    float *mr = m + (size_t)b * n;
+    for (int i = 0; i < n; ++i) mr[i] = 0.0f;
+    for (int j = 0; j < n; ++j) {
+        const float pj = expf(l[j] - mx) * inv;
+        const float tz = fminf(fmaxf(shift + cont * (v_min + (float)j * dz), v_min), v_max);
+        const float bj = (tz - v_min) / dz;
+        const int lo = (int)floorf(bj), hi = (int)ceilf(bj);
+        if (lo == hi) {
+            mr[lo] += pj;
+        } else {
+            mr[lo] += pj * ((float)hi - bj);
+            mr[hi] += pj * (bj - (float)lo);
+        }
+    }
+}
+
+// Cross-entropy to m: dL/dlogits = (softmax - m) / B; acc[1] += loss
+__global__ void k_c51_critic_grad(const float *__restrict__ q, const float *__restrict__ m, int B,
+                                  int n, float *dq, float *acc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float ll = 0.0f;
+    if (b < B) {
+        const float *l = q + (size_t)b * n, *mr = m + (size_t)b * n;
+        float mx = l[0];
+        for (int i = 1; i < n; ++i) mx = fmaxf(mx, l[i]);
+        float sum = 0.0f;
+        for (int i = 0; i < n; ++i) sum += expf(l[i] - mx);
+        const float lse = mx + logf(sum), inv = 1.0f / sum, ib = 1.0f / (float)B;
+        for (int i = 0; i < n; ++i) {
+            ll -= mr[i] * (l[i] - lse);
+            dq[(size_t)b * n + i] = (expf(l[i] - mx) * inv - mr[i]) * ib;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[1], ll);
+}
+
+// Actor loss mean(alpha logp - min_j E[Q_j]): dL/dlogp, and dL/dlogits of the
+// smaller critic, -p_i (z_i - E[Q]) / B (zero for the other)
+__global__ void k_c51_actor_loss(const float *__restrict__ logp, const float *__restrict__ l1,
+                                 const float *__restrict__ l2, const float *__restrict__ log_alpha,
+                                 int B, int n, float v_min, float v_max, float *dlogp, float *dq1,
+                                 float *dq2, float *acc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float ll = 0.0f, lp = 0.0f;
+    if (b < B) {
+        const float dz = (v_max - v_min) / (float)(n - 1), ib = 1.0f / (float)B;
+        const float *a = l1 + (size_t)b * n, *c = l2 + (size_t)b * n;
+        float mx1, s1, q1, mx2, s2, q2;
+        c51_softmax_mean(a, n, v_min, dz, mx1, s1, q1);
+        c51_softmax_mean(c, n, v_min, dz, mx2, s2, q2);
+        const bool p1 = q1 <= q2;
+        const float alpha = expf(*log_alpha);
+        dlogp[b] = alpha * ib;
+        const float *l = p1 ? a : c;
+        const float mx = p1 ? mx1 : mx2, inv = 1.0f / (p1 ? s1 : s2), qm = p1 ? q1 : q2;
+        float *dsel = (p1 ? dq1 : dq2) + (size_t)b * n, *doth = (p1 ? dq2 : dq1) + (size_t)b * n;
+        for (int i = 0; i < n; ++i) {
+            const float pi = expf(l[i] - mx) * inv;
+            dsel[i] = -pi * ((v_min + (float)i * dz) - qm) * ib;
+            doth[i] = 0.0f;
+        }
+        ll = alpha * logp[b] - qm;
+        lp = logp[b];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        lp += __shfl_xor_sync(0xffffffffu, lp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], ll);
+        atomicAdd(&acc[1], lp);
+    }
+}
+
 // dL/dbeta of Eq. 2 through the actor's input: x = s / (l - beta) gives
 // dx/dbeta = s / (l - beta)^2; summed over the batch into *acc
 __global__ void k_beta_grad(const float *__restrict__ dX, int ldx, const float *__restrict__ Lraw,
@@ -487,6 +598,8 @@ using namespace flashnav;
 struct nav_trainer {
     nav_train_cfg cfg{};
     int od = 0, ld = 0, ldc = 0, H = 0, Hp = 0, NH = 0, B = 0, ipap = 0;
+    int qout = 2;            // critic outputs: (mean, scale), or n_atoms logits (FastSAC)
+    float *tdist = nullptr;  // FastSAC target distributions [B][n_atoms]
     long long cap = 0, size = 0, head = 0;
     unsigned long long n_critic = 0, n_actor = 0, n_alpha = 0;
     Mlp actor, q[2], qt[2];
@@ -669,6 +782,10 @@ void nav_train_default_cfg(nav_train_cfg *c) {
     c->ipap_features = 0;
     c->ipap_beta_init = -0.2f;
     c->ipap_beta_max = -0.01f;
+    c->algo = 0;
+    c->n_atoms = 101;
+    c->v_min = -20.0f;
+    c->v_max = 20.0f;
 }
 
 void nav_trainer_free(nav_trainer *t) {
@@ -695,7 +812,9 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
         c.policy_freq < 1 || c.n_hidden < 1 || c.n_hidden > kMaxLayers - 1 ||
         !(c.weight_decay >= 0.0f) || c.ipap_features < 0 || c.ipap_features > c.obs_dim ||
         (c.ipap_features > 0 &&
-         !(c.ipap_beta_max < 0.0f && c.ipap_beta_init <= c.ipap_beta_max)))
+         !(c.ipap_beta_max < 0.0f && c.ipap_beta_init <= c.ipap_beta_max)) ||
+        (c.algo != 0 && c.algo != 1) ||
+        (c.algo == 1 && (c.n_atoms < 2 || c.n_atoms > kFusedMaxWidth || !(c.v_min < c.v_max))))
         return NAV_E_INVAL;
     nav_trainer *T = new (std::nothrow) nav_trainer();
     if (!T) return NAV_E_NOMEM;
@@ -709,13 +828,14 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     T->ipap = c.ipap_features;
     T->B = c.batch;
     T->cap = c.replay_capacity;
+    T->qout = c.algo == 1 ? c.n_atoms : 2;
     std::vector<int> sa(1, T->od), sq(1, T->od + 2);
     for (int l = 0; l < T->NH; ++l) {
         sa.push_back(T->H);
         sq.push_back(T->H);
     }
     sa.push_back(4);
-    sq.push_back(2);
+    sq.push_back(T->qout);
     int rc = T->actor.init(sa, c.seed * 4 + 1, T->err);
     for (int i = 0; i < 2 && rc == NAV_OK; ++i) {
         rc = T->q[i].init(sq, c.seed * 4 + 2 + i, T->err);
@@ -748,10 +868,10 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->dXa, B * T->ld);
     TA(T->out_a, B * 4);
     for (int i = 0; i < 2; ++i) {
-        TA(T->qo[i], B * 2);
-        TA(T->tq[i], B * 2);
-        TA(T->qa[i], B * 2);
-        TA(T->dq[i], B * 2);
+        TA(T->qo[i], B * T->qout);
+        TA(T->tq[i], B * T->qout);
+        TA(T->qa[i], B * T->qout);
+        TA(T->dq[i], B * T->qout);
         TA(T->dX[i], B * T->ldc);
     }
     TA(T->a_next, B * 2);
@@ -775,6 +895,12 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->ctr, 8);
     TA(T->corr, 4);
     T->fused = rc == NAV_OK && fused_ok(T->actor, T->B) && fused_ok(T->q[0], T->B);
+    if (c.algo == 1) TA(T->tdist, B * T->qout);
+    if (e == cudaSuccess && rc == NAV_OK && c.algo == 1 && !T->fused) {
+        T->err = "FastSAC needs networks on the fused passes (every width <= 128)";
+        rc = NAV_E_INVAL;
+        e = cudaErrorInvalidValue;
+    }
     if (T->fused) {
         T->n_cta = T->B / 128;
         for (int sl = 0; sl < 4; ++sl)
@@ -902,15 +1028,26 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
                                                             T->ldc, T->Xnc);
     rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
-    k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
-                                         T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr,
-                                         T->y, T->ym, T->znoise);
+    const bool c51 = c.algo == 1;
+    if (c51)
+        k_c51_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1],
+                                                 T->logp_next, T->scal + 0, B, T->qout, c.gamma,
+                                                 c.reward_scale, c.v_min, c.v_max, T->tdist);
+    else
+        k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
+                                             T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
+                                             T->ctr, T->y, T->ym, T->znoise);
     // critics
     rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
-    for (int i = 0; i < 2; ++i)
-        k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
-                                                 c.huber_delta, T->dq[i], T->scal + 4);
-    k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+    for (int i = 0; i < 2; ++i) {
+        if (c51)
+            k_c51_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->tdist, B, T->qout, T->dq[i],
+                                                         T->scal + 4);
+        else
+            k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
+                                                     c.huber_delta, T->dq[i], T->scal + 4);
+    }
+    if (!c51) k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
     rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
     rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
                             c.weight_decay, st);
@@ -925,8 +1062,13 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
                                                                 T->ldc, T->Xa);
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
         k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
-        k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0, B,
-                                                T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+        if (c51)
+            k_c51_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1],
+                                                        T->scal + 0, B, T->qout, c.v_min, c.v_max,
+                                                        T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+        else
+            k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
+                                                    B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
         rc |= fbwd(T, qs, 2, T->dq, qslot, nullptr, nullptr, T->dX, T->ldc, st);
         k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                     T->ldc, T->od, T->dlogp, B, T->dout);
@@ -1088,6 +1230,8 @@ int nav_train_overlap(nav_trainer *T, int n_pending, void *stream) {
 int nav_trainer_set_fused(nav_trainer *T, int on) {
     if (!T) return NAV_E_INVAL;
     if (on && !T->part_a) return tfail(T, NAV_E_INVAL, "networks too wide for the fused passes");
+    if (!on && T->cfg.algo == 1)
+        return tfail(T, NAV_E_INVAL, "FastSAC runs on the fused passes only");
     T->fused = on != 0;
     for (auto &g : T->graphs) cudaGraphExecDestroy(g.exec);
     T->graphs.clear();
@@ -1121,8 +1265,9 @@ int nav_trainer_io(nav_trainer *T, int what, int set, void *host) {
     struct { int id; void *p; size_t bytes; } bufs[] = {
         {20, T->idx, B * 4},        {21, T->eps_new, B * 8},  {22, T->eps_next, B * 8},
         {23, T->znoise, B * 4},     {24, T->scal, 16 * 4},    {25, T->y, B * 4},
-        {26, T->ym, B * 4},         {27, T->qo[0], B * 8},    {28, T->logp_new, B * 4},
-        {29, T->a_new, B * 8},      {30, T->out_a, B * 16},   {31, T->logp_next, B * 4}};
+        {26, T->ym, B * 4},         {27, T->qo[0], B * 4 * T->qout}, {28, T->logp_new, B * 4},
+        {29, T->a_new, B * 8},      {30, T->out_a, B * 16},   {31, T->logp_next, B * 4},
+        {32, T->tdist, T->tdist ? B * 4 * T->qout : 0}};
     for (auto &b : bufs)
         if (b.id == what) {
             const cudaError_t e = set ? cudaMemcpy(b.p, host, b.bytes, cudaMemcpyHostToDevice)

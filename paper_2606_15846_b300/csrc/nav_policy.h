@@ -56,8 +56,8 @@ int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long
                           float *act, float *logp, float *eps, void *stream);
 
 // ---------------------------------------------------------------------------
-// Fused passes for small networks (every layer's in and out <= 128, at most
-// 8 outputs, batch a multiple of 128): one CTA per 128 batch rows runs every
+// Fused passes for small networks (every layer's in and out <= 128, batch a
+// multiple of 128): one CTA per 128 batch rows runs every
 // layer of a network with its operands in shared memory and accumulators in
 // TMEM; grid.y selects one of up to two networks (the twin critics).
 // ---------------------------------------------------------------------------

@@ -46,7 +46,9 @@ class nav_train_cfg(C.Structure):
                 ("alpha_init", C.c_float), ("target_entropy", C.c_float),
                 ("policy_freq", C.c_int), ("seed", C.c_uint64), ("n_hidden", C.c_int),
                 ("weight_decay", C.c_float), ("ipap_features", C.c_int),
-                ("ipap_beta_init", C.c_float), ("ipap_beta_max", C.c_float)]
+                ("ipap_beta_init", C.c_float), ("ipap_beta_max", C.c_float),
+                ("algo", C.c_int), ("n_atoms", C.c_int), ("v_min", C.c_float),
+                ("v_max", C.c_float)]
 
 
 class NavError(RuntimeError):

@@ -55,22 +55,27 @@ class TrainConfig:
     steps_per_sync: int = 1
     graph: bool = True        # capture collector + updates in one CUDA graph once learning runs
     overlap: bool = False     # collector of step t + 1 on a second stream beside step t's updates
+    algo: str = "fastdsac"    # or "fastsac" (C51 critics, Table 5)
+    policy_freq: int = 2      # critic updates per actor update
+    reward_scale: float = 0.4
     goal_dmax: float = 6.0    # paper setting: straight-line goal distance bound (m)
     occupancy: float = 0.10   # paper setting: occupied fraction of the stand-in map
     corridors: bool = False   # paper setting: corridor walls in the stand-in map
     alpha_init: float = 0.001
 
 
-def paper_config(robot: str = "turtlebot2", **kw) -> TrainConfig:
+def paper_config(robot: str = "turtlebot2", algo: str = "fastdsac", **kw) -> TrainConfig:
     """Tables 3-4 and 7-9: 1024 envs on one shared map, 1080 beams marched at
     0.03 m and pooled into 30 sectors, (100) x 4 networks, batch 1024,
     gamma 0.97, AdamW 1e-3, UTD 40, learning start 8192, Eq. 2 inputs, actor
     sync every 1 (TurtleBot2) or 2 (Go2) env steps, collector and learner
-    overlapped (Sec. 3.3)."""
+    overlapped (Sec. 3.3).  algo "fastsac": Table 5's C51 critics."""
     base = dict(robot=robot, setting="paper", n_envs=1024, batch=1024, utd=40, hidden=100,
                 n_hidden=4, gamma=0.97, weight_decay=1e-3, ipap=True, learning_starts=8192,
                 beams=1080, max_range=20.0, steps_per_sync=1 if robot == "turtlebot2" else 2,
-                overlap=True)
+                overlap=True, algo=algo)
+    if algo == "fastsac":  # Table 5: policy frequency 1 / 2; no reward scale listed
+        base.update(policy_freq=1 if robot == "turtlebot2" else 2, reward_scale=1.0)
     base.update(kw)
     return TrainConfig(**base)
 
@@ -175,6 +180,8 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
         cfg.weight_decay
     tc.ipap_features = ipap
     tc.alpha_init = cfg.alpha_init
+    tc.policy_freq, tc.reward_scale = cfg.policy_freq, cfg.reward_scale
+    tc.algo = 1 if cfg.algo == "fastsac" else 0
     pol = C.c_void_p()
     assert lib.nav_policy_create_ex(od, cfg.hidden, cfg.n_hidden, ipap,
                                     C.c_float(tc.ipap_beta_init), max(cfg.n_envs, cfg.n_eval),

@@ -85,6 +85,8 @@ CONFIGS = {
     # the same networks on the per-layer GEMM path instead of the fused passes
     "paper_per_layer": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True,
                             fused=0),
+    # FastSAC (Table 5): twin C51 critics, 101 atoms on [-20, 20]
+    "fastsac": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True, algo=1),
 }
 
 
@@ -112,6 +114,9 @@ def run_update(flashnav, torch, name, P, strict=True):
     cfg.obs_dim, cfg.hidden, cfg.n_hidden = od, H, NH
     cfg.batch, cfg.replay_capacity, cfg.policy_freq, cfg.seed = 256, 2048, 1, 7
     cfg.weight_decay, cfg.ipap_features = P["wd"], ipap
+    c51 = P.get("algo", 0) == 1
+    if c51:
+        cfg.algo, cfg.reward_scale = 1, 1.0
     T = C.c_void_p()
     assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
     if "fused" in P:
@@ -122,7 +127,7 @@ def run_update(flashnav, torch, name, P, strict=True):
         scale[ipap:] = [0.125, 1 / np.pi, 2.0, 4 / np.pi]
         assert lib.nav_trainer_set_input_scale(T, scale.ctypes.data_as(C.c_void_p)) == 0
     sa = [od] + [H] * NH + [4]
-    sc = [od + 2] + [H] * NH + [2]
+    sc = [od + 2] + [H] * NH + [cfg.n_atoms if c51 else 2]
     n_a = sum(a * b + b for a, b in zip(sa[:-1], sa[1:]))
     n_c = sum(a * b + b for a, b in zip(sc[:-1], sc[1:]))
     actor0 = _unpack(_io(lib, T, 0, n_a), sa)
@@ -179,11 +184,19 @@ def run_update(flashnav, torch, name, P, strict=True):
     a_next, logp_next, _ = M.actor_head(out_n, eps_next)
     xnc = np.concatenate([nb, _bf16(a_next)], axis=1)
     tq = [M.mlp_forward(qt0[i], xnc)[0] for i in range(2)]
-    y, ym = M.critic_targets(rb, tb, tq[0], tq[1], logp_next, alpha, zn, cfg.gamma,
-                             cfg.reward_scale)
-    print(f"[{name}] targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
-    check("y", _rel(y_gpu, y), 2e-2)
-    check("y_mean", _rel(ym_gpu, ym), 2e-2)
+    if c51:
+        m_ref = M.c51_targets(rb, tb, tq[0], tq[1], logp_next, alpha, cfg.gamma,
+                              cfg.reward_scale, cfg.v_min, cfg.v_max)
+        m_gpu = _io(lib, T, 32, B * cfg.n_atoms).reshape(B, cfg.n_atoms).astype(np.float64)
+        print(f"[{name}] target distribution rel err {_rel(m_gpu, m_ref):.2e}")
+        check("target_dist", _rel(m_gpu, m_ref), 2e-2)
+        assert np.abs(m_gpu.sum(axis=1) - 1).max() < 1e-4
+    else:
+        y, ym = M.critic_targets(rb, tb, tq[0], tq[1], logp_next, alpha, zn, cfg.gamma,
+                                 cfg.reward_scale)
+        print(f"[{name}] targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
+        check("y", _rel(y_gpu, y), 2e-2)
+        check("y_mean", _rel(ym_gpu, ym), 2e-2)
     # critic gradients: against the same arithmetic with the GPU's BF16
     # rounding points (tight: checks the kernels), and against pure FP64
     # (the precision cost of BF16 operands, which grows with depth)
@@ -191,9 +204,14 @@ def run_update(flashnav, torch, name, P, strict=True):
     fp64_bound = 6e-2 if NH <= 2 else 3e-1
     for i in range(2):
         q, cache = M.mlp_forward(q0[i], xc)
-        _, dq = M.critic_loss(q, y, ym, sbar, cfg.huber_delta)
+        if c51:
+            _, dq = M.c51_critic_loss(q, m_ref)
+            # the BF16-emulated reference takes the GPU's own target distribution
+            emul = _emul_grads(M, q0[i], xc, M.c51_critic_loss(q, m_gpu)[1])
+        else:
+            _, dq = M.critic_loss(q, y, ym, sbar, cfg.huber_delta)
+            emul = _emul_grads(M, q0[i], xc, dq)
         grads, _ = M.mlp_backward(q0[i], cache, dq)
-        emul = _emul_grads(M, q0[i], xc, dq)
         g_gpu = _unpack(_io(lib, T, 11 + i, n_c), sc)
         for li, ((dW, db), (mW, mb), (gW, gb)) in enumerate(zip(grads, emul, g_gpu)):
             eW, eb = _rel(gW, dW), _rel(gb, db)
@@ -223,10 +241,15 @@ def run_update(flashnav, torch, name, P, strict=True):
         o, c = M.mlp_forward(q_post[i], xa)
         qa.append(o)
         caches.append(c)
-    _, dlogp, dq1, dq2 = M.actor_loss_grads(logp, qa[0][:, 0], qa[1][:, 0], alpha)
+    if c51:
+        _, dlogp, dl1, dl2 = M.c51_actor_grads(logp, qa[0], qa[1], alpha, cfg.v_min, cfg.v_max)
+        douts = (dl1, dl2)
+    else:
+        _, dlogp, dq1, dq2 = M.actor_loss_grads(logp, qa[0][:, 0], qa[1][:, 0], alpha)
+        douts = (np.stack([dq1, 0 * dq1], axis=1), np.stack([dq2, 0 * dq2], axis=1))
     da = np.zeros((B, 2))
-    for i, dqi in enumerate((dq1, dq2)):
-        _, dX = M.mlp_backward(q_post[i], caches[i], np.stack([dqi, 0 * dqi], axis=1))
+    for i, dqi in enumerate(douts):
+        _, dX = M.mlp_backward(q_post[i], caches[i], dqi)
         da += dX[:, od:od + 2]
     dout = M.actor_head_grad(out_a, eps_new, da, dlogp)
     grads_a, dxa = M.mlp_backward(actor0, cache_a, dout)
