@@ -402,113 +402,127 @@ __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc
 }
 
 // ------------------------------------------------------- FastSAC (C51) ---
-// One thread per sample; atoms z_i = v_min + i dz.
-__device__ __forceinline__ void c51_softmax_mean(const float *l, int n, float v_min, float dz,
-                                                 float &mx, float &sum, float &mean) {
-    mx = l[0];
-    for (int i = 1; i < n; ++i) mx = fmaxf(mx, l[i]);
-    sum = 0.0f;
-    float zs = 0.0f;
-    for (int i = 0; i < n; ++i) {
+// One warp per sample (8 per 256-thread block); lane i holds atoms i, i + 32,
+// ...; atoms z_i = v_min + i dz.
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// softmax statistics of one logit row: max, sum of exp, expected atom value
+__device__ __forceinline__ void c51_stats(const float *l, int n, float v_min, float dz, int lane,
+                                          float &mx, float &sum, float &mean) {
+    float m = -INFINITY;
+    for (int i = lane; i < n; i += 32) m = fmaxf(m, l[i]);
+    mx = warp_max(m);
+    float s = 0.0f, zs = 0.0f;
+    for (int i = lane; i < n; i += 32) {
         const float e = expf(l[i] - mx);
-        sum += e;
+        s += e;
         zs += e * (v_min + (float)i * dz);
     }
-    mean = zs / sum;
+    sum = warp_sum(s);
+    mean = warp_sum(zs) / sum;
 }
 
 // Target distribution m [B][n]: the target critic with the smaller expected
 // value, atoms moved to rs r + gamma (1 - term) (z - alpha logpi') and
-// clipped, projected back by linear interpolation.
-__global__ void k_c51_targets(const float *__restrict__ rew, const float *__restrict__ term,
-                              const float *__restrict__ tl1, const float *__restrict__ tl2,
-                              const float *__restrict__ logp_next,
-                              const float *__restrict__ log_alpha, int B, int n, float gamma,
-                              float rs, float v_min, float v_max, float *m) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+// clipped, projected back by linear interpolation (shared-memory bins).
+__global__ void __launch_bounds__(256) k_c51_targets(
+    const float *__restrict__ rew, const float *__restrict__ term, const float *__restrict__ tl1,
+    const float *__restrict__ tl2, const float *__restrict__ logp_next,
+    const float *__restrict__ log_alpha, int B, int n, float gamma, float rs, float v_min,
+    float v_max, float *m) {
+    __shared__ float bins[8][kFusedMaxWidth];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + w;
+    if (b >= B) return; // whole warp
     const float dz = (v_max - v_min) / (float)(n - 1);
     const float *l1 = tl1 + (size_t)b * n, *l2 = tl2 + (size_t)b * n;
     float mx1, s1, q1, mx2, s2, q2;
-    c51_softmax_mean(l1, n, v_min, dz, mx1, s1, q1);
-    c51_softmax_mean(l2, n, v_min, dz, mx2, s2, q2);
+    c51_stats(l1, n, v_min, dz, lane, mx1, s1, q1);
+    c51_stats(l2, n, v_min, dz, lane, mx2, s2, q2);
     const bool p1 = q1 <= q2;
     const float *l = p1 ? l1 : l2;
     const float mx = p1 ? mx1 : mx2, inv = 1.0f / (p1 ? s1 : s2);
     const float cont = gamma * (1.0f - term[b]);
     const float shift = rs * rew[b] - cont * expf(*log_alpha) * logp_next[b];
-    float *mr = m + (size_t)b * n;
-    for (int i = 0; i < n; ++i) mr[i] = 0.0f;
-    for (int j = 0; j < n; ++j) {
+    for (int i = lane; i < n; i += 32) bins[w][i] = 0.0f;
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
         const float pj = expf(l[j] - mx) * inv;
         const float tz = fminf(fmaxf(shift + cont * (v_min + (float)j * dz), v_min), v_max);
         const float bj = (tz - v_min) / dz;
         const int lo = (int)floorf(bj), hi = (int)ceilf(bj);
         if (lo == hi) {
-            mr[lo] += pj;
+            atomicAdd(&bins[w][lo], pj);
         } else {
-            mr[lo] += pj * ((float)hi - bj);
-            mr[hi] += pj * (bj - (float)lo);
+            atomicAdd(&bins[w][lo], pj * ((float)hi - bj));
+            atomicAdd(&bins[w][hi], pj * (bj - (float)lo));
         }
     }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) m[(size_t)b * n + i] = bins[w][i];
 }
 
 // Cross-entropy to m: dL/dlogits = (softmax - m) / B; acc[1] += loss
-__global__ void k_c51_critic_grad(const float *__restrict__ q, const float *__restrict__ m, int B,
-                                  int n, float *dq, float *acc) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_c51_critic_grad(const float *__restrict__ q,
+                                                         const float *__restrict__ m, int B, int n,
+                                                         float *dq, float *acc) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + w;
+    if (b >= B) return;
+    const float *l = q + (size_t)b * n, *mr = m + (size_t)b * n;
+    float mv = -INFINITY;
+    for (int i = lane; i < n; i += 32) mv = fmaxf(mv, l[i]);
+    const float mx = warp_max(mv);
+    float s = 0.0f;
+    for (int i = lane; i < n; i += 32) s += expf(l[i] - mx);
+    const float sum = warp_sum(s);
+    const float lse = mx + logf(sum), inv = 1.0f / sum, ib = 1.0f / (float)B;
     float ll = 0.0f;
-    if (b < B) {
-        const float *l = q + (size_t)b * n, *mr = m + (size_t)b * n;
-        float mx = l[0];
-        for (int i = 1; i < n; ++i) mx = fmaxf(mx, l[i]);
-        float sum = 0.0f;
-        for (int i = 0; i < n; ++i) sum += expf(l[i] - mx);
-        const float lse = mx + logf(sum), inv = 1.0f / sum, ib = 1.0f / (float)B;
-        for (int i = 0; i < n; ++i) {
-            ll -= mr[i] * (l[i] - lse);
-            dq[(size_t)b * n + i] = (expf(l[i] - mx) * inv - mr[i]) * ib;
-        }
+    for (int i = lane; i < n; i += 32) {
+        ll -= mr[i] * (l[i] - lse);
+        dq[(size_t)b * n + i] = (expf(l[i] - mx) * inv - mr[i]) * ib;
     }
-    for (int o = 16; o > 0; o >>= 1) ll += __shfl_xor_sync(0xffffffffu, ll, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[1], ll);
+    ll = warp_sum(ll);
+    if (lane == 0) atomicAdd(&acc[1], ll);
 }
 
 // Actor loss mean(alpha logp - min_j E[Q_j]): dL/dlogp, and dL/dlogits of the
 // smaller critic, -p_i (z_i - E[Q]) / B (zero for the other)
-__global__ void k_c51_actor_loss(const float *__restrict__ logp, const float *__restrict__ l1,
-                                 const float *__restrict__ l2, const float *__restrict__ log_alpha,
-                                 int B, int n, float v_min, float v_max, float *dlogp, float *dq1,
-                                 float *dq2, float *acc) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    float ll = 0.0f, lp = 0.0f;
-    if (b < B) {
-        const float dz = (v_max - v_min) / (float)(n - 1), ib = 1.0f / (float)B;
-        const float *a = l1 + (size_t)b * n, *c = l2 + (size_t)b * n;
-        float mx1, s1, q1, mx2, s2, q2;
-        c51_softmax_mean(a, n, v_min, dz, mx1, s1, q1);
-        c51_softmax_mean(c, n, v_min, dz, mx2, s2, q2);
-        const bool p1 = q1 <= q2;
-        const float alpha = expf(*log_alpha);
+__global__ void __launch_bounds__(256) k_c51_actor_loss(
+    const float *__restrict__ logp, const float *__restrict__ l1, const float *__restrict__ l2,
+    const float *__restrict__ log_alpha, int B, int n, float v_min, float v_max, float *dlogp,
+    float *dq1, float *dq2, float *acc) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + w;
+    if (b >= B) return;
+    const float dz = (v_max - v_min) / (float)(n - 1), ib = 1.0f / (float)B;
+    const float *a = l1 + (size_t)b * n, *c = l2 + (size_t)b * n;
+    float mx1, s1, q1, mx2, s2, q2;
+    c51_stats(a, n, v_min, dz, lane, mx1, s1, q1);
+    c51_stats(c, n, v_min, dz, lane, mx2, s2, q2);
+    const bool p1 = q1 <= q2;
+    const float alpha = expf(*log_alpha);
+    const float *l = p1 ? a : c;
+    const float mx = p1 ? mx1 : mx2, inv = 1.0f / (p1 ? s1 : s2), qm = p1 ? q1 : q2;
+    float *dsel = (p1 ? dq1 : dq2) + (size_t)b * n, *doth = (p1 ? dq2 : dq1) + (size_t)b * n;
+    for (int i = lane; i < n; i += 32) {
+        const float pi = expf(l[i] - mx) * inv;
+        dsel[i] = -pi * ((v_min + (float)i * dz) - qm) * ib;
+        doth[i] = 0.0f;
+    }
+    if (lane == 0) {
         dlogp[b] = alpha * ib;
-        const float *l = p1 ? a : c;
-        const float mx = p1 ? mx1 : mx2, inv = 1.0f / (p1 ? s1 : s2), qm = p1 ? q1 : q2;
-        float *dsel = (p1 ? dq1 : dq2) + (size_t)b * n, *doth = (p1 ? dq2 : dq1) + (size_t)b * n;
-        for (int i = 0; i < n; ++i) {
-            const float pi = expf(l[i] - mx) * inv;
-            dsel[i] = -pi * ((v_min + (float)i * dz) - qm) * ib;
-            doth[i] = 0.0f;
-        }
-        ll = alpha * logp[b] - qm;
-        lp = logp[b];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        ll += __shfl_xor_sync(0xffffffffu, ll, o);
-        lp += __shfl_xor_sync(0xffffffffu, lp, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0], ll);
-        atomicAdd(&acc[1], lp);
+        atomicAdd(&acc[0], alpha * logp[b] - qm);
+        atomicAdd(&acc[1], logp[b]);
     }
 }
 
@@ -1030,7 +1044,7 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
     const bool c51 = c.algo == 1;
     if (c51)
-        k_c51_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1],
+        k_c51_targets<<<blocks(B, 8), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1],
                                                  T->logp_next, T->scal + 0, B, T->qout, c.gamma,
                                                  c.reward_scale, c.v_min, c.v_max, T->tdist);
     else
@@ -1041,7 +1055,7 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
     for (int i = 0; i < 2; ++i) {
         if (c51)
-            k_c51_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->tdist, B, T->qout, T->dq[i],
+            k_c51_critic_grad<<<blocks(B, 8), 256, 0, st>>>(T->qo[i], T->tdist, B, T->qout, T->dq[i],
                                                          T->scal + 4);
         else
             k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
@@ -1063,7 +1077,7 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
         k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
         if (c51)
-            k_c51_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1],
+            k_c51_actor_loss<<<blocks(B, 8), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1],
                                                         T->scal + 0, B, T->qout, c.v_min, c.v_max,
                                                         T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
         else
