@@ -299,6 +299,63 @@ def paper_sensing(steps: int = 200):
     return out
 
 
+def learner_update(n_updates: int = 200, graphs: bool = True):
+    """Learner update time (Sec. 2.3) on a filled replay, replayed from a
+    captured CUDA graph: the paper's (100) x 4 networks at batch 1024 on the
+    fused passes and on the per-layer GEMM path (FastDSAC), FastSAC's C51
+    critics on the fused passes, and the benchmark learner (364-256-256,
+    batch 4096, per-layer path)."""
+    import ctypes as C
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    lib = flashnav.load()
+    P = lambda t: C.c_void_p(t.data_ptr())
+    cases = {
+        "paper_fastdsac_fused": dict(od=34, hidden=100, nh=4, batch=1024, ipap=30, fused=1),
+        "paper_fastdsac_per_layer": dict(od=34, hidden=100, nh=4, batch=1024, ipap=30, fused=0),
+        "paper_fastsac_fused": dict(od=34, hidden=100, nh=4, batch=1024, ipap=30, fused=1,
+                                    algo=1, pf=1),
+        "bench_fastdsac_per_layer": dict(od=364, hidden=256, nh=2, batch=4096, ipap=0, fused=0),
+    }
+    out = {}
+    s = torch.cuda.Stream()
+    S = C.c_void_p(s.cuda_stream)
+    for name, c in cases.items():
+        cfg = flashnav.nav_train_cfg()
+        lib.nav_train_default_cfg(C.byref(cfg))
+        cfg.obs_dim, cfg.hidden, cfg.n_hidden, cfg.batch = c["od"], c["hidden"], c["nh"], c["batch"]
+        cfg.replay_capacity, cfg.ipap_features, cfg.algo = 1 << 20, c["ipap"], c.get("algo", 0)
+        cfg.policy_freq = c.get("pf", 2)
+        T = C.c_void_p()
+        assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+        if c["fused"] == 0:
+            assert lib.nav_trainer_set_fused(T, 0) == 0
+        N = 65536
+        g = torch.Generator(device="cuda")
+        g.manual_seed(SEED)
+        obs = torch.rand(N, c["od"], device="cuda", generator=g) * 5
+        act = torch.rand(N, 2, device="cuda", generator=g) * 2 - 1
+        rew = torch.randn(N, device="cuda", generator=g)
+        done = torch.zeros(N, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(s):
+            assert lib.nav_train_insert(T, P(obs), P(act), P(rew), P(done), P(obs), None, N, S) == 0
+            assert lib.nav_trainer_set_graphs(T, 1 if graphs else 0) == 0
+            assert lib.nav_train_update(T, 40, S) == 0  # capture (or warm-up)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(n_updates // 40):
+                assert lib.nav_train_update(T, 40, S) == 0
+            e1.record(s)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / (n_updates // 40 * 40)
+        out[name] = {"ms_per_update": ms, "updates_per_s": 1e3 / ms, "batch": c["batch"]}
+        lib.nav_trainer_free(T)
+    out["config"] = ("one critic update (+ actor update every 2nd for FastDSAC, every update for "
+                     "FastSAC), " + ("graph-replayed" if graphs else "eager launches") +
+                     " in groups of 40, random replay of 65536")
+    return out
+
+
 def training_run(seconds: float):
     """FastDSAC from scratch for a bounded wall-clock budget: time at which the
     deterministic policy first reaches each success threshold on 1000 held-out
@@ -541,6 +598,7 @@ def run_gpu(args):
             line["policy_rollout"] = policy_rollout()
             line["uneven_batch"] = uneven_batch()
             line["paper_sensing"] = paper_sensing()
+            line["learner_update"] = learner_update()
             if args.train_seconds > 0:
                 line["training_paper_turtlebot2"] = training_paper(min(args.train_seconds, 25.0))
             if args.train_seconds > 0:
@@ -562,8 +620,11 @@ def main():
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "paper_sensing", "training",
-                             "training_paper", "training_paper_go2", "training_paper_fastsac"],
+                             "training_paper", "training_paper_go2", "training_paper_fastsac",
+                             "learner_update"],
                     help="run one of the extra measurements alone")
+    ap.add_argument("--eager", action="store_true",
+                    help="learner_update: eager launches instead of graph replays (profiling)")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
                          "(default: autotune)")
@@ -575,6 +636,7 @@ def main():
     elif args.only:
         fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
               "paper_sensing": paper_sensing,
+              "learner_update": lambda: learner_update(graphs=not args.eager),
               "training": lambda: training_run(args.train_seconds),
               "training_paper": lambda: training_paper(args.train_seconds),
               "training_paper_go2": lambda: training_paper(args.train_seconds, "go2"),
