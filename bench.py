@@ -224,7 +224,7 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
                       "8 moving discs, graph of 20 steps, L2 flushed between replays"}
 
 
-def paper_sensing(steps: int = 200):
+def paper_sensing(steps: int = 200, launch: str = ""):
     """The paper's sensing (Sec. 2.2.2, Eq. 6, Table 7) on its TurtleBot2
     setting: one shared 10 x 10 m map, 1080 beams over 270 deg to 20 m,
     30 sector minima.  The 0.03 m fixed-step march against the exact
@@ -245,7 +245,10 @@ def paper_sensing(steps: int = 200):
             E = w2.n_envs
             with torch.cuda.stream(s):
                 obs = sim.reset(SEED)
-                sim.autotune(steps=5)
+                if launch:
+                    sim.set_launch(*[int(v) for v in launch.split(",")])
+                else:
+                    sim.autotune(steps=5)
                 obs = sim.reset(SEED, obs)
                 acts = torch.empty(steps, E, 2, device="cuda")
                 for t in range(steps):
@@ -635,7 +638,7 @@ def main():
         run_reference(args)
     elif args.only:
         fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
-              "paper_sensing": paper_sensing,
+              "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "training": lambda: training_run(args.train_seconds),
               "training_paper": lambda: training_paper(args.train_seconds),
