@@ -137,11 +137,18 @@ int nav_reset(nav_handle *h, uint64_t seed, float *obs_dev);
 int nav_step(nav_handle *h, const float *actions_dev, float *obs_dev, float *reward_dev,
              uint8_t *done_dev, float *final_obs_dev);
 
-/* nav_step with host buffers: copies the actions in, steps, copies obs,
- * reward, done (and final obs when non-NULL) back, and waits for the stream.
- * Device staging buffers are allocated on the first call and kept. */
+/* nav_step with host buffers, synchronous; results identical to nav_step.
+ * Device staging buffers are allocated on the first call and kept.  The step
+ * runs as nav_set_host_pipeline's number of launches over consecutive env
+ * ranges (2 by default), each range's results copied out on a second stream
+ * while the next range computes; host buffers should be pinned for the
+ * copies to overlap. */
 int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host,
                   float *reward_host, uint8_t *done_host, float *final_obs_host);
+
+/* Number of env ranges nav_step_host pipelines (1..64; 1 = one launch, then
+ * the copies).  Synchronises the handle's stream. */
+int nav_set_host_pipeline(nav_handle *h, int parts);
 
 /* nav_step_host without any device allocation (the paper has no counterpart;
  * this is for callers that may not allocate device memory after start-up,

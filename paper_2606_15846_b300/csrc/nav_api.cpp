@@ -171,6 +171,15 @@ struct nav_handle {
     // nav_step_host staging
     float *h_act = nullptr, *h_obs = nullptr, *h_rew = nullptr, *h_fin = nullptr;
     unsigned char *h_done = nullptr;
+    // nav_step_host pipeline: the step runs as host_parts launches over env
+    // ranges, each part's results copied out while the next part computes
+    int host_parts = 2;
+    TileDev *d_ptiles = nullptr; // tiles of every part, part p at part_tile_off[p]
+    int *d_pperm = nullptr;      // envs ordered by (part, map, beam table)
+    int ptiles_cap = 0;
+    std::vector<int> part_tile_off, part_env_off;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> part_ev;
 };
 
 namespace {
@@ -235,6 +244,64 @@ int build_tiles(nav_handle *h) {
     h->a.tiles = h->d_tiles;
     h->a.perm = h->d_perm;
     h->a.n_tiles = (int)tiles.size();
+    // tiles of the host-step pipeline: the same grouping within each env range
+    {
+        const int P = std::max(1, std::min(h->host_parts, E));
+        // smaller tiles keep each part's launch as wide as the whole step's
+        const int pt = std::max(1, (h->cfg.tile_envs + P - 1) / P);
+        std::vector<int> pperm;
+        std::vector<TileDev> ptiles;
+        h->part_tile_off.assign(1, 0);
+        h->part_env_off.assign(1, 0);
+        for (int p = 0; p < P; ++p) {
+            const int e0 = (int)((long long)E * p / P), e1 = (int)((long long)E * (p + 1) / P);
+            const int base = (int)pperm.size();
+            for (int e = e0; e < e1; ++e) pperm.push_back(e);
+            std::stable_sort(pperm.begin() + base, pperm.end(), [&](int a, int b) {
+                const long long ka = (long long)h->env_map[a] * 4096 + h->env_tab[a];
+                const long long kb = (long long)h->env_map[b] * 4096 + h->env_tab[b];
+                return ka < kb;
+            });
+            const size_t t0 = ptiles.size();
+            int q = base;
+            while (q < (int)pperm.size()) {
+                int r = q;
+                while (r < (int)pperm.size() && h->env_map[pperm[r]] == h->env_map[pperm[q]] &&
+                       h->env_tab[pperm[r]] == h->env_tab[pperm[q]])
+                    ++r;
+                for (int b = q; b < r; b += pt) {
+                    TileDev td;
+                    td.map = h->env_map[pperm[q]];
+                    td.tab = h->env_tab[pperm[q]];
+                    td.env_begin = b;
+                    td.env_count = std::min(pt, r - b);
+                    ptiles.push_back(td);
+                }
+                q = r;
+            }
+            std::stable_sort(ptiles.begin() + t0, ptiles.end(), [&](const TileDev &x, const TileDev &y) {
+                const long long wx = (long long)h->maps[x.map].n_words * h->env_k[pperm[x.env_begin]];
+                const long long wy = (long long)h->maps[y.map].n_words * h->env_k[pperm[y.env_begin]];
+                return wx > wy;
+            });
+            h->part_tile_off.push_back((int)ptiles.size());
+            h->part_env_off.push_back(e1);
+        }
+        if ((int)ptiles.size() > h->ptiles_cap) {
+            e = h->arena.alloc(&h->d_ptiles, ptiles.size());
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(part tiles)");
+            h->ptiles_cap = (int)ptiles.size();
+        }
+        if (!h->d_pperm) {
+            e = h->arena.alloc(&h->d_pperm, (size_t)E);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(part perm)");
+        }
+        e = cudaMemcpy(h->d_ptiles, ptiles.data(), ptiles.size() * sizeof(TileDev),
+                       cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_pperm, pperm.data(), (size_t)E * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(part tiles)");
+    }
     // 32-ray chunks of every tile for the split step
     std::vector<int2> chunks;
     for (size_t t = 0; t < tiles.size(); ++t) {
@@ -665,6 +732,7 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, flo
     if (!h || !actions_host || !obs_host || !reward_host || !done_host)
         return fail(h, NAV_E_INVAL, "nav_step_host: null argument");
     const size_t E = (size_t)h->n_envs, O = (size_t)h->obs_off.back();
+
     cudaError_t e = cudaSuccess;
     if (!h->h_act) {
         e = h->arena.alloc(&h->h_act, 2 * E);
@@ -677,6 +745,56 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, flo
     e = cudaMemcpyAsync(h->h_act, actions_host, 2 * E * sizeof(float), cudaMemcpyHostToDevice,
                         h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(actions)");
+    const int P = (int)h->part_tile_off.size() - 1;
+    if (P > 1 && !(h->cfg.split && h->split_ok)) {
+        // pipeline: part p's results leave the device while part p + 1 computes
+        if (!h->copy_stream) {
+            e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate(copy)");
+        }
+        while ((int)h->part_ev.size() < P) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate(part)");
+            h->part_ev.push_back(ev);
+        }
+        StepArgs &A = h->a;
+        A.seed = h->seed;
+        A.mode = 0;
+        A.actions = h->h_act;
+        A.obs = h->h_obs;
+        A.reward = h->h_rew;
+        A.done = h->h_done;
+        A.final_obs = final_obs_host ? h->h_fin : nullptr;
+        for (int p = 0; p < P; ++p) {
+            StepArgs Ap = A;
+            Ap.tiles = h->d_ptiles + h->part_tile_off[p];
+            Ap.n_tiles = h->part_tile_off[p + 1] - h->part_tile_off[p];
+            Ap.perm = h->d_pperm;
+            const int lrc = launch_step(Ap, h->cfg, h->stream);
+            if (lrc != 0) return cuda_fail(h, (cudaError_t)lrc, "step kernel launch (part)");
+            e = cudaEventRecord(h->part_ev[p], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->part_ev[p], 0);
+            const int e0 = h->part_env_off[p], e1 = h->part_env_off[p + 1];
+            const size_t o0 = (size_t)h->obs_off[e0], o1 = (size_t)h->obs_off[e1];
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(obs_host + o0, h->h_obs + o0, (o1 - o0) * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(reward_host + e0, h->h_rew + e0, (size_t)(e1 - e0) * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(done_host + e0, h->h_done + e0, (size_t)(e1 - e0),
+                                    cudaMemcpyDeviceToHost, h->copy_stream);
+            if (e == cudaSuccess && final_obs_host)
+                e = cudaMemcpyAsync(final_obs_host + o0, h->h_fin + o0, (o1 - o0) * sizeof(float),
+                                    cudaMemcpyDeviceToHost, h->copy_stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "nav_step_host (part)");
+        }
+        e = cudaStreamSynchronize(h->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize(copy)");
+        return NAV_OK;
+    }
     int rc = nav_step(h, h->h_act, h->h_obs, h->h_rew, h->h_done, final_obs_host ? h->h_fin : nullptr);
     if (rc != NAV_OK) return rc;
     e = cudaMemcpyAsync(obs_host, h->h_obs, O * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
@@ -692,6 +810,14 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, flo
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     return NAV_OK;
+}
+
+int nav_set_host_pipeline(nav_handle *h, int parts) {
+    if (!h || parts < 1 || parts > 64) return NAV_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    h->host_parts = parts;
+    return build_tiles(h);
 }
 
 int nav_sync(nav_handle *h, int timeout_ms) {
@@ -1088,6 +1214,11 @@ void nav_free(nav_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    for (cudaEvent_t ev : h->part_ev) cudaEventDestroy(ev);
     delete h;
 }
 

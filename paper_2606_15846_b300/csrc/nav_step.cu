@@ -14,6 +14,10 @@
 // results (hit cells, flags, resets) are a fixed function of the inputs.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -1132,6 +1136,55 @@ template <bool DYN, bool MARCH> const void *pick_kernel(int max_regs) {
 
 } // namespace
 
+// (kernel, device, shared bytes, block) -> (SMs, resident CTAs per SM): the
+// attribute call and the occupancy query cost microseconds of host time, which
+// matters when a step is split into several launches
+struct OccKey {
+    const void *fn;
+    int dev;
+    size_t smem;
+    int block;
+};
+struct OccVal {
+    int n_sm, per_sm;
+};
+
+int occupancy(const void *fn, size_t smem, int block, int &n_sm, int &per_sm) {
+    static std::mutex mu;
+    static std::vector<std::pair<OccKey, OccVal>> cache;
+    // the dynamic shared-memory limit only ever rises, so that a cached
+    // launch never meets a limit lowered by another shape's launch
+    static std::vector<std::pair<std::pair<const void *, int>, size_t>> limit;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return (int)err;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &kv : cache)
+        if (kv.first.fn == fn && kv.first.dev == dev && kv.first.smem == smem &&
+            kv.first.block == block) {
+            n_sm = kv.second.n_sm;
+            per_sm = kv.second.per_sm;
+            return 0;
+        }
+    size_t *lim = nullptr;
+    for (auto &kv : limit)
+        if (kv.first.first == fn && kv.first.second == dev) lim = &kv.second;
+    if (!lim) {
+        limit.push_back({{fn, dev}, 0});
+        lim = &limit.back().second;
+    }
+    if (smem > *lim) {
+        err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return (int)err;
+        *lim = smem;
+    }
+    err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
+    if (err != cudaSuccess) return (int)err;
+    cache.push_back({OccKey{fn, dev, smem, block}, OccVal{n_sm, per_sm}});
+    return 0;
+}
+
 int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     if (a.n_tiles <= 0) return 0;
     const bool dyn = a.p.n_dyn > 0;
@@ -1143,13 +1196,8 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
                                   : pick_kernel<true, false>(cfg.max_regs))
                          : (march ? pick_kernel<false, true>(cfg.max_regs)
                                   : pick_kernel<false, false>(cfg.max_regs));
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return (int)err;
-    int dev = 0, n_sm = 0, per_sm = 0;
-    err = cudaGetDevice(&dev);
-    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (err == cudaSuccess)
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cfg.block_threads, smem);
+    int n_sm = 0, per_sm = 0;
+    cudaError_t err = (cudaError_t)occupancy(fn, smem, cfg.block_threads, n_sm, per_sm);
     if (err != cudaSuccess) return (int)err;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     const int grid = std::min(a.n_tiles, n_sm * per_sm);

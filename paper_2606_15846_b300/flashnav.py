@@ -23,7 +23,8 @@ EXPORTS = [
     "nav_default_params", "nav_create", "nav_create_ex", "nav_set_stream", "nav_obs_offsets",
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
-    "nav_get_stats", "nav_set_launch", "nav_get_launch", "nav_autotune", "nav_uniform_actions",
+    "nav_get_stats", "nav_set_host_pipeline", "nav_set_launch", "nav_get_launch",
+    "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
     "nav_policy_num_params", "nav_policy_get_weights",
@@ -96,6 +97,7 @@ def load():
         "nav_create_ex": (I, [P, I, P, P, P, I, F, P, I, P, P]),
         "nav_set_stream": (I, [P, P]),
         "nav_obs_offsets": (I, [P, P]),
+        "nav_set_host_pipeline": (I, [P, I]),
         "nav_num_envs": (I, [P]),
         "nav_obs_size": (C.c_int64, [P]),
         "nav_reset": (I, [P, U64, P]),
@@ -326,6 +328,9 @@ class NavSim:
         self._bind_stream()
         self._check(load().nav_set_launch(self._h, tile_envs, block_threads, smem_map_bytes,
                                           max_regs, byte_cells, split))
+
+    def set_host_pipeline(self, parts: int):
+        self._check(load().nav_set_host_pipeline(self._h, parts))
 
     def get_launch(self):
         v = [C.c_int() for _ in range(6)]

@@ -258,11 +258,15 @@ def test_lockstep_random_states(mods):
     _compare_state(sim, ref, "lockstep")
 
 
-def test_step_host_matches_device_step(mods):
+@pytest.mark.parametrize("parts,mixed", [(4, False), (1, False), (3, True), (7, True)])
+def test_step_host_matches_device_step(mods, parts, mixed):
+    """nav_step_host (pipelined over `parts` env ranges, results copied out
+    while the next range computes) returns exactly nav_step's results."""
     flashnav, oracle, torch = mods
-    wl = W.config_small(n_envs=64)
+    wl = _mixed(n_envs=75, n_dyn=4) if mixed else W.config_small(n_envs=64)
     a_sim = flashnav.NavSim.from_workload(wl)
     b_sim = flashnav.NavSim.from_workload(wl)
+    b_sim.set_host_pipeline(parts)
     a_sim.reset(5)
     b_sim.reset(5)
     acts = W.uniform_actions(5, 30, wl.n_envs)
@@ -283,6 +287,38 @@ def test_step_host_matches_device_step(mods):
         fa = fo.cpu().numpy()
         for e in ended:
             assert np.array_equal(fa[off[e]:off[e + 1]], hf[off[e]:off[e + 1]])
+
+
+@pytest.mark.parametrize("final", [False, True])
+def test_step_host_pinned_buffers_match_device_step(mods, final):
+    """Pinned host buffers (the copies overlap the second part's kernel):
+    results equal nav_step's."""
+    flashnav, oracle, torch = mods
+    wl = _mixed(n_envs=90)
+    a_sim = flashnav.NavSim.from_workload(wl)
+    b_sim = flashnav.NavSim.from_workload(wl)
+    a_sim.reset(8)
+    b_sim.reset(8)
+    acts = W.uniform_actions(8, 25, wl.n_envs)
+    n = a_sim.obs_size
+    h_act = torch.empty(wl.n_envs, 2, pin_memory=True)
+    h_obs = torch.full((n,), -7.0, pin_memory=True)
+    h_rew = torch.empty(wl.n_envs, pin_memory=True)
+    h_done = torch.empty(wl.n_envs, dtype=torch.uint8, pin_memory=True)
+    h_fin = torch.zeros(n, pin_memory=True) if final else None
+    for t in range(25):
+        o, r, d, fo = a_sim.step(torch.from_numpy(acts[t]).cuda(), want_final=True)
+        h_act.copy_(torch.from_numpy(acts[t]))
+        b_sim.step_host_ptrs(h_act.data_ptr(), h_obs.data_ptr(), h_rew.data_ptr(),
+                             h_done.data_ptr(), h_fin.data_ptr() if final else None)
+        assert torch.equal(o.cpu(), h_obs)
+        assert torch.equal(r.cpu(), h_rew)
+        assert torch.equal(d.cpu(), h_done)
+        if final:
+            off = a_sim.obs_offsets
+            fa = fo.cpu()
+            for e in np.flatnonzero(d.cpu().numpy() & 3):
+                assert torch.equal(fa[off[e]:off[e + 1]], h_fin[off[e]:off[e + 1]])
 
 
 def test_sync_reports_clean_status(mods):
