@@ -129,9 +129,22 @@ def cpu_baseline(wl, seconds: float = 15.0):
         el = time.perf_counter() - t0
         if (el > seconds and n >= 3) or n >= 512:
             break
+    # single-thread rate on the first 512 envs (same maps and actions)
+    one = oracle.OracleSim.from_workload(_sub_workload(wl, 512), threads=1)
+    one.reset(SEED)
+    m = 0
+    t1 = time.perf_counter()
+    while True:
+        one.step(acts[m % 64][:512])
+        m += 1
+        el1 = time.perf_counter() - t1
+        if (el1 > 3.0 and m >= 3) or m >= 256:
+            break
     return {"value": wl.n_envs * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": 512 * m / el1,
             "sample": f"{n} full steps of the {wl.n_envs}-env workload (C oracle, OpenMP over "
-                      f"envs, {cores} threads), {el:.1f} s"}
+                      f"envs, {cores} threads), {el:.1f} s; single thread: {m} steps of the "
+                      f"first 512 envs, {el1:.1f} s"}
 
 
 def policy_rollout(steps: int = 20):
@@ -386,7 +399,12 @@ def training_paper(seconds: float, robot: str = "turtlebot2", algo: str = "fastd
     1000 fresh episodes of that map."""
     from paper_2606_15846_b300 import train as TR
     cfg = TR.paper_config(robot, algo, time_budget_s=seconds, threshold=1.0)
-    res = TR.train(cfg, log=lambda *a: None)
+    res = TR.train(cfg, log=lambda *a: None, keep_policy=True)
+    # config 4's "equal eval success": the trained policy on both paths
+    s16, _ = TR.evaluate_policy(cfg, res["policy"], fp32=False)
+    s32, _ = TR.evaluate_policy(cfg, res["policy"], fp32=True)
+    import paper_2606_15846_b300.flashnav as FN
+    FN.load().nav_policy_free(res["policy"])
     hist = res["history"]
     reach = {}
     for thr in (0.90, 0.95, 1.00):
@@ -398,6 +416,7 @@ def training_paper(seconds: float, robot: str = "turtlebot2", algo: str = "fastd
     return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
             "budget_s": seconds, "env_steps": res["env_steps"],
             "cycle_ms_overlapped": res["cycle_ms"], "cycle_ms_serial": serial["cycle_ms"],
+            "final_policy_success_bf16_tensor_cores": s16, "final_policy_success_fp32": s32,
             "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
             "config": f"{robot} preset, {algo}: 1024 envs, one shared map, 1080 beams marched 0.03 m, "
                       "30 sectors, Eq. 2 inputs, (100)x4 nets on the fused passes, batch 1024, "
@@ -588,7 +607,13 @@ def run_gpu(args):
                          "unit": "Gvisit/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
                                         f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
-                         "kernel": "step kernel (fused) or ray_kernel (split), per launch.split"},
+                         "kernel": "step kernel (fused) or ray_kernel (split), per launch.split",
+                         # the instruction-issue bound that explains the gap:
+                         # 4 warp instructions/clk/SM over the ncu-measured
+                         # 0.949 warp instructions per visit of the step kernel
+                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.949 / 1e9,
+                         "frac_of_issue_bound": achieved / (SM_COUNT * 4 * sm_mhz * 1e6 /
+                                                           0.949 / 1e9)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": E * 2 * 4,
                     "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,

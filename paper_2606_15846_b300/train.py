@@ -161,6 +161,36 @@ def evaluate_reactive(cfg: TrainConfig, log=print):
     return succ.value / cfg.n_eval, ret.value / cfg.n_eval
 
 
+def evaluate_policy(cfg: TrainConfig, pol, fp32: bool = False):
+    """Success rate and mean return of a policy handle on the evaluation
+    episodes (deterministic actions), through the BF16 tensor-core path or
+    the plain FP32 path; same episodes and FP64 reduction as in training."""
+    import torch
+    lib = F.load()
+    _, eval_wl = make_workloads(cfg)
+    ev = F.NavSim.from_workload(eval_wl)
+    D = obs_features(cfg)
+    tc = F.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(tc))
+    tc.obs_dim, tc.batch, tc.replay_capacity = D + 4, 128, 256
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(tc), C.byref(T)) == 0
+    S = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    obs = ev.new_obs()
+    act = torch.empty(cfg.n_eval, 2, device="cuda")
+    ev.reset(777, obs)
+    assert lib.nav_eval_begin(T, cfg.n_eval, S) == 0
+    act_fn = lib.nav_policy_act_fp32 if fp32 else lib.nav_policy_act
+    for t in range(200):
+        assert act_fn(pol, _p(obs), D + 4, cfg.n_eval, 0, 0, t, _p(act), None, None, S) == 0
+        o, r, d = ev.step(act, obs)
+        assert lib.nav_eval_accumulate(T, _p(r), _p(d), cfg.n_eval, S) == 0
+    succ, ret = C.c_double(), C.c_double()
+    assert lib.nav_eval_result(T, cfg.n_eval, C.byref(succ), C.byref(ret), S) == 0
+    lib.nav_trainer_free(T)
+    return succ.value / cfg.n_eval, ret.value / cfg.n_eval
+
+
 def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
     """Runs FastDSAC until the threshold or the time budget.  With
     keep_policy the result also holds the trained nav_policy handle
