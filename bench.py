@@ -106,6 +106,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Max of a per-rank float over the process group (the job's wall time
+    is its slowest rank's); plain value on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, n_envs: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: the env-steps of every rank over the slowest
+    rank's time (weak scaling: each rank steps its own n_envs)."""
+    return world * n_envs * steps / seconds
+
+
 def make_workload(rank: int):
     from paper_2606_15846_b300 import workloads as W
     # each rank simulates its own 4096 envs on its own 16 maps (weak scaling)
@@ -534,11 +552,8 @@ def run_gpu(args):
     sim.sync(60000)
     dur_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     step_ms = float(np.sum(dur_ms))
-    if world > 1:
-        tt = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(tt.item())
-    value = world * E * args.steps / (step_ms / 1e3)
+    step_ms = max_over_ranks(step_ms, world, dev)
+    value = job_rate(world, E, args.steps, step_ms / 1e3)
 
     # work counted on an identical replay (same seed and actions): cell visits
     sim.reset(SEED + rank, obs)
@@ -569,11 +584,8 @@ def run_gpu(args):
         sim.step_host_ptrs(h_act[t].data_ptr(), h_obs.data_ptr(), h_rew.data_ptr(),
                            h_done.data_ptr())
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * E * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e_value = job_rate(world, E, e2e_steps, e2e_s)
 
     if rank == 0:
         peaks, src = _peaks()
