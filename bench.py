@@ -442,6 +442,38 @@ def training_paper(seconds: float, robot: str = "turtlebot2", algo: str = "fastd
                       "graph per two env steps, eval every 1 s on 1000 fresh episodes"}
 
 
+def table2(seconds: float, seeds: int):
+    """Table 2's protocol on the paper presets: for TurtleBot2 and Go2 with
+    FastDSAC and FastSAC, `seeds` training runs of `seconds` each; per
+    threshold (90 / 95 / 100 % success) the best and the mean time over the
+    seeds that reach it, and how many do (evaluation time included)."""
+    from paper_2606_15846_b300 import train as TR
+    out = {}
+    for robot in ("turtlebot2", "go2"):
+        for algo in ("fastdsac", "fastsac"):
+            times = {0.90: [], 0.95: [], 1.00: []}
+            best = []
+            for sd in range(seeds):
+                cfg = TR.paper_config(robot, algo, time_budget_s=seconds, threshold=1.0, seed=sd)
+                hist = TR.train(cfg, log=lambda *a: None)["history"]
+                best.append(max(h["success"] for h in hist))
+                for thr in times:
+                    hit = [h["t"] for h in hist if h["success"] >= thr]
+                    if hit:
+                        times[thr].append(hit[0])
+            row = {}
+            for thr, ts in times.items():
+                row[f"{int(thr * 100)}%"] = {
+                    "best_s": min(ts) if ts else None,
+                    "mean_s": sum(ts) / len(ts) if ts else None,
+                    "seeds_reached": len(ts)}
+            row["best_success_per_seed"] = best
+            out[f"{robot}_{algo}"] = row
+    out["config"] = (f"{seeds} seeds x {seconds:.0f} s per preset and learner; paper presets as in "
+                     "training_paper; mean over the seeds that reach each threshold")
+    return out
+
+
 def _sub_workload(wl, n):
     """The first n envs of a workload (same maps, beams and robots)."""
     import dataclasses
@@ -664,8 +696,9 @@ def main():
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "paper_sensing", "training",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
-                             "learner_update"],
+                             "learner_update", "table2"],
                     help="run one of the extra measurements alone")
+    ap.add_argument("--seeds", type=int, default=5, help="table2: training seeds per setting")
     ap.add_argument("--eager", action="store_true",
                     help="learner_update: eager launches instead of graph replays (profiling)")
     ap.add_argument("--launch", default="",
@@ -680,6 +713,7 @@ def main():
         fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
+              "table2": lambda: table2(args.train_seconds, args.seeds),
               "training": lambda: training_run(args.train_seconds),
               "training_paper": lambda: training_paper(args.train_seconds),
               "training_paper_go2": lambda: training_paper(args.train_seconds, "go2"),
