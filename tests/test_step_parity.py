@@ -471,3 +471,40 @@ def test_sector_count_must_divide_the_beams(mods):
     wl.params = W.Params(goal_dmin=1.0, goal_dmax=1e9, n_sectors=7)  # 180 % 7 != 0
     with pytest.raises(flashnav.NavError):
         flashnav.NavSim.from_workload(wl)
+
+
+# --------------------------------------------------------------------------
+# Limits and degenerate inputs
+# --------------------------------------------------------------------------
+def test_maximum_beams_on_a_large_map(mods):
+    """2048 beams (the per-env maximum) on one 2048 x 2048 map (102 m, the
+    global-memory path), r_max 20 m (400 cells)."""
+    occ = W.make_map(91, 2048, 2048, 0.02, corridors=True)
+    wl = W.Workload(name="max", maps=[occ], env_map=np.zeros(24, np.int32),
+                    env_beams=np.full(24, 2048, np.int32), env_robot=np.zeros(24, np.int32),
+                    robots=[W.DISC], max_range=20.0,
+                    params=W.Params(goal_dmin=1.0, goal_dmax=30.0))
+    run_parity(mods, wl, 6, seed=21, threads=16)
+
+
+def test_empty_map_every_ray_reaches_max_range(mods):
+    flashnav, oracle, torch = mods
+    occ = np.zeros((512, 512), np.uint8)
+    wl = W.Workload(name="empty", maps=[occ], env_map=np.zeros(16, np.int32),
+                    env_beams=np.full(16, 360, np.int32), env_robot=np.zeros(16, np.int32),
+                    robots=[W.DISC], max_range=4.0,
+                    params=W.Params(goal_dmin=1.0, goal_dmax=3.0))
+    sim = flashnav.NavSim.from_workload(wl)
+    sim.set_debug(True)
+    # every env at the map centre (12.8 m from any edge), heading 0
+    f = np.zeros((16, 8), np.float32)
+    f[:, 0] = f[:, 1] = 12.8
+    f[:, 5] = f[:, 6] = 14.0
+    f[:, 7] = float(np.hypot(1.2, 1.2))
+    sim.reset(1)
+    sim.set_state(1, f, np.zeros((16, 2), np.int32))
+    obs, _, done = sim.step(torch.full((16, 2), -1.0, device="cuda").contiguous())  # v = 0
+    r, h, _ = sim.debug()
+    assert (h == -2).all() and (r == np.float32(4.0)).all()
+    o = obs.cpu().numpy().reshape(16, 364)
+    assert (o[:, :360] == np.float32(4.0)).all() and (done.cpu().numpy() == 0).all()
