@@ -85,46 +85,6 @@ __device__ __forceinline__ void tmem_free(unsigned tmem, unsigned ncols) {
                      : "memory");
 }
 
-// Column sums of a 32-row x 16-column block held one row per lane: after
-// 16 shuffles lane l (even) holds the sum of column ((l >> 1) & 15) in the
-// butterfly order below; returns it (odd lanes return their pair's sum too).
-__device__ __forceinline__ float colsum16(const float *v, int lane) {
-    float a[8];
-    const bool up16 = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float send = up16 ? v[i] : v[i + 8];
-        const float keep = up16 ? v[i + 8] : v[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    const bool up8 = lane & 8;
-    float b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = up8 ? a[i] : a[i + 4];
-        const float keep = up8 ? a[i + 4] : a[i];
-        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const bool up4 = lane & 4;
-    float c[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = up4 ? b[i] : b[i + 2];
-        const float keep = up4 ? b[i + 2] : b[i];
-        c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    const bool up2 = lane & 2;
-    const float send = up2 ? c[0] : c[1];
-    const float keep = up2 ? c[1] : c[0];
-    float d = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    d += __shfl_xor_sync(0xffffffffu, d, 1);
-    return d;
-}
-// the column whose sum colsum16 leaves in lane l
-__device__ __forceinline__ int colsum16_col(int lane) {
-    return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
-}
-
 // 8 BF16 of a row as one 16-byte word
 __device__ __forceinline__ uint4 pack8(const float *v) {
     uint4 u;
@@ -432,11 +392,15 @@ __global__ void adam_fused(const OptGroup G, int n_cta, float lr, float b1, floa
     const OptNet &o = G.net[blockIdx.y];
     const long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (fi >= o.total) return;
-    float gi = 0.0f;
-    for (int c = 0; c < n_cta; ++c) gi += o.part[(long long)c * o.total + fi];
     long long i = fi;
     const int t = locate(o, i);
-    o.g[t][i] = gi;
+    float gi = 0.0f;
+    if (o.part) { // per-CTA partials of the fused backward: their sum
+        for (int c = 0; c < n_cta; ++c) gi += o.part[(long long)c * o.total + fi];
+        o.g[t][i] = gi;
+    } else {      // the per-layer path's gradient tensors
+        gi = o.g[t][i];
+    }
     const float c1 = corr[0], c2 = corr[1];
     const float mi = b1 * o.m[t][i] + (1.0f - b1) * gi;
     const float vi = b2 * o.v[t][i] + (1.0f - b2) * gi * gi;
@@ -531,7 +495,7 @@ int launch_adam_fused(Mlp *const *nets, float *const *part, int n_nets, int n_ct
     long long mx = 0;
     for (int k = 0; k < n_nets; ++k) {
         fill_opt(*nets[k], G.net[k]);
-        G.net[k].part = part[k];
+        G.net[k].part = part ? part[k] : nullptr;
         mx = mx > G.net[k].total ? mx : G.net[k].total;
     }
     adam_fused<<<dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,

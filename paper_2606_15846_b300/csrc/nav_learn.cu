@@ -358,36 +358,6 @@ __global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) 
 }
 
 // ----------------------------------------------------------- optimiser ---
-// Adam (bias-corrected) with decoupled weight decay wd (AdamW: p <- p (1 -
-// lr wd), then the Adam step; wd = 0 is plain Adam); weights also refresh
-// their BF16 copies W16 [out][ld_in] and WT16 [in][ld_out] (null for biases).
-__global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v, int n, float lr,
-                       float b1, float b2, const float *__restrict__ corr, float wd, int in,
-                       bf16 *W16, int ld_in, bf16 *WT16, int ld_out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float c1 = corr[0], c2 = corr[1];
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pd = wd != 0.0f ? p[i] * (1.0f - lr * wd) : p[i];
-    const float pi = pd - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
-    p[i] = pi;
-    if (W16) {
-        const int o = i / in, k = i - o * in;
-        const bf16 b16 = __float2bfloat16_rn(pi);
-        W16[(long long)o * ld_in + k] = b16;
-        WT16[(long long)k * ld_out + o] = b16;
-    }
-}
-
-__global__ void k_polyak(float *t, const float *__restrict__ s, int n, float tau) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) t[i] = (1.0f - tau) * t[i] + tau * s[i];
-}
-
 // log alpha <- Adam step on mean(-log alpha (logp + H_target)); acc[1] = sum logp
 __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc, int B,
                         float target_entropy, float lr, float b1, float b2,
@@ -722,31 +692,6 @@ int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 
     return rc;
 }
 
-int adam_net(nav_trainer *T, Mlp &net, float lr, const float *corr, cudaStream_t st) {
-    const float b1 = T->cfg.beta1, b2 = T->cfg.beta2;
-    for (int l = 0; l < net.n_layers; ++l) {
-        Layer &L = net.layer[l];
-        const int nw = L.in * L.out;
-        const float wd = T->cfg.weight_decay;
-        k_adam<<<blocks(nw), 256, 0, st>>>(L.W, L.gW, L.mW, L.vW, nw, lr, b1, b2, corr, wd,
-                                           L.in, static_cast<bf16 *>(L.W16), L.ld_in,
-                                           static_cast<bf16 *>(L.WT16), L.ld_out);
-        k_adam<<<blocks(L.out), 256, 0, st>>>(L.b, L.gb, L.mb, L.vb, L.out, lr, b1, b2, corr,
-                                              wd, 0, nullptr, 0, nullptr, 0);
-    }
-    return (int)cudaGetLastError();
-}
-
-int polyak_net(Mlp &tgt, const Mlp &src, float tau, cudaStream_t st) {
-    for (int l = 0; l < tgt.n_layers; ++l) {
-        const int nw = tgt.layer[l].in * tgt.layer[l].out;
-        k_polyak<<<blocks(nw), 256, 0, st>>>(tgt.layer[l].W, src.layer[l].W, nw, tau);
-        k_polyak<<<blocks(tgt.layer[l].out), 256, 0, st>>>(tgt.layer[l].b, src.layer[l].b,
-                                                           tgt.layer[l].out, tau);
-    }
-    return tgt.refresh(st);
-}
-
 int copy_net(Mlp &dst, const Mlp &src) {
     for (int l = 0; l < dst.n_layers; ++l) {
         const size_t nw = (size_t)dst.layer[l].in * dst.layer[l].out;
@@ -899,9 +844,9 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->znoise, B);
     TA(T->dlogp, B);
     TA(T->dout, B * 4);
-    TA(T->dH, B * H);
     TA(T->g16, B * 8);
     TA(T->gT16, 8 * B);
+    TA(T->dH, B * H);
     TA(T->dZ16, B * T->Hp);
     TA(T->dZT16, B * H);
     TA(T->scal, 16);
@@ -1145,9 +1090,12 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                                      c.huber_delta, T->dq[i], T->scal + 4);
         }
         k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 2; ++i)
             rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, st);
-            rc |= adam_net(T, T->q[i], c.lr_critic, T->corr, st);
+        {
+            Mlp *qs[2] = {&T->q[0], &T->q[1]};
+            rc |= launch_adam_fused(qs, nullptr, 2, 1, c.lr_critic, c.beta1, c.beta2, T->corr,
+                                    c.weight_decay, st);
         }
         ++n_critic;
         // ---- actor and temperature update every policy_freq critic updates
@@ -1171,7 +1119,11 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
             rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
                                T->ipap > 0 ? T->dXa : nullptr, T->ld, st);
-            rc |= adam_net(T, T->actor, c.lr_actor, T->corr + 2, st);
+            {
+                Mlp *act[1] = {&T->actor};
+                rc |= launch_adam_fused(act, nullptr, 1, 1, c.lr_actor, c.beta1, c.beta2,
+                                        T->corr + 2, c.weight_decay, st);
+            }
             if (T->ipap > 0) {
                 // Eq. 2's beta trained with the actor (same Adam settings)
                 k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
@@ -1182,7 +1134,10 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
             k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
                                      c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
         }
-        for (int i = 0; i < 2; ++i) rc |= polyak_net(T->qt[i], T->q[i], c.tau, st);
+        {
+            Mlp *qts[2] = {&T->qt[0], &T->qt[1]}, *qs[2] = {&T->q[0], &T->q[1]};
+            rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);
+        }
         rc |= (int)cudaGetLastError();
         if (rc) return rc;
     }

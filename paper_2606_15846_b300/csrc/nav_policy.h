@@ -110,7 +110,8 @@ int launch_mlp_bwd_fused(const FGroup &g, void *stream);
 
 // One Adam / AdamW step on every parameter of up to two networks, whose
 // gradients are the sums of n_cta partials (written back to gW / gb for
-// inspection); BF16 copies refreshed.  corr: device bias corrections.
+// inspection), or, with gWp_base null, the layers' gW / gb themselves; BF16
+// copies refreshed.  corr: device bias corrections.
 int launch_adam_fused(Mlp *const *nets, float *const *gWp_base, int n_nets, int n_cta, float lr,
                       float b1, float b2, const float *corr, float wd, void *stream);
 // Polyak averaging tgt <- (1 - tau) tgt + tau src of up to two networks, with

@@ -108,5 +108,45 @@ __device__ __forceinline__ unsigned swz(int r, int k, unsigned chunk_bytes) {
                       (k & 7) * 2);
 }
 
+// Column sums of a 32-row x 16-column block held one row per lane: after
+// 16 shuffles lane l (even) holds the sum of column ((l >> 1) & 15) in the
+// butterfly order below; returns it (odd lanes return their pair's sum too).
+__device__ __forceinline__ float colsum16(const float *v, int lane) {
+    float a[8];
+    const bool up16 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = up16 ? v[i] : v[i + 8];
+        const float keep = up16 ? v[i + 8] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    const bool up8 = lane & 8;
+    float b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = up8 ? a[i] : a[i + 4];
+        const float keep = up8 ? a[i + 4] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const bool up4 = lane & 4;
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = up4 ? b[i] : b[i + 2];
+        const float keep = up4 ? b[i + 2] : b[i];
+        c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool up2 = lane & 2;
+    const float send = up2 ? c[0] : c[1];
+    const float keep = up2 ? c[1] : c[0];
+    float d = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+// the column whose sum colsum16 leaves in lane l
+__device__ __forceinline__ int colsum16_col(int lane) {
+    return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+}
+
 } // namespace
 } // namespace flashnav
