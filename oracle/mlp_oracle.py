@@ -6,6 +6,13 @@ TEST INFRASTRUCTURE ONLY: used by tests/ and the CPU-baseline leg of the
 benchmark; it never imports the CUDA package.  Plain numpy in binary64; the
 matrix product is the only library primitive.
 
+Parity unpinned: the FastDSAC target and critic loss (critic_targets,
+critic_loss) and the clipped-double-Q choice of the C51 target (c51_targets)
+are readings of the paper's prose (Sec. 2.3 gives no equations for them);
+their gradients are pinned to the written losses by finite differences and
+the C51 projection to Bellemare et al.'s definition, but the losses
+themselves have no pin outside this file.
+
 Readings (the paper states FastDSAC only in prose):
 * Eq. 2 (IPAPRec): one trainable beta shared by the agent's networks, moved
   by the actor loss only (the critics see the transformed input with beta
