@@ -87,6 +87,9 @@ CONFIGS = {
                             fused=0),
     # FastSAC (Table 5): twin C51 critics, 101 atoms on [-20, 20]
     "fastsac": dict(od=34, hidden=100, n_hidden=4, wd=1e-3, ipap=30, scale=True, algo=1),
+    # config 5 at full batch: 4096 rows, 364-256-256 networks
+    "bench_full_batch": dict(od=OD, hidden=256, n_hidden=2, wd=0.0, ipap=0, scale=False,
+                             batch=4096),
 }
 
 
@@ -112,7 +115,7 @@ def run_update(flashnav, torch, name, P, strict=True):
     cfg = flashnav.nav_train_cfg()
     lib.nav_train_default_cfg(C.byref(cfg))
     cfg.obs_dim, cfg.hidden, cfg.n_hidden = od, H, NH
-    cfg.batch, cfg.replay_capacity, cfg.policy_freq, cfg.seed = 256, 2048, 1, 7
+    cfg.batch, cfg.replay_capacity, cfg.policy_freq, cfg.seed = P.get("batch", 256), 8192, 1, 7
     cfg.weight_decay, cfg.ipap_features = P["wd"], ipap
     c51 = P.get("algo", 0) == 1
     if c51:
@@ -135,7 +138,7 @@ def run_update(flashnav, torch, name, P, strict=True):
     qt0 = [_unpack(_io(lib, T, 3 + i, n_c), sc) for i in range(2)]
     scal0 = _io(lib, T, 24, 16)
     rng = np.random.default_rng(3)
-    N = 700
+    N = max(700, cfg.batch + 500)
     obs = rng.uniform(0, 6, (N, od)).astype(np.float32)
     nxt = np.clip(obs + rng.normal(0, 0.05, (N, od)), 0, 6).astype(np.float32)
     act = rng.uniform(-0.99, 0.99, (N, 2)).astype(np.float32)
@@ -145,7 +148,7 @@ def run_update(flashnav, torch, name, P, strict=True):
     assert lib.nav_train_insert(T, *[_p(d) for d in dev], None, N, None) == 0
     assert lib.nav_train_update(T, 1, None) == 0
     torch.cuda.synchronize()
-    B = 256
+    B = cfg.batch
     idx = _io(lib, T, 20, B, np.int32)
     eps_new = _io(lib, T, 21, 2 * B).reshape(B, 2).astype(np.float64)
     eps_next = _io(lib, T, 22, 2 * B).reshape(B, 2).astype(np.float64)

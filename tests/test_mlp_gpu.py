@@ -231,3 +231,31 @@ def test_paper_actor_with_ipap_against_fp64(env, fp32):
     print(f"paper actor ({'FP32 SIMT' if fp32 else 'BF16 tensor cores'}) rel L2 vs FP64: {rel:.2e}")
     assert rel < (1e-5 if fp32 else 3e-2)
     lib.nav_policy_free(h)
+
+
+def test_policy_forward_full_size_sampled_rows(env):
+    """Config 4's policy at full size: 65536 rows, 364-256-256-4, BF16 tensor
+    cores; 2000 sampled rows against FP64 (BF16 rounding points emulated)."""
+    from oracle import mlp_oracle as M
+    flashnav, torch = env
+    lib = flashnav.load()
+    obs_dim, n = 364, 65536
+    h, w = _policy(lib, obs_dim, n, seed=7)
+    params = _unpack(w, [obs_dim, 256, 256, 4])
+    rng = np.random.default_rng(4)
+    obs = np.concatenate([rng.uniform(0, 6, (n, 360)), rng.uniform(0, 8, (n, 1)),
+                          rng.uniform(-3, 3, (n, 1)), rng.uniform(0, 0.5, (n, 1)),
+                          rng.uniform(-1, 1, (n, 1))], axis=1).astype(np.float32)
+    obs_t = torch.from_numpy(obs).cuda()
+    act = torch.empty(n, 2, device="cuda")
+    out = torch.empty(n, 4, device="cuda")
+    assert lib.nav_policy_act(h, _p(obs_t), obs_dim, n, 0, 0, 0, _p(act), None, _p(out), None) == 0
+    torch.cuda.synchronize()
+    rows = rng.choice(n, 2000, replace=False)
+    got = out.double().cpu().numpy()[rows]
+    x = _bf16(obs[rows])
+    for li, (W_, b) in enumerate(params):
+        z = x @ _bf16(W_).T + b
+        x = _bf16(M.leaky(z)) if li < 2 else z
+    assert np.abs(got - x).max() <= 2e-3 * max(1.0, np.abs(x).max())
+    lib.nav_policy_free(h)

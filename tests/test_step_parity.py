@@ -508,3 +508,10 @@ def test_empty_map_every_ray_reaches_max_range(mods):
     assert (h == -2).all() and (r == np.float32(4.0)).all()
     o = obs.cpu().numpy().reshape(16, 364)
     assert (o[:, :360] == np.float32(4.0)).all() and (done.cpu().numpy() == 0).all()
+
+
+def test_rollout_workload_full_size(mods):
+    """Config 4's simulator at full size: 65536 envs over 16 maps of 256 x 256,
+    360 beams, autotuned launch; reset and two steps compared in full."""
+    wl = W.config_throughput(n_envs=65536)
+    run_parity(mods, wl, 2, seed=31, want_final=False, autotune=True, threads=16)
