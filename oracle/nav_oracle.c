@@ -198,7 +198,12 @@ static int or_blocked_dyn(const or_mapc *m, const or_dyn *d, int nd, float rdc, 
  * cell, Eq. 5, capped at r_max) and the hit id: j*W+i for an occupied cell,
  * -1 for leaving the map, -2 for reaching r_max.  *visits counts the cells
  * whose occupancy was looked up.
- * Ties tMaxX == tMaxY step X first (then Y on the next iteration). */
+ * Ties tMaxX == tMaxY step X first (then Y on the next iteration).
+ * The ray meets the axis-x cell boundaries at t = tMaxX0 + k * tDeltaX
+ * (k = 0, 1, ...; Eq. 4 solved for each boundary): after k steps in x the
+ * next boundary's parameter is that expression evaluated once, as one fused
+ * multiply-add (a single rounding), rather than tDeltaX added k times (k
+ * roundings).  Likewise for y. */
 static float or_cast(const or_mapc *m, const or_dyn *dyn, int nd, float rdc,
                      float xc, float yc, float dx, float dy, float max_range,
                      int32_t *hit, uint32_t *visits)
@@ -219,10 +224,17 @@ static float or_cast(const or_mapc *m, const or_dyn *dyn, int nd, float rdc,
     else if (dx < 0.0f) { sx = -1; tdx = 1.0f / -dx; tmx = (xc - floorf(xc)) * tdx; }
     if (dy > 0.0f) { sy = 1; tdy = 1.0f / dy; tmy = ((floorf(yc) + 1.0f) - yc) * tdy; }
     else if (dy < 0.0f) { sy = -1; tdy = 1.0f / -dy; tmy = (yc - floorf(yc)) * tdy; }
+    const float tmx0 = tmx, tmy0 = tmy;
+    int kx = 0, ky = 0; /* steps taken in x and in y */
     for (;;) {
         float t;
-        if (tmx <= tmy) { t = tmx; if (t > rmax_c) break; i += sx; tmx = tmx + tdx; }
-        else { t = tmy; if (t > rmax_c) break; j += sy; tmy = tmy + tdy; }
+        if (tmx <= tmy) {
+            t = tmx; if (t > rmax_c) break;
+            i += sx; kx += 1; tmx = fmaf((float)kx, tdx, tmx0);
+        } else {
+            t = tmy; if (t > rmax_c) break;
+            j += sy; ky += 1; tmy = fmaf((float)ky, tdy, tmy0);
+        }
         nv += 1;
         if (i < 0 || j < 0 || i >= m->w || j >= m->h) {
             *hit = -1; *visits = nv; return t * m->res;

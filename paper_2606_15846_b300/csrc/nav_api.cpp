@@ -193,6 +193,37 @@ int cuda_fail(nav_handle *h, cudaError_t e, const char *what) {
     return fail(h, NAV_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Chessboard distance of every cell of a padded map (rows of `stride`
+// bytes, map cell (i, j) at row j + kPad, column i + kPad) to the nearest
+// blocked cell, padding included, capped at 255: two raster passes with
+// the unit 3x3 mask (Rosenfeld & Pfaltz, 1966), exact for this metric.
+void chessboard_distance(const nav_map &mp, int stride, uint8_t *out) {
+    const int rows = mp.height + 2 * kPad, cols = mp.width + 2 * kPad;
+    for (int r = 0; r < rows; ++r)
+        for (int c = 0; c < stride; ++c) {
+            const int i = c - kPad, j = r - kPad;
+            const bool free = c < cols && i >= 0 && j >= 0 && i < mp.width && j < mp.height &&
+                              !mp.occ[(size_t)j * mp.width + i];
+            out[(size_t)r * stride + c] = free ? 255 : 0;
+        }
+    auto at = [&](int r, int c) -> uint8_t & { return out[(size_t)r * stride + c]; };
+    // free cells lie strictly inside the padding ring, so every neighbour exists
+    for (int r = kPad; r < rows - kPad; ++r)
+        for (int c = kPad; c < cols - kPad; ++c) {
+            if (!at(r, c)) continue;
+            int v = std::min({(int)at(r, c - 1), (int)at(r - 1, c - 1), (int)at(r - 1, c),
+                              (int)at(r - 1, c + 1)}) + 1;
+            at(r, c) = (uint8_t)std::min(v, (int)at(r, c));
+        }
+    for (int r = rows - kPad - 1; r >= kPad; --r)
+        for (int c = cols - kPad - 1; c >= kPad; --c) {
+            if (!at(r, c)) continue;
+            int v = std::min({(int)at(r, c + 1), (int)at(r + 1, c + 1), (int)at(r + 1, c),
+                              (int)at(r + 1, c - 1)}) + 1;
+            at(r, c) = (uint8_t)std::min(v, (int)at(r, c));
+        }
+}
+
 // Groups envs by (map, beam table) and cuts each group into tiles of at most
 // tile_envs envs; the tile list runs over the largest maps first so that the
 // longest CTAs start early.
@@ -327,7 +358,8 @@ int build_tiles(nav_handle *h) {
 int set_map_modes(nav_handle *h) {
     int region = 0;
     for (MapDev &m : h->maps) {
-        if (h->byte_cells == 1 && m.n_bytes <= h->smem_map_bytes) m.mode = kMapSharedBytes;
+        if (h->byte_cells == 1 && m.dist_off >= 0 && m.n_bytes <= h->smem_map_bytes)
+            m.mode = kMapSharedBytes;
         else if (m.n_words * 4 <= h->smem_map_bytes) m.mode = kMapSharedBits;
         else m.mode = kMapGlobal;
         const int need = m.mode == kMapSharedBytes ? m.n_bytes
@@ -440,8 +472,10 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
             !std::isfinite(rb.w_max))
             return bail(fail(h, NAV_E_INVAL, "bad nav_robot " + std::to_string(r)));
     }
-    // maps: validate and pack (free bits, one blocked padding cell per side)
+    // maps: validate and pack (free bits, one blocked padding cell per side;
+    // distance bytes for maps small enough to be staged as bytes)
     std::vector<uint32_t> words;
+    std::vector<uint8_t> dist_all;
     for (int m = 0; m < n_maps; ++m) {
         const nav_map &mp = maps[m];
         if (!mp.occ || mp.width <= 0 || mp.height <= 0 || mp.width > 16384 || mp.height > 16384 ||
@@ -478,6 +512,12 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
                     base[b >> 5] |= 1u << (b & 31);
                 }
         md.all_off = 0;
+        md.dist_off = -1;
+        if (md.n_bytes <= kMaxSmemMapBytes) {
+            md.dist_off = (long long)dist_all.size();
+            dist_all.resize(dist_all.size() + md.n_bytes, 0);
+            chessboard_distance(mp, bstride, dist_all.data() + md.dist_off);
+        }
         h->maps.push_back(md);
     }
     // envs
@@ -575,6 +615,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     std::vector<long long> obs_off_ll(h->obs_off.begin(), h->obs_off.end());
     std::vector<long long> ray_off_ll(h->ray_off.begin(), h->ray_off.end());
     uint32_t *bits;
+    uint8_t *d_dist = nullptr;
     MapDev *d_maps;
     CsDev *d_cs;
     RobotDev *d_rob;
@@ -588,6 +629,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
         if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "upload " #vec));     \
     } while (0)
     NAV_UP(bits, words);
+    if (!dist_all.empty()) NAV_UP(d_dist, dist_all);
     NAV_UP(d_maps, h->maps);
     h->d_maps = d_maps;
     NAV_UP(d_cs, cs_dev);
@@ -612,6 +654,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     NAV_UP(d_ray_off, ray_off_ll);
 #undef NAV_UP
     A.bits = bits;
+    A.dist = d_dist;
     A.maps = d_maps;
     A.cs = d_cs;
     A.robots = d_rob;
@@ -965,7 +1008,7 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
     if (!h) return NAV_E_INVAL;
     if (tile_envs < 0 || tile_envs > kMaxTileEnvs || block_threads < 0 || block_threads > 512 ||
         (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
-        smem_map_bytes < 0 || smem_map_bytes > 200 * 1024 ||
+        smem_map_bytes < 0 || smem_map_bytes > kMaxSmemMapBytes ||
         !(max_regs == 0 || max_regs == 32 || max_regs == 40 || max_regs == 64) ||
         byte_cells < 0 || byte_cells > 2 || split < 0 || split > 2)
         return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");

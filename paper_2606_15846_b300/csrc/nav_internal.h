@@ -11,12 +11,15 @@ constexpr int kMaxDyn = 8;      // moving discs per env
 constexpr int kMaxDynRows = 16; // rows spanned by one stamped disc
 constexpr int kMaxTileEnvs = 32;
 constexpr int kMaxBeams = 2048;
+constexpr int kMaxSmemMapBytes = 200 * 1024; // largest map staged in shared memory
 
 // Packed map: free bits (1 = free), kPad padding cells on every side that
 // read as blocked, rows of `pitch` 32-bit words (odd, to spread smem banks);
 // the padded bit index of cell (i, j) is (j + kPad) * pitch * 32 + (i + kPad).
-// The same padded map as one byte per cell (1 = free) has a row stride of
-// byte_stride bytes (a multiple of 4 whose word count is odd).
+// The same padded map as one byte per cell has a row stride of byte_stride
+// bytes (a multiple of 4 whose word count is odd); each byte is 0 for a
+// blocked cell, else the chessboard distance (in cells, capped at 255) to the
+// nearest blocked or padding cell.
 constexpr int kPad = 1;
 struct MapDev {
     int w, h, pitch, n_words; // n_words is a multiple of 4 (16-byte copies)
@@ -25,6 +28,7 @@ struct MapDev {
     int byte_stride, n_bytes; // byte view; n_bytes is a multiple of 16
     int mode;                 // staging, one of MapMode
     int all_off;              // word offset when every map is staged together (split step)
+    long long dist_off;       // byte offset of the distance bytes (multiple of 16), -1: none
 };
 enum MapMode { kMapGlobal = 0, kMapSharedBits = 1, kMapSharedBytes = 2 };
 
@@ -60,6 +64,7 @@ struct TileDev {
 
 struct StepArgs {
     const uint32_t *bits;
+    const uint8_t *dist; // distance bytes of the maps that have them, at dist_off
     const MapDev *maps;
     const int *spawn, *spawn_comp, *comp_start, *comp_count, *comp_cells;
     const CsDev *cs;

@@ -122,10 +122,14 @@ struct BitsGlobal {
     }
     __device__ __forceinline__ uint32_t word(int i) const { return __ldg(w + i); }
 };
+// One byte per cell: 0 = blocked, else the chessboard distance (cells,
+// capped at 255) to the nearest blocked or off-map cell.
 struct BytesShared {
+    static constexpr bool kDist = true;
     const uint8_t *c;
     int stride; // byte pitch
     __device__ __forceinline__ bool free_at(int b) const { return c[b] != 0; }
+    __device__ __forceinline__ int dist_at(int b) const { return c[b]; }
 };
 
 template <class V> __device__ __forceinline__ int cell_index(const V &v, int i, int j) {
@@ -261,11 +265,29 @@ __device__ void dyn_gate(const DynEnv &de, int nd, float xc, float yc, float dx,
 // Ray cast: Amanatides-Woo traversal over a padded map view (Eq. 4-5).
 // Starting cell (floor xc, floor yc); per step the axis whose next boundary
 // is nearer is stepped (a tie steps x first), the entry parameter t of the
-// new cell is checked against r_max, then the cell is looked up.  Leaving the
-// map stops the walk at a padding cell without a bounds test.  The walk ends
-// within 2 r_max/res + 3 steps: each step adds tDelta >= 1 to tMaxX or tMaxY.
+// new cell is checked against r_max, then the cell is looked up.  After k
+// steps on an axis its next boundary lies at t0 + k tDelta, evaluated as one
+// fused multiply-add.  Leaving the map stops the walk at a padding cell
+// without a bounds test.  The walk ends within 2 r_max/res + 3 steps: each
+// step raises tMaxX or tMaxY by tDelta >= 1.
+//
+// Views that carry a distance (one byte per cell: the chessboard distance
+// to the nearest blocked cell) also jump: from a cell at distance d the
+// next n = d - 1 columns (rows, for a ray closer to the y axis) of the ray
+// are free, so every event up to the n-th major-axis boundary is taken at
+// once.  The minor-axis count at that parameter is estimated, and the jump
+// is kept only if exact comparisons of the same fused multiply-adds confirm
+// the count and it stays within the free square (minor advance <= n);
+// otherwise the iteration takes one ordinary step.  Either way the state
+// afterwards is one the plain walk passes through: same cell, same boundary
+// parameters, same visit count.  Jump and step are one branch-free
+// iteration, so the lanes of a warp do not diverge between them.
 // Returns the range in metres; hit = j*W+i, -1 off-map, -2 r_max.
 // ---------------------------------------------------------------------------
+template <class V, class = void> struct has_dist { static constexpr bool value = false; };
+template <class V>
+struct has_dist<V, decltype((void)V::kDist)> { static constexpr bool value = V::kDist; };
+
 template <bool DYN, class V>
 __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float xc, float yc,
                                           float dx, float dy, float rmax_c, float max_range,
@@ -281,32 +303,91 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
         vis = 1;
         return 0.0f;
     }
+    // per axis: cell-index step, tDelta and the first boundary parameter t0
+    // (tDelta 0 and t0 = inf on an axis the ray does not move along)
     int sbx = 0, sby = 0;
-    float tdx = INFINITY, tdy = INFINITY, tmx = INFINITY, tmy = INFINITY;
-    if (dx > 0.0f) { sbx = 1; tdx = 1.0f / dx; tmx = ((fx + 1.0f) - xc) * tdx; }
-    else if (dx < 0.0f) { sbx = -1; tdx = 1.0f / -dx; tmx = (xc - fx) * tdx; }
-    if (dy > 0.0f) { sby = pb; tdy = 1.0f / dy; tmy = ((fy + 1.0f) - yc) * tdy; }
-    else if (dy < 0.0f) { sby = -pb; tdy = 1.0f / -dy; tmy = (yc - fy) * tdy; }
+    float tdx = 0.0f, tdy = 0.0f, tx0 = INFINITY, ty0 = INFINITY;
+    if (dx > 0.0f) { sbx = 1; tdx = 1.0f / dx; tx0 = ((fx + 1.0f) - xc) * tdx; }
+    else if (dx < 0.0f) { sbx = -1; tdx = 1.0f / -dx; tx0 = (xc - fx) * tdx; }
+    if (dy > 0.0f) { sby = pb; tdy = 1.0f / dy; ty0 = ((fy + 1.0f) - yc) * tdy; }
+    else if (dy < 0.0f) { sby = -pb; tdy = 1.0f / -dy; ty0 = (yc - fy) * tdy; }
     float glo = INFINITY, ghi = -INFINITY;
     if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
-    float t = 0.0f;
+    float t = 0.0f, kx, ky;
     bool stopped = false;
-    for (;;) {
-        const bool sx = tmx <= tmy;
-        t = sx ? tmx : tmy;
-        if (t > rmax_c) break;
-        b += sx ? sbx : sby;
-        if (sx) tmx = tmx + tdx;
-        else tmy = tmy + tdy;
-        if (!view.free_at(b)) { stopped = true; break; }
-        if (DYN && t >= glo && t <= ghi) {
-            const int r = b / pb;
-            if (dyn_cell(*de, nd, b - r * pb - kPad, r - kPad)) { stopped = true; break; }
+    if constexpr (has_dist<V>::value) {
+        // major axis M (the larger direction component), minor axis m
+        const bool xmaj = fabsf(dx) >= fabsf(dy);
+        const float tdM = xmaj ? tdx : tdy, tM0 = xmaj ? tx0 : ty0;
+        const float tdm = xmaj ? tdy : tdx, tm0 = xmaj ? ty0 : tx0;
+        const int sbM = xmaj ? sbx : sby, sbm = xmaj ? sby : sbx;
+        const float adM = xmaj ? fabsf(dx) : fabsf(dy), adm = xmaj ? fabsf(dy) : fabsf(dx);
+        // on a tie the x step comes first: the major axis wins ties iff it is x
+        const int tie = xmaj ? 1 : 0;
+        // minor boundaries at or before T: about T |d_m| + 1 - t0_m |d_m|
+        const float offm = adm > 0.0f ? 1.0f - tm0 * adm : 0.0f;
+        // about the number of major-axis events at or before r_max (a jump
+        // past r_max is refused by an exact test)
+        const float nM = floorf(__fmaf_rn(rmax_c, adM, 1.0f - tM0 * adM));
+        float kM = 0.0f, km = 0.0f, tM = tM0, tm = tm0;
+        int d = view.dist_at(b);
+        const int b0 = b;
+        for (;;) {
+            // the next event (tie: x first; parameters are >= 0, so their
+            // bit patterns order like the floats)
+            const bool sM = __float_as_int(tM) < __float_as_int(tm) + tie;
+            const float tn = sM ? tM : tm;
+            if (tn > rmax_c) break;
+            // jump candidate: every event up to the n-th next major event,
+            // n = d - 1 (capped at r_max); the minor count at that parameter
+            // is estimated and kept only if the comparisons confirm it
+            const float n = fminf((float)d - 1.0f, nM - kM);
+            const float kM2 = kM + n;
+            const float T = __fmaf_rn(kM2 - 1.0f, tdM, tM0);
+            const float km2 = fmaxf(km, floorf(__fmaf_rn(T, adm, offm)));
+            bool jump = n >= 1.0f && T <= rmax_c && km2 - km <= n &&
+                        __fmaf_rn(km2, tdm, tm0) > T &&
+                        (km2 == km || __fmaf_rn(km2 - 1.0f, tdm, tm0) <= T);
+            if (DYN) jump = jump && (T < glo || tn > ghi);
+            kM = jump ? kM2 : (sM ? kM + 1.0f : kM);
+            km = jump ? km2 : (sM ? km : km + 1.0f);
+            tM = __fmaf_rn(kM, tdM, tM0);
+            tm = __fmaf_rn(km, tdm, tm0);
+            b = b0 + (int)kM * sbM + (int)km * sbm;
+            t = tn;
+            d = view.dist_at(b);
+            if (d == 0) { stopped = true; break; } // only a single step reaches a blocked cell
+            if (DYN && !jump && t >= glo && t <= ghi) {
+                const float ax = xmaj ? kM : km, ay = xmaj ? km : kM;
+                const int ci = i0 + (sbx < 0 ? -(int)ax : (int)ax);
+                const int cj = j0 + (sby < 0 ? -(int)ay : (int)ay);
+                if (dyn_cell(*de, nd, ci, cj)) { stopped = true; break; }
+            }
+        }
+        kx = xmaj ? kM : km;
+        ky = xmaj ? km : kM;
+    } else {
+        float tmx = tx0, tmy = ty0;
+        kx = 0.0f;
+        ky = 0.0f;
+        for (;;) {
+            const bool sx = tmx <= tmy;
+            t = sx ? tmx : tmy;
+            if (t > rmax_c) break;
+            b += sx ? sbx : sby;
+            if (sx) { kx += 1.0f; tmx = __fmaf_rn(kx, tdx, tx0); }
+            else { ky += 1.0f; tmy = __fmaf_rn(ky, tdy, ty0); }
+            if (!view.free_at(b)) { stopped = true; break; }
+            if (DYN && t >= glo && t <= ghi) {
+                const int ci = i0 + (sbx < 0 ? -(int)kx : (int)kx);
+                const int cj = j0 + (sby < 0 ? -(int)ky : (int)ky);
+                if (dyn_cell(*de, nd, ci, cj)) { stopped = true; break; }
+            }
         }
     }
-    const int r = b / pb;
-    const int i = b - r * pb - kPad, j = r - kPad;
-    vis = 1u + (unsigned)(abs(i - i0) + abs(j - j0));
+    const int i = i0 + (sbx < 0 ? -(int)kx : (int)kx);
+    const int j = j0 + (sby < 0 ? -(int)ky : (int)ky);
+    vis = 1u + (unsigned)kx + (unsigned)ky;
     if (!stopped) { hit = -2; return max_range; }
     hit = (i < 0 || j < 0 || i >= M.w || j >= M.h) ? -1 : j * M.w + i;
     return t * M.res;
@@ -319,6 +400,11 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
 // sample lies beyond r_max returns r_max.  Every sample is one visit.  The
 // off-map test is explicit, so any step length is valid.  Same outputs as
 // cast_ray: range in metres, hit = j*W+i, -1 off-map, -2 r_max.
+// With a distance view, a sample in a cell at chessboard distance d is
+// followed by q samples that stay within d - 1 - 1/16 cells of it along
+// both axes (q step_c max(|dx|, |dy|) <= d - 1 - 1/16; the 1/16 cell covers
+// the rounding of the sample positions), hence in free cells, and the march
+// resumes after them; jumps stop at the first sample past r_max.
 // ---------------------------------------------------------------------------
 template <bool DYN, class V>
 __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float xc, float yc,
@@ -328,29 +414,62 @@ __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float
     if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
     int i = (int)floorf(xc), j = (int)floorf(yc);
     if (i >= M.w || j >= M.h) { hit = -1; vis = 1; return 0.0f; }
-    if (!view.free_at(cell_index(view, i, j)) || (DYN && dyn_cell(*de, nd, i, j))) {
+    int b0 = cell_index(view, i, j);
+    if (!view.free_at(b0) || (DYN && dyn_cell(*de, nd, i, j))) {
         hit = j * M.w + i;
         vis = 1;
         return 0.0f;
     }
     float glo = INFINITY, ghi = -INFINITY;
     if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
-    for (unsigned s = 1;; ++s) {
-        const float tc = (float)s * step_c;
-        if (tc > rmax_c) { hit = -2; vis = s; return max_range; }
-        const float px = xc + tc * dx, py = yc + tc * dy;
-        i = (int)floorf(px);
-        j = (int)floorf(py);
-        if ((unsigned)i >= (unsigned)M.w || (unsigned)j >= (unsigned)M.h) {
-            hit = -1;
-            vis = s + 1u;
-            return tc * M.res;
+    if constexpr (has_dist<V>::value) {
+        // s_end: the first sample past r_max
+        float s_end = fmaxf(1.0f, floorf(rmax_c / step_c));
+        while (s_end > 1.0f && (s_end - 1.0f) * step_c > rmax_c) s_end -= 1.0f;
+        while (s_end * step_c <= rmax_c) s_end += 1.0f;
+        const float per = 1.0f / (step_c * fmaxf(fabsf(dx), fabsf(dy)));
+        float s = 0.0f;
+        int d = view.dist_at(b0);
+        for (;;) {
+            float q = floorf(((float)d - 1.0625f) * per);
+            q = fmaxf(q, 0.0f);
+            if (DYN && q > 0.0f && !((s + q) * step_c < glo || (s + 1.0f) * step_c > ghi)) q = 0.0f;
+            s = fminf(s + q + 1.0f, s_end);
+            const float tc = s * step_c;
+            if (tc > rmax_c) { hit = -2; vis = (unsigned)s; return max_range; }
+            const float px = xc + tc * dx, py = yc + tc * dy;
+            i = (int)floorf(px);
+            j = (int)floorf(py);
+            if ((unsigned)i >= (unsigned)M.w || (unsigned)j >= (unsigned)M.h) {
+                hit = -1;
+                vis = (unsigned)s + 1u;
+                return tc * M.res;
+            }
+            d = view.dist_at(cell_index(view, i, j));
+            if (d == 0 || (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
+                hit = j * M.w + i;
+                vis = (unsigned)s + 1u;
+                return tc * M.res;
+            }
         }
-        if (!view.free_at(cell_index(view, i, j)) ||
-            (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
-            hit = j * M.w + i;
-            vis = s + 1u;
-            return tc * M.res;
+    } else {
+        for (unsigned s = 1;; ++s) {
+            const float tc = (float)s * step_c;
+            if (tc > rmax_c) { hit = -2; vis = s; return max_range; }
+            const float px = xc + tc * dx, py = yc + tc * dy;
+            i = (int)floorf(px);
+            j = (int)floorf(py);
+            if ((unsigned)i >= (unsigned)M.w || (unsigned)j >= (unsigned)M.h) {
+                hit = -1;
+                vis = s + 1u;
+                return tc * M.res;
+            }
+            if (!view.free_at(cell_index(view, i, j)) ||
+                (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
+                hit = j * M.w + i;
+                vis = s + 1u;
+                return tc * M.res;
+            }
         }
     }
 }
@@ -702,12 +821,12 @@ __device__ __forceinline__ void init_copy_barrier(unsigned long long *bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Issued by one thread: one arrive that expects n_words*4 bytes, then the
-// bulk copies (global -> shared, completion counted on the mbarrier).
-__device__ __forceinline__ void stage_bitmap(uint32_t *dst, const uint32_t *src, int n_words,
-                                             unsigned long long *bar) {
+// Issued by one thread: one arrive that expects `bytes` bytes (a multiple of
+// 16, both addresses 16-byte aligned), then the bulk copies (global ->
+// shared, completion counted on the mbarrier).
+__device__ __forceinline__ void stage_map(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
     const unsigned b = smem_u32(bar);
-    const unsigned bytes = (unsigned)n_words * 4u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
                  : "memory");
@@ -739,25 +858,6 @@ __device__ __forceinline__ bool wait_bitmap(unsigned long long *bar, unsigned pa
     return false;
 }
 
-// Expands a map's packed free bits (global) into one byte per cell in shared
-// memory; every thread of the CTA takes part.
-__device__ void expand_bytes(uint8_t *dst, const uint32_t *__restrict__ src, const MapDev &M) {
-    const int q4 = M.byte_stride >> 2; // 4-cell groups per row
-    const int rows = M.h + 2 * kPad;
-    const int pb = M.pitch * 32;
-    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
-    for (int q = threadIdx.x; q < rows * q4; q += blockDim.x) {
-        const int r = q / q4;
-        const int c = (q - r * q4) * 4;
-        uint32_t out = 0;
-        if (c < pb) { // four bits of one word: bit offsets are multiples of 4
-            const int bi = r * pb + c;
-            const uint32_t nib = (__ldg(src + (bi >> 5)) >> (bi & 31)) & 0xFu;
-            out = (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
-        }
-        d32[q] = out;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Ray phase
@@ -886,9 +986,11 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         const int K = A.tab_k[T.tab];
         const uint32_t *gbits = A.bits + M.word_off;
         const bool fresh = staged_map != T.map;
-        const bool copy = M.mode == kMapSharedBits && fresh;
-        if (copy && tid == 0) stage_bitmap(sbits, gbits, M.n_words, &bar);
-        if (M.mode == kMapSharedBytes && fresh) expand_bytes(sbytes, gbits, M);
+        const bool copy = (M.mode == kMapSharedBits || M.mode == kMapSharedBytes) && fresh;
+        if (copy && tid == 0) {
+            if (M.mode == kMapSharedBits) stage_map(sbits, gbits, (unsigned)M.n_words * 4u, &bar);
+            else stage_map(sbytes, A.dist + M.dist_off, (unsigned)M.n_bytes, &bar);
+        }
         if (T.tab != beam_tab) {
             const int toff = A.tab_off[T.tab];
             for (int k = tid; k < K; k += blockDim.x)

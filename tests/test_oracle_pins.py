@@ -93,6 +93,29 @@ def test_axis_wall_range_is_analytic(oracle, direction):
     assert vis == int(abs(want)) + 2
 
 
+def test_oblique_far_wall_range_is_analytic(oracle):
+    """Eq. 4-5: a ray at an oblique angle crosses ~2000 column boundaries
+    and ~1000 row boundaries before a wall at column 2000; its range is the
+    analytic (c - xc) / dx within 3 ulp.  Each boundary parameter is one
+    rounding of t0 + k tDelta; adding tDelta once per step instead drifts by
+    hundreds of ulp over this ray."""
+    n, c = 2048, 2000
+    occ = np.zeros((n, n), np.uint8)
+    occ[:, c] = 1
+    inv = np.float32(1 / RES)
+    for trial in range(20):
+        rng = np.random.default_rng(trial)
+        x0 = np.float32(rng.uniform(5, 15) * RES)
+        y0 = np.float32(rng.uniform(300, 400) * RES)
+        a = rng.uniform(0.2, 0.6)
+        dx, dy = np.float32(math.cos(a)), np.float32(math.sin(a))
+        r, hit, _ = oracle.cast_ray(occ, RES, float(x0), float(y0), float(dx), float(dy), 120.0)
+        xc = float(np.float32(x0 * inv))
+        want = (c - xc) / float(dx) * RES
+        assert abs(float(r) - want) <= 3 * ulp32(want), (trial, float(r), want)
+        assert hit % n == c
+
+
 def test_empty_map_returns_max_range(oracle):
     n = 256
     occ = np.zeros((n, n), np.uint8)

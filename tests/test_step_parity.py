@@ -487,6 +487,22 @@ def test_maximum_beams_on_a_large_map(mods):
     run_parity(mods, wl, 6, seed=21, threads=16)
 
 
+@pytest.mark.parametrize("sensor", [0, 1])
+def test_distance_jumps_on_a_sparse_map(mods, sensor):
+    """Long free stretches (2 % occupancy, 20 m = 400-cell range on a
+    20 x 20 m map) staged as distance bytes: most of each ray is covered by
+    jumps; hit cells, visit counts and ranges must equal the oracle's
+    cell-by-cell walk (exact traversal) or sample-by-sample march."""
+    occ = W.make_map(93, 400, 400, 0.02)
+    wl = W.Workload(name="sparse", maps=[occ], env_map=np.zeros(64, np.int32),
+                    env_beams=np.full(64, 360, np.int32), env_robot=np.zeros(64, np.int32),
+                    robots=[W.DISC], max_range=20.0,
+                    params=W.Params(goal_dmin=1.0, goal_dmax=12.0, sensor=sensor,
+                                    march_step=0.03))
+    sim, _, _ = run_parity(mods, wl, 30, seed=23, launch=(8, 256, 200 * 1024, 64, 1, 2))
+    assert sim.get_launch()[4] == 1
+
+
 def test_empty_map_every_ray_reaches_max_range(mods):
     flashnav, oracle, torch = mods
     occ = np.zeros((512, 512), np.uint8)
