@@ -651,16 +651,16 @@ def run_gpu(args):
                          "unit": "Gvisit/s", "frac": achieved / peak,
                          # DRAM bytes per launch of this kernel from the ncu
                          # capture in profiles/step_kernel_plain4096.md
-                         "traffic": 543.7e3 if launch == (16, 512, 163840, 40, 1, 2) else None,
+                         "traffic": 1.4697e6 if launch == (8, 512, 163840, 40, 1, 2) else None,
                          "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
                                         f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
                          "kernel": "step kernel (fused) or ray_kernel (split), per launch.split",
                          # the instruction-issue bound that explains the gap:
                          # 4 warp instructions/clk/SM over the ncu-measured
-                         # 0.784 warp instructions per visit of the step kernel
-                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.784 / 1e9,
+                         # 0.716 warp instructions per visit of the step kernel
+                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.716 / 1e9,
                          "frac_of_issue_bound": achieved / (SM_COUNT * 4 * sm_mhz * 1e6 /
-                                                           0.784 / 1e9)},
+                                                           0.716 / 1e9)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": E * 2 * 4,
                     "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,
