@@ -204,9 +204,15 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
  *                  map that does not fit is read as packed bits through L1/L2
  *   max_regs       register cap per thread: 32, 40 or 64 (more resident CTAs
  *                  against fewer registers)
- *   byte_cells     1: stage maps that fit as one byte per cell (expanded from
- *                  the packed bits; cheaper lookups), 2: stage packed bits
- *                  (bulk TMA copy)
+ *   byte_cells     map representation: 1 distance bytes (one byte per cell,
+ *                  0 blocked, else the chessboard distance to the nearest
+ *                  blocked cell; ray casts jump through free space), staged
+ *                  in shared memory when they fit, else read through L1/L2;
+ *                  2 packed bits, staged when they fit (bulk TMA copy), else
+ *                  read through L1/L2; 3 distance bytes when they fit in
+ *                  shared memory, else packed bits when they fit, else
+ *                  distance bytes through L1/L2.  Maps above 64 MiB as bytes
+ *                  always use packed bits
  *   split          1: when every map and beam table fits in one CTA's shared
  *                  memory (<= 200 KiB) and there are no moving discs, run the
  *                  step as an env-phase kernel then a ray kernel whose CTAs

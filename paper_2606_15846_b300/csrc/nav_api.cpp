@@ -351,17 +351,23 @@ int build_tiles(nav_handle *h) {
     return NAV_OK;
 }
 
-// Chooses each map's staging: one byte per cell in shared memory when byte
-// maps are enabled and it fits under the cap, else packed bits in shared
-// memory when they fit, else packed bits read through L1/L2.  The shared
-// region is sized for the largest staged map.
+// Chooses each map's staging under the shared-memory cap.  byte_cells 1:
+// distance bytes, in shared memory when they fit, else through L1/L2;
+// 2: packed bits, in shared memory when they fit, else through L1/L2;
+// 3: distance bytes in shared memory when they fit, else packed bits in
+// shared memory when they fit, else distance bytes through L1/L2.  Maps
+// without distance bytes use packed bits.  The shared region is sized for
+// the largest staged map.
 int set_map_modes(nav_handle *h) {
     int region = 0;
     for (MapDev &m : h->maps) {
-        if (h->byte_cells == 1 && m.dist_off >= 0 && m.n_bytes <= h->smem_map_bytes)
-            m.mode = kMapSharedBytes;
-        else if (m.n_words * 4 <= h->smem_map_bytes) m.mode = kMapSharedBits;
-        else m.mode = kMapGlobal;
+        const bool dist = m.dist_off >= 0 && h->byte_cells != 2;
+        const bool bytes_fit = m.n_bytes <= h->smem_map_bytes;
+        const bool bits_fit = m.n_words * 4 <= h->smem_map_bytes;
+        if (dist && bytes_fit) m.mode = kMapSharedBytes;
+        else if (dist && h->byte_cells == 1) m.mode = kMapGlobalBytes;
+        else if (bits_fit) m.mode = kMapSharedBits;
+        else m.mode = dist ? kMapGlobalBytes : kMapGlobal;
         const int need = m.mode == kMapSharedBytes ? m.n_bytes
                          : m.mode == kMapSharedBits ? m.n_words * 4 : 0;
         region = std::max(region, need);
@@ -513,7 +519,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
                 }
         md.all_off = 0;
         md.dist_off = -1;
-        if (md.n_bytes <= kMaxSmemMapBytes) {
+        if (nb <= kMaxDistBytes) {
             md.dist_off = (long long)dist_all.size();
             dist_all.resize(dist_all.size() + md.n_bytes, 0);
             chessboard_distance(mp, bstride, dist_all.data() + md.dist_off);
@@ -1010,7 +1016,7 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
         (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
         smem_map_bytes < 0 || smem_map_bytes > kMaxSmemMapBytes ||
         !(max_regs == 0 || max_regs == 32 || max_regs == 40 || max_regs == 64) ||
-        byte_cells < 0 || byte_cells > 2 || split < 0 || split > 2)
+        byte_cells < 0 || byte_cells > 3 || split < 0 || split > 2)
         return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
@@ -1166,7 +1172,7 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
         h->cfg = best_cfg;
         rc = build_tiles(h);
         const int caps[] = {24 * 1024, 80 * 1024, 160 * 1024};
-        for (int bc = 1; bc <= 2 && rc == NAV_OK; ++bc)
+        for (int bc = 1; bc <= 3 && rc == NAV_OK; ++bc)
             for (int cap : caps) {
                 h->byte_cells = bc;
                 h->smem_map_bytes = cap;

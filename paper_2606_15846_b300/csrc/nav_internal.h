@@ -12,6 +12,7 @@ constexpr int kMaxDynRows = 16; // rows spanned by one stamped disc
 constexpr int kMaxTileEnvs = 32;
 constexpr int kMaxBeams = 2048;
 constexpr int kMaxSmemMapBytes = 200 * 1024; // largest map staged in shared memory
+constexpr long long kMaxDistBytes = 64ll << 20; // largest map given distance bytes
 
 // Packed map: free bits (1 = free), kPad padding cells on every side that
 // read as blocked, rows of `pitch` 32-bit words (odd, to spread smem banks);
@@ -30,7 +31,9 @@ struct MapDev {
     int all_off;              // word offset when every map is staged together (split step)
     long long dist_off;       // byte offset of the distance bytes (multiple of 16), -1: none
 };
-enum MapMode { kMapGlobal = 0, kMapSharedBits = 1, kMapSharedBytes = 2 };
+// Where a tile reads its map: packed bits through L1/L2, packed bits or
+// distance bytes staged in shared memory, or distance bytes through L1/L2.
+enum MapMode { kMapGlobal = 0, kMapSharedBits = 1, kMapSharedBytes = 2, kMapGlobalBytes = 3 };
 
 // C-space of one (map, robot) pair: spawnable cells ascending, the component
 // of each, and every component's cells grouped and ascending.

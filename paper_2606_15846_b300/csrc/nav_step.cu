@@ -132,6 +132,15 @@ struct BytesShared {
     __device__ __forceinline__ int dist_at(int b) const { return c[b]; }
 };
 
+// Distance bytes read through L1/L2 (maps too large to stage).
+struct BytesGlobal {
+    static constexpr bool kDist = true;
+    const uint8_t *__restrict__ c;
+    int stride; // byte pitch
+    __device__ __forceinline__ bool free_at(int b) const { return __ldg(c + b) != 0; }
+    __device__ __forceinline__ int dist_at(int b) const { return __ldg(c + b); }
+};
+
 template <class V> __device__ __forceinline__ int cell_index(const V &v, int i, int j) {
     return (j + kPad) * v.stride + (i + kPad);
 }
@@ -155,6 +164,14 @@ __device__ __forceinline__ bool span_blocked<BytesShared>(const BytesShared &v, 
     const int c0 = cell_index(v, i0, j);
     for (int k = 0; k <= i1 - i0; ++k)
         if (!v.c[c0 + k]) return true;
+    return false;
+}
+template <>
+__device__ __forceinline__ bool span_blocked<BytesGlobal>(const BytesGlobal &v, int j, int i0,
+                                                          int i1) {
+    const int c0 = cell_index(v, i0, j);
+    for (int k = 0; k <= i1 - i0; ++k)
+        if (!v.free_at(c0 + k)) return true;
     return false;
 }
 
@@ -1017,13 +1034,16 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
             if (!ok) wait_bitmap(&bar, parity ^ 1u);
         }
         const int mode = failed ? (int)kMapGlobal : M.mode;
-        if (tid == 0) staged_map = mode == kMapGlobal ? -1 : T.map;
+        if (tid == 0) staged_map = mode == kMapGlobal || mode == kMapGlobalBytes ? -1 : T.map;
         if (mode == kMapSharedBytes)
             run_tile<DYN, MARCH>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         else if (mode == kMapSharedBits)
             run_tile<DYN, MARCH>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
+        else if (mode == kMapGlobalBytes)
+            run_tile<DYN, MARCH>(A, BytesGlobal{A.dist + M.dist_off, M.byte_stride}, M, T, K, sbeam,
+                                 slots, fin_slot, &n_fin, sdyn, &next_chunk);
         else
             run_tile<DYN, MARCH>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);

@@ -157,14 +157,18 @@ def test_visit_counter_matches_oracle(mods):
     assert rays >= 6 * wl.n_envs * 360
 
 
-# (tile_envs, block_threads, smem_map_bytes, max_regs, byte_cells): smem cap
-# 16 bytes forces the L1/L2 path, byte_cells 2 the packed-bit shared path
+# (tile_envs, block_threads, smem_map_bytes, max_regs, byte_cells): a smem
+# cap of 16 bytes forces the L1/L2 paths (distance bytes with byte_cells 1
+# or 3, packed bits with 2); byte_cells 2 with room stages packed bits; a
+# 4 KiB cap with byte_cells 3 stages the 64 x 64 map's bits (its bytes do
+# not fit)
 @pytest.mark.parametrize("launch", [(1, 64, 0, 32, 1), (3, 96, 0, 64, 2), (32, 512, 0, 40, 1),
                                     (8, 256, 16, 40, 1), (5, 128, 16, 32, 2),
-                                    (2, 224, 0, 64, 2)])
+                                    (2, 224, 0, 64, 2), (6, 192, 16, 40, 3),
+                                    (4, 256, 4096, 40, 3)])
 def test_launch_shapes_and_ragged_tiles(mods, launch):
     """Ragged env count, a beam count that is not a multiple of 32, tiles of
-    1..32 envs, 64..512 threads, register caps, and all three map stagings."""
+    1..32 envs, 64..512 threads, register caps, and all four map stagings."""
     wl = W.config_small(n_envs=37)
     wl.env_beams[:] = 37
     run_parity(mods, wl, 60, seed=7, launch=launch)
@@ -199,8 +203,9 @@ def test_moving_discs_packed_bits(mods):
     run_parity(mods, _mixed(n_dyn=8), 40, seed=14, launch=(4, 256, 0, 40, 2))
 
 
-def test_moving_discs_l2_path(mods):
-    run_parity(mods, _mixed(n_dyn=3), 40, seed=13, launch=(4, 128, 16, 64, 1))
+@pytest.mark.parametrize("byte_cells", [1, 2])
+def test_moving_discs_l2_path(mods, byte_cells):
+    run_parity(mods, _mixed(n_dyn=3), 40, seed=13, launch=(4, 128, 16, 64, byte_cells))
 
 
 def test_exclusive_reward_and_270_degree_fan(mods):
@@ -386,6 +391,16 @@ def test_uniform_action_generator_range(mods):
     assert not np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("byte_cells", [1, 3])
+def test_uneven_maps_distance_bytes(mods, byte_cells):
+    """The uneven workload's 64 maps of 128..1024 cells with distance bytes:
+    maps up to 160 KiB staged in shared memory, larger ones read through
+    L1/L2 (byte_cells 1) or staged as packed bits when those fit (3), with
+    8 moving discs per env gating the jumps."""
+    wl = W.config_uneven(n_envs=1536)
+    run_parity(mods, wl, 4, seed=17, launch=(8, 512, 160 * 1024, 64, byte_cells), threads=16)
+
+
 def test_uneven_workload_full_size(mods):
     """16384 envs over 64 maps of 128..1024 cells, beams 180/360/720, disc and
     rectangle robots, 8 moving discs per env, autotuned launch: reset and two
@@ -430,7 +445,8 @@ def test_paper_go2_march_and_sectors(mods):
     run_parity(mods, wl, 60, seed=5)
 
 
-@pytest.mark.parametrize("launch", [(1, 64, 0, 32, 1), (4, 256, 0, 64, 2), (32, 512, 16, 40, 1)])
+@pytest.mark.parametrize("launch", [(1, 64, 0, 32, 1), (4, 256, 0, 64, 2), (32, 512, 16, 40, 1),
+                                    (8, 256, 16, 40, 2)])
 def test_march_launch_shapes_and_staging(mods, launch):
     wl = W.config_paper("turtlebot2", n_envs=97)
     run_parity(mods, wl, 30, seed=6, launch=launch)
