@@ -145,7 +145,7 @@ struct nav_handle {
     std::vector<int> env_map, env_tab, env_k;
     std::vector<MapDev> maps;
     LaunchCfg cfg;
-    int smem_map_bytes = 80 * 1024;
+    int smem_map_bytes = 160 * 1024;
     int byte_cells = 1;
     MapDev *d_maps = nullptr;
     int debug = 0, stats = 0;

@@ -115,10 +115,12 @@ struct StepArgs {
 
 enum StatusBits { kStatusNoSpawn = 1, kStatusCopyTimeout = 2, kStatusBadPose = 4 };
 
+// Defaults: the autotuner's usual choice for 256 x 256 maps with distance
+// bytes staged (three 512-thread CTAs per SM).
 struct LaunchCfg {
-    int tile_envs = 2;     // envs per CTA tile
-    int block_threads = 256;
-    int max_regs = 32;     // register cap per thread: 32, 40 or 64
+    int tile_envs = 8;     // envs per CTA tile
+    int block_threads = 512;
+    int max_regs = 40;     // register cap per thread: 32, 40 or 64
     int split = 0;         // 1: env kernel + all-maps-resident ray kernel when eligible
 };
 
