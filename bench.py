@@ -207,6 +207,45 @@ def policy_rollout(steps: int = 20):
     return out
 
 
+def policy_forward(rows: int = 65536, calls: int = 20):
+    """The actor 364-256-256-4 alone on `rows` observation rows (the policy
+    half of the rollout workload): BF16 tensor-core path (observation
+    conversion, three products, head) and the plain FP32 path, CUDA events
+    over `calls` calls after 6 warm-up calls."""
+    import ctypes as C
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    lib = flashnav.load()
+    pol = C.c_void_p()
+    assert lib.nav_policy_create(364, 256, rows, 7, C.byref(pol)) == 0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED)
+    obs = torch.rand(rows, 364, device="cuda", generator=g) * 6.0
+    act = torch.empty(rows, 2, device="cuda")
+    logp = torch.empty(rows, device="cuda")
+    P = lambda t: C.c_void_p(t.data_ptr())
+    s = torch.cuda.Stream()
+    out = {}
+    for name, fn in (("bf16_tensor_cores", lib.nav_policy_act), ("fp32_simt", lib.nav_policy_act_fp32)):
+        with torch.cuda.stream(s):
+            for it in range(6):
+                assert fn(pol, P(obs), 364, rows, 0, 1, it, P(act), P(logp), None,
+                          C.c_void_p(s.cuda_stream)) == 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for it in range(calls):
+                assert fn(pol, P(obs), 364, rows, 0, 1, it, P(act), P(logp), None,
+                          C.c_void_p(s.cuda_stream)) == 0
+            e1.record(s)
+            e1.synchronize()
+        us = e0.elapsed_time(e1) / calls * 1e3
+        flop = 2.0 * rows * (364 * 256 + 256 * 256 + 256 * 4)
+        out[name] = {"us_per_forward": us, "tflops": flop / us / 1e6}
+    lib.nav_policy_free(pol)
+    out["config"] = f"{rows} rows of 364 features, actor 364-256-256-4, sampled actions"
+    return out
+
+
 def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
     """Uneven batch in one persistent launch per step: 16384 envs over 64 maps
     of 128..1024 cells, beams 180/360/720, disc and rectangle robots, 8 moving
@@ -700,7 +739,8 @@ def main():
     ap.add_argument("--extras", type=int, default=1,
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
-    ap.add_argument("--only", default="", choices=["", "policy_rollout", "uneven_batch", "paper_sensing", "training",
+    ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_forward", "uneven_batch",
+                             "paper_sensing", "training",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
                              "learner_update", "table2"],
                     help="run one of the extra measurements alone")
@@ -716,7 +756,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.only:
-        fn = {"policy_rollout": policy_rollout, "uneven_batch": uneven_batch,
+        fn = {"policy_rollout": policy_rollout, "policy_forward": policy_forward,
+              "uneven_batch": uneven_batch,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "table2": lambda: table2(args.train_seconds, args.seeds),
