@@ -208,7 +208,6 @@ constexpr int kWaitLimit = 1 << 22; // polls of one mbarrier before giving up
 
 struct WsArgs {
     int M, N, K, BN, n_mt, n_nt, n_tiles, per_split, stages;
-    int bres; // 1: each CTA keeps its n-tile of B resident and streams only A
     const float *bias;
     int bias_vec; // bias 16-byte aligned: read four columns per load
     int c16_v8;   // C16 rows 32-byte aligned: one 256-bit store per 16 columns
@@ -249,21 +248,11 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
-// The k-th tile of this CTA: (m tile, n tile, chunk range); false when the
-// CTA has no k-th tile.  Streaming mode walks every (m, n, split) tile with
-// stride gridDim.x; resident-B mode gives CTA b the n tile b % n_nt and the
-// m tiles b / n_nt, + G, + 2G, ... (G = gridDim.x / n_nt).
+// The k-th tile of this CTA: (m tile, n tile, chunk range) of tile
+// blockIdx.x + k gridDim.x in (m, n, split) order; false past the last.
 __device__ __forceinline__ bool ws_tile(const WsArgs &g, int k, int &mt, int &nt, int &c0,
                                         int &c1) {
     const int nkc = (g.K + kChunkK - 1) / kChunkK;
-    if (g.bres) {
-        const int G = gridDim.x / g.n_nt;
-        nt = blockIdx.x % g.n_nt;
-        mt = blockIdx.x / g.n_nt + k * G;
-        c0 = 0;
-        c1 = nkc;
-        return mt < g.n_mt;
-    }
     const int t = blockIdx.x + k * gridDim.x;
     if (t >= g.n_tiles) return false;
     mt = t % g.n_mt;
@@ -275,21 +264,17 @@ __device__ __forceinline__ bool ws_tile(const WsArgs &g, int k, int &mt, int &nt
     return true;
 }
 
-__global__ void __launch_bounds__(kWsThreads, 1)
+__global__ void __launch_bounds__(kWsThreads, 2)
     gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const WsArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[kWsMaxStages], empty[kWsMaxStages];
-    __shared__ __align__(8) unsigned long long accf[2], acce[2], fin, bfull;
+    __shared__ __align__(8) unsigned long long accf[2], acce[2], fin;
     __shared__ unsigned tmem_base;
     __shared__ int abort_flag;
-    const int nkc = (g.K + kChunkK - 1) / kChunkK;
-    const unsigned b_chunk = (unsigned)g.BN * 128;
-    // resident B (bres): nkc chunks of BN rows first, then the stage ring
-    const unsigned bres_base = (smem_addr(smem_raw) + 1023u) & ~1023u;
-    const unsigned base = g.bres ? bres_base + (unsigned)nkc * b_chunk : bres_base;
+    const unsigned base = (smem_addr(smem_raw) + 1023u) & ~1023u;
     const unsigned a_bytes = kTileM * 128;
-    const unsigned stage_bytes = g.bres ? a_bytes : a_bytes + b_chunk;
+    const unsigned stage_bytes = a_bytes + (unsigned)g.BN * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = g.stages;
     int ncols = 32;
@@ -311,7 +296,6 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&acce[b])) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&fin)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bfull)) : "memory");
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -333,15 +317,6 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmB))
                          : "memory");
             int mt, nt, c0, c1;
-            const bool any = ws_tile(g, 0, mt, nt, c0, c1);
-            if (g.bres && any) {
-                const unsigned bb = smem_addr(&bfull);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb),
-                             "r"((unsigned)nkc * b_chunk)
-                             : "memory");
-                for (int c = 0; c < nkc; ++c)
-                    tma_load_2d(bres_base + (unsigned)c * b_chunk, &tmB, c * kChunkK, nt * g.BN, bb);
-            }
             int it = 0;
             bool ok = true;
             for (int k = 0; ok && ws_tile(g, k, mt, nt, c0, c1); ++k) {
@@ -359,25 +334,19 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                                  : "memory");
                     const unsigned dst = base + (unsigned)s * stage_bytes;
                     tma_load_2d(dst, &tmA, c * kChunkK, mt * kTileM, fb);
-                    if (!g.bres) tma_load_2d(dst + a_bytes, &tmB, c * kChunkK, nt * g.BN, fb);
+                    tma_load_2d(dst + a_bytes, &tmB, c * kChunkK, nt * g.BN, fb);
                 }
             }
             // every copy issued lands before the CTA exits (a no-op when the
             // MMA warp consumed them all)
             for (int q = max(0, it - S); q < it; ++q)
                 ws_wait(smem_addr(&full[q % S]), (unsigned)(q / S) & 1u, abort_v) || (give_up(), true);
-            if (g.bres && any) ws_wait(smem_addr(&bfull), 0u, abort_v) || (give_up(), true);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const unsigned idesc = instr_desc(kTileM, g.BN);
             int it = 0, tl = 0, mt, nt, c0, c1;
             bool ok = true, issued = false;
-            if (g.bres && ws_tile(g, 0, mt, nt, c0, c1) &&
-                !ws_wait(smem_addr(&bfull), 0u, abort_v)) {
-                give_up();
-                ok = false;
-            }
             for (int k = 0; ok && ws_tile(g, k, mt, nt, c0, c1); ++k, ++tl) {
                 const int buf = tl & 1;
                 const unsigned ub = (unsigned)(tl >> 1);
@@ -396,7 +365,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const unsigned sa = base + (unsigned)s * stage_bytes;
-                    const unsigned sb = g.bres ? bres_base + (unsigned)c * b_chunk : sa + a_bytes;
+                    const unsigned sb = sa + a_bytes;
 #pragma unroll
                     for (int k16 = 0; k16 < kChunkK / 16; ++k16)
                         mma_f16(d, smem_desc(sa + 32u * k16), smem_desc(sb + 32u * k16), idesc,
@@ -623,36 +592,19 @@ int sm_count() {
     return n;
 }
 
-// Launches the persistent GEMM; returns false (nothing launched) when the
-// operands cannot be described by tensor maps.  Without split-K, when every
-// CTA gets at least two m tiles and B's n tile (all of K) fits in 128 KiB,
-// the n tile stays resident in shared memory (BN 256, else 128) and only A
-// streams through the stages.
+// Launches the persistent GEMM (two CTAs per SM: n tiles of at most 128
+// columns, stages within 96 KiB); returns false (nothing launched) when the
+// operands cannot be described by tensor maps.
 bool launch_ws(const void *A, int lda, const void *B, int ldb, int M, int N, int K, int BN,
                int per_split, int n_splits, const float *bias, int act, float *C32, int ldc32,
                void *C16, int ldc16, void *C16T, int ldct, int *status, cudaStream_t s, int &rc) {
-    const int nkc = (K + kChunkK - 1) / kChunkK;
+    BN = std::min(BN, 128);
     const int n_mt = (M + kTileM - 1) / kTileM;
-    int bres = 0;
-    if (per_split == 0) {
-        // the narrower n tile first: its smaller resident B leaves room for
-        // more A stages in flight
-        for (int bn : {std::min(BN, 128), BN}) {
-            const int n_nt = (N + bn - 1) / bn;
-            const int G = std::max(1, sm_count() / n_nt);
-            if ((long long)nkc * bn * 128 <= 128 * 1024 && n_mt >= 2 * G) {
-                bres = 1;
-                BN = bn;
-                break;
-            }
-        }
-    }
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, lda, M, K, kTileM) || !make_map(&mb, B, ldb, N, K, BN)) return false;
-    const int b_bytes = bres ? nkc * BN * 128 : 0;
-    const int stage_bytes = kTileM * 128 + (bres ? 0 : BN * 128);
-    const int stages = std::min(kWsMaxStages, (200 * 1024 - b_bytes) / stage_bytes);
-    const size_t smem = 1024 + (size_t)b_bytes + (size_t)stages * stage_bytes;
+    const int stage_bytes = kTileM * 128 + BN * 128;
+    const int stages = std::min(kWsMaxStages, (96 * 1024) / stage_bytes);
+    const size_t smem = 1024 + (size_t)stages * stage_bytes;
     {
         // the attribute only ever rises (a lower value would refuse later
         // launches still queued with a larger request)
@@ -673,7 +625,6 @@ bool launch_ws(const void *A, int lda, const void *B, int ldb, int M, int N, int
     g.n_tiles = g.n_mt * g.n_nt * n_splits;
     g.per_split = per_split;
     g.stages = stages;
-    g.bres = bres;
     g.bias = bias; g.act = act;
     g.bias_vec = (reinterpret_cast<uintptr_t>(bias) & 15u) == 0;
     g.c16_v8 = C16 && (reinterpret_cast<uintptr_t>(C16) & 31u) == 0 && (ldc16 % 16) == 0;
@@ -682,9 +633,7 @@ bool launch_ws(const void *A, int lda, const void *B, int ldb, int M, int N, int
     g.C16 = static_cast<__nv_bfloat16 *>(C16); g.ldc16 = ldc16;
     g.C16T = static_cast<__nv_bfloat16 *>(C16T); g.ldct = ldct;
     g.status = status;
-    // resident B: n_nt groups of G CTAs; streaming: one CTA per SM at most
-    const int grid = bres ? g.n_nt * std::max(1, sm_count() / g.n_nt)
-                          : std::min(g.n_tiles, sm_count());
+    const int grid = std::min(g.n_tiles, 2 * sm_count());
     gemm_ws<<<grid, kWsThreads, smem, s>>>(ma, mb, g);
     rc = (int)cudaGetLastError();
     return true;
