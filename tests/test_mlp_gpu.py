@@ -31,7 +31,10 @@ def _p(t):
 @pytest.mark.parametrize("m,n,k,lda,act", [
     (128, 256, 64, 64, 0), (4096, 256, 364, 368, 1), (200, 40, 100, 104, 0),
     (1, 4, 256, 256, 0), (333, 256, 256, 256, 1), (4096, 2, 256, 256, 0),
-    (129, 17, 16, 16, 1), (4096, 256, 256, 264, 0)])
+    (129, 17, 16, 16, 1), (4096, 256, 256, 264, 0),
+    # several tiles per persistent CTA (626 tiles for 296 CTAs): accumulator
+    # and stage-ring reuse across tiles
+    (40000, 256, 256, 256, 1)])
 def test_gemm_matches_fp64(env, m, n, k, lda, act):
     flashnav, torch = env
     lib = flashnav.load()
