@@ -102,9 +102,10 @@ __device__ __forceinline__ float draw_unit(unsigned bits24) {
 // step in x is +-1 and a step in y is +-stride.
 //   BitsShared  packed free bits staged in shared memory (bulk TMA copy)
 //   BitsGlobal  packed free bits read through L1/L2
-//   BytesShared one byte per cell in shared memory, expanded from the packed
-//               bits: a lookup is one byte load and one compare, which moves
-//               the shift and mask work of the bit lookup off the ALU pipe
+//   BytesShared distance bytes staged in shared memory (bulk TMA copy): a
+//               lookup is one byte load, and the value lets a ray jump
+//               through the free square around the cell
+//   BytesGlobal distance bytes read through L1/L2
 // ---------------------------------------------------------------------------
 struct BitsShared {
     const uint32_t *w;
@@ -961,9 +962,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
 }
 
 // Persistent CTAs: each CTA takes tiles from a global queue until none are
-// left.  A tile's map is staged into shared memory (bytes expanded from the
-// packed bits, or the packed bits by bulk TMA copy) only when the CTA's
-// previous tile used another map.  The last CTA to finish zeroes the queue
+// left.  A tile's map is staged into shared memory (its distance bytes or
+// its packed bits, by bulk TMA copies) only when the CTA's previous tile used
+// another map.  The last CTA to finish zeroes the queue
 // for the next launch on the stream.
 // MINB: resident 512-thread CTAs per SM the register allocation must allow
 // (4, 3, 2 -> at most 32, 40, 64 registers per thread).
