@@ -290,7 +290,8 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
             "beam_casts_per_step": rays / steps_per_graph,
             "cell_visits_per_s": visits / steps_per_graph / (ms / 1e3),
             "launch": dict(zip(("tile_envs", "block_threads", "smem_map_bytes", "max_regs",
-                                "byte_cells", "split"), sim.get_launch())),
+                                "byte_cells", "split"), sim.get_launch()),
+                           tile_order=sim.get_tile_order()),
             "autotune_ms_per_step": tune_ms,
             "config": "16384 envs, 64 maps 128..1024 cells, beams 180/360/720, disc+rect, "
                       "8 moving discs, graph of 20 steps, L2 flushed between replays"}
@@ -682,6 +683,7 @@ def run_gpu(args):
                        "launch": {"tile_envs": launch[0], "block_threads": launch[1],
                                   "smem_map_bytes": launch[2], "max_regs": launch[3],
                                   "byte_cells": launch[4], "split": launch[5],
+                                  "tile_order": sim.get_tile_order(),
                                   "chosen_by": "fixed" if args.launch else "autotuner"}},
             "beam_casts_per_s": world * rays / (step_ms / 1e3),
             "cell_visits_per_s": world * visits / (step_ms / 1e3),

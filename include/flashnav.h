@@ -201,7 +201,8 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
  *   tile_envs      envs per CTA tile (1..32)
  *   block_threads  threads per CTA (64..512, multiple of 32)
  *   smem_map_bytes shared-memory budget for the staged map (<= 200 KiB); a
- *                  map that does not fit is read as packed bits through L1/L2
+ *                  map that does not fit is read through L1/L2 (see
+ *                  byte_cells)
  *   max_regs       register cap per thread: 32, 40 or 64 (more resident CTAs
  *                  against fewer registers)
  *   byte_cells     map representation: 1 distance bytes (one byte per cell,
@@ -219,18 +220,27 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
  *                  keep every map resident and whose warps take 32-ray chunks
  *                  from a queue (no per-tile barriers); 2: the fused tiled
  *                  kernel.  nav_get_launch reports the path in use (1 or 2).
- * 0 keeps the current value.  Synchronises the handle's stream. */
+ * 0 keeps the current value.  A new handle starts at tile_envs 8, 512
+ * threads, 160 KiB, 40 registers, byte_cells 1, fused kernel.  Synchronises
+ * the handle's stream. */
 int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map_bytes,
                    int max_regs, int byte_cells, int split);
 int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads,
                    int *smem_map_bytes, int *max_regs, int *byte_cells, int *split);
 
+/* Order of the tile queue (no paper counterpart): 0 largest map x beam count
+ * first (ties in map order), 1 most expensive tiles first, by envs x beams x
+ * the mean cells per ray of a fixed host-side sample of rays on the map.
+ * The autotuner tries both.  Synchronises the handle's stream. */
+int nav_set_tile_order(nav_handle *h, int order);
+int nav_get_tile_order(const nav_handle *h, int *order);
+
 /* Autotuner (no paper counterpart; it picks the launch shape for this
  * handle's mix of map sizes, beam counts and robots).  From a device copy of
  * the current state it times `steps` steps of each candidate with uniform
  * random actions: first tile_envs x block_threads x max_regs, then the
- * staging mode and shared-memory budget for the best shape, then the split
- * step when eligible.  It restores the
+ * staging mode and shared-memory budget for the best shape, then the tile
+ * order, then the split step when eligible.  It restores the
  * state and keeps the fastest candidate.  Synchronous.  best_ms (host, may be
  * NULL) receives the winner's mean step time. */
 int nav_autotune(nav_handle *h, int steps, float *best_ms);

@@ -144,6 +144,7 @@ struct nav_handle {
     std::vector<int64_t> obs_off, ray_off;
     std::vector<int> env_map, env_tab, env_k;
     std::vector<MapDev> maps;
+    std::vector<float> map_ray_cost; // mean cells per ray of a host sample, per map
     LaunchCfg cfg;
     int smem_map_bytes = 160 * 1024;
     int byte_cells = 1;
@@ -224,9 +225,51 @@ void chessboard_distance(const nav_map &mp, int stride, uint8_t *out) {
         }
 }
 
+// Mean number of cells a ray walks before a blocked cell, the map edge or
+// r_max (cells), over a fixed sample of rays from free cells in seeded
+// directions: the relative cost of a tile's rays on this map.
+float sample_ray_cost(const nav_map &mp, float rmax_c) {
+    const int W = mp.width, H = mp.height;
+    auto blocked = [&](int i, int j) {
+        return i < 0 || j < 0 || i >= W || j >= H || mp.occ[(size_t)j * W + i] != 0;
+    };
+    unsigned long long z = 0x2545F4914F6CDD1Dull ^ ((unsigned long long)W << 32) ^ (unsigned)H;
+    auto next = [&]() {
+        z ^= z << 13;
+        z ^= z >> 7;
+        z ^= z << 17;
+        return z;
+    };
+    double total = 0.0;
+    int n = 0;
+    for (int tries = 0; tries < 4096 && n < 256; ++tries) {
+        const int i0 = (int)(next() % (unsigned long long)W), j0 = (int)(next() % (unsigned long long)H);
+        if (blocked(i0, j0)) continue;
+        const double a = (double)(next() >> 11) * (6.283185307179586 / 9007199254740992.0);
+        const double dx = std::cos(a), dy = std::sin(a);
+        double x = i0 + 0.5, y = j0 + 0.5;
+        int i = i0, j = j0, cells = 1;
+        const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
+        const double tdx = dx != 0 ? std::fabs(1.0 / dx) : 1e30, tdy = dy != 0 ? std::fabs(1.0 / dy) : 1e30;
+        double tx = dx > 0 ? (i + 1 - x) * tdx : dx < 0 ? (x - i) * tdx : 1e30;
+        double ty = dy > 0 ? (j + 1 - y) * tdy : dy < 0 ? (y - j) * tdy : 1e30;
+        for (;;) {
+            const double t = std::min(tx, ty);
+            if (t > rmax_c) break;
+            if (tx <= ty) { i += sx; tx += tdx; } else { j += sy; ty += tdy; }
+            ++cells;
+            if (blocked(i, j)) break;
+        }
+        total += cells;
+        ++n;
+    }
+    return n ? (float)(total / n) : 1.0f;
+}
+
 // Groups envs by (map, beam table) and cuts each group into tiles of at most
-// tile_envs envs; the tile list runs over the largest maps first so that the
-// longest CTAs start early.
+// tile_envs envs.  The queue runs over the largest tiles first so that the
+// longest CTAs start early: by map size x beams (order 0, ties in map order)
+// or by envs x beams x sampled cells per ray (order 1, ties by map size).
 int build_tiles(nav_handle *h) {
     const int E = h->n_envs;
     std::vector<int> perm(E);
@@ -256,6 +299,11 @@ int build_tiles(nav_handle *h) {
     std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &x, const TileDev &y) {
         const long long wx = (long long)h->maps[x.map].n_words * h->env_k[perm[x.env_begin]];
         const long long wy = (long long)h->maps[y.map].n_words * h->env_k[perm[y.env_begin]];
+        if (h->cfg.order == 1) {
+            const double cx = (double)x.env_count * h->env_k[perm[x.env_begin]] * h->map_ray_cost[x.map];
+            const double cy = (double)y.env_count * h->env_k[perm[y.env_begin]] * h->map_ray_cost[y.map];
+            if (cx != cy) return cx > cy;
+        }
         return wx > wy;
     });
     cudaError_t e;
@@ -525,6 +573,7 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
             chessboard_distance(mp, bstride, dist_all.data() + md.dist_off);
         }
         h->maps.push_back(md);
+        h->map_ray_cost.push_back(sample_ray_cost(mp, max_range * md.inv_res));
     }
     // envs
     h->env_map.resize(n_envs);
@@ -1034,6 +1083,22 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
     return NAV_OK;
 }
 
+int nav_set_tile_order(nav_handle *h, int order) {
+    if (!h) return NAV_E_INVAL;
+    if (order != 0 && order != 1) return fail(h, NAV_E_INVAL, "nav_set_tile_order: order 0 or 1");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if (order == h->cfg.order) return NAV_OK;
+    h->cfg.order = order;
+    return build_tiles(h);
+}
+
+int nav_get_tile_order(const nav_handle *h, int *order) {
+    if (!h || !order) return NAV_E_INVAL;
+    *order = h->cfg.order;
+    return NAV_OK;
+}
+
 int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int *smem_map_bytes,
                    int *max_regs, int *byte_cells, int *split) {
     if (!h) return NAV_E_INVAL;
@@ -1167,19 +1232,45 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
             }
         }
     }
-    // pass 2: staging (byte cells or packed bits) and the shared-memory cap
+    // pass 2: staging (byte cells or packed bits) and the shared-memory cap,
+    // with every register cap for the best shape (a smaller staged map
+    // leaves room for more resident CTAs, which shifts the best cap)
     if (rc == NAV_OK) {
-        h->cfg = best_cfg;
+        const LaunchCfg shape = best_cfg;
+        h->cfg = shape;
         rc = build_tiles(h);
         const int caps[] = {24 * 1024, 80 * 1024, 160 * 1024};
-        for (int bc = 1; bc <= 3 && rc == NAV_OK; ++bc)
-            for (int cap : caps) {
-                h->byte_cells = bc;
-                h->smem_map_bytes = cap;
-                if ((rc = set_map_modes(h)) != NAV_OK) break;
-                const float ms = time_config(h, steps, e0, e1);
-                if (ms < best) { best = ms; best_cap = cap; best_bytes = bc; }
+        for (int mr : regs)
+            for (int bc = 1; bc <= 3 && rc == NAV_OK; ++bc)
+                for (int cap : caps) {
+                    h->cfg.max_regs = mr;
+                    h->byte_cells = bc;
+                    h->smem_map_bytes = cap;
+                    if ((rc = set_map_modes(h)) != NAV_OK) break;
+                    const float ms = time_config(h, steps, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        best_cap = cap;
+                        best_bytes = bc;
+                        best_cfg = h->cfg;
+                    }
+                }
+    }
+    // pass 2b: the tile queue order
+    if (rc == NAV_OK) {
+        h->cfg = best_cfg;
+        h->smem_map_bytes = best_cap;
+        h->byte_cells = best_bytes;
+        if ((rc = set_map_modes(h)) == NAV_OK) {
+            h->cfg.order = 1 - best_cfg.order;
+            if ((rc = build_tiles(h)) == NAV_OK) {
+                const float ms = time_config(h, 3 * steps, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = h->cfg;
+                }
             }
+        }
     }
     // pass 3: the split step (env kernel + all-maps-resident ray kernel)
     if (rc == NAV_OK && h->split_ok) {

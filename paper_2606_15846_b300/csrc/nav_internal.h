@@ -122,6 +122,7 @@ struct LaunchCfg {
     int block_threads = 512;
     int max_regs = 40;     // register cap per thread: 32, 40 or 64
     int split = 0;         // 1: env kernel + all-maps-resident ray kernel when eligible
+    int order = 0;         // tile queue order: 0 map size x beams, 1 sampled ray cost
 };
 
 // Launches one step (or reset) of every tile on `stream`: persistent CTAs,

@@ -24,6 +24,7 @@ EXPORTS = [
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_host_pipeline", "nav_set_launch", "nav_get_launch",
+    "nav_set_tile_order", "nav_get_tile_order",
     "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
@@ -112,6 +113,8 @@ def load():
         "nav_get_stats": (I, [P, P, P]),
         "nav_set_launch": (I, [P, I, I, I, I, I, I]),
         "nav_get_launch": (I, [P, P, P, P, P, P, P]),
+        "nav_set_tile_order": (I, [P, I]),
+        "nav_get_tile_order": (I, [P, P]),
         "nav_autotune": (I, [P, I, P]),
         "nav_uniform_actions": (I, [P, U64, C.c_uint32, P]),
         "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
@@ -336,6 +339,15 @@ class NavSim:
         v = [C.c_int() for _ in range(6)]
         self._check(load().nav_get_launch(self._h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def set_tile_order(self, order: int):
+        self._bind_stream()
+        self._check(load().nav_set_tile_order(self._h, order))
+
+    def get_tile_order(self) -> int:
+        v = C.c_int()
+        self._check(load().nav_get_tile_order(self._h, C.byref(v)))
+        return v.value
 
     def autotune(self, steps: int = 5) -> float:
         """Picks the fastest launch shape for this handle; returns its ms/step."""

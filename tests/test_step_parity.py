@@ -76,11 +76,14 @@ def _compare_debug(sim, ref, tag):
 
 
 def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=8,
-               check_state_every=1, autotune=False):
+               check_state_every=1, autotune=False, tile_order=None):
     flashnav, oracle, torch = mods
     sim = flashnav.NavSim.from_workload(wl)
     if launch:
         sim.set_launch(*launch)
+    if tile_order is not None:
+        sim.set_tile_order(tile_order)
+        assert sim.get_tile_order() == tile_order
     ref = oracle.OracleSim.from_workload(wl, threads=threads)
     if autotune:
         sim.reset(seed)
@@ -193,6 +196,12 @@ def _mixed(n_envs=96, n_dyn=0, sizes=(48, 96, 160, 200), seed0=40):
 
 def test_mixed_maps_beams_and_rectangles(mods):
     run_parity(mods, _mixed(), 80, seed=11)
+
+
+def test_mixed_maps_tile_queue_by_ray_cost(mods):
+    """The tile queue ordered by sampled ray cost (tiles of four map sizes,
+    four beam counts and two robots interleave differently)."""
+    run_parity(mods, _mixed(), 40, seed=19, launch=(3, 256, 0, 40, 1), tile_order=1)
 
 
 def test_moving_discs(mods):
