@@ -765,8 +765,24 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         const float xc = x * M.inv_res, yc = y * M.inv_res;
         float st, ct;
         sincos_taylor(th, st, ct);
-        bool coll;
-        if (rb.shape == 0)
+        // With a distance view: the footprint lies within R cells of a point
+        // of the centre's cell, so it can only meet cells fewer than R + 1
+        // rows or columns away; when the centre cell's chessboard distance d
+        // has d - 2 >= R (R rounded up a little), all of those are free and
+        // the row scan is skipped (same result).
+        bool clear = false;
+        if constexpr (has_dist<B>::value && !DYN) {
+            const float hl = (0.5f * rb.length) * M.inv_res, hw = (0.5f * rb.width) * M.inv_res;
+            const float R = rb.shape == 0 ? rb.radius * M.inv_res : sqrtf(hl * hl + hw * hw);
+            if (xc >= 0.0f && yc >= 0.0f && xc < (float)M.w && yc < (float)M.h) {
+                const int d = bits.dist_at(cell_index(bits, (int)xc, (int)yc));
+                clear = (float)(d - 2) >= R * 1.0001f + 0.001f;
+            }
+        }
+        bool coll = false;
+        if (clear)
+            coll = false;
+        else if (rb.shape == 0)
             coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, nd);
         else
             coll = rect_blocked<DYN>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
