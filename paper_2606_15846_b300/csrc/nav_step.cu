@@ -204,9 +204,16 @@ __device__ __forceinline__ bool disc_row(float xc, float yc, float rc, int j, in
 struct DynEnv {
     short j0[kMaxDyn], nr[kMaxDyn], bi0[kMaxDyn], bi1[kMaxDyn];
     short lo[kMaxDyn][kMaxDynRows], hi[kMaxDyn][kMaxDynRows];
+    int n; // stamps kept (those within reach of the robot), entries [0, n)
 };
 
-__device__ void stamp_discs(const float4 *ob, int nd, float inv_res, float rdc, DynEnv &de) {
+// Stamps the nd discs (cells whose closed square meets the open disc, per
+// row) and keeps, in order, those whose stamp comes within `reach` cells of
+// the robot at (xc, yc): rays (t <= r_max) and the footprint only enter
+// cells that close to it, so the others cannot change any result.
+__device__ void stamp_discs(const float4 *ob, int nd, float inv_res, float rdc, float xc, float yc,
+                            float reach, DynEnv &de) {
+    int k = 0;
     for (int q = 0; q < nd; ++q) {
         const float oxc = ob[q].x * inv_res, oyc = ob[q].y * inv_res;
         const int j0 = (int)floorf(oyc - rdc);
@@ -217,28 +224,34 @@ __device__ void stamp_discs(const float4 *ob, int nd, float inv_res, float rdc, 
         for (int r = 0; r < nr; ++r) {
             int a, b;
             if (!disc_row(oxc, oyc, rdc, j0 + r, a, b)) { a = 1; b = 0; }
-            de.lo[q][r] = (short)a;
-            de.hi[q][r] = (short)b;
+            de.lo[k][r] = (short)a;
+            de.hi[k][r] = (short)b;
             if (a <= b) { bmin = min(bmin, a); bmax = max(bmax, b); }
         }
-        de.j0[q] = (short)j0;
-        de.nr[q] = (short)(bmin <= bmax ? nr : 0);
-        de.bi0[q] = (short)bmin;
-        de.bi1[q] = (short)bmax;
+        if (bmin > bmax) continue; // the disc covers no cell
+        const float gx = fmaxf(0.0f, fmaxf((float)bmin - xc, xc - (float)(bmax + 1)));
+        const float gy = fmaxf(0.0f, fmaxf((float)j0 - yc, yc - (float)(j0 + nr)));
+        if (gx * gx + gy * gy > reach * reach) continue;
+        de.j0[k] = (short)j0;
+        de.nr[k] = (short)nr;
+        de.bi0[k] = (short)bmin;
+        de.bi1[k] = (short)bmax;
+        ++k;
     }
+    de.n = k;
 }
 
-__device__ __forceinline__ bool dyn_cell(const DynEnv &de, int nd, int i, int j) {
-    for (int q = 0; q < nd; ++q) {
+__device__ __forceinline__ bool dyn_cell(const DynEnv &de, int i, int j) {
+    for (int q = 0; q < de.n; ++q) {
         const int r = j - de.j0[q];
         if ((unsigned)r < (unsigned)de.nr[q] && i >= de.lo[q][r] && i <= de.hi[q][r]) return true;
     }
     return false;
 }
 
-__device__ __forceinline__ bool dyn_row(const DynEnv &de, int nd, int j, int i0, int i1) {
+__device__ __forceinline__ bool dyn_row(const DynEnv &de, int j, int i0, int i1) {
     if (i0 > i1) return false;
-    for (int q = 0; q < nd; ++q) {
+    for (int q = 0; q < de.n; ++q) {
         const int r = j - de.j0[q];
         if ((unsigned)r < (unsigned)de.nr[q] && max(i0, (int)de.lo[q][r]) <= min(i1, (int)de.hi[q][r]))
             return true;
@@ -247,26 +260,28 @@ __device__ __forceinline__ bool dyn_row(const DynEnv &de, int nd, int j, int i0,
 }
 
 // Parameter interval along the ray in which it can enter a stamped cell: the
-// union of its crossings of every stamp's bounding box grown by one cell.
-// Outside it the per-cell disc test is skipped (it could not succeed).
-__device__ void dyn_gate(const DynEnv &de, int nd, float xc, float yc, float dx, float dy,
-                         float &glo, float &ghi) {
+// union of its crossings of every stamp's bounding box grown by one cell
+// (the margin also covers the rounding of the crossings, computed with the
+// reciprocals rdx = 1 / dx, rdy = 1 / dy).  Outside it the per-cell disc test
+// is skipped (it could not succeed).
+__device__ void dyn_gate(const DynEnv &de, float xc, float yc, float dx, float dy, float &glo,
+                         float &ghi) {
     glo = INFINITY;
     ghi = -INFINITY;
-    for (int q = 0; q < nd; ++q) {
-        if (de.nr[q] == 0) continue;
+    const float rdx = dx != 0.0f ? 1.0f / dx : 0.0f, rdy = dy != 0.0f ? 1.0f / dy : 0.0f;
+    for (int q = 0; q < de.n; ++q) {
         const float x0 = (float)(de.bi0[q] - 1), x1 = (float)(de.bi1[q] + 2);
         const float y0 = (float)(de.j0[q] - 1), y1 = (float)(de.j0[q] + de.nr[q] + 1);
         float ta = 0.0f, tb = INFINITY;
         if (dx != 0.0f) {
-            const float u = (x0 - xc) / dx, v = (x1 - xc) / dx;
+            const float u = (x0 - xc) * rdx, v = (x1 - xc) * rdx;
             ta = fmaxf(ta, fminf(u, v));
             tb = fminf(tb, fmaxf(u, v));
         } else if (xc < x0 || xc > x1) {
             continue;
         }
         if (dy != 0.0f) {
-            const float u = (y0 - yc) / dy, v = (y1 - yc) / dy;
+            const float u = (y0 - yc) * rdy, v = (y1 - yc) * rdy;
             ta = fmaxf(ta, fminf(u, v));
             tb = fminf(tb, fmaxf(u, v));
         } else if (yc < y0 || yc > y1) {
@@ -309,14 +324,14 @@ struct has_dist<V, decltype((void)V::kDist)> { static constexpr bool value = V::
 template <bool DYN, class V>
 __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float xc, float yc,
                                           float dx, float dy, float rmax_c, float max_range,
-                                          const DynEnv *de, int nd, int &hit, unsigned &vis) {
+                                          const DynEnv *de, int &hit, unsigned &vis) {
     const int pb = view.stride;
     if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
     const float fx = floorf(xc), fy = floorf(yc);
     const int i0 = (int)fx, j0 = (int)fy;
     if (i0 >= M.w || j0 >= M.h) { hit = -1; vis = 1; return 0.0f; }
     int b = cell_index(view, i0, j0);
-    if (!view.free_at(b) || (DYN && dyn_cell(*de, nd, i0, j0))) {
+    if (!view.free_at(b) || (DYN && dyn_cell(*de, i0, j0))) {
         hit = j0 * M.w + i0;
         vis = 1;
         return 0.0f;
@@ -330,7 +345,7 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
     if (dy > 0.0f) { sby = pb; tdy = 1.0f / dy; ty0 = ((fy + 1.0f) - yc) * tdy; }
     else if (dy < 0.0f) { sby = -pb; tdy = 1.0f / -dy; ty0 = (yc - fy) * tdy; }
     float glo = INFINITY, ghi = -INFINITY;
-    if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
+    if (DYN) dyn_gate(*de, xc, yc, dx, dy, glo, ghi);
     float t = 0.0f, kx, ky;
     bool stopped = false;
     if constexpr (has_dist<V>::value) {
@@ -379,7 +394,7 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
                 const float ax = xmaj ? kM : km, ay = xmaj ? km : kM;
                 const int ci = i0 + (sbx < 0 ? -(int)ax : (int)ax);
                 const int cj = j0 + (sby < 0 ? -(int)ay : (int)ay);
-                if (dyn_cell(*de, nd, ci, cj)) { stopped = true; break; }
+                if (dyn_cell(*de, ci, cj)) { stopped = true; break; }
             }
         }
         kx = xmaj ? kM : km;
@@ -399,7 +414,7 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
             if (DYN && t >= glo && t <= ghi) {
                 const int ci = i0 + (sbx < 0 ? -(int)kx : (int)kx);
                 const int cj = j0 + (sby < 0 ? -(int)ky : (int)ky);
-                if (dyn_cell(*de, nd, ci, cj)) { stopped = true; break; }
+                if (dyn_cell(*de, ci, cj)) { stopped = true; break; }
             }
         }
     }
@@ -427,19 +442,19 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
 template <bool DYN, class V>
 __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float xc, float yc,
                                            float dx, float dy, float step_c, float rmax_c,
-                                           float max_range, const DynEnv *de, int nd, int &hit,
+                                           float max_range, const DynEnv *de, int &hit,
                                            unsigned &vis) {
     if (!(xc >= 0.0f && yc >= 0.0f)) { hit = -1; vis = 1; return 0.0f; }
     int i = (int)floorf(xc), j = (int)floorf(yc);
     if (i >= M.w || j >= M.h) { hit = -1; vis = 1; return 0.0f; }
     int b0 = cell_index(view, i, j);
-    if (!view.free_at(b0) || (DYN && dyn_cell(*de, nd, i, j))) {
+    if (!view.free_at(b0) || (DYN && dyn_cell(*de, i, j))) {
         hit = j * M.w + i;
         vis = 1;
         return 0.0f;
     }
     float glo = INFINITY, ghi = -INFINITY;
-    if (DYN) dyn_gate(*de, nd, xc, yc, dx, dy, glo, ghi);
+    if (DYN) dyn_gate(*de, xc, yc, dx, dy, glo, ghi);
     if constexpr (has_dist<V>::value) {
         // s_end: the first sample past r_max
         float s_end = fmaxf(1.0f, floorf(rmax_c / step_c));
@@ -464,7 +479,7 @@ __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float
                 return tc * M.res;
             }
             d = view.dist_at(cell_index(view, i, j));
-            if (d == 0 || (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
+            if (d == 0 || (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, i, j))) {
                 hit = j * M.w + i;
                 vis = (unsigned)s + 1u;
                 return tc * M.res;
@@ -483,7 +498,7 @@ __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float
                 return tc * M.res;
             }
             if (!view.free_at(cell_index(view, i, j)) ||
-                (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, nd, i, j))) {
+                (DYN && tc >= glo && tc <= ghi && dyn_cell(*de, i, j))) {
                 hit = j * M.w + i;
                 vis = s + 1u;
                 return tc * M.res;
@@ -525,14 +540,14 @@ __device__ __forceinline__ void put_range(const StepArgs &A, float *row, int k, 
 // ---------------------------------------------------------------------------
 template <bool DYN, class B>
 __device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc, float rc,
-                             const DynEnv *de, int nd) {
+                             const DynEnv *de) {
     const int j0 = (int)floorf(yc - rc);
     const int j1 = (int)ceilf(yc + rc) - 1;
     for (int j = j0; j <= j1; ++j) {
         int a, b;
         if (!disc_row(xc, yc, rc, j, a, b)) continue;
         if (row_blocked(bits, M, j, a, b)) return true;
-        if (DYN && dyn_row(*de, nd, j, a, b)) return true;
+        if (DYN && dyn_row(*de, j, a, b)) return true;
     }
     return false;
 }
@@ -543,7 +558,7 @@ __device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc,
 // and its edges' crossings of y = j and y = j + 1.
 template <bool DYN, class B>
 __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc, float st,
-                             float ct, float hl, float hw, const DynEnv *de, int nd) {
+                             float ct, float hl, float hw, const DynEnv *de) {
     const float ax = hl * ct, ay = hl * st;
     const float bx = -(hw * st), by = hw * ct;
     float px[4], py[4];
@@ -588,7 +603,7 @@ __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc,
         if (!(xlo <= xhi)) continue;
         const int a = (int)floorf(xlo), b = (int)ceilf(xhi) - 1;
         if (row_blocked(bits, M, j, a, b)) return true;
-        if (DYN && dyn_row(*de, nd, j, a, b)) return true;
+        if (DYN && dyn_row(*de, j, a, b)) return true;
     }
     return false;
 }
@@ -696,6 +711,15 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
     const int D = A.p.n_sectors > 0 ? A.p.n_sectors : K; // range features per row
     float4 ob[kMaxDyn];
     const float rdc = A.p.dyn_radius * M.inv_res;
+    // stamps farther than this (cells) from the robot can meet neither a
+    // ray (t <= r_max) nor the footprint, and are dropped
+    float reach = 0.0f;
+    if (DYN) {
+        const RobotDev rb0 = A.robots[A.env_robot[e]];
+        const float hl = 0.5f * rb0.length, hw = 0.5f * rb0.width;
+        const float foot = rb0.shape == 0 ? rb0.radius : sqrtf(hl * hl + hw * hw);
+        reach = (A.max_range + foot) * M.inv_res + 2.0f;
+    }
     float x, y, th, v, w, gx, gy, dprev;
     int step;
     unsigned episode;
@@ -758,7 +782,7 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
                     o.y = ny;
                 ob[q] = o;
             }
-            stamp_discs(ob, nd, M.inv_res, rdc, *dmain);
+            stamp_discs(ob, nd, M.inv_res, rdc, x * M.inv_res, y * M.inv_res, reach, *dmain);
             restamp = false;
         }
         // a6: footprint against the bitmap (and the moving-disc layer)
@@ -783,10 +807,10 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         if (clear)
             coll = false;
         else if (rb.shape == 0)
-            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, nd);
+            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain);
         else
             coll = rect_blocked<DYN>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
-                                     (0.5f * rb.width) * M.inv_res, dmain, nd);
+                                     (0.5f * rb.width) * M.inv_res, dmain);
         // a7: goal test, reward, flags
         const float ddx = gx - x, ddy = gy - y;
         const float d = sqrtf(ddx * ddx + ddy * ddy);
@@ -829,7 +853,8 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
     A.episode[e] = episode;
     if (DYN) {
         for (int q = 0; q < nd; ++q) A.dyn[(size_t)e * nd + q] = ob[q];
-        if (restamp) stamp_discs(ob, nd, M.inv_res, rdc, *dmain);
+        if (restamp)
+            stamp_discs(ob, nd, M.inv_res, rdc, x * M.inv_res, y * M.inv_res, reach, *dmain);
     }
     // a9: observation tail of the scan written to obs (sector minima start at r_max)
     write_tail(A.obs + slot.obs_off + D, x, y, th, gx, gy, v, w);
@@ -905,7 +930,6 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     const int total = n_main + n_fin * K;
     const float rmax_c = A.max_range * M.inv_res;
     const float step_c = A.p.march_step * M.inv_res;
-    const int nd = DYN ? A.p.n_dyn : 0;
     for (;;) {
         int chunk = 0;
         if (lane == 0) chunk = atomicAdd(next_chunk, 1);
@@ -933,8 +957,8 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
             const DynEnv *de = DYN ? &dyn[2 * s + (fin ? 1 : 0)] : nullptr;
             int hit;
             range = MARCH ? march_ray<DYN>(bits, M, ox, oy, dx, dy, step_c, rmax_c, A.max_range,
-                                           de, nd, hit, vis)
-                          : cast_ray<DYN>(bits, M, ox, oy, dx, dy, rmax_c, A.max_range, de, nd,
+                                           de, hit, vis)
+                          : cast_ray<DYN>(bits, M, ox, oy, dx, dy, rmax_c, A.max_range, de,
                                           hit, vis);
             row = (fin ? A.final_obs : A.obs) + es.obs_off;
             if (!fin && A.dbg_range) {
@@ -1129,8 +1153,8 @@ __device__ __forceinline__ float cast_one(const StepArgs &A, const V &view, cons
     int hit;
     const float range =
         MARCH ? march_ray<false>(view, M, o.x, o.y, dx, dy, A.p.march_step * M.inv_res, rmax_c,
-                                 A.max_range, nullptr, 0, hit, vis)
-              : cast_ray<false>(view, M, o.x, o.y, dx, dy, rmax_c, A.max_range, nullptr, 0, hit,
+                                 A.max_range, nullptr, hit, vis)
+              : cast_ray<false>(view, M, o.x, o.y, dx, dy, rmax_c, A.max_range, nullptr, hit,
                                 vis);
     if (!fin && A.dbg_range) {
         const long long ro = A.ray_off[e] + k;
