@@ -930,6 +930,7 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     const int total = n_main + n_fin * K;
     const float rmax_c = A.max_range * M.inv_res;
     const float step_c = A.p.march_step * M.inv_res;
+    const float inv_k = 1.0f / (float)K; // rr / K by a multiply and one correction
     for (;;) {
         int chunk = 0;
         if (lane == 0) chunk = atomicAdd(next_chunk, 1);
@@ -943,8 +944,10 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
         int k = 0;
         if (rid < total) {
             const bool fin = rid >= n_main;
-            const int rr = fin ? rid - n_main : rid;
-            const int q = rr / K;
+            const int rr = fin ? rid - n_main : rid; // < 2^24: exact as a float
+            int q = (int)((float)rr * inv_k);
+            q -= q * K > rr ? 1 : 0;
+            q += (q + 1) * K <= rr ? 1 : 0;
             k = rr - q * K;
             const int s = fin ? fin_slot[q] : q;
             const EnvSlot &es = slots[s];
