@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "nav_internal.h"
+#include "pdl.cuh"
 #include "nav_policy.h"
 #include "tc_util.cuh"
 
@@ -109,6 +110,7 @@ __device__ __forceinline__ void zero_cols(unsigned char *tile, int row, int c0, 
 // layer l + 1's tile is copied while layer l computes).  Warp w reads TMEM
 // lanes 32 (w % 4) .. (batch rows) and columns [64 h, 64 h + 64), h = w / 4.
 __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ unsigned tmem_slot;
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
 // rewritten in place once the layer's MMAs have completed.  As in the
 // forward, warps w and w + 4 share TMEM lanes and split the columns.
 __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ unsigned tmem_slot;
@@ -389,6 +392,7 @@ __device__ __forceinline__ void refresh_w(const OptNet &o, int t, long long i, f
 
 __global__ void adam_fused(const OptGroup G, int n_cta, float lr, float b1, float b2,
                            const float *__restrict__ corr, float wd) {
+    pdl_enter();
     const OptNet &o = G.net[blockIdx.y];
     const long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (fi >= o.total) return;
@@ -414,6 +418,7 @@ __global__ void adam_fused(const OptGroup G, int n_cta, float lr, float b1, floa
 }
 
 __global__ void polyak_fused(const OptGroup G, float tau) {
+    pdl_enter();
     const OptNet &o = G.net[blockIdx.y];
     const long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (fi >= o.total) return;
@@ -477,7 +482,7 @@ int launch_mlp_fwd_fused(const FGroup &g, void *stream) {
     cudaError_t e = cudaFuncSetAttribute(mlp_fwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kFwdSmem);
     if (e != cudaSuccess) return (int)e;
-    mlp_fwd_fused<<<dim3(g.B / 128, g.n_nets), kT, kFwdSmem, static_cast<cudaStream_t>(stream)>>>(g);
+    launch_pdl(mlp_fwd_fused, dim3(g.B / 128, g.n_nets), kT, kFwdSmem, static_cast<cudaStream_t>(stream), g);
     return (int)cudaGetLastError();
 }
 
@@ -485,7 +490,7 @@ int launch_mlp_bwd_fused(const FGroup &g, void *stream) {
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kBwdSmem);
     if (e != cudaSuccess) return (int)e;
-    mlp_bwd_fused<<<dim3(g.B / 128, g.n_nets), kT, kBwdSmem, static_cast<cudaStream_t>(stream)>>>(g);
+    launch_pdl(mlp_bwd_fused, dim3(g.B / 128, g.n_nets), kT, kBwdSmem, static_cast<cudaStream_t>(stream), g);
     return (int)cudaGetLastError();
 }
 
@@ -498,8 +503,8 @@ int launch_adam_fused(Mlp *const *nets, float *const *part, int n_nets, int n_ct
         G.net[k].part = part ? part[k] : nullptr;
         mx = mx > G.net[k].total ? mx : G.net[k].total;
     }
-    adam_fused<<<dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,
-                 static_cast<cudaStream_t>(stream)>>>(G, n_cta, lr, b1, b2, corr, wd);
+    launch_pdl(adam_fused, dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,
+                 static_cast<cudaStream_t>(stream), G, n_cta, lr, b1, b2, corr, wd);
     return (int)cudaGetLastError();
 }
 
@@ -514,8 +519,8 @@ int launch_polyak_fused(Mlp *const *tgt, Mlp *const *src, int n_nets, float tau,
         }
         mx = mx > G.net[k].total ? mx : G.net[k].total;
     }
-    polyak_fused<<<dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,
-                   static_cast<cudaStream_t>(stream)>>>(G, tau);
+    launch_pdl(polyak_fused, dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,
+                   static_cast<cudaStream_t>(stream), G, tau);
     return (int)cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "nav_internal.h"
+#include "pdl.cuh"
 #include "nav_policy.h"
 
 namespace flashnav {
@@ -53,6 +54,7 @@ enum { kCtrCritic = 0, kCtrActor = 1, kCtrHead = 2, kCtrSize = 3, kCtrSnapHead =
 // Starts critic (which 0) or actor (which 1) step t = ++ctr[which]; the
 // step's kernels use t - 1 as their update index.
 __global__ void k_count(unsigned long long *ctr, int which, float b1, float b2, float *corr) {
+    pdl_enter();
     const unsigned long long t = ++ctr[which];
     corr[2 * which] = 1.0f - powf(b1, (float)t);
     corr[2 * which + 1] = 1.0f - powf(b2, (float)t);
@@ -97,6 +99,7 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
 // n = cap - E safe slots start right after them.
 __global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__ ctr,
                          unsigned long long seed, long long cap) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const unsigned long long update = ctr[kCtrCritic] - 1, E = ctr[kCtrPending];
@@ -132,6 +135,7 @@ __global__ void k_gather(const int *__restrict__ idx, const bf16 *__restrict__ r
                          int od, int ld, int ldc, int ipap, const float *__restrict__ beta_dev,
                          const float *__restrict__ scale, bf16 *Xo, bf16 *Xn, bf16 *Xc,
                          float *Lraw, float *rew, float *term) {
+    pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * ldc) return;
     const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
@@ -162,6 +166,7 @@ __global__ void k_gather(const int *__restrict__ idx, const bf16 *__restrict__ r
 // Xc = [Xo[:, :od], a] for the actor's own action
 __global__ void k_concat(const bf16 *__restrict__ Xo, int ld, const float *__restrict__ a, int B,
                          int od, int ldc, bf16 *Xc) {
+    pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * ldc) return;
     const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
@@ -174,6 +179,7 @@ __global__ void k_concat(const bf16 *__restrict__ Xo, int ld, const float *__res
 // out[c][r] = in[r][c] for r < rows, c < cols (32 x 32 tiles through smem)
 __global__ void k_transpose(const bf16 *__restrict__ in, int ld_in, int rows, int cols, bf16 *out,
                             int ld_out) {
+    pdl_enter();
     __shared__ bf16 t[32][33];
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -194,6 +200,7 @@ __global__ void k_targets(const float *__restrict__ rew, const float *__restrict
                           int B, float gamma, float rs, unsigned long long seed,
                           const unsigned long long *__restrict__ ctr, float *y, float *ym,
                           float *znoise) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const unsigned long long update = ctr[kCtrCritic] - 1;
@@ -217,6 +224,7 @@ __global__ void k_targets(const float *__restrict__ rew, const float *__restrict
 __global__ void k_critic_grad(const float *__restrict__ q, const float *__restrict__ y,
                               const float *__restrict__ ym, const float *__restrict__ sbar, int B,
                               float delta, float *dq, float *acc /*[0] sum sigma, [1] loss*/) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     float ss = 0.0f, ll = 0.0f;
     if (b < B) {
@@ -246,6 +254,7 @@ __global__ void k_critic_grad(const float *__restrict__ q, const float *__restri
 }
 
 __global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
+    pdl_enter();
     *sbar = (1.0f - tau_b) * (*sbar) + tau_b * (acc[0] / (float)n);
     acc[2] = acc[1];
     acc[0] = 0.0f;
@@ -256,6 +265,7 @@ __global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
 __global__ void k_actor_loss(const float *__restrict__ logp, const float *__restrict__ q1,
                              const float *__restrict__ q2, const float *__restrict__ log_alpha,
                              int B, float *dlogp, float *dq1, float *dq2, float *acc) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     float ll = 0.0f, lp = 0.0f;
     if (b < B) {
@@ -285,6 +295,7 @@ __global__ void k_actor_head_bwd(const float *__restrict__ out4, const float *__
                                  const float *__restrict__ dX1, const float *__restrict__ dX2,
                                  int ldx, int od, const float *__restrict__ dlogp, int B,
                                  float *dout) {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
 #pragma unroll
@@ -362,6 +373,7 @@ __global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) 
 __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc, int B,
                         float target_entropy, float lr, float b1, float b2,
                         const float *__restrict__ corr) {
+    pdl_enter();
     const float c1 = corr[0], c2 = corr[1];
     const float g = -(acc[1] / (float)B + target_entropy);
     const float mi = b1 * (*am) + (1.0f - b1) * g;
@@ -409,6 +421,7 @@ __global__ void __launch_bounds__(256) k_c51_targets(
     const float *__restrict__ tl2, const float *__restrict__ logp_next,
     const float *__restrict__ log_alpha, int B, int n, float gamma, float rs, float v_min,
     float v_max, float *m) {
+    pdl_enter();
     __shared__ float bins[8][kFusedMaxWidth];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + w;
@@ -445,6 +458,7 @@ __global__ void __launch_bounds__(256) k_c51_targets(
 __global__ void __launch_bounds__(256) k_c51_critic_grad(const float *__restrict__ q,
                                                          const float *__restrict__ m, int B, int n,
                                                          float *dq, float *acc) {
+    pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + w;
     if (b >= B) return;
@@ -471,6 +485,7 @@ __global__ void __launch_bounds__(256) k_c51_actor_loss(
     const float *__restrict__ logp, const float *__restrict__ l1, const float *__restrict__ l2,
     const float *__restrict__ log_alpha, int B, int n, float v_min, float v_max, float *dlogp,
     float *dq1, float *dq2, float *acc) {
+    pdl_enter();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + w;
     if (b >= B) return;
@@ -501,6 +516,7 @@ __global__ void __launch_bounds__(256) k_c51_actor_loss(
 __global__ void k_beta_grad(const float *__restrict__ dX, int ldx, const float *__restrict__ Lraw,
                             int B, int ipap, const float *__restrict__ beta_dev,
                             const float *__restrict__ scale, float *acc) {
+    pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float g = 0.0f;
     if (i < (long long)B * ipap) {
@@ -517,6 +533,7 @@ __global__ void k_beta_grad(const float *__restrict__ dX, int ldx, const float *
 // every range l >= 0
 __global__ void k_beta_adam(float *s, float lr, float b1, float b2, const float *__restrict__ corr,
                             float beta_max) {
+    pdl_enter();
     const float c1 = corr[0], c2 = corr[1];
     const float g = s[3];
     s[-1] = g;
@@ -529,6 +546,7 @@ __global__ void k_beta_adam(float *s, float lr, float b1, float b2, const float 
 }
 
 __global__ void k_zero(float *p, int n) {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = 0.0f;
 }
@@ -972,76 +990,76 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     const dim3 tb(32, 8);
     Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
     const int none[2] = {-1, -1}, qslot[2] = {1, 2}, aslot[1] = {0};
-    k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
-    k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed, T->cap);
-    k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
+    launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
+    launch_pdl(k_sample, blocks(B), 256, 0, st, T->idx, B, T->ctr, c.seed, T->cap);
+    launch_pdl(k_gather, blocks((long long)B * T->ldc), 256, 0, st, 
         T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
         T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
-    k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
+    launch_pdl(k_transpose, dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st, 
         T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
     // targets
     float *oa[1] = {T->out_a};
     rc |= ffwd(T, act, 1, T->Xn, T->ld, oa, none, false, st);
     rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u, 1u,
                                 T->a_next, T->logp_next, T->eps_next, st);
-    k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
+    launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
                                                             T->ldc, T->Xnc);
     rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
     const bool c51 = c.algo == 1;
     if (c51)
-        k_c51_targets<<<blocks(B, 8), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1],
+        launch_pdl(k_c51_targets, blocks(B, 8), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
                                                  T->logp_next, T->scal + 0, B, T->qout, c.gamma,
                                                  c.reward_scale, c.v_min, c.v_max, T->tdist);
     else
-        k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
+        launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
                                              T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
                                              T->ctr, T->y, T->ym, T->znoise);
     // critics
     rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
     for (int i = 0; i < 2; ++i) {
         if (c51)
-            k_c51_critic_grad<<<blocks(B, 8), 256, 0, st>>>(T->qo[i], T->tdist, B, T->qout, T->dq[i],
+            launch_pdl(k_c51_critic_grad, blocks(B, 8), 256, 0, st, T->qo[i], T->tdist, B, T->qout, T->dq[i],
                                                          T->scal + 4);
         else
-            k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
+            launch_pdl(k_critic_grad, blocks(B), 256, 0, st, T->qo[i], T->y, T->ym, T->scal + 1, B,
                                                      c.huber_delta, T->dq[i], T->scal + 4);
     }
-    if (!c51) k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+    if (!c51) launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
     rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
     rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
                             c.weight_decay, st);
     if (actor_step) {
-        k_count<<<1, 1, 0, st>>>(T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
-        k_transpose<<<dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st>>>(T->Xo, T->ld, B,
+        launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
+        launch_pdl(k_transpose, dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st, T->Xo, T->ld, B,
                                                                           T->od, T->XoT, B);
         rc |= ffwd(T, act, 1, T->Xo, T->ld, oa, aslot, true, st);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
                                     T->a_new, T->logp_new, T->eps_new, st);
-        k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xo, T->ld, T->a_new, B, T->od,
+        launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xo, T->ld, T->a_new, B, T->od,
                                                                 T->ldc, T->Xa);
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
-        k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
+        launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
         if (c51)
-            k_c51_actor_loss<<<blocks(B, 8), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1],
+            launch_pdl(k_c51_actor_loss, blocks(B, 8), 256, 0, st, T->logp_new, T->qa[0], T->qa[1],
                                                         T->scal + 0, B, T->qout, c.v_min, c.v_max,
                                                         T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
         else
-            k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
+            launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
                                                     B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
         rc |= fbwd(T, qs, 2, T->dq, qslot, nullptr, nullptr, T->dX, T->ldc, st);
-        k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
+        launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                     T->ldc, T->od, T->dlogp, B, T->dout);
         float *douts[1] = {T->dout}, *pa[1] = {T->part_a}, *dxa[1] = {T->dXa};
         rc |= fbwd(T, act, 1, douts, aslot, T->XoT, pa, T->ipap > 0 ? dxa : nullptr, T->ld, st);
         rc |= launch_adam_fused(act, pa, 1, T->n_cta, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
                                 c.weight_decay, st);
         if (T->ipap > 0) {
-            k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
+            launch_pdl(k_beta_grad, blocks((long long)B * T->ipap), 256, 0, st, 
                 T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
-            k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
+            launch_pdl(k_beta_adam, 1, 1, 0, st, T->scal + 12, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
                                          c.ipap_beta_max);
         }
-        k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
+        launch_pdl(k_alpha, 1, 1, 0, st, T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
                                  c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
     }
     rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);

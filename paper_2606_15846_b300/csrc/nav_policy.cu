@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "nav_internal.h"
+#include "pdl.cuh"
 #include "nav_policy.h"
 
 namespace flashnav {
@@ -83,6 +84,7 @@ __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
                                const unsigned long long *__restrict__ ctr, int which,
                                unsigned long long sub, unsigned mul, unsigned add, float *act,
                                float *logp, float *eps_out) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     if (ctr) step = mul * (unsigned)(ctr[which] - sub) + add;
@@ -335,8 +337,8 @@ int launch_actor_head(const float *out4, int n, int mode, unsigned long long see
 int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long seed,
                           const unsigned long long *ctr, int which, unsigned mul, unsigned add,
                           float *act, float *logp, float *eps, void *stream) {
-    actor_head_fwd<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        out4, n, mode, seed, 0u, ctr, which, 1ull, mul, add, act, logp, eps);
+    launch_pdl(actor_head_fwd, (n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream), out4, n,
+               mode, seed, 0u, ctr, which, 1ull, mul, add, act, logp, eps);
     return (int)cudaGetLastError();
 }
 
