@@ -97,11 +97,8 @@ __global__ void k_replay_insert(const float *__restrict__ obs, const float *__re
 // size) snapshot taken before the insert began and skips the E slots it
 // writes: with s + E <= cap those lie beyond the s valid ones; otherwise the
 // n = cap - E safe slots start right after them.
-__global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__ ctr,
-                         unsigned long long seed, long long cap) {
-    pdl_enter();
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+__device__ __forceinline__ int sample_index(int b, const unsigned long long *__restrict__ ctr,
+                                            unsigned long long seed, long long cap) {
     const unsigned long long update = ctr[kCtrCritic] - 1, E = ctr[kCtrPending];
     const unsigned long long s = E ? ctr[kCtrSnapSize] : ctr[kCtrSize];
     const unsigned long long hd = E ? ctr[kCtrSnapHead] : ctr[kCtrHead];
@@ -110,7 +107,15 @@ __global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__
     const unsigned long long n = wrap ? C - E : s;
     const unsigned long long h = hmix(seed ^ (update * 0xD6E8FEB86659FD93ull) ^ ((unsigned long long)b << 1));
     const unsigned long long r = ((h >> 32) * n) >> 32;
-    idx[b] = (int)(wrap ? (hd + E + r) % C : r);
+    return (int)(wrap ? (hd + E + r) % C : r);
+}
+
+__global__ void k_sample(int *idx, int B, const unsigned long long *__restrict__ ctr,
+                         unsigned long long seed, long long cap) {
+    pdl_enter();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    idx[b] = sample_index(b, ctr, seed, cap);
 }
 
 // overlapped pipeline: snapshot (head, size) and the pending insert count
@@ -158,6 +163,55 @@ __global__ void k_gather(const int *__restrict__ idx, const bf16 *__restrict__ r
     else if (c < od + 2) v = __float2bfloat16_rn(r_act[s * 2 + (c - od)]);
     Xc[(long long)b * ldc + c] = v;
     if (c == 0) {
+        rew[b] = r_rew[s];
+        term[b] = r_term[s];
+    }
+}
+
+// One launch for the fused update: the replay index of each row (as
+// k_sample, also stored in idx), the rows of k_gather, and the layouts the update reads later:
+// Xc transposed (XcT [od + 2][B]), Xo's first od columns transposed (XoT
+// [od][B]), and the observation columns (with the zero padding) of Xnc =
+// [Xn, a'] and Xa = [Xo, a], whose action columns the actor head writes.
+__global__ void k_gather_all(const bf16 *__restrict__ r_obs, const bf16 *__restrict__ r_next,
+                             const float *__restrict__ r_act, const float *__restrict__ r_rew,
+                             const float *__restrict__ r_term, int B, int od, int ld, int ldc,
+                             int ipap, const float *__restrict__ beta_dev,
+                             const float *__restrict__ scale, const unsigned long long *ctr,
+                             unsigned long long seed, long long cap, int *idx, bf16 *Xo, bf16 *Xn,
+                             bf16 *Xc, bf16 *XcT, bf16 *XoT, bf16 *Xnc, bf16 *Xa, float *Lraw,
+                             float *rew, float *term) {
+    pdl_enter();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * ldc) return;
+    const int b = (int)(i / ldc), c = (int)(i - (long long)b * ldc);
+    const long long s = sample_index(b, ctr, seed, cap);
+    const float beta = ipap > 0 ? *beta_dev : 0.0f;
+    const bf16 zero = __float2bfloat16_rn(0.0f);
+    bf16 xo = zero, xn = zero;
+    if (c < ld) {
+        xo = r_obs[s * ld + c];
+        xn = r_next[s * ld + c];
+        if (c < ipap) {
+            Lraw[(long long)b * ipap + c] = __bfloat162float(xo);
+            xo = ipap_in(xo, beta, scale, c);
+            xn = ipap_in(xn, beta, scale, c);
+        }
+        Xo[(long long)b * ld + c] = xo;
+        Xn[(long long)b * ld + c] = xn;
+    }
+    bf16 v = zero;
+    if (c < od) v = xo;
+    else if (c < od + 2) v = __float2bfloat16_rn(r_act[s * 2 + (c - od)]);
+    Xc[(long long)b * ldc + c] = v;
+    if (c < od + 2) XcT[(long long)c * B + b] = v;
+    if (c < od) XoT[(long long)c * B + b] = xo;
+    if (c < od || c >= od + 2) {
+        Xnc[(long long)b * ldc + c] = c < od ? xn : zero;
+        Xa[(long long)b * ldc + c] = c < od ? xo : zero;
+    }
+    if (c == 0) {
+        idx[b] = (int)s;
         rew[b] = r_rew[s];
         term[b] = r_term[s];
     }
@@ -221,10 +275,10 @@ __global__ void k_targets(const float *__restrict__ rew, const float *__restrict
 }
 
 // dL/dq for one critic; accumulates the batch sum of sigma and the loss
-__global__ void k_critic_grad(const float *__restrict__ q, const float *__restrict__ y,
-                              const float *__restrict__ ym, const float *__restrict__ sbar, int B,
-                              float delta, float *dq, float *acc /*[0] sum sigma, [1] loss*/) {
-    pdl_enter();
+__device__ __forceinline__ void critic_grad(const float *__restrict__ q, const float *__restrict__ y,
+                                            const float *__restrict__ ym,
+                                            const float *__restrict__ sbar, int B, float delta,
+                                            float *dq, float *acc) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     float ss = 0.0f, ll = 0.0f;
     if (b < B) {
@@ -251,6 +305,23 @@ __global__ void k_critic_grad(const float *__restrict__ q, const float *__restri
         atomicAdd(&acc[0], ss);
         atomicAdd(&acc[1], ll);
     }
+}
+
+__global__ void k_critic_grad(const float *__restrict__ q, const float *__restrict__ y,
+                              const float *__restrict__ ym, const float *__restrict__ sbar, int B,
+                              float delta, float *dq, float *acc /*[0] sum sigma, [1] loss*/) {
+    pdl_enter();
+    critic_grad(q, y, ym, sbar, B, delta, dq, acc);
+}
+
+// both critics in one launch (blockIdx.y selects the critic)
+__global__ void k_critic_grad2(const float *__restrict__ q0, const float *__restrict__ q1,
+                               const float *__restrict__ y, const float *__restrict__ ym,
+                               const float *__restrict__ sbar, int B, float delta, float *dq0,
+                               float *dq1, float *acc) {
+    pdl_enter();
+    const bool one = blockIdx.y == 1;
+    critic_grad(one ? q1 : q0, y, ym, sbar, B, delta, one ? dq1 : dq0, acc);
 }
 
 __global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
@@ -455,10 +526,9 @@ __global__ void __launch_bounds__(256) k_c51_targets(
 }
 
 // Cross-entropy to m: dL/dlogits = (softmax - m) / B; acc[1] += loss
-__global__ void __launch_bounds__(256) k_c51_critic_grad(const float *__restrict__ q,
-                                                         const float *__restrict__ m, int B, int n,
-                                                         float *dq, float *acc) {
-    pdl_enter();
+__device__ __forceinline__ void c51_critic_grad(const float *__restrict__ q,
+                                                const float *__restrict__ m, int B, int n, float *dq,
+                                                float *acc) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + w;
     if (b >= B) return;
@@ -477,6 +547,17 @@ __global__ void __launch_bounds__(256) k_c51_critic_grad(const float *__restrict
     }
     ll = warp_sum(ll);
     if (lane == 0) atomicAdd(&acc[1], ll);
+}
+
+// C51 critic gradients of both critics in one launch (blockIdx.y selects
+// the critic)
+__global__ void __launch_bounds__(256) k_c51_critic_grad2(const float *__restrict__ q0,
+                                                          const float *__restrict__ q1,
+                                                          const float *__restrict__ m, int B, int n,
+                                                          float *dq0, float *dq1, float *acc) {
+    pdl_enter();
+    const bool one = blockIdx.y == 1;
+    c51_critic_grad(one ? q1 : q0, m, B, n, one ? dq1 : dq0, acc);
 }
 
 // Actor loss mean(alpha logp - min_j E[Q_j]): dL/dlogp, and dL/dlogits of the
@@ -982,85 +1063,76 @@ int fbwd(nav_trainer *T, Mlp *const *nets, int n, float *const *dout, const int 
 }
 
 // One critic update (and the actor update that falls on it) on the fused
-// passes: the same arithmetic as the per-layer path, ~25 launches.
+// passes: the same arithmetic as the per-layer path, ~18 launches, each
+// launched with programmatic dependent launch.
 int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
     int rc = 0;
-    const dim3 tb(32, 8);
     Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
     const int none[2] = {-1, -1}, qslot[2] = {1, 2}, aslot[1] = {0};
+    const bool c51 = c.algo == 1;
     launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
-    launch_pdl(k_sample, blocks(B), 256, 0, st, T->idx, B, T->ctr, c.seed, T->cap);
-    launch_pdl(k_gather, blocks((long long)B * T->ldc), 256, 0, st, 
-        T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
-        T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
-    launch_pdl(k_transpose, dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st, 
-        T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
-    // targets
+    launch_pdl(k_gather_all, blocks((long long)B * T->ldc), 256, 0, st, T->r_obs, T->r_next,
+               T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc, T->ipap, T->scal + 12,
+               T->scale, T->ctr, c.seed, T->cap, T->idx, T->Xo, T->Xn, T->Xc, T->XcT, T->XoT,
+               T->Xnc, T->Xa, T->Lraw, T->rew, T->term);
+    // targets: a' from the actor (written into Xnc's action columns too)
     float *oa[1] = {T->out_a};
     rc |= ffwd(T, act, 1, T->Xn, T->ld, oa, none, false, st);
     rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u, 1u,
-                                T->a_next, T->logp_next, T->eps_next, st);
-    launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
-                                                            T->ldc, T->Xnc);
+                                T->a_next, T->logp_next, T->eps_next, st, T->Xnc, T->ldc, T->od);
     rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
-    const bool c51 = c.algo == 1;
     if (c51)
         launch_pdl(k_c51_targets, blocks(B, 8), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
-                                                 T->logp_next, T->scal + 0, B, T->qout, c.gamma,
-                                                 c.reward_scale, c.v_min, c.v_max, T->tdist);
+                   T->logp_next, T->scal + 0, B, T->qout, c.gamma, c.reward_scale, c.v_min,
+                   c.v_max, T->tdist);
     else
-        launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
-                                             T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
-                                             T->ctr, T->y, T->ym, T->znoise);
+        launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
+                   T->logp_next, T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr, T->y,
+                   T->ym, T->znoise);
     // critics
     rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
-    for (int i = 0; i < 2; ++i) {
-        if (c51)
-            launch_pdl(k_c51_critic_grad, blocks(B, 8), 256, 0, st, T->qo[i], T->tdist, B, T->qout, T->dq[i],
-                                                         T->scal + 4);
-        else
-            launch_pdl(k_critic_grad, blocks(B), 256, 0, st, T->qo[i], T->y, T->ym, T->scal + 1, B,
-                                                     c.huber_delta, T->dq[i], T->scal + 4);
-    }
+    if (c51)
+        launch_pdl(k_c51_critic_grad2, dim3(blocks(B, 8), 2), 256, 0, st, T->qo[0], T->qo[1],
+                   T->tdist, B, T->qout, T->dq[0], T->dq[1], T->scal + 4);
+    else
+        launch_pdl(k_critic_grad2, dim3(blocks(B), 2), 256, 0, st, T->qo[0], T->qo[1], T->y, T->ym,
+                   T->scal + 1, B, c.huber_delta, T->dq[0], T->dq[1], T->scal + 4);
     if (!c51) launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
     rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
     rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
                             c.weight_decay, st);
     if (actor_step) {
+        // the actor's own action a, written into Xa's action columns too
         launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
-        launch_pdl(k_transpose, dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st, T->Xo, T->ld, B,
-                                                                          T->od, T->XoT, B);
         rc |= ffwd(T, act, 1, T->Xo, T->ld, oa, aslot, true, st);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
-                                    T->a_new, T->logp_new, T->eps_new, st);
-        launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xo, T->ld, T->a_new, B, T->od,
-                                                                T->ldc, T->Xa);
+                                    T->a_new, T->logp_new, T->eps_new, st, T->Xa, T->ldc, T->od);
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
         launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
         if (c51)
             launch_pdl(k_c51_actor_loss, blocks(B, 8), 256, 0, st, T->logp_new, T->qa[0], T->qa[1],
-                                                        T->scal + 0, B, T->qout, c.v_min, c.v_max,
-                                                        T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+                       T->scal + 0, B, T->qout, c.v_min, c.v_max, T->dlogp, T->dq[0], T->dq[1],
+                       T->scal + 8);
         else
-            launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
-                                                    B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
+            launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1],
+                       T->scal + 0, B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
         rc |= fbwd(T, qs, 2, T->dq, qslot, nullptr, nullptr, T->dX, T->ldc, st);
-        launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0], T->dX[1],
-                                                    T->ldc, T->od, T->dlogp, B, T->dout);
+        launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0],
+                   T->dX[1], T->ldc, T->od, T->dlogp, B, T->dout);
         float *douts[1] = {T->dout}, *pa[1] = {T->part_a}, *dxa[1] = {T->dXa};
         rc |= fbwd(T, act, 1, douts, aslot, T->XoT, pa, T->ipap > 0 ? dxa : nullptr, T->ld, st);
         rc |= launch_adam_fused(act, pa, 1, T->n_cta, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
                                 c.weight_decay, st);
         if (T->ipap > 0) {
-            launch_pdl(k_beta_grad, blocks((long long)B * T->ipap), 256, 0, st, 
-                T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
-            launch_pdl(k_beta_adam, 1, 1, 0, st, T->scal + 12, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
-                                         c.ipap_beta_max);
+            launch_pdl(k_beta_grad, blocks((long long)B * T->ipap), 256, 0, st, T->dXa, T->ld,
+                       T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
+            launch_pdl(k_beta_adam, 1, 1, 0, st, T->scal + 12, c.lr_actor, c.beta1, c.beta2,
+                       T->corr + 2, c.ipap_beta_max);
         }
         launch_pdl(k_alpha, 1, 1, 0, st, T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
-                                 c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
+                   c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
     }
     rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);
     rc |= (int)cudaGetLastError();

@@ -83,7 +83,7 @@ __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
                                unsigned long long seed, unsigned step,
                                const unsigned long long *__restrict__ ctr, int which,
                                unsigned long long sub, unsigned mul, unsigned add, float *act,
-                               float *logp, float *eps_out) {
+                               float *logp, float *eps_out, __nv_bfloat16 *xc, int ldc, int col0) {
     pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -106,6 +106,7 @@ __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
         lp += -0.5f * e * e - ls - 0.91893853320467274f - logf(1.0f - a * a + 1e-6f);
         act[(size_t)r * 2 + d] = a;
         if (eps_out) eps_out[(size_t)r * 2 + d] = e;
+        if (xc) xc[(size_t)r * ldc + col0 + d] = __float2bfloat16_rn(a);
     }
     if (logp) logp[r] = lp;
 }
@@ -330,15 +331,17 @@ int launch_obs_to_fp32(const float *obs, int n, int dim, long long stride, const
 int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
                       float *act, float *logp, float *eps, void *stream) {
     actor_head_fwd<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        out4, n, mode, seed, step, nullptr, 0, 0, 0, 0, act, logp, eps);
+        out4, n, mode, seed, step, nullptr, 0, 0, 0, 0, act, logp, eps, nullptr, 0, 0);
     return (int)cudaGetLastError();
 }
 
 int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long seed,
                           const unsigned long long *ctr, int which, unsigned mul, unsigned add,
-                          float *act, float *logp, float *eps, void *stream) {
+                          float *act, float *logp, float *eps, void *stream, void *xc, int ldc,
+                          int col0) {
     launch_pdl(actor_head_fwd, (n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream), out4, n,
-               mode, seed, 0u, ctr, which, 1ull, mul, add, act, logp, eps);
+               mode, seed, 0u, ctr, which, 1ull, mul, add, act, logp, eps,
+               static_cast<__nv_bfloat16 *>(xc), ldc, col0);
     return (int)cudaGetLastError();
 }
 

@@ -50,10 +50,13 @@ int launch_obs_to_fp32(const float *obs, int n, int dim, long long stride, const
                        int ipap, const float *beta_dev, float *out, void *stream);
 int launch_actor_head(const float *out4, int n, int mode, unsigned long long seed, unsigned step,
                       float *act, float *logp, float *eps, void *stream);
-// The same with the noise step mul * (ctr[which] - 1) + add read on the device.
+// The same with the noise step mul * (ctr[which] - 1) + add read on the device;
+// with xc set, the actions are also stored as BF16 in columns col0, col0 + 1
+// of the rows of xc (leading dimension ldc).
 int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long seed,
                           const unsigned long long *ctr, int which, unsigned mul, unsigned add,
-                          float *act, float *logp, float *eps, void *stream);
+                          float *act, float *logp, float *eps, void *stream, void *xc = nullptr,
+                          int ldc = 0, int col0 = 0);
 
 // ---------------------------------------------------------------------------
 // Fused passes for small networks (every layer's in and out <= 128, batch a
