@@ -696,18 +696,19 @@ def run_gpu(args):
                          # capture in profiles/step_kernel_plain4096.md
                          # (any shared-memory cap that stages the 256x256
                          # distance maps gives the same kernel)
-                         "traffic": 1.4697e6 if (tuple(launch[i] for i in (0, 1, 3, 4, 5)) ==
-                                                 (8, 512, 40, 1, 2) and launch[2] >= 69 * 1024)
+                         "traffic": 1.468e6 if (tuple(launch[i] for i in (0, 1, 3, 5)) ==
+                                                (8, 512, 40, 2) and launch[4] in (1, 3) and
+                                                launch[2] >= 69 * 1024)
                          else None,
                          "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
                                         f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
                          "kernel": "step kernel (fused) or ray_kernel (split), per launch.split",
                          # the instruction-issue bound that explains the gap:
                          # 4 warp instructions/clk/SM over the ncu-measured
-                         # 0.716 warp instructions per visit of the step kernel
-                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.716 / 1e9,
+                         # 0.710 warp instructions per visit of the step kernel
+                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.710 / 1e9,
                          "frac_of_issue_bound": achieved / (SM_COUNT * 4 * sm_mhz * 1e6 /
-                                                           0.716 / 1e9)},
+                                                           0.710 / 1e9)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": E * 2 * 4,
                     "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,
