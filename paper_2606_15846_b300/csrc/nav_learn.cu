@@ -390,6 +390,7 @@ __global__ void k_actor_head_bwd(const float *__restrict__ out4, const float *__
 // FP32 [B][n] -> BF16 [B][ldp] (zero pad) and its transpose [n][B]
 __global__ void k_grad_to_bf16(const float *__restrict__ g, int B, int n, int ldp, bf16 *g16,
                                bf16 *gT16) {
+    pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * ldp) return;
     const int b = (int)(i / ldp), c = (int)(i - (long long)b * ldp);
@@ -403,6 +404,7 @@ __global__ void k_grad_to_bf16(const float *__restrict__ g, int B, int n, int ld
 // (32 x 32 tiles); h is BF16 [B][ldh]
 __global__ void k_leaky_bwd(float *dH, const bf16 *__restrict__ h, int B, int H, int ldh,
                             bf16 *dZ16, bf16 *dZT16) {
+    pdl_enter();
     __shared__ bf16 t[32][33];
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -425,6 +427,7 @@ __global__ void k_leaky_bwd(float *dH, const bf16 *__restrict__ h, int B, int H,
 
 // column sums of FP32 [B][n] (bias gradients)
 __global__ void k_colsum(const float *__restrict__ g, int B, int n, float *out) {
+    pdl_enter();
     __shared__ float part[8][33];
     const int c = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
@@ -763,7 +766,7 @@ int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 
     const int last = net.n_layers - 1;
     const int n_out = net.layer[last].out;
     int rc = 0;
-    k_grad_to_bf16<<<blocks((long long)B * 8), 256, 0, st>>>(dout, B, n_out, 8, T->g16, T->gT16);
+    launch_pdl(k_grad_to_bf16, blocks((long long)B * 8), 256, 0, st, dout, B, n_out, 8, T->g16, T->gT16);
     const dim3 tb(32, 8), tg((H + 31) / 32, (B + 31) / 32);
     for (int l = last; l >= 0; --l) {
         Layer &L = net.layer[l];
@@ -776,12 +779,12 @@ int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 
         if (wgrad) {
             rc |= launch_gemm_bf16_splitk(GT, B, inT, B, L.out, L.in, B, L.gW, L.in, T->status,
                                           st);
-            k_colsum<<<blocks(L.out, 32), dim3(32, 8), 0, st>>>(G32, B, L.out, L.gb);
+            launch_pdl(k_colsum, blocks(L.out, 32), dim3(32, 8), 0, st, G32, B, L.out, L.gb);
         }
         if (l > 0) {
             rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, H, L.out, nullptr, 0, T->dH, H,
                                    nullptr, 0, nullptr, 0, T->status, st);
-            k_leaky_bwd<<<tg, tb, 0, st>>>(T->dH, T->h16[s][l - 1], B, H, Hp, T->dZ16, T->dZT16);
+            launch_pdl(k_leaky_bwd, tg, tb, 0, st, T->dH, T->h16[s][l - 1], B, H, Hp, T->dZ16, T->dZT16);
         } else if (dX) {
             rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, L.in, L.out, nullptr, 0, dX, ldx,
                                    nullptr, 0, nullptr, 0, T->status, st);
@@ -1156,30 +1159,30 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
     }
     for (int u = 0; u < n_updates; ++u) {
         // ---- critic update (index ctr[critic] - 1 after k_count)
-        k_count<<<1, 1, 0, st>>>(T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
-        k_sample<<<blocks(B), 256, 0, st>>>(T->idx, B, T->ctr, c.seed, T->cap);
-        k_gather<<<blocks((long long)B * T->ldc), 256, 0, st>>>(
+        launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
+        launch_pdl(k_sample, blocks(B), 256, 0, st, T->idx, B, T->ctr, c.seed, T->cap);
+        launch_pdl(k_gather, blocks((long long)B * T->ldc), 256, 0, st, 
             T->idx, T->r_obs, T->r_next, T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc,
             T->ipap, T->scal + 12, T->scale, T->Xo, T->Xn, T->Xc, T->Lraw, T->rew, T->term);
         const dim3 tb(32, 8);
-        k_transpose<<<dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
+        launch_pdl(k_transpose, dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st, 
             T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
         // next action from the current actor (noise step 2 index + 1)
         rc |= fwd(T, T->actor, T->Xn, 3, false, T->out_a, st);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u,
                                     1u, T->a_next, T->logp_next, T->eps_next, st);
-        k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xn, T->ld, T->a_next, B, T->od,
+        launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
                                                                 T->ldc, T->Xnc);
         for (int i = 0; i < 2; ++i) rc |= fwd(T, T->qt[i], T->Xnc, 3, false, T->tq[i], st);
-        k_targets<<<blocks(B), 256, 0, st>>>(T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
+        launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
                                              T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
                                              T->ctr, T->y, T->ym, T->znoise);
         for (int i = 0; i < 2; ++i) {
             rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], st);
-            k_critic_grad<<<blocks(B), 256, 0, st>>>(T->qo[i], T->y, T->ym, T->scal + 1, B,
+            launch_pdl(k_critic_grad, blocks(B), 256, 0, st, T->qo[i], T->y, T->ym, T->scal + 1, B,
                                                      c.huber_delta, T->dq[i], T->scal + 4);
         }
-        k_sbar_update<<<1, 1, 0, st>>>(T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+        launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
         for (int i = 0; i < 2; ++i)
             rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, st);
         {
@@ -1190,22 +1193,22 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
         ++n_critic;
         // ---- actor and temperature update every policy_freq critic updates
         if (n_critic % (unsigned long long)c.policy_freq == 0) {
-            k_count<<<1, 1, 0, st>>>(T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
-            k_transpose<<<dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st>>>(T->Xo, T->ld, B,
+            launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
+            launch_pdl(k_transpose, dim3((T->od + 31) / 32, (B + 31) / 32), tb, 0, st, T->Xo, T->ld, B,
                                                                               T->od, T->XoT, B);
             rc |= fwd(T, T->actor, T->Xo, 0, true, T->out_a, st);
             rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u,
                                         0u, T->a_new, T->logp_new, T->eps_new, st);
-            k_concat<<<blocks((long long)B * T->ldc), 256, 0, st>>>(T->Xo, T->ld, T->a_new, B,
+            launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xo, T->ld, T->a_new, B,
                                                                     T->od, T->ldc, T->Xa);
             for (int i = 0; i < 2; ++i) rc |= fwd(T, T->q[i], T->Xa, 1 + i, false, T->qa[i], st);
-            k_zero<<<1, 32, 0, st>>>(T->scal + 8, 2);
-            k_actor_loss<<<blocks(B), 256, 0, st>>>(T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
+            launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
+            launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
                                                     B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
             for (int i = 0; i < 2; ++i)
                 rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, nullptr, false, T->dX[i], T->ldc,
                                    st);
-            k_actor_head_bwd<<<blocks(B), 256, 0, st>>>(T->out_a, T->eps_new, T->dX[0], T->dX[1],
+            launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
             rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
                                T->ipap > 0 ? T->dXa : nullptr, T->ld, st);
@@ -1216,12 +1219,12 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
             }
             if (T->ipap > 0) {
                 // Eq. 2's beta trained with the actor (same Adam settings)
-                k_beta_grad<<<blocks((long long)B * T->ipap), 256, 0, st>>>(
+                launch_pdl(k_beta_grad, blocks((long long)B * T->ipap), 256, 0, st, 
                     T->dXa, T->ld, T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
-                k_beta_adam<<<1, 1, 0, st>>>(T->scal + 12, c.lr_actor, c.beta1, c.beta2,
+                launch_pdl(k_beta_adam, 1, 1, 0, st, T->scal + 12, c.lr_actor, c.beta1, c.beta2,
                                              T->corr + 2, c.ipap_beta_max);
             }
-            k_alpha<<<1, 1, 0, st>>>(T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
+            launch_pdl(k_alpha, 1, 1, 0, st, T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
                                      c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
         }
         {

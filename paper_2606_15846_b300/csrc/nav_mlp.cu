@@ -30,6 +30,7 @@
 #include <mutex>
 
 #include "nav_internal.h"
+#include "pdl.cuh"
 #include "tc_util.cuh"
 
 namespace flashnav {
@@ -267,6 +268,7 @@ __device__ __forceinline__ bool ws_tile(const WsArgs &g, int k, int &mt, int &nt
 __global__ void __launch_bounds__(kWsThreads, 2)
     gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const WsArgs g) {
+    pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[kWsMaxStages], empty[kWsMaxStages];
     __shared__ __align__(8) unsigned long long accf[2], acce[2], fin;
@@ -634,7 +636,7 @@ bool launch_ws(const void *A, int lda, const void *B, int ldb, int M, int N, int
     g.C16T = static_cast<__nv_bfloat16 *>(C16T); g.ldct = ldct;
     g.status = status;
     const int grid = std::min(g.n_tiles, 2 * sm_count());
-    gemm_ws<<<grid, kWsThreads, smem, s>>>(ma, mb, g);
+    launch_pdl(gemm_ws, grid, kWsThreads, smem, s, ma, mb, g);
     rc = (int)cudaGetLastError();
     return true;
 }
