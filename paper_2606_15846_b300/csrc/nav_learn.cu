@@ -703,7 +703,7 @@ struct nav_trainer {
     bf16 *h16[4][kMaxLayers - 1] = {}, *ht16[4][kMaxLayers - 1] = {};
     float *Lraw = nullptr, *dXa = nullptr; // raw Eq. 2 ranges of obs; actor input gradient
     unsigned *mask[4][kMaxLayers - 1] = {}; // fused passes: LeakyReLU' sign bits per slot
-    float *out_a = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
+    float *out_a = nullptr, *out_an = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
     float *a_next = nullptr, *logp_next = nullptr, *a_new = nullptr, *logp_new = nullptr,
           *eps_new = nullptr, *eps_next = nullptr;
     float *y = nullptr, *ym = nullptr, *znoise = nullptr, *dq[2] = {}, *dlogp = nullptr,
@@ -928,6 +928,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->Lraw, B * std::max(T->ipap, 1));
     TA(T->dXa, B * T->ld);
     TA(T->out_a, B * 4);
+    TA(T->out_an, B * 4);
     for (int i = 0; i < 2; ++i) {
         TA(T->qo[i], B * T->qout);
         TA(T->tq[i], B * T->qout);
@@ -1009,10 +1010,11 @@ int nav_train_insert(nav_trainer *T, const float *obs_dev, const float *act_dev,
 
 namespace {
 
-// forward of up to two networks through the fused pass; slot[k] >= 0 saves
-// the hidden activations (and, with save_t, their transposes) there
-int ffwd(nav_trainer *T, Mlp *const *nets, int n, const bf16 *X, int ldx, float *const *out,
-         const int *slot, bool save_t, cudaStream_t st) {
+// forward of up to four networks through one fused launch, network k on
+// input X[k] (leading dimension ldx[k]); slot[k] >= 0 saves its hidden
+// activations' LeakyReLU' bits (and, with save_t[k], their transposes) there
+int ffwd_n(nav_trainer *T, Mlp *const *nets, int n, const bf16 *const *X, const int *ldx,
+           float *const *out, const int *slot, const bool *save_t, cudaStream_t st) {
     FGroup g{};
     g.n_nets = n;
     g.B = T->B;
@@ -1020,16 +1022,25 @@ int ffwd(nav_trainer *T, Mlp *const *nets, int n, const bf16 *X, int ldx, float 
     for (int k = 0; k < n; ++k) {
         FNet &f = g.net[k];
         fused_layers(*nets[k], f);
-        f.X = X;
-        f.ldx = ldx;
+        f.X = X[k];
+        f.ldx = ldx[k];
         f.out32 = out[k];
         f.ldh = T->Hp;
         for (int l = 0; l + 1 < nets[k]->n_layers; ++l) {
             f.M[l] = slot[k] >= 0 ? T->mask[slot[k]][l] : nullptr;
-            f.HT16[l] = (slot[k] >= 0 && save_t) ? T->ht16[slot[k]][l] : nullptr;
+            f.HT16[l] = (slot[k] >= 0 && save_t[k]) ? T->ht16[slot[k]][l] : nullptr;
         }
     }
     return launch_mlp_fwd_fused(g, st);
+}
+
+// up to two networks on one input
+int ffwd(nav_trainer *T, Mlp *const *nets, int n, const bf16 *X, int ldx, float *const *out,
+         const int *slot, bool save_t, cudaStream_t st) {
+    const bf16 *Xs[2] = {X, X};
+    const int lds[2] = {ldx, ldx};
+    const bool sv[2] = {save_t, save_t};
+    return ffwd_n(T, nets, n, Xs, lds, out, slot, sv, st);
 }
 
 // backward of up to two networks: part[k] receives the per-CTA partial
@@ -1066,26 +1077,45 @@ int fbwd(nav_trainer *T, Mlp *const *nets, int n, float *const *dout, const int 
 }
 
 // One critic update (and the actor update that falls on it) on the fused
-// passes: the same arithmetic as the per-layer path, ~18 launches, each
+// passes: the same arithmetic as the per-layer path, ~16 launches, each
 // launched with programmatic dependent launch.
 int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
     int rc = 0;
     Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
-    const int none[2] = {-1, -1}, qslot[2] = {1, 2}, aslot[1] = {0};
+    const int qslot[2] = {1, 2}, aslot[1] = {0};
     const bool c51 = c.algo == 1;
     launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
     launch_pdl(k_gather_all, blocks((long long)B * T->ldc), 256, 0, st, T->r_obs, T->r_next,
                T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc, T->ipap, T->scal + 12,
                T->scale, T->ctr, c.seed, T->cap, T->idx, T->Xo, T->Xn, T->Xc, T->XcT, T->XoT,
                T->Xnc, T->Xa, T->Lraw, T->rew, T->term);
-    // targets: a' from the actor (written into Xnc's action columns too)
-    float *oa[1] = {T->out_a};
-    rc |= ffwd(T, act, 1, T->Xn, T->ld, oa, none, false, st);
-    rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u, 1u,
+    // the actor on the next observations (targets) and, in an actor step, on
+    // the observations (activations saved for its backward) in one launch:
+    // the actor's weights do not change before its own update
+    {
+        Mlp *aa[2] = {&T->actor, &T->actor};
+        const bf16 *Xs[2] = {T->Xn, T->Xo};
+        const int lds[2] = {T->ld, T->ld};
+        float *outs[2] = {T->out_an, T->out_a};
+        const int sl[2] = {-1, 0};
+        const bool sv[2] = {false, true};
+        rc |= ffwd_n(T, aa, actor_step ? 2 : 1, Xs, lds, outs, sl, sv, st);
+    }
+    // a' (written into Xnc's action columns too)
+    rc |= launch_actor_head_ctr(T->out_an, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u, 1u,
                                 T->a_next, T->logp_next, T->eps_next, st, T->Xnc, T->ldc, T->od);
-    rc |= ffwd(T, qts, 2, T->Xnc, T->ldc, T->tq, none, false, st);
+    // the target critics on [s', a'] and the critics on [s, a] in one launch
+    {
+        Mlp *four[4] = {&T->qt[0], &T->qt[1], &T->q[0], &T->q[1]};
+        const bf16 *Xs[4] = {T->Xnc, T->Xnc, T->Xc, T->Xc};
+        const int lds[4] = {T->ldc, T->ldc, T->ldc, T->ldc};
+        float *outs[4] = {T->tq[0], T->tq[1], T->qo[0], T->qo[1]};
+        const int sl[4] = {-1, -1, 1, 2};
+        const bool sv[4] = {false, false, true, true};
+        rc |= ffwd_n(T, four, 4, Xs, lds, outs, sl, sv, st);
+    }
     if (c51)
         launch_pdl(k_c51_targets, blocks(B, 8), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
                    T->logp_next, T->scal + 0, B, T->qout, c.gamma, c.reward_scale, c.v_min,
@@ -1095,7 +1125,6 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
                    T->logp_next, T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr, T->y,
                    T->ym, T->znoise);
     // critics
-    rc |= ffwd(T, qs, 2, T->Xc, T->ldc, T->qo, qslot, true, st);
     if (c51)
         launch_pdl(k_c51_critic_grad2, dim3(blocks(B, 8), 2), 256, 0, st, T->qo[0], T->qo[1],
                    T->tdist, B, T->qout, T->dq[0], T->dq[1], T->scal + 4);
@@ -1109,7 +1138,6 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     if (actor_step) {
         // the actor's own action a, written into Xa's action columns too
         launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
-        rc |= ffwd(T, act, 1, T->Xo, T->ld, oa, aslot, true, st);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
                                     T->a_new, T->logp_new, T->eps_new, st, T->Xa, T->ldc, T->od);
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);

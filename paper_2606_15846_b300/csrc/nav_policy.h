@@ -62,7 +62,8 @@ int launch_actor_head_ctr(const float *out4, int n, int mode, unsigned long long
 // Fused passes for small networks (every layer's in and out <= 128, batch a
 // multiple of 128): one CTA per 128 batch rows runs every
 // layer of a network with its operands in shared memory and accumulators in
-// TMEM; grid.y selects one of up to two networks (the twin critics).
+// TMEM; grid.y selects one of up to four networks (e.g. the twin critics and
+// their targets, each on its own input).
 // ---------------------------------------------------------------------------
 constexpr int kFusedMaxWidth = 128;
 
@@ -98,8 +99,9 @@ struct FNet {
     int lddx;
 };
 
+constexpr int kFusedMaxNets = 4; // networks one fused launch walks (grid.y)
 struct FGroup {
-    FNet net[2];
+    FNet net[kFusedMaxNets];
     int n_nets, B;
     int *status;
 };
