@@ -297,6 +297,38 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
                       "8 moving discs, graph of 20 steps, L2 flushed between replays"}
 
 
+def gather_rates(reps: int = 10):
+    """Random single-byte gather rates of this GPU (nav_gather_probe), in
+    G reads/s: the memory ceilings of the beam traversal, whose lanes read
+    unrelated cells, with the map in shared memory (a 64 KiB table per CTA,
+    three CTAs per SM), in L2 (a 32 MiB table) or in HBM (a 2 GiB table)."""
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    s = torch.cuda.Stream()
+    out = {}
+    for name, where, nbytes, blocks, iters in (("shared_64KiB", 0, 1 << 16, 3 * sms, 512),
+                                               ("l2_32MiB", 1, 1 << 25, 8 * sms, 64),
+                                               ("hbm_2GiB", 1, 1 << 31, 8 * sms, 16)):
+        with torch.cuda.stream(s):
+            table = (torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda")
+                     if where else None)
+            sums = torch.empty(blocks, dtype=torch.int32, device="cuda")
+            for _ in range(3):
+                flashnav.gather_probe(where, table, nbytes, blocks, iters, sums, s.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                flashnav.gather_probe(where, table, nbytes, blocks, iters, sums, s.cuda_stream)
+            e1.record(s)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = blocks * 256 * iters * 8 / (ms / 1e3) / 1e9
+        del table
+    out["unit"] = "G random byte reads/s"
+    return out
+
+
 def paper_sensing(steps: int = 200, launch: str = ""):
     """The paper's sensing (Sec. 2.2.2, Eq. 6, Table 7) on its TurtleBot2
     setting: one shared 10 x 10 m map, 1080 beams over 270 deg to 20 m,
@@ -715,11 +747,22 @@ def run_gpu(args):
                     "steps": e2e_steps},
             "clocks": clk.summary(),
         }
+        if world == 1:
+            # measured random-gather ceilings beside the nominal one (the
+            # 256x256 distance maps are staged in shared memory)
+            g = gather_rates()
+            line["roofline"]["measured_random_gather"] = g
+            line["roofline"]["frac_of_measured_shared_gather"] = achieved / g["shared_64KiB"]
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         if world == 1 and args.extras:
             line["policy_rollout"] = policy_rollout()
-            line["uneven_batch"] = uneven_batch()
+            line["uneven_batch"] = ub = uneven_batch()
+            # maps up to the staged size are read from shared memory, the
+            # larger ones through L1/L2
+            gv = ub["cell_visits_per_s"] / 1e9
+            ub["frac_of_measured_gather"] = {"shared": gv / g["shared_64KiB"],
+                                             "l2": gv / g["l2_32MiB"]}
             line["paper_sensing"] = paper_sensing()
             line["learner_update"] = learner_update()
             if args.train_seconds > 0:
@@ -743,6 +786,7 @@ def main():
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_forward", "uneven_batch",
+                             "gather_rates",
                              "paper_sensing", "training",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
                              "learner_update", "table2"],
@@ -760,7 +804,7 @@ def main():
         run_reference(args)
     elif args.only:
         fn = {"policy_rollout": policy_rollout, "policy_forward": policy_forward,
-              "uneven_batch": uneven_batch,
+              "uneven_batch": uneven_batch, "gather_rates": gather_rates,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "table2": lambda: table2(args.train_seconds, args.seeds),

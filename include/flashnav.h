@@ -274,6 +274,26 @@ int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m,
                   const float *bias_dev, int act, float *c32_dev, int ldc32, void *c16_dev,
                   int ldc16, void *c16t_dev, int ldct, int *status_dev, void *stream);
 
+/* Random-gather rate probe: the memory ceiling of the beam traversal of
+ * Sec. 2.2.1, whose lanes read single map bytes at unrelated addresses.
+ * n_blocks CTAs of 256 threads; each thread keeps 8 generators
+ * s <- 1664525 s + 1013904223 (uint32), the generator for thread g of the
+ * launch (g = block * 256 + thread) and chain c starting at
+ * s = (8 g + c) * 2654435761 + 0x9E3779B9; per iteration each chain steps
+ * once and reads the byte at offset s >> (32 - log2(bytes)) of the table.
+ *   where 0: the table is the CTA's own shared memory (bytes <= 196608),
+ *            byte j = (j * 2654435761) >> 24 (uint32 arithmetic);
+ *            table_dev is ignored
+ *   where 1: the table is table_dev (device memory of at least `bytes`
+ *            bytes, caller-owned), read through the read-only data path
+ *   bytes: a power of two in [1024, 2^31]; iters >= 0 iterations per thread
+ *   sums_dev [n_blocks] uint32 (caller-owned): each CTA's sum of the bytes
+ *            it read (wrapping), written, not accumulated
+ * Launches one kernel on `stream` (cudaStream_t, NULL = default); the caller
+ * times it.  NAV_E_INVAL for an argument outside these ranges. */
+int nav_gather_probe(int where, const void *table_dev, int64_t bytes, int n_blocks, int iters,
+                     uint32_t *sums_dev, void *stream);
+
 /* Policy network (Sec. 2.1 policy MLP; the FastDSAC actor of Sec. 2.3): a
  * tanh-squashed Gaussian actor obs_dim -> hidden -> hidden -> 4 (mean 2, raw
  * log-std 2) with LeakyReLU (slope 0.01); log sigma = -5 + 5 (tanh(r) + 1)/2,

@@ -27,6 +27,7 @@ EXPORTS = [
     "nav_set_tile_order", "nav_get_tile_order",
     "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
+    "nav_gather_probe",
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
     "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_policy_act_counted",
@@ -121,6 +122,7 @@ def load():
         "nav_graph_launch": (I, [P]),
         "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
         "nav_gemm_bf16": (I, [P, I, P, I, I, I, I, P, I, P, I, P, I, P, I, P, P]),
+        "nav_gather_probe": (I, [I, P, C.c_int64, I, I, P, P]),
         "nav_policy_create": (I, [I, I, I, U64, P]),
         "nav_policy_create_ex": (I, [I, I, I, I, C.c_float, I, U64, P]),
         "nav_policy_get_beta": (I, [P, P]),
@@ -167,6 +169,17 @@ def _np_ptr(a):
 
 def _t_ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def gather_probe(where: int, table, nbytes: int, n_blocks: int, iters: int, sums,
+                 stream: int = 0):
+    """nav_gather_probe: random single-byte gathers from shared memory
+    (where 0) or from the device tensor `table` (where 1); `sums` is a
+    uint32-sized device tensor of n_blocks entries."""
+    rc = load().nav_gather_probe(where, _t_ptr(table), nbytes, n_blocks, iters, _t_ptr(sums),
+                                 C.c_void_p(stream))
+    if rc != 0:
+        raise NavError(rc, "nav_gather_probe: argument out of range or launch failed")
 
 
 def params_struct(p) -> nav_params:
