@@ -60,6 +60,24 @@ __global__ void k_count(unsigned long long *ctr, int which, float b1, float b2, 
     corr[2 * which + 1] = 1.0f - powf(b2, (float)t);
 }
 
+// k_count for the critic step and, in an actor step, for the actor step
+// too, whose loss accumulators acc[0..1] it also clears: the first launch of
+// a fused update
+__global__ void k_count_start(unsigned long long *ctr, int actor, float b1, float b2, float *corr,
+                              float *acc) {
+    pdl_enter();
+    const unsigned long long t = ++ctr[kCtrCritic];
+    corr[0] = 1.0f - powf(b1, (float)t);
+    corr[1] = 1.0f - powf(b2, (float)t);
+    if (actor) {
+        const unsigned long long ta = ++ctr[kCtrActor];
+        corr[2] = 1.0f - powf(b1, (float)ta);
+        corr[3] = 1.0f - powf(b2, (float)ta);
+        acc[0] = 0.0f;
+        acc[1] = 0.0f;
+    }
+}
+
 __global__ void k_insert_done(unsigned long long *ctr, int n, long long cap) {
     ctr[kCtrHead] = (ctr[kCtrHead] + (unsigned long long)n) % (unsigned long long)cap;
     const unsigned long long s = ctr[kCtrSize] + (unsigned long long)n;
@@ -248,6 +266,31 @@ __global__ void k_transpose(const bf16 *__restrict__ in, int ld_in, int rows, in
 }
 
 // ----------------------------------------------------------------- heads ---
+// Distributional target of sample b (Sec. 2.3 FastDSAC): the smaller-mean
+// target critic's Gaussian, sampled with clipped counter-hash noise, minus
+// the entropy term; ym uses the mean instead of the sample.
+__device__ __forceinline__ void target_row(const float *__restrict__ rew,
+                                           const float *__restrict__ term,
+                                           const float *__restrict__ tq1,
+                                           const float *__restrict__ tq2,
+                                           const float *__restrict__ logp_next, float alpha, int b,
+                                           float gamma, float rs, unsigned long long seed,
+                                           unsigned long long update, float &y, float &ym,
+                                           float &zn) {
+    const float m1 = tq1[2 * b], s1 = softplusf(tq1[2 * b + 1]) + 0.1f;
+    const float m2 = tq2[2 * b], s2 = softplusf(tq2[2 * b + 1]) + 0.1f;
+    const bool p1 = m1 <= m2;
+    const float m = p1 ? m1 : m2, s = p1 ? s1 : s2;
+    const unsigned long long h = hmix(seed ^ (update * 0x8CB92BA72F3D8DD7ull) ^ ((unsigned long long)b << 20) ^ 0xA11CEull);
+    const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = (float)((h >> 8) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+    zn = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float z = m + s * fminf(fmaxf(zn, -3.0f), 3.0f);
+    const float cont = gamma * (1.0f - term[b]);
+    y = rs * rew[b] + cont * (z - alpha * logp_next[b]);
+    ym = rs * rew[b] + cont * (m - alpha * logp_next[b]);
+}
+
 __global__ void k_targets(const float *__restrict__ rew, const float *__restrict__ term,
                           const float *__restrict__ tq1, const float *__restrict__ tq2,
                           const float *__restrict__ logp_next, const float *__restrict__ log_alpha,
@@ -257,46 +300,34 @@ __global__ void k_targets(const float *__restrict__ rew, const float *__restrict
     pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const unsigned long long update = ctr[kCtrCritic] - 1;
-    const float m1 = tq1[2 * b], s1 = softplusf(tq1[2 * b + 1]) + 0.1f;
-    const float m2 = tq2[2 * b], s2 = softplusf(tq2[2 * b + 1]) + 0.1f;
-    const bool p1 = m1 <= m2;
-    const float m = p1 ? m1 : m2, s = p1 ? s1 : s2;
-    const unsigned long long h = hmix(seed ^ (update * 0x8CB92BA72F3D8DD7ull) ^ ((unsigned long long)b << 20) ^ 0xA11CEull);
-    const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
-    const float u2 = (float)((h >> 8) & 0xFFFFFFull) * (1.0f / 16777216.0f);
-    const float zn = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-    const float z = m + s * fminf(fmaxf(zn, -3.0f), 3.0f);
-    const float alpha = expf(*log_alpha);
-    const float cont = gamma * (1.0f - term[b]);
-    y[b] = rs * rew[b] + cont * (z - alpha * logp_next[b]);
-    ym[b] = rs * rew[b] + cont * (m - alpha * logp_next[b]);
+    float yb, ymb, zn;
+    target_row(rew, term, tq1, tq2, logp_next, expf(*log_alpha), b, gamma, rs, seed,
+               ctr[kCtrCritic] - 1, yb, ymb, zn);
+    y[b] = yb;
+    ym[b] = ymb;
     if (znoise) znoise[b] = zn;
 }
 
-// dL/dq for one critic; accumulates the batch sum of sigma and the loss
-__device__ __forceinline__ void critic_grad(const float *__restrict__ q, const float *__restrict__ y,
-                                            const float *__restrict__ ym,
-                                            const float *__restrict__ sbar, int B, float delta,
-                                            float *dq, float *acc) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    float ss = 0.0f, ll = 0.0f;
-    if (b < B) {
-        const float m = q[2 * b], qr = q[2 * b + 1];
-        const float s = softplusf(qr) + 0.1f;
-        const float sb = *sbar;
-        const float w = fminf(fmaxf(sb * sb / (s * s + 1e-6f), 0.5f), 2.0f);
-        const float e = m - ym[b];
-        const float ae = fabsf(e);
-        const float hub = ae <= delta ? 0.5f * e * e : delta * (ae - 0.5f * delta);
-        const float d2 = (y[b] - m) * (y[b] - m);
-        ll = w * hub + logf(s) + d2 / (2.0f * s * s);
-        const float inv = 1.0f / (float)B;
-        dq[2 * b] = w * fminf(fmaxf(e, -delta), delta) * inv;
-        const float sig = 1.0f / (1.0f + expf(-qr));
-        dq[2 * b + 1] = (1.0f / s - d2 / (s * s * s)) * inv * sig;
-        ss = s;
-    }
+// dL/dq of one critic for sample b (written to dq); returns sigma and the
+// sample's loss
+__device__ __forceinline__ float2 critic_row(const float *__restrict__ q, float yb, float ymb,
+                                             float sb, int B, float delta, int b, float *dq) {
+    const float m = q[2 * b], qr = q[2 * b + 1];
+    const float s = softplusf(qr) + 0.1f;
+    const float w = fminf(fmaxf(sb * sb / (s * s + 1e-6f), 0.5f), 2.0f);
+    const float e = m - ymb;
+    const float ae = fabsf(e);
+    const float hub = ae <= delta ? 0.5f * e * e : delta * (ae - 0.5f * delta);
+    const float d2 = (yb - m) * (yb - m);
+    const float ll = w * hub + logf(s) + d2 / (2.0f * s * s);
+    const float inv = 1.0f / (float)B;
+    dq[2 * b] = w * fminf(fmaxf(e, -delta), delta) * inv;
+    const float sig = 1.0f / (1.0f + expf(-qr));
+    dq[2 * b + 1] = (1.0f / s - d2 / (s * s * s)) * inv * sig;
+    return make_float2(s, ll);
+}
+
+__device__ __forceinline__ void add_sigma_loss(float ss, float ll, float *acc) {
     for (int o = 16; o > 0; o >>= 1) {
         ss += __shfl_xor_sync(0xffffffffu, ss, o);
         ll += __shfl_xor_sync(0xffffffffu, ll, o);
@@ -307,21 +338,22 @@ __device__ __forceinline__ void critic_grad(const float *__restrict__ q, const f
     }
 }
 
+// dL/dq for one critic; accumulates the batch sum of sigma and the loss
+__device__ __forceinline__ void critic_grad(const float *__restrict__ q, const float *__restrict__ y,
+                                            const float *__restrict__ ym,
+                                            const float *__restrict__ sbar, int B, float delta,
+                                            float *dq, float *acc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float2 r = make_float2(0.0f, 0.0f);
+    if (b < B) r = critic_row(q, y[b], ym[b], *sbar, B, delta, b, dq);
+    add_sigma_loss(r.x, r.y, acc);
+}
+
 __global__ void k_critic_grad(const float *__restrict__ q, const float *__restrict__ y,
                               const float *__restrict__ ym, const float *__restrict__ sbar, int B,
                               float delta, float *dq, float *acc /*[0] sum sigma, [1] loss*/) {
     pdl_enter();
     critic_grad(q, y, ym, sbar, B, delta, dq, acc);
-}
-
-// both critics in one launch (blockIdx.y selects the critic)
-__global__ void k_critic_grad2(const float *__restrict__ q0, const float *__restrict__ q1,
-                               const float *__restrict__ y, const float *__restrict__ ym,
-                               const float *__restrict__ sbar, int B, float delta, float *dq0,
-                               float *dq1, float *acc) {
-    pdl_enter();
-    const bool one = blockIdx.y == 1;
-    critic_grad(one ? q1 : q0, y, ym, sbar, B, delta, one ? dq1 : dq0, acc);
 }
 
 __global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
@@ -330,6 +362,51 @@ __global__ void k_sbar_update(float *sbar, float *acc, int n, float tau_b) {
     acc[2] = acc[1];
     acc[0] = 0.0f;
     acc[1] = 0.0f;
+}
+
+// The targets, both critics' dL/dq and the running sigma of one update in
+// one launch: each thread takes one sample through k_targets' and
+// critic_grad's arithmetic (same values), and the last block to finish (a
+// ticket counter, reset by that block) folds the batch sums into sbar as
+// k_sbar_update does.
+__global__ void k_targets_grad2(const float *__restrict__ rew, const float *__restrict__ term,
+                                const float *__restrict__ tq1, const float *__restrict__ tq2,
+                                const float *__restrict__ logp_next,
+                                const float *__restrict__ log_alpha, int B, float gamma, float rs,
+                                unsigned long long seed, const unsigned long long *__restrict__ ctr,
+                                float *y, float *ym, float *znoise, const float *__restrict__ q0,
+                                const float *__restrict__ q1, float *sbar, float delta, float *dq0,
+                                float *dq1, float *acc, float tau_b, unsigned *ticket) {
+    pdl_enter();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float ss = 0.0f, ll = 0.0f;
+    if (b < B) {
+        float yb, ymb, zn;
+        target_row(rew, term, tq1, tq2, logp_next, expf(*log_alpha), b, gamma, rs, seed,
+                   ctr[kCtrCritic] - 1, yb, ymb, zn);
+        y[b] = yb;
+        ym[b] = ymb;
+        if (znoise) znoise[b] = zn;
+        const float sb = *sbar;
+        const float2 r0 = critic_row(q0, yb, ymb, sb, B, delta, b, dq0);
+        const float2 r1 = critic_row(q1, yb, ymb, sb, B, delta, b, dq1);
+        ss = r0.x + r1.x;
+        ll = r0.y + r1.y;
+    }
+    add_sigma_loss(ss, ll, acc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const float a0 = __ldcg(&acc[0]), a1 = __ldcg(&acc[1]);
+            *sbar = (1.0f - tau_b) * (*sbar) + tau_b * (a0 / (float)(2 * B));
+            acc[2] = a1;
+            acc[0] = 0.0f;
+            acc[1] = 0.0f;
+            *ticket = 0u;
+        }
+    }
 }
 
 // actor loss mean(alpha logp - min(q1, q2)) -> dL/dlogp and dL/dq_i (mean column)
@@ -449,6 +526,32 @@ __global__ void k_alpha(float *log_alpha, float *am, float *av, const float *acc
                         const float *__restrict__ corr) {
     pdl_enter();
     const float c1 = corr[0], c2 = corr[1];
+    const float g = -(acc[1] / (float)B + target_entropy);
+    const float mi = b1 * (*am) + (1.0f - b1) * g;
+    const float vi = b2 * (*av) + (1.0f - b2) * g * g;
+    *am = mi;
+    *av = vi;
+    *log_alpha -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// The actor step's last launch: Eq. 2's beta Adam step (when beta_s is not
+// null, as k_beta_adam) and the alpha Adam step (as k_alpha), one thread.
+__global__ void k_alpha_beta(float *log_alpha, float *am, float *av, const float *acc, int B,
+                             float target_entropy, float lr, float b1, float b2,
+                             const float *__restrict__ corr, float *beta_s, float beta_lr,
+                             float beta_max) {
+    pdl_enter();
+    const float c1 = corr[0], c2 = corr[1];
+    if (beta_s) {
+        const float g = beta_s[3];
+        beta_s[-1] = g;
+        const float mi = b1 * beta_s[1] + (1.0f - b1) * g;
+        const float vi = b2 * beta_s[2] + (1.0f - b2) * g * g;
+        beta_s[1] = mi;
+        beta_s[2] = vi;
+        beta_s[0] = fminf(beta_s[0] - beta_lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f), beta_max);
+        beta_s[3] = 0.0f;
+    }
     const float g = -(acc[1] / (float)B + target_entropy);
     const float mi = b1 * (*am) + (1.0f - b1) * g;
     const float vi = b2 * (*av) + (1.0f - b2) * g * g;
@@ -725,6 +828,7 @@ struct nav_trainer {
     int n_cta = 0;
     float *part_a = nullptr, *part_q[2] = {};
     unsigned long long *ctr = nullptr; // device counters (kCtr*)
+    unsigned *ticket = nullptr;        // last-block ticket of k_targets_grad2 (0 between launches)
     float *corr = nullptr;             // device Adam bias corrections
     // captured update sequences, keyed by (updates per call, policy phase)
     bool use_graphs = false;
@@ -956,6 +1060,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->status, 1);
     TA(T->ctr, 8);
     TA(T->corr, 4);
+    TA(T->ticket, 1);
     T->fused = rc == NAV_OK && fused_ok(T->actor, T->B) && fused_ok(T->q[0], T->B);
     if (c.algo == 1) TA(T->tdist, B * T->qout);
     if (e == cudaSuccess && rc == NAV_OK && c.algo == 1 && !T->fused) {
@@ -1077,8 +1182,9 @@ int fbwd(nav_trainer *T, Mlp *const *nets, int n, float *const *dout, const int 
 }
 
 // One critic update (and the actor update that falls on it) on the fused
-// passes: the same arithmetic as the per-layer path, ~16 launches, each
-// launched with programmatic dependent launch.
+// passes: the same arithmetic as the per-layer path in 9 launches (FastDSAC
+// critic step; 17-18 with an actor step), each launched with programmatic
+// dependent launch.
 int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
@@ -1086,7 +1192,8 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     Mlp *qs[2] = {&T->q[0], &T->q[1]}, *qts[2] = {&T->qt[0], &T->qt[1]}, *act[1] = {&T->actor};
     const int qslot[2] = {1, 2}, aslot[1] = {0};
     const bool c51 = c.algo == 1;
-    launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrCritic, c.beta1, c.beta2, T->corr);
+    launch_pdl(k_count_start, 1, 1, 0, st, T->ctr, actor_step ? 1 : 0, c.beta1, c.beta2, T->corr,
+               T->scal + 8);
     launch_pdl(k_gather_all, blocks((long long)B * T->ldc), 256, 0, st, T->r_obs, T->r_next,
                T->r_act, T->r_rew, T->r_term, B, T->od, T->ld, T->ldc, T->ipap, T->scal + 12,
                T->scale, T->ctr, c.seed, T->cap, T->idx, T->Xo, T->Xn, T->Xc, T->XcT, T->XoT,
@@ -1116,32 +1223,27 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
         const bool sv[4] = {false, false, true, true};
         rc |= ffwd_n(T, four, 4, Xs, lds, outs, sl, sv, st);
     }
-    if (c51)
+    // targets and dL/dq of both critics (with the running sigma for FastDSAC)
+    if (c51) {
         launch_pdl(k_c51_targets, blocks(B, 8), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
                    T->logp_next, T->scal + 0, B, T->qout, c.gamma, c.reward_scale, c.v_min,
                    c.v_max, T->tdist);
-    else
-        launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
-                   T->logp_next, T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr, T->y,
-                   T->ym, T->znoise);
-    // critics
-    if (c51)
         launch_pdl(k_c51_critic_grad2, dim3(blocks(B, 8), 2), 256, 0, st, T->qo[0], T->qo[1],
                    T->tdist, B, T->qout, T->dq[0], T->dq[1], T->scal + 4);
-    else
-        launch_pdl(k_critic_grad2, dim3(blocks(B), 2), 256, 0, st, T->qo[0], T->qo[1], T->y, T->ym,
-                   T->scal + 1, B, c.huber_delta, T->dq[0], T->dq[1], T->scal + 4);
-    if (!c51) launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
+    } else {
+        launch_pdl(k_targets_grad2, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
+                   T->logp_next, T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr, T->y,
+                   T->ym, T->znoise, T->qo[0], T->qo[1], T->scal + 1, c.huber_delta, T->dq[0],
+                   T->dq[1], T->scal + 4, c.tau_b, T->ticket);
+    }
     rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
     rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
                             c.weight_decay, st);
     if (actor_step) {
         // the actor's own action a, written into Xa's action columns too
-        launch_pdl(k_count, 1, 1, 0, st, T->ctr, kCtrActor, c.beta1, c.beta2, T->corr);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
                                     T->a_new, T->logp_new, T->eps_new, st, T->Xa, T->ldc, T->od);
         rc |= ffwd(T, qs, 2, T->Xa, T->ldc, T->qa, qslot, false, st);
-        launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
         if (c51)
             launch_pdl(k_c51_actor_loss, blocks(B, 8), 256, 0, st, T->logp_new, T->qa[0], T->qa[1],
                        T->scal + 0, B, T->qout, c.v_min, c.v_max, T->dlogp, T->dq[0], T->dq[1],
@@ -1156,14 +1258,12 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
         rc |= fbwd(T, act, 1, douts, aslot, T->XoT, pa, T->ipap > 0 ? dxa : nullptr, T->ld, st);
         rc |= launch_adam_fused(act, pa, 1, T->n_cta, c.lr_actor, c.beta1, c.beta2, T->corr + 2,
                                 c.weight_decay, st);
-        if (T->ipap > 0) {
+        if (T->ipap > 0)
             launch_pdl(k_beta_grad, blocks((long long)B * T->ipap), 256, 0, st, T->dXa, T->ld,
                        T->Lraw, B, T->ipap, T->scal + 12, T->scale, T->scal + 15);
-            launch_pdl(k_beta_adam, 1, 1, 0, st, T->scal + 12, c.lr_actor, c.beta1, c.beta2,
-                       T->corr + 2, c.ipap_beta_max);
-        }
-        launch_pdl(k_alpha, 1, 1, 0, st, T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8, B,
-                   c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2);
+        launch_pdl(k_alpha_beta, 1, 1, 0, st, T->scal + 0, T->scal + 2, T->scal + 3, T->scal + 8,
+                   B, c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2,
+                   T->ipap > 0 ? T->scal + 12 : nullptr, c.lr_actor, c.ipap_beta_max);
     }
     rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);
     rc |= (int)cudaGetLastError();
