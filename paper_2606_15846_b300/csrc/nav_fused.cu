@@ -3,7 +3,7 @@
 // a network as one launch per layer and per gradient; at batch 1024 and width
 // 100 each launch is a few microseconds of latency around almost no work, and
 // an update of the twin critics and the actor is ~180 of them.  Here one CTA
-// (4 warps) owns 128 batch rows of a network and walks all its layers:
+// (16 warps) owns 128 batch rows of a network and walks all its layers:
 //
 // forward: per layer, the weight tile [out][in] is copied (cp.async) into a
 //   swizzled K-major shared tile, one thread issues tcgen05.mma (M 128,
@@ -35,17 +35,17 @@ namespace flashnav {
 namespace {
 
 typedef __nv_bfloat16 bf16;
-constexpr int kT = 256; // threads per CTA: warps w and w + 4 share TMEM lanes 32 (w % 4) ..,
-                        // and split the columns (w / 4 selects the half)
+constexpr int kTF = 512; // threads per CTA of the passes: warps w, w + 4, w + 8, w + 12
+                         // share TMEM lanes 32 (w % 4) .. and take a quarter of the columns
 constexpr unsigned kChunk = 128 * 128; // one 64-wide K chunk of 128 rows (bytes)
 constexpr float kSlope = 0.01f;
 
 __device__ __forceinline__ int round16(int n) { return (n + 15) & ~15; }
 
-// zero `bytes` (multiple of 16 * kT) of shared memory at s
-__device__ __forceinline__ void zero_smem(unsigned char *s, unsigned bytes) {
+// zero `bytes` (multiple of 16 * NT) of shared memory at s with NT threads
+template <int NT> __device__ __forceinline__ void zero_smem(unsigned char *s, unsigned bytes) {
     uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    for (unsigned o = threadIdx.x * 16u; o < bytes; o += 16u * kT)
+    for (unsigned o = threadIdx.x * 16u; o < bytes; o += 16u * NT)
         *reinterpret_cast<uint4 *>(s + o) = z;
 }
 
@@ -108,15 +108,15 @@ __device__ __forceinline__ void zero_cols(unsigned char *tile, int row, int c0, 
 // smem: A (the layer input, 2 chunks; rewritten in place with the layer's
 // output once its MMAs have completed) | W0 | W1 (weights, double-buffered:
 // layer l + 1's tile is copied while layer l computes).  Warp w reads TMEM
-// lanes 32 (w % 4) .. (batch rows) and columns [64 h, 64 h + 64), h = w / 4.
-__global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
+// lanes 32 (w % 4) .. (batch rows) and columns [32 q, 32 q + 32), q = w / 4.
+__global__ void __launch_bounds__(kTF) mlp_fwd_fused(const FGroup g) {
     pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ unsigned tmem_slot;
     __shared__ float sbias[2][kFusedMaxWidth];
     const FNet &N = g.net[blockIdx.y];
-    const int tid = threadIdx.x, warp = tid >> 5, quad = warp & 3, half = warp >> 2;
+    const int tid = threadIdx.x, warp = tid >> 5, quad = warp & 3, qtr = warp >> 2;
     const int row = quad * 32 + (tid & 31), r0 = blockIdx.x * 128, grow = r0 + row;
     const unsigned raw = smem_addr(smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
@@ -126,20 +126,20 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    zero_smem(ap, 2 * kChunk);
+    zero_smem<kTF>(ap, 2 * kChunk);
     const unsigned tmem = tmem_alloc(&tmem_slot, 128); // synchronises: A is zero
     const unsigned tlane = (unsigned)(quad * 32) << 16;
     auto fetch = [&](int l) { // weights and bias of layer l (and the input for l = 0)
         const FLayer &L = N.L[l];
         const int np = round16(L.out), nkc = (L.in + 63) >> 6;
         for (int c = 0; c < nkc; ++c)
-            load_tile<kT>(wb[l & 1] + c * kChunk, static_cast<const bf16 *>(L.W16), L.ld_in, 0,
+            load_tile<kTF>(wb[l & 1] + c * kChunk, static_cast<const bf16 *>(L.W16), L.ld_in, 0,
                           np, L.out, 64 * c, L.in);
         if (l == 0)
             for (int c = 0; c < nkc; ++c)
-                load_tile<kT>(a + c * kChunk, static_cast<const bf16 *>(N.X), N.ldx, r0, 128, g.B,
+                load_tile<kTF>(a + c * kChunk, static_cast<const bf16 *>(N.X), N.ldx, r0, 128, g.B,
                               64 * c, L.in);
-        for (int t = tid; t < np; t += kT) sbias[l & 1][t] = t < L.out ? L.b[t] : 0.0f;
+        for (int t = tid; t < np; t += kTF) sbias[l & 1][t] = t < L.out ? L.b[t] : 0.0f;
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     fetch(0);
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
         if (!last) fetch(l + 1);
         wait_or_flag(smem_addr(&bar), (unsigned)(l & 1), g.status);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned mask[2] = {0u, 0u};
-        const int j0 = 64 * half, j1 = min(np, j0 + 64);
+        unsigned mask = 0u;
+        const int j0 = 32 * qtr, j1 = min(np, j0 + 32);
         for (int j = j0; j < j1; j += 16) {
             float v[16];
             tmem_ld16(tmem + tlane + (unsigned)j, v);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
                 v[i] = j + i < out ? x : 0.0f;
                 bits |= (v[i] > 0.0f ? 1u : 0u) << i;
             }
-            mask[(j >> 5) & 1] |= bits << (j & 16);
+            mask |= bits << (j & 16);
             if (last) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
@@ -194,10 +194,8 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
             }
         }
         if (!last) {
-            zero_cols(ap, row, max(np, j0), j0 + 64); // the next layer reads whole chunks
-            if (N.M[l] && j0 < np)
-                *reinterpret_cast<uint2 *>(N.M[l] + (long long)grow * 4 + 2 * half) =
-                    make_uint2(mask[0], mask[1]);
+            zero_cols(ap, row, max(np, j0), j0 + 32); // the next layer reads whole chunks
+            if (N.M[l] && j0 < np) N.M[l][(long long)grow * 4 + qtr] = mask;
         }
         // activations visible to the async proxy (next layer's MMA)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -211,8 +209,9 @@ __global__ void __launch_bounds__(kT) mlp_fwd_fused(const FGroup g) {
 // smem: Gn (row-major G, 2 chunks) | Gt (transposed G, 2 chunks of 64 batch
 // rows) | HT0 | HT1 | WT0 | WT1 (layer operands, double-buffered).  G is
 // rewritten in place once the layer's MMAs have completed.  As in the
-// forward, warps w and w + 4 share TMEM lanes and split the columns.
-__global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
+// forward, warps w, w + 4, w + 8 and w + 12 share TMEM lanes and split the
+// columns in quarters.
+__global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
     pdl_enter();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
     __shared__ float sdb[kFusedMaxWidth];
     const FNet &N = g.net[blockIdx.y];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = warp & 3,
-              half = warp >> 2;
+              qtr = warp >> 2;
     const int row = quad * 32 + lane, cta = blockIdx.x, r0 = cta * 128, grow = r0 + row;
     const unsigned raw = smem_addr(smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
@@ -233,8 +232,8 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    zero_smem(gnp, 4 * kChunk);
-    for (int t = tid; t < kFusedMaxWidth; t += kT) sdb[t] = 0.0f;
+    zero_smem<kTF>(gnp, 4 * kChunk);
+    for (int t = tid; t < kFusedMaxWidth; t += kTF) sdb[t] = 0.0f;
     const int top = N.n_layers - 1, nout = N.L[top].out;
     auto fetch = [&](int l, int buf) { // operands of layer l's MMAs
         const FLayer &L = N.L[l];
@@ -242,20 +241,20 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
         if (N.gWp[l]) {
             const bf16 *src = static_cast<const bf16 *>(l > 0 ? N.HT16[l - 1] : N.XT);
             for (int c = 0; c < 2; ++c)
-                load_tile<kT>(htb[buf] + c * kChunk, src, g.B, 0, inp, L.in, r0 + 64 * c, g.B);
+                load_tile<kTF>(htb[buf] + c * kChunk, src, g.B, 0, inp, L.in, r0 + 64 * c, g.B);
         }
         if (l > 0 || N.dX)
             for (int c = 0; c < koc; ++c)
-                load_tile<kT>(wtb[buf] + c * kChunk, static_cast<const bf16 *>(L.WT16), L.ld_out,
+                load_tile<kTF>(wtb[buf] + c * kChunk, static_cast<const bf16 *>(L.WT16), L.ld_out,
                               0, inp, L.in, 64 * c, L.out);
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     fetch(top, 0);
     const unsigned tmem = tmem_alloc(&tmem_slot, 256); // synchronises: G is zero
     // top layer: G = dout (FP32 for the bias sums, BF16 in both layouts);
-    // the halves split its columns as in the epilogues
+    // the quarters split its columns as in the epilogues
     {
-        const int j0 = 64 * half, j1 = min(round16(nout), j0 + 64);
+        const int j0 = 32 * qtr, j1 = min(round16(nout), j0 + 32);
         for (int j = j0; j < j1; j += 16) {
             float v[16];
             const float *src = N.dout + (long long)grow * nout + j;
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
     }
     __syncthreads();
     if (N.gbp[top])
-        for (int t = tid; t < nout; t += kT) N.gbp[top][(long long)cta * N.cta_stride + t] = sdb[t];
+        for (int t = tid; t < nout; t += kTF) N.gbp[top][(long long)cta * N.cta_stride + t] = sdb[t];
     unsigned phase = 0;
     for (int l = top; l >= 0; --l) {
         const FLayer &L = N.L[l];
@@ -293,21 +292,21 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
             if (dh) mma_chunks(tmem + 128, gn, wtb[buf], koc, instr_desc(128, inp));
             mma_commit(smem_addr(&bar));
         }
-        uint2 msk = make_uint2(0u, 0u);
+        unsigned msk = 0u;
         if (next) {
             fetch(l - 1, buf ^ 1);
-            if (dh) msk = *reinterpret_cast<const uint2 *>(N.M[l - 1] + (long long)grow * 4 + 2 * half);
-            for (int t = tid; t < kFusedMaxWidth; t += kT) sdb[t] = 0.0f;
+            if (dh) msk = N.M[l - 1][(long long)grow * 4 + qtr];
+            for (int t = tid; t < kFusedMaxWidth; t += kTF) sdb[t] = 0.0f;
         }
         if (any) wait_or_flag(smem_addr(&bar), phase & 1u, g.status);
         phase += any ? 1u : 0u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads(); // sdb cleared before the column sums
         if (wg) {
-            // lane k holds dW[n][k] for 16 outputs n per load; halves split n
+            // lane k holds dW[n][k] for 16 outputs n per load; quarters split n
             const int k = quad * 32 + lane;
             float *dst = N.gWp[l] + (long long)cta * N.cta_stride + k;
-            for (int j = 16 * half; j < onp; j += 32) {
+            for (int j = 16 * qtr; j < onp; j += 64) {
                 float v[16];
                 tmem_ld16(tmem + tlane + (unsigned)j, v);
                 if (k < in) {
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
             }
         }
         if (dh) {
-            const int j0 = 64 * half, j1 = min(inp, j0 + 64);
+            const int j0 = 32 * qtr, j1 = min(inp, j0 + 32);
             for (int j = j0; j < j1; j += 16) {
                 float v[16];
                 tmem_ld16(tmem + tlane + 128u + (unsigned)j, v);
@@ -329,7 +328,7 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
                     continue;
                 }
                 // LeakyReLU' from the sign bits of layer l-1's activation
-                const unsigned bits = (((j >> 5) & 1) ? msk.y : msk.x) >> (j & 16);
+                const unsigned bits = msk >> (j & 16);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const float z = v[i] * (((bits >> i) & 1u) ? 1.0f : kSlope);
@@ -345,13 +344,13 @@ __global__ void __launch_bounds__(kT) mlp_bwd_fused(const FGroup g) {
                 if ((lane & 1) == 0) atomicAdd(&sdb[j + colsum16_col(lane)], cs);
             }
             // the next layer's dH MMA reads whole 64-wide chunks of Gn
-            if (next) zero_cols(gnp, row, max(inp, j0), j0 + 64);
+            if (next) zero_cols(gnp, row, max(inp, j0), j0 + 32);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (next && N.gbp[l - 1])
-            for (int t = tid; t < in; t += kT) N.gbp[l - 1][(long long)cta * N.cta_stride + t] = sdb[t];
+            for (int t = tid; t < in; t += kTF) N.gbp[l - 1][(long long)cta * N.cta_stride + t] = sdb[t];
     }
     tmem_free(tmem, 256);
 }
@@ -482,7 +481,7 @@ int launch_mlp_fwd_fused(const FGroup &g, void *stream) {
     cudaError_t e = cudaFuncSetAttribute(mlp_fwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kFwdSmem);
     if (e != cudaSuccess) return (int)e;
-    launch_pdl(mlp_fwd_fused, dim3(g.B / 128, g.n_nets), kT, kFwdSmem, static_cast<cudaStream_t>(stream), g);
+    launch_pdl(mlp_fwd_fused, dim3(g.B / 128, g.n_nets), kTF, kFwdSmem, static_cast<cudaStream_t>(stream), g);
     return (int)cudaGetLastError();
 }
 
@@ -490,7 +489,7 @@ int launch_mlp_bwd_fused(const FGroup &g, void *stream) {
     cudaError_t e = cudaFuncSetAttribute(mlp_bwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kBwdSmem);
     if (e != cudaSuccess) return (int)e;
-    launch_pdl(mlp_bwd_fused, dim3(g.B / 128, g.n_nets), kT, kBwdSmem, static_cast<cudaStream_t>(stream), g);
+    launch_pdl(mlp_bwd_fused, dim3(g.B / 128, g.n_nets), kTF, kBwdSmem, static_cast<cudaStream_t>(stream), g);
     return (int)cudaGetLastError();
 }
 
