@@ -35,8 +35,12 @@ namespace flashnav {
 namespace {
 
 typedef __nv_bfloat16 bf16;
-constexpr int kTF = 512; // threads per CTA of the passes: warps w, w + 4, w + 8, w + 12
-                         // share TMEM lanes 32 (w % 4) .. and take a quarter of the columns
+constexpr int kTF = 512; // threads per CTA of the passes: warps w, w + 4, w + 8, ... share
+                         // TMEM lanes 32 (w % 4) .. and split the columns (1024 threads,
+                         // 16 columns a warp, measured slower)
+constexpr int kGroups = kTF / 128;   // warps per TMEM lane quarter
+constexpr int kSpan = 128 / kGroups; // columns per warp (16 or 32)
+static_assert(kSpan == 16 || kSpan == 32, "a warp's columns must lie in one mask word");
 constexpr unsigned kChunk = 128 * 128; // one 64-wide K chunk of 128 rows (bytes)
 constexpr float kSlope = 0.01f;
 
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kTF) mlp_fwd_fused(const FGroup g) {
         wait_or_flag(smem_addr(&bar), (unsigned)(l & 1), g.status);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         unsigned mask = 0u;
-        const int j0 = 32 * qtr, j1 = min(np, j0 + 32);
+        const int j0 = kSpan * qtr, j1 = min(np, j0 + kSpan);
         for (int j = j0; j < j1; j += 16) {
             float v[16];
             tmem_ld16(tmem + tlane + (unsigned)j, v);
@@ -194,8 +198,14 @@ __global__ void __launch_bounds__(kTF) mlp_fwd_fused(const FGroup g) {
             }
         }
         if (!last) {
-            zero_cols(ap, row, max(np, j0), j0 + 32); // the next layer reads whole chunks
-            if (N.M[l] && j0 < np) N.M[l][(long long)grow * 4 + qtr] = mask;
+            zero_cols(ap, row, max(np, j0), j0 + kSpan); // the next layer reads whole chunks
+            if (N.M[l] && j0 < np) {
+                if (kSpan == 32)
+                    N.M[l][(long long)grow * 4 + qtr] = mask;
+                else // this warp's 16 columns: one half of a mask word
+                    reinterpret_cast<unsigned short *>(N.M[l] + (long long)grow * 4)[qtr] =
+                        (unsigned short)(mask >> (j0 & 16));
+            }
         }
         // activations visible to the async proxy (next layer's MMA)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
     // top layer: G = dout (FP32 for the bias sums, BF16 in both layouts);
     // the quarters split its columns as in the epilogues
     {
-        const int j0 = 32 * qtr, j1 = min(round16(nout), j0 + 32);
+        const int j0 = kSpan * qtr, j1 = min(round16(nout), j0 + kSpan);
         for (int j = j0; j < j1; j += 16) {
             float v[16];
             const float *src = N.dout + (long long)grow * nout + j;
@@ -295,7 +305,7 @@ __global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
         unsigned msk = 0u;
         if (next) {
             fetch(l - 1, buf ^ 1);
-            if (dh) msk = N.M[l - 1][(long long)grow * 4 + qtr];
+            if (dh) msk = N.M[l - 1][(long long)grow * 4 + (kSpan * qtr >> 5)];
             for (int t = tid; t < kFusedMaxWidth; t += kTF) sdb[t] = 0.0f;
         }
         if (any) wait_or_flag(smem_addr(&bar), phase & 1u, g.status);
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
             // lane k holds dW[n][k] for 16 outputs n per load; quarters split n
             const int k = quad * 32 + lane;
             float *dst = N.gWp[l] + (long long)cta * N.cta_stride + k;
-            for (int j = 16 * qtr; j < onp; j += 64) {
+            for (int j = 16 * qtr; j < onp; j += 16 * kGroups) {
                 float v[16];
                 tmem_ld16(tmem + tlane + (unsigned)j, v);
                 if (k < in) {
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
             }
         }
         if (dh) {
-            const int j0 = 32 * qtr, j1 = min(inp, j0 + 32);
+            const int j0 = kSpan * qtr, j1 = min(inp, j0 + kSpan);
             for (int j = j0; j < j1; j += 16) {
                 float v[16];
                 tmem_ld16(tmem + tlane + 128u + (unsigned)j, v);
@@ -344,7 +354,7 @@ __global__ void __launch_bounds__(kTF) mlp_bwd_fused(const FGroup g) {
                 if ((lane & 1) == 0) atomicAdd(&sdb[j + colsum16_col(lane)], cs);
             }
             // the next layer's dH MMA reads whole 64-wide chunks of Gn
-            if (next) zero_cols(gnp, row, max(inp, j0), j0 + 32);
+            if (next) zero_cols(gnp, row, max(inp, j0), j0 + kSpan);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
