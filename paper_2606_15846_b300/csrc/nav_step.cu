@@ -268,7 +268,7 @@ __device__ void dyn_gate(const DynEnv &de, float xc, float yc, float dx, float d
                          float &ghi) {
     glo = INFINITY;
     ghi = -INFINITY;
-    const float rdx = dx != 0.0f ? 1.0f / dx : 0.0f, rdy = dy != 0.0f ? 1.0f / dy : 0.0f;
+    const float rdx = dx != 0.0f ? __frcp_rn(dx) : 0.0f, rdy = dy != 0.0f ? __frcp_rn(dy) : 0.0f;
     for (int q = 0; q < de.n; ++q) {
         const float x0 = (float)(de.bi0[q] - 1), x1 = (float)(de.bi1[q] + 2);
         const float y0 = (float)(de.j0[q] - 1), y1 = (float)(de.j0[q] + de.nr[q] + 1);
@@ -337,13 +337,15 @@ __device__ __forceinline__ float cast_ray(const V &view, const MapDev &M, float 
         return 0.0f;
     }
     // per axis: cell-index step, tDelta and the first boundary parameter t0
-    // (tDelta 0 and t0 = inf on an axis the ray does not move along)
+    // (tDelta 0 and t0 = inf on an axis the ray does not move along);
+    // __frcp_rn is the correctly rounded reciprocal, the value of 1 / d
+    // without the general division's code
     int sbx = 0, sby = 0;
     float tdx = 0.0f, tdy = 0.0f, tx0 = INFINITY, ty0 = INFINITY;
-    if (dx > 0.0f) { sbx = 1; tdx = 1.0f / dx; tx0 = ((fx + 1.0f) - xc) * tdx; }
-    else if (dx < 0.0f) { sbx = -1; tdx = 1.0f / -dx; tx0 = (xc - fx) * tdx; }
-    if (dy > 0.0f) { sby = pb; tdy = 1.0f / dy; ty0 = ((fy + 1.0f) - yc) * tdy; }
-    else if (dy < 0.0f) { sby = -pb; tdy = 1.0f / -dy; ty0 = (yc - fy) * tdy; }
+    if (dx > 0.0f) { sbx = 1; tdx = __frcp_rn(dx); tx0 = ((fx + 1.0f) - xc) * tdx; }
+    else if (dx < 0.0f) { sbx = -1; tdx = __frcp_rn(-dx); tx0 = (xc - fx) * tdx; }
+    if (dy > 0.0f) { sby = pb; tdy = __frcp_rn(dy); ty0 = ((fy + 1.0f) - yc) * tdy; }
+    else if (dy < 0.0f) { sby = -pb; tdy = __frcp_rn(-dy); ty0 = (yc - fy) * tdy; }
     float glo = INFINITY, ghi = -INFINITY;
     if (DYN) dyn_gate(*de, xc, yc, dx, dy, glo, ghi);
     float t = 0.0f, kx, ky;
@@ -460,7 +462,7 @@ __device__ __forceinline__ float march_ray(const V &view, const MapDev &M, float
         float s_end = fmaxf(1.0f, floorf(rmax_c / step_c));
         while (s_end > 1.0f && (s_end - 1.0f) * step_c > rmax_c) s_end -= 1.0f;
         while (s_end * step_c <= rmax_c) s_end += 1.0f;
-        const float per = 1.0f / (step_c * fmaxf(fabsf(dx), fabsf(dy)));
+        const float per = __frcp_rn(step_c * fmaxf(fabsf(dx), fabsf(dy)));
         float s = 0.0f;
         int d = view.dist_at(b0);
         for (;;) {
