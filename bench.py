@@ -747,7 +747,7 @@ def run_gpu(args):
                     "steps": e2e_steps},
             "clocks": clk.summary(),
         }
-        if world == 1:
+        if world == 1 and args.extras:
             # measured random-gather ceilings beside the nominal one (the
             # 256x256 distance maps are staged in shared memory)
             g = gather_rates()
