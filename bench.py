@@ -246,11 +246,12 @@ def policy_forward(rows: int = 65536, calls: int = 20):
     return out
 
 
-def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
+def uneven_batch(steps_per_graph: int = 20, replays: int = 5, eager: bool = False):
     """Uneven batch in one persistent launch per step: 16384 envs over 64 maps
     of 128..1024 cells, beams 180/360/720, disc and rectangle robots, 8 moving
     discs per env; autotuned; steps captured in one CUDA graph; L2 flushed
-    between graph replays."""
+    between graph replays.  eager: the same steps launched one by one (L2
+    flushed before each), for profilers that cannot follow graph launches."""
     import torch
     from paper_2606_15846_b300 import flashnav
     from paper_2606_15846_b300 import workloads as W
@@ -274,17 +275,30 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5):
         sim.graph_launch()
         visits, rays = sim.stats()
         sim.set_stats(False)
-        sim.graph_capture(acts, obs, rew, done)
-        sim.graph_launch()
         tot = 0.0
-        for r in range(replays):
-            flush.fill_(float(r))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
+        if eager:
+            for r in range(replays):
+                for t in range(steps_per_graph):
+                    flush.fill_(float(t))
+                    e0, e1 = (torch.cuda.Event(enable_timing=True),
+                              torch.cuda.Event(enable_timing=True))
+                    e0.record(s)
+                    sim.step(acts[t], obs, rew, done)
+                    e1.record(s)
+                    e1.synchronize()
+                    tot += e0.elapsed_time(e1)
+        else:
+            sim.graph_capture(acts, obs, rew, done)
             sim.graph_launch()
-            e1.record(s)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
+            for r in range(replays):
+                flush.fill_(float(r))
+                e0, e1 = (torch.cuda.Event(enable_timing=True),
+                          torch.cuda.Event(enable_timing=True))
+                e0.record(s)
+                sim.graph_launch()
+                e1.record(s)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
     ms = tot / (replays * steps_per_graph)
     return {"env_steps_per_s": E / (ms / 1e3), "ms_per_step": ms,
             "beam_casts_per_step": rays / steps_per_graph,
@@ -793,7 +807,8 @@ def main():
                     help="run one of the extra measurements alone")
     ap.add_argument("--seeds", type=int, default=5, help="table2: training seeds per setting")
     ap.add_argument("--eager", action="store_true",
-                    help="learner_update: eager launches instead of graph replays (profiling)")
+                    help="learner_update, uneven_batch: eager launches instead of graph "
+                         "replays (profiling)")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
                          "(default: autotune)")
@@ -804,7 +819,8 @@ def main():
         run_reference(args)
     elif args.only:
         fn = {"policy_rollout": policy_rollout, "policy_forward": policy_forward,
-              "uneven_batch": uneven_batch, "gather_rates": gather_rates,
+              "uneven_batch": lambda: uneven_batch(eager=args.eager),
+              "gather_rates": gather_rates,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "table2": lambda: table2(args.train_seconds, args.seeds),
