@@ -542,13 +542,13 @@ __device__ __forceinline__ void put_range(const StepArgs &A, float *row, int k, 
 // ---------------------------------------------------------------------------
 template <bool DYN, class B>
 __device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc, float rc,
-                             const DynEnv *de) {
+                             const DynEnv *de, bool static_clear = false) {
     const int j0 = (int)floorf(yc - rc);
     const int j1 = (int)ceilf(yc + rc) - 1;
     for (int j = j0; j <= j1; ++j) {
         int a, b;
         if (!disc_row(xc, yc, rc, j, a, b)) continue;
-        if (row_blocked(bits, M, j, a, b)) return true;
+        if (!static_clear && row_blocked(bits, M, j, a, b)) return true;
         if (DYN && dyn_row(*de, j, a, b)) return true;
     }
     return false;
@@ -560,7 +560,8 @@ __device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc,
 // and its edges' crossings of y = j and y = j + 1.
 template <bool DYN, class B>
 __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc, float st,
-                             float ct, float hl, float hw, const DynEnv *de) {
+                             float ct, float hl, float hw, const DynEnv *de,
+                             bool static_clear = false) {
     const float ax = hl * ct, ay = hl * st;
     const float bx = -(hw * st), by = hw * ct;
     float px[4], py[4];
@@ -604,7 +605,7 @@ __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc,
         }
         if (!(xlo <= xhi)) continue;
         const int a = (int)floorf(xlo), b = (int)ceilf(xhi) - 1;
-        if (row_blocked(bits, M, j, a, b)) return true;
+        if (!static_clear && row_blocked(bits, M, j, a, b)) return true;
         if (DYN && dyn_row(*de, j, a, b)) return true;
     }
     return false;
@@ -794,10 +795,11 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         // With a distance view: the footprint lies within R cells of a point
         // of the centre's cell, so it can only meet cells fewer than R + 1
         // rows or columns away; when the centre cell's chessboard distance d
-        // has d - 2 >= R (R rounded up a little), all of those are free and
-        // the row scan is skipped (same result).
+        // has d - 2 >= R (R rounded up a little), all of those are free in
+        // the static map: its row scan is skipped (same result), and only
+        // the moving discs' stamps (in shared memory) are tested.
         bool clear = false;
-        if constexpr (has_dist<B>::value && !DYN) {
+        if constexpr (has_dist<B>::value) {
             const float hl = (0.5f * rb.length) * M.inv_res, hw = (0.5f * rb.width) * M.inv_res;
             const float R = rb.shape == 0 ? rb.radius * M.inv_res : sqrtf(hl * hl + hw * hw);
             if (xc >= 0.0f && yc >= 0.0f && xc < (float)M.w && yc < (float)M.h) {
@@ -806,13 +808,13 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
             }
         }
         bool coll = false;
-        if (clear)
+        if (clear && (!DYN || dmain->n == 0))
             coll = false;
         else if (rb.shape == 0)
-            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain);
+            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, clear);
         else
             coll = rect_blocked<DYN>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
-                                     (0.5f * rb.width) * M.inv_res, dmain);
+                                     (0.5f * rb.width) * M.inv_res, dmain, clear);
         // a7: goal test, reward, flags
         const float ddx = gx - x, ddy = gy - y;
         const float d = sqrtf(ddx * ddx + ddy * ddy);
