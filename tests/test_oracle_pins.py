@@ -737,3 +737,88 @@ def test_free_running_invariants(oracle):
         assert ((done & 1) != 0).sum() == (((done & 4) != 0) | ((done & 8) != 0)).sum()
         assert not ((done & 1) & ((done & 2) >> 1)).any()
         prev_ep = i[:, 1].astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# Moving discs (the workload's dynamic layer): stamping, bounce, collision
+# --------------------------------------------------------------------------
+def _one_env_discs(oracle, occ):
+    return _one_env(oracle, occ, params=W.Params(goal_dmin=0.0, goal_dmax=1e9, n_dyn=1))
+
+
+def _set_disc(sim, x, y, th, disc):
+    f = np.array([[x, y, th, 0, 0, 0.5, 0.5, 1.0]], np.float32)
+    i = np.array([[0, 0]], np.int32)
+    sim.set_state(1, f, i, np.array([[disc]], np.float32))
+
+
+STAY = np.array([[-1.0, 0.0]], np.float32)  # v = 0, w = 0
+
+
+def test_disc_stamp_is_first_cell_meeting_the_open_disc(oracle):
+    """A ray along +x meets the first cell whose closed square meets the open
+    disc: with the disc centre at (40.0, 32.2) cells and radius 3.6, row 32
+    holds x in (36.4, 43.6), so cell 36 ([36, 37]) is stamped and 35 is not;
+    from x = 20 the range is 16 cells."""
+    sim = _one_env_discs(oracle, np.zeros((64, 64), np.uint8))
+    # beam 4 of 8 points along the heading + pi/8
+    _set_disc(sim, 20.0 * RES, 32.2 * RES, -math.pi / 8, [40.0 * RES, 32.2 * RES, 0.0, 0.0])
+    obs, _, done = sim.step(STAY)
+    r, h, _ = sim.debug()
+    assert done[0] == 0
+    assert h[4] == 32 * 64 + 36
+    assert abs(float(r[4]) - 16.0 * RES) < 1e-5
+    assert abs(float(obs[4]) - 16.0 * RES) < 1e-5
+
+
+def test_disc_with_integer_edge_stamps_the_cell_it_opens_into(oracle):
+    """Exact binary32 geometry (1/16 m cells, disc radius 3 cells, centre at
+    x = 40 cells): the open disc spans x in (37, 43) in its centre row, so
+    cell 36, whose closed square [36, 37] touches it only at its boundary
+    point, is not stamped, and the first stamped cell is 37."""
+    res = 0.0625
+    params = W.Params(goal_dmin=0.0, goal_dmax=1e9, n_dyn=1, dyn_radius=0.1875)
+    sim = oracle.OracleSim([np.zeros((64, 64), np.uint8)], np.zeros(1, np.int32),
+                           np.full(1, 8, np.int32), np.zeros(1, np.int32), [W.DISC], 2.0,
+                           params, res)
+    sim.reset(1)
+    f = np.array([[20.0 * res, 32.5 * res, -math.pi / 8, 0, 0, 0.5, 0.5, 1.0]], np.float32)
+    sim.set_state(1, f, np.array([[0, 0]], np.int32),
+                  np.array([[[40.0 * res, 32.5 * res, 0.0, 0.0]]], np.float32))
+    sim.step(STAY)
+    r, h, _ = sim.debug()
+    assert h[4] == 32 * 64 + 37
+    assert abs(float(r[4]) - 17.0 * res) < 1e-5
+
+
+def test_disc_bounces_off_a_wall_and_moves_in_free_space(oracle):
+    """Constant velocity over dt = 0.1 s; a velocity component flips, and that
+    coordinate stays, when the moved centre's cell is blocked."""
+    occ = np.zeros((64, 64), np.uint8)
+    occ[:, 30] = 1  # wall column: x in [1.50, 1.55] m
+    sim = _one_env_discs(oracle, occ)
+    _set_disc(sim, 0.5, 1.61, 0.0, [1.475, 1.61, 0.5, 0.0])  # +x into the wall
+    sim.step(STAY)
+    _, _, d = sim.get_state()
+    assert np.allclose(d[0, 0], [1.475, 1.61, -0.5, 0.0], atol=1e-6)
+    sim.step(STAY)  # now moving -x through free cells
+    _, _, d = sim.get_state()
+    assert np.allclose(d[0, 0], [1.425, 1.61, -0.5, 0.0], atol=1e-6)
+    _set_disc(sim, 0.5, 1.61, 0.0, [1.2, 1.2, 0.0, 0.5])  # +y in free space
+    sim.step(STAY)
+    _, _, d = sim.get_state()
+    assert np.allclose(d[0, 0], [1.2, 1.25, 0.0, 0.5], atol=1e-6)
+
+
+def test_robot_collides_with_a_stamped_cell_only(oracle):
+    """Robot disc (r 0.18 m) centred at x = 20 cells reaches x = 23.6 in row
+    32.  A disc whose left edge is at 23.4 stamps cell 23 of row 32: the
+    footprint meets it (collision).  With the edge at 24.4 the first stamped
+    cell of that row is 24, which the robot does not reach: no collision."""
+    sim = _one_env_discs(oracle, np.zeros((64, 64), np.uint8))
+    _set_disc(sim, 1.0, 32.5 * RES, 0.0, [1.35, 32.5 * RES, 0.0, 0.0])
+    _, _, done = sim.step(STAY)
+    assert done[0] & 1 and done[0] & 8
+    _set_disc(sim, 1.0, 32.5 * RES, 0.0, [1.40, 32.5 * RES, 0.0, 0.0])
+    _, _, done = sim.step(STAY)
+    assert done[0] == 0
