@@ -399,8 +399,12 @@ __device__ __forceinline__ void refresh_w(const OptNet &o, int t, long long i, f
     o.WT16[l][(long long)k * o.ld_out[l] + r] = h;
 }
 
+// With tau > 0, Tg holds target networks of the same shapes: each target
+// parameter then takes its Polyak step from the new value in the same pass
+// (what polyak_fused would do after this kernel, element by element).
 __global__ void adam_fused(const OptGroup G, int n_cta, float lr, float b1, float b2,
-                           const float *__restrict__ corr, float wd) {
+                           const float *__restrict__ corr, float wd, const OptGroup Tg,
+                           float tau) {
     pdl_enter();
     const OptNet &o = G.net[blockIdx.y];
     const long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -424,6 +428,12 @@ __global__ void adam_fused(const OptGroup G, int n_cta, float lr, float b1, floa
     const float pn = pd - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
     o.p[t][i] = pn;
     refresh_w(o, t, i, pn);
+    if (tau > 0.0f) {
+        const OptNet &tn = Tg.net[blockIdx.y];
+        const float tv = (1.0f - tau) * tn.p[t][i] + tau * pn;
+        tn.p[t][i] = tv;
+        refresh_w(tn, t, i, tv);
+    }
 }
 
 __global__ void polyak_fused(const OptGroup G, float tau) {
@@ -504,16 +514,22 @@ int launch_mlp_bwd_fused(const FGroup &g, void *stream) {
 }
 
 int launch_adam_fused(Mlp *const *nets, float *const *part, int n_nets, int n_cta, float lr,
-                      float b1, float b2, const float *corr, float wd, void *stream) {
-    OptGroup G{};
+                      float b1, float b2, const float *corr, float wd, void *stream,
+                      Mlp *const *targets, float tau) {
+    OptGroup G{}, Tg{};
     long long mx = 0;
     for (int k = 0; k < n_nets; ++k) {
         fill_opt(*nets[k], G.net[k]);
         G.net[k].part = part ? part[k] : nullptr;
         mx = mx > G.net[k].total ? mx : G.net[k].total;
+        if (targets) {
+            fill_opt(*targets[k], Tg.net[k]);
+            if (Tg.net[k].total != G.net[k].total) return (int)cudaErrorInvalidValue;
+        }
     }
     launch_pdl(adam_fused, dim3((unsigned)((mx + 255) / 256), n_nets), 256, 0,
-                 static_cast<cudaStream_t>(stream), G, n_cta, lr, b1, b2, corr, wd);
+               static_cast<cudaStream_t>(stream), G, n_cta, lr, b1, b2, corr, wd, Tg,
+               targets ? tau : 0.0f);
     return (int)cudaGetLastError();
 }
 

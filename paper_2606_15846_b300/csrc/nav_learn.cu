@@ -1182,8 +1182,8 @@ int fbwd(nav_trainer *T, Mlp *const *nets, int n, float *const *dout, const int 
 }
 
 // One critic update (and the actor update that falls on it) on the fused
-// passes: the same arithmetic as the per-layer path in 9 launches (FastDSAC
-// critic step; 17-18 with an actor step), each launched with programmatic
+// passes: the same arithmetic as the per-layer path in 8 launches (FastDSAC
+// critic step; 16-17 with an actor step), each launched with programmatic
 // dependent launch.
 int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
@@ -1237,8 +1237,10 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
                    T->dq[1], T->scal + 4, c.tau_b, T->ticket);
     }
     rc |= fbwd(T, qs, 2, T->dq, qslot, T->XcT, T->part_q, nullptr, 0, st);
+    // the critics' Adam step and the target critics' Polyak step in one pass
+    // (nothing after it in the update reads the targets)
     rc |= launch_adam_fused(qs, T->part_q, 2, T->n_cta, c.lr_critic, c.beta1, c.beta2, T->corr,
-                            c.weight_decay, st);
+                            c.weight_decay, st, qts, c.tau);
     if (actor_step) {
         // the actor's own action a, written into Xa's action columns too
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0xA5A5ull, T->ctr, kCtrActor, 2u, 0u,
@@ -1265,7 +1267,6 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
                    B, c.target_entropy, c.lr_alpha, c.beta1, c.beta2, T->corr + 2,
                    T->ipap > 0 ? T->scal + 12 : nullptr, c.lr_actor, c.ipap_beta_max);
     }
-    rc |= launch_polyak_fused(qts, qs, 2, c.tau, st);
     rc |= (int)cudaGetLastError();
     return rc;
 }

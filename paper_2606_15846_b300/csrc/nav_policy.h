@@ -117,8 +117,12 @@ int launch_mlp_bwd_fused(const FGroup &g, void *stream);
 // gradients are the sums of n_cta partials (written back to gW / gb for
 // inspection), or, with gWp_base null, the layers' gW / gb themselves; BF16
 // copies refreshed.  corr: device bias corrections.
+// With `targets` (networks of the same shapes), each target parameter also
+// takes its Polyak step target <- (1 - tau) target + tau new in the same
+// pass, its BF16 copies refreshed.
 int launch_adam_fused(Mlp *const *nets, float *const *gWp_base, int n_nets, int n_cta, float lr,
-                      float b1, float b2, const float *corr, float wd, void *stream);
+                      float b1, float b2, const float *corr, float wd, void *stream,
+                      Mlp *const *targets = nullptr, float tau = 0.0f);
 // Polyak averaging tgt <- (1 - tau) tgt + tau src of up to two networks, with
 // the targets' BF16 copies refreshed.
 int launch_polyak_fused(Mlp *const *tgt, Mlp *const *src, int n_nets, float tau, void *stream);
