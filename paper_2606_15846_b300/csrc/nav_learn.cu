@@ -590,14 +590,39 @@ __device__ __forceinline__ void c51_stats(const float *l, int n, float v_min, fl
     mean = warp_sum(zs) / sum;
 }
 
+// Cross-entropy of sample b's logits to the target row mr (one warp):
+// dL/dlogits = (softmax - m) / B; acc[1] += loss
+__device__ __forceinline__ void c51_ce_row(const float *__restrict__ q, const float *mr, int b,
+                                           int B, int n, float *dq, float *acc) {
+    const int lane = threadIdx.x & 31;
+    const float *l = q + (size_t)b * n;
+    float mv = -INFINITY;
+    for (int i = lane; i < n; i += 32) mv = fmaxf(mv, l[i]);
+    const float mx = warp_max(mv);
+    float s = 0.0f;
+    for (int i = lane; i < n; i += 32) s += expf(l[i] - mx);
+    const float sum = warp_sum(s);
+    const float lse = mx + logf(sum), inv = 1.0f / sum, ib = 1.0f / (float)B;
+    float ll = 0.0f;
+    for (int i = lane; i < n; i += 32) {
+        ll -= mr[i] * (l[i] - lse);
+        dq[(size_t)b * n + i] = (expf(l[i] - mx) * inv - mr[i]) * ib;
+    }
+    ll = warp_sum(ll);
+    if (lane == 0) atomicAdd(&acc[1], ll);
+}
+
 // Target distribution m [B][n]: the target critic with the smaller expected
 // value, atoms moved to rs r + gamma (1 - term) (z - alpha logpi') and
 // clipped, projected back by linear interpolation (shared-memory bins).
+// With qc0 (and qc1, dq0, dq1, acc), the same warp then forms both
+// critics' cross-entropy gradients from the row it holds.
 __global__ void __launch_bounds__(256) k_c51_targets(
     const float *__restrict__ rew, const float *__restrict__ term, const float *__restrict__ tl1,
     const float *__restrict__ tl2, const float *__restrict__ logp_next,
     const float *__restrict__ log_alpha, int B, int n, float gamma, float rs, float v_min,
-    float v_max, float *m) {
+    float v_max, float *m, const float *__restrict__ qc0, const float *__restrict__ qc1,
+    float *dq0, float *dq1, float *acc) {
     pdl_enter();
     __shared__ float bins[8][kFusedMaxWidth];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -629,41 +654,11 @@ __global__ void __launch_bounds__(256) k_c51_targets(
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) m[(size_t)b * n + i] = bins[w][i];
-}
-
-// Cross-entropy to m: dL/dlogits = (softmax - m) / B; acc[1] += loss
-__device__ __forceinline__ void c51_critic_grad(const float *__restrict__ q,
-                                                const float *__restrict__ m, int B, int n, float *dq,
-                                                float *acc) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * 8 + w;
-    if (b >= B) return;
-    const float *l = q + (size_t)b * n, *mr = m + (size_t)b * n;
-    float mv = -INFINITY;
-    for (int i = lane; i < n; i += 32) mv = fmaxf(mv, l[i]);
-    const float mx = warp_max(mv);
-    float s = 0.0f;
-    for (int i = lane; i < n; i += 32) s += expf(l[i] - mx);
-    const float sum = warp_sum(s);
-    const float lse = mx + logf(sum), inv = 1.0f / sum, ib = 1.0f / (float)B;
-    float ll = 0.0f;
-    for (int i = lane; i < n; i += 32) {
-        ll -= mr[i] * (l[i] - lse);
-        dq[(size_t)b * n + i] = (expf(l[i] - mx) * inv - mr[i]) * ib;
+    // both critics' cross-entropy gradients against this target row
+    if (qc0) {
+        c51_ce_row(qc0, bins[w], b, B, n, dq0, acc);
+        c51_ce_row(qc1, bins[w], b, B, n, dq1, acc);
     }
-    ll = warp_sum(ll);
-    if (lane == 0) atomicAdd(&acc[1], ll);
-}
-
-// C51 critic gradients of both critics in one launch (blockIdx.y selects
-// the critic)
-__global__ void __launch_bounds__(256) k_c51_critic_grad2(const float *__restrict__ q0,
-                                                          const float *__restrict__ q1,
-                                                          const float *__restrict__ m, int B, int n,
-                                                          float *dq0, float *dq1, float *acc) {
-    pdl_enter();
-    const bool one = blockIdx.y == 1;
-    c51_critic_grad(one ? q1 : q0, m, B, n, one ? dq1 : dq0, acc);
 }
 
 // Actor loss mean(alpha logp - min_j E[Q_j]): dL/dlogp, and dL/dlogits of the
@@ -1227,9 +1222,7 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
     if (c51) {
         launch_pdl(k_c51_targets, blocks(B, 8), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
                    T->logp_next, T->scal + 0, B, T->qout, c.gamma, c.reward_scale, c.v_min,
-                   c.v_max, T->tdist);
-        launch_pdl(k_c51_critic_grad2, dim3(blocks(B, 8), 2), 256, 0, st, T->qo[0], T->qo[1],
-                   T->tdist, B, T->qout, T->dq[0], T->dq[1], T->scal + 4);
+                   c.v_max, T->tdist, T->qo[0], T->qo[1], T->dq[0], T->dq[1], T->scal + 4);
     } else {
         launch_pdl(k_targets_grad2, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1],
                    T->logp_next, T->scal + 0, B, c.gamma, c.reward_scale, c.seed, T->ctr, T->y,
