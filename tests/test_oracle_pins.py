@@ -822,3 +822,43 @@ def test_robot_collides_with_a_stamped_cell_only(oracle):
     _set_disc(sim, 1.0, 32.5 * RES, 0.0, [1.40, 32.5 * RES, 0.0, 0.0])
     _, _, done = sim.step(STAY)
     assert done[0] == 0
+
+
+def _pick(h, n):
+    return ((h >> 32) * n) >> 32
+
+
+def test_goal_falls_back_to_the_draw_nearest_the_band(oracle):
+    """Sec. 2.2.3 reset with an unreachable band: in a 1.2 m room no two
+    spawnable cells are 2 m apart, so all 64 goal draws miss [2, 8] m and the
+    goal is the draw closest to the band (the farthest one; the first on
+    ties).  Brute force over the 64 draws from the published hash and the
+    component lists (both pinned above)."""
+    occ = np.zeros((24, 24), np.uint8)
+    params = W.Params(goal_dmin=2.0, goal_dmax=8.0)
+    sim = oracle.OracleSim([occ], np.zeros(4, np.int32), np.full(4, 8, np.int32),
+                           np.zeros(4, np.int32), [W.DISC], 2.0, params, RES)
+    seed = 5
+    sim.reset(seed)
+    f, _, _ = sim.get_state()
+    labels = sim.comp_labels(0).ravel()
+    spawn = np.flatnonzero(labels >= 0)  # spawnable cells, ascending
+    f32 = np.float32
+    for e in range(4):
+        cell = int(spawn[_pick(oracle.hash64(seed, e, 0, 0), len(spawn))])
+        x = (f32(cell % 24) + f32(0.5)) * f32(RES)
+        y = (f32(cell // 24) + f32(0.5)) * f32(RES)
+        comp = spawn[labels[spawn] == labels[cell]]
+        best, bx, by = np.inf, x, y
+        for a in range(64):
+            gc = int(comp[_pick(oracle.hash64(seed, e, 0, 2 + a), len(comp))])
+            gx = (f32(gc % 24) + f32(0.5)) * f32(RES)
+            gy = (f32(gc // 24) + f32(0.5)) * f32(RES)
+            dx, dy = gx - x, gy - y
+            d = np.sqrt(dx * dx + dy * dy)
+            assert d < 2.0
+            err = f32(2.0) - d
+            if err < best:
+                best, bx, by = err, gx, gy
+        assert f[e, 0] == x and f[e, 1] == y
+        assert f[e, 5] == bx and f[e, 6] == by
