@@ -862,3 +862,37 @@ def test_goal_falls_back_to_the_draw_nearest_the_band(oracle):
                 best, bx, by = err, gx, gy
         assert f[e, 0] == x and f[e, 1] == y
         assert f[e, 5] == bx and f[e, 6] == by
+
+
+def test_moving_discs_drawn_at_reset_by_their_rule(oracle):
+    """Moving discs at reset: disc q takes the first of 16 spawn-cell draws
+    at least dyn_min_sep from the robot (else the 16th), speed U[0, max) and
+    a uniform heading from one more draw; brute force from the published hash
+    and the spawn list."""
+    occ = np.zeros((40, 40), np.uint8)
+    params = W.Params(goal_dmin=0.0, goal_dmax=1e9, n_dyn=3, dyn_min_sep=0.8,
+                      dyn_speed_max=0.5)
+    sim = oracle.OracleSim([occ], np.zeros(3, np.int32), np.full(3, 8, np.int32),
+                           np.zeros(3, np.int32), [W.DISC], 2.0, params, RES)
+    seed = 11
+    sim.reset(seed)
+    f, _, d = sim.get_state()
+    spawn = np.flatnonzero(sim.comp_labels(0).ravel() >= 0)
+    f32 = np.float32
+    two_pi, pi = f32(6.2831853071795864769), f32(3.14159265358979323846)
+    for e in range(3):
+        x, y = f[e, 0], f[e, 1]
+        for q in range(3):
+            for a in range(16):
+                oc = int(spawn[_pick(oracle.hash64(seed, e, 0, 1024 + 64 * q + a), len(spawn))])
+                ox = (f32(oc % 40) + f32(0.5)) * f32(RES)
+                oy = (f32(oc // 40) + f32(0.5)) * f32(RES)
+                dx, dy = ox - x, oy - y
+                if np.sqrt(dx * dx + dy * dy) >= f32(0.8):
+                    break
+            hv = oracle.hash64(seed, e, 0, 1024 + 64 * q + 48)
+            sp = f32(hv >> 40) * f32(1.0 / 16777216.0) * f32(0.5)
+            hd = f32((hv >> 8) & 0xFFFFFF) * f32(1.0 / 16777216.0) * two_pi - pi
+            sh, ch = oracle.sincosf(float(hd))
+            assert d[e, q, 0] == ox and d[e, q, 1] == oy
+            assert d[e, q, 2] == sp * ch and d[e, q, 3] == sp * sh
