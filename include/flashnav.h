@@ -219,7 +219,14 @@ int nav_get_stats(nav_handle *h, uint64_t *visits, uint64_t *rays);
  *                  step as an env-phase kernel then a ray kernel whose CTAs
  *                  keep every map resident and whose warps take 32-ray chunks
  *                  from a queue (no per-tile barriers); 2: the fused tiled
- *                  kernel.  nav_get_launch reports the path in use (1 or 2).
+ *                  kernel; 4: the fused tiled kernel whose ray phase
+ *                  refills lanes (exact traversal over distance bytes,
+ *                  without moving discs; otherwise as 2): a tile's rays
+ *                  form one range, every lane walks its own ray and a warp
+ *                  with idle lanes takes as many new rays as it has idle
+ *                  lanes from a shared counter, instead of retiring 32-ray
+ *                  chunks when their slowest ray ends.  3 is rejected.
+ *                  nav_get_launch reports the path in use (1, 2 or 4).
  * 0 keeps the current value.  A new handle starts at tile_envs 8, 512
  * threads, 160 KiB, 40 registers, byte_cells 1, fused kernel.  Synchronises
  * the handle's stream. */
@@ -238,7 +245,8 @@ int nav_get_tile_order(const nav_handle *h, int *order);
 /* Autotuner (no paper counterpart; it picks the launch shape for this
  * handle's mix of map sizes, beam counts and robots).  From a device copy of
  * the current state it times `steps` steps of each candidate with uniform
- * random actions: first tile_envs x block_threads x max_regs, then the
+ * random actions: first tile_envs x block_threads x max_regs, with chunked
+ * and (when eligible) refilled lanes, then the
  * staging mode and shared-memory budget for the best shape, then the tile
  * order, then the split step when eligible.  It restores the
  * state and keeps the fastest candidate.  Synchronous.  best_ms (host, may be

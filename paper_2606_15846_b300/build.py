@@ -19,7 +19,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_GEOMETRY = ["nav_step.cu", "nav_flow.cu"]
+CU_GEOMETRY = ["nav_step.cu"]
 CU_DEFAULT = ["nav_noalloc.cu", "nav_mlp.cu", "nav_fused.cu", "nav_policy.cu", "nav_learn.cu",
               "nav_gather.cu"]
 CPP = ["nav_api.cpp"]

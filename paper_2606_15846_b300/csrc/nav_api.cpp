@@ -161,19 +161,6 @@ struct nav_handle {
     int2 *d_chunks = nullptr;
     int chunks_cap = 0;
     bool split_ok = false; // every map (and beam table) fits in one CTA's shared memory
-    bool flow_ok = false;  // the pipelined step can run this handle (see nav_flow.cu)
-    // pipelined step: per-launch group plans (whole step, host-step parts)
-    struct FlowDev {
-        int *beg = nullptr, *end = nullptr, *map = nullptr, *tab = nullptr, *ncta = nullptr;
-        int *cta = nullptr, *next = nullptr;
-        int n_groups = 0;
-    };
-    FlowDev flow_all;
-    std::vector<FlowDev> flow_parts;
-    int *d_flow = nullptr; // every plan's arrays, packed
-    size_t flow_cap = 0;   // ints in d_flow
-    int *d_flow_q = nullptr;
-    int n_sm = 0;
     float *d_dbg_range = nullptr;
     int *d_dbg_hit = nullptr;
     unsigned *d_dbg_vis = nullptr;
@@ -279,137 +266,9 @@ float sample_ray_cost(const nav_map &mp, float rmax_c) {
     return n ? (float)(total / n) : 1.0f;
 }
 
-// Pipelined-step plan over perm[lo, hi) (sorted by map, then beam table):
-// groups = runs of one (map, beam table); each group's home CTAs are a
-// share of the n_cta CTAs proportional to its estimated ray cost (envs x
-// beams x the map's sampled cells per ray), by largest remainders; CTA c
-// starts on group cta[c].
-struct FlowPlanHost {
-    std::vector<int> beg, end, map, tab, ncta, cta;
-};
-
-void plan_groups(const nav_handle *h, const std::vector<int> &perm, int lo, int hi, int n_cta,
-                 FlowPlanHost &P) {
-    std::vector<double> cost;
-    int s = lo;
-    while (s < hi) {
-        int t = s;
-        while (t < hi && h->env_map[perm[t]] == h->env_map[perm[s]] &&
-               h->env_tab[perm[t]] == h->env_tab[perm[s]])
-            ++t;
-        P.beg.push_back(s);
-        P.end.push_back(t);
-        P.map.push_back(h->env_map[perm[s]]);
-        P.tab.push_back(h->env_tab[perm[s]]);
-        cost.push_back((double)(t - s) * h->env_k[perm[s]] * h->map_ray_cost[h->env_map[perm[s]]]);
-        s = t;
-    }
-    const int G = (int)P.beg.size();
-    double total = 0.0;
-    for (double c : cost) total += c;
-    P.ncta.assign(G, 0);
-    std::vector<std::pair<double, int>> rem;
-    int given = 0;
-    for (int g = 0; g < G; ++g) {
-        const double share = total > 0.0 ? cost[g] / total * n_cta : 0.0;
-        P.ncta[g] = (int)share;
-        given += P.ncta[g];
-        rem.push_back({share - P.ncta[g], g});
-    }
-    std::stable_sort(rem.begin(), rem.end(),
-                     [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-                         return a.first > b.first;
-                     });
-    for (size_t i = 0; given < n_cta && i < rem.size(); ++i, ++given) ++P.ncta[rem[i].second];
-    P.cta.clear();
-    for (int g = 0; g < G; ++g)
-        for (int c = 0; c < P.ncta[g]; ++c) P.cta.push_back(g);
-    P.cta.resize(n_cta, -1);
-}
-
-// Builds the pipelined step's plans (whole step and each host-step part) and
-// uploads them; a no-op for handles the pipelined step cannot run.
-int build_flow(nav_handle *h, const std::vector<int> &perm, const std::vector<int> &pperm) {
-    if (!h->flow_ok) return NAV_OK;
-    if (h->n_sm <= 0) {
-        cudaError_t e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute(SMs)");
-    }
-    std::vector<FlowPlanHost> plans(1);
-    plan_groups(h, perm, 0, h->n_envs, h->n_sm, plans[0]);
-    const int P = (int)h->part_env_off.size() - 1;
-    for (int p = 0; p < P; ++p) {
-        plans.emplace_back();
-        plan_groups(h, pperm, h->part_env_off[p], h->part_env_off[p + 1], h->n_sm, plans.back());
-    }
-    size_t need = 0;
-    for (const FlowPlanHost &q : plans) need += 6 * q.beg.size() + q.cta.size();
-    cudaError_t e;
-    if (need > h->flow_cap) {
-        e = h->arena.alloc(&h->d_flow, need);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(flow plan)");
-        h->flow_cap = need;
-    }
-    if (!h->d_flow_q) {
-        e = h->arena.alloc(&h->d_flow_q, 1);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(flow queue)");
-        cudaMemset(h->d_flow_q, 0, sizeof(int));
-    }
-    std::vector<int> packed;
-    packed.reserve(need);
-    std::vector<nav_handle::FlowDev> devs;
-    for (const FlowPlanHost &q : plans) {
-        nav_handle::FlowDev d;
-        const int G = (int)q.beg.size();
-        d.n_groups = G;
-        int *base = h->d_flow + packed.size();
-        d.beg = base;
-        d.end = base + G;
-        d.map = base + 2 * G;
-        d.tab = base + 3 * G;
-        d.ncta = base + 4 * G;
-        d.next = base + 5 * G;
-        d.cta = base + 6 * G;
-        packed.insert(packed.end(), q.beg.begin(), q.beg.end());
-        packed.insert(packed.end(), q.end.begin(), q.end.end());
-        packed.insert(packed.end(), q.map.begin(), q.map.end());
-        packed.insert(packed.end(), q.tab.begin(), q.tab.end());
-        packed.insert(packed.end(), q.ncta.begin(), q.ncta.end());
-        packed.insert(packed.end(), (size_t)G, 0);
-        packed.insert(packed.end(), q.cta.begin(), q.cta.end());
-        devs.push_back(d);
-    }
-    e = cudaMemcpy(h->d_flow, packed.data(), packed.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(flow plan)");
-    h->flow_all = devs[0];
-    h->flow_parts.assign(devs.begin() + 1, devs.end());
-    return NAV_OK;
-}
-
-// The pipelined step's fields of a launch over plan d.
-void apply_flow(const nav_handle *h, const nav_handle::FlowDev &d, StepArgs &A) {
-    A.grp_beg = d.beg;
-    A.grp_end = d.end;
-    A.grp_map = d.map;
-    A.grp_tab = d.tab;
-    A.grp_ncta = d.ncta;
-    A.grp_next = d.next;
-    A.cta_grp = d.cta;
-    A.n_groups = d.n_groups;
-    A.flow_q = h->d_flow_q;
-    A.flow_grid = h->n_sm;
-    A.flow_claim = std::max(1, std::min(h->cfg.tile_envs, 32));
-}
-
-bool use_flow(const nav_handle *h) { return h->cfg.flow && h->flow_ok && h->flow_all.n_groups > 0; }
-
 // One step (or reset) of the envs that A covers, on the kernel the handle's
 // launch configuration selects.
-int launch_args(nav_handle *h, StepArgs A, const nav_handle::FlowDev *plan = nullptr) {
-    if (use_flow(h)) {
-        apply_flow(h, plan ? *plan : h->flow_all, A);
-        return launch_step_flow(A, h->stream);
-    }
+int launch_args(nav_handle *h, const StepArgs &A) {
     if (h->cfg.split && h->split_ok) return launch_step_split(A, h->n_envs, h->stream);
     return launch_step(A, h->cfg, h->stream);
 }
@@ -544,7 +403,7 @@ int build_tiles(nav_handle *h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(chunks)");
     h->a.chunks = h->d_chunks;
     h->a.n_chunks = (int)chunks.size();
-    return build_flow(h, perm, pperm);
+    return NAV_OK;
 }
 
 // Chooses each map's staging under the shared-memory cap.  byte_cells 1:
@@ -569,26 +428,6 @@ int set_map_modes(nav_handle *h) {
         region = std::max(region, need);
     }
     h->a.smem_region_bytes = region;
-    // pipelined step: one or two shared buffers of the largest map whose
-    // distance bytes fit the budget; the others are read through L1/L2
-    {
-        int fr = 0;
-        for (const MapDev &m : h->maps)
-            if (m.dist_off >= 0 && m.n_bytes <= h->smem_map_bytes) fr = std::max(fr, m.n_bytes);
-        fr = (fr + 127) & ~127;
-        StepArgs probe = h->a;
-        probe.flow_bufs = 0;
-        probe.flow_region = 0;
-        const long long fixed = (long long)flow_smem_bytes(probe) + 1024;
-        int bufs = 0;
-        if (fr > 0 && 2ll * fr + fixed <= kFlowSmemBytes) bufs = 2;
-        else if (fr > 0 && (long long)fr + fixed <= kFlowSmemBytes) bufs = 1;
-        bool all = bufs > 0;
-        for (const MapDev &m : h->maps) all = all && m.dist_off >= 0 && m.n_bytes <= fr;
-        h->a.flow_region = bufs ? fr : 0;
-        h->a.flow_bufs = bufs;
-        h->a.flow_all_shared = all ? 1 : 0;
-    }
     if (h->d_maps) {
         cudaError_t e = cudaMemcpy(h->d_maps, h->maps.data(), h->maps.size() * sizeof(MapDev),
                                    cudaMemcpyHostToDevice);
@@ -870,8 +709,6 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     h->a.n_beams_total = (int)beam_c.size();
     h->split_ok = P.n_dyn == 0 &&
                   (long long)h->a.all_words * 4 + (long long)beam_c.size() * 8 <= 200 * 1024;
-    h->flow_ok = P.n_dyn == 0 && P.sensor == 0 && (int)beam_c.size() <= kFlowMaxBeams;
-    for (const MapDev &m : h->maps) h->flow_ok = h->flow_ok && m.dist_off >= 0;
     NAV_UP(d_bc, beam_c);
     NAV_UP(d_bs, beam_s);
     NAV_UP(d_obs_off, obs_off_ll);
@@ -1038,7 +875,7 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, flo
             Ap.tiles = h->d_ptiles + h->part_tile_off[p];
             Ap.n_tiles = h->part_tile_off[p + 1] - h->part_tile_off[p];
             Ap.perm = h->d_pperm;
-            const int lrc = launch_args(h, Ap, use_flow(h) ? &h->flow_parts[p] : nullptr);
+            const int lrc = launch_args(h, Ap);
             if (lrc != 0) return cuda_fail(h, (cudaError_t)lrc, "step kernel launch (part)");
             e = cudaEventRecord(h->part_ev[p], h->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->part_ev[p], 0);
@@ -1234,7 +1071,7 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
         (block_threads % 32) != 0 || (block_threads > 0 && block_threads < 64) ||
         smem_map_bytes < 0 || smem_map_bytes > kMaxSmemMapBytes ||
         !(max_regs == 0 || max_regs == 32 || max_regs == 40 || max_regs == 64) ||
-        byte_cells < 0 || byte_cells > 3 || split < 0 || split > 3)
+        byte_cells < 0 || byte_cells > 3 || split < 0 || split > 4 || split == 3)
         return fail(h, NAV_E_INVAL, "nav_set_launch: out of range");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
@@ -1244,7 +1081,7 @@ int nav_set_launch(nav_handle *h, int tile_envs, int block_threads, int smem_map
     if (byte_cells) h->byte_cells = byte_cells;
     if (split) {
         h->cfg.split = split == 1 ? 1 : 0;
-        h->cfg.flow = split == 3 ? 1 : 0;
+        h->cfg.refill = split == 4 ? 1 : 0;
     }
     int rc = set_map_modes(h);
     if (rc != NAV_OK) return rc;
@@ -1279,7 +1116,8 @@ int nav_get_launch(const nav_handle *h, int *tile_envs, int *block_threads, int 
     if (smem_map_bytes) *smem_map_bytes = h->smem_map_bytes;
     if (max_regs) *max_regs = h->cfg.max_regs;
     if (byte_cells) *byte_cells = h->byte_cells;
-    if (split) *split = use_flow(h) ? 3 : (h->cfg.split && h->split_ok) ? 1 : 2;
+    if (split)
+        *split = (h->cfg.split && h->split_ok) ? 1 : h->cfg.refill ? 4 : 2;
     return NAV_OK;
 }
 
@@ -1369,26 +1207,29 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = INFINITY;
-    h->cfg.flow = 0; // passes 1-3 tune the tiled and split kernels
     LaunchCfg best_cfg = h->cfg;
     int best_cap = h->smem_map_bytes, best_bytes = h->byte_cells;
     // pass 1: launch shape with the current staging choice; the three
     // fastest shapes are timed again with three times the steps
-    const int tiles[] = {1, 2, 4, 8, 16};
+    const int tiles[] = {1, 2, 4, 8, 16, 32};
     const int blocks[] = {128, 256, 512};
     const int regs[] = {32, 40, 64};
+    // refilled lanes apply to the exact traversal without moving discs
+    const int n_refill = (h->par.n_dyn == 0 && h->par.sensor == 0) ? 2 : 1;
     std::vector<std::pair<float, LaunchCfg>> cand;
-    for (int te : tiles) {
-        if (te > 1 && te > h->n_envs) continue;
-        h->cfg.tile_envs = te;
-        if ((rc = build_tiles(h)) != NAV_OK) break;
-        for (int bt : blocks)
-            for (int mr : regs) {
-                h->cfg.block_threads = bt;
-                h->cfg.max_regs = mr;
-                cand.push_back({time_config(h, steps, e0, e1), h->cfg});
-            }
-    }
+    for (int rf = 0; rf < n_refill && rc == NAV_OK; ++rf)
+        for (int te : tiles) {
+            if (te > 1 && te > h->n_envs) continue;
+            h->cfg.tile_envs = te;
+            h->cfg.refill = rf;
+            if ((rc = build_tiles(h)) != NAV_OK) break;
+            for (int bt : blocks)
+                for (int mr : regs) {
+                    h->cfg.block_threads = bt;
+                    h->cfg.max_regs = mr;
+                    cand.push_back({time_config(h, steps, e0, e1), h->cfg});
+                }
+        }
     if (rc == NAV_OK && !cand.empty()) {
         std::sort(cand.begin(), cand.end(),
                   [](const std::pair<float, LaunchCfg> &a, const std::pair<float, LaunchCfg> &b) {
@@ -1459,30 +1300,6 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
             }
             h->cfg.split = 0;
         }
-    }
-    // pass 4: the pipelined step, by the most envs one claim takes and the
-    // shared-memory budget (which decides one or two map buffers)
-    if (rc == NAV_OK && h->flow_ok) {
-        const int claims[] = {4, 8, 16, 32};
-        const int fcaps[] = {80 * 1024, 160 * 1024, kMaxSmemMapBytes};
-        for (int cap : fcaps)
-            for (int cl : claims) {
-                if (rc != NAV_OK) break;
-                h->cfg = best_cfg;
-                h->cfg.split = 0;
-                h->cfg.flow = 1;
-                h->cfg.tile_envs = cl;
-                h->byte_cells = 1;
-                h->smem_map_bytes = cap;
-                if ((rc = set_map_modes(h)) != NAV_OK || (rc = build_tiles(h)) != NAV_OK) break;
-                const float ms = time_config(h, 3 * steps, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    best_cfg = h->cfg;
-                    best_cap = cap;
-                    best_bytes = 1;
-                }
-            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -645,16 +645,29 @@ __device__ void reset_env(const StepArgs &A, const B &bits, const MapDev &M, int
     const int ccount = A.comp_count[cs.comp_off + comp];
     const float dmin = A.p.goal_dmin, dmax = A.p.goal_dmax;
     float bx = x, by = y, berr = INFINITY;
-    for (int a = 0; a < 64; ++a) {
-        const unsigned long long hg = draw64(A.seed, (unsigned)e, episode, 2u + (unsigned)a);
-        const int gc = A.comp_cells[cstart + draw_index(hg, ccount)];
-        const float cx = ((float)(gc % M.w) + 0.5f) * M.res;
-        const float cy = ((float)(gc / M.w) + 0.5f) * M.res;
-        const float ddx = cx - x, ddy = cy - y;
-        const float d = sqrtf(ddx * ddx + ddy * ddy);
-        const float err = d < dmin ? dmin - d : (d > dmax ? d - dmax : 0.0f);
-        if (err < berr) { berr = err; bx = cx; by = cy; }
-        if (err == 0.0f) break;
+    // draws taken in batches of 8: the 8 cell loads are issued together, then
+    // examined in draw order (same result as one draw at a time)
+    bool found = false;
+    for (int a0 = 0; a0 < 64 && !found; a0 += 8) {
+        int gcs[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned long long hg =
+                draw64(A.seed, (unsigned)e, episode, 2u + (unsigned)(a0 + q));
+            gcs[q] = __ldg(A.comp_cells + cstart + draw_index(hg, ccount));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (found) break;
+            const int gc = gcs[q];
+            const float cx = ((float)(gc % M.w) + 0.5f) * M.res;
+            const float cy = ((float)(gc / M.w) + 0.5f) * M.res;
+            const float ddx = cx - x, ddy = cy - y;
+            const float d = sqrtf(ddx * ddx + ddy * ddy);
+            const float err = d < dmin ? dmin - d : (d > dmax ? d - dmax : 0.0f);
+            if (err < berr) { berr = err; bx = cx; by = cy; }
+            if (err == 0.0f) found = true;
+        }
     }
     gx = bx;
     gy = by;

@@ -111,26 +111,12 @@ struct StepArgs {
     int all_words;              // words of every map together
     int n_maps_split;           // maps staged by the ray kernel
     int n_beams_total;          // entries of the concatenated beam tables
-    // pipelined step (nav_flow.cu): envs in perm are grouped by (map, beam
-    // table); group g is perm[grp_beg[g], grp_end[g]), home of grp_ncta[g]
-    // CTAs; CTA c starts on group cta_grp[c] (-1: none)
-    const int *grp_beg, *grp_end, *grp_map, *grp_tab, *grp_ncta;
-    int n_groups;
-    const int *cta_grp;
-    int *grp_next;       // [n_groups] envs claimed per group; zero between launches
-    int *flow_q;         // [0] CTAs finished; zero between launches
-    int flow_region;     // bytes of one shared map buffer (multiple of 128)
-    int flow_bufs;       // shared map buffers (0, 1 or 2)
-    int flow_claim;      // most envs one claim takes (<= 32)
-    int flow_grid;       // CTAs (one per SM)
-    int flow_all_shared; // 1: every map fits a buffer (shared loads only)
 };
 
 enum StatusBits {
     kStatusNoSpawn = 1,
     kStatusCopyTimeout = 2,
-    kStatusBadPose = 4,
-    kStatusFlowTimeout = 8 // a wait of the pipelined step ran out
+    kStatusBadPose = 4
 };
 
 // Defaults: the autotuner's usual choice for 256 x 256 maps with distance
@@ -141,7 +127,7 @@ struct LaunchCfg {
     int max_regs = 40;     // register cap per thread: 32, 40 or 64
     int split = 0;         // 1: env kernel + all-maps-resident ray kernel when eligible
     int order = 0;         // tile queue order: 0 map size x beams, 1 sampled ray cost
-    int flow = 0;          // 1: the pipelined step (nav_flow.cu) when eligible
+    int refill = 0;        // 1: tiled kernel with refilled lanes (exact traversal, no discs)
 };
 
 // Launches one step (or reset) of every tile on `stream`: persistent CTAs,
@@ -151,12 +137,6 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
 // Split step: env phase for every env, then the ray kernel (all maps staged
 // in shared memory once per CTA, warps take 32-ray chunks from a queue).
 int launch_step_split(const StepArgs &a, int n_envs, void *stream);
-
-// Pipelined step: one CTA per SM, producer warp + ray-casting warps.
-int launch_step_flow(const StepArgs &a, void *stream);
-size_t flow_smem_bytes(const StepArgs &a);
-constexpr int kFlowMaxBeams = 4096;    // beam-table entries the pipelined step stages
-constexpr int kFlowSmemBytes = 227 * 1024; // dynamic shared memory of one CTA
 
 // (SMs, resident CTAs per SM) of a kernel at a shared-memory size and block
 // (raises the kernel's dynamic shared-memory limit when needed; cached).

@@ -94,7 +94,207 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
     }
 }
 
-template <bool DYN, bool MARCH, class V>
+// ---------------------------------------------------------------------------
+// Ray phase with refilled lanes (distance-byte views, no moving discs, exact
+// traversal).  The tile's rays form one range [0, envs x K + finals x K);
+// every lane walks its own ray with a branch-free iteration (the lanes of a
+// warp never diverge), and when enough lanes of a warp are idle the warp
+// writes their results and takes as many new rays as it has idle lanes with
+// one shared-memory atomic, so lanes do not idle until the slowest ray of a
+// fixed 32-ray chunk ends.  The arithmetic of a ray is cast_ray's.
+// ---------------------------------------------------------------------------
+constexpr int kTileRefill = 16; // idle lanes that make a warp take new rays
+
+struct TileRay {
+    float tM, tm, tdM, tdm, tM0, tm0, kM, km, adm, offm, nM, t;
+    int b, b0, sbM, sbm, d, tie;
+    int rid; // ray of the tile: slot x K + k, final scans after the tile's own
+    bool stopped;
+};
+
+// Sets up ray rid of the tile (cast_ray's set-up; a blocked or off-map origin
+// ends the ray at once, at its cell or at a padding cell).
+template <class V>
+__device__ __forceinline__ void tile_ray_init(const V &view, const MapDev &M, int rid, int n_main,
+                                              int K, float inv_k, float rmax_c,
+                                              const float2 *beams, const EnvSlot *slots,
+                                              const int *fin_slot, TileRay &R) {
+    const bool fin = rid >= n_main;
+    const int rr = fin ? rid - n_main : rid; // < 2^24: exact as a float
+    int q = (int)((float)rr * inv_k);
+    q -= q * K > rr ? 1 : 0;
+    q += (q + 1) * K <= rr ? 1 : 0;
+    const int k = rr - q * K;
+    const EnvSlot &es = slots[fin ? fin_slot[q] : q];
+    const float sx = fin ? es.fst : es.st, cx = fin ? es.fct : es.ct;
+    const float xc = fin ? es.fxc : es.xc, yc = fin ? es.fyc : es.yc;
+    const float2 ab = beams[k];
+    // Eq. 4: direction of theta + alpha_k by angle addition
+    const float dx = cx * ab.x - sx * ab.y;
+    const float dy = sx * ab.x + cx * ab.y;
+    R.rid = rid;
+    R.kM = R.km = 0.0f;
+    R.t = 0.0f;
+    R.stopped = true;
+    R.b = R.b0 = 0; // a padding cell: an off-map origin reports hit -1
+    R.d = 0;
+    R.tM = R.tm = INFINITY;
+    if (!(xc >= 0.0f && yc >= 0.0f)) return;
+    const float fx = floorf(xc), fy = floorf(yc);
+    const int i0 = (int)fx, j0 = (int)fy;
+    if (i0 >= M.w || j0 >= M.h) return;
+    const int pb = view.stride;
+    R.b = R.b0 = cell_index(view, i0, j0);
+    R.d = view.dist_at(R.b);
+    if (R.d == 0) return;
+    R.stopped = false;
+    int sbx = 0, sby = 0;
+    float tdx = 0.0f, tdy = 0.0f, tx0 = INFINITY, ty0 = INFINITY;
+    if (dx > 0.0f) { sbx = 1; tdx = __frcp_rn(dx); tx0 = ((fx + 1.0f) - xc) * tdx; }
+    else if (dx < 0.0f) { sbx = -1; tdx = __frcp_rn(-dx); tx0 = (xc - fx) * tdx; }
+    if (dy > 0.0f) { sby = pb; tdy = __frcp_rn(dy); ty0 = ((fy + 1.0f) - yc) * tdy; }
+    else if (dy < 0.0f) { sby = -pb; tdy = __frcp_rn(-dy); ty0 = (yc - fy) * tdy; }
+    const bool xmaj = fabsf(dx) >= fabsf(dy);
+    R.tdM = xmaj ? tdx : tdy;
+    R.tM0 = xmaj ? tx0 : ty0;
+    R.tdm = xmaj ? tdy : tdx;
+    R.tm0 = xmaj ? ty0 : tx0;
+    R.sbM = xmaj ? sbx : sby;
+    R.sbm = xmaj ? sby : sbx;
+    const float adM = xmaj ? fabsf(dx) : fabsf(dy), adm = xmaj ? fabsf(dy) : fabsf(dx);
+    R.adm = adm;
+    R.tie = xmaj ? 1 : 0;
+    R.offm = adm > 0.0f ? 1.0f - R.tm0 * adm : 0.0f;
+    R.nM = floorf(__fmaf_rn(rmax_c, adM, 1.0f - R.tM0 * adM));
+    R.tM = R.tM0;
+    R.tm = R.tm0;
+}
+
+// One iteration for the lanes with act set (cast_ray's step or jump),
+// branch-free; a lane whose ray ends moves from act to res.  Idle lanes
+// re-read their own cell, which lies inside the view.
+template <class V>
+__device__ __forceinline__ void tile_ray_step(const V &view, float rmax_c, TileRay &R, bool &act,
+                                              bool &res) {
+    const bool sM = __float_as_int(R.tM) < __float_as_int(R.tm) + R.tie;
+    const float tn = sM ? R.tM : R.tm;
+    const bool go = act && tn <= rmax_c;
+    const float n = fminf((float)R.d - 1.0f, R.nM - R.kM);
+    const float kM2 = R.kM + n;
+    const float T = __fmaf_rn(kM2 - 1.0f, R.tdM, R.tM0);
+    const float km2 = fmaxf(R.km, floorf(__fmaf_rn(T, R.adm, R.offm)));
+    const bool jump = n >= 1.0f && T <= rmax_c && km2 - R.km <= n &&
+                      __fmaf_rn(km2, R.tdm, R.tm0) > T &&
+                      (km2 == R.km || __fmaf_rn(km2 - 1.0f, R.tdm, R.tm0) <= T);
+    const float kMn = jump ? kM2 : (sM ? R.kM + 1.0f : R.kM);
+    const float kmn = jump ? km2 : (sM ? R.km : R.km + 1.0f);
+    const int bn = R.b0 + (int)kMn * R.sbM + (int)kmn * R.sbm;
+    const int dn = view.dist_at(go ? bn : R.b);
+    if (go) {
+        R.kM = kMn;
+        R.km = kmn;
+        R.tM = __fmaf_rn(kMn, R.tdM, R.tM0);
+        R.tm = __fmaf_rn(kmn, R.tdm, R.tm0);
+        R.b = bn;
+        R.t = tn;
+        R.d = dn;
+    }
+    const bool cont = go && dn != 0;
+    R.stopped = R.stopped || (go && dn == 0);
+    res = res || (act && !cont);
+    act = cont;
+}
+
+template <class V>
+__device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev &M,
+                                 const TileDev &T, int K, const float2 *beams,
+                                 const EnvSlot *slots, const int *fin_slot, int n_fin,
+                                 int *next_ray) {
+    const int lane = threadIdx.x & 31;
+    const int n_main = T.env_count * K;
+    const int total = n_main + n_fin * K;
+    const float rmax_c = A.max_range * M.inv_res;
+    const float inv_k = 1.0f / (float)K;
+    const int m = A.p.n_sectors;
+    TileRay R;
+    R.tM = R.tm = INFINITY;
+    R.tdM = R.tdm = R.tM0 = R.tm0 = R.kM = R.km = R.adm = R.offm = R.nM = R.t = 0.0f;
+    R.b = R.b0 = R.sbM = R.sbm = R.d = R.tie = R.rid = 0;
+    R.stopped = false;
+    bool act = false, res = false, more = true;
+    unsigned vis = 0, nrays = 0;
+    int thr = kTileRefill;
+    for (;;) {
+        if (__any_sync(kFull, act)) {
+            for (;;) {
+                tile_ray_step(view, rmax_c, R, act, res);
+                tile_ray_step(view, rmax_c, R, act, res);
+                if (__popc(__ballot_sync(kFull, !act)) >= thr) break;
+            }
+        }
+        if (res) {
+            // cast_ray's results: range, hit cell, visits
+            const bool fin = R.rid >= n_main;
+            const int rr = fin ? R.rid - n_main : R.rid;
+            int q = (int)((float)rr * inv_k);
+            q -= q * K > rr ? 1 : 0;
+            q += (q + 1) * K <= rr ? 1 : 0;
+            const int k = rr - q * K;
+            const EnvSlot &es = slots[fin ? fin_slot[q] : q];
+            const float range = R.stopped ? R.t * M.res : A.max_range;
+            const float c = fminf(range, A.max_range);
+            float *row = (fin ? A.final_obs : A.obs) + es.obs_off;
+            if (m == 0) row[k] = c;
+            else atomicMin(reinterpret_cast<int *>(row + k / (K / m)), __float_as_int(c));
+            const unsigned v = 1u + (unsigned)R.kM + (unsigned)R.km;
+            if (!fin && A.dbg_range) {
+                int hit = -2;
+                if (R.stopped) {
+                    const int jj = R.b / view.stride, ii = R.b - jj * view.stride;
+                    const int i = ii - kPad, j = jj - kPad;
+                    hit = (i < 0 || j < 0 || i >= M.w || j >= M.h) ? -1 : j * M.w + i;
+                }
+                const long long ro = es.ray_off + k;
+                A.dbg_range[ro] = range;
+                A.dbg_hit[ro] = hit;
+                A.dbg_vis[ro] = v;
+            }
+            vis += v;
+            nrays += 1u;
+            res = false;
+        }
+        const unsigned want = __ballot_sync(kFull, !act);
+        if (more && want) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(next_ray, __popc(want));
+            base = __shfl_sync(kFull, base, 0);
+            const int r = base + __popc(want & ((1u << lane) - 1u));
+            if (((want >> lane) & 1u) && r < total) {
+                tile_ray_init(view, M, r, n_main, K, inv_k, rmax_c, beams, slots, fin_slot, R);
+                act = !R.stopped;
+                res = R.stopped;
+            }
+            if (base + __popc(want) >= total) more = false;
+        }
+        if (!more) {
+            if (!__any_sync(kFull, act || res)) break;
+            thr = 32;
+        }
+    }
+    if (A.stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vis += __shfl_xor_sync(kFull, vis, o);
+            nrays += __shfl_xor_sync(kFull, nrays, o);
+        }
+        if (lane == 0 && nrays) {
+            atomicAdd(&A.stats[0], (unsigned long long)vis);
+            atomicAdd(&A.stats[1], (unsigned long long)nrays);
+        }
+    }
+}
+
+template <bool DYN, bool MARCH, bool REFILL, class V>
 __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const MapDev &M,
                                          const TileDev &T, int K, const float2 *sbeam,
                                          EnvSlot *slots, int *fin_slot, int *n_fin, DynEnv *sdyn,
@@ -110,7 +310,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
         if (tid == 0) *n_fin = __popc(m);
     }
     __syncthreads();
-    ray_phase<DYN, MARCH>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
+    if constexpr (REFILL && !DYN && !MARCH && has_dist<V>::value)
+        ray_phase_refill(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, next_chunk);
+    else
+        ray_phase<DYN, MARCH>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
 }
 
 // Persistent CTAs: each CTA takes tiles from a global queue until none are
@@ -120,7 +323,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
 // for the next launch on the stream.
 // MINB: resident 512-thread CTAs per SM the register allocation must allow
 // (4, 3, 2 -> at most 32, 40, 64 registers per thread).
-template <bool DYN, int MINB, bool MARCH>
+template <bool DYN, int MINB, bool MARCH, bool REFILL>
 __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ EnvSlot slots[kMaxTileEnvs];
@@ -189,16 +392,16 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         const int mode = failed ? (int)kMapGlobal : M.mode;
         if (tid == 0) staged_map = mode == kMapGlobal || mode == kMapGlobalBytes ? -1 : T.map;
         if (mode == kMapSharedBytes)
-            run_tile<DYN, MARCH>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH, REFILL>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         else if (mode == kMapSharedBits)
-            run_tile<DYN, MARCH>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH, REFILL>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         else if (mode == kMapGlobalBytes)
-            run_tile<DYN, MARCH>(A, BytesGlobal{A.dist + M.dist_off, M.byte_stride}, M, T, K, sbeam,
+            run_tile<DYN, MARCH, REFILL>(A, BytesGlobal{A.dist + M.dist_off, M.byte_stride}, M, T, K, sbeam,
                                  slots, fin_slot, &n_fin, sdyn, &next_chunk);
         else
-            run_tile<DYN, MARCH>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
+            run_tile<DYN, MARCH, REFILL>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, &next_chunk);
         __syncthreads();
     }
@@ -403,10 +606,10 @@ __global__ void __launch_bounds__(1024, 1) ray_kernel(const StepArgs A) {
     }
 }
 
-template <bool DYN, bool MARCH> const void *pick_kernel(int max_regs) {
-    if (max_regs <= 32) return (const void *)step_kernel<DYN, 4, MARCH>;
-    if (max_regs <= 40) return (const void *)step_kernel<DYN, 3, MARCH>;
-    return (const void *)step_kernel<DYN, 2, MARCH>;
+template <bool DYN, bool MARCH, bool REFILL> const void *pick_kernel(int max_regs) {
+    if (max_regs <= 32) return (const void *)step_kernel<DYN, 4, MARCH, REFILL>;
+    if (max_regs <= 40) return (const void *)step_kernel<DYN, 3, MARCH, REFILL>;
+    return (const void *)step_kernel<DYN, 2, MARCH, REFILL>;
 }
 
 } // namespace
@@ -467,10 +670,12 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
                         (dyn ? (size_t)2 * cfg.tile_envs * sizeof(DynEnv) : 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool march = a.p.sensor == 1;
-    const void *fn = dyn ? (march ? pick_kernel<true, true>(cfg.max_regs)
-                                  : pick_kernel<true, false>(cfg.max_regs))
-                         : (march ? pick_kernel<false, true>(cfg.max_regs)
-                                  : pick_kernel<false, false>(cfg.max_regs));
+    // lane refill applies to the exact traversal without moving discs
+    const void *fn = dyn ? (march ? pick_kernel<true, true, false>(cfg.max_regs)
+                                  : pick_kernel<true, false, false>(cfg.max_regs))
+                         : (march ? pick_kernel<false, true, false>(cfg.max_regs)
+                            : cfg.refill ? pick_kernel<false, false, true>(cfg.max_regs)
+                                         : pick_kernel<false, false, false>(cfg.max_regs));
     int n_sm = 0, per_sm = 0;
     cudaError_t err = (cudaError_t)occupancy(fn, smem, cfg.block_threads, n_sm, per_sm);
     if (err != cudaSuccess) return (int)err;
