@@ -6,12 +6,16 @@ TEST INFRASTRUCTURE ONLY: used by tests/ and the CPU-baseline leg of the
 benchmark; it never imports the CUDA package.  Plain numpy in binary64; the
 matrix product is the only library primitive.
 
-Parity unpinned: the FastDSAC target and critic loss (critic_targets,
-critic_loss) and the clipped-double-Q choice of the C51 target (c51_targets)
-are readings of the paper's prose (Sec. 2.3 gives no equations for them);
-their gradients are pinned to the written losses by finite differences and
-the C51 projection to Bellemare et al.'s definition, but the losses
-themselves have no pin outside this file.
+The FastDSAC target and critic loss (critic_targets, critic_loss) and the
+C51 target (c51_targets) are readings of the paper's prose (Sec. 2.3 gives
+no equations for them).  Outside this file they are pinned by single
+transitions worked by hand (entropy sign, terminal mask, the smaller-mean
+critic and its own sigma, the 3-sigma clip, a three-atom projection), by
+limits with a closed form (zero noise gives the clipped-double-Q soft TD
+target; the NLL's sigma gradient vanishes at the maximum-likelihood sigma;
+the NLL term gives the mean no gradient), and by scipy's Huber loss and
+normal log-density for the unit-weight loss; their gradients are pinned by
+finite differences.
 
 Readings (the paper states FastDSAC only in prose):
 * Eq. 2 (IPAPRec): one trainable beta shared by the agent's networks, moved

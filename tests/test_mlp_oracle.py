@@ -261,3 +261,176 @@ def test_c51_actor_gradient_matches_finite_differences():
     f = lambda: M.c51_actor_grads(logp, l1, l2, 0.3, -20, 20)[0]
     assert _rel(d1, _fd(f, l1)) < 1e-6 and _rel(d2, _fd(f, l2)) < 1e-6
     assert _rel(dlogp, _fd(f, logp)) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Pins of the FastDSAC target and critic loss and of the C51 target that do
+# not go through the oracle's own formulas: single transitions worked by
+# hand (the arithmetic is in each docstring), limits with a closed form, and
+# library routines (scipy's Huber loss and normal log-density).
+# --------------------------------------------------------------------------
+LN2 = math.log(2.0)
+
+
+def test_fastdsac_target_single_transition_by_hand():
+    """r = 1, not terminal, gamma 0.9, reward scale 0.4, alpha 0.2,
+    logpi(a'|s') = -1.5, noise 0.5.  Target critic 1: mean 2, raw scale 0
+    (sigma = softplus(0) + 0.1 = ln 2 + 0.1); critic 2: mean 3.  The smaller
+    mean is critic 1's, so z = 2 + 0.5 (ln 2 + 0.1) = 2.3965735902799725;
+    the entropy bonus -alpha logpi = +0.3 is added:
+    y = 0.4 + 0.9 (z + 0.3) = 2.826916231251975,
+    y_mean = 0.4 + 0.9 (2 + 0.3) = 2.47."""
+    y, ym = M.critic_targets(np.array([1.0]), np.array([0.0]), np.array([[2.0, 0.0]]),
+                             np.array([[3.0, 0.0]]), np.array([-1.5]), 0.2, np.array([0.5]),
+                             0.9, 0.4)
+    z = 2.0 + 0.5 * (LN2 + 0.1)
+    assert y[0] == pytest.approx(0.4 + 0.9 * (z + 0.3), abs=1e-14)
+    assert y[0] == pytest.approx(2.826916231251975, abs=1e-12)
+    assert ym[0] == pytest.approx(2.47, abs=1e-14)
+
+
+def test_fastdsac_target_takes_sigma_from_the_smaller_mean_critic():
+    """Critic 1: mean 5, raw scale 3; critic 2: mean 1, raw scale -2.  The
+    smaller mean is critic 2's, so the draw uses its sigma,
+    ln(1 + e^-2) + 0.1 = 0.22692801104297263 (critic 1's would be
+    ln(1 + e^3) + 0.1 = 3.148587351...): with noise 1, r = 0, no entropy
+    (alpha 0), gamma 1, y = 1 + 0.22692801104297263."""
+    y, ym = M.critic_targets(np.array([0.0]), np.array([0.0]), np.array([[5.0, 3.0]]),
+                             np.array([[1.0, -2.0]]), np.array([0.0]), 0.0, np.array([1.0]),
+                             1.0, 1.0)
+    assert y[0] == pytest.approx(1.0 + math.log1p(math.exp(-2.0)) + 0.1, abs=1e-14)
+    assert ym[0] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_fastdsac_target_terminal_and_entropy_sign():
+    """A terminal transition's target is the scaled reward alone, whatever
+    the critics, the noise and the entropy (the (1 - term) mask); a less
+    random next action (larger logpi) lowers the target by gamma alpha per
+    unit of logpi."""
+    tq1, tq2 = np.array([[7.0, 1.0]]), np.array([[-4.0, 2.0]])
+    y, ym = M.critic_targets(np.array([2.5]), np.array([1.0]), tq1, tq2, np.array([9.0]), 0.7,
+                             np.array([2.0]), 0.99, 0.4)
+    assert y[0] == 1.0 and ym[0] == 1.0
+    ya, _ = M.critic_targets(np.array([0.0]), np.array([0.0]), tq1, tq2, np.array([1.0]), 0.5,
+                             np.array([0.0]), 0.8, 1.0)
+    yb, _ = M.critic_targets(np.array([0.0]), np.array([0.0]), tq1, tq2, np.array([3.0]), 0.5,
+                             np.array([0.0]), 0.8, 1.0)
+    assert yb[0] - ya[0] == pytest.approx(-0.8 * 0.5 * 2.0, abs=1e-12)
+
+
+def test_fastdsac_target_noise_is_clipped_at_three_sigma():
+    """Noise -7 is clipped to -3: z = m - 3 sigma (critic 2, mean -1, raw
+    scale 0: z = -1 - 3 (ln 2 + 0.1))."""
+    y, _ = M.critic_targets(np.array([0.0]), np.array([0.0]), np.array([[4.0, 0.0]]),
+                            np.array([[-1.0, 0.0]]), np.array([0.0]), 0.0, np.array([-7.0]),
+                            1.0, 1.0)
+    assert y[0] == pytest.approx(-1.0 - 3.0 * (LN2 + 0.1), abs=1e-14)
+
+
+def test_fastdsac_target_without_noise_is_the_clipped_double_q_td_target():
+    """Limit sigma' draw -> 0 (noise 0): the sampled target equals the
+    deterministic soft TD target with clipped double Q (Fujimoto et al.
+    2018; Haarnoja et al. 2018), r_s r + gamma (1 - d) (min(Q1', Q2') -
+    alpha logpi'), for every transition of a random batch."""
+    rng = np.random.default_rng(11)
+    B = 64
+    rew, term = rng.normal(size=B), (rng.random(B) < 0.3).astype(float)
+    tq1, tq2 = rng.normal(size=(B, 2)), rng.normal(size=(B, 2))
+    lp = rng.normal(size=B)
+    y, ym = M.critic_targets(rew, term, tq1, tq2, lp, 0.3, np.zeros(B), 0.97, 0.4)
+    td = 0.4 * rew + 0.97 * (1.0 - term) * (np.minimum(tq1[:, 0], tq2[:, 0]) - 0.3 * lp)
+    np.testing.assert_allclose(y, td, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(ym, td, rtol=0, atol=1e-13)
+
+
+def test_fastdsac_critic_loss_with_unit_weight_is_huber_plus_gaussian_nll():
+    """With every sigma equal and sbar^2 = sigma^2 + 1e-6 the weight is 1,
+    and the loss is the batch mean of scipy's Huber loss (delta 50) of
+    m - y_mean plus the Gaussian negative log-density of y under (m, sigma)
+    less its constant (1/2) log(2 pi)."""
+    from scipy import special, stats
+    rng = np.random.default_rng(12)
+    B = 16
+    q = np.stack([rng.normal(0, 80, B), np.full(B, 0.7)], axis=1)  # errors on both Huber branches
+    y, ym = rng.normal(0, 60, B), rng.normal(0, 60, B)
+    s = math.log1p(math.exp(0.7)) + 0.1
+    loss, _ = M.critic_loss(q, y, ym, math.sqrt(s * s + 1e-6), delta=50.0)
+    ref = (special.huber(50.0, q[:, 0] - ym) - stats.norm.logpdf(y, q[:, 0], s)
+           - 0.5 * math.log(2 * math.pi)).mean()
+    assert loss == pytest.approx(ref, rel=1e-12)
+
+
+def test_fastdsac_critic_loss_weight_is_clipped_to_half_and_two():
+    """Table 4's scale range: a tiny sbar gives weight 0.5, a huge one 2
+    (the mean term only; the NLL term is unweighted)."""
+    from scipy import special
+    q = np.array([[3.0, 0.2], [-40.0, -1.0]])
+    y = q[:, 0].copy()  # NLL term at its minimum over m (y - m = 0)
+    ym = np.array([1.0, 100.0])
+    s = np.log1p(np.exp(q[:, 1])) + 0.1
+    nll = np.log(s)
+    for sbar, w in ((1e-6, 0.5), (1e6, 2.0)):
+        loss, _ = M.critic_loss(q, y, ym, sbar, delta=50.0)
+        assert loss == pytest.approx((w * special.huber(50.0, q[:, 0] - ym) + nll).mean(), rel=1e-12)
+
+
+def test_fastdsac_nll_term_gives_the_mean_no_gradient():
+    """The NLL term uses a stop-gradient copy of the mean: with m = y_mean
+    (Huber term flat) the mean's gradient is exactly zero although y != m."""
+    q = np.array([[1.0, 0.3], [-2.0, 1.5]])
+    _, dq = M.critic_loss(q, np.array([4.0, 7.0]), q[:, 0].copy(), 1.0)
+    assert np.all(dq[:, 0] == 0.0)
+
+
+def test_fastdsac_sigma_gradient_vanishes_at_the_maximum_likelihood_sigma():
+    """The Gaussian NLL of one sample y under (m, sigma) is smallest at
+    sigma = |y - m|: choose the raw scale so that softplus(q) + 0.1 = |y - m|
+    (and m = y_mean); the gradient in q is then zero, and positive / negative
+    for sigma above / below it."""
+    m, y = 0.5, 2.5  # |y - m| = 2
+    qr = math.log(math.expm1(2.0 - 0.1))  # softplus(qr) = 1.9
+    for dq_raw, sign in ((0.0, 0), (0.3, 1), (-0.3, -1)):
+        q = np.array([[m, qr + dq_raw]])
+        _, dq = M.critic_loss(q, np.array([y]), np.array([m]), 1.0)
+        if sign == 0:
+            assert abs(dq[0, 1]) < 1e-12
+        else:
+            assert np.sign(dq[0, 1]) == sign
+
+
+def _logits(p):
+    return np.log(np.asarray(p, np.float64))[None, :]
+
+
+def test_c51_target_single_transition_by_hand():
+    """Three atoms on [-1, 1] (spacing 1).  Target critic 1: p = (0.2, 0.5,
+    0.3), mean 0.1; critic 2: p = (0.1, 0.2, 0.7), mean 0.6: critic 1 is the
+    smaller.  r = 0.5, r_s = 1, gamma 0.5, alpha 0.2, logpi' = 0.5:
+    shift = 0.5 - 0.5 * 0.2 * 0.5 = 0.45, scale = 0.5, so the atoms move to
+    (-0.05, 0.45, 0.95), i.e. positions b = (0.95, 1.45, 1.95):
+    atom 0: 0.2 * 0.05 = 0.01 to 0, 0.2 * 0.95 = 0.19 to 1;
+    atom 1: 0.5 * 0.55 = 0.275 to 1, 0.5 * 0.45 = 0.225 to 2;
+    atom 2: 0.3 * 0.05 = 0.015 to 1, 0.3 * 0.95 = 0.285 to 2;
+    target (0.01, 0.48, 0.51), whose mean 0.5 = 0.45 + 0.5 * 0.1."""
+    m = M.c51_targets(np.array([0.5]), np.array([0.0]), _logits([0.2, 0.5, 0.3]),
+                      _logits([0.1, 0.2, 0.7]), np.array([0.5]), 0.2, 0.5, 1.0, -1.0, 1.0)
+    np.testing.assert_allclose(m[0], [0.01, 0.48, 0.51], rtol=0, atol=1e-14)
+    # swapped critics: the same choice (critic 2's distribution is now the smaller)
+    m2 = M.c51_targets(np.array([0.5]), np.array([0.0]), _logits([0.1, 0.2, 0.7]),
+                       _logits([0.2, 0.5, 0.3]), np.array([0.5]), 0.2, 0.5, 1.0, -1.0, 1.0)
+    np.testing.assert_allclose(m2[0], [0.01, 0.48, 0.51], rtol=0, atol=1e-14)
+
+
+def test_c51_target_terminal_and_entropy_sign():
+    """Terminal: every atom collapses onto r_s r = 0.5, half-way between
+    atoms 1 and 2: (0, 0.5, 0.5).  Not terminal, no reward, gamma 1: the
+    mean moves by -alpha logpi' (0.1 for logpi' = -0.5, alpha 0.2)."""
+    m = M.c51_targets(np.array([0.5]), np.array([1.0]), _logits([0.2, 0.5, 0.3]),
+                      _logits([0.1, 0.2, 0.7]), np.array([3.0]), 0.9, 0.5, 1.0, -1.0, 1.0)
+    np.testing.assert_allclose(m[0], [0.0, 0.5, 0.5], rtol=0, atol=1e-14)
+    z = np.array([-1.0, 0.0, 1.0])
+    # no mass (1e-12) on the top atom, so the 0.1 shift clips nothing
+    p = np.array([0.5 - 5e-13, 0.5 - 5e-13, 1e-12])
+    m = M.c51_targets(np.array([0.0]), np.array([0.0]), _logits(p), _logits([1e-3, 1e-3, 0.998]),
+                      np.array([-0.5]), 0.2, 1.0, 1.0, -1.0, 1.0)
+    assert float(m[0] @ z) - float(p @ z) == pytest.approx(0.1, abs=1e-12)
