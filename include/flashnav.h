@@ -163,9 +163,15 @@ int nav_set_host_pipeline(nav_handle *h, int parts);
  * must fit, else NAV_E_INVAL (4096 envs x 360 beams fit without final_obs_host;
  * 2048 envs x 360 beams fit with it).  The handle's device
  * must be current.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls on a device share the array: calls that overlap on the
- * GPU (other threads, other handles, other streams) race.  Synchronous. */
+ * address (cudaGetSymbolAddress); with CUDA's default lazy module loading
+ * that lookup is also when the library's module holding the array is loaded
+ * and the 8 MiB array is placed on the device, which allocates device memory
+ * at that moment.  So make one call on each device during start-up (a
+ * warm-up step of any handle on that device), before any stream capture and
+ * before the phase in which the caller may not allocate; later calls, on any
+ * handle of that device, allocate nothing.  All calls on a device share the
+ * array: calls that overlap on the GPU (other threads, other handles, other
+ * streams) race.  Synchronous. */
 int nav_step_host_noalloc(nav_handle *h, const float *actions_host, float *obs_host,
                           float *reward_host, uint8_t *done_host, float *final_obs_host);
 

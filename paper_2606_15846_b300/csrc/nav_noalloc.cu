@@ -64,7 +64,10 @@ extern "C" int nav_step_host_noalloc(nav_handle *h, const float *actions_host, f
                            "nav_step_host_noalloc: make the handle's device current first");
     unsigned char *base;
     {
-        // one-time set-up per device (the first call on a device does it)
+        // one-time set-up per device (the first call on a device does it;
+        // under lazy module loading this lookup loads this file's module and
+        // places g_stage on the device, so that call should be made at
+        // start-up)
         std::lock_guard<std::mutex> lock(g_stage_mutex);
         if (!g_stage_addr[cur]) {
             void *p = nullptr;

@@ -53,6 +53,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def _rowwise(g, ref, floor=1e-3):
+    """Largest element error scaled by its row's magnitude (plus a floor of
+    the whole matrix's): a few wrong rows or columns (a mis-indexed bias, a
+    bad accumulator lane group) show here although a norm could hide them."""
+    g, ref = np.atleast_2d(np.asarray(g, np.float64)), np.atleast_2d(np.asarray(ref, np.float64))
+    scale = np.abs(ref).max(axis=1, keepdims=True) + floor * np.abs(ref).max() + 1e-30
+    return float((np.abs(g - ref) / scale).max())
+
+
 def _emul_grads(M, params, x16, dout):
     """The GPU's arithmetic with its BF16 rounding points, in FP64: forward on
     BF16 weights with BF16 activations; backward with the upstream gradient
@@ -200,6 +209,9 @@ def run_update(flashnav, torch, name, P, strict=True):
         print(f"[{name}] targets rel err y {_rel(y_gpu, y):.2e}  y_mean {_rel(ym_gpu, ym):.2e}")
         check("y", _rel(y_gpu, y), 2e-2)
         check("y_mean", _rel(ym_gpu, ym), 2e-2)
+        ey = float(np.abs(y_gpu - y).max() / (np.abs(y).max() + 1e-30))
+        print(f"[{name}] targets element-wise max err / max |y| {ey:.2e}")
+        check("y.elem", ey, 5e-2)
     # critic gradients: against the same arithmetic with the GPU's BF16
     # rounding points (tight: checks the kernels), and against pure FP64
     # (the precision cost of BF16 operands, which grows with depth)
@@ -225,6 +237,12 @@ def run_update(flashnav, torch, name, P, strict=True):
             check(f"q{i + 1}.b{li + 1}", eb, fp64_bound)
             check(f"q{i + 1}.W{li + 1}.emul", mW_, 3e-2)
             check(f"q{i + 1}.b{li + 1}.emul", mb_, 3e-2)
+            # element by element, each row against its own scale
+            rW, rb = _rowwise(gW, mW), _rowwise(gb, mb)
+            print(f"[{name}] critic {i + 1} layer {li + 1} element-wise vs BF16-emulated "
+                  f"W {rW:.2e} b {rb:.2e}")
+            check(f"q{i + 1}.W{li + 1}.elem", rW, 1e-1)
+            check(f"q{i + 1}.b{li + 1}.elem", rb, 1e-1)
     # Adam / AdamW first step on the GPU's own gradients
     q1_post = _unpack(_io(lib, T, 1, n_c), sc)
     g1 = _unpack(_io(lib, T, 11, n_c), sc)

@@ -82,3 +82,43 @@ def test_no_alloc_rejects_handles_beyond_its_buffer(fn):
     rc = lib.nav_step_host_noalloc(sim._h, _ptr(a), _ptr(o), _ptr(r), _ptr(d), None)
     assert rc == -1
     assert b"staging bytes" in lib.nav_last_error(sim._h)
+
+
+def _noalloc_step(lib, sim, acts, want_final):
+    o, r, d, f = _buffers(sim, want_final)
+    sim._bind_stream()
+    rc = lib.nav_step_host_noalloc(sim._h, _ptr(np.ascontiguousarray(acts)), _ptr(o), _ptr(r),
+                                   _ptr(d), _ptr(f))
+    assert rc == 0, lib.nav_last_error(sim._h)
+
+
+def test_no_alloc_calls_allocate_no_device_memory(fn):
+    """After one warm-up call on the device (start-up: under lazy module
+    loading that call places the fixed array on the device), a fresh handle's
+    calls leave the device's free memory unchanged, with and without final
+    observations.  The same measurement sees nav_step_host's first call on a
+    fresh handle allocate its staging buffers."""
+    import torch
+    lib = fn.load()
+    wl = W.config_throughput(n_envs=1024, n_maps=4)
+    acts = W.uniform_actions(7, 6, wl.n_envs)
+    warm = fn.NavSim.from_workload(wl)
+    warm.reset(3)
+    _noalloc_step(lib, warm, acts[0], True)
+    sim = fn.NavSim.from_workload(wl)  # a fresh handle
+    sim.reset(5)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for t in range(4):
+        _noalloc_step(lib, sim, acts[t], t % 2 == 1)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0, "nav_step_host_noalloc allocated device memory"
+    # contrast: nav_step_host allocates on its first call on a fresh handle
+    other = fn.NavSim.from_workload(wl)
+    other.reset(5)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    o, r, d, f = _buffers(other, True)
+    other.step_host(np.ascontiguousarray(acts[0]), o, r, d, f)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1
