@@ -377,6 +377,28 @@ int nav_rollout(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t se
                 uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
                 uint8_t *done_dev, int fp32_path);
 
+/* The same rollout with the actor evaluated inside the step kernel (Sec. 2.3
+ * collector, Eq. 7 with the policy in the loop): the actions for obs_dev come
+ * from nav_policy_act once (or, with actions_ready set, are already in
+ * actions_dev: the actions a previous call left there for this obs_dev),
+ * then each of the n_steps launches steps a tile of
+ * up to 128 envs (env phase, ray casts), writes the new observation rows to
+ * obs_dev and, scaled and rounded to BF16, into a tile in shared memory, runs
+ * the actor on that tile on the tensor cores (weights streamed from L2 by
+ * 64-wide chunks, FP32 accumulation in tensor memory) and writes each env's
+ * next action to actions_dev: the policy never reads the observations back
+ * from global memory and there is no separate policy launch.  Step t's
+ * actions use the noise step step0 + t as in nav_rollout (mode 0:
+ * deterministic tanh(mean)).  On return obs_dev, reward_dev and done_dev hold
+ * the last step's values and actions_dev the actions for obs_dev.
+ * Requirements (else NAV_E_INVAL): one beam count K, raw beams (no sectors),
+ * the exact traversal, no moving discs, every map's distance bytes within
+ * ~120 KiB; an actor (K + 4) -> H -> H -> 4 with H <= 256, K + 4 <= 384, no
+ * Eq. 2 input, max_batch >= n_envs. */
+int nav_rollout_fused(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t seed,
+                      uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
+                      uint8_t *done_dev, int actions_ready);
+
 /* FastDSAC learner (Sec. 2.3, FastDSAC paragraph; hyperparameters of Table 4,
  * workload overrides for batch, gamma and the optimiser).  Actor as in
  * nav_policy; twin critics (obs_dim + 2) -> hidden -> hidden -> (mean, raw

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "nav_internal.h"
+#include "nav_policy.h"
 
 using namespace flashnav;
 
@@ -181,6 +182,9 @@ struct nav_handle {
     std::vector<int> part_tile_off, part_env_off;
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> part_ev;
+    // fused act-step rollout: tiles of up to 128 envs
+    TileDev *d_act_tiles = nullptr;
+    int act_tiles_cap = 0, act_n_tiles = 0, act_tile_envs = 0;
 };
 
 namespace {
@@ -1195,6 +1199,127 @@ float time_config(nav_handle *h, int steps, cudaEvent_t e0, cudaEvent_t e1) {
 }
 
 } // namespace
+
+namespace {
+
+// Tiles of at most `te` envs of one (map, beam table) for the fused
+// act-step kernel, over the handle's env order (perm), largest first.
+int build_act_tiles(nav_handle *h, int te) {
+    if (te == h->act_tile_envs && h->d_act_tiles) return NAV_OK;
+    std::vector<int> perm(h->n_envs);
+    cudaError_t e = cudaMemcpy(perm.data(), h->a.perm, perm.size() * sizeof(int),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(perm)");
+    std::vector<TileDev> tiles;
+    int s = 0;
+    const int E = h->n_envs;
+    while (s < E) {
+        int t = s;
+        while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
+               h->env_tab[perm[t]] == h->env_tab[perm[s]])
+            ++t;
+        for (int b = s; b < t; b += te)
+            tiles.push_back(TileDev{h->env_map[perm[s]], h->env_tab[perm[s]], b, std::min(te, t - b)});
+        s = t;
+    }
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const TileDev &x, const TileDev &y) { return x.env_count > y.env_count; });
+    if ((int)tiles.size() > h->act_tiles_cap) {
+        e = h->arena.alloc(&h->d_act_tiles, tiles.size());
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(act tiles)");
+        h->act_tiles_cap = (int)tiles.size();
+    }
+    e = cudaMemcpy(h->d_act_tiles, tiles.data(), tiles.size() * sizeof(TileDev),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(act tiles)");
+    h->act_n_tiles = (int)tiles.size();
+    h->act_tile_envs = te;
+    return NAV_OK;
+}
+
+} // namespace
+
+int nav_rollout_fused(nav_handle *h, nav_policy *p, int n_steps, int mode, uint64_t seed,
+                      uint32_t step0, float *obs_dev, float *actions_dev, float *reward_dev,
+                      uint8_t *done_dev, int actions_ready) {
+    if (!h || !p || !obs_dev || !actions_dev || !reward_dev || !done_dev || n_steps <= 0 ||
+        (mode != 0 && mode != 1))
+        return fail(h, NAV_E_INVAL, "nav_rollout_fused: bad argument");
+    if ((reinterpret_cast<uintptr_t>(actions_dev) & 7u) != 0)
+        return fail(h, NAV_E_INVAL, "nav_rollout_fused: actions must be 8-byte aligned");
+    const StepArgs &H = h->a;
+    const int K = h->env_k.empty() ? 0 : h->env_k[0];
+    bool uniform = true;
+    for (int k : h->env_k) uniform = uniform && k == K;
+    if (!uniform || h->par.n_sectors != 0 || h->par.sensor != 0 || h->par.n_dyn != 0)
+        return fail(h, NAV_E_INVAL,
+                    "nav_rollout_fused: needs one beam count, raw beams, the exact traversal "
+                    "and no moving discs");
+    Mlp *net = policy_actor(p);
+    if (!net || net->n_layers != 3 || policy_ipap(p) != 0 || policy_obs_dim(p) != K + 4 ||
+        K + 4 > 384 || net->layer[0].in != K + 4 || net->layer[0].out > 256 ||
+        net->layer[1].in != net->layer[0].out || net->layer[1].out > 256 ||
+        net->layer[2].in != net->layer[1].out || net->layer[2].out != 4 ||
+        policy_max_batch(p) < h->n_envs)
+        return fail(h, NAV_E_INVAL,
+                    "nav_rollout_fused: the policy must be obs_dim = beams + 4 <= 384 -> H -> H "
+                    "-> 4 with H <= 256, no Eq. 2 input, max_batch >= n_envs");
+    // shared memory: the staged map (or the two 32 KiB weight buffers) and
+    // the 96 KiB input tile
+    int region = 64 * 1024;
+    for (const MapDev &m : h->maps) {
+        if (m.dist_off < 0) return fail(h, NAV_E_INVAL, "nav_rollout_fused: a map has no distance bytes");
+        region = std::max(region, m.n_bytes);
+    }
+    region = (region + 1023) & ~1023;
+    StepArgs A = H;
+    A.smem_region_bytes = region;
+    if (act_step_smem(A) + 8 * 1024 > 227 * 1024)
+        return fail(h, NAV_E_INVAL, "nav_rollout_fused: the maps are too large to stage");
+    // tiles: as many as the SMs take in whole waves, at most 128 envs each
+    int n_sm = 0;
+    cudaError_t ce = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaDeviceGetAttribute");
+    const long long waves = std::max(1LL, ((long long)h->n_envs + 128LL * n_sm - 1) / (128LL * n_sm));
+    const int te = (int)std::max(1LL, std::min(128LL, ((long long)h->n_envs + waves * n_sm - 1) /
+                                                          (waves * n_sm)));
+    int rc = build_act_tiles(h, te);
+    if (rc != NAV_OK) return rc;
+    // the first action from the current observation (the inference path),
+    // unless the previous call left it in actions_dev
+    if (!actions_ready) {
+        rc = nav_policy_act(p, obs_dev, K + 4, h->n_envs, mode, seed, step0, actions_dev, nullptr,
+                            nullptr, h->stream);
+        if (rc != NAV_OK) return fail(h, rc, "nav_rollout_fused: first action");
+    }
+    A.seed = h->seed;
+    A.mode = 0;
+    A.actions = actions_dev;
+    A.obs = obs_dev;
+    A.reward = reward_dev;
+    A.done = done_dev;
+    A.final_obs = nullptr;
+    A.tiles = h->d_act_tiles;
+    A.n_tiles = h->act_n_tiles;
+    ActArgs P{};
+    for (int l = 0; l < 3; ++l) {
+        P.W[l] = static_cast<const __nv_bfloat16 *>(net->layer[l].W16);
+        P.b[l] = net->layer[l].b;
+        P.ld[l] = net->layer[l].ld_in;
+        P.in[l] = net->layer[l].in;
+        P.out[l] = net->layer[l].out;
+    }
+    P.scale = policy_scale(p);
+    P.act = actions_dev;
+    P.mode = mode;
+    P.seed = seed;
+    for (int t = 0; t < n_steps; ++t) {
+        P.step = step0 + (uint32_t)t + 1u;
+        const int lrc = launch_act_step(A, P, h->stream);
+        if (lrc != 0) return cuda_fail(h, (cudaError_t)lrc, "act-step kernel launch");
+    }
+    return NAV_OK;
+}
 
 int nav_autotune(nav_handle *h, int steps, float *best_ms) {
     if (!h || steps <= 0) return fail(h, NAV_E_INVAL, "nav_autotune: bad argument");

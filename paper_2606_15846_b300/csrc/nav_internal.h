@@ -3,6 +3,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "../../include/flashnav.h"
 
 namespace flashnav {
@@ -141,6 +143,26 @@ int launch_step_split(const StepArgs &a, int n_envs, void *stream);
 // (SMs, resident CTAs per SM) of a kernel at a shared-memory size and block
 // (raises the kernel's dynamic shared-memory limit when needed; cached).
 int occupancy(const void *fn, size_t smem, int block, int &n_sm, int &per_sm);
+
+// The actor of the fused act-step kernel: a network in -> H -> H -> 4 with
+// H <= 256 and in <= 384 (BF16 W [out][ld] K-major, FP32 bias), the input
+// scale (null: none), and the head's noise: act[e] receives the action for
+// the next step of env e (mode 1: a = tanh(u + sigma eps), eps keyed by
+// (seed, e, step); mode 0: tanh(u)).
+struct ActArgs {
+    const __nv_bfloat16 *W[3];
+    const float *b[3];
+    int ld[3], in[3], out[3];
+    const float *scale;
+    float *act;
+    int mode;
+    unsigned long long seed;
+    unsigned step;
+};
+// One fused step + actor of every tile (tiles of <= 128 envs, exact
+// traversal over staged distance bytes, no moving discs, raw beams).
+int launch_act_step(const StepArgs &a, const ActArgs &p, void *stream);
+size_t act_step_smem(const StepArgs &a);
 
 // Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step).
 int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,

@@ -364,6 +364,9 @@ struct nav_policy {
 namespace flashnav {
 Mlp *policy_actor(nav_policy *p) { return p ? &p->actor : nullptr; }
 int policy_ipap(const nav_policy *p) { return p ? p->ipap : 0; }
+int policy_obs_dim(const nav_policy *p) { return p ? p->obs_dim : 0; }
+int policy_max_batch(const nav_policy *p) { return p ? p->max_batch : 0; }
+const float *policy_scale(const nav_policy *p) { return p ? p->scale : nullptr; }
 float *policy_beta(nav_policy *p) { return p ? p->beta : nullptr; }
 } // namespace flashnav
 

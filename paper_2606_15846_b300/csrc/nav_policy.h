@@ -136,5 +136,8 @@ namespace flashnav {
 // float holding its beta.
 Mlp *policy_actor(nav_policy *p);
 int policy_ipap(const nav_policy *p);
+int policy_obs_dim(const nav_policy *p);
+int policy_max_batch(const nav_policy *p);
+const float *policy_scale(const nav_policy *p); // per-feature input scale (null: none)
 float *policy_beta(nav_policy *p);
 } // namespace flashnav

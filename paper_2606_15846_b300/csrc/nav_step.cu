@@ -21,8 +21,11 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "nav_geom.cuh"
 #include "nav_internal.h"
+#include "tc_util.cuh"
 
 namespace flashnav {
 namespace {
@@ -104,6 +107,47 @@ __device__ void ray_phase(const StepArgs &A, const B &bits, const MapDev &M, con
 // fixed 32-ray chunk ends.  The arithmetic of a ray is cast_ray's.
 // ---------------------------------------------------------------------------
 constexpr int kTileRefill = 16; // idle lanes that make a warp take new rays
+
+// Byte offset of element (row, col) of the fused act-step kernel's actor
+// input tile: 128 rows, 64-wide K chunks of 16 KiB, 128-byte swizzle (the
+// tensor cores' K-major operand layout).
+__device__ __forceinline__ unsigned act_swz(int row, int col) { return swz(row, col, 128u * 128u); }
+
+// 8 floats as 8 BF16 in one 16-byte word
+__device__ __forceinline__ uint4 act_pack8(const float *v) {
+    uint4 u;
+    unsigned *w = reinterpret_cast<unsigned *>(&u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<const unsigned *>(&h);
+    }
+    return u;
+}
+
+// TMEM columns for the CTA (warp 0 allocates; every thread gets the base).
+__device__ __forceinline__ unsigned tmem_alloc_cols(unsigned *slot, unsigned ncols) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *slot;
+}
+
+__device__ __forceinline__ void tmem_free_cols(unsigned tmem, unsigned ncols) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ncols)
+                     : "memory");
+}
 
 struct TileRay {
     float tM, tm, tdM, tdm, tM0, tm0, kM, km, adm, offm, nM, t;
@@ -205,11 +249,15 @@ __device__ __forceinline__ void tile_ray_step(const V &view, float rmax_c, TileR
     act = cont;
 }
 
+// With xt set (the fused act-step kernel), each range also goes, times
+// xscale[k] (if set) and rounded to BF16, into row q (the env's place in the
+// tile), column k of the actor's swizzled input tile at xt.
 template <class V>
 __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev &M,
                                  const TileDev &T, int K, const float2 *beams,
                                  const EnvSlot *slots, const int *fin_slot, int n_fin,
-                                 int *next_ray) {
+                                 int *next_ray, unsigned char *xt = nullptr,
+                                 const float *xscale = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n_main = T.env_count * K;
     const int total = n_main + n_fin * K;
@@ -246,6 +294,9 @@ __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev 
             float *row = (fin ? A.final_obs : A.obs) + es.obs_off;
             if (m == 0) row[k] = c;
             else atomicMin(reinterpret_cast<int *>(row + k / (K / m)), __float_as_int(c));
+            if (xt && !fin)
+                *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(q, k)) =
+                    __float2bfloat16_rn(xscale ? c * __ldg(xscale + k) : c);
             const unsigned v = 1u + (unsigned)R.kM + (unsigned)R.km;
             if (!fin && A.dbg_range) {
                 int hit = -2;
@@ -410,6 +461,235 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         const int done = atomicAdd(&A.tile_queue[1], 1);
         if (done == (int)gridDim.x - 1) {
             // every CTA has taken its last (empty) tile: reset for the next launch
+            A.tile_queue[0] = 0;
+            A.tile_queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused act-step kernel: the step of a tile of up to 128 envs (env phase,
+// refilled ray phase) and then the FastDSAC actor (Sec. 2.3; Sec. 2.1 MLP)
+// on the tile's new observations, on the tensor cores, from shared memory:
+// the observation rows the ray and env phases produce are written, scaled
+// and rounded to BF16, straight into the actor's swizzled input tile; the
+// three layers (in -> H -> H -> 4, LeakyReLU) stream their weights by
+// 64-wide K chunks (cp.async into two 32 KiB buffers that reuse the staged
+// map's region, the load of chunk c + 1 overlapping the MMAs of chunk c),
+// accumulate in TMEM (tcgen05.mma, M 128, one thread issuing) and are read
+// back by every warp (tcgen05.ld) for bias, LeakyReLU and the next layer's
+// BF16 tile, written in place; the head turns the last layer's
+// (mean, raw log-std) into the action of each env for the next step,
+// a = tanh(u + sigma eps) with sigma = exp(-5 + 5 (tanh(r) + 1) / 2) and eps
+// from the counter-hash Box-Muller draw keyed by (seed, env, step), or
+// tanh(u) when deterministic.  The step's observations are still written to
+// obs (the replay needs them), but the policy never reads them back.
+// ---------------------------------------------------------------------------
+constexpr int kActThreads = 1024;
+constexpr int kActMaxEnvs = 128;                 // rows of the MMA tile
+constexpr unsigned kActChunk = 128u * 128u;      // a 64-wide K chunk of the input tile
+constexpr unsigned kActWChunk = 256u * 128u;     // a 64-wide K chunk of a 256-row weight tile
+constexpr int kActKChunks = 6;                   // input features <= 384
+
+__device__ __forceinline__ unsigned long long act_mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Input feature of a tail value (goal distance, bearing, v, w) of row q.
+__device__ __forceinline__ void act_tail(unsigned char *xt, const ActArgs &P, int q, int K,
+                                         const float *obs_row) {
+    for (int i = 0; i < 4; ++i) {
+        const float x = obs_row[K + i];
+        *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(q, K + i)) =
+            __float2bfloat16_rn(P.scale ? x * __ldg(P.scale + K + i) : x);
+    }
+    for (int c = K + 4; c < kActKChunks * 64; ++c)
+        *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(q, c)) = __float2bfloat16_rn(0.0f);
+}
+
+__device__ __forceinline__ bool act_wait(unsigned bar, unsigned parity, int *status) {
+    if (mbar_wait(bar, parity)) return true;
+    atomicOr(status, kStatusCopyTimeout);
+    return false;
+}
+
+__global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs A, const ActArgs P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ EnvSlot slots[kActMaxEnvs];
+    __shared__ int fin_slot[1];
+    __shared__ int next_ray;
+    __shared__ int tile_id;
+    __shared__ __align__(8) unsigned long long bar_map;
+    __shared__ __align__(8) unsigned long long bar_mma;
+    __shared__ unsigned tmem_slot;
+    // [0, region): the staged map, or during the actor the two weight buffers
+    // [region, region + 96 KiB): the actor's input tile (then H1, H2)
+    // then the beam table
+    // the swizzled tiles need 1024-byte alignment (act_step_smem adds the slack)
+    unsigned char *base = smem + ((1024u - (smem_addr(smem) & 1023u)) & 1023u);
+    const unsigned region = (unsigned)A.smem_region_bytes; // a multiple of 1024, >= 64 KiB
+    uint8_t *sbytes = base;
+    unsigned char *xt = base + region;
+    float2 *sbeam = reinterpret_cast<float2 *>(base + region + kActKChunks * kActChunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, grp = warp >> 2; // TMEM lane quarter, column group (8 of 32)
+    unsigned map_parity = 0, mma_parity = 0;
+    int beam_tab = -1;
+    if (tid == 0) {
+        init_copy_barrier(&bar_map);
+        init_copy_barrier(&bar_mma);
+    }
+    const unsigned tmem = tmem_alloc_cols(&tmem_slot, 256);
+    const unsigned tlane = (unsigned)(quad * 32) << 16;
+    const unsigned xt_a = smem_addr(xt), wb[2] = {smem_addr(base), smem_addr(base) + kActWChunk};
+    for (;;) {
+        if (tid == 0) {
+            tile_id = atomicAdd(&A.tile_queue[0], 1);
+            next_ray = 0;
+        }
+        __syncthreads();
+        const int tile = tile_id;
+        if (tile >= A.n_tiles) break;
+        const TileDev T = A.tiles[tile];
+        const MapDev M = A.maps[T.map];
+        const int K = A.tab_k[T.tab];
+        // the map region held weights during the previous tile: restage
+        if (tid == 0) stage_map(sbytes, A.dist + M.dist_off, (unsigned)M.n_bytes, &bar_map);
+        if (T.tab != beam_tab) {
+            const int toff = A.tab_off[T.tab];
+            for (int k = tid; k < K; k += blockDim.x)
+                sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
+            beam_tab = T.tab;
+        }
+        if (tid < T.env_count) {
+            const int e = A.perm[T.env_begin + tid];
+            slots[tid].env = e;
+            slots[tid].obs_off = A.obs_off[e];
+            slots[tid].ray_off = A.ray_off[e];
+        }
+        // rows beyond the tile's envs: zero (their outputs are not used)
+        for (int p = tid; p < (kActMaxEnvs - T.env_count) * kActKChunks * 8; p += blockDim.x) {
+            const int r = T.env_count + p / (kActKChunks * 8), c = (p % (kActKChunks * 8)) * 8;
+            *reinterpret_cast<uint4 *>(xt + act_swz(r, c)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        bool ok = true;
+        if (tid == 0) {
+            ok = wait_bitmap(&bar_map, map_parity);
+            if (!ok) {
+                atomicOr(A.status, kStatusCopyTimeout);
+                wait_bitmap(&bar_map, map_parity); // the copy in flight, bounded
+            }
+        }
+        map_parity ^= 1u;
+        if (__syncthreads_or(!ok)) break;
+        const BytesShared view{sbytes, M.byte_stride};
+        if (tid < T.env_count) {
+            env_phase<false>(A, view, M, K, tid, slots[tid], nullptr, nullptr);
+            act_tail(xt, P, tid, K, A.obs + slots[tid].obs_off);
+        }
+        __syncthreads();
+        ray_phase_refill(A, view, M, T, K, sbeam, slots, fin_slot, 0, &next_ray, xt, P.scale);
+        // ---- the actor on the tile's observations ----
+        __syncthreads();
+        for (int l = 0; l < 3; ++l) {
+            const int in = P.in[l], out = P.out[l], np = (out + 15) & ~15, nkc = (in + 63) >> 6;
+            const bool last = l == 2;
+            load_tile<kActThreads>(wb[0], P.W[l], P.ld[l], 0, np, out, 0, in);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            for (int c = 0; c < nkc; ++c) {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned a = xt_a + c * kActChunk, b = wb[c & 1];
+#pragma unroll
+                    for (int k16 = 0; k16 < 4; ++k16) {
+                        const unsigned acc = (c > 0 || k16 > 0) ? 1u : 0u;
+                        if (np > 128) {
+                            mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(b + 32u * k16),
+                                    instr_desc(128, 128), acc);
+                            mma_f16(tmem + 128u, smem_desc(a + 32u * k16),
+                                    smem_desc(b + 128u * 128u + 32u * k16),
+                                    instr_desc(128, np - 128), acc);
+                        } else {
+                            mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(b + 32u * k16),
+                                    instr_desc(128, np), acc);
+                        }
+                    }
+                    mma_commit(smem_addr(&bar_mma));
+                }
+                // the other buffer was read by chunk c - 1's MMAs, which have completed
+                if (c + 1 < nkc) {
+                    load_tile<kActThreads>(wb[(c + 1) & 1], P.W[l], P.ld[l], 0, np, out,
+                                           64 * (c + 1), in);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                }
+                act_wait(smem_addr(&bar_mma), mma_parity, A.status);
+                mma_parity ^= 1u;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = quad * 32 + lane;
+            if (!last) {
+                // bias, LeakyReLU, BF16, in place into the input tile (its
+                // columns [out, in) zeroed for the next layer)
+                const int j0 = 32 * grp;
+                for (int j = j0; j < j0 + 32; j += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + tlane + (unsigned)j, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float x = j + i < out ? v[i] + __ldg(P.b[l] + j + i) : 0.0f;
+                        v[i] = x > 0.0f ? x : 0.01f * x;
+                    }
+                    if (j < np) {
+                        *reinterpret_cast<uint4 *>(xt + act_swz(row, j)) = act_pack8(v);
+                        *reinterpret_cast<uint4 *>(xt + act_swz(row, j + 8)) = act_pack8(v + 8);
+                    }
+                }
+                // the next layer reads whole 64-wide chunks: columns [np, 64
+                // ceil(out / 64)) must be zero too
+                if (grp == 0)
+                    for (int c0 = np; c0 < ((out + 63) & ~63); c0 += 8)
+                        *reinterpret_cast<uint4 *>(xt + act_swz(row, c0)) = make_uint4(0u, 0u, 0u, 0u);
+            } else if (grp == 0) {
+                // the head: (mean u, raw log-std r) -> the env's next action
+                float v[16];
+                tmem_ld16(tmem + tlane, v);
+                if (row < T.env_count) {
+                    const int e = slots[row].env;
+#pragma unroll
+                    for (int d = 0; d < 2; ++d) {
+                        const float u = v[d] + __ldg(P.b[2] + d);
+                        const float r = v[2 + d] + __ldg(P.b[2] + 2 + d);
+                        const float ls = -5.0f + 5.0f * 0.5f * (tanhf(r) + 1.0f);
+                        float ep = 0.0f;
+                        if (P.mode == 1) {
+                            const unsigned long long h =
+                                act_mix64(P.seed ^ ((unsigned long long)e * 0xD1B54A32D192ED03ull) ^
+                                          ((unsigned long long)P.step << 32) ^ (unsigned)d);
+                            const float u1 = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+                            const float u2 = (float)((h >> 8) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+                            ep = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+                        }
+                        P.act[(size_t)e * 2 + d] = tanhf(u + expf(ls) * ep);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    tmem_free_cols(tmem, 256);
+    if (tid == 0) {
+        __threadfence();
+        const int done = atomicAdd(&A.tile_queue[1], 1);
+        if (done == (int)gridDim.x - 1) {
             A.tile_queue[0] = 0;
             A.tile_queue[1] = 0;
             __threadfence();
@@ -702,6 +982,27 @@ int launch_step_split(const StepArgs &a, int n_envs, void *stream) {
     if (err != cudaSuccess) return (int)err;
     void *args[] = {const_cast<StepArgs *>(&a)};
     err = cudaLaunchKernel(fn, dim3(n_sm), dim3(1024), args, smem, s);
+    if (err != cudaSuccess) return (int)err;
+    return (int)cudaGetLastError();
+}
+
+size_t act_step_smem(const StepArgs &a) {
+    return 1024 + (size_t)a.smem_region_bytes + (size_t)kActKChunks * kActChunk +
+           (size_t)a.max_k * sizeof(float2);
+}
+
+int launch_act_step(const StepArgs &a, const ActArgs &p, void *stream) {
+    if (a.n_tiles <= 0) return 0;
+    const size_t smem = act_step_smem(a);
+    const void *fn = (const void *)act_step_kernel;
+    int n_sm = 0, per_sm = 0;
+    cudaError_t err = (cudaError_t)occupancy(fn, smem, kActThreads, n_sm, per_sm);
+    if (err != cudaSuccess) return (int)err;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    const int grid = std::min(a.n_tiles, n_sm);
+    void *args[] = {const_cast<StepArgs *>(&a), const_cast<ActArgs *>(&p)};
+    err = cudaLaunchKernel(fn, dim3(grid), dim3(kActThreads), args, smem,
+                           static_cast<cudaStream_t>(stream));
     if (err != cudaSuccess) return (int)err;
     return (int)cudaGetLastError();
 }

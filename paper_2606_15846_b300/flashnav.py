@@ -31,7 +31,7 @@ EXPORTS = [
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
     "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_policy_act_counted",
-    "nav_rollout", "nav_trainer_set_graphs", "nav_trainer_set_fused", "nav_train_overlap",
+    "nav_rollout", "nav_rollout_fused", "nav_trainer_set_graphs", "nav_trainer_set_fused", "nav_train_overlap",
     "nav_train_default_cfg", "nav_trainer_create", "nav_trainer_free", "nav_trainer_last_error",
     "nav_train_insert", "nav_train_update", "nav_trainer_sync_policy", "nav_trainer_io",
     "nav_trainer_counts", "nav_eval_begin", "nav_eval_accumulate", "nav_eval_result",
@@ -133,6 +133,7 @@ def load():
         "nav_policy_act": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
         "nav_policy_act_fp32": (I, [P, P, C.c_int64, I, I, U64, C.c_uint32, P, P, P, P]),
         "nav_rollout": (I, [P, P, I, I, U64, C.c_uint32, P, P, P, P, I]),
+        "nav_rollout_fused": (I, [P, P, I, I, U64, C.c_uint32, P, P, P, P, I]),
         "nav_train_default_cfg": (None, [P]),
         "nav_trainer_create": (I, [P, P]),
         "nav_trainer_free": (None, [P]),
