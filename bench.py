@@ -31,8 +31,29 @@ METRIC = "env-steps/s (360-beam scan)"
 UNIT = "env-steps/s"
 SEED = 12345
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT = 148
 SM_MAX_MHZ = 2032.0
+# ncu counters of the step kernel per launch shape (DRAM bytes and warp
+# instructions per launch, cell visits per launch), from the captures whose
+# commands profiles/ records; a shape without a capture reports null
+COUNTERS = os.path.join(ROOT, "profiles", "step_kernel_counters.json")
+
+
+def _counters(launch):
+    """(DRAM bytes, warp instructions per visit) of the ncu capture of this
+    launch shape (tile_envs, block_threads, smem_map_bytes, max_regs,
+    byte_cells, split), or (None, None): the same shape, with any
+    shared-memory cap that stages the captured workload's maps."""
+    try:
+        with open(COUNTERS) as f:
+            entries = json.load(f)["captures"]
+    except (OSError, ValueError, KeyError):
+        return None, None
+    key = lambda l: (l[0], l[1], l[3], l[4], l[5])
+    for e in entries:
+        if key(e["launch"]) == key(launch) and launch[2] >= e.get("smem_min", e["launch"][2]):
+            return float(e["dram_bytes_per_launch"]), float(e["warp_inst_per_launch"]) / float(
+                e["visits_per_launch"])
+    return None, None
 
 
 def _peaks():
@@ -167,8 +188,10 @@ def cpu_baseline(wl, seconds: float = 15.0):
 
 def policy_rollout(steps: int = 20):
     """Rollout with the policy in the loop on 65536 envs over 16 256x256 maps,
-    360 beams: the BF16 tensor-core policy against the plain FP32 SIMT policy
-    (same simulator kernel, same random-init weights)."""
+    360 beams, actor 364-256-256-4 (random init, sampled actions): the actor
+    inside the step kernel (nav_rollout_fused), the BF16 tensor-core policy
+    as separate launches beside the step (nav_rollout), and the plain FP32
+    SIMT policy (register-blocked shared-memory GEMM) beside the step."""
     import ctypes as C
     import torch
     from paper_2606_15846_b300 import flashnav
@@ -176,32 +199,45 @@ def policy_rollout(steps: int = 20):
     wl = W.config_throughput(n_envs=65536)
     sim = flashnav.NavSim.from_workload(wl)
     sim.reset(SEED)
-    sim.autotune(steps=3)  # one simulator launch shape for both arms
+    sim.autotune(steps=3)  # one simulator launch shape for the unfused arms
     lib = flashnav.load()
     pol = C.c_void_p()
     assert lib.nav_policy_create(364, 256, wl.n_envs, 7, C.byref(pol)) == 0
+    scale = np.ones(364, np.float32)
+    scale[:360] = 1.0 / wl.max_range
+    scale[360:] = [0.125, 1.0 / np.pi, 2.0, 1.0]
+    assert lib.nav_policy_set_input_scale(pol, scale.ctypes.data_as(C.c_void_p)) == 0
     E = wl.n_envs
     obs = sim.new_obs()
     act = torch.empty(E, 2, device="cuda")
     rew = torch.empty(E, device="cuda")
     done = torch.empty(E, dtype=torch.uint8, device="cuda")
     P = lambda t: C.c_void_p(t.data_ptr())
-    out = {}
-    for name, fp32 in (("bf16_tensor_core_policy", 0), ("fp32_simt_policy", 1)):
-        sim.reset(SEED, obs)
+
+    def run(name, n, step0):
         sim._bind_stream()
-        assert lib.nav_rollout(sim._h, pol, 3, 1, 5, 0, P(obs), P(act), P(rew), P(done), fp32) == 0
+        if name == "fused_actor_in_step":
+            return lib.nav_rollout_fused(sim._h, pol, n, 1, 5, step0, P(obs), P(act), P(rew),
+                                         P(done), 0)
+        return lib.nav_rollout(sim._h, pol, n, 1, 5, step0, P(obs), P(act), P(rew), P(done),
+                               1 if name == "fp32_simt_policy" else 0)
+
+    out = {}
+    for name in ("fused_actor_in_step", "bf16_tensor_core_policy", "fp32_simt_policy"):
+        sim.reset(SEED, obs)
+        assert run(name, 3, 0) == 0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        assert lib.nav_rollout(sim._h, pol, steps, 1, 5, 3, P(obs), P(act), P(rew), P(done),
-                               fp32) == 0
+        assert run(name, steps, 3) == 0
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         out[name] = {"env_steps_per_s": E / (ms / 1e3), "ms_per_step": ms}
-    out["speedup_bf16_vs_fp32"] = (out["bf16_tensor_core_policy"]["env_steps_per_s"] /
-                                   out["fp32_simt_policy"]["env_steps_per_s"])
+    sim.sync(60000)
+    f32 = out["fp32_simt_policy"]["env_steps_per_s"]
+    out["speedup_fused_vs_fp32"] = out["fused_actor_in_step"]["env_steps_per_s"] / f32
+    out["speedup_bf16_vs_fp32"] = out["bf16_tensor_core_policy"]["env_steps_per_s"] / f32
     out["config"] = "65536 envs, 16 maps 256x256, 360 beams, actor 364-256-256-4, sampled actions"
     lib.nav_policy_free(pol)
     return out
@@ -478,23 +514,66 @@ def learner_update(n_updates: int = 200, graphs: bool = True):
     return out
 
 
-def training_run(seconds: float):
-    """FastDSAC from scratch for a bounded wall-clock budget: time at which the
-    deterministic policy first reaches each success threshold on 1000 held-out
-    maps (evaluation time included)."""
+def training_run(seconds: float, robot: str = "disc"):
+    """Config 5's training (FastDSAC from scratch): 16384 envs on 64 seeded
+    256x256 training maps, 4 M replay, actor 364-256-256-4 and twin critics,
+    batch 4096, 16 updates per env step, for a bounded wall-clock budget;
+    the time at which the deterministic policy first reaches each success
+    threshold on 1000 held-out maps (evaluation time included), and the share
+    of held-out episodes a perfect planner could reach within the horizon."""
     from paper_2606_15846_b300 import train as TR
-    cfg = TR.TrainConfig(time_budget_s=seconds, threshold=1.0)
+    cfg = TR.TrainConfig(robot=robot, n_envs=16384, utd=16, time_budget_s=seconds, threshold=1.0)
     res = TR.train(cfg, log=lambda *a: None)
     hist = res["history"]
-    reach = {}
-    for thr in (0.25, 0.40, 0.50, 1.00):
+    reach = TR.reachable_fraction(cfg)
+    times = {}
+    for thr in (0.25, 0.50, 0.75, 1.00):
         hit = [h["t"] for h in hist if h["success"] >= thr]
-        reach[f"{int(thr * 100)}%"] = hit[0] if hit else None
-    return {"seconds_to_success": reach, "best_success": max(h["success"] for h in hist),
-            "budget_s": seconds, "env_steps": res["env_steps"],
+        times[f"{int(thr * 100)}%"] = hit[0] if hit else None
+    best = max(h["success"] for h in hist)
+    hit = [h["t"] for h in hist if h["success"] >= reach["upper"]]
+    return {"seconds_to_success": times, "best_success": best,
+            "reachable_share": reach, "seconds_to_reachable_share": hit[0] if hit else None,
+            "budget_s": seconds, "env_steps": res["env_steps"], "cycle_ms": res["cycle_ms"],
             "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
-            "config": "4096 envs on 64 training maps 256x256, 1000 held-out maps, disc robot, "
-                      "batch 4096, 8 updates per env step, eval every 1 s"}
+            "config": f"{robot} robot, 16384 envs on 64 training maps 256x256, 1000 held-out "
+                      "maps, batch 4096, 16 updates per env step, eval every 1 s"}
+
+
+def compact(extras: dict) -> dict:
+    """Headline numbers of the extra measurements (the full records go to
+    stderr), short enough to stay in a truncated log's tail."""
+    r = lambda v, n=4: None if v is None else float(f"{v:.{n}g}")
+    c = {}
+    pr = extras.get("policy_rollout")
+    if pr:
+        c["rollout_65536_Msteps"] = {k: r(pr[k]["env_steps_per_s"] / 1e6) for k in
+                                     ("fused_actor_in_step", "bf16_tensor_core_policy",
+                                      "fp32_simt_policy")}
+        c["rollout_65536_Msteps"]["fused_vs_fp32"] = r(pr["speedup_fused_vs_fp32"], 3)
+    ub = extras.get("uneven_batch")
+    if ub:
+        c["uneven_16384_Msteps"] = r(ub["env_steps_per_s"] / 1e6)
+    ps = extras.get("paper_sensing")
+    if ps:
+        c["paper_sensing_16384_Msteps"] = {"march": r(ps["march_0.03m_16384env"]["env_steps_per_s"] / 1e6),
+                                           "exact": r(ps["exact_traversal_16384env"]["env_steps_per_s"] / 1e6)}
+    lu = extras.get("learner_update")
+    if lu:
+        c["learner_ms_per_update"] = {k: r(v["ms_per_update"], 3) for k, v in lu.items()
+                                      if isinstance(v, dict)}
+    tp = extras.get("training_paper_turtlebot2")
+    if tp:
+        c["train_turtlebot2_s"] = {**{k: r(v, 3) for k, v in tp["seconds_to_success"].items()},
+                                   "best": r(tp["best_success"], 3)}
+    for robot in ("disc", "rect"):
+        t = extras.get(f"training_config5_{robot}")
+        if t:
+            c[f"train_cfg5_{robot}_s"] = {**{k: r(v, 3) for k, v in t["seconds_to_success"].items()},
+                                          "best": r(t["best_success"], 3),
+                                          "reachable": r(t["reachable_share"]["upper"], 3),
+                                          "to_reachable": r(t["seconds_to_reachable_share"], 3)}
+    return c
 
 
 def training_paper(seconds: float, robot: str = "turtlebot2", algo: str = "fastdsac"):
@@ -710,12 +789,15 @@ def run_gpu(args):
     if rank == 0:
         peaks, src = _peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        traffic, ipv = _counters(launch)
         mean_launch_s = step_ms / 1e3 / args.steps
         visits_per_launch = visits / args.steps
         achieved = visits_per_launch / mean_launch_s / 1e9
         # one visit = one 32-bit shared-memory word gathered per lane; the SM
         # serves 32 such lanes per clock
-        peak = SM_COUNT * 32 * sm_mhz * 1e6 / 1e9
+        peak = n_sm * 32 * sm_mhz * 1e6 / 1e9
+        issue = n_sm * 4 * sm_mhz * 1e6 / ipv / 1e9 if ipv else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -738,23 +820,16 @@ def run_gpu(args):
             "gpu_launches": args.steps * (2 if launch[5] == 1 else 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Gvisit/s", "frac": achieved / peak,
-                         # DRAM bytes per launch of this kernel from the ncu
-                         # capture in profiles/step_kernel_plain4096.md
-                         # (any shared-memory cap that stages the 256x256
-                         # distance maps gives the same kernel)
-                         "traffic": 1.468e6 if (tuple(launch[i] for i in (0, 1, 3, 5)) ==
-                                                (8, 512, 40, 2) and launch[4] in (1, 3) and
-                                                launch[2] >= 69 * 1024)
-                         else None,
-                         "peak_source": f"{SM_COUNT} SMs x 32 shared-word gathers/clk x "
-                                        f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
-                         "kernel": "step kernel (fused) or ray_kernel (split), per launch.split",
-                         # the instruction-issue bound that explains the gap:
-                         # 4 warp instructions/clk/SM over the ncu-measured
-                         # 0.710 warp instructions per visit of the step kernel
-                         "issue_bound": SM_COUNT * 4 * sm_mhz * 1e6 / 0.710 / 1e9,
-                         "frac_of_issue_bound": achieved / (SM_COUNT * 4 * sm_mhz * 1e6 /
-                                                           0.710 / 1e9)},
+                         "traffic": traffic,
+                         "peak_source": f"{n_sm} SMs x 32 shared-memory word gathers/clk x "
+                                        f"{sm_mhz:.0f} MHz ({src} sm_max_mhz): the textbook "
+                                        "walk's one lookup per visit; the kernel itself is "
+                                        "bound by instruction issue (issue_bound)",
+                         "kernel": "step kernel per launch.split (4: refilled lanes)",
+                         # 4 warp instructions/clk/SM over the warp instructions
+                         # per visit of this launch shape's ncu capture
+                         "issue_bound": issue,
+                         "frac_of_issue_bound": achieved / issue if issue else None},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": E * 2 * 4,
                     "d2h_bytes_per_step": sim.obs_size * 4 + E * 4 + E,
@@ -770,19 +845,19 @@ def run_gpu(args):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         if world == 1 and args.extras:
-            line["policy_rollout"] = policy_rollout()
-            line["uneven_batch"] = ub = uneven_batch()
-            # maps up to the staged size are read from shared memory, the
-            # larger ones through L1/L2
-            gv = ub["cell_visits_per_s"] / 1e9
-            ub["frac_of_measured_gather"] = {"shared": gv / g["shared_64KiB"],
-                                             "l2": gv / g["l2_32MiB"]}
-            line["paper_sensing"] = paper_sensing()
-            line["learner_update"] = learner_update()
+            ex = {"policy_rollout": policy_rollout()}
+            ex["uneven_batch"] = ub = uneven_batch()
+            # maps up to the staged size are read from shared memory
+            ub["frac_of_measured_shared_gather"] = ub["cell_visits_per_s"] / 1e9 / g["shared_64KiB"]
+            ex["paper_sensing"] = paper_sensing()
+            ex["learner_update"] = learner_update()
             if args.train_seconds > 0:
-                line["training_paper_turtlebot2"] = training_paper(min(args.train_seconds, 25.0))
-            if args.train_seconds > 0:
-                line["training"] = training_run(args.train_seconds)
+                ex["training_paper_turtlebot2"] = training_paper(min(args.train_seconds, 25.0))
+                for robot in ("disc", "rect"):
+                    ex[f"training_config5_{robot}"] = training_run(min(args.train_seconds, 30.0),
+                                                                   robot)
+            print(json.dumps(ex), file=sys.stderr, flush=True)
+            line["extras"] = compact(ex)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -801,7 +876,7 @@ def main():
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_forward", "uneven_batch",
                              "gather_rates",
-                             "paper_sensing", "training",
+                             "paper_sensing", "training", "training_rect",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
                              "learner_update", "table2"],
                     help="run one of the extra measurements alone")
@@ -825,6 +900,7 @@ def main():
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "table2": lambda: table2(args.train_seconds, args.seeds),
               "training": lambda: training_run(args.train_seconds),
+              "training_rect": lambda: training_run(args.train_seconds, "rect"),
               "training_paper": lambda: training_paper(args.train_seconds),
               "training_paper_go2": lambda: training_paper(args.train_seconds, "go2"),
               "training_paper_fastsac": lambda: training_paper(args.train_seconds, "turtlebot2",

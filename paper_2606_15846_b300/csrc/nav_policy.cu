@@ -10,8 +10,8 @@
 //   log sigma = -5 + 5 (tanh(r) + 1) / 2,  a = tanh(u + sigma eps)
 // with eps standard normal from the counter hash keyed by (seed, row, step)
 // (Box-Muller), or a = tanh(u) when deterministic.  A plain FP32 SIMT path
-// (one thread per output element, no tensor cores) is kept as the unfused
-// baseline.
+// (register-blocked shared-memory GEMM on the CUDA cores, no tensor cores) is
+// kept as the unfused baseline.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -113,20 +113,73 @@ __global__ void actor_head_fwd(const float *__restrict__ out4, int n, int mode,
 
 __global__ void k_bump(unsigned long long *c) { *c += 1; }
 
-// Plain FP32 layer: y[r][o] = act(sum_k x[r][k] W[o][k] + b[o]); one thread
-// per output element (the unfused baseline; no tensor cores).
-__global__ void dense_fp32(const float *__restrict__ x, long long ldx, int n, int in,
-                           const float *__restrict__ W, const float *__restrict__ b, int out,
-                           int leaky, float *y) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n * out) return;
-    const int r = (int)(i / out), o = (int)(i - (long long)r * out);
-    const float *xr = x + r * ldx;
-    const float *w = W + (size_t)o * in;
-    float s = b[o];
-    for (int k = 0; k < in; ++k) s = fmaf(xr[k], w[k], s);
-    if (leaky) s = s > 0.0f ? s : 0.01f * s;
-    y[i] = s;
+// Plain FP32 layer on the CUDA cores (the unfused baseline; no tensor
+// cores): y[r][o] = act(sum_k x[r][k] W[o][k] + b[o]).  A register-blocked
+// SIMT GEMM: each 256-thread CTA computes a 128-row x 64-output tile from
+// 16-wide K tiles of x and W staged in shared memory (stored K-major, so a
+// thread reads its 8 rows and 4 outputs as vectors), each thread 8 x 4
+// results with FP32 FMAs.
+constexpr int kSgBM = 128, kSgBN = 64, kSgBK = 16;
+
+__global__ void __launch_bounds__(256) dense_fp32(const float *__restrict__ x, long long ldx, int n,
+                                                  int in, const float *__restrict__ W,
+                                                  const float *__restrict__ b, int out, int leaky,
+                                                  float *y) {
+    __shared__ __align__(16) float As[kSgBK][kSgBM + 4];
+    __shared__ __align__(16) float Bs[kSgBK][kSgBN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long r0 = (long long)blockIdx.x * kSgBM;
+    const int o0 = blockIdx.y * kSgBN;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < in; k0 += kSgBK) {
+        // x tile: row tid / 2, 8 consecutive k; W tile: output tid / 4, 4 k
+        {
+            const int r = tid >> 1, kk = (tid & 1) * 8;
+            const long long gr = r0 + r;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + kk + q;
+                As[kk + q][r] = (gr < n && k < in) ? x[gr * ldx + k] : 0.0f;
+            }
+            const int o = tid >> 2, kb = (tid & 3) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = k0 + kb + q;
+                Bs[kb + q][o] = (o0 + o < out && k < in) ? W[(size_t)(o0 + o) * in + k] : 0.0f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSgBK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[k][ty * 8 + 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const long long r = r0 + ty * 8 + i;
+        if (r >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = o0 + tx * 4 + j;
+            if (o >= out) continue;
+            float v = acc[i][j] + b[o];
+            if (leaky) v = v > 0.0f ? v : 0.01f * v;
+            y[r * out + o] = v;
+        }
+    }
 }
 
 // FP32 master -> BF16 W [out][ld_in] and W^T [in][ld_out] (pads zero)
@@ -303,9 +356,9 @@ int Mlp::forward_fp32(const float *x, long long ldx, int n, float *const *h32, f
         const Layer &L = layer[l];
         const bool last = l == n_layers - 1;
         float *y = last ? out32 : h32[l];
-        const long long tot = (long long)n * L.out;
-        dense_fp32<<<(unsigned)((tot + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-            in, ld, n, L.in, L.W, L.b, L.out, last ? 0 : 1, y);
+        const dim3 grid((unsigned)((n + kSgBM - 1) / kSgBM), (unsigned)((L.out + kSgBN - 1) / kSgBN));
+        dense_fp32<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, ld, n, L.in, L.W, L.b,
+                                                                        L.out, last ? 0 : 1, y);
         in = y;
         ld = L.out;
     }

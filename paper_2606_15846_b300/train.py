@@ -387,3 +387,63 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
     else:
         lib.nav_policy_free(pol)
     return out
+
+
+def reachable_fraction(cfg: TrainConfig, horizon: int = 200, dt: float = 0.1) -> dict:
+    """What 100 % success can mean on the held-out episodes: the share of
+    them whose goal a perfect planner could reach within the horizon at the
+    robot's top speed.  Per episode (the reset the evaluation uses), the
+    shortest 8-connected grid path from the start cell to a cell within the
+    goal tolerance, through the cells whose centre keeps the robot's
+    circumscribed disc clear of every occupied cell square (Dijkstra, scipy),
+    is compared with v_max dt horizon.  An 8-connected path is at most
+    1.0824 times a straight segment's length, so `upper` (path <= 1.0824 x
+    budget) bounds from above the share any policy can reach; `grid` uses
+    the budget itself."""
+    from scipy import ndimage
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    _, ev_wl = make_workloads(cfg)
+    ev = F.NavSim.from_workload(ev_wl)
+    ev.reset(777)
+    f, _, _ = ev.get_state()
+    rb = ev_wl.robots[0]
+    rc = rb.radius if rb.shape == 0 else 0.5 * float(np.hypot(rb.length, rb.width))
+    budget = rb.v_max * dt * horizon
+    res = ev_wl.res
+    tol = ev_wl.params.goal_tol / res
+    lens = np.full(ev_wl.n_envs, np.inf)
+    for e in range(ev_wl.n_envs):
+        occ = ev_wl.maps[int(ev_wl.env_map[e])]
+        H, Wd = occ.shape
+        # distance from a cell centre to the nearest occupied cell square is at
+        # least the distance between the centres minus half a cell
+        free = ndimage.distance_transform_edt(occ == 0) - 0.5 > rc / res
+        sj, si = int(f[e, 1] / res), int(f[e, 0] / res)
+        if not (0 <= sj < H and 0 <= si < Wd):
+            continue
+        free[sj, si] = True
+        idx = np.full(occ.shape, -1, np.int64)
+        cells = np.flatnonzero(free.ravel())
+        idx.ravel()[cells] = np.arange(cells.size)
+        rows, cols, wts = [], [], []
+        for dj, di, w in ((0, 1, 1.0), (1, 0, 1.0), (1, 1, 2 ** 0.5), (1, -1, 2 ** 0.5)):
+            a = free[max(0, -dj):H - max(0, dj), max(0, -di):Wd - max(0, di)]
+            b = free[max(0, dj):H - max(0, -dj) if dj < 0 else H, max(0, di):Wd - max(0, -di) if di < 0 else Wd]
+            ia = idx[max(0, -dj):H - max(0, dj), max(0, -di):Wd - max(0, di)]
+            ib = idx[max(0, dj):H - max(0, -dj) if dj < 0 else H, max(0, di):Wd - max(0, -di) if di < 0 else Wd]
+            both = a & b
+            rows.append(ia[both])
+            cols.append(ib[both])
+            wts.append(np.full(int(both.sum()), w))
+        r_, c_, w_ = np.concatenate(rows), np.concatenate(cols), np.concatenate(wts)
+        G = csr_matrix((np.concatenate([w_, w_]), (np.concatenate([r_, c_]), np.concatenate([c_, r_]))),
+                       shape=(cells.size, cells.size))
+        d = dijkstra(G, indices=int(idx[sj, si]), limit=1.0824 * budget / res + 1.0)
+        jj, ii = np.divmod(cells, Wd)
+        near = np.hypot(ii + 0.5 - f[e, 5] / res, jj + 0.5 - f[e, 6] / res) <= tol
+        if near.any():
+            lens[e] = float(d[near].min()) * res
+    return {"grid": float(np.mean(lens <= budget)), "upper": float(np.mean(lens <= 1.0824 * budget)),
+            "budget_m": budget, "median_path_m": float(np.median(lens[np.isfinite(lens)]))
+            if np.isfinite(lens).any() else None}
