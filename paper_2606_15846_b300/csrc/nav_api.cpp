@@ -277,8 +277,43 @@ int launch_args(nav_handle *h, const StepArgs &A) {
     return launch_step(A, h->cfg, h->stream);
 }
 
+// Sizes of the (map, beam table) groups of the handle's envs.
+std::vector<int> group_sizes(const nav_handle *h) {
+    std::vector<std::pair<int, int>> keys;
+    for (int e = 0; e < h->n_envs; ++e) keys.push_back({h->env_map[e], h->env_tab[e]});
+    std::sort(keys.begin(), keys.end());
+    std::vector<int> n;
+    for (size_t i = 0; i < keys.size(); ++i)
+        if (i == 0 || keys[i] != keys[i - 1]) n.push_back(1);
+        else ++n.back();
+    return n;
+}
+
+// The smallest tile size (<= te_max) whose balanced tiles (cut_group) number
+// at most `slots` (whole waves of resident CTAs), else te_max.
+int fit_tile(const nav_handle *h, long long slots, int te_max) {
+    const std::vector<int> n = group_sizes(h);
+    for (int te = 1; te < te_max; ++te) {
+        long long tiles = 0;
+        for (int g : n) tiles += (g + te - 1) / te;
+        if (tiles <= slots) return te;
+    }
+    return te_max;
+}
+
+// Cuts the envs perm[s, t) of one (map, beam table) group into
+// ceil((t - s) / te) tiles of nearly equal size (sizes differ by at most
+// one), so that no tile is a small remainder.
+void cut_group(int s, int t, int te, int map, int tab, std::vector<TileDev> &out) {
+    const int n = t - s, k = (n + te - 1) / te;
+    for (int i = 0; i < k; ++i) {
+        const int b = s + (int)((long long)n * i / k), e = s + (int)((long long)n * (i + 1) / k);
+        out.push_back(TileDev{map, tab, b, e - b});
+    }
+}
+
 // Groups envs by (map, beam table) and cuts each group into tiles of at most
-// tile_envs envs.  The queue runs over the largest tiles first so that the
+// tile_envs envs (cut_group).  The queue runs over the largest tiles first so that the
 // longest CTAs start early: by map size x beams (order 0, ties in map order)
 // or by envs x beams x sampled cells per ray (order 1, ties by map size).
 int build_tiles(nav_handle *h) {
@@ -297,14 +332,7 @@ int build_tiles(nav_handle *h) {
         while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
                h->env_tab[perm[t]] == h->env_tab[perm[s]])
             ++t;
-        for (int b = s; b < t; b += h->cfg.tile_envs) {
-            TileDev td;
-            td.map = h->env_map[perm[s]];
-            td.tab = h->env_tab[perm[s]];
-            td.env_begin = b;
-            td.env_count = std::min(h->cfg.tile_envs, t - b);
-            tiles.push_back(td);
-        }
+        cut_group(s, t, h->cfg.tile_envs, h->env_map[perm[s]], h->env_tab[perm[s]], tiles);
         s = t;
     }
     std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &x, const TileDev &y) {
@@ -359,14 +387,7 @@ int build_tiles(nav_handle *h) {
                 while (r < (int)pperm.size() && h->env_map[pperm[r]] == h->env_map[pperm[q]] &&
                        h->env_tab[pperm[r]] == h->env_tab[pperm[q]])
                     ++r;
-                for (int b = q; b < r; b += pt) {
-                    TileDev td;
-                    td.map = h->env_map[pperm[q]];
-                    td.tab = h->env_tab[pperm[q]];
-                    td.env_begin = b;
-                    td.env_count = std::min(pt, r - b);
-                    ptiles.push_back(td);
-                }
+                cut_group(q, r, pt, h->env_map[pperm[q]], h->env_tab[pperm[q]], ptiles);
                 q = r;
             }
             std::stable_sort(ptiles.begin() + t0, ptiles.end(), [&](const TileDev &x, const TileDev &y) {
@@ -1218,8 +1239,7 @@ int build_act_tiles(nav_handle *h, int te) {
         while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
                h->env_tab[perm[t]] == h->env_tab[perm[s]])
             ++t;
-        for (int b = s; b < t; b += te)
-            tiles.push_back(TileDev{h->env_map[perm[s]], h->env_tab[perm[s]], b, std::min(te, t - b)});
+        cut_group(s, t, te, h->env_map[perm[s]], h->env_tab[perm[s]], tiles);
         s = t;
     }
     std::stable_sort(tiles.begin(), tiles.end(),
@@ -1281,8 +1301,7 @@ int nav_rollout_fused(nav_handle *h, nav_policy *p, int n_steps, int mode, uint6
     cudaError_t ce = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaDeviceGetAttribute");
     const long long waves = std::max(1LL, ((long long)h->n_envs + 128LL * n_sm - 1) / (128LL * n_sm));
-    const int te = (int)std::max(1LL, std::min(128LL, ((long long)h->n_envs + waves * n_sm - 1) /
-                                                          (waves * n_sm)));
+    const int te = fit_tile(h, waves * n_sm, 128);
     int rc = build_act_tiles(h, te);
     if (rc != NAV_OK) return rc;
     // the first action from the current observation (the inference path),
@@ -1336,7 +1355,17 @@ int nav_autotune(nav_handle *h, int steps, float *best_ms) {
     int best_cap = h->smem_map_bytes, best_bytes = h->byte_cells;
     // pass 1: launch shape with the current staging choice; the three
     // fastest shapes are timed again with three times the steps
-    const int tiles[] = {1, 2, 4, 8, 16, 32};
+    // fixed sizes, and sizes whose tiles fill 1-4 whole waves of one to four
+    // resident CTAs per SM
+    std::vector<int> tiles = {1, 2, 4, 8, 16, 32};
+    {
+        int n_sm = 0;
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess)
+            for (int k = 1; k <= 8; ++k) {
+                const int te = fit_tile(h, (long long)n_sm * k, kMaxTileEnvs);
+                if (std::find(tiles.begin(), tiles.end(), te) == tiles.end()) tiles.push_back(te);
+            }
+    }
     const int blocks[] = {128, 256, 512};
     const int regs[] = {32, 40, 64};
     // refilled lanes apply to the exact traversal without moving discs
