@@ -153,6 +153,10 @@ struct ActArgs {
     const __nv_bfloat16 *W[3];
     const float *b[3];
     int ld[3], in[3], out[3];
+    // the weights as 16 KiB units in the tensor cores' swizzled layout (unit
+    // u at Wu + u * 16 KiB: 128 output rows, or the layer's last rows, of
+    // one 64-wide K chunk), written by launch_act_swizzle
+    const unsigned char *Wu;
     const float *scale;
     float *act;
     int mode;
@@ -162,6 +166,9 @@ struct ActArgs {
 // One fused step + actor of every tile (tiles of <= 128 envs, exact
 // traversal over staged distance bytes, no moving discs, raw beams).
 int launch_act_step(const StepArgs &a, const ActArgs &p, void *stream);
+// Writes the weight units of p's layers into dst (act_units(p) x 16 KiB).
+int launch_act_swizzle(const ActArgs &p, unsigned char *dst, void *stream);
+int act_units(const ActArgs &p);
 size_t act_step_smem(const StepArgs &a);
 
 // Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step).

@@ -474,9 +474,10 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
 // on the tile's new observations, on the tensor cores, from shared memory:
 // the observation rows the ray and env phases produce are written, scaled
 // and rounded to BF16, straight into the actor's swizzled input tile; the
-// three layers (in -> H -> H -> 4, LeakyReLU) stream their weights by
-// 64-wide K chunks (cp.async into two 32 KiB buffers that reuse the staged
-// map's region, the load of chunk c + 1 overlapping the MMAs of chunk c),
+// three layers (in -> H -> H -> 4, LeakyReLU) stream their weights in
+// 16 KiB units of 128 output rows x one 64-wide K chunk, pre-swizzled in
+// global memory (bulk copies issued by one thread into four buffers that
+// reuse the staged map's region, up to four units ahead of the MMAs),
 // accumulate in TMEM (tcgen05.mma, M 128, one thread issuing) and are read
 // back by every warp (tcgen05.ld) for bias, LeakyReLU and the next layer's
 // BF16 tile, written in place; the head turns the last layer's
@@ -489,7 +490,6 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
 constexpr int kActThreads = 1024;
 constexpr int kActMaxEnvs = 128;                 // rows of the MMA tile
 constexpr unsigned kActChunk = 128u * 128u;      // a 64-wide K chunk of the input tile
-constexpr unsigned kActWChunk = 256u * 128u;     // a 64-wide K chunk of a 256-row weight tile
 constexpr int kActKChunks = 6;                   // input features <= 384
 
 __device__ __forceinline__ unsigned long long act_mix64(unsigned long long z) {
@@ -511,6 +511,45 @@ __device__ __forceinline__ void act_tail(unsigned char *xt, const ActArgs &P, in
         *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(q, c)) = __float2bfloat16_rn(0.0f);
 }
 
+// Weight unit u of the actor: layer l, 64-wide K chunk c, output half h
+// (rows 128 h ..), and its rows (the layer's width rounded up to 16, at most
+// 128).  Units run over the layers in order, K chunks outer, halves inner.
+__device__ __forceinline__ void act_unit(const ActArgs &P, int u, int &l, int &c, int &h,
+                                         int &rows) {
+    l = 0;
+    for (;;) {
+        const int nk = (P.in[l] + 63) >> 6, nh = P.out[l] > 128 ? 2 : 1;
+        if (u < nk * nh || l == 2) {
+            c = u / nh;
+            h = u % nh;
+            rows = min(128, ((P.out[l] + 15) & ~15) - 128 * h);
+            return;
+        }
+        u -= nk * nh;
+        ++l;
+    }
+}
+
+// One thread per 16-byte piece (8 BF16) of a unit: the weights W[l] [out][ld]
+// rearranged into the 128-byte-swizzled K-major tile the MMAs read (zero
+// beyond the layer's rows and inputs), so that one bulk copy stages a unit.
+__global__ void act_swizzle_kernel(const ActArgs P, unsigned char *dst, int nunits) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = t >> 10, r = (t >> 3) & 127, p = t & 7;
+    if (u >= nunits) return;
+    int l, c, h, rows;
+    act_unit(P, u, l, c, h, rows);
+    if (r >= rows) return;
+    const int row = 128 * h + r, k = 64 * c + 8 * p;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        v[e] = (row < P.out[l] && k + e < P.in[l]) ? P.W[l][(size_t)row * P.ld[l] + k + e]
+                                                   : __float2bfloat16_rn(0.0f);
+    *reinterpret_cast<uint4 *>(dst + (size_t)u * kActChunk + (r >> 3) * 1024 + (r & 7) * 128 +
+                               ((p ^ (r & 7)) << 4)) = *reinterpret_cast<const uint4 *>(v);
+}
+
 __device__ __forceinline__ bool act_wait(unsigned bar, unsigned parity, int *status) {
     if (mbar_wait(bar, parity)) return true;
     atomicOr(status, kStatusCopyTimeout);
@@ -524,9 +563,10 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     __shared__ int next_ray;
     __shared__ int tile_id;
     __shared__ __align__(8) unsigned long long bar_map;
-    __shared__ __align__(8) unsigned long long bar_mma;
+    __shared__ __align__(8) unsigned long long bar_ld[4]; // weight unit landed, per buffer
+    __shared__ __align__(8) unsigned long long bar_w[4];  // MMAs done reading, per buffer
     __shared__ unsigned tmem_slot;
-    // [0, region): the staged map, or during the actor the two weight buffers
+    // [0, region): the staged map, or during the actor four 16 KiB weight buffers
     // [region, region + 96 KiB): the actor's input tile (then H1, H2)
     // then the beam table
     // the swizzled tiles need 1024-byte alignment (act_step_smem adds the slack)
@@ -537,15 +577,43 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     float2 *sbeam = reinterpret_cast<float2 *>(base + region + kActKChunks * kActChunk);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, grp = warp >> 2; // TMEM lane quarter, column group (8 of 32)
-    unsigned map_parity = 0, mma_parity = 0;
+    unsigned map_parity = 0;
     int beam_tab = -1;
+    // The weights stream as 16 KiB units (act_unit) from their swizzled copy
+    // by bulk copies into four buffers in the map's region (free once the ray
+    // phase ends), up to four units ahead of the MMAs; thread 0 alone issues
+    // the copies and the MMAs and tracks, per buffer, the phase bits of its
+    // two mbarriers and whether an MMA commit on it is still to be waited for.
+    unsigned ph_ld = 0u, ph_w = 0u, pend_w = 0u;
+    int nunits = 0;
+    for (int l = 0; l < 3; ++l) nunits += ((P.in[l] + 63) >> 6) * (P.out[l] > 128 ? 2 : 1);
     if (tid == 0) {
         init_copy_barrier(&bar_map);
-        init_copy_barrier(&bar_mma);
+        for (int b = 0; b < 4; ++b) {
+            init_copy_barrier(&bar_ld[b]);
+            init_copy_barrier(&bar_w[b]);
+        }
     }
     const unsigned tmem = tmem_alloc_cols(&tmem_slot, 256);
     const unsigned tlane = (unsigned)(quad * 32) << 16;
-    const unsigned xt_a = smem_addr(xt), wb[2] = {smem_addr(base), smem_addr(base) + kActWChunk};
+    const unsigned xt_a = smem_addr(xt);
+    const unsigned wb0 = smem_addr(base); // buffer b at wb0 + b * 16 KiB
+    // (thread 0) waits for the outstanding MMA commit on buffer b, if any
+    auto wait_mma = [&](int b) {
+        if ((pend_w >> b) & 1u) {
+            act_wait(smem_addr(&bar_w[b]), (ph_w >> b) & 1u, A.status);
+            ph_w ^= 1u << b;
+            pend_w &= ~(1u << b);
+        }
+    };
+    // (thread 0) stages unit u once its buffer's previous MMAs have completed
+    auto issue_unit = [&](int u) {
+        int l, c, h, rows;
+        act_unit(P, u, l, c, h, rows);
+        wait_mma(u & 3);
+        stage_map(base + (size_t)(u & 3) * kActChunk, P.Wu + (size_t)u * kActChunk,
+                  (unsigned)rows * 128u, &bar_ld[u & 3]);
+    };
     for (;;) {
         if (tid == 0) {
             tile_id = atomicAdd(&A.tile_queue[0], 1);
@@ -594,44 +662,39 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
         __syncthreads();
         ray_phase_refill(A, view, M, T, K, sbeam, slots, fin_slot, 0, &next_ray, xt, P.scale);
         // ---- the actor on the tile's observations ----
-        __syncthreads();
+        // the input tile, written by generic stores, is read by the MMAs
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads(); // the map's region is free: the weight buffers
+        int u = 0;
+        if (tid == 0)
+            for (int q = 0; q < 4 && q < nunits; ++q) issue_unit(q);
         for (int l = 0; l < 3; ++l) {
-            const int in = P.in[l], out = P.out[l], np = (out + 15) & ~15, nkc = (in + 63) >> 6;
+            const int out = P.out[l], np = (out + 15) & ~15;
             const bool last = l == 2;
-            load_tile<kActThreads>(wb[0], P.W[l], P.ld[l], 0, np, out, 0, in);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            for (int c = 0; c < nkc; ++c) {
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned a = xt_a + c * kActChunk, b = wb[c & 1];
+            const int nk = (P.in[l] + 63) >> 6, nh = out > 128 ? 2 : 1;
+            if (tid == 0) {
+                for (int c = 0; c < nk; ++c)
+                    for (int h = 0; h < nh; ++h, ++u) {
+                        const int b = u & 3;
+                        act_wait(smem_addr(&bar_ld[b]), (ph_ld >> b) & 1u, A.status);
+                        ph_ld ^= 1u << b;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const unsigned a = xt_a + c * kActChunk, wbuf = wb0 + (unsigned)b * kActChunk;
+                        const int n = min(128, np - 128 * h);
 #pragma unroll
-                    for (int k16 = 0; k16 < 4; ++k16) {
-                        const unsigned acc = (c > 0 || k16 > 0) ? 1u : 0u;
-                        if (np > 128) {
-                            mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(b + 32u * k16),
-                                    instr_desc(128, 128), acc);
-                            mma_f16(tmem + 128u, smem_desc(a + 32u * k16),
-                                    smem_desc(b + 128u * 128u + 32u * k16),
-                                    instr_desc(128, np - 128), acc);
-                        } else {
-                            mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(b + 32u * k16),
-                                    instr_desc(128, np), acc);
-                        }
+                        for (int k16 = 0; k16 < 4; ++k16)
+                            mma_f16(tmem + 128u * h, smem_desc(a + 32u * k16),
+                                    smem_desc(wbuf + 32u * k16), instr_desc(128, n),
+                                    (c > 0 || k16 > 0) ? 1u : 0u);
+                        mma_commit(smem_addr(&bar_w[b]));
+                        pend_w |= 1u << b;
+                        // four units ahead, into this buffer once these MMAs are done
+                        if (u + 4 < nunits) issue_unit(u + 4);
                     }
-                    mma_commit(smem_addr(&bar_mma));
-                }
-                // the other buffer was read by chunk c - 1's MMAs, which have completed
-                if (c + 1 < nkc) {
-                    load_tile<kActThreads>(wb[(c + 1) & 1], P.W[l], P.ld[l], 0, np, out,
-                                           64 * (c + 1), in);
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                }
-                act_wait(smem_addr(&bar_mma), mma_parity, A.status);
-                mma_parity ^= 1u;
+                // the layer's last MMAs (and so every one of its MMAs) have completed
+                wait_mma((u - 1) & 3);
             }
+            __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = quad * 32 + lane;
             if (!last) {
@@ -1004,6 +1067,19 @@ int launch_act_step(const StepArgs &a, const ActArgs &p, void *stream) {
     err = cudaLaunchKernel(fn, dim3(grid), dim3(kActThreads), args, smem,
                            static_cast<cudaStream_t>(stream));
     if (err != cudaSuccess) return (int)err;
+    return (int)cudaGetLastError();
+}
+
+int act_units(const ActArgs &p) {
+    int n = 0;
+    for (int l = 0; l < 3; ++l) n += ((p.in[l] + 63) >> 6) * (p.out[l] > 128 ? 2 : 1);
+    return n;
+}
+
+int launch_act_swizzle(const ActArgs &p, unsigned char *dst, void *stream) {
+    const int n = act_units(p);
+    act_swizzle_kernel<<<(n * 1024 + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(p, dst,
+                                                                                          n);
     return (int)cudaGetLastError();
 }
 
