@@ -231,10 +231,17 @@ void chessboard_distance(const nav_map &mp, int stride, uint8_t *out) {
         }
 }
 
-// Mean number of cells a ray walks before a blocked cell, the map edge or
-// r_max (cells), over a fixed sample of rays from free cells in seeded
-// directions: the relative cost of a tile's rays on this map.
-float sample_ray_cost(const nav_map &mp, float rmax_c) {
+// Relative cost of one ray on this map, in iterations of the ray loop, over
+// a fixed sample of rays from free cells in seeded directions: a fixed
+// per-ray part (set-up, result, refill: about as much as kRayFixedIters
+// iterations, measured with rays cut to one cell) plus the iterations of
+// the walk to a blocked cell, the map edge or r_max.  With distance bytes
+// (dist, rows of `stride` bytes, padded like the device copy) an iteration
+// at a cell of distance d >= 2 covers the next d - 1 boundaries of the
+// ray's major axis, as the device's jumps do; without, every cell is one.
+constexpr double kRayFixedIters = 8.0;
+
+float sample_ray_cost(const nav_map &mp, float rmax_c, const uint8_t *dist, int stride) {
     const int W = mp.width, H = mp.height;
     auto blocked = [&](int i, int j) {
         return i < 0 || j < 0 || i >= W || j >= H || mp.occ[(size_t)j * W + i] != 0;
@@ -248,25 +255,36 @@ float sample_ray_cost(const nav_map &mp, float rmax_c) {
     };
     double total = 0.0;
     int n = 0;
-    for (int tries = 0; tries < 4096 && n < 256; ++tries) {
+    for (int tries = 0; tries < 16384 && n < 1024; ++tries) {
         const int i0 = (int)(next() % (unsigned long long)W), j0 = (int)(next() % (unsigned long long)H);
         if (blocked(i0, j0)) continue;
         const double a = (double)(next() >> 11) * (6.283185307179586 / 9007199254740992.0);
         const double dx = std::cos(a), dy = std::sin(a);
+        const bool xmaj = std::fabs(dx) >= std::fabs(dy);
         double x = i0 + 0.5, y = j0 + 0.5;
-        int i = i0, j = j0, cells = 1;
+        int i = i0, j = j0;
         const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
         const double tdx = dx != 0 ? std::fabs(1.0 / dx) : 1e30, tdy = dy != 0 ? std::fabs(1.0 / dy) : 1e30;
         double tx = dx > 0 ? (i + 1 - x) * tdx : dx < 0 ? (x - i) * tdx : 1e30;
         double ty = dy > 0 ? (j + 1 - y) * tdy : dy < 0 ? (y - j) * tdy : 1e30;
+        // cover: the major-axis count at which the current jump ends; -1: the
+        // next cell starts an iteration; -2: a single step is under way
+        int iters = 0, major = 0, cover = -1;
         for (;;) {
+            if (cover == -1 || (cover >= 0 && major >= cover)) {
+                ++iters;
+                const int d = dist ? dist[(size_t)(j + kPad) * stride + (i + kPad)] : 1;
+                cover = d >= 2 ? major + d - 1 : -2;
+            }
             const double t = std::min(tx, ty);
             if (t > rmax_c) break;
-            if (tx <= ty) { i += sx; tx += tdx; } else { j += sy; ty += tdy; }
-            ++cells;
+            const bool stepx = tx <= ty;
+            if (stepx) { i += sx; tx += tdx; } else { j += sy; ty += tdy; }
+            if (stepx == xmaj) ++major;
+            if (cover == -2) cover = -1;
             if (blocked(i, j)) break;
         }
-        total += cells;
+        total += kRayFixedIters + iters;
         ++n;
     }
     return n ? (float)(total / n) : 1.0f;
@@ -306,16 +324,64 @@ int fit_tile(const nav_handle *h, long long slots, int te_max) {
 // Cuts the envs perm[s, t) of one (map, beam table) group into
 // ceil((t - s) / te) tiles of nearly equal size (sizes differ by at most
 // one), so that no tile is a small remainder.
-void cut_group(int s, int t, int te, int map, int tab, std::vector<TileDev> &out) {
-    const int n = t - s, k = (n + te - 1) / te;
+void cut_group_n(int s, int t, int k, int map, int tab, std::vector<TileDev> &out) {
+    const int n = t - s;
     for (int i = 0; i < k; ++i) {
         const int b = s + (int)((long long)n * i / k), e = s + (int)((long long)n * (i + 1) / k);
         out.push_back(TileDev{map, tab, b, e - b});
     }
 }
 
-// Groups envs by (map, beam table) and cuts each group into tiles of at most
-// tile_envs envs (cut_group).  The queue runs over the largest tiles first so that the
+void cut_group(int s, int t, int te, int map, int tab, std::vector<TileDev> &out) {
+    cut_group_n(s, t, (t - s + te - 1) / te, map, tab, out);
+}
+
+// Tiles per (map, beam table) group: as many in all as tiles of at most te
+// envs would make (sum of ceil(n_g / te)), shared out in proportion to each
+// group's sampled ray cost (envs x beams x cost per ray on its map), so that
+// the tiles of cheap and dear maps take about equal time; each group gets at
+// least ceil(n_g / kMaxTileEnvs) and at most n_g tiles.
+std::vector<int> weighted_tile_counts(const nav_handle *h, const std::vector<int> &perm,
+                                      const std::vector<std::pair<int, int>> &groups, int te) {
+    const size_t G = groups.size();
+    std::vector<int> k(G), lo(G), hi(G);
+    std::vector<double> want(G);
+    long long total = 0;
+    double cost = 0.0;
+    for (size_t g = 0; g < G; ++g) {
+        const int n = groups[g].second - groups[g].first;
+        const int e = perm[groups[g].first];
+        total += (n + te - 1) / te;
+        want[g] = (double)n * h->env_k[e] * h->map_ray_cost[h->env_map[e]];
+        cost += want[g];
+        lo[g] = (n + kMaxTileEnvs - 1) / kMaxTileEnvs;
+        hi[g] = n;
+    }
+    long long used = 0;
+    std::vector<std::pair<double, int>> frac;
+    for (size_t g = 0; g < G; ++g) {
+        want[g] = want[g] / cost * (double)total;
+        k[g] = std::min(hi[g], std::max(lo[g], (int)std::floor(want[g])));
+        used += k[g];
+        frac.push_back({want[g] - std::floor(want[g]), (int)g});
+    }
+    std::stable_sort(frac.begin(), frac.end(),
+                     [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+                         return a.first > b.first;
+                     });
+    for (size_t r = 0; used < total && r < 4 * G + 4; ++r) {
+        const int g = frac[r % G].second;
+        if (k[g] < hi[g]) {
+            ++k[g];
+            ++used;
+        }
+    }
+    return k;
+}
+
+// Groups envs by (map, beam table) and cuts each group into nearly equal
+// tiles, as many per group as weighted_tile_counts gives (tile_envs sets
+// their number).  The queue runs over the largest tiles first so that the
 // longest CTAs start early: by map size x beams (order 0, ties in map order)
 // or by envs x beams x sampled cells per ray (order 1, ties by map size).
 int build_tiles(nav_handle *h) {
@@ -328,14 +394,20 @@ int build_tiles(nav_handle *h) {
         return ka < kb;
     });
     std::vector<TileDev> tiles;
-    int s = 0;
-    while (s < E) {
+    std::vector<std::pair<int, int>> groups;
+    for (int s = 0; s < E;) {
         int t = s;
         while (t < E && h->env_map[perm[t]] == h->env_map[perm[s]] &&
                h->env_tab[perm[t]] == h->env_tab[perm[s]])
             ++t;
-        cut_group(s, t, h->cfg.tile_envs, h->env_map[perm[s]], h->env_tab[perm[s]], tiles);
+        groups.push_back({s, t});
         s = t;
+    }
+    const std::vector<int> counts = weighted_tile_counts(h, perm, groups, h->cfg.tile_envs);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const int s = groups[g].first;
+        cut_group_n(s, groups[g].second, counts[g], h->env_map[perm[s]], h->env_tab[perm[s]],
+                    tiles);
     }
     std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &x, const TileDev &y) {
         const long long wx = (long long)h->maps[x.map].n_words * h->env_k[perm[x.env_begin]];
@@ -364,6 +436,8 @@ int build_tiles(nav_handle *h) {
     h->a.tiles = h->d_tiles;
     h->a.perm = h->d_perm;
     h->a.n_tiles = (int)tiles.size();
+    h->a.max_tile_envs = 1;
+    for (const TileDev &t : tiles) h->a.max_tile_envs = std::max(h->a.max_tile_envs, t.env_count);
     // tiles of the host-step pipeline: the same grouping within each env range
     std::vector<int> pperm;
     {
@@ -397,6 +471,8 @@ int build_tiles(nav_handle *h) {
                 const long long wy = (long long)h->maps[y.map].n_words * h->env_k[pperm[y.env_begin]];
                 return wx > wy;
             });
+            for (size_t i = t0; i < ptiles.size(); ++i)
+                h->a.max_tile_envs = std::max(h->a.max_tile_envs, ptiles[i].env_count);
             h->part_tile_off.push_back((int)ptiles.size());
             h->part_env_off.push_back(e1);
         }
@@ -606,7 +682,9 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
             chessboard_distance(mp, bstride, dist_all.data() + md.dist_off);
         }
         h->maps.push_back(md);
-        h->map_ray_cost.push_back(sample_ray_cost(mp, max_range * md.inv_res));
+        h->map_ray_cost.push_back(sample_ray_cost(
+            mp, max_range * md.inv_res,
+            md.dist_off >= 0 ? dist_all.data() + md.dist_off : nullptr, bstride));
     }
     // envs
     h->env_map.resize(n_envs);
@@ -773,6 +851,8 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     ce = h->arena.alloc(&A.step, E);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.episode, E);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.dyn, E * std::max(P.n_dyn, 1));
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.nxt_pose, E);
+    if (ce == cudaSuccess) ce = h->arena.alloc(&A.nxt_goal, E);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.status, 1);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.tile_queue, 2);
     if (ce == cudaSuccess) ce = h->arena.alloc(&A.split_q, 4);
@@ -783,6 +863,8 @@ int nav_create_ex(const nav_map *maps, int n_maps, const int *env_map, const int
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMalloc(state)"));
     cudaMemset(A.step, 0, E * sizeof(int));
     cudaMemset(A.episode, 0, E * sizeof(unsigned));
+    cudaMemset(A.nxt_pose, 0, E * sizeof(float4));
+    cudaMemset(A.nxt_goal, 0, E * sizeof(float2));
     cudaMemset(A.status, 0, sizeof(int));
     cudaMemset(A.tile_queue, 0, 2 * sizeof(int));
     cudaMemset(A.split_q, 0, 4 * sizeof(int));
@@ -1034,6 +1116,12 @@ int nav_set_state(nav_handle *h, uint64_t seed, const float *f8_host, const int3
         e = cudaMemcpy(h->a.dyn, dyn_host, E * h->par.n_dyn * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(state)");
     h->seed = seed;
+    // the next-episode records follow from (seed, env, episode + 1)
+    StepArgs A = h->a;
+    A.seed = seed;
+    e = (cudaError_t)launch_prep_all(A, h->n_envs, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "next-episode records");
     return NAV_OK;
 }
 
@@ -1157,7 +1245,7 @@ int copy_state(nav_handle *h, bool save) {
     const size_t nd = (size_t)std::max(h->par.n_dyn, 1);
     cudaError_t e = cudaSuccess;
     if (!h->snap) {
-        e = h->arena.alloc(&h->snap, 10 * E + 4 * nd * E);
+        e = h->arena.alloc(&h->snap, 10 * E + 4 * nd * E + 6 * E);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(snapshot)");
     }
     StepArgs &A = h->a;
@@ -1171,6 +1259,16 @@ int copy_state(nav_handle *h, bool save) {
         float *sn = h->snap + 10 * E;
         e = save ? cudaMemcpyAsync(sn, A.dyn, nd * E * 16, cudaMemcpyDeviceToDevice, h->stream)
                  : cudaMemcpyAsync(A.dyn, sn, nd * E * 16, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e == cudaSuccess) {
+        float *sn = h->snap + 10 * E + 4 * nd * E;
+        e = save ? cudaMemcpyAsync(sn, A.nxt_pose, E * 16, cudaMemcpyDeviceToDevice, h->stream)
+                 : cudaMemcpyAsync(A.nxt_pose, sn, E * 16, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = save ? cudaMemcpyAsync(sn + 4 * E, A.nxt_goal, E * 8, cudaMemcpyDeviceToDevice,
+                                       h->stream)
+                     : cudaMemcpyAsync(A.nxt_goal, sn + 4 * E, E * 8, cudaMemcpyDeviceToDevice,
+                                       h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "state snapshot copy");
     return NAV_OK;

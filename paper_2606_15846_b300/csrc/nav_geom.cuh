@@ -610,7 +610,48 @@ struct EnvSlot {
     long long obs_off, ray_off;
     int env;
     int fin;
+    int prep;     // 1: the env started episode ep; its next-episode record is due
+    unsigned ep;
 };
+
+// Origin of one scan for the refilled ray phase, set up once per env
+// instead of once per ray: pose in cells, heading's sin and cos, floors of
+// the position, the origin cell's view index (0, a padding cell, when off
+// the map) and its distance byte (0: every ray stops at once), and the
+// env's row offsets.
+struct __align__(16) RayOrigin {
+    float xc, yc, st, ct;
+    float flx, fly;
+    int b0, d0;
+    long long obs_off, ray_off;
+};
+
+// cast_ray's set-up before its first step, for a scan from (xc, yc) cells.
+template <class V>
+__device__ __forceinline__ void set_origin(const V &view, const MapDev &M, float xc, float yc,
+                                           float st, float ct, long long obs_off,
+                                           long long ray_off, RayOrigin &o) {
+    RayOrigin r;
+    r.xc = xc;
+    r.yc = yc;
+    r.st = st;
+    r.ct = ct;
+    r.flx = r.fly = 0.0f;
+    r.b0 = r.d0 = 0;
+    r.obs_off = obs_off;
+    r.ray_off = ray_off;
+    if (xc >= 0.0f && yc >= 0.0f) {
+        const float fx = floorf(xc), fy = floorf(yc);
+        const int i0 = (int)fx, j0 = (int)fy;
+        if (i0 < M.w && j0 < M.h) {
+            r.b0 = cell_index(view, i0, j0);
+            r.d0 = view.dist_at(r.b0);
+            r.flx = fx;
+            r.fly = fy;
+        }
+    }
+    o = r;
+}
 
 template <class V>
 __device__ __forceinline__ bool static_blocked(const V &v, const MapDev &M, int i, int j) {
@@ -624,10 +665,9 @@ __device__ __forceinline__ bool static_blocked(const V &v, const MapDev &M, int 
 // 64 misses the draw nearest the band, first on ties), moving discs from
 // spawnable cells at least dyn_min_sep away (draws 1024 + 64 q + a, a < 16)
 // with speed and heading from draw 1024 + 64 q + 48.
-template <class B>
-__device__ void reset_env(const StepArgs &A, const B &bits, const MapDev &M, int e,
-                          unsigned episode, float &x, float &y, float &th, float &gx, float &gy,
-                          float &dprev, float4 *ob) {
+// Spawn pose and goal of env e for `episode` (draws 0..65).
+__device__ void reset_pose(const StepArgs &A, const MapDev &M, int e, unsigned episode, float &x,
+                           float &y, float &th, float &gx, float &gy, float &dprev) {
     const CsDev cs = A.cs[A.env_cs[e]];
     if (cs.n_spawn <= 0) {
         atomicOr(A.status, kStatusNoSpawn);
@@ -675,7 +715,19 @@ __device__ void reset_env(const StepArgs &A, const B &bits, const MapDev &M, int
         const float ddx = bx - x, ddy = by - y;
         dprev = sqrtf(ddx * ddx + ddy * ddy);
     }
+}
+
+// Moving discs of env e for `episode`, spawned around the robot's spawn
+// point (x, y) (draws 1024 + 64 q + a).
+__device__ void reset_discs(const StepArgs &A, const MapDev &M, int e, unsigned episode, float x,
+                            float y, float4 *ob) {
     const int nd = A.p.n_dyn;
+    if (nd <= 0) return;
+    const CsDev cs = A.cs[A.env_cs[e]];
+    if (cs.n_spawn <= 0) {
+        for (int q = 0; q < nd; ++q) ob[q] = make_float4(x, y, 0.0f, 0.0f);
+        return;
+    }
     for (int q = 0; q < nd; ++q) {
         float ox = x, oy = y;
         for (int a = 0; a < 16; ++a) {
@@ -694,6 +746,25 @@ __device__ void reset_env(const StepArgs &A, const B &bits, const MapDev &M, int
         sincos_taylor(hd, sh, ch);
         ob[q] = make_float4(ox, oy, sp * ch, sp * sh);
     }
+}
+
+template <class B>
+__device__ void reset_env(const StepArgs &A, const B &, const MapDev &M, int e, unsigned episode,
+                          float &x, float &y, float &th, float &gx, float &gy, float &dprev,
+                          float4 *ob) {
+    reset_pose(A, M, e, episode, x, y, th, gx, gy, dprev);
+    reset_discs(A, M, e, episode, x, y, ob);
+}
+
+// The next-episode record of env e: spawn pose, goal and initial goal
+// distance of episode ep + 1, a function of (seed, e, ep + 1) alone.  A step
+// that ends an episode takes the env's record and has the record of the
+// episode after it written here, off the path of the step's scan.
+__device__ void prep_next(const StepArgs &A, const MapDev &M, int e, unsigned ep) {
+    float x, y, th, gx, gy, dprev;
+    reset_pose(A, M, e, ep + 1u, x, y, th, gx, gy, dprev);
+    A.nxt_pose[e] = make_float4(x, y, th, dprev);
+    A.nxt_goal[e] = make_float2(gx, gy);
 }
 
 // Observation tail (Eq. 1): goal distance, bearing in the body frame, v, w.
@@ -731,16 +802,22 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
     unsigned episode;
     bool restamp = true; // spans in dmain must describe the discs after this step
     slot.fin = 0;
+    slot.prep = 0;
     if (A.mode == 1) {
         episode = 0;
         reset_env(A, bits, M, e, episode, x, y, th, gx, gy, dprev, ob);
         v = w = 0.0f;
         step = 0;
+        slot.prep = 1;
+        slot.ep = 0;
     } else {
         x = A.x[e]; y = A.y[e]; th = A.th[e];
         gx = A.gx[e]; gy = A.gy[e]; dprev = A.dprev[e];
         step = A.step[e];
         episode = A.episode[e];
+        // the next episode's start, read with the state (used on a reset)
+        const float4 np = A.nxt_pose[e];
+        const float2 ng = A.nxt_goal[e];
         if (DYN)
             for (int q = 0; q < nd; ++q) ob[q] = A.dyn[(size_t)e * nd + q];
         const RobotDev rb = A.robots[A.env_robot[e]];
@@ -846,12 +923,17 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
                 slot.fxc = xc; slot.fyc = yc; slot.fst = st; slot.fct = ct;
                 if (DYN) *dfin = *dmain;
             }
-            // a8: sparse reset in place
+            // a8: sparse reset in place, from the next-episode record (the
+            // record of the episode after it is written by prep_next)
             episode += 1;
-            reset_env(A, bits, M, e, episode, x, y, th, gx, gy, dprev, ob);
+            x = np.x; y = np.y; th = np.z; dprev = np.w;
+            gx = ng.x; gy = ng.y;
+            if (DYN) reset_discs(A, M, e, episode, x, y, ob);
             v = w = 0.0f;
             step = 0;
             restamp = true;
+            slot.prep = 1;
+            slot.ep = episode;
         }
     }
     A.x[e] = x; A.y[e] = y; A.th[e] = th; A.v[e] = v; A.w[e] = w;

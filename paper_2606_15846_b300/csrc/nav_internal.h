@@ -81,11 +81,16 @@ struct StepArgs {
     const TileDev *tiles;
     const int *perm;
     int n_tiles;
+    int max_tile_envs; // envs of the largest tile
     int *tile_queue; // [0] next tile to hand out, [1] CTAs finished; zero between launches
     // state (structure of arrays)
     float *x, *y, *th, *v, *w, *gx, *gy, *dprev;
     int *step;
     unsigned *episode;
+    // next-episode record per env: spawn (x, y, theta, goal distance) and
+    // goal of episode + 1 (written by prep_next, read by the env phase)
+    float4 *nxt_pose;
+    float2 *nxt_goal;
     float4 *dyn; // [n_envs][n_dyn]
     // io
     const float *actions;
@@ -118,7 +123,8 @@ struct StepArgs {
 enum StatusBits {
     kStatusNoSpawn = 1,
     kStatusCopyTimeout = 2,
-    kStatusBadPose = 4
+    kStatusBadPose = 4,
+    kStatusQueue = 8 // a CTA drew more tiles than a launch holds
 };
 
 // Defaults: the autotuner's usual choice for 256 x 256 maps with distance
@@ -170,6 +176,10 @@ int launch_act_step(const StepArgs &a, const ActArgs &p, void *stream);
 int launch_act_swizzle(const ActArgs &p, unsigned char *dst, void *stream);
 int act_units(const ActArgs &p);
 size_t act_step_smem(const StepArgs &a);
+
+// Rewrites every env's next-episode record from its episode counter (after
+// the state was set from outside).
+int launch_prep_all(const StepArgs &a, int n_envs, void *stream);
 
 // Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step).
 int launch_uniform_actions(float *out, int n_envs, unsigned long long seed, unsigned step,

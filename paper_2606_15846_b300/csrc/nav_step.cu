@@ -152,52 +152,64 @@ __device__ __forceinline__ void tmem_free_cols(unsigned tmem, unsigned ncols) {
 struct TileRay {
     float tM, tm, tdM, tdm, tM0, tm0, kM, km, adm, offm, nM, t;
     int b, b0, sbM, sbm, d, tie;
-    int rid; // ray of the tile: slot x K + k, final scans after the tile's own
+    int o, k;  // origin record and beam of the ray
     bool stopped;
 };
 
-// Sets up ray rid of the tile (cast_ray's set-up; a blocked or off-map origin
-// ends the ray at once, at its cell or at a padding cell).
-template <class V>
-__device__ __forceinline__ void tile_ray_init(const V &view, const MapDev &M, int rid, int n_main,
-                                              int K, float inv_k, float rmax_c,
-                                              const float2 *beams, const EnvSlot *slots,
-                                              const int *fin_slot, TileRay &R) {
+// Quotient by K of a ray index 0 <= r < 2^31 for 1 <= K < 2^16: a
+// multiply-high by m = ceil(2^(32+s) / K) with s = ceil(log2 K) - 1, so
+// m < 2^32; m K exceeds 2^(32+s) by e < K <= 2^(s+1), and r e < 2^(32+s)
+// keeps floor(r m / 2^(32+s)) equal to floor(r / K).
+struct DivK {
+    unsigned m;
+    int s;
+    bool one;
+    __device__ __forceinline__ explicit DivK(int K) {
+        one = K == 1;
+        s = one ? 0 : 31 - __clz(K - 1);
+        m = one ? 0u
+                : (unsigned)((((unsigned long long)1 << (32 + s)) + (unsigned long long)K - 1ull) /
+                             (unsigned long long)K);
+    }
+    __device__ __forceinline__ int operator()(int r) const {
+        return one ? r : (int)(__umulhi((unsigned)r, m) >> s);
+    }
+};
+
+// Sets up ray rid of the tile (cast_ray's set-up from the origin record;
+// a blocked or off-map origin ends the ray at once, at its cell or at a
+// padding cell).  Rays [0, n_main) are the envs' own scans (origin q), the
+// rest the final scans (origin fin_base + q).  Branch-free: the lanes of a
+// warp set up rays of any direction together.
+__device__ __forceinline__ void tile_ray_init(int pb, int rid, int n_main, int K, DivK divk,
+                                              int fin_base, float rmax_c, const float2 *beams,
+                                              const RayOrigin *org, TileRay &R) {
     const bool fin = rid >= n_main;
-    const int rr = fin ? rid - n_main : rid; // < 2^24: exact as a float
-    int q = (int)((float)rr * inv_k);
-    q -= q * K > rr ? 1 : 0;
-    q += (q + 1) * K <= rr ? 1 : 0;
+    const int rr = fin ? rid - n_main : rid;
+    const int q = divk(rr);
     const int k = rr - q * K;
-    const EnvSlot &es = slots[fin ? fin_slot[q] : q];
-    const float sx = fin ? es.fst : es.st, cx = fin ? es.fct : es.ct;
-    const float xc = fin ? es.fxc : es.xc, yc = fin ? es.fyc : es.yc;
+    R.o = fin ? fin_base + q : q;
+    R.k = k;
+    const float4 o0 = *reinterpret_cast<const float4 *>(&org[R.o].xc);
+    const float4 o1 = *reinterpret_cast<const float4 *>(&org[R.o].flx);
+    const float xc = o0.x, yc = o0.y, sx = o0.z, cx = o0.w;
+    const float fx = o1.x, fy = o1.y;
+    const int b0 = __float_as_int(o1.z), d0 = __float_as_int(o1.w);
     const float2 ab = beams[k];
     // Eq. 4: direction of theta + alpha_k by angle addition
     const float dx = cx * ab.x - sx * ab.y;
     const float dy = sx * ab.x + cx * ab.y;
-    R.rid = rid;
     R.kM = R.km = 0.0f;
     R.t = 0.0f;
-    R.stopped = true;
-    R.b = R.b0 = 0; // a padding cell: an off-map origin reports hit -1
-    R.d = 0;
-    R.tM = R.tm = INFINITY;
-    if (!(xc >= 0.0f && yc >= 0.0f)) return;
-    const float fx = floorf(xc), fy = floorf(yc);
-    const int i0 = (int)fx, j0 = (int)fy;
-    if (i0 >= M.w || j0 >= M.h) return;
-    const int pb = view.stride;
-    R.b = R.b0 = cell_index(view, i0, j0);
-    R.d = view.dist_at(R.b);
-    if (R.d == 0) return;
-    R.stopped = false;
-    int sbx = 0, sby = 0;
-    float tdx = 0.0f, tdy = 0.0f, tx0 = INFINITY, ty0 = INFINITY;
-    if (dx > 0.0f) { sbx = 1; tdx = __frcp_rn(dx); tx0 = ((fx + 1.0f) - xc) * tdx; }
-    else if (dx < 0.0f) { sbx = -1; tdx = __frcp_rn(-dx); tx0 = (xc - fx) * tdx; }
-    if (dy > 0.0f) { sby = pb; tdy = __frcp_rn(dy); ty0 = ((fy + 1.0f) - yc) * tdy; }
-    else if (dy < 0.0f) { sby = -pb; tdy = __frcp_rn(-dy); ty0 = (yc - fy) * tdy; }
+    R.b = R.b0 = b0;
+    R.d = d0;
+    R.stopped = d0 == 0;
+    const float rx = __frcp_rn(fabsf(dx)), ry = __frcp_rn(fabsf(dy));
+    const float tdx = dx != 0.0f ? rx : 0.0f, tdy = dy != 0.0f ? ry : 0.0f;
+    const float tx0 = dx > 0.0f ? ((fx + 1.0f) - xc) * rx : (dx < 0.0f ? (xc - fx) * rx : INFINITY);
+    const float ty0 = dy > 0.0f ? ((fy + 1.0f) - yc) * ry : (dy < 0.0f ? (yc - fy) * ry : INFINITY);
+    const int sbx = dx > 0.0f ? 1 : (dx < 0.0f ? -1 : 0);
+    const int sby = dy > 0.0f ? pb : (dy < 0.0f ? -pb : 0);
     const bool xmaj = fabsf(dx) >= fabsf(dy);
     R.tdM = xmaj ? tdx : tdy;
     R.tM0 = xmaj ? tx0 : ty0;
@@ -210,8 +222,8 @@ __device__ __forceinline__ void tile_ray_init(const V &view, const MapDev &M, in
     R.tie = xmaj ? 1 : 0;
     R.offm = adm > 0.0f ? 1.0f - R.tm0 * adm : 0.0f;
     R.nM = floorf(__fmaf_rn(rmax_c, adM, 1.0f - R.tM0 * adM));
-    R.tM = R.tM0;
-    R.tm = R.tm0;
+    R.tM = R.stopped ? INFINITY : R.tM0;
+    R.tm = R.stopped ? INFINITY : R.tm0;
 }
 
 // One iteration for the lanes with act set (cast_ray's step or jump),
@@ -255,19 +267,18 @@ __device__ __forceinline__ void tile_ray_step(const V &view, float rmax_c, TileR
 template <class V>
 __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev &M,
                                  const TileDev &T, int K, const float2 *beams,
-                                 const EnvSlot *slots, const int *fin_slot, int n_fin,
-                                 int *next_ray, unsigned char *xt = nullptr,
-                                 const float *xscale = nullptr) {
+                                 const RayOrigin *org, int fin_base, int n_fin, int *next_ray,
+                                 unsigned char *xt = nullptr, const float *xscale = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n_main = T.env_count * K;
     const int total = n_main + n_fin * K;
     const float rmax_c = A.max_range * M.inv_res;
-    const float inv_k = 1.0f / (float)K;
+    const DivK divk(K);
     const int m = A.p.n_sectors;
     TileRay R;
     R.tM = R.tm = INFINITY;
     R.tdM = R.tdm = R.tM0 = R.tm0 = R.kM = R.km = R.adm = R.offm = R.nM = R.t = 0.0f;
-    R.b = R.b0 = R.sbM = R.sbm = R.d = R.tie = R.rid = 0;
+    R.b = R.b0 = R.sbM = R.sbm = R.d = R.tie = R.o = R.k = 0;
     R.stopped = false;
     bool act = false, res = false, more = true;
     unsigned vis = 0, nrays = 0;
@@ -277,27 +288,25 @@ __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev 
             for (;;) {
                 tile_ray_step(view, rmax_c, R, act, res);
                 tile_ray_step(view, rmax_c, R, act, res);
+                tile_ray_step(view, rmax_c, R, act, res);
+                tile_ray_step(view, rmax_c, R, act, res);
                 if (__popc(__ballot_sync(kFull, !act)) >= thr) break;
             }
         }
         if (res) {
             // cast_ray's results: range, hit cell, visits
-            const bool fin = R.rid >= n_main;
-            const int rr = fin ? R.rid - n_main : R.rid;
-            int q = (int)((float)rr * inv_k);
-            q -= q * K > rr ? 1 : 0;
-            q += (q + 1) * K <= rr ? 1 : 0;
-            const int k = rr - q * K;
-            const EnvSlot &es = slots[fin ? fin_slot[q] : q];
+            const bool fin = R.o >= fin_base;
+            const int k = R.k;
             const float range = R.stopped ? R.t * M.res : A.max_range;
             const float c = fminf(range, A.max_range);
-            float *row = (fin ? A.final_obs : A.obs) + es.obs_off;
+            float *row = (fin ? A.final_obs : A.obs) + org[R.o].obs_off;
             if (m == 0) row[k] = c;
             else atomicMin(reinterpret_cast<int *>(row + k / (K / m)), __float_as_int(c));
             if (xt && !fin)
-                *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(q, k)) =
+                *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(R.o, k)) =
                     __float2bfloat16_rn(xscale ? c * __ldg(xscale + k) : c);
-            const unsigned v = 1u + (unsigned)R.kM + (unsigned)R.km;
+            // visits (exact: both counts are integers below 2^24)
+            const unsigned v = 1u + (unsigned)(R.kM + R.km);
             if (!fin && A.dbg_range) {
                 int hit = -2;
                 if (R.stopped) {
@@ -305,7 +314,7 @@ __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev 
                     const int i = ii - kPad, j = jj - kPad;
                     hit = (i < 0 || j < 0 || i >= M.w || j >= M.h) ? -1 : j * M.w + i;
                 }
-                const long long ro = es.ray_off + k;
+                const long long ro = org[R.o].ray_off + k;
                 A.dbg_range[ro] = range;
                 A.dbg_hit[ro] = hit;
                 A.dbg_vis[ro] = v;
@@ -321,7 +330,7 @@ __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev 
             base = __shfl_sync(kFull, base, 0);
             const int r = base + __popc(want & ((1u << lane) - 1u));
             if (((want >> lane) & 1u) && r < total) {
-                tile_ray_init(view, M, r, n_main, K, inv_k, rmax_c, beams, slots, fin_slot, R);
+                tile_ray_init(view.stride, r, n_main, K, divk, fin_base, rmax_c, beams, org, R);
                 act = !R.stopped;
                 res = R.stopped;
             }
@@ -349,20 +358,37 @@ template <bool DYN, bool MARCH, bool REFILL, class V>
 __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const MapDev &M,
                                          const TileDev &T, int K, const float2 *sbeam,
                                          EnvSlot *slots, int *fin_slot, int *n_fin, DynEnv *sdyn,
-                                         int *next_chunk) {
+                                         RayOrigin *org, int *next_chunk) {
     const int tid = threadIdx.x;
-    if (tid < T.env_count)
+    constexpr bool kRefill = REFILL && !DYN && !MARCH && has_dist<V>::value;
+    if (tid < T.env_count) {
         env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1]);
+        if constexpr (kRefill) {
+            const EnvSlot &es = slots[tid];
+            set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[tid]);
+        }
+    }
     __syncthreads();
     if (tid < 32) {
         const bool f = tid < T.env_count && slots[tid].fin;
         const unsigned m = __ballot_sync(kFull, f);
-        if (f) fin_slot[__popc(m & ((1u << tid) - 1u))] = tid;
+        const int fi = __popc(m & ((1u << tid) - 1u));
+        if (f) {
+            fin_slot[fi] = tid;
+            if constexpr (kRefill) {
+                const EnvSlot &es = slots[tid];
+                set_origin(view, M, es.fxc, es.fyc, es.fst, es.fct, es.obs_off, es.ray_off,
+                           org[kMaxTileEnvs + fi]);
+            }
+        }
         if (tid == 0) *n_fin = __popc(m);
     }
     __syncthreads();
-    if constexpr (REFILL && !DYN && !MARCH && has_dist<V>::value)
-        ray_phase_refill(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, next_chunk);
+    // next-episode records of the envs that reset, written by warp 0 while
+    // the other warps start on the rays
+    if (tid < T.env_count && slots[tid].prep) prep_next(A, M, slots[tid].env, slots[tid].ep);
+    if constexpr (kRefill)
+        ray_phase_refill(A, view, M, T, K, sbeam, org, kMaxTileEnvs, *n_fin, next_chunk);
     else
         ray_phase<DYN, MARCH>(A, view, M, T, K, sbeam, slots, fin_slot, *n_fin, sdyn, next_chunk);
 }
@@ -370,7 +396,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
 // Persistent CTAs: each CTA takes tiles from a global queue until none are
 // left.  A tile's map is staged into shared memory (its distance bytes or
 // its packed bits, by bulk TMA copies) only when the CTA's previous tile used
-// another map.  The last CTA to finish zeroes the queue
+// another map.  The CTA that draws the launch's last index zeroes the queue
 // for the next launch on the stream.
 // MINB: resident 512-thread CTAs per SM the register allocation must allow
 // (4, 3, 2 -> at most 32, 40, 64 registers per thread).
@@ -378,6 +404,7 @@ template <bool DYN, int MINB, bool MARCH, bool REFILL>
 __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ EnvSlot slots[kMaxTileEnvs];
+    __shared__ RayOrigin org[REFILL ? 2 * kMaxTileEnvs : 1];
     __shared__ int fin_slot[kMaxTileEnvs];
     __shared__ int n_fin;
     __shared__ int next_chunk;
@@ -393,14 +420,27 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
     const int tid = threadIdx.x;
     unsigned parity = 0;
     int beam_tab = -1;
+    // Every CTA draws tile indices until it gets one past the last tile, so a
+    // launch makes exactly n_tiles + gridDim draws; the CTA holding the last
+    // one zeroes the queue for the next launch (nobody draws after it).
+    const int last_draw = A.n_tiles + (int)gridDim.x - 1;
+    int cur = 0;
     if (tid == 0) {
         init_copy_barrier(&bar);
         staged_map = -1;
+        cur = atomicAdd(&A.tile_queue[0], 1);
     }
-    for (;;) {
+    // a CTA runs at most n_tiles tiles: a queue left non-zero by a failed
+    // launch ends the loop with a status bit instead of running on
+    for (int iter = 0;; ++iter) {
         if (tid == 0) {
-            tile_id = atomicAdd(&A.tile_queue[0], 1);
+            tile_id = cur;
             next_chunk = 0;
+            if (cur == last_draw) A.tile_queue[0] = 0;
+            if (iter >= A.n_tiles && cur < A.n_tiles) {
+                atomicOr(A.status, kStatusQueue);
+                tile_id = A.n_tiles;
+            }
         }
         __syncthreads();
         const int tile = tile_id;
@@ -444,27 +484,18 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         if (tid == 0) staged_map = mode == kMapGlobal || mode == kMapGlobalBytes ? -1 : T.map;
         if (mode == kMapSharedBytes)
             run_tile<DYN, MARCH, REFILL>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk);
         else if (mode == kMapSharedBits)
             run_tile<DYN, MARCH, REFILL>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk);
         else if (mode == kMapGlobalBytes)
             run_tile<DYN, MARCH, REFILL>(A, BytesGlobal{A.dist + M.dist_off, M.byte_stride}, M, T, K, sbeam,
-                                 slots, fin_slot, &n_fin, sdyn, &next_chunk);
+                                 slots, fin_slot, &n_fin, sdyn, org, &next_chunk);
         else
             run_tile<DYN, MARCH, REFILL>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk);
         __syncthreads();
-    }
-    if (tid == 0) {
-        __threadfence();
-        const int done = atomicAdd(&A.tile_queue[1], 1);
-        if (done == (int)gridDim.x - 1) {
-            // every CTA has taken its last (empty) tile: reset for the next launch
-            A.tile_queue[0] = 0;
-            A.tile_queue[1] = 0;
-            __threadfence();
-        }
+        if (tid == 0) cur = atomicAdd(&A.tile_queue[0], 1);
     }
 }
 
@@ -559,7 +590,7 @@ __device__ __forceinline__ bool act_wait(unsigned bar, unsigned parity, int *sta
 __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs A, const ActArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ EnvSlot slots[kActMaxEnvs];
-    __shared__ int fin_slot[1];
+    __shared__ RayOrigin org[kActMaxEnvs];
     __shared__ int next_ray;
     __shared__ int tile_id;
     __shared__ __align__(8) unsigned long long bar_map;
@@ -657,10 +688,14 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
         const BytesShared view{sbytes, M.byte_stride};
         if (tid < T.env_count) {
             env_phase<false>(A, view, M, K, tid, slots[tid], nullptr, nullptr);
-            act_tail(xt, P, tid, K, A.obs + slots[tid].obs_off);
+            const EnvSlot &es = slots[tid];
+            set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[tid]);
+            act_tail(xt, P, tid, K, A.obs + es.obs_off);
         }
         __syncthreads();
-        ray_phase_refill(A, view, M, T, K, sbeam, slots, fin_slot, 0, &next_ray, xt, P.scale);
+        // next-episode records of the envs that reset (their warps cast later)
+        if (tid < T.env_count && slots[tid].prep) prep_next(A, M, slots[tid].env, slots[tid].ep);
+        ray_phase_refill(A, view, M, T, K, sbeam, org, kActMaxEnvs, 0, &next_ray, xt, P.scale);
         // ---- the actor on the tile's observations ----
         // the input tile, written by generic stores, is read by the MMAs
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -781,6 +816,12 @@ __global__ void uniform_actions_kernel(float2 *out, int n_envs, unsigned long lo
 // chunks from a global queue and casts them with no CTA-wide barrier, then
 // takes the pending final scans env by env.  The last CTA resets the queues.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) prep_all_kernel(const StepArgs A, int n_envs) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_envs) return;
+    prep_next(A, A.maps[A.env_map[e]], e, A.episode[e]);
+}
+
 __global__ void __launch_bounds__(128) env_kernel(const StepArgs A, int n_envs) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_envs) return;
@@ -792,6 +833,7 @@ __global__ void __launch_bounds__(128) env_kernel(const StepArgs A, int n_envs) 
     slot.ray_off = A.ray_off[e];
     env_phase<false>(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, K, 0, slot, nullptr,
                      nullptr);
+    if (slot.prep) prep_next(A, M, e, slot.ep);
     A.ray_main[e] = make_float4(slot.xc, slot.yc, slot.st, slot.ct);
     if (slot.fin) {
         A.ray_fin[e] = make_float4(slot.fxc, slot.fyc, slot.fst, slot.fct);
@@ -1010,7 +1052,7 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     if (a.n_tiles <= 0) return 0;
     const bool dyn = a.p.n_dyn > 0;
     const size_t smem = (size_t)a.smem_region_bytes + (size_t)a.max_k * sizeof(float2) +
-                        (dyn ? (size_t)2 * cfg.tile_envs * sizeof(DynEnv) : 0);
+                        (dyn ? (size_t)2 * a.max_tile_envs * sizeof(DynEnv) : 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool march = a.p.sensor == 1;
     // lane refill applies to the exact traversal without moving discs
@@ -1080,6 +1122,11 @@ int launch_act_swizzle(const ActArgs &p, unsigned char *dst, void *stream) {
     const int n = act_units(p);
     act_swizzle_kernel<<<(n * 1024 + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(p, dst,
                                                                                           n);
+    return (int)cudaGetLastError();
+}
+
+int launch_prep_all(const StepArgs &a, int n_envs, void *stream) {
+    prep_all_kernel<<<(n_envs + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a, n_envs);
     return (int)cudaGetLastError();
 }
 
