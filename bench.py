@@ -186,9 +186,11 @@ def cpu_baseline(wl, seconds: float = 15.0):
                       f"first 512 envs, {el1:.1f} s"}
 
 
-def policy_rollout(steps: int = 20):
-    """Rollout with the policy in the loop on 65536 envs over 16 256x256 maps,
-    360 beams, actor 364-256-256-4 (random init, sampled actions): the actor
+def policy_rollout(steps: int = 20, n_envs: int = 65536, n_maps: int = 16):
+    """Rollout with the policy in the loop on 65536 envs over 16 256x256 maps
+    (or n_envs over n_maps; 18944 over 4 is one wave of the fused kernel's
+    128-env tiles), 360 beams, actor 364-256-256-4 (random init, sampled
+    actions): the actor
     inside the step kernel (nav_rollout_fused), the BF16 tensor-core policy
     as separate launches beside the step (nav_rollout), and the plain FP32
     SIMT policy (register-blocked shared-memory GEMM) beside the step."""
@@ -196,7 +198,7 @@ def policy_rollout(steps: int = 20):
     import torch
     from paper_2606_15846_b300 import flashnav
     from paper_2606_15846_b300 import workloads as W
-    wl = W.config_throughput(n_envs=65536)
+    wl = W.config_throughput(n_envs=n_envs, n_maps=n_maps)
     sim = flashnav.NavSim.from_workload(wl)
     sim.reset(SEED)
     sim.autotune(steps=3)  # one simulator launch shape for the unfused arms
@@ -238,7 +240,8 @@ def policy_rollout(steps: int = 20):
     f32 = out["fp32_simt_policy"]["env_steps_per_s"]
     out["speedup_fused_vs_fp32"] = out["fused_actor_in_step"]["env_steps_per_s"] / f32
     out["speedup_bf16_vs_fp32"] = out["bf16_tensor_core_policy"]["env_steps_per_s"] / f32
-    out["config"] = "65536 envs, 16 maps 256x256, 360 beams, actor 364-256-256-4, sampled actions"
+    out["config"] = (f"{E} envs, {n_maps} maps 256x256, 360 beams, actor 364-256-256-4, "
+                     "sampled actions")
     lib.nav_policy_free(pol)
     return out
 
@@ -874,7 +877,8 @@ def main():
     ap.add_argument("--extras", type=int, default=1,
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
-    ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_forward", "uneven_batch",
+    ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_rollout_one_wave",
+                             "policy_forward", "uneven_batch",
                              "gather_rates",
                              "paper_sensing", "training", "training_rect",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
@@ -893,7 +897,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.only:
-        fn = {"policy_rollout": policy_rollout, "policy_forward": policy_forward,
+        fn = {"policy_rollout": policy_rollout,
+              "policy_rollout_one_wave": lambda: policy_rollout(n_envs=18944, n_maps=4),
+              "policy_forward": policy_forward,
               "uneven_batch": lambda: uneven_batch(eager=args.eager),
               "gather_rates": gather_rates,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
