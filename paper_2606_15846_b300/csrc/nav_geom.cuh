@@ -780,9 +780,34 @@ __device__ __forceinline__ void write_tail(float *row, float x, float y, float t
     row[3] = w;
 }
 
+// An env's inputs to a step (state, next-episode record, action, robot),
+// loaded before the tile's map has landed so that their DRAM latency
+// overlaps the staging.
+struct EnvIn {
+    float x, y, th, gx, gy, dprev;
+    int step;
+    unsigned episode;
+    float4 np;
+    float2 ng, act;
+    RobotDev rb;
+};
+
+__device__ __forceinline__ EnvIn load_env(const StepArgs &A, int e) {
+    EnvIn in;
+    in.x = A.x[e]; in.y = A.y[e]; in.th = A.th[e];
+    in.gx = A.gx[e]; in.gy = A.gy[e]; in.dprev = A.dprev[e];
+    in.step = A.step[e];
+    in.episode = A.episode[e];
+    in.np = A.nxt_pose[e];
+    in.ng = A.nxt_goal[e];
+    in.act = reinterpret_cast<const float2 *>(A.actions)[e];
+    in.rb = A.robots[A.env_robot[e]];
+    return in;
+}
+
 template <bool DYN, class B>
 __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int K, int slot_id,
-                          EnvSlot &slot, DynEnv *dmain, DynEnv *dfin) {
+                          EnvSlot &slot, DynEnv *dmain, DynEnv *dfin, const EnvIn &in) {
     const int e = slot.env;
     const int nd = DYN ? A.p.n_dyn : 0;
     const int D = A.p.n_sectors > 0 ? A.p.n_sectors : K; // range features per row
@@ -811,18 +836,18 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         slot.prep = 1;
         slot.ep = 0;
     } else {
-        x = A.x[e]; y = A.y[e]; th = A.th[e];
-        gx = A.gx[e]; gy = A.gy[e]; dprev = A.dprev[e];
-        step = A.step[e];
-        episode = A.episode[e];
+        x = in.x; y = in.y; th = in.th;
+        gx = in.gx; gy = in.gy; dprev = in.dprev;
+        step = in.step;
+        episode = in.episode;
         // the next episode's start, read with the state (used on a reset)
-        const float4 np = A.nxt_pose[e];
-        const float2 ng = A.nxt_goal[e];
+        const float4 np = in.np;
+        const float2 ng = in.ng;
         if (DYN)
             for (int q = 0; q < nd; ++q) ob[q] = A.dyn[(size_t)e * nd + q];
-        const RobotDev rb = A.robots[A.env_robot[e]];
+        const RobotDev rb = in.rb;
         // a1: clamp and map the normalised action onto the preset's bounds
-        const float2 act = reinterpret_cast<const float2 *>(A.actions)[e];
+        const float2 act = in.act;
         const float a0 = fminf(fmaxf(act.x, -1.0f), 1.0f);
         const float a1 = fminf(fmaxf(act.y, -1.0f), 1.0f);
         v = rb.v_min + ((a0 + 1.0f) * 0.5f) * (rb.v_max - rb.v_min);

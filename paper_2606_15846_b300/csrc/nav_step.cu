@@ -305,8 +305,9 @@ __device__ void ray_phase_refill(const StepArgs &A, const V &view, const MapDev 
             if (xt && !fin)
                 *reinterpret_cast<__nv_bfloat16 *>(xt + act_swz(R.o, k)) =
                     __float2bfloat16_rn(xscale ? c * __ldg(xscale + k) : c);
-            // visits (exact: both counts are integers below 2^24)
-            const unsigned v = 1u + (unsigned)(R.kM + R.km);
+            // visits (exact: both counts are integers below 2^24), only when
+            // counted or captured
+            const unsigned v = (A.stats || A.dbg_range) ? 1u + (unsigned)(R.kM + R.km) : 0u;
             if (!fin && A.dbg_range) {
                 int hit = -2;
                 if (R.stopped) {
@@ -358,11 +359,11 @@ template <bool DYN, bool MARCH, bool REFILL, class V>
 __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const MapDev &M,
                                          const TileDev &T, int K, const float2 *sbeam,
                                          EnvSlot *slots, int *fin_slot, int *n_fin, DynEnv *sdyn,
-                                         RayOrigin *org, int *next_chunk) {
+                                         RayOrigin *org, int *next_chunk, const EnvIn &pre) {
     const int tid = threadIdx.x;
     constexpr bool kRefill = REFILL && !DYN && !MARCH && has_dist<V>::value;
     if (tid < T.env_count) {
-        env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1]);
+        env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1], pre);
         if constexpr (kRefill) {
             const EnvSlot &es = slots[tid];
             set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[tid]);
@@ -461,11 +462,13 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
                 sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
             beam_tab = T.tab;
         }
+        EnvIn pre{};
         if (tid < T.env_count) {
             const int e = A.perm[T.env_begin + tid];
             slots[tid].env = e;
             slots[tid].obs_off = A.obs_off[e];
             slots[tid].ray_off = A.ray_off[e];
+            if (A.mode == 0) pre = load_env(A, e); // overlaps the map's staging
         }
         bool ok = true;
         if (copy) {
@@ -484,16 +487,16 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         if (tid == 0) staged_map = mode == kMapGlobal || mode == kMapGlobalBytes ? -1 : T.map;
         if (mode == kMapSharedBytes)
             run_tile<DYN, MARCH, REFILL>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, org, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk, pre);
         else if (mode == kMapSharedBits)
             run_tile<DYN, MARCH, REFILL>(A, BitsShared{sbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, org, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk, pre);
         else if (mode == kMapGlobalBytes)
             run_tile<DYN, MARCH, REFILL>(A, BytesGlobal{A.dist + M.dist_off, M.byte_stride}, M, T, K, sbeam,
-                                 slots, fin_slot, &n_fin, sdyn, org, &next_chunk);
+                                 slots, fin_slot, &n_fin, sdyn, org, &next_chunk, pre);
         else
             run_tile<DYN, MARCH, REFILL>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
-                          &n_fin, sdyn, org, &next_chunk);
+                          &n_fin, sdyn, org, &next_chunk, pre);
         __syncthreads();
         if (tid == 0) cur = atomicAdd(&A.tile_queue[0], 1);
     }
@@ -664,11 +667,13 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
                 sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
             beam_tab = T.tab;
         }
+        EnvIn pre{};
         if (tid < T.env_count) {
             const int e = A.perm[T.env_begin + tid];
             slots[tid].env = e;
             slots[tid].obs_off = A.obs_off[e];
             slots[tid].ray_off = A.ray_off[e];
+            if (A.mode == 0) pre = load_env(A, e); // overlaps the map's staging
         }
         // rows beyond the tile's envs: zero (their outputs are not used)
         for (int p = tid; p < (kActMaxEnvs - T.env_count) * kActKChunks * 8; p += blockDim.x) {
@@ -687,7 +692,7 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
         if (__syncthreads_or(!ok)) break;
         const BytesShared view{sbytes, M.byte_stride};
         if (tid < T.env_count) {
-            env_phase<false>(A, view, M, K, tid, slots[tid], nullptr, nullptr);
+            env_phase<false>(A, view, M, K, tid, slots[tid], nullptr, nullptr, pre);
             const EnvSlot &es = slots[tid];
             set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[tid]);
             act_tail(xt, P, tid, K, A.obs + es.obs_off);
@@ -831,8 +836,9 @@ __global__ void __launch_bounds__(128) env_kernel(const StepArgs A, int n_envs) 
     slot.env = e;
     slot.obs_off = A.obs_off[e];
     slot.ray_off = A.ray_off[e];
+    const EnvIn pre = A.mode == 0 ? load_env(A, e) : EnvIn{};
     env_phase<false>(A, BitsGlobal{A.bits + M.word_off, M.pitch * 32}, M, K, 0, slot, nullptr,
-                     nullptr);
+                     nullptr, pre);
     if (slot.prep) prep_next(A, M, e, slot.ep);
     A.ray_main[e] = make_float4(slot.xc, slot.yc, slot.st, slot.ct);
     if (slot.fin) {
