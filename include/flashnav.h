@@ -120,7 +120,9 @@ int nav_num_envs(const nav_handle *h);
 int64_t nav_obs_size(const nav_handle *h);
 
 /* Resets every env (episode 0) from the counter RNG keyed by seed and writes
- * the first observation to obs_dev (nav_obs_size floats). */
+ * the first observation to obs_dev (nav_obs_size floats); also writes each
+ * env's next-episode record (episode 1), which a step that ends an episode
+ * takes instead of drawing the reset on its critical path. */
 int nav_reset(nav_handle *h, uint64_t seed, float *obs_dev);
 
 /* One simulator step (Eq. 7): A_t -> X_{t+1} -> R_{t+1} -> (c, r, delta)
@@ -183,7 +185,10 @@ int nav_sync(nav_handle *h, int timeout_ms);
  *   f8  [n_envs][8] float: x, y, theta, v, w, goal_x, goal_y, d_prev
  *   i2  [n_envs][2] int32: step counter, episode counter
  *   dyn [n_envs][n_dyn][4] float (x, y, vx, vy) or NULL
- * nav_set_state also sets the RNG seed used by later resets. */
+ * nav_set_state also sets the RNG seed used by later resets, and rewrites
+ * every env's next-episode record (the spawn pose, goal and initial goal
+ * distance its next reset takes, a function of seed, env and episode + 1)
+ * from the new episode counters. */
 int nav_get_state(nav_handle *h, float *f8_host, int32_t *i2_host, float *dyn_host);
 int nav_set_state(nav_handle *h, uint64_t seed, const float *f8_host, const int32_t *i2_host,
                   const float *dyn_host);
@@ -254,9 +259,12 @@ int nav_get_tile_order(const nav_handle *h, int *order);
  * random actions: first tile_envs x block_threads x max_regs, with chunked
  * and (when eligible) refilled lanes, then the
  * staging mode and shared-memory budget for the best shape, then the tile
- * order, then the split step when eligible.  It restores the
- * state and keeps the fastest candidate.  Synchronous.  best_ms (host, may be
- * NULL) receives the winner's mean step time. */
+ * order, then the split step when eligible; last, the four fastest distinct
+ * settings again with four times the steps and the L2 flushed between steps
+ * (a 160 MiB device scratch, allocated on the first call and kept by the
+ * handle).  It restores the state and keeps the fastest candidate of that
+ * last pass.  Synchronous.  best_ms (host, may be NULL) receives the
+ * winner's mean step time with the L2 flushed. */
 int nav_autotune(nav_handle *h, int steps, float *best_ms);
 
 /* Writes n_envs uniform [-1, 1]^2 actions keyed by (seed, env, step) to
