@@ -149,21 +149,32 @@ __device__ __forceinline__ bool span_blocked(const V &v, int j, int i0, int i1) 
     }
     return false;
 }
+// With distance bytes: a cell at distance d has every cell within d - 1
+// columns of it free, so the span's middle cell is read first (d beyond the
+// half-span clears the whole span with one lookup), and otherwise the scan
+// steps d cells at a time from the span's first cell; both give the answer
+// of the cell-by-cell test.
+template <class V> __device__ __forceinline__ bool dist_span_blocked(const V &v, int c0, int n) {
+    const int h = n >> 1;
+    const int dm = v.dist_at(c0 + h);
+    if (dm == 0) return true;
+    if (dm > n - h) return false;
+    for (int k = 0; k <= n;) {
+        const int d = v.dist_at(c0 + k);
+        if (d == 0) return true;
+        k += d;
+    }
+    return false;
+}
 template <>
 __device__ __forceinline__ bool span_blocked<BytesShared>(const BytesShared &v, int j, int i0,
                                                           int i1) {
-    const int c0 = cell_index(v, i0, j);
-    for (int k = 0; k <= i1 - i0; ++k)
-        if (!v.c[c0 + k]) return true;
-    return false;
+    return dist_span_blocked(v, cell_index(v, i0, j), i1 - i0);
 }
 template <>
 __device__ __forceinline__ bool span_blocked<BytesGlobal>(const BytesGlobal &v, int j, int i0,
                                                           int i1) {
-    const int c0 = cell_index(v, i0, j);
-    for (int k = 0; k <= i1 - i0; ++k)
-        if (!v.free_at(c0 + k)) return true;
-    return false;
+    return dist_span_blocked(v, cell_index(v, i0, j), i1 - i0);
 }
 
 // Is any cell of row j, columns [i0, i1], blocked (occupied or off-map)?
@@ -801,7 +812,7 @@ __device__ __forceinline__ EnvIn load_env(const StepArgs &A, int e) {
     in.np = A.nxt_pose[e];
     in.ng = A.nxt_goal[e];
     in.act = reinterpret_cast<const float2 *>(A.actions)[e];
-    in.rb = A.robots[A.env_robot[e]];
+    in.rb = A.env_rb[e];
     return in;
 }
 

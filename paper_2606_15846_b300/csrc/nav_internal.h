@@ -78,8 +78,10 @@ struct StepArgs {
     const int *env_map, *env_tab, *env_robot, *env_cs;
     const long long *obs_off, *ray_off;
     const RobotDev *robots;
+    const RobotDev *env_rb; // [n_envs] each env's robot record (robots[env_robot[e]])
     const TileDev *tiles;
     const int *perm;
+    const int *tile_env; // [n_tiles][kMaxTileEnvs] envs of each tile, or null: perm
     int n_tiles;
     int max_tile_envs; // envs of the largest tile
     int *tile_queue; // [0] next tile to hand out, [1] CTAs finished; zero between launches

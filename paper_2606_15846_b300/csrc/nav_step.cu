@@ -446,6 +446,8 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         __syncthreads();
         const int tile = tile_id;
         if (tile >= A.n_tiles) break;
+        // the tile's env (read with its record: one dependent load less)
+        const int e_tile = A.tile_env && tid < kMaxTileEnvs ? A.tile_env[tile * kMaxTileEnvs + tid] : -1;
         const TileDev T = A.tiles[tile];
         const MapDev M = A.maps[T.map];
         const int K = A.tab_k[T.tab];
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         }
         EnvIn pre{};
         if (tid < T.env_count) {
-            const int e = A.perm[T.env_begin + tid];
+            const int e = A.tile_env ? e_tile : A.perm[T.env_begin + tid];
             slots[tid].env = e;
             slots[tid].obs_off = A.obs_off[e];
             slots[tid].ray_off = A.ray_off[e];
