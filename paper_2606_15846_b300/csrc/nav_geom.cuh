@@ -541,25 +541,29 @@ __device__ __forceinline__ void put_range(const StepArgs &A, float *row, int k, 
 // ---------------------------------------------------------------------------
 // Footprints (Sec. 2.2.3 collision check; Tables 8-9 presets)
 // ---------------------------------------------------------------------------
-template <bool DYN, class B>
+// WARP: the 32 lanes of a warp call it together for one env (same
+// arguments) and test its rows in parallel, lane l the rows j0 + l, j0 + l
+// + 32, ...; the answer (any row blocked) is the same.
+template <bool DYN, bool WARP = false, class B>
 __device__ bool disc_blocked(const B &bits, const MapDev &M, float xc, float yc, float rc,
                              const DynEnv *de, bool static_clear = false) {
     const int j0 = (int)floorf(yc - rc);
     const int j1 = (int)ceilf(yc + rc) - 1;
-    for (int j = j0; j <= j1; ++j) {
+    bool hit = false;
+    for (int j = j0 + (WARP ? (int)(threadIdx.x & 31) : 0); j <= j1 && !hit; j += WARP ? 32 : 1) {
         int a, b;
         if (!disc_row(xc, yc, rc, j, a, b)) continue;
-        if (!static_clear && row_blocked(bits, M, j, a, b)) return true;
-        if (DYN && dyn_row(*de, j, a, b)) return true;
+        if (!static_clear && row_blocked(bits, M, j, a, b)) hit = true;
+        else if (DYN && dyn_row(*de, j, a, b)) hit = true;
     }
-    return false;
+    return WARP ? __any_sync(kFull, hit) : hit;
 }
 
 // Open rectangle (half-length hl along the heading (ct, st), half-width hw,
 // cell units) against closed cells: per row slab [j, j+1], the x-extent of
 // the polygon within the slab is the hull of its vertices inside the slab
 // and its edges' crossings of y = j and y = j + 1.
-template <bool DYN, class B>
+template <bool DYN, bool WARP = false, class B>
 __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc, float st,
                              float ct, float hl, float hw, const DynEnv *de,
                              bool static_clear = false) {
@@ -578,7 +582,8 @@ __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc,
     }
     const int j0 = (int)floorf(ymin);
     const int j1 = (int)ceilf(ymax) - 1;
-    for (int j = j0; j <= j1; ++j) {
+    bool hit = false;
+    for (int j = j0 + (WARP ? (int)(threadIdx.x & 31) : 0); j <= j1 && !hit; j += WARP ? 32 : 1) {
         const float lo = (float)j, hi = (float)j + 1.0f;
         float xlo = INFINITY, xhi = -INFINITY;
 #pragma unroll
@@ -606,10 +611,10 @@ __device__ bool rect_blocked(const B &bits, const MapDev &M, float xc, float yc,
         }
         if (!(xlo <= xhi)) continue;
         const int a = (int)floorf(xlo), b = (int)ceilf(xhi) - 1;
-        if (!static_clear && row_blocked(bits, M, j, a, b)) return true;
-        if (DYN && dyn_row(*de, j, a, b)) return true;
+        if (!static_clear && row_blocked(bits, M, j, a, b)) hit = true;
+        else if (DYN && dyn_row(*de, j, a, b)) hit = true;
     }
-    return false;
+    return WARP ? __any_sync(kFull, hit) : hit;
 }
 
 // ---------------------------------------------------------------------------
@@ -816,7 +821,9 @@ __device__ __forceinline__ EnvIn load_env(const StepArgs &A, int e) {
     return in;
 }
 
-template <bool DYN, class B>
+// WARP: all 32 lanes of a warp run the same env (same values, so their
+// stores agree) and test the footprint's rows in parallel.
+template <bool DYN, bool WARP = false, class B>
 __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int K, int slot_id,
                           EnvSlot &slot, DynEnv *dmain, DynEnv *dfin, const EnvIn &in) {
     const int e = slot.env;
@@ -927,9 +934,9 @@ __device__ void env_phase(const StepArgs &A, const B &bits, const MapDev &M, int
         if (clear && (!DYN || dmain->n == 0))
             coll = false;
         else if (rb.shape == 0)
-            coll = disc_blocked<DYN>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, clear);
+            coll = disc_blocked<DYN, WARP>(bits, M, xc, yc, rb.radius * M.inv_res, dmain, clear);
         else
-            coll = rect_blocked<DYN>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
+            coll = rect_blocked<DYN, WARP>(bits, M, xc, yc, st, ct, (0.5f * rb.length) * M.inv_res,
                                      (0.5f * rb.width) * M.inv_res, dmain, clear);
         // a7: goal test, reward, flags
         const float ddx = gx - x, ddy = gy - y;

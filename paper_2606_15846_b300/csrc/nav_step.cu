@@ -362,11 +362,22 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
                                          RayOrigin *org, int *next_chunk, const EnvIn &pre) {
     const int tid = threadIdx.x;
     constexpr bool kRefill = REFILL && !DYN && !MARCH && has_dist<V>::value;
-    if (tid < T.env_count) {
-        env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1], pre);
+    // without moving discs, one warp per env (its lanes test the footprint's
+    // rows in parallel; `pre` holds the inputs of the warp's first env); with
+    // them, one thread per env (`pre`: that env's inputs), since the discs'
+    // motion and stamps would run on every lane of the warp
+    const int warp = DYN ? tid : tid >> 5, nw = DYN ? (int)blockDim.x : (int)(blockDim.x >> 5);
+    for (int q = warp; q < T.env_count; q += nw) {
+        if (q == warp) {
+            env_phase<DYN, !DYN>(A, view, M, K, q, slots[q], &sdyn[2 * q], &sdyn[2 * q + 1], pre);
+        } else {
+            // tiles with more envs than warps: the later envs load their own
+            const EnvIn in = A.mode == 0 ? load_env(A, slots[q].env) : EnvIn{};
+            env_phase<DYN, !DYN>(A, view, M, K, q, slots[q], &sdyn[2 * q], &sdyn[2 * q + 1], in);
+        }
         if constexpr (kRefill) {
-            const EnvSlot &es = slots[tid];
-            set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[tid]);
+            const EnvSlot &es = slots[q];
+            set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[q]);
         }
     }
     __syncthreads();
@@ -464,13 +475,19 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
                 sbeam[k] = make_float2(A.beam_c[toff + k], A.beam_s[toff + k]);
             beam_tab = T.tab;
         }
-        EnvIn pre{};
         if (tid < T.env_count) {
             const int e = A.tile_env ? e_tile : A.perm[T.env_begin + tid];
             slots[tid].env = e;
             slots[tid].obs_off = A.obs_off[e];
             slots[tid].ray_off = A.ray_off[e];
-            if (A.mode == 0) pre = load_env(A, e); // overlaps the map's staging
+        }
+        // the inputs of the env whose phase this thread's warp (or, with
+        // moving discs, this thread) runs first, loaded before the map has
+        // landed so that their latency overlaps it
+        EnvIn pre{};
+        if ((DYN ? tid : tid >> 5) < T.env_count && A.mode == 0) {
+            const int q = DYN ? tid : tid >> 5;
+            pre = load_env(A, A.tile_env ? A.tile_env[tile * kMaxTileEnvs + q] : A.perm[T.env_begin + q]);
         }
         bool ok = true;
         if (copy) {
