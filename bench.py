@@ -48,7 +48,10 @@ def _counters(launch):
             entries = json.load(f)["captures"]
     except (OSError, ValueError, KeyError):
         return None, None
-    key = lambda l: (l[0], l[1], l[3], l[4], l[5])
+    # byte_cells 1 (distance bytes) and 3 (bytes when they fit in shared
+    # memory) stage the same maps when the cap holds the captured bytes
+    cells = lambda c: 1 if c == 3 else c
+    key = lambda l: (l[0], l[1], l[3], cells(l[4]), l[5])
     for e in entries:
         if key(e["launch"]) == key(launch) and launch[2] >= e.get("smem_min", e["launch"][2]):
             return float(e["dram_bytes_per_launch"]), float(e["warp_inst_per_launch"]) / float(
