@@ -459,3 +459,81 @@ def test_overlapped_draws_skip_the_slots_being_written(env, size, pending, lo, h
     # the safe set is covered roughly uniformly
     assert len(set(idx.tolist())) > 0.9 * min(2048 - pending, len(idx)) * 0.6
     lib.nav_trainer_free(T)
+
+
+def test_overlapped_schedule_matches_serial_schedule(env):
+    """Producer-consumer pipeline (Sec. 3.3) against the serial schedule it
+    replaces: four cycles of (insert 1000 transitions, 4 updates), once on
+    one stream and once with every insert on a collector stream running
+    beside the updates on the learner's stream.  The serial run takes the
+    same replay snapshot before its insert (nav_train_overlap), so both runs
+    draw the same batches from the same slots; the weights, the scalars and
+    the counts must then agree, up to the summation order of the loss sums'
+    atomics, which a race on the replay (an update reading a slot while the
+    concurrent insert writes it, or reading the live replay size) would
+    break."""
+    flashnav, torch = env
+    lib = flashnav.load()
+    cfg = flashnav.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(cfg))
+    cfg.obs_dim, cfg.hidden, cfg.n_hidden, cfg.ipap_features = 34, 100, 4, 30
+    cfg.batch, cfg.replay_capacity, cfg.seed, cfg.weight_decay = 512, 8192, 7, 1e-3
+    rng = np.random.default_rng(11)
+
+    def chunk(n):
+        return [torch.from_numpy(a).cuda() for a in (
+            rng.uniform(0, 6, (n, 34)).astype(np.float32),
+            rng.uniform(-1, 1, (n, 2)).astype(np.float32),
+            rng.normal(0, 1, n).astype(np.float32),
+            rng.choice([0, 0, 0, 1, 2], n).astype(np.uint8),
+            rng.uniform(0, 6, (n, 34)).astype(np.float32))]
+
+    N0, E, cycles, utd = 2000, 1000, 4, 4
+    prefill = chunk(N0)
+    data = [chunk(E) for _ in range(cycles)]
+    sa = [34, 100, 100, 100, 100, 4]
+    sc = [36, 100, 100, 100, 100, 2]
+    n_a = sum(a * b + b for a, b in zip(sa[:-1], sa[1:]))
+    n_c = sum(a * b + b for a, b in zip(sc[:-1], sc[1:]))
+    learn, coll = torch.cuda.Stream(), torch.cuda.Stream()
+    SL, SC = C.c_void_p(learn.cuda_stream), C.c_void_p(coll.cuda_stream)
+    out = []
+    for overlapped in (False, True):
+        T = C.c_void_p()
+        assert lib.nav_trainer_create(C.byref(cfg), C.byref(T)) == 0
+        assert lib.nav_train_insert(T, *[_p(d) for d in prefill], None, N0, SL) == 0
+        idx = []
+        for c in range(cycles):
+            assert lib.nav_train_overlap(T, E, SL) == 0
+            if overlapped:
+                fork, join = torch.cuda.Event(), torch.cuda.Event()
+                fork.record(learn)
+                coll.wait_event(fork)
+                assert lib.nav_train_insert(T, *[_p(d) for d in data[c]], None, E, SC) == 0
+                assert lib.nav_train_update(T, utd, SL) == 0
+                join.record(coll)
+                learn.wait_event(join)
+            else:
+                assert lib.nav_train_insert(T, *[_p(d) for d in data[c]], None, E, SL) == 0
+                assert lib.nav_train_update(T, utd, SL) == 0
+            assert lib.nav_train_overlap(T, 0, SL) == 0
+            learn.synchronize()
+            idx.append(_io(lib, T, 20, 512, np.int32))
+        rs, cu, au = C.c_int64(), C.c_int64(), C.c_int64()
+        assert lib.nav_trainer_counts(T, C.byref(rs), C.byref(cu), C.byref(au)) == 0
+        out.append(dict(counts=(rs.value, cu.value, au.value), idx=np.stack(idx),
+                        actor=_io(lib, T, 0, n_a), c1=_io(lib, T, 1, n_c), c2=_io(lib, T, 2, n_c),
+                        t1=_io(lib, T, 3, n_c), t2=_io(lib, T, 4, n_c), scalars=_io(lib, T, 24, 16)))
+        lib.nav_trainer_free(T)
+    ser, ovl = out
+    assert ser["counts"] == ovl["counts"] == (N0 + cycles * E, cycles * utd, cycles * utd // 2)
+    # the same batches, and none of them touches the slots of its cycle's insert
+    assert np.array_equal(ser["idx"], ovl["idx"])
+    for c in range(cycles):
+        head = N0 + c * E
+        assert not (set(ovl["idx"][c].tolist()) & set(range(head, head + E)))
+    for k in ("actor", "c1", "c2", "t1", "t2"):
+        e = _rel(ovl[k], ser[k])
+        print(f"overlapped vs serial {k}: rel {e:.2e}")
+        assert e < 1e-5, (k, e)
+    assert abs(float(ovl["scalars"][12]) - float(ser["scalars"][12])) < 1e-6  # beta
