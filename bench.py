@@ -527,10 +527,19 @@ def training_run(seconds: float, robot: str = "disc"):
     the time at which the deterministic policy first reaches each success
     threshold on 1000 held-out maps (evaluation time included), and the share
     of held-out episodes a perfect planner could reach within the horizon."""
+    from paper_2606_15846_b300 import flashnav
     from paper_2606_15846_b300 import train as TR
     cfg = TR.TrainConfig(robot=robot, n_envs=16384, utd=16, time_budget_s=seconds, threshold=1.0)
-    res = TR.train(cfg, log=lambda *a: None)
+    res = TR.train(cfg, log=lambda *a: None, keep_policy=True)
     hist = res["history"]
+    # the final policy on the held-out episodes through the three policy
+    # paths: BF16 tensor-core GEMMs, plain FP32, and the actor inside the
+    # step kernel (deterministic actions; BF16 and FP32 round differently)
+    pol = res["policy"]
+    final = {"bf16_tensor_cores": TR.evaluate_policy(cfg, pol, fp32=False)[0],
+             "fp32_simt": TR.evaluate_policy(cfg, pol, fp32=True)[0],
+             "fused_actor_in_step": TR.evaluate_policy_fused(cfg, pol)[0]}
+    flashnav.load().nav_policy_free(pol)
     reach = TR.reachable_fraction(cfg)
     times = {}
     for thr in (0.25, 0.50, 0.75, 1.00):
@@ -539,6 +548,7 @@ def training_run(seconds: float, robot: str = "disc"):
     best = max(h["success"] for h in hist)
     hit = [h["t"] for h in hist if h["success"] >= reach["upper"]]
     return {"seconds_to_success": times, "best_success": best,
+            "final_policy_success": final,
             "reachable_share": reach, "seconds_to_reachable_share": hit[0] if hit else None,
             "budget_s": seconds, "env_steps": res["env_steps"], "cycle_ms": res["cycle_ms"],
             "reactive_controller_success": TR.evaluate_reactive(cfg)[0],
@@ -578,7 +588,11 @@ def compact(extras: dict) -> dict:
             c[f"train_cfg5_{robot}_s"] = {**{k: r(v, 3) for k, v in t["seconds_to_success"].items()},
                                           "best": r(t["best_success"], 3),
                                           "reachable": r(t["reachable_share"]["upper"], 3),
-                                          "to_reachable": r(t["seconds_to_reachable_share"], 3)}
+                                          "to_reachable": r(t["seconds_to_reachable_share"], 3),
+                                          "final_bf16_fp32_fused": [
+                                              r(t["final_policy_success"][k], 3) for k in
+                                              ("bf16_tensor_cores", "fp32_simt",
+                                               "fused_actor_in_step")]}
     return c
 
 

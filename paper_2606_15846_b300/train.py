@@ -191,6 +191,40 @@ def evaluate_policy(cfg: TrainConfig, pol, fp32: bool = False):
     return succ.value / cfg.n_eval, ret.value / cfg.n_eval
 
 
+def evaluate_policy_fused(cfg: TrainConfig, pol):
+    """The same evaluation through the actor inside the step kernel
+    (nav_rollout_fused, one launch per env step, deterministic actions): the
+    collector form of the policy in the loop, scored on the same episodes."""
+    import torch
+    lib = F.load()
+    _, eval_wl = make_workloads(cfg)
+    ev = F.NavSim.from_workload(eval_wl)
+    D = obs_features(cfg)
+    tc = F.nav_train_cfg()
+    lib.nav_train_default_cfg(C.byref(tc))
+    tc.obs_dim, tc.batch, tc.replay_capacity = D + 4, 128, 256
+    T = C.c_void_p()
+    assert lib.nav_trainer_create(C.byref(tc), C.byref(T)) == 0
+    S = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ev._bind_stream()
+    obs = ev.new_obs()
+    act = torch.empty(cfg.n_eval, 2, device="cuda")
+    rew = torch.empty(cfg.n_eval, device="cuda")
+    done = torch.empty(cfg.n_eval, dtype=torch.uint8, device="cuda")
+    ev.reset(777, obs)
+    assert lib.nav_eval_begin(T, cfg.n_eval, S) == 0
+    for t in range(200):
+        rc = lib.nav_rollout_fused(ev._h, pol, 1, 0, 0, t, _p(obs), _p(act), _p(rew), _p(done),
+                                   1 if t else 0)
+        if rc:
+            raise F.NavError(rc, "nav_rollout_fused")
+        assert lib.nav_eval_accumulate(T, _p(rew), _p(done), cfg.n_eval, S) == 0
+    succ, ret = C.c_double(), C.c_double()
+    assert lib.nav_eval_result(T, cfg.n_eval, C.byref(succ), C.byref(ret), S) == 0
+    lib.nav_trainer_free(T)
+    return succ.value / cfg.n_eval, ret.value / cfg.n_eval
+
+
 def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
     """Runs FastDSAC until the threshold or the time budget.  With
     keep_policy the result also holds the trained nav_policy handle
