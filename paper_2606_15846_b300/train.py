@@ -62,6 +62,7 @@ class TrainConfig:
     occupancy: float = 0.10   # paper setting: occupied fraction of the stand-in map
     corridors: bool = False   # paper setting: corridor walls in the stand-in map
     alpha_init: float = 0.001
+    target_entropy: float = -1.0  # of the tanh-squashed actions (2 dims)
 
 
 def paper_config(robot: str = "turtlebot2", algo: str = "fastdsac", **kw) -> TrainConfig:
@@ -244,6 +245,7 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
         cfg.weight_decay
     tc.ipap_features = ipap
     tc.alpha_init = cfg.alpha_init
+    tc.target_entropy = cfg.target_entropy
     tc.policy_freq, tc.reward_scale = cfg.policy_freq, cfg.reward_scale
     tc.algo = 1 if cfg.algo == "fastsac" else 0
     pol = C.c_void_p()
