@@ -806,8 +806,12 @@ struct nav_trainer {
           *eps_new = nullptr, *eps_next = nullptr;
     float *y = nullptr, *ym = nullptr, *znoise = nullptr, *dq[2] = {}, *dlogp = nullptr,
           *dout = nullptr;
-    float *dH = nullptr, *dX[2] = {};
-    bf16 *g16 = nullptr, *gT16 = nullptr, *dZ16 = nullptr, *dZT16 = nullptr;
+    // backward scratch per chain: the twin critics' backward passes run
+    // concurrently on two streams (chain 0 also serves the actor)
+    float *dH[2] = {}, *dX[2] = {};
+    bf16 *g16[2] = {}, *gT16[2] = {}, *dZ16[2] = {}, *dZT16[2] = {};
+    cudaStream_t st2 = nullptr;          // second stream of the per-layer twin-critic chains
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float *scal = nullptr; // [0] log_alpha [1] sbar [2..3] alpha Adam [4..7] critic acc
                            // [8..9] actor acc [11] last beta gradient [12] beta
                            // [13..14] its Adam moments [15] its gradient accumulator
@@ -860,20 +864,22 @@ int tfail(nav_trainer *t, int code, const std::string &m) {
 // sums), then the gradient of the layer's input dZ W, gated by LeakyReLU'
 // into the next dZ.
 int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 *XT, bool wgrad,
-                 float *dX, int ldx, cudaStream_t st) {
+                 float *dX, int ldx, cudaStream_t st, int ch = 0) {
     const int B = T->B, H = T->H, Hp = T->Hp;
     const int last = net.n_layers - 1;
     const int n_out = net.layer[last].out;
     int rc = 0;
-    launch_pdl(k_grad_to_bf16, blocks((long long)B * 8), 256, 0, st, dout, B, n_out, 8, T->g16, T->gT16);
+    bf16 *g16 = T->g16[ch], *gT16 = T->gT16[ch], *dZ16 = T->dZ16[ch], *dZT16 = T->dZT16[ch];
+    float *dH = T->dH[ch];
+    launch_pdl(k_grad_to_bf16, blocks((long long)B * 8), 256, 0, st, dout, B, n_out, 8, g16, gT16);
     const dim3 tb(32, 8), tg((H + 31) / 32, (B + 31) / 32);
     for (int l = last; l >= 0; --l) {
         Layer &L = net.layer[l];
         const bool top = l == last;
-        const bf16 *G = top ? T->g16 : T->dZ16;
+        const bf16 *G = top ? g16 : dZ16;
         const int ldg = top ? 8 : Hp;
-        const bf16 *GT = top ? T->gT16 : T->dZT16;
-        const float *G32 = top ? dout : T->dH;
+        const bf16 *GT = top ? gT16 : dZT16;
+        const float *G32 = top ? dout : dH;
         const bf16 *inT = l == 0 ? XT : T->ht16[s][l - 1];
         if (wgrad) {
             rc |= launch_gemm_bf16_splitk(GT, B, inT, B, L.out, L.in, B, L.gW, L.in, T->status,
@@ -881,9 +887,9 @@ int mlp_backward(nav_trainer *T, Mlp &net, const float *dout, int s, const bf16 
             launch_pdl(k_colsum, blocks(L.out, 32), dim3(32, 8), 0, st, G32, B, L.out, L.gb);
         }
         if (l > 0) {
-            rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, H, L.out, nullptr, 0, T->dH, H,
+            rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, H, L.out, nullptr, 0, dH, H,
                                    nullptr, 0, nullptr, 0, T->status, st);
-            launch_pdl(k_leaky_bwd, tg, tb, 0, st, T->dH, T->h16[s][l - 1], B, H, Hp, T->dZ16, T->dZT16);
+            launch_pdl(k_leaky_bwd, tg, tb, 0, st, dH, T->h16[s][l - 1], B, H, Hp, dZ16, dZT16);
         } else if (dX) {
             rc |= launch_gemm_bf16(G, ldg, L.WT16, L.ld_out, B, L.in, L.out, nullptr, 0, dX, ldx,
                                    nullptr, 0, nullptr, 0, T->status, st);
@@ -958,6 +964,9 @@ void nav_trainer_free(nav_trainer *t) {
         t->qt[i].release();
     }
     for (void *p : t->mem) cudaFree(p);
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
+    if (t->st2) cudaStreamDestroy(t->st2);
     delete t;
 }
 
@@ -1046,11 +1055,16 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->znoise, B);
     TA(T->dlogp, B);
     TA(T->dout, B * 4);
-    TA(T->g16, B * 8);
-    TA(T->gT16, 8 * B);
-    TA(T->dH, B * H);
-    TA(T->dZ16, B * T->Hp);
-    TA(T->dZT16, B * H);
+    for (int ch = 0; ch < 2; ++ch) {
+        TA(T->g16[ch], B * 8);
+        TA(T->gT16[ch], 8 * B);
+        TA(T->dH[ch], B * H);
+        TA(T->dZ16[ch], B * T->Hp);
+        TA(T->dZT16[ch], B * H);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&T->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_join, cudaEventDisableTiming);
     TA(T->scal, 16);
     TA(T->status, 1);
     TA(T->ctr, 8);
@@ -1267,6 +1281,18 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
 // The launches of n critic updates (and the actor updates that fall among
 // them) on `st`; every value that changes from update to update is read from
 // the device counters, so the sequence can be captured once and replayed.
+// The twin critics' per-layer chains run side by side: fork2 makes the
+// second stream wait for the work `st` has queued, join2 makes `st` wait for
+// the second stream's (events, so a graph capture records both branches).
+void fork2(nav_trainer *T, cudaStream_t st) {
+    cudaEventRecord(T->ev_fork, st);
+    cudaStreamWaitEvent(T->st2, T->ev_fork, 0);
+}
+void join2(nav_trainer *T, cudaStream_t st) {
+    cudaEventRecord(T->ev_join, T->st2);
+    cudaStreamWaitEvent(st, T->ev_join, 0);
+}
+
 int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
     const int B = T->B;
@@ -1295,18 +1321,28 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                     1u, T->a_next, T->logp_next, T->eps_next, st);
         launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
                                                                 T->ldc, T->Xnc);
-        for (int i = 0; i < 2; ++i) rc |= fwd(T, T->qt[i], T->Xnc, 3, false, T->tq[i], st);
+        // target critics side by side (activation slots 1 and 2: the online
+        // critics overwrite them only after the targets are formed)
+        fork2(T, st);
+        rc |= fwd(T, T->qt[1], T->Xnc, 2, false, T->tq[1], T->st2);
+        rc |= fwd(T, T->qt[0], T->Xnc, 1, false, T->tq[0], st);
+        join2(T, st);
         launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
                                              T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
                                              T->ctr, T->y, T->ym, T->znoise);
-        for (int i = 0; i < 2; ++i) {
-            rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], st);
-            launch_pdl(k_critic_grad, blocks(B), 256, 0, st, T->qo[i], T->y, T->ym, T->scal + 1, B,
+        fork2(T, st);
+        for (int i = 1; i >= 0; --i) {
+            cudaStream_t si = i ? T->st2 : st;
+            rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], si);
+            launch_pdl(k_critic_grad, blocks(B), 256, 0, si, T->qo[i], T->y, T->ym, T->scal + 1, B,
                                                      c.huber_delta, T->dq[i], T->scal + 4);
         }
+        join2(T, st);
         launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
-        for (int i = 0; i < 2; ++i)
-            rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, st);
+        fork2(T, st);
+        rc |= mlp_backward(T, T->q[1], T->dq[1], 2, T->XcT, true, nullptr, 0, T->st2, 1);
+        rc |= mlp_backward(T, T->q[0], T->dq[0], 1, T->XcT, true, nullptr, 0, st, 0);
+        join2(T, st);
         {
             Mlp *qs[2] = {&T->q[0], &T->q[1]};
             rc |= launch_adam_fused(qs, nullptr, 2, 1, c.lr_critic, c.beta1, c.beta2, T->corr,
@@ -1323,13 +1359,17 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                         0u, T->a_new, T->logp_new, T->eps_new, st);
             launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xo, T->ld, T->a_new, B,
                                                                     T->od, T->ldc, T->Xa);
-            for (int i = 0; i < 2; ++i) rc |= fwd(T, T->q[i], T->Xa, 1 + i, false, T->qa[i], st);
+            fork2(T, st);
+            rc |= fwd(T, T->q[1], T->Xa, 2, false, T->qa[1], T->st2);
+            rc |= fwd(T, T->q[0], T->Xa, 1, false, T->qa[0], st);
+            join2(T, st);
             launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
             launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
                                                     B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
-            for (int i = 0; i < 2; ++i)
-                rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, nullptr, false, T->dX[i], T->ldc,
-                                   st);
+            fork2(T, st);
+            rc |= mlp_backward(T, T->q[1], T->dq[1], 2, nullptr, false, T->dX[1], T->ldc, T->st2, 1);
+            rc |= mlp_backward(T, T->q[0], T->dq[0], 1, nullptr, false, T->dX[0], T->ldc, st, 0);
+            join2(T, st);
             launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
             rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
