@@ -556,6 +556,22 @@ def training_run(seconds: float, robot: str = "disc"):
                       "maps, batch 4096, 16 updates per env step, eval every 1 s"}
 
 
+def training_cycle(robot: str = "disc", seconds: float = 3.0):
+    """Config 5's training cycle (one collector step of 16384 envs and 16
+    updates of the 364-256-256 networks, batch 4096), serial and with the
+    collector on a second stream beside the updates (Sec. 3.3): device time
+    per cycle from graph replays after a short run of each."""
+    from paper_2606_15846_b300 import train as TR
+    out = {}
+    for name, ov, cap in (("serial", False, 0), ("overlapped", True, -1),
+                          ("overlapped_uncapped", True, 0), ("overlapped_cap74", True, 74)):
+        cfg = TR.TrainConfig(robot=robot, n_envs=16384, utd=16, time_budget_s=seconds,
+                             threshold=2.0, overlap=ov, collector_ctas=cap, eval_every_s=1e9)
+        out[name + "_ms"] = TR.train(cfg, log=lambda *a: None)["cycle_ms"]
+    out["config"] = f"{robot} robot, 16384 envs, 16 updates per env step, batch 4096"
+    return out
+
+
 def compact(extras: dict) -> dict:
     """Headline numbers of the extra measurements (the full records go to
     stderr), short enough to stay in a truncated log's tail."""
@@ -593,6 +609,9 @@ def compact(extras: dict) -> dict:
                                               r(t["final_policy_success"][k], 3) for k in
                                               ("bf16_tensor_cores", "fp32_simt",
                                                "fused_actor_in_step")]}
+    tc = extras.get("training_cycle_config5")
+    if tc:
+        c["cycle_cfg5_ms"] = {"serial": r(tc["serial_ms"]), "overlapped": r(tc["overlapped_ms"])}
     return c
 
 
@@ -876,6 +895,7 @@ def run_gpu(args):
                 for robot in ("disc", "rect"):
                     ex[f"training_config5_{robot}"] = training_run(min(args.train_seconds, 30.0),
                                                                    robot)
+                ex["training_cycle_config5"] = training_cycle()
             print(json.dumps(ex), file=sys.stderr, flush=True)
             line["extras"] = compact(ex)
         print(json.dumps(line), flush=True)
@@ -897,7 +917,7 @@ def main():
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_rollout_one_wave",
                              "policy_forward", "uneven_batch",
                              "gather_rates",
-                             "paper_sensing", "training", "training_rect",
+                             "paper_sensing", "training", "training_rect", "training_cycle",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
                              "learner_update", "table2"],
                     help="run one of the extra measurements alone")
@@ -924,6 +944,7 @@ def main():
               "table2": lambda: table2(args.train_seconds, args.seeds),
               "training": lambda: training_run(args.train_seconds),
               "training_rect": lambda: training_run(args.train_seconds, "rect"),
+              "training_cycle": training_cycle,
               "training_paper": lambda: training_paper(args.train_seconds),
               "training_paper_go2": lambda: training_paper(args.train_seconds, "go2"),
               "training_paper_fastsac": lambda: training_paper(args.train_seconds, "turtlebot2",

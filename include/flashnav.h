@@ -152,6 +152,17 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host,
  * the copies).  Synchronises the handle's stream. */
 int nav_set_host_pipeline(nav_handle *h, int parts);
 
+/* Cap on the persistent CTAs of the fused tiled step kernels (no paper
+ * counterpart): max_ctas > 0 launches at most that many (each still takes
+ * tiles from the queue until none are left, so every env is stepped and the
+ * results are unchanged); 0 (the default) fills every SM.  For a collector
+ * that runs beside other kernels (the overlapped collector / learner of
+ * Sec. 3.3): a capped step leaves SMs to the learner instead of holding the
+ * whole GPU while it runs.  The split step ignores the cap.  Synchronises
+ * the handle's stream. */
+int nav_set_grid_cap(nav_handle *h, int max_ctas);
+int nav_get_grid_cap(const nav_handle *h, int *max_ctas);
+
 /* nav_step_host without any device allocation (the paper has no counterpart;
  * this is for callers that may not allocate device memory after start-up,
  * such as a robot control loop or embedded process that sizes its GPU memory

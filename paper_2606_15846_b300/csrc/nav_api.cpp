@@ -1056,6 +1056,20 @@ int nav_set_host_pipeline(nav_handle *h, int parts) {
     return build_tiles(h);
 }
 
+int nav_set_grid_cap(nav_handle *h, int max_ctas) {
+    if (!h || max_ctas < 0) return NAV_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    h->cfg.max_ctas = max_ctas;
+    return NAV_OK;
+}
+
+int nav_get_grid_cap(const nav_handle *h, int *max_ctas) {
+    if (!h || !max_ctas) return NAV_E_INVAL;
+    *max_ctas = h->cfg.max_ctas;
+    return NAV_OK;
+}
+
 int nav_sync(nav_handle *h, int timeout_ms) {
     if (!h) return NAV_E_INVAL;
     cudaEvent_t ev;

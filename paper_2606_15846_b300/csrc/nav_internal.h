@@ -138,6 +138,7 @@ struct LaunchCfg {
     int split = 0;         // 1: env kernel + all-maps-resident ray kernel when eligible
     int order = 0;         // tile queue order: 0 map size x beams, 1 sampled ray cost
     int refill = 0;        // 1: tiled kernel with refilled lanes (exact traversal, no discs)
+    int max_ctas = 0;      // > 0: at most this many persistent CTAs (the rest of the GPU free)
 };
 
 // Launches one step (or reset) of every tile on `stream`: persistent CTAs,

@@ -1090,7 +1090,8 @@ int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
     cudaError_t err = (cudaError_t)occupancy(fn, smem, cfg.block_threads, n_sm, per_sm);
     if (err != cudaSuccess) return (int)err;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
-    const int grid = std::min(a.n_tiles, n_sm * per_sm);
+    int grid = std::min(a.n_tiles, n_sm * per_sm);
+    if (cfg.max_ctas > 0) grid = std::min(grid, cfg.max_ctas);
     void *args[] = {const_cast<StepArgs *>(&a)};
     err = cudaLaunchKernel(fn, dim3(grid), dim3(cfg.block_threads), args, smem, s);
     if (err != cudaSuccess) return (int)err;

@@ -24,7 +24,7 @@ EXPORTS = [
     "nav_num_envs", "nav_obs_size", "nav_reset", "nav_step", "nav_step_host", "nav_sync",
     "nav_get_state", "nav_set_state", "nav_set_debug", "nav_get_debug", "nav_set_stats",
     "nav_get_stats", "nav_set_host_pipeline", "nav_set_launch", "nav_get_launch",
-    "nav_set_tile_order", "nav_get_tile_order",
+    "nav_set_tile_order", "nav_get_tile_order", "nav_set_grid_cap", "nav_get_grid_cap",
     "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
     "nav_gather_probe",
@@ -116,6 +116,8 @@ def load():
         "nav_get_launch": (I, [P, P, P, P, P, P, P]),
         "nav_set_tile_order": (I, [P, I]),
         "nav_get_tile_order": (I, [P, P]),
+        "nav_set_grid_cap": (I, [P, I]),
+        "nav_get_grid_cap": (I, [P, P]),
         "nav_autotune": (I, [P, I, P]),
         "nav_uniform_actions": (I, [P, U64, C.c_uint32, P]),
         "nav_graph_capture": (I, [P, I, P, P, P, P, P]),
@@ -348,6 +350,16 @@ class NavSim:
 
     def set_host_pipeline(self, parts: int):
         self._check(load().nav_set_host_pipeline(self._h, parts))
+
+    def set_grid_cap(self, max_ctas: int):
+        """At most max_ctas persistent CTAs for the tiled step (0: every SM)."""
+        self._bind_stream()
+        self._check(load().nav_set_grid_cap(self._h, max_ctas))
+
+    def get_grid_cap(self) -> int:
+        v = C.c_int()
+        self._check(load().nav_get_grid_cap(self._h, C.byref(v)))
+        return v.value
 
     def get_launch(self):
         v = [C.c_int() for _ in range(6)]

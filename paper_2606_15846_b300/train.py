@@ -55,6 +55,7 @@ class TrainConfig:
     steps_per_sync: int = 1
     graph: bool = True        # capture collector + updates in one CUDA graph once learning runs
     overlap: bool = False     # collector of step t + 1 on a second stream beside step t's updates
+    collector_ctas: int = -1  # overlapped: the step kernel's CTA cap (-1: one per SM, 0: none)
     algo: str = "fastdsac"    # or "fastsac" (C51 critics, Table 5)
     policy_freq: int = 2      # critic updates per actor update
     reward_scale: float = 0.4
@@ -283,6 +284,10 @@ def train(cfg: TrainConfig, log=print, keep_policy: bool = False):
     sim.autotune(steps=5)
     ev.reset(777, ev_obs)
     ev.autotune(steps=5)
+    if cfg.overlap and cfg.collector_ctas != 0:
+        # the overlapped collector's step leaves SMs to the concurrent updates
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sim.set_grid_cap(n_sm if cfg.collector_ctas < 0 else cfg.collector_ctas)
     sim.reset(cfg.seed + 100, obs[0])
     assert lib.nav_trainer_sync_policy(T, pol, S) == 0
     history = []

@@ -76,11 +76,14 @@ def _compare_debug(sim, ref, tag):
 
 
 def run_parity(mods, wl, n_steps, seed=1, want_final=True, launch=None, threads=8,
-               check_state_every=1, autotune=False, tile_order=None):
+               check_state_every=1, autotune=False, tile_order=None, grid_cap=0):
     flashnav, oracle, torch = mods
     sim = flashnav.NavSim.from_workload(wl)
     if launch:
         sim.set_launch(*launch)
+    if grid_cap:
+        sim.set_grid_cap(grid_cap)
+        assert sim.get_grid_cap() == grid_cap
     if tile_order is not None:
         sim.set_tile_order(tile_order)
         assert sim.get_tile_order() == tile_order
@@ -556,3 +559,10 @@ def test_rollout_workload_full_size(mods):
     360 beams, autotuned launch; reset and two steps compared in full."""
     wl = W.config_throughput(n_envs=65536)
     run_parity(mods, wl, 2, seed=31, want_final=False, autotune=True, threads=16)
+
+
+@pytest.mark.parametrize("cap,launch", [(3, (4, 256, 0, 64, 1, 4)), (5, (8, 512, 0, 40, 1, 2))])
+def test_capped_grid(mods, cap, launch):
+    """A step kernel capped at a few persistent CTAs (the overlapped
+    collector's setting) takes every tile from the queue: same results."""
+    run_parity(mods, W.config_small(n_envs=37), 60, seed=12, launch=launch, grid_cap=cap)
