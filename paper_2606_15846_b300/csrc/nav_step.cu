@@ -362,22 +362,27 @@ __device__ __forceinline__ void run_tile(const StepArgs &A, const V &view, const
                                          RayOrigin *org, int *next_chunk, const EnvIn &pre) {
     const int tid = threadIdx.x;
     constexpr bool kRefill = REFILL && !DYN && !MARCH && has_dist<V>::value;
-    // without moving discs, one warp per env (its lanes test the footprint's
-    // rows in parallel; `pre` holds the inputs of the warp's first env); with
-    // them, one thread per env (`pre`: that env's inputs), since the discs'
-    // motion and stamps would run on every lane of the warp
-    const int warp = DYN ? tid : tid >> 5, nw = DYN ? (int)blockDim.x : (int)(blockDim.x >> 5);
-    for (int q = warp; q < T.env_count; q += nw) {
-        if (q == warp) {
-            env_phase<DYN, !DYN>(A, view, M, K, q, slots[q], &sdyn[2 * q], &sdyn[2 * q + 1], pre);
-        } else {
-            // tiles with more envs than warps: the later envs load their own
-            const EnvIn in = A.mode == 0 ? load_env(A, slots[q].env) : EnvIn{};
-            env_phase<DYN, !DYN>(A, view, M, K, q, slots[q], &sdyn[2 * q], &sdyn[2 * q + 1], in);
-        }
-        if constexpr (kRefill) {
-            const EnvSlot &es = slots[q];
-            set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[q]);
+    if constexpr (DYN) {
+        // with moving discs, one thread per env (`pre`: that env's inputs):
+        // the discs' motion and stamps would otherwise run on every lane
+        if (tid < T.env_count)
+            env_phase<DYN>(A, view, M, K, tid, slots[tid], &sdyn[2 * tid], &sdyn[2 * tid + 1], pre);
+    } else {
+        // one warp per env (its lanes test the footprint's rows in parallel;
+        // `pre` holds the inputs of the warp's first env)
+        const int warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+        for (int q = warp; q < T.env_count; q += nw) {
+            if (q == warp) {
+                env_phase<DYN, true>(A, view, M, K, q, slots[q], nullptr, nullptr, pre);
+            } else {
+                // tiles with more envs than warps: the later envs load their own
+                const EnvIn in = A.mode == 0 ? load_env(A, slots[q].env) : EnvIn{};
+                env_phase<DYN, true>(A, view, M, K, q, slots[q], nullptr, nullptr, in);
+            }
+            if constexpr (kRefill) {
+                const EnvSlot &es = slots[q];
+                set_origin(view, M, es.xc, es.yc, es.st, es.ct, es.obs_off, es.ray_off, org[q]);
+            }
         }
     }
     __syncthreads();
