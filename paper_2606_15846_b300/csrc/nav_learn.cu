@@ -797,8 +797,10 @@ struct nav_trainer {
     bf16 *Xo = nullptr, *Xn = nullptr, *Xc = nullptr, *Xnc = nullptr, *Xa = nullptr;
     bf16 *XoT = nullptr, *XcT = nullptr;
     float *rew = nullptr, *term = nullptr;
-    // activations per hidden layer: [0] actor, [1] q0, [2] q1, [3] scratch
-    bf16 *h16[4][kMaxLayers - 1] = {}, *ht16[4][kMaxLayers - 1] = {};
+    // activations per hidden layer: [0] actor, [1] q0, [2] q1, [3] scratch,
+    // [4] [5] the target critics (per-layer path: their forward runs beside
+    // the online critics')
+    bf16 *h16[6][kMaxLayers - 1] = {}, *ht16[6][kMaxLayers - 1] = {};
     float *Lraw = nullptr, *dXa = nullptr; // raw Eq. 2 ranges of obs; actor input gradient
     unsigned *mask[4][kMaxLayers - 1] = {}; // fused passes: LeakyReLU' sign bits per slot
     float *out_a = nullptr, *out_an = nullptr, *qo[2] = {}, *tq[2] = {}, *qa[2] = {};
@@ -811,7 +813,8 @@ struct nav_trainer {
     float *dH[2] = {}, *dX[2] = {};
     bf16 *g16[2] = {}, *gT16[2] = {}, *dZ16[2] = {}, *dZT16[2] = {};
     cudaStream_t st2 = nullptr;          // second stream of the per-layer twin-critic chains
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t st3 = nullptr, st4 = nullptr; // online critic 0, target critic 1
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr, ev_join4 = nullptr;
     float *scal = nullptr; // [0] log_alpha [1] sbar [2..3] alpha Adam [4..7] critic acc
                            // [8..9] actor acc [11] last beta gradient [12] beta
                            // [13..14] its Adam moments [15] its gradient accumulator
@@ -964,9 +967,10 @@ void nav_trainer_free(nav_trainer *t) {
         t->qt[i].release();
     }
     for (void *p : t->mem) cudaFree(p);
-    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
-    if (t->ev_join) cudaEventDestroy(t->ev_join);
-    if (t->st2) cudaStreamDestroy(t->st2);
+    for (cudaEvent_t ev : {t->ev_fork, t->ev_join, t->ev_join3, t->ev_join4})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t s : {t->st2, t->st3, t->st4})
+        if (s) cudaStreamDestroy(s);
     delete t;
 }
 
@@ -1028,7 +1032,7 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
     TA(T->XcT, (long long)(T->od + 2) * B);
     TA(T->rew, B);
     TA(T->term, B);
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 6; ++s)
         for (int l = 0; l < T->NH; ++l) {
             TA(T->h16[s][l], B * T->Hp);
             TA(T->ht16[s][l], B * H);
@@ -1063,8 +1067,12 @@ int nav_trainer_create(const nav_train_cfg *cfg, nav_trainer **out) {
         TA(T->dZT16[ch], B * H);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&T->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&T->st3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&T->st4, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_join3, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&T->ev_join4, cudaEventDisableTiming);
     TA(T->scal, 16);
     TA(T->status, 1);
     TA(T->ctr, 8);
@@ -1284,14 +1292,16 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
 // The twin critics' per-layer chains run side by side: fork2 makes the
 // second stream wait for the work `st` has queued, join2 makes `st` wait for
 // the second stream's (events, so a graph capture records both branches).
-void fork2(nav_trainer *T, cudaStream_t st) {
+void fork_to(nav_trainer *T, cudaStream_t st, cudaStream_t to) {
     cudaEventRecord(T->ev_fork, st);
-    cudaStreamWaitEvent(T->st2, T->ev_fork, 0);
+    cudaStreamWaitEvent(to, T->ev_fork, 0);
 }
-void join2(nav_trainer *T, cudaStream_t st) {
-    cudaEventRecord(T->ev_join, T->st2);
-    cudaStreamWaitEvent(st, T->ev_join, 0);
+void join_from(cudaEvent_t ev, cudaStream_t from, cudaStream_t st) {
+    cudaEventRecord(ev, from);
+    cudaStreamWaitEvent(st, ev, 0);
 }
+void fork2(nav_trainer *T, cudaStream_t st) { fork_to(T, st, T->st2); }
+void join2(nav_trainer *T, cudaStream_t st) { join_from(T->ev_join, T->st2, st); }
 
 int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
@@ -1315,34 +1325,38 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
         const dim3 tb(32, 8);
         launch_pdl(k_transpose, dim3((T->od + 2 + 31) / 32, (B + 31) / 32), tb, 0, st, 
             T->Xc, T->ldc, B, T->od + 2, T->XcT, B);
+        // three branches: the online critics' forwards (slots 1, 2, on st3 and
+        // st2) beside the target path on st (next action, the target critics
+        // in slots 4, 5 side by side, the targets)
+        fork_to(T, st, T->st3);
+        fork_to(T, st, T->st2);
+        rc |= fwd(T, T->q[0], T->Xc, 1, true, T->qo[0], T->st3);
+        rc |= fwd(T, T->q[1], T->Xc, 2, true, T->qo[1], T->st2);
         // next action from the current actor (noise step 2 index + 1)
         rc |= fwd(T, T->actor, T->Xn, 3, false, T->out_a, st);
         rc |= launch_actor_head_ctr(T->out_a, B, 1, c.seed ^ 0x5A5Aull, T->ctr, kCtrCritic, 2u,
                                     1u, T->a_next, T->logp_next, T->eps_next, st);
         launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
                                                                 T->ldc, T->Xnc);
-        // target critics side by side (activation slots 1 and 2: the online
-        // critics overwrite them only after the targets are formed)
-        fork2(T, st);
-        rc |= fwd(T, T->qt[1], T->Xnc, 2, false, T->tq[1], T->st2);
-        rc |= fwd(T, T->qt[0], T->Xnc, 1, false, T->tq[0], st);
-        join2(T, st);
+        fork_to(T, st, T->st4);
+        rc |= fwd(T, T->qt[1], T->Xnc, 5, false, T->tq[1], T->st4);
+        rc |= fwd(T, T->qt[0], T->Xnc, 4, false, T->tq[0], st);
+        join_from(T->ev_join4, T->st4, st);
         launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
                                              T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
                                              T->ctr, T->y, T->ym, T->znoise);
-        fork2(T, st);
+        // each online critic: loss gradient (needs the targets) and backward
+        fork_to(T, st, T->st3);
+        fork_to(T, st, T->st2);
         for (int i = 1; i >= 0; --i) {
-            cudaStream_t si = i ? T->st2 : st;
-            rc |= fwd(T, T->q[i], T->Xc, 1 + i, true, T->qo[i], si);
+            cudaStream_t si = i ? T->st2 : T->st3;
             launch_pdl(k_critic_grad, blocks(B), 256, 0, si, T->qo[i], T->y, T->ym, T->scal + 1, B,
                                                      c.huber_delta, T->dq[i], T->scal + 4);
+            rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, si, i);
         }
+        join_from(T->ev_join3, T->st3, st);
         join2(T, st);
         launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
-        fork2(T, st);
-        rc |= mlp_backward(T, T->q[1], T->dq[1], 2, T->XcT, true, nullptr, 0, T->st2, 1);
-        rc |= mlp_backward(T, T->q[0], T->dq[0], 1, T->XcT, true, nullptr, 0, st, 0);
-        join2(T, st);
         {
             Mlp *qs[2] = {&T->q[0], &T->q[1]};
             rc |= launch_adam_fused(qs, nullptr, 2, 1, c.lr_critic, c.beta1, c.beta2, T->corr,
