@@ -1292,16 +1292,18 @@ int fused_update(nav_trainer *T, bool actor_step, cudaStream_t st) {
 // The twin critics' per-layer chains run side by side: fork2 makes the
 // second stream wait for the work `st` has queued, join2 makes `st` wait for
 // the second stream's (events, so a graph capture records both branches).
-void fork_to(nav_trainer *T, cudaStream_t st, cudaStream_t to) {
-    cudaEventRecord(T->ev_fork, st);
-    cudaStreamWaitEvent(to, T->ev_fork, 0);
+int fork_to(nav_trainer *T, cudaStream_t st, cudaStream_t to) {
+    cudaError_t e = cudaEventRecord(T->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, T->ev_fork, 0);
+    return (int)e;
 }
-void join_from(cudaEvent_t ev, cudaStream_t from, cudaStream_t st) {
-    cudaEventRecord(ev, from);
-    cudaStreamWaitEvent(st, ev, 0);
+int join_from(cudaEvent_t ev, cudaStream_t from, cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    return (int)e;
 }
-void fork2(nav_trainer *T, cudaStream_t st) { fork_to(T, st, T->st2); }
-void join2(nav_trainer *T, cudaStream_t st) { join_from(T->ev_join, T->st2, st); }
+int fork2(nav_trainer *T, cudaStream_t st) { return fork_to(T, st, T->st2); }
+int join2(nav_trainer *T, cudaStream_t st) { return join_from(T->ev_join, T->st2, st); }
 
 int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cudaStream_t st) {
     const nav_train_cfg &c = T->cfg;
@@ -1328,8 +1330,8 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
         // three branches: the online critics' forwards (slots 1, 2, on st3 and
         // st2) beside the target path on st (next action, the target critics
         // in slots 4, 5 side by side, the targets)
-        fork_to(T, st, T->st3);
-        fork_to(T, st, T->st2);
+        rc |= fork_to(T, st, T->st3);
+        rc |= fork_to(T, st, T->st2);
         rc |= fwd(T, T->q[0], T->Xc, 1, true, T->qo[0], T->st3);
         rc |= fwd(T, T->q[1], T->Xc, 2, true, T->qo[1], T->st2);
         // next action from the current actor (noise step 2 index + 1)
@@ -1338,24 +1340,24 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                     1u, T->a_next, T->logp_next, T->eps_next, st);
         launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xn, T->ld, T->a_next, B, T->od,
                                                                 T->ldc, T->Xnc);
-        fork_to(T, st, T->st4);
+        rc |= fork_to(T, st, T->st4);
         rc |= fwd(T, T->qt[1], T->Xnc, 5, false, T->tq[1], T->st4);
         rc |= fwd(T, T->qt[0], T->Xnc, 4, false, T->tq[0], st);
-        join_from(T->ev_join4, T->st4, st);
+        rc |= join_from(T->ev_join4, T->st4, st);
         launch_pdl(k_targets, blocks(B), 256, 0, st, T->rew, T->term, T->tq[0], T->tq[1], T->logp_next,
                                              T->scal + 0, B, c.gamma, c.reward_scale, c.seed,
                                              T->ctr, T->y, T->ym, T->znoise);
         // each online critic: loss gradient (needs the targets) and backward
-        fork_to(T, st, T->st3);
-        fork_to(T, st, T->st2);
+        rc |= fork_to(T, st, T->st3);
+        rc |= fork_to(T, st, T->st2);
         for (int i = 1; i >= 0; --i) {
             cudaStream_t si = i ? T->st2 : T->st3;
             launch_pdl(k_critic_grad, blocks(B), 256, 0, si, T->qo[i], T->y, T->ym, T->scal + 1, B,
                                                      c.huber_delta, T->dq[i], T->scal + 4);
             rc |= mlp_backward(T, T->q[i], T->dq[i], 1 + i, T->XcT, true, nullptr, 0, si, i);
         }
-        join_from(T->ev_join3, T->st3, st);
-        join2(T, st);
+        rc |= join_from(T->ev_join3, T->st3, st);
+        rc |= join2(T, st);
         launch_pdl(k_sbar_update, 1, 1, 0, st, T->scal + 1, T->scal + 4, 2 * B, c.tau_b);
         {
             Mlp *qs[2] = {&T->q[0], &T->q[1]};
@@ -1373,17 +1375,17 @@ int update_body(nav_trainer *T, int n_updates, unsigned long long n_critic, cuda
                                         0u, T->a_new, T->logp_new, T->eps_new, st);
             launch_pdl(k_concat, blocks((long long)B * T->ldc), 256, 0, st, T->Xo, T->ld, T->a_new, B,
                                                                     T->od, T->ldc, T->Xa);
-            fork2(T, st);
+            rc |= fork2(T, st);
             rc |= fwd(T, T->q[1], T->Xa, 2, false, T->qa[1], T->st2);
             rc |= fwd(T, T->q[0], T->Xa, 1, false, T->qa[0], st);
-            join2(T, st);
+            rc |= join2(T, st);
             launch_pdl(k_zero, 1, 32, 0, st, T->scal + 8, 2);
             launch_pdl(k_actor_loss, blocks(B), 256, 0, st, T->logp_new, T->qa[0], T->qa[1], T->scal + 0,
                                                     B, T->dlogp, T->dq[0], T->dq[1], T->scal + 8);
-            fork2(T, st);
+            rc |= fork2(T, st);
             rc |= mlp_backward(T, T->q[1], T->dq[1], 2, nullptr, false, T->dX[1], T->ldc, T->st2, 1);
             rc |= mlp_backward(T, T->q[0], T->dq[0], 1, nullptr, false, T->dX[0], T->ldc, st, 0);
-            join2(T, st);
+            rc |= join2(T, st);
             launch_pdl(k_actor_head_bwd, blocks(B), 256, 0, st, T->out_a, T->eps_new, T->dX[0], T->dX[1],
                                                         T->ldc, T->od, T->dlogp, B, T->dout);
             rc |= mlp_backward(T, T->actor, T->dout, 0, T->XoT, true,
