@@ -288,12 +288,15 @@ def policy_forward(rows: int = 65536, calls: int = 20):
     return out
 
 
-def uneven_batch(steps_per_graph: int = 20, replays: int = 5, eager: bool = False):
+def uneven_batch(steps_per_graph: int = 20, replays: int = 5, eager: bool = False,
+                 launch: str = "", tile_order: int = -1):
     """Uneven batch in one persistent launch per step: 16384 envs over 64 maps
     of 128..1024 cells, beams 180/360/720, disc and rectangle robots, 8 moving
     discs per env; autotuned; steps captured in one CUDA graph; L2 flushed
     between graph replays.  eager: the same steps launched one by one (L2
-    flushed before each), for profilers that cannot follow graph launches."""
+    flushed before each), for profilers that cannot follow graph launches.
+    launch / tile_order: a fixed launch shape instead of the autotuner's (to
+    profile the shape the benchmark's own run chose)."""
     import torch
     from paper_2606_15846_b300 import flashnav
     from paper_2606_15846_b300 import workloads as W
@@ -304,7 +307,13 @@ def uneven_batch(steps_per_graph: int = 20, replays: int = 5, eager: bool = Fals
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(s):
         obs = sim.reset(SEED)
-        tune_ms = sim.autotune(steps=3)
+        if launch:
+            sim.set_launch(*[int(v) for v in launch.split(",")])
+            if tile_order >= 0:
+                sim.set_tile_order(tile_order)
+            tune_ms = None
+        else:
+            tune_ms = sim.autotune(steps=3)
         obs = sim.reset(SEED, obs)
         acts = torch.empty(steps_per_graph, E, 2, device="cuda")
         for t in range(steps_per_graph):
@@ -925,6 +934,8 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="learner_update, uneven_batch: eager launches instead of graph "
                          "replays (profiling)")
+    ap.add_argument("--tile-order", type=int, default=-1,
+                    help="uneven_batch with --launch: the tile queue order (0 or 1)")
     ap.add_argument("--launch", default="",
                     help="tile_envs,block_threads,smem_map_bytes,max_regs,byte_cells,split "
                          "(default: autotune)")
@@ -937,7 +948,8 @@ def main():
         fn = {"policy_rollout": policy_rollout,
               "policy_rollout_one_wave": lambda: policy_rollout(n_envs=18944, n_maps=4),
               "policy_forward": policy_forward,
-              "uneven_batch": lambda: uneven_batch(eager=args.eager),
+              "uneven_batch": lambda: uneven_batch(eager=args.eager, launch=args.launch,
+                                                   tile_order=args.tile_order),
               "gather_rates": gather_rates,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
