@@ -339,22 +339,21 @@ void cut_group(int s, int t, int te, int map, int tab, std::vector<TileDev> &out
     cut_group_n(s, t, (t - s + te - 1) / te, map, tab, out);
 }
 
-// Tiles per (map, beam table) group: as many in all as tiles of at most te
-// envs would make (sum of ceil(n_g / te)), shared out in proportion to each
-// group's sampled ray cost (envs x beams x cost per ray on its map), so that
-// the tiles of cheap and dear maps take about equal time; each group gets at
-// least ceil(n_g / kMaxTileEnvs) and at most n_g tiles.
+// Tiles per (map, beam table) group: `total` tiles in all, shared out in
+// proportion to each group's sampled ray cost (envs x beams x cost per ray
+// on its map), so that the tiles of cheap and dear maps take about equal
+// time; each group gets at least ceil(n_g / kMaxTileEnvs) and at most n_g
+// tiles.
 std::vector<int> weighted_tile_counts(const nav_handle *h, const std::vector<int> &perm,
-                                      const std::vector<std::pair<int, int>> &groups, int te) {
+                                      const std::vector<std::pair<int, int>> &groups,
+                                      long long total) {
     const size_t G = groups.size();
     std::vector<int> k(G), lo(G), hi(G);
     std::vector<double> want(G);
-    long long total = 0;
     double cost = 0.0;
     for (size_t g = 0; g < G; ++g) {
         const int n = groups[g].second - groups[g].first;
         const int e = perm[groups[g].first];
-        total += (n + te - 1) / te;
         want[g] = (double)n * h->env_k[e] * h->map_ray_cost[h->env_map[e]];
         cost += want[g];
         lo[g] = (n + kMaxTileEnvs - 1) / kMaxTileEnvs;
@@ -406,7 +405,18 @@ int build_tiles(nav_handle *h) {
         groups.push_back({s, t});
         s = t;
     }
-    const std::vector<int> counts = weighted_tile_counts(h, perm, groups, h->cfg.tile_envs);
+    // as many tiles in all as tiles of at most tile_envs envs make; a count
+    // just short of one wave of resident CTAs (within 10 %) is raised to
+    // the full wave, so that no SM holds fewer tiles than the others (the
+    // tiles shrink a little instead)
+    long long total = 0;
+    for (const auto &gr : groups)
+        total += (gr.second - gr.first + h->cfg.tile_envs - 1) / h->cfg.tile_envs;
+    if (h->par.n_dyn == 0 && !(h->cfg.split && h->split_ok)) {
+        const long long R = step_resident(h->a, h->cfg);
+        if (R > 0 && total < R && 10 * total >= 9 * R) total = std::min<long long>(R, E);
+    }
+    const std::vector<int> counts = weighted_tile_counts(h, perm, groups, total);
     for (size_t g = 0; g < groups.size(); ++g) {
         const int s = groups[g].first;
         cut_group_n(s, groups[g].second, counts[g], h->env_map[perm[s]], h->env_tab[perm[s]],

@@ -145,6 +145,10 @@ struct LaunchCfg {
 // grid = SMs x resident CTAs per SM, capped by the tile count.
 int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream);
 
+// Resident CTAs of the tiled step kernel launch_step would run (SMs x CTAs
+// per SM), 0 if the occupancy query fails.
+int step_resident(const StepArgs &a, const LaunchCfg &cfg);
+
 // Split step: env phase for every env, then the ray kernel (all maps staged
 // in shared memory once per CTA, warps take 32-ray chunks from a queue).
 int launch_step_split(const StepArgs &a, int n_envs, void *stream);

@@ -1078,19 +1078,34 @@ int occupancy(const void *fn, size_t smem, int block, int &n_sm, int &per_sm) {
     return 0;
 }
 
-int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
-    if (a.n_tiles <= 0) return 0;
+// The tiled step kernel launch_step runs for (a, cfg), and its dynamic
+// shared memory.
+const void *step_fn(const StepArgs &a, const LaunchCfg &cfg, size_t &smem) {
     const bool dyn = a.p.n_dyn > 0;
-    const size_t smem = (size_t)a.smem_region_bytes + (size_t)a.max_k * sizeof(float2) +
-                        (dyn ? (size_t)2 * a.max_tile_envs * sizeof(DynEnv) : 0);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    smem = (size_t)a.smem_region_bytes + (size_t)a.max_k * sizeof(float2) +
+           (dyn ? (size_t)2 * a.max_tile_envs * sizeof(DynEnv) : 0);
     const bool march = a.p.sensor == 1;
     // lane refill applies to the exact traversal without moving discs
-    const void *fn = dyn ? (march ? pick_kernel<true, true, false>(cfg.max_regs)
-                                  : pick_kernel<true, false, false>(cfg.max_regs))
-                         : (march ? pick_kernel<false, true, false>(cfg.max_regs)
-                            : cfg.refill ? pick_kernel<false, false, true>(cfg.max_regs)
-                                         : pick_kernel<false, false, false>(cfg.max_regs));
+    return dyn ? (march ? pick_kernel<true, true, false>(cfg.max_regs)
+                        : pick_kernel<true, false, false>(cfg.max_regs))
+               : (march ? pick_kernel<false, true, false>(cfg.max_regs)
+                        : cfg.refill ? pick_kernel<false, false, true>(cfg.max_regs)
+                                     : pick_kernel<false, false, false>(cfg.max_regs));
+}
+
+int step_resident(const StepArgs &a, const LaunchCfg &cfg) {
+    size_t smem = 0;
+    const void *fn = step_fn(a, cfg, smem);
+    int n_sm = 0, per_sm = 0;
+    if (occupancy(fn, smem, cfg.block_threads, n_sm, per_sm) != 0) return 0;
+    return n_sm * per_sm;
+}
+
+int launch_step(const StepArgs &a, const LaunchCfg &cfg, void *stream) {
+    if (a.n_tiles <= 0) return 0;
+    size_t smem = 0;
+    const void *fn = step_fn(a, cfg, smem);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int n_sm = 0, per_sm = 0;
     cudaError_t err = (cudaError_t)occupancy(fn, smem, cfg.block_threads, n_sm, per_sm);
     if (err != cudaSuccess) return (int)err;
