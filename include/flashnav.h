@@ -142,9 +142,10 @@ int nav_step(nav_handle *h, const float *actions_dev, float *obs_dev, float *rew
 /* nav_step with host buffers, synchronous; results identical to nav_step.
  * Device staging buffers are allocated on the first call and kept.  The step
  * runs as nav_set_host_pipeline's number of launches over consecutive env
- * ranges (2 by default), each range's results copied out on a second stream
- * while the next range computes; host buffers should be pinned for the
- * copies to overlap. */
+ * ranges (3 by default), each range's observations copied out on a second
+ * stream while the next range computes, the rewards and flags of all ranges
+ * after the last one; host buffers should be pinned for the copies to
+ * overlap. */
 int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host,
                   float *reward_host, uint8_t *done_host, float *final_obs_host);
 
