@@ -441,11 +441,15 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
     // launch makes exactly n_tiles + gridDim draws; the CTA holding the last
     // one zeroes the queue for the next launch (nobody draws after it).
     const int last_draw = A.n_tiles + (int)gridDim.x - 1;
+    // exactly one tile per CTA (a full wave): CTA b takes tile b and the
+    // queue is not touched (its first draw, an atomic that waits on L2, is
+    // off the path to the tile's map)
+    const bool one_each = A.n_tiles == (int)gridDim.x;
     int cur = 0;
     if (tid == 0) {
         init_copy_barrier(&bar);
         staged_map = -1;
-        cur = atomicAdd(&A.tile_queue[0], 1);
+        cur = one_each ? (int)blockIdx.x : atomicAdd(&A.tile_queue[0], 1);
     }
     // a CTA runs at most n_tiles tiles: a queue left non-zero by a failed
     // launch ends the loop with a status bit instead of running on
@@ -522,7 +526,7 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
             run_tile<DYN, MARCH, REFILL>(A, BitsGlobal{gbits, M.pitch * 32}, M, T, K, sbeam, slots, fin_slot,
                           &n_fin, sdyn, org, &next_chunk, pre);
         __syncthreads();
-        if (tid == 0) cur = atomicAdd(&A.tile_queue[0], 1);
+        if (tid == 0) cur = one_each ? A.n_tiles : atomicAdd(&A.tile_queue[0], 1);
     }
 }
 
