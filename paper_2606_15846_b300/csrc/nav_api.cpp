@@ -160,6 +160,9 @@ struct nav_handle {
     int tiles_cap = 0;
     int *d_tile_env = nullptr; // [tile][kMaxTileEnvs]: the envs of each tile (-1 past its count)
     int tile_env_cap = 0;
+    std::vector<TileDev> tiles_host;  // the main tiles, in queue order
+    int4 *d_tile_stage = nullptr;     // [tile] how its map is staged (refresh_tile_stage)
+    int tile_stage_cap = 0;
     unsigned long long *d_stats = nullptr;
     int2 *d_chunks = nullptr;
     int chunks_cap = 0;
@@ -386,6 +389,8 @@ std::vector<int> weighted_tile_counts(const nav_handle *h, const std::vector<int
 // their number).  The queue runs over the largest tiles first so that the
 // longest CTAs start early: by map size x beams (order 0, ties in map order)
 // or by envs x beams x sampled cells per ray (order 1, ties by map size).
+int refresh_tile_stage(nav_handle *h);
+
 int build_tiles(nav_handle *h) {
     const int E = h->n_envs;
     std::vector<int> perm(E);
@@ -463,6 +468,11 @@ int build_tiles(nav_handle *h) {
     h->a.tiles = h->d_tiles;
     h->a.perm = h->d_perm;
     h->a.tile_env = h->d_tile_env;
+    h->tiles_host = tiles;
+    {
+        const int rs = refresh_tile_stage(h);
+        if (rs != NAV_OK) return rs;
+    }
     h->a.n_tiles = (int)tiles.size();
     h->a.max_tile_envs = 1;
     for (const TileDev &t : tiles) h->a.max_tile_envs = std::max(h->a.max_tile_envs, t.env_count);
@@ -544,6 +554,39 @@ int build_tiles(nav_handle *h) {
 // shared memory when they fit, else distance bytes through L1/L2.  Maps
 // without distance bytes use packed bits.  The shared region is sized for
 // the largest staged map.
+// Per main tile, how its map is staged, so that a CTA starts the copy from
+// the tile's own record instead of after a second load of the map's:
+// {map mode, bytes to copy, byte offset into the bitmap or distance-byte
+// buffer (low, high 32 bits)}.  Rebuilt whenever tiles or map modes change.
+int refresh_tile_stage(nav_handle *h) {
+    const size_t n = h->tiles_host.size();
+    if (n == 0) return NAV_OK;
+    std::vector<int4> st(n);
+    for (size_t t = 0; t < n; ++t) {
+        const MapDev &m = h->maps[h->tiles_host[t].map];
+        long long off = 0;
+        int bytes = 0;
+        if (m.mode == kMapSharedBits) {
+            off = m.word_off * 4;
+            bytes = m.n_words * 4;
+        } else if (m.mode == kMapSharedBytes) {
+            off = m.dist_off;
+            bytes = m.n_bytes;
+        }
+        st[t] = make_int4(m.mode, bytes, (int)(off & 0xffffffffll), (int)(off >> 32));
+    }
+    cudaError_t e = cudaSuccess;
+    if ((int)n > h->tile_stage_cap) {
+        e = h->arena.alloc(&h->d_tile_stage, n);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc(tile stage)");
+        h->tile_stage_cap = (int)n;
+    }
+    e = cudaMemcpy(h->d_tile_stage, st.data(), n * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(tile stage)");
+    h->a.tile_stage = h->d_tile_stage;
+    return NAV_OK;
+}
+
 int set_map_modes(nav_handle *h) {
     int region = 0;
     for (MapDev &m : h->maps) {
@@ -564,7 +607,7 @@ int set_map_modes(nav_handle *h) {
                                    cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(maps)");
     }
-    return NAV_OK;
+    return refresh_tile_stage(h);
 }
 
 int launch(nav_handle *h) {
@@ -1017,6 +1060,7 @@ int nav_step_host(nav_handle *h, const float *actions_host, float *obs_host, flo
             Ap.n_tiles = h->part_tile_off[p + 1] - h->part_tile_off[p];
             Ap.perm = h->d_pperm;
             Ap.tile_env = nullptr;
+            Ap.tile_stage = nullptr;
             const int lrc = launch_args(h, Ap);
             if (lrc != 0) return cuda_fail(h, (cudaError_t)lrc, "step kernel launch (part)");
             e = cudaEventRecord(h->part_ev[p], h->stream);
@@ -1483,6 +1527,7 @@ int nav_rollout_fused(nav_handle *h, nav_policy *p, int n_steps, int mode, uint6
     A.tiles = h->d_act_tiles;
     A.n_tiles = h->act_n_tiles;
     A.tile_env = nullptr;
+    A.tile_stage = nullptr;
     ActArgs P{};
     for (int l = 0; l < 3; ++l) {
         P.W[l] = static_cast<const __nv_bfloat16 *>(net->layer[l].W16);

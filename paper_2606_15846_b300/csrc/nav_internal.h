@@ -82,6 +82,7 @@ struct StepArgs {
     const TileDev *tiles;
     const int *perm;
     const int *tile_env; // [n_tiles][kMaxTileEnvs] envs of each tile, or null: perm
+    const int4 *tile_stage; // [n_tiles] {map mode, bytes, byte offset lo, hi}, or null: maps
     int n_tiles;
     int max_tile_envs; // envs of the largest tile
     int *tile_queue; // [0] next tile to hand out, [1] CTAs finished; zero between launches

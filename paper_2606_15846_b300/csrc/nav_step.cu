@@ -468,15 +468,30 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
         if (tile >= A.n_tiles) break;
         // the tile's env (read with its record: one dependent load less)
         const int e_tile = A.tile_env && tid < kMaxTileEnvs ? A.tile_env[tile * kMaxTileEnvs + tid] : -1;
+        // the tile's staging record, read with the tile's (the copy starts
+        // before the map's own record has arrived)
+        const int4 ts = A.tile_stage ? A.tile_stage[tile] : make_int4(-1, 0, 0, 0);
         const TileDev T = A.tiles[tile];
         const MapDev M = A.maps[T.map];
         const int K = A.tab_k[T.tab];
         const uint32_t *gbits = A.bits + M.word_off;
         const bool fresh = staged_map != T.map;
-        const bool copy = (M.mode == kMapSharedBits || M.mode == kMapSharedBytes) && fresh;
+        const int smode = ts.x >= 0 ? ts.x : M.mode;
+        const bool copy = (smode == kMapSharedBits || smode == kMapSharedBytes) && fresh;
         if (copy && tid == 0) {
-            if (M.mode == kMapSharedBits) stage_map(sbits, gbits, (unsigned)M.n_words * 4u, &bar);
-            else stage_map(sbytes, A.dist + M.dist_off, (unsigned)M.n_bytes, &bar);
+            if (ts.x >= 0) {
+                const long long off = ((long long)(unsigned)ts.w << 32) | (long long)(unsigned)ts.z;
+                const unsigned char *src = smode == kMapSharedBits
+                                               ? reinterpret_cast<const unsigned char *>(A.bits)
+                                               : A.dist;
+                stage_map(smode == kMapSharedBits ? static_cast<void *>(sbits)
+                                                  : static_cast<void *>(sbytes),
+                          src + off, (unsigned)ts.y, &bar);
+            } else if (smode == kMapSharedBits) {
+                stage_map(sbits, gbits, (unsigned)M.n_words * 4u, &bar);
+            } else {
+                stage_map(sbytes, A.dist + M.dist_off, (unsigned)M.n_bytes, &bar);
+            }
         }
         if (T.tab != beam_tab) {
             const int toff = A.tab_off[T.tab];
@@ -511,7 +526,7 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
             if (tid == 0) atomicOr(A.status, kStatusCopyTimeout);
             if (!ok) wait_bitmap(&bar, parity ^ 1u);
         }
-        const int mode = failed ? (int)kMapGlobal : M.mode;
+        const int mode = failed ? (int)kMapGlobal : smode;
         if (tid == 0) staged_map = mode == kMapGlobal || mode == kMapGlobalBytes ? -1 : T.map;
         if (mode == kMapSharedBytes)
             run_tile<DYN, MARCH, REFILL>(A, BytesShared{sbytes, M.byte_stride}, M, T, K, sbeam, slots, fin_slot,
