@@ -377,7 +377,7 @@ int nav_policy_act_counted(nav_policy *p, const float *obs_dev, int64_t obs_stri
  * observation before the network (NULL removes it).  Synchronous. */
 int nav_policy_set_input_scale(nav_policy *p, const float *scale_host);
 
-/* Reactive goal-seeking controller, the fallback policy without learning
+/* Reactive goal-seeking controller, a hand-written baseline policy without learning
  * (no paper counterpart): among beams whose range and both neighbours' exceed
  * 0.6 m, head for the one closest to the goal bearing; turn rate 2 x heading
  * error, speed scaled by the heading error's cosine and the range straight
