@@ -568,6 +568,8 @@ constexpr int kActThreads = 1024;
 constexpr int kActMaxEnvs = 128;                 // rows of the MMA tile
 constexpr unsigned kActChunk = 128u * 128u;      // a 64-wide K chunk of the input tile
 constexpr int kActKChunks = 6;                   // input features <= 384
+constexpr unsigned kActSlot = 2u * kActChunk;    // a weight slot: one K chunk of 256 rows
+constexpr int kActMaxSlots = 4;
 
 __device__ __forceinline__ unsigned long long act_mix64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -607,6 +609,29 @@ __device__ __forceinline__ void act_unit(const ActArgs &P, int u, int &l, int &c
     }
 }
 
+// Weight item i of the actor: layer l, 64-wide K chunk c, the first of its
+// units (u0: both halves of the chunk, units u0 and u0 + 1, when the layer
+// has more than 128 outputs; they lie next to each other in the unit array)
+// and the layer's rows rounded up to 16 (the MMA's N).  Items run over the
+// layers in order, K chunks inner.
+__device__ __forceinline__ void act_item(const ActArgs &P, int i, int &l, int &c, int &u0,
+                                         int &np) {
+    l = 0;
+    u0 = 0;
+    for (;;) {
+        const int nk = (P.in[l] + 63) >> 6, nh = P.out[l] > 128 ? 2 : 1;
+        if (i < nk || l == 2) {
+            c = i;
+            u0 += i * nh;
+            np = (P.out[l] + 15) & ~15;
+            return;
+        }
+        i -= nk;
+        u0 += nk * nh;
+        ++l;
+    }
+}
+
 // One thread per 16-byte piece (8 BF16) of a unit: the weights W[l] [out][ld]
 // rearranged into the 128-byte-swizzled K-major tile the MMAs read (zero
 // beyond the layer's rows and inputs), so that one bulk copy stages a unit.
@@ -640,10 +665,10 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     __shared__ int next_ray;
     __shared__ int tile_id;
     __shared__ __align__(8) unsigned long long bar_map;
-    __shared__ __align__(8) unsigned long long bar_ld[4]; // weight unit landed, per buffer
-    __shared__ __align__(8) unsigned long long bar_w[4];  // MMAs done reading, per buffer
+    __shared__ __align__(8) unsigned long long bar_ld[kActMaxSlots]; // weight item landed, per slot
+    __shared__ __align__(8) unsigned long long bar_w[kActMaxSlots];  // MMAs done reading, per slot
     __shared__ unsigned tmem_slot;
-    // [0, region): the staged map, or during the actor four 16 KiB weight buffers
+    // [0, region): the staged map, or during the actor NS 32 KiB weight slots
     // [region, region + 96 KiB): the actor's input tile (then H1, H2)
     // then the beam table
     // the swizzled tiles need 1024-byte alignment (act_step_smem adds the slack)
@@ -656,17 +681,25 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     const int quad = warp & 3, grp = warp >> 2; // TMEM lane quarter, column group (8 of 32)
     unsigned map_parity = 0;
     int beam_tab = -1;
-    // The weights stream as 16 KiB units (act_unit) from their swizzled copy
-    // by bulk copies into four buffers in the map's region (free once the ray
-    // phase ends), up to four units ahead of the MMAs; thread 0 alone issues
-    // the copies and the MMAs and tracks, per buffer, the phase bits of its
-    // two mbarriers and whether an MMA commit on it is still to be waited for.
+    // The weights stream from their swizzled copy as items (act_item: one
+    // 64-wide K chunk of all of a layer's output rows, up to 32 KiB) by bulk
+    // copies into the NS slots of the map's region (free once the ray phase
+    // ends).  A K chunk's MMAs run at N = the layer's rows (up to 256): an
+    // MMA costs about the same at N 128 as at 256, and each commit drains the
+    // tensor pipe, so one commit per chunk rather than per 128-row half.  A
+    // slot is refilled one item after its MMAs were issued (by then they have
+    // completed, so the refill does not wait on the MMAs just issued).
+    // Thread 0 alone issues the copies and the MMAs and tracks, per slot, the
+    // phase bits of its two mbarriers and whether an MMA commit on it is
+    // still to be waited for.
     unsigned ph_ld = 0u, ph_w = 0u, pend_w = 0u;
-    int nunits = 0;
-    for (int l = 0; l < 3; ++l) nunits += ((P.in[l] + 63) >> 6) * (P.out[l] > 128 ? 2 : 1);
+    int nitems = 0;
+    for (int l = 0; l < 3; ++l) nitems += (P.in[l] + 63) >> 6;
+    const int NS = min(kActMaxSlots, (int)(region / kActSlot)); // >= 2: region >= 64 KiB
+    int next_item = 0;
     if (tid == 0) {
         init_copy_barrier(&bar_map);
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < NS; ++b) {
             init_copy_barrier(&bar_ld[b]);
             init_copy_barrier(&bar_w[b]);
         }
@@ -674,7 +707,7 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     const unsigned tmem = tmem_alloc_cols(&tmem_slot, 256);
     const unsigned tlane = (unsigned)(quad * 32) << 16;
     const unsigned xt_a = smem_addr(xt);
-    const unsigned wb0 = smem_addr(base); // buffer b at wb0 + b * 16 KiB
+    const unsigned wb0 = smem_addr(base); // slot b at wb0 + b * 32 KiB
     // (thread 0) waits for the outstanding MMA commit on buffer b, if any
     auto wait_mma = [&](int b) {
         if ((pend_w >> b) & 1u) {
@@ -683,13 +716,19 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
             pend_w &= ~(1u << b);
         }
     };
-    // (thread 0) stages unit u once its buffer's previous MMAs have completed
-    auto issue_unit = [&](int u) {
-        int l, c, h, rows;
-        act_unit(P, u, l, c, h, rows);
-        wait_mma(u & 3);
-        stage_map(base + (size_t)(u & 3) * kActChunk, P.Wu + (size_t)u * kActChunk,
-                  (unsigned)rows * 128u, &bar_ld[u & 3]);
+    // (thread 0) stages item i once its slot's previous MMAs have completed
+    auto issue_item = [&](int i) {
+        int l, c, u0, np;
+        act_item(P, i, l, c, u0, np);
+        const int s = i % NS;
+        wait_mma(s);
+        stage_map(base + (size_t)s * kActSlot, P.Wu + (size_t)u0 * kActChunk, (unsigned)np * 128u,
+                  &bar_ld[s]);
+    };
+    // (thread 0) stages every item not yet staged whose slot held item x or
+    // an earlier one
+    auto refill = [&](int x) {
+        while (next_item < nitems && next_item - NS <= x) issue_item(next_item++);
     };
     for (;;) {
         if (tid == 0) {
@@ -748,34 +787,35 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
         // the input tile, written by generic stores, is read by the MMAs
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads(); // the map's region is free: the weight buffers
-        int u = 0;
-        if (tid == 0)
-            for (int q = 0; q < 4 && q < nunits; ++q) issue_unit(q);
+        int it = 0;
+        if (tid == 0) {
+            next_item = 0;
+            refill(-1);
+        }
         for (int l = 0; l < 3; ++l) {
             const int out = P.out[l], np = (out + 15) & ~15;
             const bool last = l == 2;
-            const int nk = (P.in[l] + 63) >> 6, nh = out > 128 ? 2 : 1;
+            const int nk = (P.in[l] + 63) >> 6;
             if (tid == 0) {
-                for (int c = 0; c < nk; ++c)
-                    for (int h = 0; h < nh; ++h, ++u) {
-                        const int b = u & 3;
-                        act_wait(smem_addr(&bar_ld[b]), (ph_ld >> b) & 1u, A.status);
-                        ph_ld ^= 1u << b;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const unsigned a = xt_a + c * kActChunk, wbuf = wb0 + (unsigned)b * kActChunk;
-                        const int n = min(128, np - 128 * h);
+                const unsigned idesc = instr_desc(128, np);
+                for (int c = 0; c < nk; ++c, ++it) {
+                    const int b = it % NS;
+                    act_wait(smem_addr(&bar_ld[b]), (ph_ld >> b) & 1u, A.status);
+                    ph_ld ^= 1u << b;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned a = xt_a + c * kActChunk, wbuf = wb0 + (unsigned)b * kActSlot;
 #pragma unroll
-                        for (int k16 = 0; k16 < 4; ++k16)
-                            mma_f16(tmem + 128u * h, smem_desc(a + 32u * k16),
-                                    smem_desc(wbuf + 32u * k16), instr_desc(128, n),
-                                    (c > 0 || k16 > 0) ? 1u : 0u);
-                        mma_commit(smem_addr(&bar_w[b]));
-                        pend_w |= 1u << b;
-                        // four units ahead, into this buffer once these MMAs are done
-                        if (u + 4 < nunits) issue_unit(u + 4);
-                    }
-                // the layer's last MMAs (and so every one of its MMAs) have completed
-                wait_mma((u - 1) & 3);
+                    for (int k16 = 0; k16 < 4; ++k16)
+                        mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(wbuf + 32u * k16), idesc,
+                                (c > 0 || k16 > 0) ? 1u : 0u);
+                    mma_commit(smem_addr(&bar_w[b]));
+                    pend_w |= 1u << b;
+                    refill(it - 1);
+                }
+                // the layer's last MMAs (and so every one of its MMAs) have
+                // completed; the slots they read take the next items
+                wait_mma((it - 1) % NS);
+                refill(it - 1);
             }
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
