@@ -288,6 +288,48 @@ def policy_forward(rows: int = 65536, calls: int = 20):
     return out
 
 
+def step_sizes(steps: int = 300, sizes=(1024, 2048, 4096, 8192, 16384, 32768, 65536)):
+    """The plain step (16 maps 256x256, 360 beams, uniform actions) at batch
+    sizes from 1024 to 65536 envs on one GPU: autotuned launch shape, L2
+    flushed before each step, CUDA events around each step."""
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    from paper_2606_15846_b300 import workloads as W
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for n in sizes:
+        wl = W.config_throughput(n_envs=n)
+        sim = flashnav.NavSim.from_workload(wl)
+        obs = sim.new_obs()
+        rew = torch.empty(n, device="cuda")
+        done = torch.empty(n, dtype=torch.uint8, device="cuda")
+        g = torch.Generator(device="cuda")
+        g.manual_seed(SEED)
+        acts = torch.rand(steps + 20, n, 2, device="cuda", generator=g) * 2 - 1
+        sim.reset(SEED, obs)
+        sim.autotune(steps=12)
+        launch = sim.get_launch()
+        sim.reset(SEED, obs)
+        for t in range(20):
+            sim.step(acts[t], obs, rew, done)
+        stream = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        for t in range(steps):
+            flush.fill_(float(t))
+            ev[t][0].record(stream)
+            sim.step(acts[20 + t], obs, rew, done)
+            ev[t][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        out[str(n)] = {"us_per_step": ms * 1e3, "env_steps_per_s": n / (ms / 1e3),
+                       "launch": list(launch)}
+        del sim, obs, acts
+    out["config"] = "16 maps 256x256, 360 beams, r_max 6 m, uniform actions, L2 flushed"
+    return out
+
+
 def uneven_batch(steps_per_graph: int = 20, replays: int = 5, eager: bool = False,
                  launch: str = "", tile_order: int = -1):
     """Uneven batch in one persistent launch per step: 16384 envs over 64 maps
@@ -924,7 +966,7 @@ def main():
                     help="1: also time the policy-in-the-loop rollout and a training run")
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_rollout_one_wave",
-                             "policy_forward", "uneven_batch",
+                             "policy_forward", "uneven_batch", "step_sizes",
                              "gather_rates",
                              "paper_sensing", "training", "training_rect", "training_cycle",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
@@ -948,6 +990,7 @@ def main():
         fn = {"policy_rollout": policy_rollout,
               "policy_rollout_one_wave": lambda: policy_rollout(n_envs=18944, n_maps=4),
               "policy_forward": policy_forward,
+              "step_sizes": step_sizes,
               "uneven_batch": lambda: uneven_batch(eager=args.eager, launch=args.launch,
                                                    tile_order=args.tile_order),
               "gather_rates": gather_rates,
