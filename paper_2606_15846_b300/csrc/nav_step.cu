@@ -551,11 +551,11 @@ __global__ void __launch_bounds__(512, MINB) step_kernel(const StepArgs A) {
 // on the tile's new observations, on the tensor cores, from shared memory:
 // the observation rows the ray and env phases produce are written, scaled
 // and rounded to BF16, straight into the actor's swizzled input tile; the
-// three layers (in -> H -> H -> 4, LeakyReLU) stream their weights in
-// 16 KiB units of 128 output rows x one 64-wide K chunk, pre-swizzled in
-// global memory (bulk copies issued by one thread into four buffers that
-// reuse the staged map's region, up to four units ahead of the MMAs),
-// accumulate in TMEM (tcgen05.mma, M 128, one thread issuing) and are read
+// three layers (in -> H -> H -> 4, LeakyReLU) stream their weights one
+// 64-wide K chunk of all of a layer's output rows at a time (up to 32 KiB),
+// pre-swizzled in global memory (bulk copies issued by one thread into
+// 32 KiB slots that reuse the staged map's region), accumulate in TMEM
+// (tcgen05.mma, M 128, N up to 256, one thread issuing) and are read
 // back by every warp (tcgen05.ld) for bias, LeakyReLU and the next layer's
 // BF16 tile, written in place; the head turns the last layer's
 // (mean, raw log-std) into the action of each env for the next step,
