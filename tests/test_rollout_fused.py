@@ -70,8 +70,12 @@ def _actor_bf16(params, obs, scale):
     return x
 
 
-@pytest.mark.parametrize("n_envs,n_maps,mode", [(2048, 4, 0), (300, 3, 1), (18944, 16, 0)])
-def test_fused_rollout_lockstep_with_oracle_and_fp64_actor(env, n_envs, n_maps, mode):
+# hidden widths: 256 (the benchmark actor: two 128-row halves per K chunk),
+# 200 (a partial second half) and 96 (one half)
+@pytest.mark.parametrize("n_envs,n_maps,mode,hidden", [(2048, 4, 0, 256), (300, 3, 1, 256),
+                                                       (18944, 16, 0, 256), (1024, 4, 0, 200),
+                                                       (600, 3, 1, 96)])
+def test_fused_rollout_lockstep_with_oracle_and_fp64_actor(env, n_envs, n_maps, mode, hidden):
     flashnav, torch, oracle = env
     lib = flashnav.load()
     wl = W.config_throughput(n_envs=n_envs, n_maps=n_maps)
@@ -79,10 +83,10 @@ def test_fused_rollout_lockstep_with_oracle_and_fp64_actor(env, n_envs, n_maps, 
     sim = flashnav.NavSim.from_workload(wl)
     ref = oracle.OracleSim.from_workload(wl, threads=16)
     h = C.c_void_p()
-    assert lib.nav_policy_create(K + 4, 256, n_envs, 13, C.byref(h)) == 0
+    assert lib.nav_policy_create(K + 4, hidden, n_envs, 13, C.byref(h)) == 0
     w = np.zeros(lib.nav_policy_num_params(h), np.float32)
     assert lib.nav_policy_get_weights(h, w.ctypes.data_as(C.c_void_p)) == 0
-    params = _unpack(w, [K + 4, 256, 256, 4])
+    params = _unpack(w, [K + 4, hidden, hidden, 4])
     scale = _scale(K, wl.max_range)
     assert lib.nav_policy_set_input_scale(h, scale.ctypes.data_as(C.c_void_p)) == 0
     sim.set_debug(True)
