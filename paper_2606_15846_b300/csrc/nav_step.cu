@@ -613,16 +613,30 @@ __device__ __forceinline__ void act_unit(const ActArgs &P, int u, int &l, int &c
 // units (u0: both halves of the chunk, units u0 and u0 + 1, when the layer
 // has more than 128 outputs; they lie next to each other in the unit array)
 // and the layer's rows rounded up to 16 (the MMA's N).  Items run over the
-// layers in order, K chunks inner.
+// layers in order, K chunks inner; the last layer, when all of its K chunks
+// fit one slot (the head's 4 outputs: 2 KiB a chunk), is one item of nc
+// chunks (each commit drains the tensor pipe, so one instead of nc).
+__device__ __forceinline__ bool act_last_whole(const ActArgs &P) {
+    return P.out[2] <= 128 &&
+           (unsigned)((P.in[2] + 63) >> 6) * (unsigned)((P.out[2] + 15) & ~15) * 128u <= kActSlot;
+}
+
+__device__ __forceinline__ int act_items(const ActArgs &P) {
+    return ((P.in[0] + 63) >> 6) + ((P.in[1] + 63) >> 6) +
+           (act_last_whole(P) ? 1 : (P.in[2] + 63) >> 6);
+}
+
 __device__ __forceinline__ void act_item(const ActArgs &P, int i, int &l, int &c, int &u0,
-                                         int &np) {
+                                         int &np, int &nc) {
     l = 0;
     u0 = 0;
     for (;;) {
         const int nk = (P.in[l] + 63) >> 6, nh = P.out[l] > 128 ? 2 : 1;
         if (i < nk || l == 2) {
-            c = i;
-            u0 += i * nh;
+            const bool whole = l == 2 && act_last_whole(P);
+            c = whole ? 0 : i;
+            nc = whole ? nk : 1;
+            u0 += c * nh;
             np = (P.out[l] + 15) & ~15;
             return;
         }
@@ -693,8 +707,8 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     // phase bits of its two mbarriers and whether an MMA commit on it is
     // still to be waited for.
     unsigned ph_ld = 0u, ph_w = 0u, pend_w = 0u;
-    int nitems = 0;
-    for (int l = 0; l < 3; ++l) nitems += (P.in[l] + 63) >> 6;
+    const int nitems = act_items(P);
+    const bool last_whole = act_last_whole(P);
     const int NS = min(kActMaxSlots, (int)(region / kActSlot)); // >= 2: region >= 64 KiB
     int next_item = 0;
     if (tid == 0) {
@@ -718,12 +732,27 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
     };
     // (thread 0) stages item i once its slot's previous MMAs have completed
     auto issue_item = [&](int i) {
-        int l, c, u0, np;
-        act_item(P, i, l, c, u0, np);
+        int l, c, u0, np, nc;
+        act_item(P, i, l, c, u0, np, nc);
         const int s = i % NS;
         wait_mma(s);
-        stage_map(base + (size_t)s * kActSlot, P.Wu + (size_t)u0 * kActChunk, (unsigned)np * 128u,
-                  &bar_ld[s]);
+        if (nc == 1) {
+            stage_map(base + (size_t)s * kActSlot, P.Wu + (size_t)u0 * kActChunk,
+                      (unsigned)np * 128u, &bar_ld[s]);
+        } else {
+            // nc chunks of np rows, each from its own unit, packed in the slot
+            const unsigned b = smem_u32(&bar_ld[s]), part = (unsigned)np * 128u;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                         "r"(part * (unsigned)nc)
+                         : "memory");
+            for (int q = 0; q < nc; ++q)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                    "%2, [%3];" ::"r"(wb0 + (unsigned)s * kActSlot + (unsigned)q * part),
+                    "l"(P.Wu + (size_t)(u0 + q) * kActChunk), "r"(part), "r"(b)
+                    : "memory");
+        }
     };
     // (thread 0) stages every item not yet staged whose slot held item x or
     // an earlier one
@@ -796,18 +825,23 @@ __global__ void __launch_bounds__(kActThreads, 1) act_step_kernel(const StepArgs
             const int out = P.out[l], np = (out + 15) & ~15;
             const bool last = l == 2;
             const int nk = (P.in[l] + 63) >> 6;
+            // chunks per item: all of them for a last layer that is one item
+            const int per = last && last_whole ? nk : 1;
             if (tid == 0) {
                 const unsigned idesc = instr_desc(128, np);
-                for (int c = 0; c < nk; ++c, ++it) {
+                for (int c = 0; c < nk; c += per, ++it) {
                     const int b = it % NS;
                     act_wait(smem_addr(&bar_ld[b]), (ph_ld >> b) & 1u, A.status);
                     ph_ld ^= 1u << b;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const unsigned a = xt_a + c * kActChunk, wbuf = wb0 + (unsigned)b * kActSlot;
+                    for (int q = 0; q < per; ++q) {
+                        const unsigned a = xt_a + (c + q) * kActChunk;
+                        const unsigned wbuf = wb0 + (unsigned)b * kActSlot + (unsigned)(q * np * 128);
 #pragma unroll
-                    for (int k16 = 0; k16 < 4; ++k16)
-                        mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(wbuf + 32u * k16), idesc,
-                                (c > 0 || k16 > 0) ? 1u : 0u);
+                        for (int k16 = 0; k16 < 4; ++k16)
+                            mma_f16(tmem, smem_desc(a + 32u * k16), smem_desc(wbuf + 32u * k16),
+                                    idesc, (c + q > 0 || k16 > 0) ? 1u : 0u);
+                    }
                     mma_commit(smem_addr(&bar_w[b]));
                     pend_w |= 1u << b;
                     refill(it - 1);
