@@ -436,6 +436,33 @@ def gather_rates(reps: int = 10):
     return out
 
 
+def mma_rates(n_mma: int = 1024):
+    """Cost of back-to-back tcgen05.mma (M 128, K 16, BF16) on this GPU by N,
+    and of tcgen05.commit (nav_mma_probe): one CTA per SM, one thread issuing
+    n_mma MMAs with no commit before the last, a commit every 4 MMAs that it
+    waits on, a commit every 4 or every MMA that nobody waits on; ns per MMA
+    (the slowest CTA) and the dense BF16 rate per SM it implies."""
+    import torch
+    from paper_2606_15846_b300 import flashnav
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ns = torch.zeros(sms, dtype=torch.int64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = {}
+    for label, every, wait in (("no_commit", 0, 0), ("commit_every_4_waited", 4, 1),
+                               ("commit_every_4", 4, 0), ("commit_every_1", 1, 0)):
+        row = {}
+        for n in (16, 64, 128, 256):
+            for _ in range(2):
+                flashnav.mma_probe(n, n_mma, every, wait, ns, status)
+            torch.cuda.synchronize()
+            per = float(ns.max().item()) / n_mma
+            row[str(n)] = {"ns_per_mma": per, "tflops_per_sm": 2.0 * 128 * n * 16 / per / 1e3}
+        out[label] = row
+    assert int(status.item()) == 0, "a bounded wait in the MMA probe gave up"
+    out["config"] = f"{sms} CTAs (one per SM), {n_mma} MMAs each, M 128, K 16, BF16 zero operands"
+    return out
+
+
 def paper_sensing(steps: int = 200, launch: str = ""):
     """The paper's sensing (Sec. 2.2.2, Eq. 6, Table 7) on its TurtleBot2
     setting: one shared 10 x 10 m map, 1080 beams over 270 deg to 20 m,
@@ -967,7 +994,7 @@ def main():
     ap.add_argument("--train-seconds", type=float, default=45.0)
     ap.add_argument("--only", default="", choices=["", "policy_rollout", "policy_rollout_one_wave",
                              "policy_forward", "uneven_batch", "step_sizes",
-                             "gather_rates",
+                             "gather_rates", "mma_rates",
                              "paper_sensing", "training", "training_rect", "training_cycle",
                              "training_paper", "training_paper_go2", "training_paper_fastsac",
                              "learner_update", "table2"],
@@ -994,6 +1021,7 @@ def main():
               "uneven_batch": lambda: uneven_batch(eager=args.eager, launch=args.launch,
                                                    tile_order=args.tile_order),
               "gather_rates": gather_rates,
+              "mma_rates": mma_rates,
               "paper_sensing": lambda: paper_sensing(launch=args.launch),
               "learner_update": lambda: learner_update(graphs=not args.eager),
               "table2": lambda: table2(args.train_seconds, args.seeds),

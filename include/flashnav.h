@@ -328,6 +328,24 @@ int nav_gemm_bf16(const void *a_dev, int lda, const void *b_dev, int ldb, int m,
 int nav_gather_probe(int where, const void *table_dev, int64_t bytes, int n_blocks, int iters,
                      uint32_t *sums_dev, void *stream);
 
+/* Tensor-pipe rate probe (measurement, no paper counterpart: the costs that
+ * set how the fused actor of nav_rollout_fused stages its weights).  Each of
+ * n_blocks CTAs has one thread issue n_mma back-to-back tcgen05.mma
+ * (kind::f16, M 128, N n, K 16, BF16 zero operands in shared memory) into
+ * its own 256 TMEM columns, with a tcgen05.commit after every commit_every
+ * MMAs (0: none but the final one) that the thread waits on when wait is 1,
+ * and a final commit it waits on; ns_dev[b] (uint64, caller-owned, n_blocks
+ * entries) receives CTA b's %globaltimer nanoseconds from its first issue
+ * to the final completion.  At most two CTAs share an SM.
+ *   n: a multiple of 16 in [16, 256]; n_mma in [1, 2^20]; commit_every >= 0;
+ *   wait 0 or 1; n_blocks in [1, 1024]
+ *   status_dev (int, caller-owned): bit 0 set when a bounded wait gave up
+ *   (the CTA then waits once more, frees its TMEM and returns)
+ * Launches one kernel on `stream`; NAV_E_INVAL for an argument outside these
+ * ranges. */
+int nav_mma_probe(int n, int n_mma, int commit_every, int wait, int n_blocks,
+                  unsigned long long *ns_dev, int *status_dev, void *stream);
+
 /* Policy network (Sec. 2.1 policy MLP; the FastDSAC actor of Sec. 2.3): a
  * tanh-squashed Gaussian actor obs_dim -> hidden -> hidden -> 4 (mean 2, raw
  * log-std 2) with LeakyReLU (slope 0.01); log sigma = -5 + 5 (tanh(r) + 1)/2,

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "nav_internal.h"
+#include "tc_util.cuh"
 
 namespace flashnav {
 namespace {
@@ -80,8 +81,116 @@ __global__ void __launch_bounds__(kProbeThreads)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-pipe rate probe: the costs behind the weight staging of the fused
+// actor.  One thread of each CTA issues n_mma back-to-back tcgen05.mma
+// (kind::f16, M 128, N n, K 16; A and B are zero BF16 tiles in shared
+// memory with the 128-byte swizzle, 16 KiB of A and 32 KiB of B, the four
+// K steps of one 64-wide chunk in turn) into a TMEM accumulator of 256
+// columns, with a tcgen05.commit after every commit_every MMAs (0: none
+// before the last) that it waits on when `wait` is set, then a final commit
+// and wait; it records the %globaltimer nanoseconds from the first issue to
+// the last completion.  The CTA's ~100 KiB of shared memory keeps at most
+// two CTAs on an SM, so their TMEM allocations (256 columns each) never wait
+// on each other.
+// ---------------------------------------------------------------------------
+constexpr int kMmaProbeThreads = 128;
+constexpr unsigned kMmaProbeSmem = 100u * 1024u;
+
+__device__ __forceinline__ unsigned long long probe_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(kMmaProbeThreads)
+    mma_probe(int n, int n_mma, int commit_every, int wait, unsigned long long *ns,
+              int *status) {
+    extern __shared__ __align__(1024) unsigned char mp_smem[];
+    __shared__ unsigned tslot;
+    __shared__ __align__(8) unsigned long long bar;    // the commits waited on
+    __shared__ __align__(8) unsigned long long bar_nw; // the others (never completes a phase)
+    const unsigned raw = smem_addr(mp_smem);
+    const unsigned base = (raw + 1023u) & ~1023u; // A at base, B at base + 16 KiB
+    unsigned char *tiles = mp_smem + (base - raw);
+    for (unsigned o = threadIdx.x * 16u; o < 48u * 1024u; o += kMmaProbeThreads * 16u)
+        *reinterpret_cast<uint4 *>(tiles + o) = make_uint4(0u, 0u, 0u, 0u);
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tslot)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar_nw)),
+                     "r"((1u << 20) - 1u)
+                     : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tslot;
+    if (threadIdx.x == 0) {
+        const unsigned idesc = instr_desc(128, n);
+        const unsigned b = smem_addr(&bar);
+        unsigned phase = 0;
+        bool ok = true;
+        const unsigned long long t0 = probe_clock_ns();
+        for (int i = 0; i < n_mma; ++i) {
+            mma_f16(tmem, smem_desc(base + 32u * (unsigned)(i & 3)),
+                    smem_desc(base + 16384u + 32u * (unsigned)(i & 3)), idesc, i > 0 ? 1u : 0u);
+            if (commit_every > 0 && (i + 1) % commit_every == 0 && i + 1 < n_mma) {
+                if (wait) {
+                    mma_commit(b);
+                    ok = ok && mbar_wait(b, phase);
+                    phase ^= 1u;
+                } else {
+                    // not waited on: its arrival goes to a barrier whose
+                    // count is never reached, so `bar` holds one pending
+                    // phase at a time and the waits on it are unambiguous
+                    mma_commit(smem_addr(&bar_nw));
+                }
+            }
+        }
+        mma_commit(b);
+        // commits complete in order: this one completes after every MMA
+        ok = ok && mbar_wait(b, phase);
+        const unsigned long long t1 = probe_clock_ns();
+        ns[blockIdx.x] = t1 - t0;
+        if (!ok) {
+            atomicOr(status, 1);
+            mbar_wait(b, phase); // once more (bounded) before the TMEM is freed
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                     : "memory");
+}
+
 } // namespace
 } // namespace flashnav
+
+// C ABI: see include/flashnav.h (nav_mma_probe).
+extern "C" int nav_mma_probe(int n, int n_mma, int commit_every, int wait, int n_blocks,
+                             unsigned long long *ns_dev, int *status_dev, void *stream) {
+    using namespace flashnav;
+    if (n < 16 || n > 256 || (n % 16) != 0) return NAV_E_INVAL;
+    if (n_mma < 1 || n_mma > (1 << 20) || commit_every < 0 || (wait != 0 && wait != 1))
+        return NAV_E_INVAL;
+    if (n_blocks < 1 || n_blocks > 1024 || !ns_dev || !status_dev) return NAV_E_INVAL;
+    if (cudaFuncSetAttribute(mma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMmaProbeSmem) != cudaSuccess)
+        return NAV_E_CUDA;
+    mma_probe<<<n_blocks, kMmaProbeThreads, kMmaProbeSmem, static_cast<cudaStream_t>(stream)>>>(
+        n, n_mma, commit_every, wait, ns_dev, status_dev);
+    return cudaGetLastError() == cudaSuccess ? NAV_OK : NAV_E_CUDA;
+}
 
 // C ABI: see include/flashnav.h (nav_gather_probe).
 extern "C" int nav_gather_probe(int where, const void *table_dev, int64_t bytes, int n_blocks,

@@ -27,7 +27,7 @@ EXPORTS = [
     "nav_set_tile_order", "nav_get_tile_order", "nav_set_grid_cap", "nav_get_grid_cap",
     "nav_autotune", "nav_uniform_actions",
     "nav_graph_capture", "nav_graph_launch", "nav_step_host_noalloc", "nav_gemm_bf16",
-    "nav_gather_probe",
+    "nav_gather_probe", "nav_mma_probe",
     "nav_policy_create", "nav_policy_create_ex", "nav_policy_get_beta", "nav_policy_free",
     "nav_policy_num_params", "nav_policy_get_weights",
     "nav_policy_set_weights", "nav_policy_act", "nav_policy_act_fp32", "nav_policy_act_counted",
@@ -125,6 +125,7 @@ def load():
         "nav_step_host_noalloc": (I, [P, P, P, P, P, P]),
         "nav_gemm_bf16": (I, [P, I, P, I, I, I, I, P, I, P, I, P, I, P, I, P, P]),
         "nav_gather_probe": (I, [I, P, C.c_int64, I, I, P, P]),
+        "nav_mma_probe": (I, [I, I, I, I, I, P, P, P]),
         "nav_policy_create": (I, [I, I, I, U64, P]),
         "nav_policy_create_ex": (I, [I, I, I, I, C.c_float, I, U64, P]),
         "nav_policy_get_beta": (I, [P, P]),
@@ -183,6 +184,16 @@ def gather_probe(where: int, table, nbytes: int, n_blocks: int, iters: int, sums
                                  C.c_void_p(stream))
     if rc != 0:
         raise NavError(rc, "nav_gather_probe: argument out of range or launch failed")
+
+
+def mma_probe(n: int, n_mma: int, commit_every: int, wait: int, ns, status, stream: int = 0):
+    """nav_mma_probe: back-to-back tcgen05.mma (M 128, N n, K 16) from one
+    thread per CTA; `ns` a device int64 tensor of one entry per CTA (the
+    grid is its length), `status` a device int32 tensor of one entry."""
+    rc = load().nav_mma_probe(n, n_mma, commit_every, wait, ns.numel(), _t_ptr(ns),
+                              _t_ptr(status), C.c_void_p(stream))
+    if rc != 0:
+        raise NavError(rc, "nav_mma_probe: argument out of range or launch failed")
 
 
 def params_struct(p) -> nav_params:
